@@ -1,0 +1,580 @@
+/*
+ * rs_oracle.c -- plain CPU oracle (FP64 / complex128) of the dense-block HSS inverse of
+ * arXiv:1303.5466.  TEST INFRASTRUCTURE ONLY: see rs_oracle.h.  Built with
+ * -ffp-contract=off so that its rounding does not depend on the host's FMA support.
+ *
+ * Readings of the paper taken here (the paper is silent or ambiguous on these):
+ *   - grid: cell centres x_g = ((i1+1/2)h, (i2+1/2)h) of [0,1]^2, g = i1 + n i2;
+ *   - tree: binary, depth t splits along x1 when t is even and x2 when t is odd; box j
+ *     of level l has children 2j (lower half) and 2j+1 (upper half) (Sec. 2.2);
+ *   - leaf points ascend in g; a parent's active set is sk(c1) then sk(c2), each
+ *     ascending in g (Sec. 2.2, re-blocking: I_i = I_c1^sk u I_c2^sk);
+ *   - neighbours: same-level boxes whose closed rectangles touch (edge or corner);
+ *     near rows: neighbours' active points strictly inside the proxy circle, in
+ *     (neighbour, active) order; proxy: P points c + R(cos 2 pi j/P, sin 2 pi j/P) with
+ *     R = factor x the larger half-width (Sec. 2.2, equivalent densities);
+ *   - E_i = (R_i F_i^{-1} L_i)^{-1} as in Algorithm 1 line 11 (the "E = R F^{-1} L" of
+ *     Sec. 2.4 contradicts Algorithm 1 and the derivation of Eq. 2.11);
+ *   - the Helmholtz kernel is +(i/4) H0 and the system is put in the symmetric form
+ *     of Eq. (5.6) by the diagonal similarity S = diag(kappa sqrt(b)).
+ */
+#define _DEFAULT_SOURCE
+#ifndef RO_PLANT
+#define RO_PLANT 0
+#endif
+#include "rs_oracle.h"
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int m, k, r, nnear;
+    int64_t* active;   /* m globals                        */
+    int64_t* near;     /* nnear globals                    */
+    int64_t* skel;     /* k globals, ascending             */
+    int* sk_local;     /* k local indices (skeleton order) */
+    int* rs_local;     /* m-k local indices, ascending     */
+    double* T;         /* k x (m-k) scalars                */
+    double* Finv;      /* m x m scalars                    */
+    double* E;         /* k x k scalars                    */
+} ro_box;
+
+struct ro_op {
+    int n, leaf, d;
+    double h, eps;
+    ro_opts opts;
+    int nthreads;
+    double* a;          /* N (diagonal coefficient a(x))            */
+    double* s;          /* N (Helmholtz symmetric scaling kappa sqrt b) */
+    double* b;          /* N (Helmholtz b) or NULL                  */
+    double lap_c0;      /* -h^2/(4 pi): multiplies log r^2          */
+    double lap_self;    /* -(1/2pi) C_h                             */
+    double complex hz_self; /* (i/4) * integral of H0 over the cell */
+    double* pcos;       /* proxy unit circle                        */
+    double* psin;
+    ro_box** lev;       /* lev[l][j], l = 1..d                      */
+    int m0;
+    int64_t* active0;
+    double* root_inv;
+};
+
+/* ------------------------------------------------------------------ geometry */
+
+/* Integer description of box j at level l: x-index bx, y-index by, extents wx, wy in
+ * grid cells.  The bit of j for depth t (MSB first) selects the half at that split. */
+static void box_int(int n, int l, int j, int* bx, int* by, int* wx, int* wy)
+{
+    int x = 0, y = 0, nx = 0, ny = 0;
+    for (int t = 0; t < l; ++t) {
+        int bit = (j >> (l - 1 - t)) & 1;
+        if ((t & 1) == 0) { x = 2 * x + bit; ++nx; } else { y = 2 * y + bit; ++ny; }
+    }
+    *bx = x; *by = y; *wx = n >> nx; *wy = n >> ny;
+}
+
+static void box_center_radius(const ro_op* op, int l, int j, double* cx, double* cy, double* R)
+{
+    int bx, by, wx, wy;
+    box_int(op->n, l, j, &bx, &by, &wx, &wy);
+    double hh = 0.5 * op->h;
+    *cx = (double)((2 * bx + 1) * wx) * hh;
+    *cy = (double)((2 * by + 1) * wy) * hh;
+    int w = wx > wy ? wx : wy;
+    *R = (op->opts.proxy_radius_factor * (double)w) * hh;
+}
+
+/* ------------------------------------------------------------------ quadrature */
+
+double ro_laplace_cell_integral(double h)
+{
+    /* integral of log|y| over [-h/2,h/2]^2 = h^2 (log h - (1/2) log 2 - 3/2 + pi/4),
+     * from the polar form over the eight triangles of the square */
+#if RO_PLANT == 3
+    return -h * h * (log(h) - 0.5 * log(2.0) - 1.5 + M_PI / 4.0);
+#else
+    return h * h * (log(h) - 0.5 * log(2.0) - 1.5 + M_PI / 4.0);
+#endif
+}
+
+void ro_gauss_legendre(int n, double* x, double* w)
+{
+    /* roots of P_n by Newton's method from the Chebyshev-like initial guess; the weight is
+     * 2 / ((1 - z^2) P_n'(z)^2), with P_n' from the three-term recurrence */
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-15) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1; p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void ro_helmholtz_cell_integral(double h, double kappa, int nodes, double* re, double* im)
+{
+    /* integral over the cell of H0(kappa r) = 8 * int_0^{pi/4} int_0^{rho(th)} H0(kappa r) r dr dth,
+     * rho = (h/2)/cos th, and int_0^rho r H0(kappa r) dr = (kappa rho H1(kappa rho) + 2i/pi)/kappa^2 */
+    double* x = (double*)malloc(sizeof(double) * (size_t)nodes);
+    double* w = (double*)malloc(sizeof(double) * (size_t)nodes);
+    ro_gauss_legendre(nodes, x, w);
+    double complex acc = 0.0;
+    for (int i = 0; i < nodes; ++i) {
+        double th = (M_PI / 8.0) * (1.0 + x[i]);
+        double rho = 0.5 * h / cos(th);
+        double z = kappa * rho;
+        double complex H1 = j1(z) + I * y1(z);
+        acc += (M_PI / 8.0) * w[i] * (z * H1 + 2.0 * I / M_PI) / (kappa * kappa);
+    }
+    acc *= 8.0;
+    *re = creal(acc); *im = cimag(acc);
+    free(x); free(w);
+}
+
+/* ------------------------------------------------------------------ matrix entries */
+
+static inline void gxy(const ro_op* op, int64_t g, double* x, double* y)
+{
+    int64_t i1 = g % op->n, i2 = g / op->n;
+    *x = ((double)i1 + 0.5) * op->h;
+    *y = ((double)i2 + 0.5) * op->h;
+}
+
+/* Laplace, Sec. 5: A_gg' = -(1/2pi) h^2 log|x_g - x_g'|, A_gg = a_g - (1/2pi) C_h */
+static double entry_d(const ro_op* op, int64_t g, int64_t gp)
+{
+    if (g == gp) return op->a[g] + op->lap_self;
+    double x, y, xp, yp;
+    gxy(op, g, &x, &y); gxy(op, gp, &xp, &yp);
+    double dx = x - xp, dy = y - yp;
+    return op->lap_c0 * log(dx * dx + dy * dy);
+}
+
+static double proxy_entry_d(const ro_op* op, double zx, double zy, int64_t g)
+{
+    double x, y;
+    gxy(op, g, &x, &y);
+    double dx = zx - x, dy = zy - y;
+    return op->lap_c0 * log(dx * dx + dy * dy);
+}
+
+/* Helmholtz in the symmetric form of Eq. (5.6):
+ * A_gg' = s_g (i/4) H0(kappa r) h^2 s_g',  A_gg = a_g + s_g^2 (i/4) int_cell H0 */
+static double complex entry_z(const ro_op* op, int64_t g, int64_t gp)
+{
+    if (g == gp) return op->a[g] + op->s[g] * op->s[g] * op->hz_self;
+    double x, y, xp, yp;
+    gxy(op, g, &x, &y); gxy(op, gp, &xp, &yp);
+    double dx = x - xp, dy = y - yp;
+    double z = op->opts.kappa * sqrt(dx * dx + dy * dy);
+    double complex k = 0.25 * I * (j0(z) + I * y0(z)) * (op->h * op->h);
+    return op->s[g] * k * op->s[gp];
+}
+
+static double complex proxy_entry_z(const ro_op* op, double zx, double zy, int64_t g)
+{
+    double x, y;
+    gxy(op, g, &x, &y);
+    double dx = zx - x, dy = zy - y;
+    double z = op->opts.kappa * sqrt(dx * dx + dy * dy);
+    double complex k = 0.25 * I * (j0(z) + I * y0(z)) * (op->h * op->h);
+    return k * op->s[g];
+}
+
+/* ------------------------------------------------------------------ numeric core x2 */
+
+#define SC double
+#define FN(x) x##_d
+#define ABS2(z) ((z) * (z))
+#define ABSV(z) fabs(z)
+#define CONJ(z) (z)
+#define IS_CPLX 0
+#include "ro_core.inc"
+#undef SC
+#undef FN
+#undef ABS2
+#undef ABSV
+#undef CONJ
+#undef IS_CPLX
+
+#define SC double complex
+#define FN(x) x##_z
+#define ABS2(z) (creal(z) * creal(z) + cimag(z) * cimag(z))
+#define ABSV(z) cabs(z)
+#define CONJ(z) conj(z)
+#define IS_CPLX 1
+#include "ro_core.inc"
+#undef SC
+#undef FN
+#undef ABS2
+#undef ABSV
+#undef CONJ
+#undef IS_CPLX
+
+/* ------------------------------------------------------------------ public API */
+
+void ro_opts_default(ro_opts* o)
+{
+    o->kind = 0;
+    o->kappa = 0.0;
+    o->proxy_points = 64;
+    o->proxy_radius_factor = 1.5;
+    o->near_all = 0;
+    o->tie_rel = 1e-8;
+    o->threads = 0;
+}
+
+int ro_id(int cplx, const double* Y, int r, int m, double eps, double tie_rel, int* k_out,
+          int* perm, double* T)
+{
+    if (r < 0 || m < 1 || !Y || !k_out || !perm || !T) return -1;
+    if (cplx) return id_z((const double complex*)Y, r, m, eps, tie_rel, k_out, perm, (double complex*)T);
+    return id_d(Y, r, m, eps, tie_rel, k_out, perm, T);
+}
+
+int ro_inverse(int cplx, const double* A, int m, double* Ainv)
+{
+    if (m < 1 || !A || !Ainv) return -1;
+    if (cplx) return inverse_z((const double complex*)A, m, (double complex*)Ainv);
+    return inverse_d(A, m, Ainv);
+}
+
+static int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return ((1 << r) == v) ? r : -1; }
+
+/* Active sets and near lists of level l, from the skeletons of level l+1 (or the grid). */
+static void level_bookkeeping(ro_op* op, int l)
+{
+    int nb = 1 << l, n = op->n;
+    for (int j = 0; j < nb; ++j) {
+        ro_box* B = &op->lev[l][j];
+        if (l == op->d) {
+            int bx, by, wx, wy;
+            box_int(n, l, j, &bx, &by, &wx, &wy);
+            B->m = wx * wy;
+            B->active = (int64_t*)malloc(sizeof(int64_t) * (size_t)B->m);
+            int q = 0;
+            for (int i2 = by * wy; i2 < (by + 1) * wy; ++i2)
+                for (int i1 = bx * wx; i1 < (bx + 1) * wx; ++i1) B->active[q++] = (int64_t)i1 + (int64_t)n * i2;
+        } else {
+            ro_box* C1 = &op->lev[l + 1][2 * j];
+            ro_box* C2 = &op->lev[l + 1][2 * j + 1];
+            B->m = C1->k + C2->k;
+            B->active = (int64_t*)malloc(sizeof(int64_t) * (size_t)(B->m + 1));
+            memcpy(B->active, C1->skel, sizeof(int64_t) * (size_t)C1->k);
+            memcpy(B->active + C1->k, C2->skel, sizeof(int64_t) * (size_t)C2->k);
+        }
+    }
+    for (int j = 0; j < nb; ++j) {
+        ro_box* B = &op->lev[l][j];
+        int bx, by, wx, wy;
+        box_int(n, l, j, &bx, &by, &wx, &wy);
+        int64_t cx2 = (int64_t)(2 * bx + 1) * wx, cy2 = (int64_t)(2 * by + 1) * wy;
+        int w = wx > wy ? wx : wy;
+        double R2 = op->opts.proxy_radius_factor * (double)w;   /* in units of h/2 */
+        double R2sq = R2 * R2;
+        int cap = 0;
+        for (int q = 0; q < nb; ++q) if (q != j) cap += op->lev[l][q].m;
+        B->near = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cap + 1));
+        int cnt = 0;
+        for (int q = 0; q < nb; ++q) {
+            if (q == j) continue;
+            int qx, qy, qwx, qwy;
+            box_int(n, l, q, &qx, &qy, &qwx, &qwy);
+            if (!op->opts.near_all && (abs(qx - bx) > 1 || abs(qy - by) > 1)) continue;
+            const ro_box* Q = &op->lev[l][q];
+            for (int p = 0; p < Q->m; ++p) {
+                int64_t g = Q->active[p];
+                if (!op->opts.near_all) {
+                    int64_t i1 = g % n, i2 = g / n;
+                    int64_t dx = 2 * i1 + 1 - cx2, dy = 2 * i2 + 1 - cy2;
+                    if (!((double)(dx * dx + dy * dy) < R2sq)) continue;
+                }
+                B->near[cnt++] = g;
+            }
+        }
+        B->nnear = cnt;
+    }
+}
+
+int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps,
+              const ro_opts* opts, ro_op** out)
+{
+    if (!out || n < 2 || leaf_side < 1 || n % leaf_side) return -1;
+    int L = ilog2(n / leaf_side);
+    if (L < 1) return -1;
+    ro_opts o;
+    if (opts) o = *opts; else ro_opts_default(&o);
+    if (o.kind != 0 && o.kind != 1) return -1;
+    if (o.kind == 0 && b) return -1;
+    if (o.proxy_points < 0) return -1;
+    int64_t N = (int64_t)n * n;
+    ro_op* op = (ro_op*)calloc(1, sizeof(ro_op));
+    op->n = n; op->leaf = leaf_side; op->d = 2 * L; op->h = 1.0 / n; op->eps = eps; op->opts = o;
+#ifdef _OPENMP
+    op->nthreads = o.threads > 0 ? o.threads : omp_get_max_threads();
+#else
+    op->nthreads = 1;
+#endif
+    op->a = (double*)malloc(sizeof(double) * (size_t)N);
+    op->s = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int64_t g = 0; g < N; ++g) {
+        op->a[g] = a ? a[g] : 1.0;
+        double bg = b ? b[g] : 1.0;
+        if (o.kind == 1 && !(bg > 0.0)) { ro_free(op); return -1; }
+        op->s[g] = (o.kind == 1) ? o.kappa * sqrt(bg) : 1.0;
+    }
+    op->lap_c0 = -(op->h * op->h) / (4.0 * M_PI);
+    op->lap_self = -ro_laplace_cell_integral(op->h) / (2.0 * M_PI);
+    if (o.kind == 1) {
+        double re, im;
+        ro_helmholtz_cell_integral(op->h, o.kappa, 32, &re, &im);
+        op->hz_self = 0.25 * I * (re + I * im);
+    }
+    int P = o.proxy_points;
+    op->pcos = (double*)malloc(sizeof(double) * (size_t)(P + 1));
+    op->psin = (double*)malloc(sizeof(double) * (size_t)(P + 1));
+    for (int q = 0; q < P; ++q) {
+        double ang = (2.0 * M_PI * (double)q) / (double)P;
+        op->pcos[q] = cos(ang); op->psin[q] = sin(ang);
+    }
+    op->lev = (ro_box**)calloc((size_t)(op->d + 1), sizeof(ro_box*));
+    for (int l = 1; l <= op->d; ++l) op->lev[l] = (ro_box*)calloc((size_t)1 << l, sizeof(ro_box));
+    int rc = 0;
+    for (int l = op->d; l >= 1 && rc == 0; --l) {
+        level_bookkeeping(op, l);
+        int nb = 1 << l;
+        int err = 0;
+        #pragma omp parallel for schedule(dynamic) num_threads(op->nthreads)
+        for (int j = 0; j < nb; ++j) {
+            int e = (o.kind == 0) ? factor_box_d(op, l, j) : factor_box_z(op, l, j);
+            if (e) {
+                #pragma omp critical
+                err = e;
+            }
+        }
+        rc = err;
+    }
+    if (rc == 0) rc = (o.kind == 0) ? factor_root_d(op) : factor_root_z(op);
+    if (rc) { ro_free(op); return rc; }
+    *out = op;
+    return 0;
+}
+
+int ro_solve(const ro_op* op, const double* f, int nrhs, double* x)
+{
+    if (!op || !f || !x || nrhs < 1) return -1;
+    if (op->opts.kind == 0) return solve_sym_d(op, f, nrhs, x);
+    int64_t N = (int64_t)op->n * op->n;
+    const double complex* fz = (const double complex*)f;
+    double complex* xz = (double complex*)x;
+    double complex* ft = (double complex*)malloc(sizeof(double complex) * (size_t)N * nrhs);
+    for (int c = 0; c < nrhs; ++c)
+        for (int64_t g = 0; g < N; ++g) ft[(size_t)c * N + g] = fz[(size_t)c * N + g] / op->s[g];
+    int rc = solve_sym_z(op, ft, nrhs, xz);
+    for (int c = 0; c < nrhs; ++c)
+        for (int64_t g = 0; g < N; ++g) xz[(size_t)c * N + g] *= op->s[g];
+    free(ft);
+    return rc;
+}
+
+void ro_free(ro_op* op)
+{
+    if (!op) return;
+    if (op->lev) {
+        for (int l = 1; l <= op->d; ++l) {
+            if (!op->lev[l]) continue;
+            for (int j = 0; j < (1 << l); ++j) {
+                ro_box* B = &op->lev[l][j];
+                free(B->active); free(B->near); free(B->skel); free(B->sk_local); free(B->rs_local);
+                free(B->T); free(B->Finv); free(B->E);
+            }
+            free(op->lev[l]);
+        }
+        free(op->lev);
+    }
+    free(op->a); free(op->s); free(op->pcos); free(op->psin); free(op->active0); free(op->root_inv);
+    free(op);
+}
+
+/* ------------------------------------------------------------------ inspection */
+
+static const ro_box* getbox(const ro_op* op, int l, int j)
+{
+    if (!op || l < 1 || l > op->d || j < 0 || j >= (1 << l)) return NULL;
+    return &op->lev[l][j];
+}
+
+int ro_depth(const ro_op* op) { return op ? op->d : -1; }
+
+int ro_box_sizes(const ro_op* op, int l, int j, int* m, int* k, int* r, int* nnear)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    if (m) *m = B->m;
+    if (k) *k = B->k;
+    if (r) *r = B->r;
+    if (nnear) *nnear = B->nnear;
+    return 0;
+}
+
+int ro_box_active(const ro_op* op, int l, int j, int64_t* out)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    memcpy(out, B->active, sizeof(int64_t) * (size_t)B->m);
+    return 0;
+}
+
+int ro_box_skel(const ro_op* op, int l, int j, int64_t* out)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    memcpy(out, B->skel, sizeof(int64_t) * (size_t)B->k);
+    return 0;
+}
+
+int ro_box_near(const ro_op* op, int l, int j, int64_t* out)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    memcpy(out, B->near, sizeof(int64_t) * (size_t)B->nnear);
+    return 0;
+}
+
+static size_t esz(const ro_op* op) { return op->opts.kind == 1 ? 2 * sizeof(double) : sizeof(double); }
+
+int ro_box_T(const ro_op* op, int l, int j, double* out)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    memcpy(out, B->T, esz(op) * (size_t)B->k * (size_t)(B->m - B->k));
+    return 0;
+}
+
+int ro_box_Finv(const ro_op* op, int l, int j, double* out)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    memcpy(out, B->Finv, esz(op) * (size_t)B->m * (size_t)B->m);
+    return 0;
+}
+
+int ro_box_E(const ro_op* op, int l, int j, double* out)
+{
+    const ro_box* B = getbox(op, l, j);
+    if (!B) return -1;
+    memcpy(out, B->E, esz(op) * (size_t)B->k * (size_t)B->k);
+    return 0;
+}
+
+int ro_root_size(const ro_op* op) { return op ? op->m0 : -1; }
+
+int ro_root_inv(const ro_op* op, double* out)
+{
+    if (!op) return -1;
+    memcpy(out, op->root_inv, esz(op) * (size_t)op->m0 * (size_t)op->m0);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ brute force */
+
+/* Entry of the system matrix as posed (not symmetrised): Laplace as in entry_d,
+ * Helmholtz A_gg' = kappa^2 b_g (i/4) H0(kappa r) h^2, A_gg = a_g + kappa^2 b_g (i/4) int_cell H0. */
+typedef struct { int n; double h, c0, lself; double complex hself; int kind; double kappa; } bf_ctx;
+
+static void bf_init(bf_ctx* c, int n, int kind, double kappa)
+{
+    c->n = n; c->h = 1.0 / n; c->kind = kind; c->kappa = kappa;
+    c->c0 = -(c->h * c->h) / (4.0 * M_PI);
+    c->lself = -ro_laplace_cell_integral(c->h) / (2.0 * M_PI);
+    c->hself = 0.0;
+    if (kind == 1) {
+        double re, im;
+        ro_helmholtz_cell_integral(c->h, kappa, 32, &re, &im);
+        c->hself = 0.25 * I * (re + I * im);
+    }
+}
+
+static double complex bf_entry(const bf_ctx* c, const double* a, const double* b, int64_t g, int64_t gp)
+{
+    double ag = a ? a[g] : 1.0;
+    if (c->kind == 0) {
+        if (g == gp) return ag + c->lself;
+        double x = ((double)(g % c->n) + 0.5) * c->h, y = ((double)(g / c->n) + 0.5) * c->h;
+        double xp = ((double)(gp % c->n) + 0.5) * c->h, yp = ((double)(gp / c->n) + 0.5) * c->h;
+        double dx = x - xp, dy = y - yp;
+        return c->c0 * log(dx * dx + dy * dy);
+    }
+    double bg = b ? b[g] : 1.0;
+    double kb = c->kappa * c->kappa * bg;
+    if (g == gp) return ag + kb * c->hself;
+    double x = ((double)(g % c->n) + 0.5) * c->h, y = ((double)(g / c->n) + 0.5) * c->h;
+    double xp = ((double)(gp % c->n) + 0.5) * c->h, yp = ((double)(gp / c->n) + 0.5) * c->h;
+    double dx = x - xp, dy = y - yp;
+    double z = c->kappa * sqrt(dx * dx + dy * dy);
+    return kb * 0.25 * I * (j0(z) + I * y0(z)) * (c->h * c->h);
+}
+
+void ro_entry(int n, int kind, double kappa, const double* a, const double* b, int64_t g,
+              int64_t gp, double* re, double* im)
+{
+    bf_ctx c;
+    bf_init(&c, n, kind, kappa);
+    double complex v = bf_entry(&c, a, b, g, gp);
+    *re = creal(v); *im = cimag(v);
+}
+
+int ro_matvec_rows(int n, int kind, double kappa, const double* a, const double* b,
+                   const double* x, int nrhs, const int64_t* rows, int nrows, double* y)
+{
+    if (n < 1 || nrhs < 1 || !x || !y || (kind != 0 && kind != 1)) return -1;
+    bf_ctx c;
+    bf_init(&c, n, kind, kappa);
+    int64_t N = (int64_t)n * n;
+    #pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nrows; ++q) {
+        int64_t g = rows[q];
+        for (int col = 0; col < nrhs; ++col) {
+            if (kind == 0) {
+                double s = 0.0;
+                for (int64_t gp = 0; gp < N; ++gp) s += creal(bf_entry(&c, a, b, g, gp)) * x[(size_t)col * N + gp];
+                y[(size_t)col * nrows + q] = s;
+            } else {
+                const double complex* xz = (const double complex*)x;
+                double complex s = 0.0;
+                for (int64_t gp = 0; gp < N; ++gp) s += bf_entry(&c, a, b, g, gp) * xz[(size_t)col * N + gp];
+                ((double complex*)y)[(size_t)col * nrows + q] = s;
+            }
+        }
+    }
+    return 0;
+}
+
+int ro_matvec(int n, int kind, double kappa, const double* a, const double* b, const double* x,
+              int nrhs, double* y)
+{
+    int64_t N = (int64_t)n * n;
+    int64_t* rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t g = 0; g < N; ++g) rows[g] = g;
+    int rc = ro_matvec_rows(n, kind, kappa, a, b, x, nrhs, rows, (int)N, y);
+    free(rows);
+    return rc;
+}

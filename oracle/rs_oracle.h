@@ -1,0 +1,101 @@
+/*
+ * rs_oracle.h -- plain, slow CPU oracle of the dense-block recursive-skeletonization
+ * inverse of Corona, Martinsson & Zorin, "An O(N) Direct Solver for Integral Equations
+ * on the Plane" (arXiv:1303.5466).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library against the
+ * paper.  Only tests, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (paper references are to sections, equations and algorithms):
+ *   - Nystrom matrix on an n x n cell-centre grid of [0,1]^2 (Sec. 5, general formulation):
+ *       Laplace:   A_gg' = -(1/2pi) h^2 log|x_g - x_g'|,  A_gg = a_g - (1/2pi) C_h
+ *       Helmholtz: A_gg' = kappa^2 b_g (i/4) H0(kappa r) h^2,
+ *                  A_gg  = a_g + kappa^2 b_g (i/4) * (integral of H0 over the h x h cell),
+ *                  factored in the symmetric form of Eq. (5.6), S^{-1} A S with
+ *                  S = diag(kappa sqrt(b)); ro_solve takes and returns the unscaled f, x
+ *   - binary tree by alternating bisection (Sec. 2.2), proxy-accelerated IDs (Sec. 2.2,
+ *     Eq. 2.1), the HSS inversion of Algorithm 1 with the E formula of Algorithm 2 line 9,
+ *     and the inverse apply of Algorithm 6 restated from Eqs. (2.10)-(2.12).
+ *
+ * All arrays are host memory, caller-owned unless stated.  Complex values are interleaved
+ * (re, im) doubles.  Functions return 0 on success and a negative value on bad input.
+ */
+#ifndef RS_ORACLE_H
+#define RS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ro_op ro_op;
+
+typedef struct {
+    int kind;                    /* 0 = Laplace, 1 = Helmholtz (complex)                  */
+    double kappa;                /* Helmholtz wavenumber                                   */
+    int proxy_points;            /* P points on the proxy circle; 0 = no proxy rows        */
+    double proxy_radius_factor;  /* R = factor * (larger box half-width)                   */
+    int near_all;                /* 1: rows = every other box's active points (the full
+                                    off-diagonal block row of Sec. 2.2, no acceleration)   */
+    double tie_rel;              /* pivot near-tie tolerance on squared column norms       */
+    int threads;                 /* OpenMP threads over the boxes of a level (<=0: default) */
+} ro_opts;
+
+void ro_opts_default(ro_opts* o);
+
+/* Exact integral of log|y - x| over the h x h cell centred at x (Laplace diagonal). */
+double ro_laplace_cell_integral(double h);
+/* Integral of H0^(1)(kappa |y - x|) over the h x h cell centred at x (re, im out). */
+void ro_helmholtz_cell_integral(double h, double kappa, int nodes, double* re, double* im);
+
+/* Gauss-Legendre nodes/weights on [-1,1] (used by the Helmholtz cell integral). */
+void ro_gauss_legendre(int n, double* x, double* w);
+
+/* Column-pivoted Householder QR interpolative decomposition (Sec. 2.1, Eq. 2.1).
+ * Y: r x m row-major (real: r*m doubles; complex: 2*r*m).  Outputs k, perm (m entries:
+ * pivot order, first k = skeleton), T (k x (m-k) row-major, rows/cols in pivot order). */
+int ro_id(int cplx, const double* Y, int r, int m, double eps, double tie_rel,
+          int* k_out, int* perm, double* T);
+
+/* Inverse by LU with partial pivoting.  A, Ainv: m x m row-major. */
+int ro_inverse(int cplx, const double* A, int m, double* Ainv);
+
+/* Factor (Algorithm 1) for the n x n grid with leaf_side x leaf_side leaves.
+ * a: N values (grid order g = i1 + n*i2) or NULL (= 1); b: N values of b(x) (Helmholtz)
+ * or NULL (= 1). */
+int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps,
+              const ro_opts* opts, ro_op** out);
+/* Inverse apply (Algorithm 6).  f, x: N x nrhs column-major in grid order. */
+int ro_solve(const ro_op* op, const double* f, int nrhs, double* x);
+void ro_free(ro_op* op);
+
+/* Inspection.  Levels are 0 (root) .. d (leaves); boxes 0 .. 2^l - 1. */
+int ro_depth(const ro_op* op);
+int ro_box_sizes(const ro_op* op, int level, int box, int* m, int* k, int* r, int* nnear);
+int ro_box_active(const ro_op* op, int level, int box, int64_t* out);   /* m globals   */
+int ro_box_skel(const ro_op* op, int level, int box, int64_t* out);     /* k globals,
+                                                                           ascending   */
+int ro_box_near(const ro_op* op, int level, int box, int64_t* out);     /* nnear       */
+int ro_box_T(const ro_op* op, int level, int box, double* out);  /* k x (m-k), rows in
+                                 skeleton (ascending global) order, columns in residual
+                                 (ascending local) order                                 */
+int ro_box_Finv(const ro_op* op, int level, int box, double* out);  /* m x m            */
+int ro_box_E(const ro_op* op, int level, int box, double* out);     /* k x k            */
+int ro_root_size(const ro_op* op);
+int ro_root_inv(const ro_op* op, double* out);
+
+/* Brute-force y = A x over all N x N entries (nrhs columns, grid order). */
+int ro_matvec(int n, int kind, double kappa, const double* a, const double* b,
+              const double* x, int nrhs, double* y);
+/* Rows `rows[0..nrows)` of A x (nrhs columns): y is nrows x nrhs column-major. */
+int ro_matvec_rows(int n, int kind, double kappa, const double* a, const double* b,
+                   const double* x, int nrhs, const int64_t* rows, int nrows, double* y);
+/* One dense entry A(g, g') (re, im). */
+void ro_entry(int n, int kind, double kappa, const double* a, const double* b,
+              int64_t g, int64_t gp, double* re, double* im);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
