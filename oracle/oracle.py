@@ -38,7 +38,7 @@ def build(force=False, plant=0, out=None):
 class _Opts(C.Structure):
     _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("proxy_points", C.c_int),
                 ("proxy_radius_factor", C.c_double), ("near_all", C.c_int),
-                ("tie_rel", C.c_double), ("threads", C.c_int)]
+                ("threads", C.c_int)]
 
 
 def load(path):
@@ -70,7 +70,7 @@ def _declare(L):
     L.ro_laplace_cell_integral.argtypes = [C.c_double]
     L.ro_helmholtz_cell_integral.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp]
     L.ro_gauss_legendre.argtypes = [C.c_int, dp, dp]
-    L.ro_id.argtypes = [C.c_int, dp, C.c_int, C.c_int, C.c_double, C.c_double, ip, ip, dp]
+    L.ro_id.argtypes = [C.c_int, dp, C.c_int, C.c_int, C.c_double, ip, ip, dp]
     L.ro_inverse.argtypes = [C.c_int, dp, C.c_int, dp]
     L.ro_factor.argtypes = [C.c_int, C.c_int, dp, dp, C.c_double, C.POINTER(_Opts), C.POINTER(C.c_void_p)]
     L.ro_solve.argtypes = [C.c_void_p, dp, C.c_int, dp]
@@ -119,7 +119,7 @@ def gauss_legendre(n):
     return x, w
 
 
-def interp_decomp(Y, eps, tie_rel=1e-8):
+def interp_decomp(Y, eps):
     """ID of Y (r x m, real or complex): returns (k, perm, T) with T in pivot order."""
     cplx = np.iscomplexobj(Y)
     Y = np.ascontiguousarray(Y, dtype=np.complex128 if cplx else np.float64)
@@ -127,7 +127,7 @@ def interp_decomp(Y, eps, tie_rel=1e-8):
     perm = np.zeros(m, dtype=np.int32)
     T = np.zeros(max(m * m, 1), dtype=Y.dtype)
     k = C.c_int()
-    rc = lib().ro_id(int(cplx), Y.ctypes.data_as(C.POINTER(C.c_double)), r, m, eps, tie_rel, C.byref(k),
+    rc = lib().ro_id(int(cplx), Y.ctypes.data_as(C.POINTER(C.c_double)), r, m, eps, C.byref(k),
                      perm.ctypes.data_as(C.POINTER(C.c_int)), T.ctypes.data_as(C.POINTER(C.c_double)))
     if rc:
         raise RuntimeError("ro_id failed: %d" % rc)
@@ -151,12 +151,12 @@ class Factorization:
     """Dense-block HSS inverse built by ro_factor (Algorithm 1)."""
 
     def __init__(self, n, leaf, eps, a=None, b=None, kind=LAPLACE, kappa=0.0, proxy_points=64,
-                 proxy_radius_factor=1.5, near_all=False, tie_rel=1e-8, threads=0):
+                 proxy_radius_factor=1.5, near_all=False, threads=0):
         L = self._L = lib()
         o = _Opts()
         L.ro_opts_default(C.byref(o))
         o.kind, o.kappa, o.proxy_points = kind, kappa, proxy_points
-        o.proxy_radius_factor, o.near_all, o.tie_rel, o.threads = proxy_radius_factor, int(near_all), tie_rel, threads
+        o.proxy_radius_factor, o.near_all, o.threads = proxy_radius_factor, int(near_all), threads
         self.n, self.leaf, self.eps, self.kind, self.kappa = n, leaf, eps, kind, kappa
         N = n * n
         self.a, self.b = _f64(a, N), _f64(b, N)

@@ -199,6 +199,16 @@ static double complex proxy_entry_z(const ro_op* op, double zx, double zy, int64
     return k * op->s[g];
 }
 
+/* Pivot key of the column-pivoted QR: the squared norm with its 26 low mantissa bits
+ * cleared (a monotone map of non-negative doubles onto a coarser grid). */
+static uint64_t pivot_key(double v)
+{
+    if (!(v > 0.0)) v = 0.0;
+    uint64_t u;
+    memcpy(&u, &v, sizeof u);
+    return u & ~((UINT64_C(1) << 26) - 1);
+}
+
 /* ------------------------------------------------------------------ numeric core x2 */
 
 #define SC double
@@ -238,16 +248,14 @@ void ro_opts_default(ro_opts* o)
     o->proxy_points = 64;
     o->proxy_radius_factor = 1.5;
     o->near_all = 0;
-    o->tie_rel = 1e-8;
     o->threads = 0;
 }
 
-int ro_id(int cplx, const double* Y, int r, int m, double eps, double tie_rel, int* k_out,
-          int* perm, double* T)
+int ro_id(int cplx, const double* Y, int r, int m, double eps, int* k_out, int* perm, double* T)
 {
     if (r < 0 || m < 1 || !Y || !k_out || !perm || !T) return -1;
-    if (cplx) return id_z((const double complex*)Y, r, m, eps, tie_rel, k_out, perm, (double complex*)T);
-    return id_d(Y, r, m, eps, tie_rel, k_out, perm, T);
+    if (cplx) return id_z((const double complex*)Y, r, m, eps, k_out, perm, (double complex*)T);
+    return id_d(Y, r, m, eps, k_out, perm, T);
 }
 
 int ro_inverse(int cplx, const double* A, int m, double* Ainv)

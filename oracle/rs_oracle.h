@@ -38,7 +38,6 @@ typedef struct {
     double proxy_radius_factor;  /* R = factor * (larger box half-width)                   */
     int near_all;                /* 1: rows = every other box's active points (the full
                                     off-diagonal block row of Sec. 2.2, no acceleration)   */
-    double tie_rel;              /* pivot near-tie tolerance on squared column norms       */
     int threads;                 /* OpenMP threads over the boxes of a level (<=0: default) */
 } ro_opts;
 
@@ -53,10 +52,12 @@ void ro_helmholtz_cell_integral(double h, double kappa, int nodes, double* re, d
 void ro_gauss_legendre(int n, double* x, double* w);
 
 /* Column-pivoted Householder QR interpolative decomposition (Sec. 2.1, Eq. 2.1).
+ * Pivots compare squared column norms with their 26 low mantissa bits cleared; ties go to
+ * the lowest column index.
  * Y: r x m row-major (real: r*m doubles; complex: 2*r*m).  Outputs k, perm (m entries:
  * pivot order, first k = skeleton), T (k x (m-k) row-major, rows/cols in pivot order). */
-int ro_id(int cplx, const double* Y, int r, int m, double eps, double tie_rel,
-          int* k_out, int* perm, double* T);
+int ro_id(int cplx, const double* Y, int r, int m, double eps, int* k_out, int* perm,
+          double* T);
 
 /* Inverse by LU with partial pivoting.  A, Ainv: m x m row-major. */
 int ro_inverse(int cplx, const double* A, int m, double* Ainv);
