@@ -38,7 +38,7 @@ def build(force=False, plant=0, out=None):
 class _Opts(C.Structure):
     _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("proxy_points", C.c_int),
                 ("proxy_radius_factor", C.c_double), ("near_all", C.c_int),
-                ("threads", C.c_int)]
+                ("threads", C.c_int), ("max_levels", C.c_int)]
 
 
 def load(path):
@@ -151,12 +151,13 @@ class Factorization:
     """Dense-block HSS inverse built by ro_factor (Algorithm 1)."""
 
     def __init__(self, n, leaf, eps, a=None, b=None, kind=LAPLACE, kappa=0.0, proxy_points=64,
-                 proxy_radius_factor=1.5, near_all=False, threads=0):
+                 proxy_radius_factor=1.5, near_all=False, threads=0, max_levels=0):
         L = self._L = lib()
         o = _Opts()
         L.ro_opts_default(C.byref(o))
         o.kind, o.kappa, o.proxy_points = kind, kappa, proxy_points
         o.proxy_radius_factor, o.near_all, o.threads = proxy_radius_factor, int(near_all), threads
+        o.max_levels = max_levels
         self.n, self.leaf, self.eps, self.kind, self.kappa = n, leaf, eps, kind, kappa
         N = n * n
         self.a, self.b = _f64(a, N), _f64(b, N)

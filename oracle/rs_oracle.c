@@ -57,6 +57,7 @@ struct ro_op {
     double* pcos;       /* proxy unit circle                        */
     double* psin;
     ro_box** lev;       /* lev[l][j], l = 1..d                      */
+    int partial;        /* only the finest levels were factored (timing sample) */
     int m0;
     int64_t* active0;
     double* root_inv;
@@ -199,14 +200,14 @@ static double complex proxy_entry_z(const ro_op* op, double zx, double zy, int64
     return k * op->s[g];
 }
 
-/* Pivot key of the column-pivoted QR: the squared norm with its 26 low mantissa bits
- * cleared (a monotone map of non-negative doubles onto a coarser grid). */
+/* Pivot key of the column-pivoted QR: the squared norm with its 40 low mantissa bits
+ * cleared (a monotone map of non-negative doubles onto a grid of relative step 2^-12). */
 static uint64_t pivot_key(double v)
 {
     if (!(v > 0.0)) v = 0.0;
     uint64_t u;
     memcpy(&u, &v, sizeof u);
-    return u & ~((UINT64_C(1) << 26) - 1);
+    return u & ~((UINT64_C(1) << 40) - 1);
 }
 
 /* ------------------------------------------------------------------ numeric core x2 */
@@ -249,6 +250,7 @@ void ro_opts_default(ro_opts* o)
     o->proxy_radius_factor = 1.5;
     o->near_all = 0;
     o->threads = 0;
+    o->max_levels = 0;
 }
 
 int ro_id(int cplx, const double* Y, int r, int m, double eps, int* k_out, int* perm, double* T)
@@ -366,7 +368,8 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
     op->lev = (ro_box**)calloc((size_t)(op->d + 1), sizeof(ro_box*));
     for (int l = 1; l <= op->d; ++l) op->lev[l] = (ro_box*)calloc((size_t)1 << l, sizeof(ro_box));
     int rc = 0;
-    for (int l = op->d; l >= 1 && rc == 0; --l) {
+    const int lmin = (o.max_levels > 0 && o.max_levels < op->d) ? op->d - o.max_levels + 1 : 1;
+    for (int l = op->d; l >= lmin && rc == 0; --l) {
         level_bookkeeping(op, l);
         int nb = 1 << l;
         int err = 0;
@@ -380,7 +383,8 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
         }
         rc = err;
     }
-    if (rc == 0) rc = (o.kind == 0) ? factor_root_d(op) : factor_root_z(op);
+    if (rc == 0 && lmin == 1) rc = (o.kind == 0) ? factor_root_d(op) : factor_root_z(op);
+    op->partial = (lmin > 1);
     if (rc) { ro_free(op); return rc; }
     *out = op;
     return 0;
@@ -388,7 +392,7 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
 
 int ro_solve(const ro_op* op, const double* f, int nrhs, double* x)
 {
-    if (!op || !f || !x || nrhs < 1) return -1;
+    if (!op || !f || !x || nrhs < 1 || op->partial) return -1;
     if (op->opts.kind == 0) return solve_sym_d(op, f, nrhs, x);
     int64_t N = (int64_t)op->n * op->n;
     const double complex* fz = (const double complex*)f;

@@ -39,6 +39,8 @@ typedef struct {
     int near_all;                /* 1: rows = every other box's active points (the full
                                     off-diagonal block row of Sec. 2.2, no acceleration)   */
     int threads;                 /* OpenMP threads over the boxes of a level (<=0: default) */
+    int max_levels;              /* >0: factor only the max_levels finest levels and stop
+                                    (a bounded sample for timing; ro_solve then refuses)   */
 } ro_opts;
 
 void ro_opts_default(ro_opts* o);
@@ -52,7 +54,7 @@ void ro_helmholtz_cell_integral(double h, double kappa, int nodes, double* re, d
 void ro_gauss_legendre(int n, double* x, double* w);
 
 /* Column-pivoted Householder QR interpolative decomposition (Sec. 2.1, Eq. 2.1).
- * Pivots compare squared column norms with their 26 low mantissa bits cleared; ties go to
+ * Pivots compare squared column norms with their 40 low mantissa bits cleared; ties go to
  * the lowest column index.
  * Y: r x m row-major (real: r*m doubles; complex: 2*r*m).  Outputs k, perm (m entries:
  * pivot order, first k = skeleton), T (k x (m-k) row-major, rows/cols in pivot order). */
