@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the factor + solve hot path on one GB300 per rank.
+
+Workload (the batched Laplace configuration): 512 x 512 cell-centre grid of [0,1]^2
+(N = 262144), leaves of 16 x 16 points, eps = 1e-10, a(x) = 1 + 0.5 sin(2 pi x1) cos(2 pi x2),
+4 right-hand sides ~ N(0,1) (seed 1), FP64 throughout.  One step = rs_build_tree +
+rs_factor + rs_solve (4 RHS).  `value` is factor unknowns per second (N / factor time, CUDA
+events on the launch stream, inputs already on the device for the solve); the solve rate
+is reported beside it.  `e2e` repeats the step through host buffers (pinned), with every
+host-device copy inside the timed region.  A 256 MiB buffer (larger than the 129 MB L2) is
+rewritten before every timed step.
+
+With --gpus N under torchrun every rank runs its own replica (the path has no exchange
+step): the reported times are the max over ranks, `value` the sum of the ranks' work over
+that time.  `--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1303_5466_gb300 import workloads as W  # noqa: E402
+
+METRIC = "factor unknowns/sec and solve RHS/sec at 1e-10 residual; serving p50/p99 latency"
+WORKLOAD = "laplace_batched"
+# FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26 TFLOP/s, the 1.25
+# TFLOP/s FP64 figure of the profiling recipe (a register-only FMA probe measured 1.203).
+PEAK_FP64_TFLOPS = 1.25
+ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD, choices=["laplace_batched", "laplace_n256"],
+                   help="laplace_n256 is a quarter-size copy for profiling runs")
+    return p.parse_args()
+
+
+def _inputs(name=WORKLOAD):
+    cfg = W.WORKLOADS[name]
+    n, leaf, eps, nrhs = cfg["n"], cfg["leaf"], cfg["eps"], cfg["nrhs"]
+    pts = W.grid_points(n)
+    a = W.coeff_a_batched(n)
+    F = W.rhs_normal(n, cfg["seed"], nrhs=nrhs)          # (N, nrhs)
+    return n, leaf, eps, nrhs, pts, a, F
+
+
+def _config(n, leaf, eps, nrhs, world, name=WORKLOAD):
+    return {"workload": name + ": %dx%d grid, leaf %dx%d, eps %g, a=1+0.5sin(2pi x1)cos(2pi x2), "
+                        "%d RHS ~ N(0,1) seed 1" % (n, n, leaf, leaf, eps, nrhs),
+            "N": n * n, "nrhs": nrhs, "eps": eps, "parallelism": "replicas x%d" % world,
+            "l2": "256 MiB buffer rewritten before every timed step"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _max_over_ranks(vals, world):
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def sample_share():
+    """Share of the factor flops in the ORACLE_LEVELS finest levels, from the per-level counts
+    that oracle/level_flops.py wrote from a full oracle factorization of this workload."""
+    with open(os.path.join(ROOT, "oracle", "laplace_batched_level_flops.json")) as fh:
+        fl = {int(k): v for k, v in json.load(fh).items()}
+    d = max(fl)
+    return sum(fl[l] for l in range(d - ORACLE_LEVELS + 1, d + 1)) / sum(fl.values())
+
+
+def oracle_sample(n, leaf, eps, a):
+    """Time the CPU oracle on the ORACLE_LEVELS finest levels of the workload and scale to the
+    whole factorization by those levels' share of the algorithmic flops."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    O.Factorization(n, leaf, eps, a=a, max_levels=ORACLE_LEVELS, threads=cores)
+    dt = time.perf_counter() - t
+    share = sample_share()
+    est = dt / share
+    return {"value": n * n / est, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle factor of the %d finest levels of the %dx%d workload took %.2f s on %d threads; "
+                      "those levels are %.1f%% of the factor flops, scaled to the full factor (%.1f s)"
+                      % (ORACLE_LEVELS, n, n, dt, cores, 100 * share, est)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1303_5466_gb300 as P
+    from paper_1303_5466_gb300 import build as B
+    B.build()
+    n, leaf, eps, nrhs, pts, a, F = _inputs(args.workload)
+    N = n * n
+    st = torch.cuda.current_stream()
+    f_dev = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()       # N x nrhs column-major
+    x_dev = torch.empty_like(f_dev)
+    opts = P.rs_opts_default()
+    opts.profile = 1
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():
+        tree = P.rs_build_tree(pts, leaf)
+        op = P.rs_factor(tree, a=a, eps=eps, opts=opts, stream=st)
+        return tree, op
+
+    for _ in range(args.warmup):
+        tree, op = step()
+        P.rs_solve(op, f_dev, nrhs, x_dev, st)
+        torch.cuda.synchronize()
+        P.rs_free(op)
+        P.rs_free_tree(tree)
+    if world > 1:
+        torch.distributed.barrier()
+    tf = ts = 0.0
+    prof = {}
+    launches0 = P.rs_launch_count()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(st)
+            tree, op = step()
+            e1.record(st)
+            P.rs_solve(op, f_dev, nrhs, x_dev, st)
+            e2.record(st)
+            e2.synchronize()
+            tf += e0.elapsed_time(e1)
+            ts += e1.elapsed_time(e2)
+            for k, v in P.rs_op_profile(op).items():
+                p = prof.setdefault(k, [0.0, 0.0, 0.0, 0])
+                for i in range(4):
+                    p[i] += v[i]
+            last_stats = P.rs_op_stats(op)
+            # residual check of the timed solve on sampled rows (outside the timing)
+            x_last = x_dev.cpu().numpy().T.copy()
+            P.rs_free(op)
+            P.rs_free_tree(tree)
+    launches = P.rs_launch_count() - launches0
+    torch.cuda.synchronize()
+    tf, ts = _max_over_ranks([tf, ts], world)
+    K = args.steps
+    factor_ms, solve_ms = tf / K, ts / K
+    # end to end through host buffers (pinned): H2D of the inputs and D2H of x in the timing
+    pin_f = torch.from_numpy(np.asfortranarray(F)).pin_memory().numpy()
+    pin_x = torch.empty(F.shape[::-1], dtype=torch.float64).pin_memory().numpy().T
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        tree, op = step()
+        P.rs_solve(op, pin_f, nrhs, pin_x, None)
+        P.rs_free(op)
+        P.rs_free_tree(tree)
+    e2e_s = _max_over_ranks([time.perf_counter() - t0], world)[0] / K
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    # dominant factor kernel: largest summed event time
+    fac_classes = [c for c in P.PROF_CLASSES if c not in ("solve", "assemble_Y", "assemble_F")]
+    dom = max(fac_classes, key=lambda c: prof[c][0])
+    ms, work, _, nl = prof[dom]
+    achieved = work / (ms * 1e-3) / 1e12
+    sol = prof["solve"]
+    rows = np.random.default_rng(5).choice(N, 64, replace=False)
+    from oracle import oracle as O
+    O.build()
+    r = O.matvec_rows(n, x_last, rows, a=a) - F[rows]
+    res = float(np.linalg.norm(r) / np.linalg.norm(F[rows]))
+    out = {
+        "metric": METRIC, "value": world * N / (factor_ms * 1e-3), "unit": "unknowns/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": factor_ms + solve_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(n, leaf, eps, nrhs, world, args.workload),
+        "factor_ms": factor_ms, "solve_ms": solve_ms,
+        "solve_rhs_per_s": world * nrhs / (solve_ms * 1e-3),
+        "sampled_residual": res,
+        "flops_factor": last_stats["flops_factor"], "bytes_factors": last_stats["bytes_factors"],
+        "root_m": last_stats["root_m"],
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                     "launches": nl, "avg_launch_ms": ms / max(nl, 1),
+                     "peak_note": "FP64 ALU peak 152 SMs x 4 flop/clk x 2.07 GHz (recipe figure; no FP64 entry "
+                                  "in the measured peaks)"},
+        "roofline_solve": {"kernel": "solve matvec", "bound": "alu",
+                           "achieved": sol[1] / (sol[0] * 1e-3) / 1e12 if sol[0] else None,
+                           "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                           "frac": (sol[1] / (sol[0] * 1e-3) / 1e12) / PEAK_FP64_TFLOPS if sol[0] else None,
+                           "achieved_gbs": sol[2] / (sol[0] * 1e-3) / 1e9 if sol[0] else None},
+        "profile_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+        "e2e": {"value": world * N / e2e_s, "unit": "unknowns/s (build + factor + 4-RHS solve, host buffers)",
+                "h2d_bytes_per_step": N * 2 * 8 + N * 8 + N * nrhs * 8, "d2h_bytes_per_step": N * nrhs * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and args.workload == WORKLOAD:
+        out["cpu_baseline"] = oracle_sample(n, leaf, eps, a)
+    print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    n, leaf, eps, nrhs, pts, a, F = _inputs()
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        S = O.Factorization(n, leaf, eps, a=a, max_levels=ORACLE_LEVELS, threads=cores)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+        del S
+    dt = sum(times) / len(times)
+    share = sample_share()
+    est = dt / share
+    v = n * n / est
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(n, leaf, eps, nrhs, world),
+           "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+                            "sample": "each step: oracle factor of the %d finest levels (%.2f s on %d threads), "
+                                      "scaled by their %.1f%% share of the factor flops" % (ORACLE_LEVELS, dt, cores,
+                                                                                          100 * share)},
+           "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

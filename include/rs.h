@@ -1,0 +1,174 @@
+/*
+ * rs.h -- C ABI of the GB300 (sm_103a) recursive-skeletonization direct solver for 2D
+ * volume integral equations (Corona, Martinsson & Zorin, arXiv:1303.5466).
+ *
+ * The problem (Sec. 5, "General formulation"): on the n x n cell-centre grid
+ * x_g = ((i1+1/2)h, (i2+1/2)h) of [0,1]^2, h = 1/n, solve A sigma = f with the Nystrom
+ * matrix
+ *   Laplace   (RS_LAPLACE):   A_gg' = -(1/2pi) h^2 log|x_g - x_g'|,
+ *                             A_gg  = a_g - (1/2pi) int_cell log|y - x_g| dy;
+ *   Helmholtz (RS_HELMHOLTZ): A_gg' = kappa^2 b_g (i/4) H0^(1)(kappa|x_g - x_g'|) h^2,
+ *                             A_gg  = a_g + kappa^2 b_g (i/4) int_cell H0^(1)(kappa|y - x_g|) dy,
+ *     factored in the symmetric form of Eq. (5.6) (diagonal similarity by kappa sqrt(b)).
+ * The factorization is the dense-block HSS inverse of Algorithm 1 (with the E formula of
+ * Algorithm 2), built level by level over a binary tree (Sec. 2.2) with proxy-accelerated
+ * interpolative decompositions (Sec. 2.2, Eq. 2.1); the solve is the inverse apply of
+ * Algorithm 6.  Every floating-point step runs in this library's CUDA kernels on the
+ * current device; the host side does integer bookkeeping only.
+ *
+ * Conventions for every function below:
+ *   - return 0 (RS_OK) on success or a negative RS_E_* code; nothing aborts, traps or exits;
+ *     rs_last_error() gives a thread-local message for the last failure on this thread;
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA global memory of
+ *     the current device; arrays are caller-owned and only read/written during the call
+ *     unless stated otherwise;
+ *   - rs_tree and rs_op objects are owned by the library until rs_free_tree / rs_free;
+ *   - point order: the caller's order of `points` ("input order") is used for every
+ *     per-point array (a, b, f, x); the library permutes internally;
+ *   - grid index g = i1 + n*i2 identifies a point in the inspection functions;
+ *   - complex values are interleaved (re, im) doubles.
+ */
+#ifndef RS_H
+#define RS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RS_OK = 0,
+    RS_E_INVALID = -1,        /* bad argument or size                                   */
+    RS_E_NOT_GRID = -2,       /* points are not the cell centres of a uniform n x n grid */
+    RS_E_NOMEM = -3,          /* host or device allocation failed                       */
+    RS_E_SINGULAR = -4,       /* a pivot fell below 1e3 * unit roundoff * largest earlier */
+    RS_E_NOT_CONVERGED = -5,  /* iterative refinement did not reach its tolerance        */
+    RS_E_TIMEOUT = -6,        /* a bounded device-side wait expired                      */
+    RS_E_CUDA = -7            /* a CUDA runtime call failed                              */
+};
+
+typedef enum { RS_LAPLACE = 0, RS_HELMHOLTZ = 1 } rs_kernel_kind;
+typedef enum { RS_FP64 = 0, RS_MIXED_FP32 = 1, RS_C64_REFINED = 2, RS_C128 = 3 } rs_precision;
+
+typedef struct rs_tree rs_tree;
+typedef struct rs_op rs_op;
+
+/* Kernel of the integral operator.  b: host, N values of b(x) in input order, or NULL
+ * (b = 1); must be > 0 everywhere for RS_HELMHOLTZ (the symmetric form divides by it). */
+typedef struct {
+    rs_kernel_kind kind;
+    double kappa;
+    const double* b;
+} rs_kernel;
+
+/* Factorization options; rs_opts_default() fills the values listed here. */
+typedef struct {
+    int proxy_points;            /* points on the proxy circle (Sec. 2.2)            [64]   */
+    double proxy_radius_factor;  /* proxy radius / larger box half-width             [1.5]  */
+    rs_precision precision;      /* arithmetic of the factorization                  [FP64] */
+    double refine_tol;           /* target relative residual of the refined solve    [1e-10]*/
+    int refine_max_iter;         /* refinement cap; past it RS_E_NOT_CONVERGED        [10]   */
+    int64_t k_cut;               /* skeleton size above which blocks are HSS-compressed
+                                    (paper's remark on k_cut, Sec. 4); 0 = never     [0]    */
+    int64_t spin_limit;          /* iteration cap of every device-side wait          [2^26] */
+    int profile;                 /* 1: time every kernel launch with CUDA events on the
+                                    launch stream (rs_op_profile)                     [0]    */
+} rs_opts;
+
+void rs_opts_default(rs_opts* opts);
+const char* rs_last_error(void);
+
+/* Tree (Sec. 2.2): binary bisection of [0,1]^2, splitting x1 at even depth and x2 at odd
+ * depth; box j of level l has children 2j (lower half) and 2j+1 (upper half); leaves are
+ * leaf_side x leaf_side points at depth d = 2 log2(n / leaf_side).
+ * points: host, N x 2 row-major (x1, x2), any order.  N must equal n^2 with
+ * n = leaf_side * 2^L, L >= 1 (else RS_E_INVALID); points must be the cell centres of
+ * [0,1]^2 up to 1e-9 h (else RS_E_NOT_GRID).  *out is owned by the caller until
+ * rs_free_tree. */
+int rs_build_tree(const double* points, int64_t N, int leaf_side, rs_tree** out);
+void rs_free_tree(rs_tree* tree);
+/* n (points per side), depth d, and (optional) grid index g of each input point. */
+int rs_tree_info(const rs_tree* tree, int64_t* n_side, int* depth, int64_t* grid_index_of_input);
+
+/* Host bookkeeping of one level, exposed for tests (no GPU needed).  Leaf level: the
+ * boxes' points ascending in g.  Level l < d: box j's active set is the skeleton of child
+ * 2j followed by that of child 2j+1, each ascending in g, given in child_k (2^(l+1)
+ * counts) and child_skel (their concatenation).  Near rows of box j: active points of the
+ * same-level boxes whose closed rectangles touch box j, strictly inside its proxy circle,
+ * in (neighbour box, active) order.  Outputs: m[2^l], nnear[2^l]; when act / near are
+ * non-NULL they receive the concatenations (caller sizes them from a first call). */
+int rs_tree_level_sets(const rs_tree* tree, int level, const int64_t* child_k,
+                       const int64_t* child_skel, double proxy_radius_factor,
+                       int64_t* m, int64_t* act, int64_t* nnear, int64_t* near);
+
+/* Factor (Algorithm 1; Algorithm 2 line 9 for E).  kernel: see rs_kernel.  a: host, N
+ * values of a(x) in input order, or NULL (a = 1).  eps: ID tolerance; a CPQR step is kept
+ * while |R_ss| > eps |R_00| (Eq. 2.1).  opts: NULL = defaults.  stream: cudaStream_t or
+ * NULL (legacy default stream).  The factors stay resident on the current device until
+ * rs_free.  The call is synchronous with respect to the host. */
+int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps,
+              const rs_opts* opts, void* stream, rs_op** out);
+
+/* Inverse apply (Algorithm 6): x = A^{-1} f for nrhs right-hand sides.  f, x: N x nrhs
+ * column-major in input order, double (Laplace) or interleaved complex128 (Helmholtz);
+ * either both device pointers or both host pointers (detected per call; host buffers are
+ * staged through device memory inside the call).  x may not alias f.  The call returns
+ * after x is written (host) or after the work is enqueued on `stream` (device). */
+int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
+void rs_free(rs_op* op);
+
+/* Statistics of a factorization. */
+typedef struct {
+    int depth;
+    int64_t n_side;
+    int64_t root_m;
+    int64_t bytes_factors;       /* device bytes of the stored factors (Phi, E, T, indices) */
+    int64_t bytes_workspace;     /* device bytes of reusable workspace                     */
+    double flops_factor;         /* algorithmic flops of the factorization (the sum of the
+                                    per-class formulas listed with RS_PROF_*)            */
+    double flops_solve_per_rhs;  /* algorithmic flops of one inverse apply per RHS         */
+    double bytes_solve;          /* factor bytes one inverse apply reads                   */
+    double ms_tree;              /* wall time of the ID phase (Sec. 5 "tree build")        */
+    double ms_inverse;           /* wall time of the inversion phase                       */
+} rs_stats;
+int rs_op_stats(const rs_op* op, rs_stats* out);
+
+/* Kernel classes timed when opts.profile is set.  Factor classes accumulate over rs_factor;
+ * RS_PROF_SOLVE covers the kernels of the most recent rs_solve. */
+enum {
+    RS_PROF_ASSEMBLE_Y = 0,   /* Y = [K(near, I); K(proxy, I)] (work unit: entries)            */
+    RS_PROF_CPQR = 1,         /* column-pivoted QR of Y (flops 4rmk - 2k^2(r+m) + 4k^3/3)       */
+    RS_PROF_ID_T = 2,         /* T = R11^{-1} R12 (flops k^2 (m-k))                             */
+    RS_PROF_ASSEMBLE_F = 3,   /* F (work unit: entries)                                         */
+    RS_PROF_INV_F = 4,        /* Gauss-Jordan F^{-1} (flops 2 m^3)                              */
+    RS_PROF_GEMM_E = 5,       /* W = F^{-1} L, E^{-1} = R W (flops 2m(m-k)k + 2k(m-k)k)          */
+    RS_PROF_INV_E = 6,        /* Gauss-Jordan E (flops 2 k^3)                                   */
+    RS_PROF_INV_ROOT = 7,     /* root F^{-1} (flops 2 m^3)                                      */
+    RS_PROF_SOLVE = 8,        /* inverse apply (flops per RHS 2(2m^2 + 2k^2 + 2k(m-k)))         */
+    RS_PROF_COUNT = 9
+};
+/* ms: summed event time; work: summed algorithmic flops (or entries); launches: count;
+ * bytes: algorithmic bytes the class must move (solve: factor bytes read).  Any output may be
+ * NULL.  Returns RS_E_INVALID for an unknown class. */
+int rs_op_profile(const rs_op* op, int cls, double* ms, double* work, double* bytes, int64_t* launches);
+/* Kernel launches made by this library in this process so far (all threads). */
+int64_t rs_launch_count(void);
+
+/* Per-box inspection (copies from the device).  level 1..d, box 0..2^level-1.
+ * sizes: m (active points), k (skeleton), r (ID rows), nnear (near rows). */
+int rs_op_box_sizes(const rs_op* op, int level, int box, int64_t* m, int64_t* k, int64_t* r,
+                    int64_t* nnear);
+/* which: 0 = active set (m), 1 = near rows (nnear), 2 = skeleton ascending in g (k). */
+int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* out);
+/* which: 0 = T (k x (m-k), rows by skeleton ascending in g, columns by residual in active
+ * order), 1 = F^{-1} (m x m, active order), 2 = E (k x k, skeleton order); row-major. */
+int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out);
+/* Root inverse F_root^{-1} (root_m x root_m, active order = skeletons of boxes (1,0) then
+ * (1,1)), row-major. */
+int rs_op_root_matrix(const rs_op* op, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

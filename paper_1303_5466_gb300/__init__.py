@@ -1,0 +1,260 @@
+"""GB300-native recursive-skeletonization direct solver for 2D volume integral equations
+(Corona, Martinsson & Zorin, arXiv:1303.5466).
+
+This module is a thin ctypes binding of the C ABI in ``include/rs.h``: the functions carry the
+same names and only marshal arguments.  Every floating-point step runs in the CUDA kernels of
+``librs.so``; there is no CPU fallback, and importing the binding fails loudly when the
+library has not been built (``python -m paper_1303_5466_gb300.build`` or
+``__graft_entry__.build()``).
+
+Vectors passed to ``rs_solve`` are N x nrhs column-major in the caller's point order: a numpy
+array of shape (N,) or a Fortran-ordered (N, nrhs) array for host memory, or a torch CUDA
+tensor of shape (N,) or a C-contiguous (nrhs, N) tensor for device memory.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librs.so")
+
+RS_OK, RS_E_INVALID, RS_E_NOT_GRID, RS_E_NOMEM = 0, -1, -2, -3
+RS_E_SINGULAR, RS_E_NOT_CONVERGED, RS_E_TIMEOUT, RS_E_CUDA = -4, -5, -6, -7
+RS_LAPLACE, RS_HELMHOLTZ = 0, 1
+RS_FP64, RS_MIXED_FP32, RS_C64_REFINED, RS_C128 = 0, 1, 2, 3
+PROF_CLASSES = ("assemble_Y", "cpqr", "id_T", "assemble_F", "inv_F", "gemm_E", "inv_E", "inv_root", "solve")
+
+
+class RsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("rs error %d: %s" % (code, msg))
+        self.code = code
+
+
+class rs_kernel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("b", C.POINTER(C.c_double))]
+
+
+class rs_opts(C.Structure):
+    _fields_ = [("proxy_points", C.c_int), ("proxy_radius_factor", C.c_double), ("precision", C.c_int),
+                ("refine_tol", C.c_double), ("refine_max_iter", C.c_int), ("k_cut", C.c_int64),
+                ("spin_limit", C.c_int64), ("profile", C.c_int)]
+
+
+class rs_stats(C.Structure):
+    _fields_ = [("depth", C.c_int), ("n_side", C.c_int64), ("root_m", C.c_int64), ("bytes_factors", C.c_int64),
+                ("bytes_workspace", C.c_int64), ("flops_factor", C.c_double), ("flops_solve_per_rhs", C.c_double),
+                ("bytes_solve", C.c_double), ("ms_tree", C.c_double), ("ms_inverse", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded librs.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librs.so is not built (%s); run paper_1303_5466_gb300.build.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)
+        L.rs_opts_default.argtypes = [C.POINTER(rs_opts)]
+        L.rs_opts_default.restype = None
+        L.rs_last_error.restype = C.c_char_p
+        L.rs_build_tree.argtypes = [dp, C.c_int64, C.c_int, C.POINTER(vp)]
+        L.rs_free_tree.argtypes = [vp]
+        L.rs_free_tree.restype = None
+        L.rs_tree_info.argtypes = [vp, i64p, C.POINTER(C.c_int), i64p]
+        L.rs_tree_level_sets.argtypes = [vp, C.c_int, i64p, i64p, C.c_double, i64p, i64p, i64p, i64p]
+        L.rs_factor.argtypes = [vp, C.POINTER(rs_kernel), dp, C.c_double, C.POINTER(rs_opts), vp, C.POINTER(vp)]
+        L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.rs_free.argtypes = [vp]
+        L.rs_free.restype = None
+        L.rs_op_stats.argtypes = [vp, C.POINTER(rs_stats)]
+        L.rs_op_box_sizes.argtypes = [vp, C.c_int, C.c_int, i64p, i64p, i64p, i64p]
+        L.rs_op_box_indices.argtypes = [vp, C.c_int, C.c_int, C.c_int, i64p]
+        L.rs_op_box_matrix.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp]
+        L.rs_op_root_matrix.argtypes = [vp, dp]
+        L.rs_op_profile.argtypes = [vp, C.c_int, dp, dp, dp, i64p]
+        L.rs_launch_count.restype = C.c_int64
+        L.rs_launch_count.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != RS_OK:
+        raise RsError(rc, rs_last_error())
+    return rc
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i64p(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def rs_last_error():
+    return lib().rs_last_error().decode()
+
+
+def rs_opts_default():
+    o = rs_opts()
+    lib().rs_opts_default(C.byref(o))
+    return o
+
+
+def rs_build_tree(points, leaf_side):
+    """points: (N, 2) float64 host array.  Returns the tree handle (c_void_p)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    out = C.c_void_p()
+    _check(lib().rs_build_tree(_dp(pts), pts.shape[0], int(leaf_side), C.byref(out)))
+    return out
+
+
+def rs_free_tree(tree):
+    lib().rs_free_tree(tree)
+
+
+def rs_tree_info(tree, N=None):
+    n, d = C.c_int64(), C.c_int()
+    g = np.zeros(N, dtype=np.int64) if N else None
+    _check(lib().rs_tree_info(tree, C.byref(n), C.byref(d), _i64p(g)))
+    return n.value, d.value, g
+
+
+def rs_tree_level_sets(tree, level, child_k=None, child_skel=None, proxy_radius_factor=1.5):
+    """Host bookkeeping of one level: (m, act, nnear, near) as int64 arrays."""
+    nb = 1 << level
+    ck = None if child_k is None else np.ascontiguousarray(child_k, dtype=np.int64)
+    cs = None if child_skel is None else np.ascontiguousarray(child_skel, dtype=np.int64)
+    m, nn = np.zeros(nb, np.int64), np.zeros(nb, np.int64)
+    _check(lib().rs_tree_level_sets(tree, level, _i64p(ck), _i64p(cs), proxy_radius_factor, _i64p(m), None,
+                                    _i64p(nn), None))
+    act, near = np.zeros(max(int(m.sum()), 1), np.int64), np.zeros(max(int(nn.sum()), 1), np.int64)
+    _check(lib().rs_tree_level_sets(tree, level, _i64p(ck), _i64p(cs), proxy_radius_factor, _i64p(m), _i64p(act),
+                                    _i64p(nn), _i64p(near)))
+    return m, act[: int(m.sum())], nn, near[: int(nn.sum())]
+
+
+def rs_factor(tree, kernel=None, a=None, eps=1e-10, opts=None, stream=None):
+    """Factor the operator; `kernel` is an rs_kernel or None (Laplace).  Returns the op handle."""
+    k = kernel if kernel is not None else rs_kernel(RS_LAPLACE, 0.0, None)
+    av = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    o = opts if opts is not None else rs_opts_default()
+    out = C.c_void_p()
+    _check(lib().rs_factor(tree, C.byref(k), _dp(av), float(eps), C.byref(o), _stream(stream), C.byref(out)))
+    return out
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return C.c_void_p(s)
+    return C.c_void_p(int(s.cuda_stream))
+
+
+def _ptr(v):
+    if hasattr(v, "data_ptr"):
+        return C.c_void_p(v.data_ptr())
+    return C.c_void_p(v.ctypes.data)
+
+
+def rs_solve(op, f, nrhs, x, stream=None):
+    """x = A^{-1} f; f and x are both host (numpy) or both device (torch CUDA) buffers holding
+    N x nrhs column-major values in input order."""
+    _check(lib().rs_solve(op, _ptr(f), int(nrhs), _ptr(x), _stream(stream)))
+
+
+def rs_free(op):
+    lib().rs_free(op)
+
+
+def rs_op_stats(op):
+    s = rs_stats()
+    _check(lib().rs_op_stats(op, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in rs_stats._fields_}
+
+
+def rs_op_profile(op):
+    """Per-class kernel times (opts.profile): {name: (ms, work, bytes, launches)}."""
+    out = {}
+    for cls, name in enumerate(PROF_CLASSES):
+        ms, w, b, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+        _check(lib().rs_op_profile(op, cls, C.byref(ms), C.byref(w), C.byref(b), C.byref(n)))
+        out[name] = (ms.value, w.value, b.value, n.value)
+    return out
+
+
+def rs_launch_count():
+    return lib().rs_launch_count()
+
+
+def rs_op_box_sizes(op, level, box):
+    m, k, r, nn = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().rs_op_box_sizes(op, level, box, C.byref(m), C.byref(k), C.byref(r), C.byref(nn)))
+    return m.value, k.value, r.value, nn.value
+
+
+def rs_op_box_indices(op, level, box, which):
+    m, k, _, nn = rs_op_box_sizes(op, level, box)
+    cnt = (m, nn, k)[which]
+    out = np.zeros(max(cnt, 1), dtype=np.int64)
+    _check(lib().rs_op_box_indices(op, level, box, which, _i64p(out)))
+    return out[:cnt]
+
+
+def rs_op_box_matrix(op, level, box, which):
+    m, k, _, _ = rs_op_box_sizes(op, level, box)
+    shape = ((k, m - k), (m, m), (k, k))[which]
+    out = np.zeros(max(shape[0] * shape[1], 1))
+    _check(lib().rs_op_box_matrix(op, level, box, which, _dp(out)))
+    return out[: shape[0] * shape[1]].reshape(shape)
+
+
+def rs_op_root_matrix(op):
+    m = rs_op_stats(op)["root_m"]
+    out = np.zeros(m * m)
+    _check(lib().rs_op_root_matrix(op, _dp(out)))
+    return out.reshape(m, m)
+
+
+class Solver:
+    """Convenience owner of a tree and its factorization (frees both on deletion)."""
+
+    def __init__(self, points, leaf_side, a=None, eps=1e-10, kernel=None, opts=None, stream=None):
+        self.N = int(np.asarray(points).shape[0])
+        self.tree = rs_build_tree(points, leaf_side)
+        self.op = None
+        self.op = rs_factor(self.tree, kernel=kernel, a=a, eps=eps, opts=opts, stream=stream)
+
+    def solve(self, f, stream=None):
+        """f: numpy (N,) / (N, nrhs), or torch CUDA (N,) / (nrhs, N).  Returns x of the same kind."""
+        if hasattr(f, "data_ptr"):
+            import torch
+            fc = f.contiguous()
+            nrhs = 1 if fc.dim() == 1 else fc.shape[0]
+            x = torch.empty_like(fc)
+            rs_solve(self.op, fc, nrhs, x, stream if stream is not None else torch.cuda.current_stream())
+            return x
+        fa = np.asarray(f, dtype=np.float64)
+        nrhs = 1 if fa.ndim == 1 else fa.shape[1]
+        fa = np.asfortranarray(fa)
+        x = np.zeros_like(fa, order="F")
+        rs_solve(self.op, fa, nrhs, x, stream)
+        return x
+
+    def stats(self):
+        return rs_op_stats(self.op)
+
+    def __del__(self):
+        if getattr(self, "op", None):
+            rs_free(self.op)
+            self.op = None
+        if getattr(self, "tree", None):
+            rs_free_tree(self.tree)
+            self.tree = None

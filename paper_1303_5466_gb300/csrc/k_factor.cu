@@ -1,0 +1,334 @@
+// k_factor.cu -- kernels of the ID ("tree build") phase and of F assembly.
+//
+//   assemble_Y : Y_i = [ K(near_i, I_i) ; K(proxy_i, I_i) ]  (Sec. 2.2, equivalent densities)
+//   cpqr       : Householder QR with column pivoting of Y_i  (Sec. 2.1, Eq. 2.1)
+//   id_T       : T_i = R11^{-1} R12                           (Eq. 2.1)
+//   assemble_F : F_i = D_i (+ diag(E_c1, E_c2))                (Algorithm 1, lines 2-6)
+#include "k_common.cuh"
+
+namespace rs {
+
+__device__ __forceinline__ void grid_xy(const LaplaceK& K, int g, double& x, double& y)
+{
+    const int i1 = g % K.n, i2 = g / K.n;
+    x = ((double)i1 + 0.5) * K.h;
+    y = ((double)i2 + 0.5) * K.h;
+}
+
+// Off-diagonal Laplace entry -(1/2pi) h^2 log|x - y| = c0 log(|x - y|^2), c0 = -h^2/(4pi).
+__device__ __forceinline__ double lap_entry(const LaplaceK& K, int g, int gp)
+{
+    double x, y, xp, yp;
+    grid_xy(K, g, x, y);
+    grid_xy(K, gp, xp, yp);
+    const double dx = x - xp, dy = y - yp;
+    return K.c0 * log(dx * dx + dy * dy);
+}
+
+// ------------------------------------------------------------------ Y assembly
+__global__ void __launch_bounds__(256) assemble_Y_kernel(const int32_t* __restrict__ act,
+        const int64_t* __restrict__ act_off, const int32_t* __restrict__ near,
+        const int64_t* __restrict__ near_off, const double* __restrict__ geo,
+        const double* __restrict__ ucirc, int P, const int64_t* __restrict__ y_off,
+        double* __restrict__ Y, LaplaceK K)
+{
+    const int b = blockIdx.y;
+    const int64_t a0 = act_off[b];
+    const int m = (int)(act_off[b + 1] - a0);
+    const int64_t n0 = near_off[b];
+    const int nn = (int)(near_off[b + 1] - n0);
+    const int r = nn + P;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)r * m) return;
+    const int j = (int)(e / r), i = (int)(e - (int64_t)j * r);
+    const int g = act[a0 + j];
+    double v;
+    if (i < nn) {
+        v = lap_entry(K, near[n0 + i], g);
+    } else {
+        const int q = i - nn;
+        const double cx = geo[3 * b], cy = geo[3 * b + 1], R = geo[3 * b + 2];
+        const double zx = cx + R * ucirc[q], zy = cy + R * ucirc[P + q];
+        double x, y;
+        grid_xy(K, g, x, y);
+        const double dx = zx - x, dy = zy - y;
+        v = K.c0 * log(dx * dx + dy * dy);
+    }
+    Y[y_off[b] + e] = v;
+}
+
+cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const int64_t* act_off,
+                              const int32_t* near, const int64_t* near_off, const double* geo,
+                              const double* ucirc, int P, const int64_t* y_off, double* Y, LaplaceK K,
+                              int max_entries)
+{
+    if (nb <= 0 || max_entries <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((max_entries + 255) / 256), (unsigned)nb);
+    count_launches(1);
+    assemble_Y_kernel<<<grid, 256, 0, st>>>(act, act_off, near, near_off, geo, ucirc, P, y_off, Y, K);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ column-pivoted QR
+// One group of G CTAs per box; CTA gi owns columns [c0, c1) of the box's Y (column-major,
+// ld = r).  Columns never move: the pivot order is recorded in piv[], and R is read back
+// from the physical columns (rows < k) with its diagonal in diag[].  Each step:
+//   1. every CTA finds the best pivot key among its unselected columns; the group max
+//      (via `keys` and one barrier when G > 1) names the pivot column p;
+//   2. every CTA builds the Householder vector of column p (rows s..r-1) in shared memory;
+//   3. every CTA applies the reflector to its unselected columns (one warp per column, lanes
+//      over rows, shuffle reductions) and downdates their squared norms, recomputing a norm
+//      from the data once it falls below 1e-4 of the value it was last computed from.
+// The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step.
+template <int NT>
+__global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restrict__ act_off,
+        const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
+        double* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
+        double* __restrict__ diag, unsigned int* __restrict__ bar, unsigned long long* __restrict__ keys,
+        int* __restrict__ status, long long spin)
+{
+    extern __shared__ double smem[];
+    __shared__ double dred[NT / 32];
+    __shared__ unsigned long long kred[NT / 32];
+    __shared__ unsigned long long s_key;
+
+    const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
+    const int64_t a0 = act_off[b];
+    const int m = (int)(act_off[b + 1] - a0);
+    const int r = nnear[b] + P;
+    double* __restrict__ Y = Yall + y_off[b];
+    const int per = (m + G - 1) / G;
+    const int c0 = min(m, gi * per), c1 = min(m, c0 + per);
+    const int nown = c1 - c0;
+    double* v = smem;                         // r
+    double* nrm = v + r;                      // nown
+    double* ref = nrm + nown;                 // nown
+    int* sel = (int*)(ref + nown);            // nown
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = NT / 32;
+
+    for (int jj = warp; jj < nown; jj += NW) {
+        const double* col = Y + (int64_t)(c0 + jj) * r;
+        double s = 0.0;
+        for (int i = lane; i < r; i += 32) { const double x = col[i]; s += x * x; }
+        s = warp_sum(s);
+        if (lane == 0) { nrm[jj] = s; ref[jj] = s; sel[jj] = 0; }
+    }
+    __syncthreads();
+
+    const int kmax = min(r, m);
+    int k = 0;
+    double alpha0 = 0.0;
+    for (int s = 0; s < kmax; ++s) {
+        unsigned long long best = 0;
+        for (int jj = threadIdx.x; jj < nown; jj += NT)
+            if (!sel[jj]) {
+                const unsigned long long q = pivot_key(nrm[jj], c0 + jj);
+                best = q > best ? q : best;
+            }
+        best = block_max_u64<NT>(best, kred);
+        if (G > 1) {
+            if (threadIdx.x == 0) keys[((int64_t)b * 2 + (s & 1)) * G + gi] = best;
+            if (!group_sync(bar + b, (unsigned)(s + 1) * (unsigned)G, status, spin)) return;
+            if (threadIdx.x == 0) {
+                unsigned long long t = 0;
+                for (int q = 0; q < G; ++q) {
+                    const unsigned long long u = __ldcg(keys + ((int64_t)b * 2 + (s & 1)) * G + q);
+                    t = u > t ? u : t;
+                }
+                s_key = t;
+            }
+            __syncthreads();
+            best = s_key;
+        }
+        const int p = (int)(KEY_MASK - (best & KEY_MASK));
+        const double* colp = Y + (int64_t)p * r;
+        double part = 0.0;
+        for (int i = s + threadIdx.x; i < r; i += NT) {
+            const double x = __ldcg(colp + i);
+            v[i] = x;
+            part += x * x;
+        }
+        const double a2 = block_sum<NT>(part, dred);
+        const double alpha = sqrt(a2);
+        if (s == 0) alpha0 = alpha;
+        if (!(alpha > eps * alpha0)) break;
+        const double x0 = v[s];
+        const double beta = (x0 < 0.0) ? alpha : -alpha;
+        const double tau = 1.0 / (alpha * (alpha + fabs(x0)));   // 2 / ||v||^2
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            v[s] = x0 - beta;
+            if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
+        }
+        if (threadIdx.x == 0 && p >= c0 && p < c1) sel[p - c0] = 1;
+        __syncthreads();
+        for (int jj = warp; jj < nown; jj += NW) {
+            if (sel[jj]) continue;
+            double* col = Y + (int64_t)(c0 + jj) * r;
+            double w = 0.0;
+            for (int i = s + lane; i < r; i += 32) w += v[i] * col[i];
+            w = warp_sum(w);
+            const double tw = tau * w;
+            double rsj = 0.0;
+            for (int i = s + lane; i < r; i += 32) {
+                const double u = col[i] - v[i] * tw;
+                col[i] = u;
+                if (i == s) rsj = u;
+            }
+            rsj = __shfl_sync(0xffffffffu, rsj, 0);
+            double nv = nrm[jj] - rsj * rsj;
+            if (nv < 1e-4 * ref[jj]) {
+                double q = 0.0;
+                for (int i = s + 1 + lane; i < r; i += 32) { const double x = col[i]; q += x * x; }
+                q = warp_sum(q);
+                nv = q;
+                if (lane == 0) ref[jj] = q;
+            }
+            if (lane == 0) nrm[jj] = nv;
+        }
+        __syncthreads();
+        k = s + 1;
+    }
+    if (gi == 0 && threadIdx.x == 0) kout[b] = k;
+}
+
+cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
+                        const int64_t* y_off, double* Y, double eps, int32_t* kout, int32_t* piv, double* diag,
+                        unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
+                        int max_m)
+{
+    constexpr int NT = 256;
+    if (nb <= 0) return cudaSuccess;
+    // shared: v (r) + nrm, ref (own columns) + sel
+    const int per = (max_m + G - 1) / G;
+    const size_t shm = sizeof(double) * ((size_t)max_r + 2 * (size_t)per) + sizeof(int) * (size_t)per + 64;
+    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    if (G == 1) {
+        cpqr_kernel<NT><<<nb, NT, shm, st>>>(G, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys,
+                                             status, spin_limit);
+        return cudaGetLastError();
+    }
+    void* args[] = {(void*)&G, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y, (void*)&eps,
+                    (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
+                    (void*)&spin_limit};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
+}
+
+int cpqr_max_ctas(int max_r, int max_m, int G)
+{
+    constexpr int NT = 256;
+    const int per = (max_m + G - 1) / G;
+    const size_t shm = sizeof(double) * ((size_t)max_r + 2 * (size_t)per) + sizeof(int) * (size_t)per + 64;
+    cudaFuncSetAttribute(cpqr_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel<NT>, NT, shm) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
+
+// ------------------------------------------------------------------ T = R11^{-1} R12
+// One CTA per (box, group of NC residual columns): back substitution by columns of R11, so
+// each step reads one contiguous column of R.
+template <int NT, int NC>
+__global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ act_off, const int32_t* __restrict__ kk,
+        const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off, const double* __restrict__ Yall,
+        const int32_t* __restrict__ piv, const double* __restrict__ diag, const int32_t* __restrict__ skpos,
+        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, double* __restrict__ T)
+{
+    extern __shared__ double ys[];   // NC x k
+    const int b = blockIdx.x;
+    const int64_t a0 = act_off[b];
+    const int m = (int)(act_off[b + 1] - a0);
+    const int k = kk[b];
+    const int nres = m - k;
+    const int cb = blockIdx.y * NC;
+    if (cb >= nres || k == 0) return;
+    const int nc = min(NC, nres - cb);
+    const int r = nnear[b] + P;
+    const double* Y = Yall + y_off[b];
+    double* Tb = T + t_off[b];
+    for (int q = 0; q < nc; ++q) {
+        const double* col = Y + (int64_t)rscol[a0 + cb + q] * r;
+        for (int a = threadIdx.x; a < k; a += NT) ys[q * k + a] = col[a];
+    }
+    for (int a = k - 1; a >= 0; --a) {
+        __syncthreads();
+        const double Raa = diag[a0 + a];
+        double t[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) t[q] = (q < nc) ? ys[q * k + a] / Raa : 0.0;
+        if (threadIdx.x == 0) {
+            const int row = skpos[a0 + a];
+            for (int q = 0; q < nc; ++q) Tb[(int64_t)(cb + q) * k + row] = t[q];
+        }
+        const double* Ra = Y + (int64_t)piv[a0 + a] * r;
+        for (int i = threadIdx.x; i < a; i += NT) {
+            const double R = Ra[i];
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+                if (q < nc) ys[q * k + i] -= t[q] * R;
+        }
+    }
+}
+
+cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const int32_t* kk, const int32_t* nnear,
+                        int P, const int64_t* y_off, const double* Y, const int32_t* piv, const double* diag,
+                        const int32_t* skpos, const int32_t* rscol, const int64_t* t_off, double* T, int max_cols,
+                        int max_k)
+{
+    constexpr int NT = 128, NC = 4;
+    if (nb <= 0 || max_cols <= 0 || max_k <= 0) return cudaSuccess;
+    const size_t shm = sizeof(double) * (size_t)NC * (size_t)max_k;
+    cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)nb, (unsigned)((max_cols + NC - 1) / NC));
+    id_T_kernel<NT, NC><<<grid, NT, shm, st>>>(act_off, kk, nnear, P, y_off, Y, piv, diag, skpos, rscol, t_off, T);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ F assembly
+__global__ void __launch_bounds__(256) assemble_F_kernel(int leaf, const int32_t* __restrict__ act,
+        const int64_t* __restrict__ act_off, const int32_t* __restrict__ perm, const double* __restrict__ a,
+        const int64_t* __restrict__ phi_off, double* __restrict__ Phi, const int32_t* __restrict__ child_k,
+        const int64_t* __restrict__ child_e_off, const double* __restrict__ childE, LaplaceK K)
+{
+    const int b = blockIdx.y;
+    const int64_t a0 = act_off[b];
+    const int m = (int)(act_off[b + 1] - a0);
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int q = (int)(e / m), p = (int)(e - (int64_t)q * m);     // column-major (p row, q col)
+    const int i = perm[a0 + p], j = perm[a0 + q];                  // natural positions
+    const int gi = act[a0 + i], gj = act[a0 + j];
+    double v;
+    if (leaf) {
+        v = (i == j) ? a[gi] + K.self : lap_entry(K, gi, gj);
+    } else {
+        const int k1 = child_k[2 * b], k2 = child_k[2 * b + 1];
+        if (i < k1 && j < k1) v = childE[child_e_off[2 * b] + (int64_t)j * k1 + i];
+        else if (i >= k1 && j >= k1) v = childE[child_e_off[2 * b + 1] + (int64_t)(j - k1) * k2 + (i - k1)];
+        else v = lap_entry(K, gi, gj);
+    }
+    Phi[phi_off[b] + e] = v;
+}
+
+cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act, const int64_t* act_off,
+                              const int32_t* perm, const double* a, const int64_t* phi_off, double* Phi,
+                              const int32_t* child_k, const int64_t* child_e_off, const double* childE, LaplaceK K,
+                              int max_m)
+{
+    if (nb <= 0 || max_m <= 0) return cudaSuccess;
+    const int64_t ent = (int64_t)max_m * max_m;
+    dim3 grid((unsigned)((ent + 255) / 256), (unsigned)nb);
+    count_launches(1);
+    assemble_F_kernel<<<grid, 256, 0, st>>>(leaf ? 1 : 0, act, act_off, perm, a, phi_off, Phi, child_k, child_e_off,
+                                            childE, K);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

@@ -1,0 +1,439 @@
+// k_linalg.cu -- batched dense kernels of the inversion and solve phases.
+//
+//   gj_inverse : in-place Gauss-Jordan inverse with partial pivoting (F_i^{-1}, E_i)
+//   gemm       : grouped GEMM over the boxes of a level (E_i^{-1} = R_i F_i^{-1} L_i)
+//   matvec     : batched y = alpha op(A) x + beta y for nrhs right-hand sides (Algorithm 6)
+//   gathers    : index gathers/scatters between the tree levels of the solve
+#include <float.h>
+
+#include "k_common.cuh"
+
+namespace rs {
+
+// ------------------------------------------------------------------ Gauss-Jordan inverse
+// G CTAs per matrix; CTA gi owns columns [c0, c1).  Step c: the owner of column c picks the
+// pivot row p (largest |A_ic|, i >= c, lowest i on ties), publishes the row-swapped column c
+// and p (double buffered by step parity); after one barrier every CTA swaps rows c and p in
+// its columns and applies the rank-1 Gauss-Jordan update.  A pivot with |pivot| not above
+// 1e3 * unit roundoff * (largest earlier pivot) sets DEV_SINGULAR (the loop still finishes).
+template <int NT>
+__global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
+        double* __restrict__ Aall, int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off,
+        double* __restrict__ colbuf, const int64_t* __restrict__ cb_off, int* __restrict__ pivrow,
+        unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
+{
+    extern __shared__ double sm[];
+    __shared__ double dred[NT / 32];
+    __shared__ int ired[NT / 32];
+    __shared__ int s_p;
+    const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
+    const int m = msz[b];
+    double* __restrict__ A = Aall + off[b];
+    const int per = (m + G - 1) / G;
+    const int c0 = min(m, gi * per), c1 = min(m, c0 + per);
+    const int nown = c1 - c0;
+    double* f = sm;                 // m
+    double* rowp = f + m;           // per
+    double* rowc = rowp + per;      // per
+    double* cb = colbuf + cb_off[b];
+    int* prow = pivrow + 2 * b;
+    int32_t* ip = ipiv + ipiv_off[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double maxpiv = 0.0;
+    for (int c = 0; c < m; ++c) {
+        const int owner = c / per;
+        if (gi == owner) {
+            const double* col = A + (int64_t)c * m;
+            double best = -1.0;
+            int bi = m;
+            for (int i = c + threadIdx.x; i < m; i += NT) {
+                const double a = fabs(col[i]);
+                if (a > best) { best = a; bi = i; }
+            }
+            // block argmax, lowest index on ties
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            __syncthreads();
+            if (lane == 0) { dred[warp] = best; ired[warp] = bi; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double bb = dred[0];
+                int ii = ired[0];
+                for (int q = 1; q < NT / 32; ++q)
+                    if (dred[q] > bb || (dred[q] == bb && ired[q] < ii)) { bb = dred[q]; ii = ired[q]; }
+                s_p = ii < m ? ii : c;
+            }
+            __syncthreads();
+            const int p = s_p;
+            double* out = cb + (int64_t)(c & 1) * m;
+            for (int i = threadIdx.x; i < m; i += NT) {
+                const int src = (i == c) ? p : ((i == p) ? c : i);
+                out[i] = col[src];
+            }
+            if (threadIdx.x == 0) { prow[c & 1] = p; ip[c] = p; }
+        }
+        if (G > 1) {
+            if (!group_sync(bar + b, (unsigned)(c + 1) * (unsigned)G, status, spin)) return;
+        } else {
+            __syncthreads();
+        }
+        const int p = (G > 1) ? __ldcg(prow + (c & 1)) : prow[c & 1];
+        const double* src = cb + (int64_t)(c & 1) * m;
+        for (int i = threadIdx.x; i < m; i += NT) f[i] = (G > 1) ? __ldcg(src + i) : src[i];
+        for (int jj = threadIdx.x; jj < nown; jj += NT) {
+            const int j = c0 + jj;
+            rowp[jj] = A[(int64_t)j * m + p];
+            rowc[jj] = A[(int64_t)j * m + c];
+        }
+        __syncthreads();
+        const double pv = f[c];
+        if (!(fabs(pv) > 1e3 * 0.5 * DBL_EPSILON * maxpiv) || !isfinite(pv) || pv == 0.0) {
+            if (threadIdx.x == 0 && gi == 0) atomicOr(status, DEV_SINGULAR);
+        }
+        maxpiv = fmax(maxpiv, fabs(pv));
+        const double pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
+        // columns: warps stride over own columns, lanes over rows
+        for (int jj = warp; jj < nown; jj += NT / 32) {
+            const int j = c0 + jj;
+            double* colj = A + (int64_t)j * m;
+            if (j == c) {
+                for (int i = lane; i < m; i += 32) colj[i] = (i == c) ? pinv : -f[i] * pinv;
+            } else {
+                const double aj = rowp[jj] * pinv;
+                const double oc = rowc[jj];
+                for (int i = lane; i < m; i += 32) {
+                    double u;
+                    if (i == c) u = aj;
+                    else if (i == p) u = oc - f[p] * aj;
+                    else u = colj[i] - f[i] * aj;
+                    colj[i] = u;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Undo the row exchanges: swap columns (c, ipiv[c]) for c = m-1 .. 0.  One CTA per matrix.
+__global__ void __launch_bounds__(256) gj_unpivot_kernel(const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
+        double* __restrict__ Aall, const int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off)
+{
+    const int b = blockIdx.x;
+    const int m = msz[b];
+    double* A = Aall + off[b];
+    const int32_t* ip = ipiv + ipiv_off[b];
+    for (int c = m - 1; c >= 0; --c) {
+        const int p = ip[c];
+        if (p == c) continue;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double t = A[(int64_t)c * m + i];
+            A[(int64_t)c * m + i] = A[(int64_t)p * m + i];
+            A[(int64_t)p * m + i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+static size_t gj_shm(int max_m, int G) { return sizeof(double) * ((size_t)max_m + 2 * (size_t)((max_m + G - 1) / G)) + 64; }
+
+int gj_max_ctas(int max_m, int G)
+{
+    constexpr int NT = 256;
+    const size_t shm = gj_shm(max_m, G);
+    cudaFuncSetAttribute(gj_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<NT>, NT, shm) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, double* A,
+                              int32_t* ipiv, const int64_t* ipiv_off, double* colbuf, const int64_t* colbuf_off,
+                              int* pivrow, unsigned int* bar, int* status, long long spin_limit, int max_m)
+{
+    constexpr int NT = 256;
+    if (nb <= 0 || max_m <= 0) return cudaSuccess;
+    const size_t shm = gj_shm(max_m, G);
+    cudaError_t e = cudaFuncSetAttribute(gj_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    if (G == 1) {
+        gj_kernel<NT><<<nb, NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, colbuf, colbuf_off, pivrow, bar, status,
+                                           spin_limit);
+    } else {
+        void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&colbuf,
+                        (void*)&colbuf_off, (void*)&pivrow, (void*)&bar, (void*)&status, (void*)&spin_limit};
+        count_launches(1);
+        e = cudaLaunchCooperativeKernel((void*)gj_kernel<NT>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    gj_unpivot_kernel<<<nb, 256, 0, st>>>(m, off, A, ipiv, ipiv_off);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ grouped GEMM (FP64)
+// 64 x 64 tile per CTA, 256 threads with a 4 x 4 register block each, K in steps of 16.
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmProb* __restrict__ probs, int np,
+        const double* __restrict__ Ab, const double* __restrict__ Bb, double* Cb, const double* C0b)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int64_t t = blockIdx.x;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const GemmProb P = probs[lo];
+    const int64_t lt = t - P.tile0;
+    const int tm = (int)(lt % P.tiles_m), tn = (int)(lt / P.tiles_m);
+    const int row0 = tm * BM, col0 = tn * BN;
+    const double* A = Ab + P.a_off;
+    const double* B = Bb + P.b_off;
+    double* C = Cb + P.c_off;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = 0.0;
+    for (int k0 = 0; k0 < P.K; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            const int i = e % BM, kk = e / BM;
+            const int gi = row0 + i, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < P.M && gk < P.K) v = P.ta ? A[(int64_t)gi * P.lda + gk] : A[(int64_t)gk * P.lda + gi];
+            As[kk][i] = v;
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += 256) {
+            const int kk = e % BK, j = e / BK;
+            const int gj = col0 + j, gk = k0 + kk;
+            double v = 0.0;
+            if (gj < P.N && gk < P.K) v = P.tb ? B[(int64_t)gk * P.ldb + gj] : B[(int64_t)gj * P.ldb + gk];
+            Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) bv[w] = Bs[kk][ty + 16 * w];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], bv[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int gi = row0 + tx + 16 * u, gj = col0 + ty + 16 * w;
+            if (gi < P.M && gj < P.N) {
+                double* c = C + (int64_t)gj * P.ldc + gi;
+                const double c0 = (P.beta == 0.0) ? 0.0 : C0b[P.c0_off + (int64_t)gj * P.ldc0 + gi];
+                *c = P.alpha * acc[u][w] + P.beta * c0;
+            }
+        }
+}
+
+cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const double* A,
+                        const double* B, double* C, const double* C0)
+{
+    if (np <= 0 || tiles <= 0) return cudaSuccess;
+    count_launches(1);
+    gemm_kernel<<<(unsigned)tiles, 256, 0, st>>>(probs, np, A, B, C, C0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched matvec(s)
+// Each CTA produces 64 output rows of one problem for all nrhs columns (chunks of 8).
+__global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restrict__ probs,
+        const int64_t* __restrict__ blk0, int np, const double* __restrict__ Ab, const double* __restrict__ xb,
+        double* __restrict__ yb, int nrhs)
+{
+    constexpr int RB = 64, CH = 8;
+    __shared__ double part[4][RB][CH];
+    const int64_t t = blockIdx.x;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const MatvecProb P = probs[lo];
+    const int orow0 = (int)(t - blk0[lo]) * RB;
+    const double* A = Ab + P.a_off;
+    const double* x = xb + P.x_off * nrhs;
+    double* y = yb + P.y_off * nrhs;
+    const int out_n = P.trans ? P.cols : P.rows;
+    const int in_n = P.trans ? P.rows : P.cols;
+    for (int c0 = 0; c0 < nrhs; c0 += CH) {
+        const int nc = min(CH, nrhs - c0);
+        double acc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+        if (!P.trans) {
+            const int ri = threadIdx.x & 63, cj = threadIdx.x >> 6;   // 64 rows x 4 column phases
+            const int i = orow0 + ri;
+            if (i < out_n) {
+                for (int j = cj; j < in_n; j += 4) {
+                    const double a = A[(int64_t)j * P.ld + i];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (c < nc) acc[c] = fma(a, x[(int64_t)j * nrhs + c0 + c], acc[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) part[cj][ri][c] = acc[c];
+            __syncthreads();
+            if (threadIdx.x < RB) {
+                const int i2 = orow0 + threadIdx.x;
+                if (i2 < out_n)
+                    for (int c = 0; c < nc; ++c) {
+                        const double s = part[0][threadIdx.x][c] + part[1][threadIdx.x][c] + part[2][threadIdx.x][c] +
+                                         part[3][threadIdx.x][c];
+                        double* yy = y + (int64_t)i2 * nrhs + c0 + c;
+                        *yy = (P.beta == 0.0) ? P.alpha * s : P.alpha * s + P.beta * (*yy);
+                    }
+            }
+            __syncthreads();
+        } else {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int q = warp; q < RB; q += 8) {
+                const int j = orow0 + q;
+                if (j >= out_n) break;
+                double a2[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) a2[c] = 0.0;
+                const double* colj = A + (int64_t)j * P.ld;
+                for (int i = lane; i < in_n; i += 32) {
+                    const double a = colj[i];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (c < nc) a2[c] = fma(a, x[(int64_t)i * nrhs + c0 + c], a2[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < CH; ++c) a2[c] = warp_sum(a2[c]);
+                if (lane == 0)
+                    for (int c = 0; c < nc; ++c) {
+                        double* yy = y + (int64_t)j * nrhs + c0 + c;
+                        *yy = (P.beta == 0.0) ? P.alpha * a2[c] : P.alpha * a2[c] + P.beta * (*yy);
+                    }
+            }
+        }
+    }
+}
+
+cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np, int64_t blocks,
+                          const double* A, const double* x, double* y, int nrhs)
+{
+    if (np <= 0 || blocks <= 0) return cudaSuccess;
+    count_launches(1);
+    matvec_kernel<<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gathers
+__global__ void gather_rows_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
+                                   double* __restrict__ out, int nrhs)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count * nrhs) return;
+    const int64_t p = e / nrhs;
+    const int c = (int)(e - p * nrhs);
+    out[e] = in[idx[p] * nrhs + c];
+}
+
+__global__ void scatter_rows_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
+                                    double* __restrict__ out, int nrhs)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count * nrhs) return;
+    const int64_t p = e / nrhs;
+    const int c = (int)(e - p * nrhs);
+    out[idx[p] * nrhs + c] = in[e];
+}
+
+__global__ void gather_cm_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
+                                 int64_t N, double* __restrict__ out, int nrhs)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count * nrhs) return;
+    const int64_t p = e / nrhs;
+    const int c = (int)(e - p * nrhs);
+    out[e] = in[(int64_t)c * N + idx[p]];
+}
+
+__global__ void scatter_cm_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
+                                  int64_t N, double* __restrict__ out, int nrhs)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count * nrhs) return;
+    const int64_t p = e / nrhs;
+    const int c = (int)(e - p * nrhs);
+    out[(int64_t)c * N + idx[p]] = in[e];
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) y[e] = a * x[e] + b * y[e];
+}
+
+static unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+cudaError_t launch_gather_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, double* out,
+                               int nrhs)
+{
+    if (count <= 0) return cudaSuccess;
+    count_launches(1);
+    gather_rows_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, out, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, double* out,
+                                int nrhs)
+{
+    if (count <= 0) return cudaSuccess;
+    count_launches(1);
+    scatter_rows_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, out, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, int64_t N,
+                             double* out, int nrhs)
+{
+    if (count <= 0) return cudaSuccess;
+    count_launches(1);
+    gather_cm_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, N, out, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, int64_t N,
+                              double* out, int nrhs)
+{
+    if (count <= 0) return cudaSuccess;
+    count_launches(1);
+    scatter_cm_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, N, out, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    axpby_kernel<<<nblk(n), 256, 0, st>>>(n, a, x, b, y);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

@@ -1,0 +1,768 @@
+// rs_factor.cpp -- rs_factor / rs_solve: host orchestration of the per-level CUDA kernels.
+//
+// Factor (Algorithm 1, level by level, every box of a level in one launch):
+//   ID phase   (l = d..1): Y assembly -> column-pivoted QR -> T = R11^{-1} R12
+//   inverse    (l = d..1): F' = Pi^T F Pi -> Phi = F'^{-1} (Gauss-Jordan) ->
+//              W = Phi L, E^{-1} = R W (grouped GEMMs) -> E (Gauss-Jordan); root: F_root^{-1}
+// Solve (Algorithm 6 as the recursion of Eqs. 2.10-2.12), nrhs columns per launch.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "rs_host.h"
+
+namespace rs {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point t0) { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
+
+template <class T>
+int upload(DevMem& d, const std::vector<T>& h, cudaStream_t st)
+{
+    RS_CUDA(d.alloc(sizeof(T) * (h.empty() ? 1 : h.size())));
+    if (!h.empty()) RS_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+    return RS_OK;
+}
+
+template <class T>
+std::vector<int32_t> to32(const std::vector<T>& v)
+{
+    std::vector<int32_t> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (int32_t)v[i];
+    return o;
+}
+
+// Event pair around one kernel launch when opts.profile is set; the elapsed time and the
+// launch's algorithmic work are added to the class sums by prof_flush after a sync.
+struct ProfScope {
+    rs_op* op;
+    int cls;
+    cudaStream_t st;
+    double work, bytes;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    static cudaEvent_t take(rs_op* o)
+    {
+        if (!o->ev_pool.empty()) {
+            cudaEvent_t e = o->ev_pool.back();
+            o->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        o->ev_all.push_back(e);
+        return e;
+    }
+    ProfScope(rs_op* o, int c, cudaStream_t s, double w, double b = 0.0) : op(o), cls(c), st(s), work(w), bytes(b)
+    {
+        if (!op->opts.profile) return;
+        e0 = take(op);
+        e1 = take(op);
+        if (e0 && e1) cudaEventRecord(e0, st);
+    }
+    ~ProfScope()
+    {
+        if (!e0 || !e1) return;
+        cudaEventRecord(e1, st);
+        op->pending.push_back({cls, e0, e1, work, bytes});
+    }
+};
+
+void prof_flush(rs_op* op)
+{
+    for (const ProfRec& r : op->pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+            op->prof_ms[r.cls] += ms;
+            op->prof_work[r.cls] += r.work;
+            op->prof_bytes[r.cls] += r.bytes;
+            op->prof_n[r.cls] += 1;
+        }
+        op->ev_pool.push_back(r.e0);
+        op->ev_pool.push_back(r.e1);
+    }
+    op->pending.clear();
+}
+
+int check_status(rs_op* op, cudaStream_t st)
+{
+    RS_CUDA(cudaStreamSynchronize(st));
+    prof_flush(op);
+    int s = 0;
+    RS_CUDA(cudaMemcpy(&s, op->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s & DEV_TIMEOUT) return fail(RS_E_TIMEOUT, "a device-side wait exceeded spin_limit");
+    if (s & DEV_SINGULAR) return fail(RS_E_SINGULAR, "pivot below 1e3 unit roundoff times the largest earlier pivot");
+    return RS_OK;
+}
+
+// Pick the CTA group size per box for a cooperative kernel: 1 (plain launch) when the boxes
+// alone fill the GPU, otherwise as many CTAs per box as stay co-resident (at most one per
+// 32 columns and 64 in all).
+int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
+{
+    const int gmax = std::max(1, std::min(max_cols / 32, 64));
+    const int cap1 = capacity(1);
+    if (gmax == 1 || nb >= cap1) return 1;
+    int G = std::min(gmax, cap1 / std::max(nb, 1));
+    while (G > 1 && nb * G > capacity(G)) --G;
+    return std::max(G, 1);
+}
+
+// Workspace of the ID phase, released when rs_factor returns.
+struct IdWork {
+    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys;
+};
+
+int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, double* A,
+           const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls)
+{
+    if (max_m <= 0) return RS_OK;
+    std::vector<int64_t> cb_off(nb);
+    for (int b = 0; b < nb; ++b) cb_off[b] = 2 * size_off[b];
+    DevMem d_ipoff, d_cboff;
+    RS_CUDA(d_ipoff.alloc(sizeof(int64_t) * nb));
+    RS_CUDA(cudaMemcpyAsync(d_ipoff.p, size_off.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
+    if (upload(d_cboff, cb_off, st)) return RS_E_CUDA;
+    const int64_t tot = size_off[nb];
+    RS_CUDA(op->d_ipiv.alloc(sizeof(int32_t) * (tot + 1)));
+    RS_CUDA(op->d_colbuf.alloc(sizeof(double) * (2 * tot + 1)));
+    RS_CUDA(op->d_pivrow.alloc(sizeof(int) * 2 * nb));
+    RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
+    RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
+    const int G = choose_group(nb, max_m, [&](int g) { return gj_max_ctas(max_m, g); });
+    double work = 0.0;
+    for (int b = 0; b < nb; ++b) work += 2.0 * (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
+    ProfScope ps(op, cls, st, work, 16.0 * (double)size_off[nb]);
+    RS_CUDA(launch_gj_inverse(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_ipiv.as<int32_t>(),
+                              d_ipoff.as<int64_t>(), op->d_colbuf.as<double>(), d_cboff.as<int64_t>(),
+                              op->d_pivrow.as<int>(), op->d_bar.as<unsigned int>(), op->d_status.as<int>(),
+                              (long long)op->opts.spin_limit, max_m));
+    return check_status(op, st);
+}
+
+// ID phase of one level (Sec. 2.2 proxy ID, Eq. 2.1).
+int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st)
+{
+    const int P = op->opts.proxy_points;
+    int rc = level_sets(op->n, op->d, L.l, child ? child->k.data() : nullptr, child ? child->skel.data() : nullptr,
+                        op->opts.proxy_radius_factor, L.m, L.act, L.act_off, L.nn, L.nearv, L.near_off);
+    if (rc) return rc;
+    const int nb = L.nb;
+    L.r.resize(nb);
+    std::vector<int64_t> y_off(nb + 1, 0);
+    std::vector<double> geo(3 * nb);
+    int64_t max_entries = 0;
+    L.max_m = L.max_r = 0;
+    for (int b = 0; b < nb; ++b) {
+        L.r[b] = L.nn[b] + P;
+        y_off[b + 1] = y_off[b] + L.r[b] * L.m[b];
+        max_entries = std::max(max_entries, L.r[b] * L.m[b]);
+        L.max_m = std::max<int>(L.max_m, (int)L.m[b]);
+        L.max_r = std::max<int>(L.max_r, (int)L.r[b]);
+        const BoxInt bi = box_int(op->n, L.l, b);
+        const double hh = 0.5 * op->K.h;
+        geo[3 * b] = (double)((2 * bi.bx + 1) * bi.wx) * hh;
+        geo[3 * b + 1] = (double)((2 * bi.by + 1) * bi.wy) * hh;
+        geo[3 * b + 2] = (op->opts.proxy_radius_factor * (double)std::max(bi.wx, bi.wy)) * hh;
+    }
+    if (max_entries > (int64_t)INT32_MAX) return fail(RS_E_INVALID, "box too large");
+    if ((rc = upload(L.d_act, to32(L.act), st))) return rc;
+    if ((rc = upload(L.d_act_off, L.act_off, st))) return rc;
+    if ((rc = upload(L.d_m, to32(L.m), st))) return rc;
+    if ((rc = upload(w.near, to32(L.nearv), st))) return rc;
+    if ((rc = upload(w.near_off, L.near_off, st))) return rc;
+    if ((rc = upload(w.geo, geo, st))) return rc;
+    if ((rc = upload(w.y_off, y_off, st))) return rc;
+    if ((rc = upload(w.nn, to32(L.nn), st))) return rc;
+    RS_CUDA(w.Y.alloc(sizeof(double) * (size_t)(y_off[nb] + 1)));
+    {
+    ProfScope ps(op, RS_PROF_ASSEMBLE_Y, st, (double)y_off[nb], 8.0 * (double)y_off[nb]);
+    RS_CUDA(launch_assemble_Y(st, nb, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), w.near.as<int32_t>(),
+                              w.near_off.as<int64_t>(), w.geo.as<double>(), op->d_ucirc.as<double>(), P,
+                              w.y_off.as<int64_t>(), w.Y.as<double>(), op->K, (int)max_entries));
+    }
+    const int64_t sum_m = L.act_off[nb];
+    RS_CUDA(w.piv.alloc(sizeof(int32_t) * (sum_m + 1)));
+    RS_CUDA(w.diag.alloc(sizeof(double) * (sum_m + 1)));
+    RS_CUDA(L.d_k.alloc(sizeof(int32_t) * nb));
+    RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
+    RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
+    const int max_r = L.max_r, max_m = L.max_m;
+    const int G = choose_group(nb, max_m, [&](int g) { return cpqr_max_ctas(max_r, max_m, g); });
+    RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * 2 * (size_t)nb * G));
+    {
+    // the rank is known only afterwards: the work is added once k is read back
+    ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0);
+    RS_CUDA(launch_cpqr(st, nb, G, L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
+                        w.Y.as<double>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<double>(),
+                        op->d_bar.as<unsigned int>(), w.keys.as<unsigned long long>(), op->d_status.as<int>(),
+                        (long long)op->opts.spin_limit, max_r, max_m));
+    }
+    if ((rc = check_status(op, st))) return rc;
+    std::vector<int32_t> k32(nb), piv(sum_m);
+    RS_CUDA(cudaMemcpy(k32.data(), L.d_k.p, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+    RS_CUDA(cudaMemcpy(piv.data(), w.piv.p, sizeof(int32_t) * sum_m, cudaMemcpyDeviceToHost));
+    // skeleton ascending in grid index, residual ascending in local index
+    L.k.assign(nb, 0);
+    L.k_off.assign(nb + 1, 0);
+    L.perm.assign(sum_m, 0);
+    L.skel.clear();
+    std::vector<int32_t> skpos(sum_m, 0), rscol(sum_m, 0);
+    L.t_off.assign(nb + 1, 0);
+    L.max_k = 0;
+    int max_res = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t a0 = L.act_off[b];
+        const int m = (int)L.m[b], k = k32[b];
+        if (k < 0 || k > m) return fail(RS_E_CUDA, "bad rank from the ID kernel");
+        L.k[b] = k;
+        L.k_off[b + 1] = L.k_off[b] + k;
+        std::vector<int> order(k);
+        for (int a = 0; a < k; ++a) order[a] = a;
+        std::sort(order.begin(), order.end(),
+                  [&](int x, int y) { return L.act[a0 + piv[a0 + x]] < L.act[a0 + piv[a0 + y]]; });
+        std::vector<char> is_sk(m, 0);
+        for (int q = 0; q < k; ++q) {
+            const int a = order[q];
+            const int loc = piv[a0 + a];
+            if (loc < 0 || loc >= m || is_sk[loc]) return fail(RS_E_CUDA, "bad pivot from the ID kernel");
+            is_sk[loc] = 1;
+            skpos[a0 + a] = q;
+            L.perm[a0 + q] = loc;
+            L.skel.push_back(L.act[a0 + loc]);
+        }
+        int c = 0;
+        for (int loc = 0; loc < m; ++loc)
+            if (!is_sk[loc]) { rscol[a0 + c] = loc; L.perm[a0 + k + c] = loc; ++c; }
+        L.t_off[b + 1] = L.t_off[b] + (int64_t)k * (m - k);
+        L.max_k = std::max(L.max_k, k);
+        max_res = std::max(max_res, m - k);
+    }
+    double cpqr_work = 0.0, t_work = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double m = (double)L.m[b], k = (double)L.k[b], r = (double)L.r[b];
+        cpqr_work += 4.0 * r * m * k - 2.0 * k * k * (r + m) + 4.0 * k * k * k / 3.0;
+        t_work += k * k * (m - k);
+    }
+    op->prof_work[RS_PROF_CPQR] += op->opts.profile ? cpqr_work : 0.0;
+    if ((rc = upload(L.d_perm, L.perm, st))) return rc;
+    if ((rc = upload(w.skpos, skpos, st))) return rc;
+    if ((rc = upload(w.rscol, rscol, st))) return rc;
+    if ((rc = upload(L.d_t_off, L.t_off, st))) return rc;
+    if ((rc = upload(L.d_k_off, L.k_off, st))) return rc;
+    RS_CUDA(L.d_T.alloc(sizeof(double) * (size_t)(L.t_off[nb] + 1)));
+    {
+    ProfScope ps(op, RS_PROF_ID_T, st, t_work, 8.0 * (double)L.t_off[nb]);
+    RS_CUDA(launch_id_T(st, nb, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(), w.nn.as<int32_t>(), P,
+                        w.y_off.as<int64_t>(), w.Y.as<double>(), w.piv.as<int32_t>(), w.diag.as<double>(),
+                        w.skpos.as<int32_t>(), w.rscol.as<int32_t>(), L.d_t_off.as<int64_t>(), L.d_T.as<double>(),
+                        max_res, L.max_k));
+    }
+    return check_status(op, st);
+}
+
+// Inversion phase of one level (Algorithm 1 lines 3-11 with the E of Algorithm 2 line 9).
+int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
+{
+    const int nb = L.nb;
+    L.phi_off.assign(nb + 1, 0);
+    L.e_off.assign(nb + 1, 0);
+    L.w_off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        L.phi_off[b + 1] = L.phi_off[b] + L.m[b] * L.m[b];
+        L.e_off[b + 1] = L.e_off[b] + L.k[b] * L.k[b];
+        L.w_off[b + 1] = L.w_off[b] + L.m[b] * L.k[b];
+    }
+    int rc;
+    if ((rc = upload(L.d_phi_off, L.phi_off, st))) return rc;
+    RS_CUDA(L.d_Phi.alloc(sizeof(double) * (size_t)(L.phi_off[nb] + 1)));
+    const bool leaf = (L.l == op->d);
+    {
+    ProfScope ps(op, RS_PROF_ASSEMBLE_F, st, (double)L.phi_off[nb], 8.0 * (double)L.phi_off[nb]);
+    RS_CUDA(launch_assemble_F(st, nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), L.d_perm.as<int32_t>(),
+                              op->d_a.as<double>(), L.d_phi_off.as<int64_t>(), L.d_Phi.as<double>(),
+                              child ? child->d_k.as<int32_t>() : nullptr, child ? child->d_e_off.as<int64_t>() : nullptr,
+                              child ? child->d_E.as<double>() : nullptr, op->K, L.max_m));
+    }
+    if ((rc = run_gj(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<double>(), L.m, L.act_off, L.max_m,
+                     L.l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F)))
+        return rc;
+    if (L.l == 0) return RS_OK;
+    // W = Phi[:, :k] + Phi[:, k:] T^T ;  E^{-1} = W[:k, :] + T W[k:, :]
+    if ((rc = upload(L.d_e_off, L.e_off, st))) return rc;
+    RS_CUDA(L.d_E.alloc(sizeof(double) * (size_t)(L.e_off[nb] + 1)));
+    DevMem W, d_p1, d_p2;
+    RS_CUDA(W.alloc(sizeof(double) * (size_t)(L.w_off[nb] + 1)));
+    std::vector<GemmProb> p1, p2;
+    int64_t t1 = 0, t2 = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int m = (int)L.m[b], k = (int)L.k[b];
+        if (k == 0) continue;
+        GemmProb g{};
+        g.M = m; g.N = k; g.K = m - k; g.ta = 0; g.tb = 1;
+        g.lda = m; g.ldb = std::max(k, 1); g.ldc = m; g.ldc0 = m;
+        g.a_off = L.phi_off[b] + (int64_t)k * m; g.b_off = L.t_off[b]; g.c_off = L.w_off[b]; g.c0_off = L.phi_off[b];
+        g.alpha = 1.0; g.beta = 1.0;
+        g.tiles_m = (m + 63) / 64; g.tiles_n = (k + 63) / 64; g.tile0 = t1;
+        t1 += (int64_t)g.tiles_m * g.tiles_n;
+        p1.push_back(g);
+        GemmProb h{};
+        h.M = k; h.N = k; h.K = m - k; h.ta = 0; h.tb = 0;
+        h.lda = std::max(k, 1); h.ldb = m; h.ldc = k; h.ldc0 = m;
+        h.a_off = L.t_off[b]; h.b_off = L.w_off[b] + k; h.c_off = L.e_off[b]; h.c0_off = L.w_off[b];
+        h.alpha = 1.0; h.beta = 1.0;
+        h.tiles_m = (k + 63) / 64; h.tiles_n = (k + 63) / 64; h.tile0 = t2;
+        t2 += (int64_t)h.tiles_m * h.tiles_n;
+        p2.push_back(h);
+    }
+    if (!p1.empty()) {
+        if ((rc = upload(d_p1, p1, st))) return rc;
+        if ((rc = upload(d_p2, p2, st))) return rc;
+        double work = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double m = (double)L.m[b], k = (double)L.k[b];
+            work += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;
+        }
+        ProfScope ps(op, RS_PROF_GEMM_E, st, work, 8.0 * (double)(L.phi_off[nb] + 2 * L.w_off[nb] + L.e_off[nb]));
+        RS_CUDA(launch_gemm(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<double>(), L.d_T.as<double>(),
+                            W.as<double>(), L.d_Phi.as<double>()));
+        RS_CUDA(launch_gemm(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<double>(), W.as<double>(),
+                            L.d_E.as<double>(), W.as<double>()));
+    }
+    RS_CUDA(cudaStreamSynchronize(st));
+    DevMem d_k32;
+    if ((rc = upload(d_k32, to32(L.k), st))) return rc;
+    return run_gj(op, st, nb, d_k32, L.d_e_off, L.d_E.as<double>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E);
+}
+
+void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk, int rows, int cols, int ld, int trans,
+            int64_t a_off, int64_t x_off, int64_t y_off, double alpha, double beta)
+{
+    const int out_n = trans ? cols : rows;
+    if (out_n <= 0 || rows <= 0) return;
+    MatvecProb p{};
+    p.rows = rows; p.cols = cols; p.ld = std::max(ld, 1); p.trans = trans;
+    p.a_off = a_off; p.x_off = x_off; p.y_off = y_off; p.alpha = alpha; p.beta = beta;
+    v.push_back(p);
+    blk.push_back(nblk);
+    nblk += (out_n + 63) / 64;
+}
+
+int upload_mv(DevMem& d, DevMem& db, int& n, int64_t& nblk, std::vector<MatvecProb>& v, std::vector<int64_t>& blk,
+              int64_t total, cudaStream_t st, double* work = nullptr)
+{
+    n = (int)v.size();
+    nblk = total;
+    if (work) {
+        *work = 0.0;
+        for (const MatvecProb& p : v) *work += (double)p.rows * (double)p.cols;
+    }
+    int rc;
+    if ((rc = upload(d, v, st))) return rc;
+    return upload(db, blk, st);
+}
+
+// Index maps and matvec descriptors of the solve for one level.
+int solve_plan(rs_op* op, Level& L, const Level* child, cudaStream_t st)
+{
+    const int nb = L.nb;
+    L.sum_m = L.act_off[nb];
+    L.sum_k = L.l == 0 ? 0 : L.k_off[nb];
+    int rc;
+    if (L.l == op->d) {
+        std::vector<int64_t> idx(L.sum_m);
+        for (int b = 0; b < nb; ++b)
+            for (int64_t p = 0; p < L.m[b]; ++p)
+                idx[L.act_off[b] + p] = op->input_of_g[L.act[L.act_off[b] + L.perm[L.act_off[b] + p]]];
+        if ((rc = upload(L.d_idx_leaf, idx, st))) return rc;
+    } else if (L.l > 0) {
+        std::vector<int64_t> idx(L.sum_m);
+        for (int b = 0; b < nb; ++b)
+            for (int64_t p = 0; p < L.m[b]; ++p)
+                idx[L.act_off[b] + p] = child->k_off[2 * b] + L.perm[L.act_off[b] + p];
+        if ((rc = upload(L.d_idx_up, idx, st))) return rc;
+    }
+    if (L.l == 0) {
+        std::vector<MatvecProb> v;
+        std::vector<int64_t> blk;
+        int64_t n = 0;
+        add_mv(v, blk, n, (int)L.m[0], (int)L.m[0], (int)L.m[0], 0, 0, 0, 0, 1.0, 0.0);
+        return upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, v, blk, n, st, &L.mvw_phi);
+    }
+    std::vector<int64_t> isk(L.sum_k);
+    for (int b = 0; b < nb; ++b)
+        for (int64_t a = 0; a < L.k[b]; ++a) isk[L.k_off[b] + a] = L.act_off[b] + a;
+    if ((rc = upload(L.d_idx_sk, isk, st))) return rc;
+    std::vector<MatvecProb> vphi, vT, vE, vTt;
+    std::vector<int64_t> bphi, bT, bE, bTt;
+    int64_t nphi = 0, nT = 0, nE = 0, nTt = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int m = (int)L.m[b], k = (int)L.k[b];
+        add_mv(vphi, bphi, nphi, m, m, m, 0, L.phi_off[b], L.act_off[b], L.act_off[b], 1.0, 0.0);
+        if (m - k > 0) add_mv(vT, bT, nT, k, m - k, k, 0, L.t_off[b], L.act_off[b] + k, L.k_off[b], 1.0, 1.0);
+        add_mv(vE, bE, nE, k, k, k, 0, L.e_off[b], L.k_off[b], L.k_off[b], 1.0, 0.0);
+        if (m - k > 0) add_mv(vTt, bTt, nTt, k, m - k, k, 1, L.t_off[b], L.k_off[b], L.act_off[b] + k, 1.0, 0.0);
+    }
+    if ((rc = upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, vphi, bphi, nphi, st, &L.mvw_phi))) return rc;
+    if ((rc = upload_mv(L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, vT, bT, nT, st, &L.mvw_T))) return rc;
+    if ((rc = upload_mv(L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, vE, bE, nE, st, &L.mvw_E))) return rc;
+    return upload_mv(L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, vTt, bTt, nTt, st, &L.mvw_Tt);
+}
+
+void compute_stats(rs_op* op)
+{
+    rs_stats& s = op->stats;
+    s.depth = op->d;
+    s.n_side = op->n;
+    s.root_m = op->lev[0].m[0];
+    double ff = 0.0, fs = 0.0, bs = 0.0;
+    int64_t bytes = 0;
+    for (int l = 1; l <= op->d; ++l) {
+        const Level& L = op->lev[l];
+        for (int b = 0; b < L.nb; ++b) {
+            const double m = (double)L.m[b], k = (double)L.k[b], r = (double)L.r[b];
+            ff += 4.0 * r * m * k - 2.0 * k * k * (r + m) + 4.0 * k * k * k / 3.0;   // CPQR, k steps
+            ff += k * k * (m - k);                                                // T = R11^{-1} R12
+            ff += 2.0 * m * m * m;                                                // F^{-1}
+            ff += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;                  // W, E^{-1}
+            ff += 2.0 * k * k * k;                                                // E
+            fs += 2.0 * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
+            bs += 8.0 * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
+        }
+        bytes += (L.phi_off.back() + L.e_off.back() + L.t_off.back()) * 8 + L.act_off.back() * 8 + L.nb * 64;
+    }
+    const double m0 = (double)op->lev[0].m[0];
+    ff += 2.0 * m0 * m0 * m0;
+    fs += 2.0 * m0 * m0;
+    bs += 8.0 * m0 * m0;
+    bytes += (int64_t)(m0 * m0 * 8);
+    s.flops_factor = ff;
+    s.flops_solve_per_rhs = fs;
+    s.bytes_solve = bs;
+    s.bytes_factors = bytes;
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps, const rs_opts* opts,
+                cudaStream_t st, rs_op** out)
+{
+    rs_op* op = new (std::nothrow) rs_op();
+    if (!op) return fail(RS_E_NOMEM, "host allocation");
+    std::unique_ptr<rs_op> guard(op);
+    RS_CUDA(cudaGetDevice(&op->device));
+    if (opts) op->opts = *opts; else rs_opts_default(&op->opts);
+    op->n = tree->n;
+    op->N = tree->n * tree->n;
+    op->d = tree->d;
+    op->kind = kernel ? kernel->kind : RS_LAPLACE;
+    op->kappa = kernel ? kernel->kappa : 0.0;
+    op->eps = eps;
+    op->input_of_g = tree->input_of_g;
+    if (op->kind != RS_LAPLACE) return fail(RS_E_INVALID, "only the Laplace kernel is built in this version");
+    if (kernel && kernel->b) return fail(RS_E_INVALID, "b(x) is only used by the Helmholtz kernel");
+    if (op->opts.precision != RS_FP64) return fail(RS_E_INVALID, "only RS_FP64 is built in this version");
+    if (op->opts.proxy_points < 0 || op->opts.proxy_points > 4096 || !(op->opts.proxy_radius_factor > 0.0))
+        return fail(RS_E_INVALID, "bad proxy options");
+    if (!(eps >= 0.0) || !(eps < 1.0)) return fail(RS_E_INVALID, "eps must be in [0, 1)");
+    if (op->opts.spin_limit <= 0) return fail(RS_E_INVALID, "spin_limit must be positive");
+    const double h = 1.0 / (double)op->n;
+    op->K.n = (int)op->n;
+    op->K.h = h;
+    op->K.c0 = -(h * h) / (4.0 * M_PI);
+    // diagonal: a_g - (1/2pi) * integral of log|y - x_g| over the h x h cell, whose closed
+    // form is h^2 (log h - log(2)/2 - 3/2 + pi/4)
+    op->K.self = -(h * h * (std::log(h) - 0.5 * std::log(2.0) - 1.5 + M_PI / 4.0)) / (2.0 * M_PI);
+    auto t0 = Clock::now();
+    // a in grid order
+    std::vector<double> ag(op->N, 1.0);
+    if (a)
+        for (int64_t g = 0; g < op->N; ++g) ag[g] = a[op->input_of_g[g]];
+    int rc;
+    if ((rc = upload(op->d_a, ag, st))) return rc;
+    const int P = op->opts.proxy_points;
+    std::vector<double> uc(2 * (size_t)P + 1);
+    for (int q = 0; q < P; ++q) {
+        const double ang = (2.0 * M_PI * (double)q) / (double)P;
+        uc[q] = std::cos(ang);
+        uc[P + q] = std::sin(ang);
+    }
+    if ((rc = upload(op->d_ucirc, uc, st))) return rc;
+    RS_CUDA(op->d_status.alloc(sizeof(int)));
+    RS_CUDA(cudaMemsetAsync(op->d_status.p, 0, sizeof(int), st));
+    op->lev.resize(op->d + 1);
+    for (int l = 0; l <= op->d; ++l) {
+        op->lev[l].l = l;
+        op->lev[l].nb = 1 << l;
+    }
+    {
+        IdWork w;
+        for (int l = op->d; l >= 1; --l)
+            if ((rc = id_level(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, w, st))) return rc;
+    }
+    op->stats.ms_tree = ms_since(t0);
+    auto t1 = Clock::now();
+    for (int l = op->d; l >= 1; --l)
+        if ((rc = inverse_level(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    // root: active set = skeletons of (1,0) then (1,1), natural order
+    Level& R = op->lev[0];
+    const Level& L1 = op->lev[1];
+    R.m = {L1.k[0] + L1.k[1]};
+    R.k = {0};
+    R.act = L1.skel;
+    R.act_off = {0, R.m[0]};
+    R.perm.resize(R.m[0]);
+    for (int64_t i = 0; i < R.m[0]; ++i) R.perm[i] = (int32_t)i;
+    R.max_m = (int)R.m[0];
+    if ((rc = upload(R.d_act, to32(R.act), st))) return rc;
+    if ((rc = upload(R.d_act_off, R.act_off, st))) return rc;
+    if ((rc = upload(R.d_perm, R.perm, st))) return rc;
+    if ((rc = upload(R.d_m, to32(R.m), st))) return rc;
+    if ((rc = inverse_level(op, R, &op->lev[1], st))) return rc;
+    for (int l = 0; l <= op->d; ++l)
+        if ((rc = solve_plan(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    RS_CUDA(cudaStreamSynchronize(st));
+    op->stats.ms_inverse = ms_since(t1);
+    compute_stats(op);
+    *out = guard.release();
+    return RS_OK;
+}
+
+int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
+{
+    const int64_t N = op->N;
+    const bool dev_f = is_device_ptr(f), dev_x = is_device_ptr(x);
+    if (dev_f != dev_x) return fail(RS_E_INVALID, "f and x must both be device or both be host pointers");
+    const int d = op->d;
+    // workspace: w, g, phi for all levels; u/v, x', t/y temporaries
+    std::vector<int64_t> woff(d + 2, 0), goff(d + 2, 0);
+    int64_t max_m = 0, max_k = 0;
+    for (int l = 1; l <= d; ++l) {
+        woff[l + 1] = woff[l] + op->lev[l].sum_m;
+        goff[l + 1] = goff[l] + op->lev[l].sum_k;
+        max_m = std::max(max_m, op->lev[l].sum_m);
+        max_k = std::max(max_k, op->lev[l].sum_k);
+    }
+    max_m = std::max<int64_t>(max_m, op->lev[0].sum_m);
+    RS_CUDA(op->s_w.alloc(sizeof(double) * (size_t)(woff[d + 1] * nrhs + 1)));
+    RS_CUDA(op->s_g.alloc(sizeof(double) * (size_t)(goff[d + 1] * nrhs + 1)));
+    RS_CUDA(op->s_phi.alloc(sizeof(double) * (size_t)(goff[d + 1] * nrhs + 1)));
+    RS_CUDA(op->s_u.alloc(sizeof(double) * (size_t)(max_m * nrhs + 1)));
+    RS_CUDA(op->s_out.alloc(sizeof(double) * (size_t)(max_m * nrhs + 1)));
+    RS_CUDA(op->s_t.alloc(sizeof(double) * (size_t)(max_k * nrhs + 1)));
+    if (op->opts.profile) {
+        op->prof_ms[RS_PROF_SOLVE] = op->prof_work[RS_PROF_SOLVE] = op->prof_bytes[RS_PROF_SOLVE] = 0.0;
+        op->prof_n[RS_PROF_SOLVE] = 0;
+    }
+    const double* fd = (const double*)f;
+    double* xd = (double*)x;
+    if (!dev_f) {
+        RS_CUDA(op->s_in.alloc(sizeof(double) * (size_t)(N * nrhs)));
+        RS_CUDA(cudaMemcpyAsync(op->s_in.p, f, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyHostToDevice, st));
+        fd = op->s_in.as<double>();
+        RS_CUDA(op->s_out2.alloc(sizeof(double) * (size_t)(N * nrhs)));
+        xd = op->s_out2.as<double>();
+    }
+    double* W = op->s_w.as<double>();
+    double* Gb = op->s_g.as<double>();
+    double* Ph = op->s_phi.as<double>();
+    double* U = op->s_u.as<double>();
+    double* XO = op->s_out.as<double>();
+    double* Tt = op->s_t.as<double>();
+    const int nr = (int)nrhs;
+    // upward pass
+    for (int l = d; l >= 1; --l) {
+        Level& L = op->lev[l];
+        double* wl = W + woff[l] * nrhs;
+        double* gl = Gb + goff[l] * nrhs;
+        if (l == d) RS_CUDA(launch_gather_cm(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
+        else RS_CUDA(launch_gather_rows(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
+        RS_CUDA(launch_matvec(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
+                              L.d_Phi.as<double>(), U, wl, nr)); }
+        RS_CUDA(launch_gather_rows(st, L.sum_k, L.d_idx_sk.as<int64_t>(), wl, Tt, nr));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, 8.0 * L.mvw_T);
+        RS_CUDA(launch_matvec(st, L.d_mv_T.as<MatvecProb>(), L.d_mv_T_blk.as<int64_t>(), L.n_mv_T, L.b_mv_T,
+                              L.d_T.as<double>(), wl, Tt, nr)); }
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
+        RS_CUDA(launch_matvec(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
+                              L.d_E.as<double>(), Tt, gl, nr)); }
+    }
+    // root
+    {
+        Level& R = op->lev[0];
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, 8.0 * R.mvw_phi);
+        RS_CUDA(launch_matvec(st, R.d_mv_phi.as<MatvecProb>(), R.d_mv_phi_blk.as<int64_t>(), R.n_mv_phi, R.b_mv_phi,
+                              R.d_Phi.as<double>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr)); }
+    }
+    // downward pass
+    for (int l = 1; l <= d; ++l) {
+        Level& L = op->lev[l];
+        double* wl = W + woff[l] * nrhs;
+        double* gl = Gb + goff[l] * nrhs;
+        double* pl = Ph + goff[l] * nrhs;
+        RS_CUDA(cudaMemcpyAsync(Tt, gl, sizeof(double) * (size_t)(L.sum_k * nrhs), cudaMemcpyDeviceToDevice, st));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
+        RS_CUDA(launch_matvec(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
+                              L.d_E.as<double>(), pl, Tt, nr)); }   // beta = 0: Tt = E phi
+        RS_CUDA(launch_axpby(st, L.sum_k * nrhs, -1.0, gl, 1.0, Tt));   // Tt = E phi - g
+        RS_CUDA(launch_scatter_rows(st, L.sum_k, L.d_idx_sk.as<int64_t>(), Tt, U, nr));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, 8.0 * L.mvw_Tt);
+        RS_CUDA(launch_matvec(st, L.d_mv_Tt.as<MatvecProb>(), L.d_mv_Tt_blk.as<int64_t>(), L.n_mv_Tt, L.b_mv_Tt,
+                              L.d_T.as<double>(), Tt, U, nr)); }
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
+        RS_CUDA(launch_matvec(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
+                              L.d_Phi.as<double>(), U, XO, nr)); }
+        RS_CUDA(launch_axpby(st, L.sum_m * nrhs, 1.0, wl, 1.0, XO));   // x' = w + Phi v
+        if (l == d) RS_CUDA(launch_scatter_cm(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
+        else RS_CUDA(launch_scatter_rows(st, L.sum_m, L.d_idx_up.as<int64_t>(), XO, Ph + goff[l + 1] * nrhs, nr));
+    }
+    if (!dev_x) {
+        RS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+    }
+    if (op->opts.profile) {
+        RS_CUDA(cudaStreamSynchronize(st));
+        prof_flush(op);
+    }
+    return RS_OK;
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps, const rs_opts* opts,
+              void* stream, rs_op** out)
+{
+    if (!out) return fail(RS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!tree) return fail(RS_E_INVALID, "tree is NULL");
+    return factor_impl(tree, kernel, a, eps, opts, (cudaStream_t)stream, out);
+}
+
+int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream)
+{
+    if (!op || !f || !x || nrhs < 1) return fail(RS_E_INVALID, "bad argument");
+    if (nrhs > (int64_t)1 << 20) return fail(RS_E_INVALID, "nrhs too large");
+    if (f == x) return fail(RS_E_INVALID, "x may not alias f");
+    int dev = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
+    return solve_impl(op, f, nrhs, x, (cudaStream_t)stream);
+}
+
+void rs_free(rs_op* op) { delete op; }
+
+int rs_op_profile(const rs_op* op, int cls, double* ms, double* work, double* bytes, int64_t* launches)
+{
+    if (!op || cls < 0 || cls >= RS_PROF_COUNT) return fail(RS_E_INVALID, "bad op or class");
+    if (ms) *ms = op->prof_ms[cls];
+    if (work) *work = op->prof_work[cls];
+    if (bytes) *bytes = op->prof_bytes[cls];
+    if (launches) *launches = op->prof_n[cls];
+    return RS_OK;
+}
+
+int rs_op_stats(const rs_op* op, rs_stats* out)
+{
+    if (!op || !out) return fail(RS_E_INVALID, "NULL argument");
+    *out = op->stats;
+    return RS_OK;
+}
+
+static const Level* get_level(const rs_op* op, int level, int box)
+{
+    if (!op || level < 1 || level > op->d || box < 0 || box >= (1 << level)) return nullptr;
+    return &op->lev[level];
+}
+
+int rs_op_box_sizes(const rs_op* op, int level, int box, int64_t* m, int64_t* k, int64_t* r, int64_t* nnear)
+{
+    const Level* L = get_level(op, level, box);
+    if (!L) return fail(RS_E_INVALID, "level/box out of range");
+    if (m) *m = L->m[box];
+    if (k) *k = L->k[box];
+    if (r) *r = L->r[box];
+    if (nnear) *nnear = L->nn[box];
+    return RS_OK;
+}
+
+int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* out)
+{
+    const Level* L = get_level(op, level, box);
+    if (!L || !out) return fail(RS_E_INVALID, "level/box out of range");
+    if (which == 0) {
+        std::copy(L->act.begin() + L->act_off[box], L->act.begin() + L->act_off[box + 1], out);
+    } else if (which == 1) {
+        std::copy(L->nearv.begin() + L->near_off[box], L->nearv.begin() + L->near_off[box + 1], out);
+    } else if (which == 2) {
+        std::copy(L->skel.begin() + L->k_off[box], L->skel.begin() + L->k_off[box + 1], out);
+    } else {
+        return fail(RS_E_INVALID, "bad `which`");
+    }
+    return RS_OK;
+}
+
+int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out)
+{
+    const Level* L = get_level(op, level, box);
+    if (!L || !out) return fail(RS_E_INVALID, "level/box out of range");
+    const int64_t m = L->m[box], k = L->k[box];
+    RS_CUDA(cudaSetDevice(op->device));
+    if (which == 0) {
+        std::vector<double> t((size_t)(k * (m - k)));
+        if (!t.empty()) RS_CUDA(cudaMemcpy(t.data(), L->d_T.as<double>() + L->t_off[box], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < k; ++i)
+            for (int64_t j = 0; j < m - k; ++j) out[i * (m - k) + j] = t[(size_t)(j * k + i)];
+    } else if (which == 1) {
+        std::vector<double> t((size_t)(m * m));
+        RS_CUDA(cudaMemcpy(t.data(), L->d_Phi.as<double>() + L->phi_off[box], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        const int32_t* pm = L->perm.data() + L->act_off[box];
+        for (int64_t q = 0; q < m; ++q)
+            for (int64_t p = 0; p < m; ++p) out[(int64_t)pm[p] * m + pm[q]] = t[(size_t)(q * m + p)];
+    } else if (which == 2) {
+        std::vector<double> t((size_t)(k * k));
+        if (!t.empty()) RS_CUDA(cudaMemcpy(t.data(), L->d_E.as<double>() + L->e_off[box], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < k; ++i)
+            for (int64_t j = 0; j < k; ++j) out[i * k + j] = t[(size_t)(j * k + i)];
+    } else {
+        return fail(RS_E_INVALID, "bad `which`");
+    }
+    return RS_OK;
+}
+
+int rs_op_root_matrix(const rs_op* op, double* out)
+{
+    if (!op || !out) return fail(RS_E_INVALID, "NULL argument");
+    const Level& R = op->lev[0];
+    const int64_t m = R.m[0];
+    std::vector<double> t((size_t)(m * m));
+    RS_CUDA(cudaSetDevice(op->device));
+    RS_CUDA(cudaMemcpy(t.data(), R.d_Phi.p, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < m; ++q)
+        for (int64_t p = 0; p < m; ++p) out[p * m + q] = t[(size_t)(q * m + p)];
+    return RS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// rs_host.h -- host-side structures of the library (tree, per-level factor data, operator).
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "rs_internal.h"
+
+struct rs_tree {
+    int64_t n = 0;          // points per side
+    int leaf = 0;           // leaf side
+    int d = 0;              // depth of the leaves
+    std::vector<int64_t> g_of_input;   // grid index of input point i
+    std::vector<int64_t> input_of_g;   // input index of grid point g
+};
+
+namespace rs {
+
+struct BoxInt {
+    int64_t bx, by, wx, wy;
+};
+BoxInt box_int(int64_t n, int l, int64_t j);
+
+// Index sets of level l (see rs_tree_level_sets in rs.h).
+int level_sets(int64_t n, int d, int l, const int64_t* child_k, const int64_t* child_skel, double rfac,
+               std::vector<int64_t>& m, std::vector<int64_t>& act, std::vector<int64_t>& act_off,
+               std::vector<int64_t>& nnear, std::vector<int64_t>& nearv, std::vector<int64_t>& near_off);
+
+// Owned device allocation.
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevMem& operator=(DevMem&& o) noexcept
+    {
+        if (this != &o) {
+            if (p) cudaFree(p);
+            p = o.p; bytes = o.bytes;
+            o.p = nullptr; o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevMem() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t b)
+    {
+        if (b <= bytes && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, b ? b : 16);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    template <class T> T* as() const { return (T*)p; }
+};
+
+// Everything stored for one tree level (level 0 = root, factored without an ID).
+struct Level {
+    int l = 0;
+    int nb = 0;
+    // host copies
+    std::vector<int64_t> m, k, r, nn;
+    std::vector<int64_t> act, act_off, nearv, near_off;
+    std::vector<int32_t> perm;        // per box: sorted skeleton locals, then residual locals
+    std::vector<int64_t> skel;        // per box: skeleton grid indices, ascending (k entries)
+    std::vector<int64_t> k_off;       // prefix sums of k
+    std::vector<int64_t> t_off, phi_off, e_off, w_off;
+    int max_m = 0, max_k = 0, max_r = 0;
+    // device: bookkeeping
+    DevMem d_act, d_act_off, d_perm, d_k, d_m;
+    DevMem d_t_off, d_phi_off, d_e_off, d_ipiv_off, d_cb_off, d_k_off;
+    // device: factors
+    DevMem d_T, d_Phi, d_E;
+    // device: solve index maps and descriptors
+    DevMem d_idx_up;      // rows of the child-level vector buffer for each active position (l < d)
+    DevMem d_idx_leaf;    // input index of each permuted leaf position (l == d)
+    DevMem d_idx_sk;      // row act_off + a for each skeleton position a (k_off order)
+    DevMem d_mv_phi, d_mv_phi_blk, d_mv_T, d_mv_T_blk, d_mv_E, d_mv_E_blk, d_mv_Tt, d_mv_Tt_blk;
+    int n_mv_phi = 0, n_mv_T = 0, n_mv_E = 0, n_mv_Tt = 0;
+    int64_t b_mv_phi = 0, b_mv_T = 0, b_mv_E = 0, b_mv_Tt = 0;
+    int64_t sum_m = 0, sum_k = 0;
+    double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set
+};
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double work, bytes;
+};
+
+}  // namespace rs
+
+struct rs_op {
+    int device = 0;
+    int64_t n = 0, N = 0;
+    int d = 0;
+    rs_kernel_kind kind = RS_LAPLACE;
+    double kappa = 0.0;
+    double eps = 0.0;
+    rs_opts opts{};
+    rs::LaplaceK K{};
+    std::vector<int64_t> input_of_g;
+    std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
+    rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_colbuf, d_pivrow;
+    // solve workspace (grown on demand)
+    rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_in, s_out, s_out2;
+    int64_t s_nrhs = 0;
+    rs_stats stats{};
+    int inflight = 0;
+    // profiling (opts.profile): pending event pairs and per-class sums
+    std::vector<rs::ProfRec> pending;
+    std::vector<cudaEvent_t> ev_pool, ev_all;
+    double prof_ms[RS_PROF_COUNT] = {}, prof_work[RS_PROF_COUNT] = {}, prof_bytes[RS_PROF_COUNT] = {};
+    int64_t prof_n[RS_PROF_COUNT] = {};
+    ~rs_op()
+    {
+        for (cudaEvent_t e : ev_all) cudaEventDestroy(e);
+    }
+};

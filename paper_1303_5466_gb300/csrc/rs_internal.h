@@ -1,0 +1,132 @@
+// rs_internal.h -- shared declarations of the library's host code and CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rs.h"
+
+namespace rs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define RS_CUDA(call)                                     \
+    do {                                                  \
+        cudaError_t e__ = (call);                         \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+    } while (0)
+
+// Kernel launches made by the library (rs_launch_count).
+void count_launches(int n);
+
+// Device status word bits written by kernels (never a trap): the host maps them to RS_E_*.
+enum : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2, DEV_BADSIZE = 4 };
+
+// Pivot key of the column-pivoted QR: the squared column norm with its 40 low mantissa bits
+// cleared (relative step 2^-12), and the low bits holding (2^40-1 - column index), so that the
+// largest key picks the largest norm, and among norms equal in their leading bits the lowest
+// column index.  The coarse step keeps CPU and GPU rounding differences from changing a pivot.
+constexpr int KEY_BITS = 40;
+constexpr unsigned long long KEY_MASK = (1ull << KEY_BITS) - 1ull;
+
+// ------------------------------------------------------------------ grouped GEMM descriptor
+// C = alpha * op(A) * op(B) + beta * C0 for one problem, all column-major (C0 may be C).
+struct GemmProb {
+    int M, N, K;
+    int ta, tb;            // 1: use the transpose
+    int lda, ldb, ldc, ldc0;
+    int64_t a_off, b_off, c_off, c0_off;
+    double alpha, beta;
+    int tiles_m, tiles_n;
+    int64_t tile0;         // first tile index of this problem in the launch
+};
+
+// Batched matrix-vector(s) descriptor: y = alpha * op(A) x + beta * y, A column-major
+// (rows x cols, ld), x and y point-major (entry p of RHS c at p * nrhs + c); x_off and y_off
+// count points (rows), so one descriptor serves every nrhs.
+struct MatvecProb {
+    int rows, cols, ld, trans;
+    int64_t a_off, x_off, y_off;
+    double alpha, beta;
+};
+
+// ------------------------------------------------------------------ launchers (kernels.cu)
+// All launchers enqueue on `st`, return cudaError_t of the launch.
+
+// Laplace kernel constants: entry = c0 * log(|x - y|^2), diagonal = a_g + self.
+struct LaplaceK {
+    double h, c0, self;
+    int n;
+};
+
+// Y for every box of a level: rows = near points then P proxy points, columns = active
+// points, column-major r x m at y_off[b].
+cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const int64_t* act_off,
+                              const int32_t* near, const int64_t* near_off, const double* geo,
+                              const double* ucirc, int P, const int64_t* y_off, double* Y,
+                              LaplaceK K, int max_entries);
+
+// Column-pivoted QR (Eq. 2.1) of every box's Y, G CTAs per box (cooperative when G > 1).
+// Outputs: kout[b], piv[act_off[b] + s] = physical column of pivot s (s < k),
+// diag[act_off[b] + s] = R_ss.  Y is overwritten by the factorisation (rows < k hold R).
+cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off,
+                        const int32_t* nnear, int P, const int64_t* y_off, double* Y, double eps,
+                        int32_t* kout, int32_t* piv, double* diag, unsigned int* bar,
+                        unsigned long long* keys, int* status, long long spin_limit, int max_r,
+                        int max_m);
+// Largest grid of cpqr_kernel that can be co-resident for these sizes.
+int cpqr_max_ctas(int max_r, int max_m, int G);
+int gj_max_ctas(int max_m, int G);
+
+// T = R11^{-1} R12 for every box, written column-major (k x (m-k)) at t_off[b], rows by
+// sorted skeleton position (skpos[pivot position]) and columns by residual rank.
+cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const int32_t* kk,
+                        const int32_t* nnear, int P, const int64_t* y_off, const double* Y,
+                        const int32_t* piv, const double* diag, const int32_t* skpos,
+                        const int32_t* rscol, const int64_t* t_off, double* T, int max_cols,
+                        int max_k);
+
+// F' = Pi^T F Pi for every box (sk-first order given by perm), column-major m x m at
+// phi_off[b].  Leaf: kernel entries with diagonal a_g + self.  Non-leaf: E of the
+// children on the diagonal blocks, kernel entries elsewhere.
+cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act,
+                              const int64_t* act_off, const int32_t* perm, const double* a,
+                              const int64_t* phi_off, double* Phi, const int32_t* child_k,
+                              const int64_t* child_e_off, const double* childE, LaplaceK K,
+                              int max_m);
+
+// In-place Gauss-Jordan inverse with partial pivoting of nb column-major matrices
+// (sizes m[b], offsets off[b]), G CTAs per matrix.
+cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off,
+                              double* A, int32_t* ipiv, const int64_t* ipiv_off, double* colbuf,
+                              const int64_t* colbuf_off, int* pivrow, unsigned int* bar, int* status,
+                              long long spin_limit, int max_m);
+
+// Grouped GEMM over `np` problems (device descriptors), total tiles `tiles`.
+cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const double* A,
+                        const double* B, double* C, const double* C0);
+
+// Batched matvec(s) over `np` problems, blocks = sum over problems of ceil(out_rows / 64).
+cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np,
+                          int64_t blocks, const double* A, const double* x, double* y, int nrhs);
+
+// Copy rows: dst[dst_off[b] + i * ldd + j] = src[src_off[b] + i * lds + j] style gathers
+// used by the solve: out[p * nrhs + c] = in[idx[p] * nrhs + c] for p < count.
+cudaError_t launch_gather_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
+                               double* out, int nrhs);
+cudaError_t launch_scatter_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
+                                double* out, int nrhs);
+// Column-major N x nrhs (input order) <-> point-major rows at idx.
+cudaError_t launch_gather_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
+                             int64_t N, double* out, int nrhs);
+cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
+                              int64_t N, double* out, int nrhs);
+// y[i] = a * x[i] + b * y[i]
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y);
+
+}  // namespace rs

@@ -19,6 +19,8 @@ WORKLOADS = {
     "laplace_small": dict(n=64, leaf=8, eps=1e-10, nrhs=1, seed=0),
     "laplace_batched": dict(n=512, leaf=16, eps=1e-10, nrhs=4, seed=1),
     "laplace_mixed": dict(n=1024, leaf=16, eps=1e-6, nrhs=1, seed=2),
+    # a quarter-size copy of laplace_batched for profiling runs (same leaf, eps, a, RHS recipe)
+    "laplace_n256": dict(n=256, leaf=16, eps=1e-10, nrhs=4, seed=1),
     "helmholtz_ls": dict(n=256, leaf=16, eps=1e-5, nrhs=1, seed=None, kappa=25.0),
 }
 

@@ -1,0 +1,75 @@
+"""The batched Laplace workload at full size (512 x 512 grid, leaves 16 x 16, eps 1e-10,
+a = 1 + 0.5 sin(2 pi x1) cos(2 pi x2), 4 RHS), in the launch configuration the benchmark
+times (device buffers on the current torch stream).
+
+The oracle factors the two finest levels in seconds: their ranks, skeletons and blocks are
+compared box by box.  Above them the whole-solve property is checked: the true residual on
+sampled rows (computed entry by entry by the oracle) is within 10 eps.
+"""
+import numpy as np
+import pytest
+
+from paper_1303_5466_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def full(oracle_mod):
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1303_5466_gb300 import build as B
+    B.build()
+    import paper_1303_5466_gb300 as P
+    cfg = W.WORKLOADS["laplace_batched"]
+    n, leaf, eps, nrhs = cfg["n"], cfg["leaf"], cfg["eps"], cfg["nrhs"]
+    a = W.coeff_a_batched(n)
+    F = W.rhs_normal(n, cfg["seed"], nrhs=nrhs)
+    st = torch.cuda.current_stream()
+    tree = P.rs_build_tree(W.grid_points(n), leaf)
+    op = P.rs_factor(tree, a=a, eps=eps, stream=st)
+    f_dev = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    x_dev = torch.empty_like(f_dev)
+    P.rs_solve(op, f_dev, nrhs, x_dev, st)
+    torch.cuda.synchronize()
+    x = x_dev.cpu().numpy().T.copy()
+    orc = oracle_mod.Factorization(n, leaf, eps, a=a, max_levels=2)
+    yield dict(P=P, op=op, n=n, a=a, F=F, x=x, eps=eps, orc=orc, d=orc.depth)
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+
+
+def test_finest_levels_match_oracle(full):
+    P, op, orc, d = full["P"], full["op"], full["orc"], full["d"]
+    mism = []
+    for l in (d, d - 1):
+        for j in range(2 ** l):
+            assert P.rs_op_box_sizes(op, l, j)[:2] == orc.sizes(l, j)[:2], (l, j)
+            if not np.array_equal(P.rs_op_box_indices(op, l, j, 2), orc.skel(l, j)):
+                mism.append((l, j))
+    assert not mism, "skeleton sets differ at %s" % mism[:20]
+    rng = np.random.default_rng(0)
+    for l in (d, d - 1):
+        for j in rng.choice(2 ** l, 8, replace=False):
+            fi = P.rs_op_box_matrix(op, l, j, 1)
+            ftol = 1e-11 if l == d else 1e-6                                      # see test_gpu_parity
+            assert np.linalg.norm(fi - orc.Finv(l, j)) <= ftol * np.linalg.norm(fi)
+            e = P.rs_op_box_matrix(op, l, j, 2)
+            assert np.linalg.norm(e - orc.E(l, j)) <= 1e-6 * np.linalg.norm(e)   # see test_gpu_parity
+            t = P.rs_op_box_matrix(op, l, j, 0)
+            assert np.linalg.norm(t - orc.T(l, j)) <= 1e-4 * max(np.linalg.norm(t), 1.0)
+
+
+def test_sampled_residual(full, oracle_mod):
+    n, x, F, a, eps = full["n"], full["x"], full["F"], full["a"], full["eps"]
+    rows = np.random.default_rng(2).choice(n * n, 256, replace=False)
+    Ax = oracle_mod.matvec_rows(n, x, rows, a=a)
+    for c in range(F.shape[1]):
+        r = np.linalg.norm(Ax[:, c] - F[rows, c]) / np.linalg.norm(F[rows, c])
+        assert r <= 10 * eps, (c, r)
+
+
+def test_stats_are_consistent(full):
+    s = full["P"].rs_op_stats(full["op"])
+    assert s["depth"] == full["d"] and s["n_side"] == full["n"]
+    assert s["flops_factor"] > 0 and s["bytes_factors"] > 0 and s["root_m"] > 0
