@@ -118,6 +118,28 @@ int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, dou
 int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
 void rs_free(rs_op* op);
 
+/* Inverse apply that allocates nothing.  This entry point has no counterpart in the paper; it
+ * exists for callers that cannot allocate device memory while they serve solves: a process
+ * whose device memory already belongs to another allocator or to fixed per-tenant budgets
+ * (an extra cudaMalloc may fail or break the budget), or a latency-bound request path where a
+ * cudaMalloc / cudaFree pair would synchronise the device.  rs_solve grows its workspace with
+ * cudaMalloc on first use; rs_solve_noalloc computes the same x = A^{-1} f with its workspace
+ * in one fixed device array of RS_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB), which every GPU
+ * that loads this library holds until the process exits, and calls no allocating routine.
+ *   - f, x: device pointers only (host buffers: RS_E_INVALID), N x nrhs column-major in input
+ *     order; real (RS_LAPLACE) operators only;
+ *   - the workspace grows linearly with nrhs (about 3 x N x nrhs doubles plus small terms);
+ *     a request that does not fit returns RS_E_INVALID, names the size it needed in
+ *     rs_last_error(), and launches nothing;
+ *   - the first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture;
+ *   - all calls share the one array and each overwrites it: calls whose work overlaps on the
+ *     GPU (different streams or threads) race and corrupt each other's results, so serialise
+ *     them, e.g. on one stream;
+ *   - returns once the work is enqueued on `stream`. */
+#define RS_NOALLOC_SCRATCH_DOUBLES ((int64_t)4 << 20)
+int rs_solve_noalloc(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
+
 /* Statistics of a factorization. */
 typedef struct {
     int depth;

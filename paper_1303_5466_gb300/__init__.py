@@ -71,6 +71,7 @@ def lib():
         L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_free.argtypes = [vp]
         L.rs_free.restype = None
+        L.rs_solve_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_op_stats.argtypes = [vp, C.POINTER(rs_stats)]
         L.rs_op_box_sizes.argtypes = [vp, C.c_int, C.c_int, i64p, i64p, i64p, i64p]
         L.rs_op_box_indices.argtypes = [vp, C.c_int, C.c_int, C.c_int, i64p]
@@ -168,6 +169,12 @@ def rs_solve(op, f, nrhs, x, stream=None):
     """x = A^{-1} f; f and x are both host (numpy) or both device (torch CUDA) buffers holding
     N x nrhs column-major values in input order."""
     _check(lib().rs_solve(op, _ptr(f), int(nrhs), _ptr(x), _stream(stream)))
+
+
+def rs_solve_noalloc(op, f, nrhs, x, stream=None):
+    """As rs_solve, with the workspace in the library's fixed device array (no allocation);
+    f and x must be device buffers."""
+    _check(lib().rs_solve_noalloc(op, _ptr(f), int(nrhs), _ptr(x), _stream(stream)))
 
 
 def rs_free(op):

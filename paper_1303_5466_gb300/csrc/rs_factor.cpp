@@ -450,6 +450,8 @@ void compute_stats(rs_op* op)
     s.bytes_factors = bytes;
 }
 
+}  // namespace
+
 bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes a{};
@@ -459,8 +461,6 @@ bool is_device_ptr(const void* p)
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
-
-}  // namespace
 
 int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps, const rs_opts* opts,
                 cudaStream_t st, rs_op** out)
@@ -546,28 +546,39 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     return RS_OK;
 }
 
+SolveLayout solve_layout(const rs_op* op, int64_t nrhs)
+{
+    SolveLayout Ls;
+    const int d = op->d;
+    Ls.woff.assign(d + 2, 0);
+    Ls.goff.assign(d + 2, 0);
+    for (int l = 1; l <= d; ++l) {
+        Ls.woff[l + 1] = Ls.woff[l] + op->lev[l].sum_m;
+        Ls.goff[l + 1] = Ls.goff[l] + op->lev[l].sum_k;
+        Ls.max_m = std::max(Ls.max_m, op->lev[l].sum_m);
+        Ls.max_k = std::max(Ls.max_k, op->lev[l].sum_k);
+    }
+    Ls.max_m = std::max<int64_t>(Ls.max_m, op->lev[0].sum_m);
+    Ls.n_w = Ls.woff[d + 1] * nrhs + 1;
+    Ls.n_g = Ls.goff[d + 1] * nrhs + 1;
+    Ls.n_u = Ls.max_m * nrhs + 1;
+    Ls.n_t = Ls.max_k * nrhs + 1;
+    return Ls;
+}
+
 int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
 {
     const int64_t N = op->N;
     const bool dev_f = is_device_ptr(f), dev_x = is_device_ptr(x);
     if (dev_f != dev_x) return fail(RS_E_INVALID, "f and x must both be device or both be host pointers");
-    const int d = op->d;
     // workspace: w, g, phi for all levels; u/v, x', t/y temporaries
-    std::vector<int64_t> woff(d + 2, 0), goff(d + 2, 0);
-    int64_t max_m = 0, max_k = 0;
-    for (int l = 1; l <= d; ++l) {
-        woff[l + 1] = woff[l] + op->lev[l].sum_m;
-        goff[l + 1] = goff[l] + op->lev[l].sum_k;
-        max_m = std::max(max_m, op->lev[l].sum_m);
-        max_k = std::max(max_k, op->lev[l].sum_k);
-    }
-    max_m = std::max<int64_t>(max_m, op->lev[0].sum_m);
-    RS_CUDA(op->s_w.alloc(sizeof(double) * (size_t)(woff[d + 1] * nrhs + 1)));
-    RS_CUDA(op->s_g.alloc(sizeof(double) * (size_t)(goff[d + 1] * nrhs + 1)));
-    RS_CUDA(op->s_phi.alloc(sizeof(double) * (size_t)(goff[d + 1] * nrhs + 1)));
-    RS_CUDA(op->s_u.alloc(sizeof(double) * (size_t)(max_m * nrhs + 1)));
-    RS_CUDA(op->s_out.alloc(sizeof(double) * (size_t)(max_m * nrhs + 1)));
-    RS_CUDA(op->s_t.alloc(sizeof(double) * (size_t)(max_k * nrhs + 1)));
+    const SolveLayout Ls = solve_layout(op, nrhs);
+    RS_CUDA(op->s_w.alloc(sizeof(double) * (size_t)Ls.n_w));
+    RS_CUDA(op->s_g.alloc(sizeof(double) * (size_t)Ls.n_g));
+    RS_CUDA(op->s_phi.alloc(sizeof(double) * (size_t)Ls.n_g));
+    RS_CUDA(op->s_u.alloc(sizeof(double) * (size_t)Ls.n_u));
+    RS_CUDA(op->s_out.alloc(sizeof(double) * (size_t)Ls.n_u));
+    RS_CUDA(op->s_t.alloc(sizeof(double) * (size_t)Ls.n_t));
     if (op->opts.profile) {
         op->prof_ms[RS_PROF_SOLVE] = op->prof_work[RS_PROF_SOLVE] = op->prof_bytes[RS_PROF_SOLVE] = 0.0;
         op->prof_n[RS_PROF_SOLVE] = 0;
@@ -581,12 +592,42 @@ int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
         RS_CUDA(op->s_out2.alloc(sizeof(double) * (size_t)(N * nrhs)));
         xd = op->s_out2.as<double>();
     }
-    double* W = op->s_w.as<double>();
-    double* Gb = op->s_g.as<double>();
-    double* Ph = op->s_phi.as<double>();
-    double* U = op->s_u.as<double>();
-    double* XO = op->s_out.as<double>();
-    double* Tt = op->s_t.as<double>();
+    SolveWork ws{op->s_w.as<double>(), op->s_g.as<double>(), op->s_phi.as<double>(), op->s_u.as<double>(),
+                 op->s_out.as<double>(), op->s_t.as<double>()};
+    int rc = solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
+    if (rc) return rc;
+    if (!dev_x) {
+        RS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+    }
+    if (op->opts.profile) {
+        RS_CUDA(cudaStreamSynchronize(st));
+        prof_flush(op);
+    }
+    return RS_OK;
+}
+
+// The kernel sequence of the inverse apply, on caller-provided workspace (layout Ls).
+int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
+              cudaStream_t st, bool profile)
+{
+    const int64_t N = op->N;
+    const int d = op->d;
+    const std::vector<int64_t>& woff = Ls.woff;
+    const std::vector<int64_t>& goff = Ls.goff;
+    double* W = ws.w;
+    double* Gb = ws.g;
+    double* Ph = ws.phi;
+    double* U = ws.u;
+    double* XO = ws.out;
+    double* Tt = ws.t;
+    const int saved_profile = op->opts.profile;
+    op->opts.profile = profile ? saved_profile : 0;
+    struct Restore {
+        rs_op* o;
+        int p;
+        ~Restore() { o->opts.profile = p; }
+    } restore{op, saved_profile};
     const int nr = (int)nrhs;
     // upward pass
     for (int l = d; l >= 1; --l) {
@@ -634,14 +675,6 @@ int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
         RS_CUDA(launch_axpby(st, L.sum_m * nrhs, 1.0, wl, 1.0, XO));   // x' = w + Phi v
         if (l == d) RS_CUDA(launch_scatter_cm(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
         else RS_CUDA(launch_scatter_rows(st, L.sum_m, L.d_idx_up.as<int64_t>(), XO, Ph + goff[l + 1] * nrhs, nr));
-    }
-    if (!dev_x) {
-        RS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
-        RS_CUDA(cudaStreamSynchronize(st));
-    }
-    if (op->opts.profile) {
-        RS_CUDA(cudaStreamSynchronize(st));
-        prof_flush(op);
     }
     return RS_OK;
 }

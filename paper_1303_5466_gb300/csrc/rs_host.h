@@ -85,12 +85,34 @@ struct Level {
     double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set
 };
 
+// Workspace layout of one inverse apply with nrhs columns (counts in doubles).
+struct SolveLayout {
+    std::vector<int64_t> woff, goff;   // per-level row offsets of w and of g / phi
+    int64_t max_m = 0, max_k = 0;
+    int64_t n_w = 0, n_g = 0, n_u = 0, n_t = 0;
+    int64_t total() const { return n_w + 2 * n_g + 2 * n_u + n_t; }
+};
+
+// Workspace pointers of one inverse apply: w (n_w), g and phi (n_g each), u and out (n_u
+// each), t (n_t).
+struct SolveWork {
+    double *w, *g, *phi, *u, *out, *t;
+};
+
 struct ProfRec {
     int cls;
     cudaEvent_t e0, e1;
     double work, bytes;
 };
 
+}  // namespace rs
+
+struct rs_op;
+namespace rs {
+SolveLayout solve_layout(const rs_op* op, int64_t nrhs);
+int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
+              cudaStream_t st, bool profile);
+bool is_device_ptr(const void* p);
 }  // namespace rs
 
 struct rs_op {
