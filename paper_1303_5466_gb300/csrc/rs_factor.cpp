@@ -347,7 +347,7 @@ void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk
             int64_t a_off, int64_t x_off, int64_t y_off, double alpha, double beta)
 {
     const int out_n = trans ? cols : rows;
-    if (out_n <= 0 || rows <= 0) return;
+    if (out_n <= 0) return;      // an empty inner dimension still writes beta * y (zeros)
     MatvecProb p{};
     p.rows = rows; p.cols = cols; p.ld = std::max(ld, 1); p.trans = trans;
     p.a_off = a_off; p.x_off = x_off; p.y_off = y_off; p.alpha = alpha; p.beta = beta;
