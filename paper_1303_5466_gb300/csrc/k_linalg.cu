@@ -11,109 +11,146 @@
 namespace rs {
 
 // ------------------------------------------------------------------ Gauss-Jordan inverse
-// G CTAs per matrix; CTA gi owns columns [c0, c1).  Step c: the owner of column c picks the
-// pivot row p (largest |A_ic|, i >= c, lowest i on ties), publishes the row-swapped column c
-// and p (double buffered by step parity); after one barrier every CTA swaps rows c and p in
-// its columns and applies the rank-1 Gauss-Jordan update.  A pivot with |pivot| not above
-// 1e3 * unit roundoff * (largest earlier pivot) sets DEV_SINGULAR (the loop still finishes).
-template <int NT>
+// Blocked in-place Gauss-Jordan inverse with partial pivoting, G CTAs per matrix.  Columns are
+// cut into panels of NB; panel q belongs to CTA q % G.  Block step q:
+//   1. the owner runs unblocked Gauss-Jordan on its panel alone (pivot = largest |A_ic|,
+//      i >= c, lowest i on ties; the row swap only touches the panel), leaving in the panel
+//      P = the panel of the partial inverse, and publishes the NB pivot rows;
+//   2. after one barrier every CTA updates each of its other columns j: apply the NB row
+//      swaps, then A[:, j] = D_K A[:, j] + P A[K, j] (D_K zeroes the panel's rows K), a rank-NB
+//      update with NB FMAs per element loaded.
+// This equals the unblocked algorithm step for step (same pivots, same operations per row).
+// A pivot with |pivot| not above 1e3 * unit roundoff * (largest earlier pivot of the same CTA)
+// sets DEV_SINGULAR; the loop still finishes.
+template <int NT, int NB>
 __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
         double* __restrict__ Aall, int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off,
-        double* __restrict__ colbuf, const int64_t* __restrict__ cb_off, int* __restrict__ pivrow,
-        unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
+        int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
 {
+    constexpr int CB = 32;                 // own columns updated per chunk
     extern __shared__ double sm[];
     __shared__ double dred[NT / 32];
     __shared__ int ired[NT / 32];
-    __shared__ int s_p;
+    __shared__ int s_piv[NB];
+    __shared__ double s_row[NB];
+    __shared__ double s_aK[NB][CB];
+    __shared__ int s_col[CB];
     const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
     const int m = msz[b];
     double* __restrict__ A = Aall + off[b];
-    const int per = (m + G - 1) / G;
-    const int c0 = min(m, gi * per), c1 = min(m, c0 + per);
-    const int nown = c1 - c0;
-    double* f = sm;                 // m
-    double* rowp = f + m;           // per
-    double* rowc = rowp + per;      // per
-    double* cb = colbuf + cb_off[b];
-    int* prow = pivrow + 2 * b;
+    double* f = sm;                        // m: the current pivot column (panel step)
     int32_t* ip = ipiv + ipiv_off[b];
+    int* pb = pivbuf + (int64_t)b * 2 * NB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int npan = (m + NB - 1) / NB;
     double maxpiv = 0.0;
-    for (int c = 0; c < m; ++c) {
-        const int owner = c / per;
-        if (gi == owner) {
-            const double* col = A + (int64_t)c * m;
-            double best = -1.0;
-            int bi = m;
-            for (int i = c + threadIdx.x; i < m; i += NT) {
-                const double a = fabs(col[i]);
-                if (a > best) { best = a; bi = i; }
+    for (int q = 0; q < npan; ++q) {
+        const int k0 = q * NB, kw = min(NB, m - k0);
+        if (q % G == gi) {
+            for (int t = 0; t < kw; ++t) {
+                const int c = k0 + t;
+                const double* col = A + (int64_t)c * m;
+                double best = -1.0;
+                int bi = m;
+                for (int i = c + threadIdx.x; i < m; i += NT) {
+                    const double a = fabs(col[i]);
+                    if (a > best) { best = a; bi = i; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (lane == 0) { dred[warp] = best; ired[warp] = bi; }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double bb = dred[0];
+                    int ii = ired[0];
+                    for (int w = 1; w < NT / 32; ++w)
+                        if (dred[w] > bb || (dred[w] == bb && ired[w] < ii)) { bb = dred[w]; ii = ired[w]; }
+                    s_piv[t] = ii < m ? ii : c;
+                    ip[c] = s_piv[t];
+                }
+                __syncthreads();
+                const int p = s_piv[t];
+                if (threadIdx.x < kw && p != c) {           // swap rows c, p inside the panel
+                    double* cj = A + (int64_t)(k0 + threadIdx.x) * m;
+                    const double u = cj[c];
+                    cj[c] = cj[p];
+                    cj[p] = u;
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < m; i += NT) f[i] = col[i];
+                if (threadIdx.x < kw) s_row[threadIdx.x] = A[(int64_t)(k0 + threadIdx.x) * m + c];
+                __syncthreads();
+                const double pv = f[c];
+                if (threadIdx.x == 0 && (!(fabs(pv) > 1e3 * 0.5 * DBL_EPSILON * maxpiv) || !isfinite(pv)))
+                    atomicOr(status, DEV_SINGULAR);
+                maxpiv = fmax(maxpiv, fabs(pv));
+                const double pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
+                for (int e = threadIdx.x; e < m * kw; e += NT) {
+                    const int jj = e / m, i = e - jj * m;
+                    double* cj = A + (int64_t)(k0 + jj) * m;
+                    if (k0 + jj == c) {
+                        cj[i] = (i == c) ? pinv : -f[i] * pinv;
+                    } else {
+                        const double aj = s_row[jj] * pinv;
+                        cj[i] = (i == c) ? aj : fma(-f[i], aj, cj[i]);
+                    }
+                }
+                __syncthreads();
             }
-            // block argmax, lowest index on ties
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            __syncthreads();
-            if (lane == 0) { dred[warp] = best; ired[warp] = bi; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double bb = dred[0];
-                int ii = ired[0];
-                for (int q = 1; q < NT / 32; ++q)
-                    if (dred[q] > bb || (dred[q] == bb && ired[q] < ii)) { bb = dred[q]; ii = ired[q]; }
-                s_p = ii < m ? ii : c;
-            }
-            __syncthreads();
-            const int p = s_p;
-            double* out = cb + (int64_t)(c & 1) * m;
-            for (int i = threadIdx.x; i < m; i += NT) {
-                const int src = (i == c) ? p : ((i == p) ? c : i);
-                out[i] = col[src];
-            }
-            if (threadIdx.x == 0) { prow[c & 1] = p; ip[c] = p; }
+            if (threadIdx.x < kw) pb[(q & 1) * NB + threadIdx.x] = s_piv[threadIdx.x];
         }
         if (G > 1) {
-            if (!group_sync(bar + b, (unsigned)(c + 1) * (unsigned)G, status, spin)) return;
+            if (!group_sync(bar + b, (unsigned)(q + 1) * (unsigned)G, status, spin)) return;
         } else {
             __syncthreads();
         }
-        const int p = (G > 1) ? __ldcg(prow + (c & 1)) : prow[c & 1];
-        const double* src = cb + (int64_t)(c & 1) * m;
-        for (int i = threadIdx.x; i < m; i += NT) f[i] = (G > 1) ? __ldcg(src + i) : src[i];
-        for (int jj = threadIdx.x; jj < nown; jj += NT) {
-            const int j = c0 + jj;
-            rowp[jj] = A[(int64_t)j * m + p];
-            rowc[jj] = A[(int64_t)j * m + c];
-        }
+        if (threadIdx.x < kw) s_piv[threadIdx.x] = (G > 1) ? __ldcg(pb + (q & 1) * NB + threadIdx.x) : pb[(q & 1) * NB + threadIdx.x];
         __syncthreads();
-        const double pv = f[c];
-        if (!(fabs(pv) > 1e3 * 0.5 * DBL_EPSILON * maxpiv) || !isfinite(pv) || pv == 0.0) {
-            if (threadIdx.x == 0 && gi == 0) atomicOr(status, DEV_SINGULAR);
-        }
-        maxpiv = fmax(maxpiv, fabs(pv));
-        const double pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
-        // columns: warps stride over own columns, lanes over rows
-        for (int jj = warp; jj < nown; jj += NT / 32) {
-            const int j = c0 + jj;
-            double* colj = A + (int64_t)j * m;
-            if (j == c) {
-                for (int i = lane; i < m; i += 32) colj[i] = (i == c) ? pinv : -f[i] * pinv;
-            } else {
-                const double aj = rowp[jj] * pinv;
-                const double oc = rowc[jj];
-                for (int i = lane; i < m; i += 32) {
-                    double u;
-                    if (i == c) u = aj;
-                    else if (i == p) u = oc - f[p] * aj;
-                    else u = colj[i] - f[i] * aj;
-                    colj[i] = u;
+        // trailing update of this CTA's other columns, CB at a time
+        int qq = gi, jin = 0;
+        while (qq < npan) {
+            int nc = 0;
+            while (nc < CB && qq < npan) {
+                if (qq == q) { qq += G; jin = 0; continue; }
+                const int w = min(NB, m - qq * NB);
+                if (threadIdx.x == 0) s_col[nc] = qq * NB + jin;
+                ++nc;
+                if (++jin == w) { qq += G; jin = 0; }
+            }
+            __syncthreads();
+            if (nc == 0) break;
+            // row swaps of block q, then the pivot rows a_K of each column
+            if (threadIdx.x < nc) {
+                double* cj = A + (int64_t)s_col[threadIdx.x] * m;
+                for (int t = 0; t < kw; ++t) {
+                    const int p = s_piv[t];
+                    if (p != k0 + t) {
+                        const double u = cj[k0 + t];
+                        cj[k0 + t] = cj[p];
+                        cj[p] = u;
+                    }
+                }
+                for (int t = 0; t < kw; ++t) s_aK[t][threadIdx.x] = cj[k0 + t];
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < m; i += NT) {
+                double P[NB];
+#pragma unroll
+                for (int t = 0; t < NB; ++t) P[t] = (t < kw) ? __ldcg(A + (int64_t)(k0 + t) * m + i) : 0.0;
+                const bool inK = (i >= k0) && (i < k0 + kw);
+                for (int jj = 0; jj < nc; ++jj) {
+                    double* cj = A + (int64_t)s_col[jj] * m;
+                    double v = inK ? 0.0 : cj[i];
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) v = fma(P[t], s_aK[t][jj], v);
+                    cj[i] = v;
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -137,37 +174,42 @@ __global__ void __launch_bounds__(256) gj_unpivot_kernel(const int32_t* __restri
     }
 }
 
-static size_t gj_shm(int max_m, int G) { return sizeof(double) * ((size_t)max_m + 2 * (size_t)((max_m + G - 1) / G)) + 64; }
+constexpr int GJ_NT = 256, GJ_NB = 8;
+
+static size_t gj_shm(int max_m) { return sizeof(double) * (size_t)max_m + 64; }
 
 int gj_max_ctas(int max_m, int G)
 {
-    constexpr int NT = 256;
-    const size_t shm = gj_shm(max_m, G);
-    cudaFuncSetAttribute(gj_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    (void)G;
+    const size_t shm = gj_shm(max_m);
+    cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<NT>, NT, shm) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<GJ_NT, GJ_NB>, GJ_NT, shm) != cudaSuccess)
+        return 0;
     return per_sm * sms;
 }
 
+int gj_panel_width() { return GJ_NB; }
+
 cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, double* A,
-                              int32_t* ipiv, const int64_t* ipiv_off, double* colbuf, const int64_t* colbuf_off,
-                              int* pivrow, unsigned int* bar, int* status, long long spin_limit, int max_m)
+                              int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf, unsigned int* bar, int* status,
+                              long long spin_limit, int max_m)
 {
-    constexpr int NT = 256;
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
-    const size_t shm = gj_shm(max_m, G);
-    cudaError_t e = cudaFuncSetAttribute(gj_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = gj_shm(max_m);
+    cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     if (G == 1) {
-        gj_kernel<NT><<<nb, NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, colbuf, colbuf_off, pivrow, bar, status,
-                                           spin_limit);
-    } else {
-        void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&colbuf,
-                        (void*)&colbuf_off, (void*)&pivrow, (void*)&bar, (void*)&status, (void*)&spin_limit};
         count_launches(1);
-        e = cudaLaunchCooperativeKernel((void*)gj_kernel<NT>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
+        gj_kernel<GJ_NT, GJ_NB><<<nb, GJ_NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status, spin_limit);
+    } else {
+        void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&pivbuf,
+                        (void*)&bar, (void*)&status, (void*)&spin_limit};
+        count_launches(1);
+        e = cudaLaunchCooperativeKernel((void*)gj_kernel<GJ_NT, GJ_NB>, dim3((unsigned)(nb * G)), dim3(GJ_NT), args,
+                                        shm, st);
         if (e != cudaSuccess) return e;
     }
     e = cudaGetLastError();

@@ -108,7 +108,7 @@ int check_status(rs_op* op, cudaStream_t st)
 // 32 columns and 64 in all).
 int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
 {
-    const int gmax = std::max(1, std::min(max_cols / 32, 64));
+    const int gmax = std::max(1, std::min(max_cols / 32, 1024));
     const int cap1 = capacity(1);
     if (gmax == 1 || nb >= cap1) return 1;
     int G = std::min(gmax, cap1 / std::max(nb, 1));
@@ -125,26 +125,22 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
            const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls)
 {
     if (max_m <= 0) return RS_OK;
-    std::vector<int64_t> cb_off(nb);
-    for (int b = 0; b < nb; ++b) cb_off[b] = 2 * size_off[b];
-    DevMem d_ipoff, d_cboff;
+    DevMem d_ipoff;
     RS_CUDA(d_ipoff.alloc(sizeof(int64_t) * nb));
     RS_CUDA(cudaMemcpyAsync(d_ipoff.p, size_off.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
-    if (upload(d_cboff, cb_off, st)) return RS_E_CUDA;
     const int64_t tot = size_off[nb];
     RS_CUDA(op->d_ipiv.alloc(sizeof(int32_t) * (tot + 1)));
-    RS_CUDA(op->d_colbuf.alloc(sizeof(double) * (2 * tot + 1)));
-    RS_CUDA(op->d_pivrow.alloc(sizeof(int) * 2 * nb));
+    RS_CUDA(op->d_pivrow.alloc(sizeof(int) * 2 * (size_t)gj_panel_width() * nb));
     RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
-    const int G = choose_group(nb, max_m, [&](int g) { return gj_max_ctas(max_m, g); });
+    // one CTA per panel of columns at most
+    const int G = choose_group(nb, max_m * 32 / gj_panel_width(), [&](int g) { return gj_max_ctas(max_m, g); });
     double work = 0.0;
     for (int b = 0; b < nb; ++b) work += 2.0 * (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
     ProfScope ps(op, cls, st, work, 16.0 * (double)size_off[nb]);
     RS_CUDA(launch_gj_inverse(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_ipiv.as<int32_t>(),
-                              d_ipoff.as<int64_t>(), op->d_colbuf.as<double>(), d_cboff.as<int64_t>(),
-                              op->d_pivrow.as<int>(), op->d_bar.as<unsigned int>(), op->d_status.as<int>(),
-                              (long long)op->opts.spin_limit, max_m));
+                              d_ipoff.as<int64_t>(), op->d_pivrow.as<int>(), op->d_bar.as<unsigned int>(),
+                              op->d_status.as<int>(), (long long)op->opts.spin_limit, max_m));
     return check_status(op, st);
 }
 

@@ -100,12 +100,14 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
                               const int64_t* child_e_off, const double* childE, LaplaceK K,
                               int max_m);
 
-// In-place Gauss-Jordan inverse with partial pivoting of nb column-major matrices
-// (sizes m[b], offsets off[b]), G CTAs per matrix.
+// In-place blocked Gauss-Jordan inverse with partial pivoting of nb column-major matrices
+// (sizes m[b], offsets off[b]), G CTAs per matrix (cooperative when G > 1).  ipiv: one int
+// per row (ipiv_off[b]); pivbuf: 2 * gj_panel_width() ints per matrix; bar: one counter per
+// matrix, zeroed before the launch.
 cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off,
-                              double* A, int32_t* ipiv, const int64_t* ipiv_off, double* colbuf,
-                              const int64_t* colbuf_off, int* pivrow, unsigned int* bar, int* status,
-                              long long spin_limit, int max_m);
+                              double* A, int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf,
+                              unsigned int* bar, int* status, long long spin_limit, int max_m);
+int gj_panel_width();
 
 // Grouped GEMM over `np` problems (device descriptors), total tiles `tiles`.
 cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const double* A,
