@@ -118,6 +118,16 @@ int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, dou
 int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
 void rs_free(rs_op* op);
 
+/* Relative residuals |f_c - A x_c| / |f_c| of nrhs columns by an FP64 direct sum over all N^2
+ * pairs (Laplace operators; the off-diagonal entries are tabulated over the (2n-1)^2 integer
+ * offsets of the grid, one FMA per pair).  x, f: N x nrhs column-major FP64 in input order,
+ * both device or both host.  rel_out: host, nrhs values.  Synchronous.  For RS_MIXED_FP32
+ * operators rs_solve uses this residual for iterative refinement: x = 0, then repeatedly
+ * x += A_eps^{-1} r, r = f - A x, until every column's relative residual is at most
+ * opts.refine_tol (RS_E_NOT_CONVERGED after opts.refine_max_iter low-precision solves; x then
+ * holds the last iterate). */
+int rs_residual(rs_op* op, const void* x, const void* f, int64_t nrhs, double* rel_out, void* stream);
+
 /* Inverse apply that allocates nothing.  This entry point has no counterpart in the paper; it
  * exists for callers that cannot allocate device memory while they serve solves: a process
  * whose device memory already belongs to another allocator or to fixed per-tenant budgets
@@ -127,7 +137,7 @@ void rs_free(rs_op* op);
  * in one fixed device array of RS_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB), which every GPU
  * that loads this library holds until the process exits, and calls no allocating routine.
  *   - f, x: device pointers only (host buffers: RS_E_INVALID), N x nrhs column-major in input
- *     order; real (RS_LAPLACE) operators only;
+ *     order; real FP64 operators only (RS_LAPLACE factored in RS_FP64);
  *   - the workspace grows linearly with nrhs (about 3 x N x nrhs doubles plus small terms);
  *     a request that does not fit returns RS_E_INVALID, names the size it needed in
  *     rs_last_error(), and launches nothing;
@@ -153,6 +163,8 @@ typedef struct {
     double bytes_solve;          /* factor bytes one inverse apply reads                   */
     double ms_tree;              /* wall time of the ID phase (Sec. 5 "tree build")        */
     double ms_inverse;           /* wall time of the inversion phase                       */
+    int refine_iters;            /* RS_MIXED_FP32: low-precision solves of the last rs_solve */
+    double refine_residual;      /* RS_MIXED_FP32: its final max relative FP64 residual     */
 } rs_stats;
 int rs_op_stats(const rs_op* op, rs_stats* out);
 

@@ -45,7 +45,8 @@ class rs_opts(C.Structure):
 class rs_stats(C.Structure):
     _fields_ = [("depth", C.c_int), ("n_side", C.c_int64), ("root_m", C.c_int64), ("bytes_factors", C.c_int64),
                 ("bytes_workspace", C.c_int64), ("flops_factor", C.c_double), ("flops_solve_per_rhs", C.c_double),
-                ("bytes_solve", C.c_double), ("ms_tree", C.c_double), ("ms_inverse", C.c_double)]
+                ("bytes_solve", C.c_double), ("ms_tree", C.c_double), ("ms_inverse", C.c_double),
+                ("refine_iters", C.c_int), ("refine_residual", C.c_double)]
 
 
 _lib = None
@@ -72,6 +73,7 @@ def lib():
         L.rs_free.argtypes = [vp]
         L.rs_free.restype = None
         L.rs_solve_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.rs_residual.argtypes = [vp, vp, vp, C.c_int64, dp, vp]
         L.rs_op_stats.argtypes = [vp, C.POINTER(rs_stats)]
         L.rs_op_box_sizes.argtypes = [vp, C.c_int, C.c_int, i64p, i64p, i64p, i64p]
         L.rs_op_box_indices.argtypes = [vp, C.c_int, C.c_int, C.c_int, i64p]
@@ -175,6 +177,13 @@ def rs_solve_noalloc(op, f, nrhs, x, stream=None):
     """As rs_solve, with the workspace in the library's fixed device array (no allocation);
     f and x must be device buffers."""
     _check(lib().rs_solve_noalloc(op, _ptr(f), int(nrhs), _ptr(x), _stream(stream)))
+
+
+def rs_residual(op, x, f, nrhs, stream=None):
+    """Relative FP64 residuals |f - A x| / |f| per column (x, f: both host or both device)."""
+    out = np.zeros(int(nrhs))
+    _check(lib().rs_residual(op, _ptr(x), _ptr(f), int(nrhs), _dp(out), _stream(stream)))
+    return out
 
 
 def rs_free(op):

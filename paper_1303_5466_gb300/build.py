@@ -29,7 +29,7 @@ def _deps():
 
 def _compile(src, verbose):
     obj = os.path.join(OBJ, os.path.basename(src) + ".o")
-    cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wpointer-arith",
                            "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
     if src.endswith(".cu") and verbose:
         cmd[1:1] = ["-Xptxas", "-v"]

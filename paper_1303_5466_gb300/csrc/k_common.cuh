@@ -14,7 +14,8 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
     return v;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

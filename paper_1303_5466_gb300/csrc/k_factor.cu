@@ -15,8 +15,13 @@ __device__ __forceinline__ void grid_xy(const LaplaceK& K, int g, double& x, dou
     y = ((double)i2 + 0.5) * K.h;
 }
 
-// Off-diagonal Laplace entry -(1/2pi) h^2 log|x - y| = c0 log(|x - y|^2), c0 = -h^2/(4pi).
-__device__ __forceinline__ double lap_entry(const LaplaceK& K, int g, int gp)
+// Off-diagonal Laplace entry -(1/2pi) h^2 log|x - y| = c0 log(|x - y|^2), c0 = -h^2/(4pi),
+// evaluated in the storage precision T (FP32 arithmetic for the mixed-precision factor).
+template <class T>
+__device__ __forceinline__ T lap_entry(const LaplaceK& K, int g, int gp);
+
+template <>
+__device__ __forceinline__ double lap_entry<double>(const LaplaceK& K, int g, int gp)
 {
     double x, y, xp, yp;
     grid_xy(K, g, x, y);
@@ -25,12 +30,35 @@ __device__ __forceinline__ double lap_entry(const LaplaceK& K, int g, int gp)
     return K.c0 * log(dx * dx + dy * dy);
 }
 
+template <>
+__device__ __forceinline__ float lap_entry<float>(const LaplaceK& K, int g, int gp)
+{
+    const int d1 = g % K.n - gp % K.n, d2 = g / K.n - gp / K.n;
+    const float hf = (float)K.h;
+    const float dx = (float)d1 * hf, dy = (float)d2 * hf;
+    return (float)K.c0 * logf(dx * dx + dy * dy);
+}
+
+template <class T>
+__device__ __forceinline__ T proxy_entry(const LaplaceK& K, double zx, double zy, int g)
+{
+    double x, y;
+    grid_xy(K, g, x, y);
+    if (sizeof(T) == sizeof(float)) {
+        const float dx = (float)(zx - x), dy = (float)(zy - y);
+        return (T)((float)K.c0 * logf(dx * dx + dy * dy));
+    }
+    const double dx = zx - x, dy = zy - y;
+    return (T)(K.c0 * log(dx * dx + dy * dy));
+}
+
 // ------------------------------------------------------------------ Y assembly
+template <class T>
 __global__ void __launch_bounds__(256) assemble_Y_kernel(const int32_t* __restrict__ act,
         const int64_t* __restrict__ act_off, const int32_t* __restrict__ near,
         const int64_t* __restrict__ near_off, const double* __restrict__ geo,
         const double* __restrict__ ucirc, int P, const int64_t* __restrict__ y_off,
-        double* __restrict__ Y, LaplaceK K)
+        T* __restrict__ Y, LaplaceK K)
 {
     const int b = blockIdx.y;
     const int64_t a0 = act_off[b];
@@ -42,30 +70,27 @@ __global__ void __launch_bounds__(256) assemble_Y_kernel(const int32_t* __restri
     if (e >= (int64_t)r * m) return;
     const int j = (int)(e / r), i = (int)(e - (int64_t)j * r);
     const int g = act[a0 + j];
-    double v;
+    T v;
     if (i < nn) {
-        v = lap_entry(K, near[n0 + i], g);
+        v = lap_entry<T>(K, near[n0 + i], g);
     } else {
         const int q = i - nn;
         const double cx = geo[3 * b], cy = geo[3 * b + 1], R = geo[3 * b + 2];
-        const double zx = cx + R * ucirc[q], zy = cy + R * ucirc[P + q];
-        double x, y;
-        grid_xy(K, g, x, y);
-        const double dx = zx - x, dy = zy - y;
-        v = K.c0 * log(dx * dx + dy * dy);
+        v = proxy_entry<T>(K, cx + R * ucirc[q], cy + R * ucirc[P + q], g);
     }
     Y[y_off[b] + e] = v;
 }
 
+template <class T>
 cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const int64_t* act_off,
                               const int32_t* near, const int64_t* near_off, const double* geo,
-                              const double* ucirc, int P, const int64_t* y_off, double* Y, LaplaceK K,
+                              const double* ucirc, int P, const int64_t* y_off, T* Y, LaplaceK K,
                               int max_entries)
 {
     if (nb <= 0 || max_entries <= 0) return cudaSuccess;
     dim3 grid((unsigned)((max_entries + 255) / 256), (unsigned)nb);
     count_launches(1);
-    assemble_Y_kernel<<<grid, 256, 0, st>>>(act, act_off, near, near_off, geo, ucirc, P, y_off, Y, K);
+    assemble_Y_kernel<T><<<grid, 256, 0, st>>>(act, act_off, near, near_off, geo, ucirc, P, y_off, Y, K);
     return cudaGetLastError();
 }
 
@@ -80,11 +105,11 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 //      over rows, shuffle reductions) and downdates their squared norms, recomputing a norm
 //      from the data once it falls below 1e-4 of the value it was last computed from.
 // The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step.
-template <int NT>
+template <int NT, class T>
 __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
-        double* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
-        double* __restrict__ diag, unsigned int* __restrict__ bar, unsigned long long* __restrict__ keys,
+        T* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
+        T* __restrict__ diag, unsigned int* __restrict__ bar, unsigned long long* __restrict__ keys,
         int* __restrict__ status, long long spin)
 {
     extern __shared__ double smem[];
@@ -96,22 +121,22 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     const int64_t a0 = act_off[b];
     const int m = (int)(act_off[b + 1] - a0);
     const int r = nnear[b] + P;
-    double* __restrict__ Y = Yall + y_off[b];
+    T* __restrict__ Y = Yall + y_off[b];
     const int per = (m + G - 1) / G;
     const int c0 = min(m, gi * per), c1 = min(m, c0 + per);
     const int nown = c1 - c0;
-    double* v = smem;                         // r
-    double* nrm = v + r;                      // nown
+    double* nrm = smem;                       // nown: squared norms (FP64 in every precision)
     double* ref = nrm + nown;                 // nown
     int* sel = (int*)(ref + nown);            // nown
+    T* v = (T*)(sel + ((nown + 1) & ~1));     // r: Householder vector
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
 
     for (int jj = warp; jj < nown; jj += NW) {
-        const double* col = Y + (int64_t)(c0 + jj) * r;
+        const T* col = Y + (int64_t)(c0 + jj) * r;
         double s = 0.0;
-        for (int i = lane; i < r; i += 32) { const double x = col[i]; s += x * x; }
+        for (int i = lane; i < r; i += 32) { const double x = (double)col[i]; s += x * x; }
         s = warp_sum(s);
         if (lane == 0) { nrm[jj] = s; ref[jj] = s; sel[jj] = 0; }
     }
@@ -143,45 +168,45 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             best = s_key;
         }
         const int p = (int)(KEY_MASK - (best & KEY_MASK));
-        const double* colp = Y + (int64_t)p * r;
+        const T* colp = Y + (int64_t)p * r;
         double part = 0.0;
         for (int i = s + threadIdx.x; i < r; i += NT) {
-            const double x = __ldcg(colp + i);
+            const T x = __ldcg(colp + i);
             v[i] = x;
-            part += x * x;
+            part += (double)x * (double)x;
         }
         const double a2 = block_sum<NT>(part, dred);
         const double alpha = sqrt(a2);
         if (s == 0) alpha0 = alpha;
         if (!(alpha > eps * alpha0)) break;
-        const double x0 = v[s];
+        const double x0 = (double)v[s];
         const double beta = (x0 < 0.0) ? alpha : -alpha;
-        const double tau = 1.0 / (alpha * (alpha + fabs(x0)));   // 2 / ||v||^2
+        const T tau = (T)(1.0 / (alpha * (alpha + fabs(x0))));   // 2 / ||v||^2
         __syncthreads();
         if (threadIdx.x == 0) {
-            v[s] = x0 - beta;
-            if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
+            v[s] = (T)(x0 - beta);
+            if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = (T)beta; }
         }
         if (threadIdx.x == 0 && p >= c0 && p < c1) sel[p - c0] = 1;
         __syncthreads();
         for (int jj = warp; jj < nown; jj += NW) {
             if (sel[jj]) continue;
-            double* col = Y + (int64_t)(c0 + jj) * r;
-            double w = 0.0;
+            T* col = Y + (int64_t)(c0 + jj) * r;
+            T w = 0;
             for (int i = s + lane; i < r; i += 32) w += v[i] * col[i];
             w = warp_sum(w);
-            const double tw = tau * w;
-            double rsj = 0.0;
+            const T tw = tau * w;
+            T rsj = 0;
             for (int i = s + lane; i < r; i += 32) {
-                const double u = col[i] - v[i] * tw;
+                const T u = col[i] - v[i] * tw;
                 col[i] = u;
                 if (i == s) rsj = u;
             }
             rsj = __shfl_sync(0xffffffffu, rsj, 0);
-            double nv = nrm[jj] - rsj * rsj;
+            double nv = nrm[jj] - (double)rsj * (double)rsj;
             if (nv < 1e-4 * ref[jj]) {
                 double q = 0.0;
-                for (int i = s + 1 + lane; i < r; i += 32) { const double x = col[i]; q += x * x; }
+                for (int i = s + 1 + lane; i < r; i += 32) { const double x = (double)col[i]; q += x * x; }
                 q = warp_sum(q);
                 nv = q;
                 if (lane == 0) ref[jj] = q;
@@ -194,53 +219,61 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     if (gi == 0 && threadIdx.x == 0) kout[b] = k;
 }
 
+template <class T>
+static size_t cpqr_shm(int max_r, int max_m, int G)
+{
+    const int per = (max_m + G - 1) / G;
+    return sizeof(double) * 2 * (size_t)per + sizeof(int) * (size_t)(per + 2) + sizeof(T) * (size_t)max_r + 64;
+}
+
+template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
-                        const int64_t* y_off, double* Y, double eps, int32_t* kout, int32_t* piv, double* diag,
+                        const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
                         int max_m)
 {
     constexpr int NT = 256;
     if (nb <= 0) return cudaSuccess;
-    // shared: v (r) + nrm, ref (own columns) + sel
-    const int per = (max_m + G - 1) / G;
-    const size_t shm = sizeof(double) * ((size_t)max_r + 2 * (size_t)per) + sizeof(int) * (size_t)per + 64;
-    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = cpqr_shm<T>(max_r, max_m, G);
+    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     if (G == 1) {
-        cpqr_kernel<NT><<<nb, NT, shm, st>>>(G, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys,
-                                             status, spin_limit);
+        count_launches(1);
+        cpqr_kernel<NT, T><<<nb, NT, shm, st>>>(G, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys,
+                                                status, spin_limit);
         return cudaGetLastError();
     }
     void* args[] = {(void*)&G, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y, (void*)&eps,
                     (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
                     (void*)&spin_limit};
     count_launches(1);
-    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
+    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, T>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
 }
 
+template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G)
 {
     constexpr int NT = 256;
-    const int per = (max_m + G - 1) / G;
-    const size_t shm = sizeof(double) * ((size_t)max_r + 2 * (size_t)per) + sizeof(int) * (size_t)per + 64;
-    cudaFuncSetAttribute(cpqr_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = cpqr_shm<T>(max_r, max_m, G);
+    cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel<NT>, NT, shm) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel<NT, T>, NT, shm) != cudaSuccess) return 0;
     return per_sm * sms;
 }
 
 // ------------------------------------------------------------------ T = R11^{-1} R12
 // One CTA per (box, group of NC residual columns): back substitution by columns of R11, so
 // each step reads one contiguous column of R.
-template <int NT, int NC>
+template <int NT, int NC, class T>
 __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ act_off, const int32_t* __restrict__ kk,
-        const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off, const double* __restrict__ Yall,
-        const int32_t* __restrict__ piv, const double* __restrict__ diag, const int32_t* __restrict__ skpos,
-        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, double* __restrict__ T)
+        const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off, const T* __restrict__ Yall,
+        const int32_t* __restrict__ piv, const T* __restrict__ diag, const int32_t* __restrict__ skpos,
+        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, T* __restrict__ Tout)
 {
-    extern __shared__ double ys[];   // NC x k
+    extern __shared__ double ys_raw[];
+    T* ys = (T*)ys_raw;              // NC x k
     const int b = blockIdx.x;
     const int64_t a0 = act_off[b];
     const int m = (int)(act_off[b + 1] - a0);
@@ -250,25 +283,25 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
     if (cb >= nres || k == 0) return;
     const int nc = min(NC, nres - cb);
     const int r = nnear[b] + P;
-    const double* Y = Yall + y_off[b];
-    double* Tb = T + t_off[b];
+    const T* Y = Yall + y_off[b];
+    T* Tb = Tout + t_off[b];
     for (int q = 0; q < nc; ++q) {
-        const double* col = Y + (int64_t)rscol[a0 + cb + q] * r;
+        const T* col = Y + (int64_t)rscol[a0 + cb + q] * r;
         for (int a = threadIdx.x; a < k; a += NT) ys[q * k + a] = col[a];
     }
     for (int a = k - 1; a >= 0; --a) {
         __syncthreads();
-        const double Raa = diag[a0 + a];
-        double t[NC];
+        const T Raa = diag[a0 + a];
+        T t[NC];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) t[q] = (q < nc) ? ys[q * k + a] / Raa : 0.0;
+        for (int q = 0; q < NC; ++q) t[q] = (q < nc) ? ys[q * k + a] / Raa : (T)0;
         if (threadIdx.x == 0) {
             const int row = skpos[a0 + a];
             for (int q = 0; q < nc; ++q) Tb[(int64_t)(cb + q) * k + row] = t[q];
         }
-        const double* Ra = Y + (int64_t)piv[a0 + a] * r;
+        const T* Ra = Y + (int64_t)piv[a0 + a] * r;
         for (int i = threadIdx.x; i < a; i += NT) {
-            const double R = Ra[i];
+            const T R = Ra[i];
 #pragma unroll
             for (int q = 0; q < NC; ++q)
                 if (q < nc) ys[q * k + i] -= t[q] * R;
@@ -276,26 +309,30 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
     }
 }
 
+template <class T>
 cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const int32_t* kk, const int32_t* nnear,
-                        int P, const int64_t* y_off, const double* Y, const int32_t* piv, const double* diag,
-                        const int32_t* skpos, const int32_t* rscol, const int64_t* t_off, double* T, int max_cols,
+                        int P, const int64_t* y_off, const T* Y, const int32_t* piv, const T* diag,
+                        const int32_t* skpos, const int32_t* rscol, const int64_t* t_off, T* Tout, int max_cols,
                         int max_k)
 {
     constexpr int NT = 128, NC = 4;
     if (nb <= 0 || max_cols <= 0 || max_k <= 0) return cudaSuccess;
-    const size_t shm = sizeof(double) * (size_t)NC * (size_t)max_k;
-    cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = sizeof(T) * (size_t)NC * (size_t)max_k;
+    cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)nb, (unsigned)((max_cols + NC - 1) / NC));
-    id_T_kernel<NT, NC><<<grid, NT, shm, st>>>(act_off, kk, nnear, P, y_off, Y, piv, diag, skpos, rscol, t_off, T);
+    count_launches(1);
+    id_T_kernel<NT, NC, T><<<grid, NT, shm, st>>>(act_off, kk, nnear, P, y_off, Y, piv, diag, skpos, rscol, t_off,
+                                                  Tout);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ F assembly
+template <class T>
 __global__ void __launch_bounds__(256) assemble_F_kernel(int leaf, const int32_t* __restrict__ act,
         const int64_t* __restrict__ act_off, const int32_t* __restrict__ perm, const double* __restrict__ a,
-        const int64_t* __restrict__ phi_off, double* __restrict__ Phi, const int32_t* __restrict__ child_k,
-        const int64_t* __restrict__ child_e_off, const double* __restrict__ childE, LaplaceK K)
+        const int64_t* __restrict__ phi_off, T* __restrict__ Phi, const int32_t* __restrict__ child_k,
+        const int64_t* __restrict__ child_e_off, const T* __restrict__ childE, LaplaceK K)
 {
     const int b = blockIdx.y;
     const int64_t a0 = act_off[b];
@@ -305,30 +342,48 @@ __global__ void __launch_bounds__(256) assemble_F_kernel(int leaf, const int32_t
     const int q = (int)(e / m), p = (int)(e - (int64_t)q * m);     // column-major (p row, q col)
     const int i = perm[a0 + p], j = perm[a0 + q];                  // natural positions
     const int gi = act[a0 + i], gj = act[a0 + j];
-    double v;
+    T v;
     if (leaf) {
-        v = (i == j) ? a[gi] + K.self : lap_entry(K, gi, gj);
+        v = (i == j) ? (T)(a[gi] + K.self) : lap_entry<T>(K, gi, gj);
     } else {
         const int k1 = child_k[2 * b], k2 = child_k[2 * b + 1];
         if (i < k1 && j < k1) v = childE[child_e_off[2 * b] + (int64_t)j * k1 + i];
         else if (i >= k1 && j >= k1) v = childE[child_e_off[2 * b + 1] + (int64_t)(j - k1) * k2 + (i - k1)];
-        else v = lap_entry(K, gi, gj);
+        else v = lap_entry<T>(K, gi, gj);
     }
     Phi[phi_off[b] + e] = v;
 }
 
+template <class T>
 cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act, const int64_t* act_off,
-                              const int32_t* perm, const double* a, const int64_t* phi_off, double* Phi,
-                              const int32_t* child_k, const int64_t* child_e_off, const double* childE, LaplaceK K,
+                              const int32_t* perm, const double* a, const int64_t* phi_off, T* Phi,
+                              const int32_t* child_k, const int64_t* child_e_off, const T* childE, LaplaceK K,
                               int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
     const int64_t ent = (int64_t)max_m * max_m;
     dim3 grid((unsigned)((ent + 255) / 256), (unsigned)nb);
     count_launches(1);
-    assemble_F_kernel<<<grid, 256, 0, st>>>(leaf ? 1 : 0, act, act_off, perm, a, phi_off, Phi, child_k, child_e_off,
-                                            childE, K);
+    assemble_F_kernel<T><<<grid, 256, 0, st>>>(leaf ? 1 : 0, act, act_off, perm, a, phi_off, Phi, child_k, child_e_off,
+                                               childE, K);
     return cudaGetLastError();
 }
+
+#define RS_INST_FACTOR(T)                                                                                              \
+    template cudaError_t launch_assemble_Y<T>(cudaStream_t, int, const int32_t*, const int64_t*, const int32_t*,     \
+                                              const int64_t*, const double*, const double*, int, const int64_t*, T*, \
+                                              LaplaceK, int);                                                        \
+    template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int64_t*, const int32_t*, int, const int64_t*, \
+                                        T*, double, int32_t*, int32_t*, T*, unsigned int*, unsigned long long*,     \
+                                        int*, long long, int, int);                                                 \
+    template int cpqr_max_ctas<T>(int, int, int);                                                                    \
+    template cudaError_t launch_id_T<T>(cudaStream_t, int, const int64_t*, const int32_t*, const int32_t*, int,      \
+                                        const int64_t*, const T*, const int32_t*, const T*, const int32_t*,         \
+                                        const int32_t*, const int64_t*, T*, int, int);                              \
+    template cudaError_t launch_assemble_F<T>(cudaStream_t, int, bool, const int32_t*, const int64_t*,              \
+                                              const int32_t*, const double*, const int64_t*, T*, const int32_t*,     \
+                                              const int64_t*, const T*, LaplaceK, int);
+RS_INST_FACTOR(double)
+RS_INST_FACTOR(float)
 
 }  // namespace rs

@@ -21,10 +21,12 @@ namespace rs {
 //      update with NB FMAs per element loaded.
 // This equals the unblocked algorithm step for step (same pivots, same operations per row).
 // A pivot with |pivot| not above 1e3 * unit roundoff * (largest earlier pivot of the same CTA)
-// sets DEV_SINGULAR; the loop still finishes.
-template <int NT, int NB>
+// sets DEV_SINGULAR; the loop still finishes.  The panel arithmetic (pivot values and the
+// panel's own elimination) runs in FP64 for every storage type T; the rank-NB trailing update
+// runs in T.
+template <int NT, int NB, class T>
 __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
-        double* __restrict__ Aall, int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off,
+        T* __restrict__ Aall, int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off,
         int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
 {
     constexpr int CB = 32;                 // own columns updated per chunk
@@ -33,11 +35,11 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
     __shared__ int ired[NT / 32];
     __shared__ int s_piv[NB];
     __shared__ double s_row[NB];
-    __shared__ double s_aK[NB][CB];
+    __shared__ T s_aK[NB][CB];
     __shared__ int s_col[CB];
     const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
     const int m = msz[b];
-    double* __restrict__ A = Aall + off[b];
+    T* __restrict__ A = Aall + off[b];
     double* f = sm;                        // m: the current pivot column (panel step)
     int32_t* ip = ipiv + ipiv_off[b];
     int* pb = pivbuf + (int64_t)b * 2 * NB;
@@ -49,11 +51,11 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
         if (q % G == gi) {
             for (int t = 0; t < kw; ++t) {
                 const int c = k0 + t;
-                const double* col = A + (int64_t)c * m;
+                const T* col = A + (int64_t)c * m;
                 double best = -1.0;
                 int bi = m;
                 for (int i = c + threadIdx.x; i < m; i += NT) {
-                    const double a = fabs(col[i]);
+                    const double a = fabs((double)col[i]);
                     if (a > best) { best = a; bi = i; }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
@@ -74,14 +76,14 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 __syncthreads();
                 const int p = s_piv[t];
                 if (threadIdx.x < kw && p != c) {           // swap rows c, p inside the panel
-                    double* cj = A + (int64_t)(k0 + threadIdx.x) * m;
-                    const double u = cj[c];
+                    T* cj = A + (int64_t)(k0 + threadIdx.x) * m;
+                    const T u = cj[c];
                     cj[c] = cj[p];
                     cj[p] = u;
                 }
                 __syncthreads();
-                for (int i = threadIdx.x; i < m; i += NT) f[i] = col[i];
-                if (threadIdx.x < kw) s_row[threadIdx.x] = A[(int64_t)(k0 + threadIdx.x) * m + c];
+                for (int i = threadIdx.x; i < m; i += NT) f[i] = (double)col[i];
+                if (threadIdx.x < kw) s_row[threadIdx.x] = (double)A[(int64_t)(k0 + threadIdx.x) * m + c];
                 __syncthreads();
                 const double pv = f[c];
                 if (threadIdx.x == 0 && (!(fabs(pv) > 1e3 * 0.5 * DBL_EPSILON * maxpiv) || !isfinite(pv)))
@@ -90,12 +92,12 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 const double pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
                 for (int e = threadIdx.x; e < m * kw; e += NT) {
                     const int jj = e / m, i = e - jj * m;
-                    double* cj = A + (int64_t)(k0 + jj) * m;
+                    T* cj = A + (int64_t)(k0 + jj) * m;
                     if (k0 + jj == c) {
-                        cj[i] = (i == c) ? pinv : -f[i] * pinv;
+                        cj[i] = (T)((i == c) ? pinv : -f[i] * pinv);
                     } else {
                         const double aj = s_row[jj] * pinv;
-                        cj[i] = (i == c) ? aj : fma(-f[i], aj, cj[i]);
+                        cj[i] = (T)((i == c) ? aj : fma(-f[i], aj, (double)cj[i]));
                     }
                 }
                 __syncthreads();
@@ -124,11 +126,11 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
             if (nc == 0) break;
             // row swaps of block q, then the pivot rows a_K of each column
             if (threadIdx.x < nc) {
-                double* cj = A + (int64_t)s_col[threadIdx.x] * m;
+                T* cj = A + (int64_t)s_col[threadIdx.x] * m;
                 for (int t = 0; t < kw; ++t) {
                     const int p = s_piv[t];
                     if (p != k0 + t) {
-                        const double u = cj[k0 + t];
+                        const T u = cj[k0 + t];
                         cj[k0 + t] = cj[p];
                         cj[p] = u;
                     }
@@ -137,13 +139,13 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
             }
             __syncthreads();
             for (int i = threadIdx.x; i < m; i += NT) {
-                double P[NB];
+                T P[NB];
 #pragma unroll
-                for (int t = 0; t < NB; ++t) P[t] = (t < kw) ? __ldcg(A + (int64_t)(k0 + t) * m + i) : 0.0;
+                for (int t = 0; t < NB; ++t) P[t] = (t < kw) ? __ldcg(A + (int64_t)(k0 + t) * m + i) : (T)0;
                 const bool inK = (i >= k0) && (i < k0 + kw);
                 for (int jj = 0; jj < nc; ++jj) {
-                    double* cj = A + (int64_t)s_col[jj] * m;
-                    double v = inK ? 0.0 : cj[i];
+                    T* cj = A + (int64_t)s_col[jj] * m;
+                    T v = inK ? (T)0 : cj[i];
 #pragma unroll
                     for (int t = 0; t < NB; ++t) v = fma(P[t], s_aK[t][jj], v);
                     cj[i] = v;
@@ -155,18 +157,19 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
 }
 
 // Undo the row exchanges: swap columns (c, ipiv[c]) for c = m-1 .. 0.  One CTA per matrix.
+template <class T>
 __global__ void __launch_bounds__(256) gj_unpivot_kernel(const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
-        double* __restrict__ Aall, const int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off)
+        T* __restrict__ Aall, const int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off)
 {
     const int b = blockIdx.x;
     const int m = msz[b];
-    double* A = Aall + off[b];
+    T* A = Aall + off[b];
     const int32_t* ip = ipiv + ipiv_off[b];
     for (int c = m - 1; c >= 0; --c) {
         const int p = ip[c];
         if (p == c) continue;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double t = A[(int64_t)c * m + i];
+            const T t = A[(int64_t)c * m + i];
             A[(int64_t)c * m + i] = A[(int64_t)p * m + i];
             A[(int64_t)p * m + i] = t;
         }
@@ -178,55 +181,59 @@ constexpr int GJ_NT = 256, GJ_NB = 8;
 
 static size_t gj_shm(int max_m) { return sizeof(double) * (size_t)max_m + 64; }
 
+template <class T>
 int gj_max_ctas(int max_m, int G)
 {
     (void)G;
     const size_t shm = gj_shm(max_m);
-    cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<GJ_NT, GJ_NB>, GJ_NT, shm) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<GJ_NT, GJ_NB, T>, GJ_NT, shm) != cudaSuccess)
         return 0;
     return per_sm * sms;
 }
 
 int gj_panel_width() { return GJ_NB; }
 
-cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, double* A,
+template <class T>
+cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A,
                               int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf, unsigned int* bar, int* status,
                               long long spin_limit, int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
     const size_t shm = gj_shm(max_m);
-    cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     if (G == 1) {
         count_launches(1);
-        gj_kernel<GJ_NT, GJ_NB><<<nb, GJ_NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status, spin_limit);
+        gj_kernel<GJ_NT, GJ_NB, T><<<nb, GJ_NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status,
+                                                           spin_limit);
     } else {
         void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&pivbuf,
                         (void*)&bar, (void*)&status, (void*)&spin_limit};
         count_launches(1);
-        e = cudaLaunchCooperativeKernel((void*)gj_kernel<GJ_NT, GJ_NB>, dim3((unsigned)(nb * G)), dim3(GJ_NT), args,
+        e = cudaLaunchCooperativeKernel((void*)gj_kernel<GJ_NT, GJ_NB, T>, dim3((unsigned)(nb * G)), dim3(GJ_NT), args,
                                         shm, st);
         if (e != cudaSuccess) return e;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launches(1);
-    gj_unpivot_kernel<<<nb, 256, 0, st>>>(m, off, A, ipiv, ipiv_off);
+    gj_unpivot_kernel<T><<<nb, 256, 0, st>>>(m, off, A, ipiv, ipiv_off);
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ grouped GEMM (FP64)
+// ------------------------------------------------------------------ grouped GEMM
 // 64 x 64 tile per CTA, 256 threads with a 4 x 4 register block each, K in steps of 16.
+template <class T>
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmProb* __restrict__ probs, int np,
-        const double* __restrict__ Ab, const double* __restrict__ Bb, double* Cb, const double* C0b)
+        const T* __restrict__ Ab, const T* __restrict__ Bb, T* Cb, const T* C0b)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
     const int64_t t = blockIdx.x;
     int lo = 0, hi = np - 1;
     while (lo < hi) {
@@ -237,34 +244,34 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmProb* __restrict__ 
     const int64_t lt = t - P.tile0;
     const int tm = (int)(lt % P.tiles_m), tn = (int)(lt / P.tiles_m);
     const int row0 = tm * BM, col0 = tn * BN;
-    const double* A = Ab + P.a_off;
-    const double* B = Bb + P.b_off;
-    double* C = Cb + P.c_off;
+    const T* A = Ab + P.a_off;
+    const T* B = Bb + P.b_off;
+    T* C = Cb + P.c_off;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = 0.0;
+        for (int w = 0; w < 4; ++w) acc[u][w] = 0;
     for (int k0 = 0; k0 < P.K; k0 += BK) {
         for (int e = threadIdx.x; e < BM * BK; e += 256) {
             const int i = e % BM, kk = e / BM;
             const int gi = row0 + i, gk = k0 + kk;
-            double v = 0.0;
+            T v = 0;
             if (gi < P.M && gk < P.K) v = P.ta ? A[(int64_t)gi * P.lda + gk] : A[(int64_t)gk * P.lda + gi];
             As[kk][i] = v;
         }
         for (int e = threadIdx.x; e < BN * BK; e += 256) {
             const int kk = e % BK, j = e / BK;
             const int gj = col0 + j, gk = k0 + kk;
-            double v = 0.0;
+            T v = 0;
             if (gj < P.N && gk < P.K) v = P.tb ? B[(int64_t)gk * P.ldb + gj] : B[(int64_t)gj * P.ldb + gk];
             Bs[kk][j] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], bv[4];
+            T a[4], bv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
 #pragma unroll
@@ -282,30 +289,32 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmProb* __restrict__ 
         for (int w = 0; w < 4; ++w) {
             const int gi = row0 + tx + 16 * u, gj = col0 + ty + 16 * w;
             if (gi < P.M && gj < P.N) {
-                double* c = C + (int64_t)gj * P.ldc + gi;
-                const double c0 = (P.beta == 0.0) ? 0.0 : C0b[P.c0_off + (int64_t)gj * P.ldc0 + gi];
-                *c = P.alpha * acc[u][w] + P.beta * c0;
+                T* c = C + (int64_t)gj * P.ldc + gi;
+                const T c0 = (P.beta == 0.0) ? (T)0 : C0b[P.c0_off + (int64_t)gj * P.ldc0 + gi];
+                *c = (T)P.alpha * acc[u][w] + (T)P.beta * c0;
             }
         }
 }
 
-cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const double* A,
-                        const double* B, double* C, const double* C0)
+template <class T>
+cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const T* A, const T* B, T* C,
+                        const T* C0)
 {
     if (np <= 0 || tiles <= 0) return cudaSuccess;
     count_launches(1);
-    gemm_kernel<<<(unsigned)tiles, 256, 0, st>>>(probs, np, A, B, C, C0);
+    gemm_kernel<T><<<(unsigned)tiles, 256, 0, st>>>(probs, np, A, B, C, C0);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ batched matvec(s)
 // Each CTA produces 64 output rows of one problem for all nrhs columns (chunks of 8).
+template <class T>
 __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restrict__ probs,
-        const int64_t* __restrict__ blk0, int np, const double* __restrict__ Ab, const double* __restrict__ xb,
-        double* __restrict__ yb, int nrhs)
+        const int64_t* __restrict__ blk0, int np, const T* __restrict__ Ab, const T* __restrict__ xb,
+        T* __restrict__ yb, int nrhs)
 {
     constexpr int RB = 64, CH = 8;
-    __shared__ double part[4][RB][CH];
+    __shared__ T part[4][RB][CH];
     const int64_t t = blockIdx.x;
     int lo = 0, hi = np - 1;
     while (lo < hi) {
@@ -314,22 +323,22 @@ __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restric
     }
     const MatvecProb P = probs[lo];
     const int orow0 = (int)(t - blk0[lo]) * RB;
-    const double* A = Ab + P.a_off;
-    const double* x = xb + P.x_off * nrhs;
-    double* y = yb + P.y_off * nrhs;
+    const T* A = Ab + P.a_off;
+    const T* x = xb + P.x_off * nrhs;
+    T* y = yb + P.y_off * nrhs;
     const int out_n = P.trans ? P.cols : P.rows;
     const int in_n = P.trans ? P.rows : P.cols;
     for (int c0 = 0; c0 < nrhs; c0 += CH) {
         const int nc = min(CH, nrhs - c0);
-        double acc[CH];
+        T acc[CH];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+        for (int c = 0; c < CH; ++c) acc[c] = 0;
         if (!P.trans) {
             const int ri = threadIdx.x & 63, cj = threadIdx.x >> 6;   // 64 rows x 4 column phases
             const int i = orow0 + ri;
             if (i < out_n) {
                 for (int j = cj; j < in_n; j += 4) {
-                    const double a = A[(int64_t)j * P.ld + i];
+                    const T a = A[(int64_t)j * P.ld + i];
 #pragma unroll
                     for (int c = 0; c < CH; ++c)
                         if (c < nc) acc[c] = fma(a, x[(int64_t)j * nrhs + c0 + c], acc[c]);
@@ -342,10 +351,10 @@ __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restric
                 const int i2 = orow0 + threadIdx.x;
                 if (i2 < out_n)
                     for (int c = 0; c < nc; ++c) {
-                        const double s = part[0][threadIdx.x][c] + part[1][threadIdx.x][c] + part[2][threadIdx.x][c] +
-                                         part[3][threadIdx.x][c];
-                        double* yy = y + (int64_t)i2 * nrhs + c0 + c;
-                        *yy = (P.beta == 0.0) ? P.alpha * s : P.alpha * s + P.beta * (*yy);
+                        const T s = part[0][threadIdx.x][c] + part[1][threadIdx.x][c] + part[2][threadIdx.x][c] +
+                                    part[3][threadIdx.x][c];
+                        T* yy = y + (int64_t)i2 * nrhs + c0 + c;
+                        *yy = (P.beta == 0.0) ? (T)P.alpha * s : (T)P.alpha * s + (T)P.beta * (*yy);
                     }
             }
             __syncthreads();
@@ -354,12 +363,12 @@ __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restric
             for (int q = warp; q < RB; q += 8) {
                 const int j = orow0 + q;
                 if (j >= out_n) break;
-                double a2[CH];
+                T a2[CH];
 #pragma unroll
-                for (int c = 0; c < CH; ++c) a2[c] = 0.0;
-                const double* colj = A + (int64_t)j * P.ld;
+                for (int c = 0; c < CH; ++c) a2[c] = 0;
+                const T* colj = A + (int64_t)j * P.ld;
                 for (int i = lane; i < in_n; i += 32) {
-                    const double a = colj[i];
+                    const T a = colj[i];
 #pragma unroll
                     for (int c = 0; c < CH; ++c)
                         if (c < nc) a2[c] = fma(a, x[(int64_t)i * nrhs + c0 + c], a2[c]);
@@ -368,26 +377,28 @@ __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restric
                 for (int c = 0; c < CH; ++c) a2[c] = warp_sum(a2[c]);
                 if (lane == 0)
                     for (int c = 0; c < nc; ++c) {
-                        double* yy = y + (int64_t)j * nrhs + c0 + c;
-                        *yy = (P.beta == 0.0) ? P.alpha * a2[c] : P.alpha * a2[c] + P.beta * (*yy);
+                        T* yy = y + (int64_t)j * nrhs + c0 + c;
+                        *yy = (P.beta == 0.0) ? (T)P.alpha * a2[c] : (T)P.alpha * a2[c] + (T)P.beta * (*yy);
                     }
             }
         }
     }
 }
 
+template <class T>
 cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np, int64_t blocks,
-                          const double* A, const double* x, double* y, int nrhs)
+                          const T* A, const T* x, T* y, int nrhs)
 {
     if (np <= 0 || blocks <= 0) return cudaSuccess;
     count_launches(1);
-    matvec_kernel<<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
+    matvec_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ gathers
-__global__ void gather_rows_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
-                                   double* __restrict__ out, int nrhs)
+template <class T>
+__global__ void gather_rows_kernel(int64_t count, const int64_t* __restrict__ idx, const T* __restrict__ in,
+                                   T* __restrict__ out, int nrhs)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count * nrhs) return;
@@ -396,8 +407,9 @@ __global__ void gather_rows_kernel(int64_t count, const int64_t* __restrict__ id
     out[e] = in[idx[p] * nrhs + c];
 }
 
-__global__ void scatter_rows_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
-                                    double* __restrict__ out, int nrhs)
+template <class T>
+__global__ void scatter_rows_kernel(int64_t count, const int64_t* __restrict__ idx, const T* __restrict__ in,
+                                    T* __restrict__ out, int nrhs)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count * nrhs) return;
@@ -406,27 +418,30 @@ __global__ void scatter_rows_kernel(int64_t count, const int64_t* __restrict__ i
     out[idx[p] * nrhs + c] = in[e];
 }
 
-__global__ void gather_cm_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
-                                 int64_t N, double* __restrict__ out, int nrhs)
+template <class Ti, class To>
+__global__ void gather_cm_kernel(int64_t count, const int64_t* __restrict__ idx, const Ti* __restrict__ in,
+                                 int64_t N, To* __restrict__ out, int nrhs)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count * nrhs) return;
     const int64_t p = e / nrhs;
     const int c = (int)(e - p * nrhs);
-    out[e] = in[(int64_t)c * N + idx[p]];
+    out[e] = (To)in[(int64_t)c * N + idx[p]];
 }
 
-__global__ void scatter_cm_kernel(int64_t count, const int64_t* __restrict__ idx, const double* __restrict__ in,
-                                  int64_t N, double* __restrict__ out, int nrhs)
+template <class Ti, class To>
+__global__ void scatter_cm_kernel(int64_t count, const int64_t* __restrict__ idx, const Ti* __restrict__ in,
+                                  int64_t N, To* __restrict__ out, int nrhs)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count * nrhs) return;
     const int64_t p = e / nrhs;
     const int c = (int)(e - p * nrhs);
-    out[(int64_t)c * N + idx[p]] = in[e];
+    out[(int64_t)c * N + idx[p]] = (To)in[e];
 }
 
-__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y)
+template <class T>
+__global__ void axpby_kernel(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) y[e] = a * x[e] + b * y[e];
@@ -434,48 +449,69 @@ __global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, 
 
 static unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-cudaError_t launch_gather_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, double* out,
-                               int nrhs)
+template <class T>
+cudaError_t launch_gather_rows(cudaStream_t st, int64_t count, const int64_t* idx, const T* in, T* out, int nrhs)
 {
     if (count <= 0) return cudaSuccess;
     count_launches(1);
-    gather_rows_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, out, nrhs);
+    gather_rows_kernel<T><<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, out, nrhs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, double* out,
-                                int nrhs)
+template <class T>
+cudaError_t launch_scatter_rows(cudaStream_t st, int64_t count, const int64_t* idx, const T* in, T* out, int nrhs)
 {
     if (count <= 0) return cudaSuccess;
     count_launches(1);
-    scatter_rows_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, out, nrhs);
+    scatter_rows_kernel<T><<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, out, nrhs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, int64_t N,
-                             double* out, int nrhs)
+template <class Ti, class To>
+cudaError_t launch_gather_cm(cudaStream_t st, int64_t count, const int64_t* idx, const Ti* in, int64_t N, To* out,
+                             int nrhs)
 {
     if (count <= 0) return cudaSuccess;
     count_launches(1);
-    gather_cm_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, N, out, nrhs);
+    gather_cm_kernel<Ti, To><<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, N, out, nrhs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in, int64_t N,
-                              double* out, int nrhs)
+template <class Ti, class To>
+cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx, const Ti* in, int64_t N, To* out,
+                              int nrhs)
 {
     if (count <= 0) return cudaSuccess;
     count_launches(1);
-    scatter_cm_kernel<<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, N, out, nrhs);
+    scatter_cm_kernel<Ti, To><<<nblk(count * nrhs), 256, 0, st>>>(count, idx, in, N, out, nrhs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y)
+template <class T>
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y)
 {
     if (n <= 0) return cudaSuccess;
     count_launches(1);
-    axpby_kernel<<<nblk(n), 256, 0, st>>>(n, a, x, b, y);
+    axpby_kernel<T><<<nblk(n), 256, 0, st>>>(n, a, x, b, y);
     return cudaGetLastError();
 }
+
+#define RS_INST_LINALG(T)                                                                                             \
+    template int gj_max_ctas<T>(int, int);                                                                          \
+    template cudaError_t launch_gj_inverse<T>(cudaStream_t, int, int, const int32_t*, const int64_t*, T*, int32_t*, \
+                                              const int64_t*, int*, unsigned int*, int*, long long, int);           \
+    template cudaError_t launch_gemm<T>(cudaStream_t, const GemmProb*, int, int64_t, const T*, const T*, T*,        \
+                                        const T*);                                                                  \
+    template cudaError_t launch_matvec<T>(cudaStream_t, const MatvecProb*, const int64_t*, int, int64_t, const T*,  \
+                                          const T*, T*, int);                                                       \
+    template cudaError_t launch_gather_rows<T>(cudaStream_t, int64_t, const int64_t*, const T*, T*, int);           \
+    template cudaError_t launch_scatter_rows<T>(cudaStream_t, int64_t, const int64_t*, const T*, T*, int);          \
+    template cudaError_t launch_gather_cm<double, T>(cudaStream_t, int64_t, const int64_t*, const double*, int64_t, \
+                                                     T*, int);                                                      \
+    template cudaError_t launch_scatter_cm<T, double>(cudaStream_t, int64_t, const int64_t*, const T*, int64_t,     \
+                                                      double*, int);                                                \
+    template cudaError_t launch_axpby<T>(cudaStream_t, int64_t, T, const T*, T, T*);
+RS_INST_LINALG(double)
+RS_INST_LINALG(float)
 
 }  // namespace rs

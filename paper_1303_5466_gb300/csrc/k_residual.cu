@@ -1,0 +1,153 @@
+// k_residual.cu -- FP64 direct-sum residual r = f - A x of the Laplace Nystrom matrix, used by
+// the iterative refinement of the mixed-precision factorization and by rs_residual.
+//
+// The off-diagonal entries depend only on the integer offset (d1, d2) between two grid points,
+// so they are tabulated once for the (2n-1)^2 offsets; the sum over all N^2 pairs is then one
+// FP64 FMA per pair with the table and the sources staged in shared memory, 16 x 16 targets
+// against 16 x 16 sources per step.
+#include "k_common.cuh"
+
+namespace rs {
+
+// Kt[(d1 + n - 1) + (2n - 1)(d2 + n - 1)] = c0 log((d1 h)^2 + (d2 h)^2), 0 at d1 = d2 = 0.
+__global__ void laplace_table_kernel(int n, double h, double c0, double* __restrict__ Kt)
+{
+    const int W = 2 * n - 1;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)W * W) return;
+    const int d1 = (int)(e % W) - (n - 1), d2 = (int)(e / W) - (n - 1);
+    const double dx = (double)d1 * h, dy = (double)d2 * h;
+    Kt[e] = (d1 == 0 && d2 == 0) ? 0.0 : c0 * log(dx * dx + dy * dy);
+}
+
+constexpr int DS = 16;          // tile side of targets and sources
+constexpr int DS_RHS = 4;       // right-hand sides per pass
+
+// yg = A xg in grid order: yg[c N + g] = dg[g] xg[c N + g] + sum_{g' != g} K(g - g') xg[c N + g'].
+__global__ void __launch_bounds__(256) direct_sum_kernel(int n, const double* __restrict__ Kt,
+        const double* __restrict__ dg, const double* __restrict__ xg, double* __restrict__ yg, int nrhs)
+{
+    __shared__ double Kw[2 * DS - 1][2 * DS];
+    __shared__ double xs[DS_RHS][DS * DS];
+    const int64_t N = (int64_t)n * n;
+    const int W = 2 * n - 1;
+    const int tx0 = blockIdx.x * DS, ty0 = blockIdx.y * DS;
+    const int lx = threadIdx.x % DS, ly = threadIdx.x / DS;
+    const int ti1 = tx0 + lx, ti2 = ty0 + ly;
+    const bool tin = ti1 < n && ti2 < n;
+    for (int c0 = 0; c0 < nrhs; c0 += DS_RHS) {
+        const int nc = min(DS_RHS, nrhs - c0);
+        double acc[DS_RHS];
+#pragma unroll
+        for (int c = 0; c < DS_RHS; ++c) acc[c] = 0.0;
+        for (int sy0 = 0; sy0 < n; sy0 += DS) {
+            for (int sx0 = 0; sx0 < n; sx0 += DS) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < (2 * DS - 1) * (2 * DS - 1); e += blockDim.x) {
+                    const int e1 = e % (2 * DS - 1), e2 = e / (2 * DS - 1);
+                    const int d1 = tx0 - sx0 - (DS - 1) + e1, d2 = ty0 - sy0 - (DS - 1) + e2;
+                    Kw[e2][e1] = (d1 > -n && d1 < n && d2 > -n && d2 < n)
+                                     ? Kt[(int64_t)(d1 + n - 1) + (int64_t)W * (d2 + n - 1)]
+                                     : 0.0;
+                }
+                for (int e = threadIdx.x; e < nc * DS * DS; e += blockDim.x) {
+                    const int c = e / (DS * DS), j = e - c * (DS * DS);
+                    const int s1 = sx0 + j % DS, s2 = sy0 + j / DS;
+                    xs[c][j] = (s1 < n && s2 < n) ? xg[(int64_t)(c0 + c) * N + s1 + (int64_t)n * s2] : 0.0;
+                }
+                __syncthreads();
+                if (tin) {
+#pragma unroll 4
+                    for (int j2 = 0; j2 < DS; ++j2) {
+#pragma unroll
+                        for (int j1 = 0; j1 < DS; ++j1) {
+                            const double k = Kw[ly - j2 + DS - 1][lx - j1 + DS - 1];
+#pragma unroll
+                            for (int c = 0; c < DS_RHS; ++c)
+                                if (c < nc) acc[c] = fma(k, xs[c][j2 * DS + j1], acc[c]);
+                        }
+                    }
+                }
+            }
+        }
+        if (tin) {
+            const int64_t g = ti1 + (int64_t)n * ti2;
+            for (int c = 0; c < nc; ++c)
+                yg[(int64_t)(c0 + c) * N + g] = fma(dg[g], xg[(int64_t)(c0 + c) * N + g], acc[c]);
+        }
+    }
+}
+
+// xg[c N + g] = x[c N + ing[g]]
+__global__ void to_grid_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing, const double* __restrict__ x,
+                               double* __restrict__ xg)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * nrhs) return;
+    const int64_t c = e / N, g = e - c * N;
+    xg[e] = x[c * N + ing[g]];
+}
+
+// r[c N + ing[g]] = f[c N + ing[g]] - yg[c N + g]
+__global__ void residual_finish_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing,
+                                       const double* __restrict__ f, const double* __restrict__ yg,
+                                       double* __restrict__ r)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * nrhs) return;
+    const int64_t c = e / N, g = e - c * N;
+    const int64_t i = c * N + ing[g];
+    r[i] = f[i] - yg[e];
+}
+
+// out[2c] += sum_i r[c N + i]^2, out[2c + 1] += sum_i f[c N + i]^2
+__global__ void __launch_bounds__(256) colnorm2_kernel(int64_t N, int nrhs, const double* __restrict__ r,
+                                                       const double* __restrict__ f, double* __restrict__ out)
+{
+    __shared__ double sr[8], sf[8];
+    const int c = blockIdx.y;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double u = r[(int64_t)c * N + i], v = f[(int64_t)c * N + i];
+        a = fma(u, u, a);
+        b = fma(v, v, b);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = a; sf[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < 8; ++w) { ta += sr[w]; tb += sf[w]; }
+        atomicAdd(out + 2 * c, ta);
+        atomicAdd(out + 2 * c + 1, tb);
+    }
+}
+
+static unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+cudaError_t launch_laplace_table(cudaStream_t st, int n, double h, double c0, double* Kt)
+{
+    const int64_t W = 2 * (int64_t)n - 1;
+    count_launches(1);
+    laplace_table_kernel<<<nblk(W * W), 256, 0, st>>>(n, h, c0, Kt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const double* Kt, const double* dg, const int64_t* ing,
+                            const double* x, const double* f, double* xg, double* yg, double* r, double* norms)
+{
+    const int64_t N = (int64_t)n * n;
+    count_launches(4);
+    to_grid_kernel<<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, x, xg);
+    dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
+    direct_sum_kernel<<<grid, 256, 0, st>>>(n, Kt, dg, xg, yg, nrhs);
+    residual_finish_kernel<<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, f, yg, r);
+    cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nrhs, st);
+    if (e != cudaSuccess) return e;
+    dim3 g2((unsigned)std::min<int64_t>(nblk(N), 1024), (unsigned)nrhs);
+    colnorm2_kernel<<<g2, 256, 0, st>>>(N, nrhs, r, f, norms);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

@@ -121,7 +121,8 @@ struct IdWork {
     DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys;
 };
 
-int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, double* A,
+template <class T>
+int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, T* A,
            const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls)
 {
     if (max_m <= 0) return RS_OK;
@@ -134,17 +135,18 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
     RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
     // one CTA per panel of columns at most
-    const int G = choose_group(nb, max_m * 32 / gj_panel_width(), [&](int g) { return gj_max_ctas(max_m, g); });
+    const int G = choose_group(nb, max_m * 32 / gj_panel_width(), [&](int g) { return gj_max_ctas<T>(max_m, g); });
     double work = 0.0;
     for (int b = 0; b < nb; ++b) work += 2.0 * (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
-    ProfScope ps(op, cls, st, work, 16.0 * (double)size_off[nb]);
-    RS_CUDA(launch_gj_inverse(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_ipiv.as<int32_t>(),
+    ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb]);
+    RS_CUDA(launch_gj_inverse<T>(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_ipiv.as<int32_t>(),
                               d_ipoff.as<int64_t>(), op->d_pivrow.as<int>(), op->d_bar.as<unsigned int>(),
                               op->d_status.as<int>(), (long long)op->opts.spin_limit, max_m));
     return check_status(op, st);
 }
 
 // ID phase of one level (Sec. 2.2 proxy ID, Eq. 2.1).
+template <class T>
 int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st)
 {
     const int P = op->opts.proxy_points;
@@ -178,27 +180,27 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     if ((rc = upload(w.geo, geo, st))) return rc;
     if ((rc = upload(w.y_off, y_off, st))) return rc;
     if ((rc = upload(w.nn, to32(L.nn), st))) return rc;
-    RS_CUDA(w.Y.alloc(sizeof(double) * (size_t)(y_off[nb] + 1)));
+    RS_CUDA(w.Y.alloc(sizeof(T) * (size_t)(y_off[nb] + 1)));
     {
-    ProfScope ps(op, RS_PROF_ASSEMBLE_Y, st, (double)y_off[nb], 8.0 * (double)y_off[nb]);
-    RS_CUDA(launch_assemble_Y(st, nb, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), w.near.as<int32_t>(),
-                              w.near_off.as<int64_t>(), w.geo.as<double>(), op->d_ucirc.as<double>(), P,
-                              w.y_off.as<int64_t>(), w.Y.as<double>(), op->K, (int)max_entries));
+    ProfScope ps(op, RS_PROF_ASSEMBLE_Y, st, (double)y_off[nb], sizeof(T) * (double)y_off[nb]);
+    RS_CUDA(launch_assemble_Y<T>(st, nb, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), w.near.as<int32_t>(),
+                                 w.near_off.as<int64_t>(), w.geo.as<double>(), op->d_ucirc.as<double>(), P,
+                                 w.y_off.as<int64_t>(), w.Y.as<T>(), op->K, (int)max_entries));
     }
     const int64_t sum_m = L.act_off[nb];
     RS_CUDA(w.piv.alloc(sizeof(int32_t) * (sum_m + 1)));
-    RS_CUDA(w.diag.alloc(sizeof(double) * (sum_m + 1)));
+    RS_CUDA(w.diag.alloc(sizeof(T) * (sum_m + 1)));
     RS_CUDA(L.d_k.alloc(sizeof(int32_t) * nb));
     RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
     const int max_r = L.max_r, max_m = L.max_m;
-    const int G = choose_group(nb, max_m, [&](int g) { return cpqr_max_ctas(max_r, max_m, g); });
+    const int G = choose_group(nb, max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
     RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * 2 * (size_t)nb * G));
     {
     // the rank is known only afterwards: the work is added once k is read back
     ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0);
-    RS_CUDA(launch_cpqr(st, nb, G, L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
-                        w.Y.as<double>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<double>(),
+    RS_CUDA(launch_cpqr<T>(st, nb, G, L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
+                        w.Y.as<T>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<T>(),
                         op->d_bar.as<unsigned int>(), w.keys.as<unsigned long long>(), op->d_status.as<int>(),
                         (long long)op->opts.spin_limit, max_r, max_m));
     }
@@ -254,18 +256,19 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     if ((rc = upload(w.rscol, rscol, st))) return rc;
     if ((rc = upload(L.d_t_off, L.t_off, st))) return rc;
     if ((rc = upload(L.d_k_off, L.k_off, st))) return rc;
-    RS_CUDA(L.d_T.alloc(sizeof(double) * (size_t)(L.t_off[nb] + 1)));
+    RS_CUDA(L.d_T.alloc(sizeof(T) * (size_t)(L.t_off[nb] + 1)));
     {
-    ProfScope ps(op, RS_PROF_ID_T, st, t_work, 8.0 * (double)L.t_off[nb]);
-    RS_CUDA(launch_id_T(st, nb, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(), w.nn.as<int32_t>(), P,
-                        w.y_off.as<int64_t>(), w.Y.as<double>(), w.piv.as<int32_t>(), w.diag.as<double>(),
-                        w.skpos.as<int32_t>(), w.rscol.as<int32_t>(), L.d_t_off.as<int64_t>(), L.d_T.as<double>(),
+    ProfScope ps(op, RS_PROF_ID_T, st, t_work, sizeof(T) * (double)L.t_off[nb]);
+    RS_CUDA(launch_id_T<T>(st, nb, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(), w.nn.as<int32_t>(), P,
+                        w.y_off.as<int64_t>(), w.Y.as<T>(), w.piv.as<int32_t>(), w.diag.as<T>(),
+                        w.skpos.as<int32_t>(), w.rscol.as<int32_t>(), L.d_t_off.as<int64_t>(), L.d_T.as<T>(),
                         max_res, L.max_k));
     }
     return check_status(op, st);
 }
 
 // Inversion phase of one level (Algorithm 1 lines 3-11 with the E of Algorithm 2 line 9).
+template <class T>
 int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
 {
     const int nb = L.nb;
@@ -279,24 +282,24 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     }
     int rc;
     if ((rc = upload(L.d_phi_off, L.phi_off, st))) return rc;
-    RS_CUDA(L.d_Phi.alloc(sizeof(double) * (size_t)(L.phi_off[nb] + 1)));
+    RS_CUDA(L.d_Phi.alloc(sizeof(T) * (size_t)(L.phi_off[nb] + 1)));
     const bool leaf = (L.l == op->d);
     {
-    ProfScope ps(op, RS_PROF_ASSEMBLE_F, st, (double)L.phi_off[nb], 8.0 * (double)L.phi_off[nb]);
-    RS_CUDA(launch_assemble_F(st, nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), L.d_perm.as<int32_t>(),
-                              op->d_a.as<double>(), L.d_phi_off.as<int64_t>(), L.d_Phi.as<double>(),
+    ProfScope ps(op, RS_PROF_ASSEMBLE_F, st, (double)L.phi_off[nb], sizeof(T) * (double)L.phi_off[nb]);
+    RS_CUDA(launch_assemble_F<T>(st, nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), L.d_perm.as<int32_t>(),
+                              op->d_a.as<double>(), L.d_phi_off.as<int64_t>(), L.d_Phi.as<T>(),
                               child ? child->d_k.as<int32_t>() : nullptr, child ? child->d_e_off.as<int64_t>() : nullptr,
-                              child ? child->d_E.as<double>() : nullptr, op->K, L.max_m));
+                              child ? child->d_E.as<T>() : nullptr, op->K, L.max_m));
     }
-    if ((rc = run_gj(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<double>(), L.m, L.act_off, L.max_m,
+    if ((rc = run_gj<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m,
                      L.l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F)))
         return rc;
     if (L.l == 0) return RS_OK;
     // W = Phi[:, :k] + Phi[:, k:] T^T ;  E^{-1} = W[:k, :] + T W[k:, :]
     if ((rc = upload(L.d_e_off, L.e_off, st))) return rc;
-    RS_CUDA(L.d_E.alloc(sizeof(double) * (size_t)(L.e_off[nb] + 1)));
+    RS_CUDA(L.d_E.alloc(sizeof(T) * (size_t)(L.e_off[nb] + 1)));
     DevMem W, d_p1, d_p2;
-    RS_CUDA(W.alloc(sizeof(double) * (size_t)(L.w_off[nb] + 1)));
+    RS_CUDA(W.alloc(sizeof(T) * (size_t)(L.w_off[nb] + 1)));
     std::vector<GemmProb> p1, p2;
     int64_t t1 = 0, t2 = 0;
     for (int b = 0; b < nb; ++b) {
@@ -327,16 +330,17 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
             const double m = (double)L.m[b], k = (double)L.k[b];
             work += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;
         }
-        ProfScope ps(op, RS_PROF_GEMM_E, st, work, 8.0 * (double)(L.phi_off[nb] + 2 * L.w_off[nb] + L.e_off[nb]));
-        RS_CUDA(launch_gemm(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<double>(), L.d_T.as<double>(),
-                            W.as<double>(), L.d_Phi.as<double>()));
-        RS_CUDA(launch_gemm(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<double>(), W.as<double>(),
-                            L.d_E.as<double>(), W.as<double>()));
+        ProfScope ps(op, RS_PROF_GEMM_E, st, work,
+                     sizeof(T) * (double)(L.phi_off[nb] + 2 * L.w_off[nb] + L.e_off[nb]));
+        RS_CUDA(launch_gemm<T>(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<T>(), L.d_T.as<T>(),
+                               W.as<T>(), L.d_Phi.as<T>()));
+        RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
+                               L.d_E.as<T>(), W.as<T>()));
     }
     RS_CUDA(cudaStreamSynchronize(st));
     DevMem d_k32;
     if ((rc = upload(d_k32, to32(L.k), st))) return rc;
-    return run_gj(op, st, nb, d_k32, L.d_e_off, L.d_E.as<double>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E);
+    return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E);
 }
 
 void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk, int rows, int cols, int ld, int trans,
@@ -431,15 +435,15 @@ void compute_stats(rs_op* op)
             ff += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;                  // W, E^{-1}
             ff += 2.0 * k * k * k;                                                // E
             fs += 2.0 * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
-            bs += 8.0 * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
+            bs += op->esz * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
         }
-        bytes += (L.phi_off.back() + L.e_off.back() + L.t_off.back()) * 8 + L.act_off.back() * 8 + L.nb * 64;
+        bytes += (L.phi_off.back() + L.e_off.back() + L.t_off.back()) * op->esz + L.act_off.back() * 8 + L.nb * 64;
     }
     const double m0 = (double)op->lev[0].m[0];
     ff += 2.0 * m0 * m0 * m0;
     fs += 2.0 * m0 * m0;
-    bs += 8.0 * m0 * m0;
-    bytes += (int64_t)(m0 * m0 * 8);
+    bs += op->esz * m0 * m0;
+    bytes += (int64_t)(m0 * m0 * op->esz);
     s.flops_factor = ff;
     s.flops_solve_per_rhs = fs;
     s.bytes_solve = bs;
@@ -456,6 +460,43 @@ bool is_device_ptr(const void* p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Algorithm 1 over all levels in storage precision T: IDs (d..1), inverses (d..1), root.
+template <class T>
+int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
+{
+    int rc;
+    {
+        IdWork w;
+        for (int l = op->d; l >= 1; --l)
+            if ((rc = id_level<T>(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, w, st))) return rc;
+    }
+    op->stats.ms_tree = ms_since(t0);
+    auto t1 = Clock::now();
+    for (int l = op->d; l >= 1; --l)
+        if ((rc = inverse_level<T>(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    // root: active set = skeletons of (1,0) then (1,1), natural order
+    Level& R = op->lev[0];
+    const Level& L1 = op->lev[1];
+    R.m = {L1.k[0] + L1.k[1]};
+    R.k = {0};
+    R.act = L1.skel;
+    R.act_off = {0, R.m[0]};
+    R.perm.resize(R.m[0]);
+    for (int64_t i = 0; i < R.m[0]; ++i) R.perm[i] = (int32_t)i;
+    R.max_m = (int)R.m[0];
+    if ((rc = upload(R.d_act, to32(R.act), st))) return rc;
+    if ((rc = upload(R.d_act_off, R.act_off, st))) return rc;
+    if ((rc = upload(R.d_perm, R.perm, st))) return rc;
+    if ((rc = upload(R.d_m, to32(R.m), st))) return rc;
+    if ((rc = inverse_level<T>(op, R, &op->lev[1], st))) return rc;
+    for (int l = 0; l <= op->d; ++l)
+        if ((rc = solve_plan(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    RS_CUDA(cudaStreamSynchronize(st));
+    op->stats.ms_inverse = ms_since(t1);
+    compute_stats(op);
+    return RS_OK;
 }
 
 int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps, const rs_opts* opts,
@@ -475,7 +516,11 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     op->input_of_g = tree->input_of_g;
     if (op->kind != RS_LAPLACE) return fail(RS_E_INVALID, "only the Laplace kernel is built in this version");
     if (kernel && kernel->b) return fail(RS_E_INVALID, "b(x) is only used by the Helmholtz kernel");
-    if (op->opts.precision != RS_FP64) return fail(RS_E_INVALID, "only RS_FP64 is built in this version");
+    if (op->opts.precision != RS_FP64 && op->opts.precision != RS_MIXED_FP32)
+        return fail(RS_E_INVALID, "Laplace operators are factored in RS_FP64 or RS_MIXED_FP32");
+    op->esz = op->opts.precision == RS_MIXED_FP32 ? (int)sizeof(float) : (int)sizeof(double);
+    if (op->opts.precision == RS_MIXED_FP32 && !(op->opts.refine_tol > 0.0 && op->opts.refine_max_iter >= 1))
+        return fail(RS_E_INVALID, "mixed precision needs refine_tol > 0 and refine_max_iter >= 1");
     if (op->opts.proxy_points < 0 || op->opts.proxy_points > 4096 || !(op->opts.proxy_radius_factor > 0.0))
         return fail(RS_E_INVALID, "bad proxy options");
     if (!(eps >= 0.0) || !(eps < 1.0)) return fail(RS_E_INVALID, "eps must be in [0, 1)");
@@ -509,35 +554,8 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         op->lev[l].l = l;
         op->lev[l].nb = 1 << l;
     }
-    {
-        IdWork w;
-        for (int l = op->d; l >= 1; --l)
-            if ((rc = id_level(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, w, st))) return rc;
-    }
-    op->stats.ms_tree = ms_since(t0);
-    auto t1 = Clock::now();
-    for (int l = op->d; l >= 1; --l)
-        if ((rc = inverse_level(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
-    // root: active set = skeletons of (1,0) then (1,1), natural order
-    Level& R = op->lev[0];
-    const Level& L1 = op->lev[1];
-    R.m = {L1.k[0] + L1.k[1]};
-    R.k = {0};
-    R.act = L1.skel;
-    R.act_off = {0, R.m[0]};
-    R.perm.resize(R.m[0]);
-    for (int64_t i = 0; i < R.m[0]; ++i) R.perm[i] = (int32_t)i;
-    R.max_m = (int)R.m[0];
-    if ((rc = upload(R.d_act, to32(R.act), st))) return rc;
-    if ((rc = upload(R.d_act_off, R.act_off, st))) return rc;
-    if ((rc = upload(R.d_perm, R.perm, st))) return rc;
-    if ((rc = upload(R.d_m, to32(R.m), st))) return rc;
-    if ((rc = inverse_level(op, R, &op->lev[1], st))) return rc;
-    for (int l = 0; l <= op->d; ++l)
-        if ((rc = solve_plan(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
-    RS_CUDA(cudaStreamSynchronize(st));
-    op->stats.ms_inverse = ms_since(t1);
-    compute_stats(op);
+    rc = op->esz == (int)sizeof(float) ? factor_levels<float>(op, st, t0) : factor_levels<double>(op, st, t0);
+    if (rc) return rc;
     *out = guard.release();
     return RS_OK;
 }
@@ -562,19 +580,108 @@ SolveLayout solve_layout(const rs_op* op, int64_t nrhs)
     return Ls;
 }
 
+namespace {
+
+// The kernel sequence of the inverse apply (Algorithm 6 as the recursion of Eqs. 2.10-2.12)
+// in storage type T; f (fd) and x (xd) are FP64 N x nrhs column-major in input order.
+template <class T>
+int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
+                cudaStream_t st)
+{
+    const int64_t N = op->N;
+    const int d = op->d;
+    const std::vector<int64_t>& woff = Ls.woff;
+    const std::vector<int64_t>& goff = Ls.goff;
+    T* W = (T*)ws.w;
+    T* Gb = (T*)ws.g;
+    T* Ph = (T*)ws.phi;
+    T* U = (T*)ws.u;
+    T* XO = (T*)ws.out;
+    T* Tt = (T*)ws.t;
+    const int nr = (int)nrhs;
+    // upward pass
+    for (int l = d; l >= 1; --l) {
+        Level& L = op->lev[l];
+        T* wl = W + woff[l] * nrhs;
+        T* gl = Gb + goff[l] * nrhs;
+        if (l == d) RS_CUDA(launch_gather_cm<double, T>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
+        else RS_CUDA(launch_gather_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
+        RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
+                              L.d_Phi.as<T>(), U, wl, nr)); }
+        RS_CUDA(launch_gather_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), wl, Tt, nr));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, 8.0 * L.mvw_T);
+        RS_CUDA(launch_matvec<T>(st, L.d_mv_T.as<MatvecProb>(), L.d_mv_T_blk.as<int64_t>(), L.n_mv_T, L.b_mv_T,
+                              L.d_T.as<T>(), wl, Tt, nr)); }
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
+        RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
+                              L.d_E.as<T>(), Tt, gl, nr)); }
+    }
+    // root
+    {
+        Level& R = op->lev[0];
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, 8.0 * R.mvw_phi);
+        RS_CUDA(launch_matvec<T>(st, R.d_mv_phi.as<MatvecProb>(), R.d_mv_phi_blk.as<int64_t>(), R.n_mv_phi, R.b_mv_phi,
+                              R.d_Phi.as<T>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr)); }
+    }
+    // downward pass
+    for (int l = 1; l <= d; ++l) {
+        Level& L = op->lev[l];
+        T* wl = W + woff[l] * nrhs;
+        T* gl = Gb + goff[l] * nrhs;
+        T* pl = Ph + goff[l] * nrhs;
+        RS_CUDA(cudaMemcpyAsync(Tt, gl, sizeof(T) * (size_t)(L.sum_k * nrhs), cudaMemcpyDeviceToDevice, st));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
+        RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
+                              L.d_E.as<T>(), pl, Tt, nr)); }   // beta = 0: Tt = E phi
+        RS_CUDA(launch_axpby<T>(st, L.sum_k * nrhs, (T)-1, gl, (T)1, Tt));   // Tt = E phi - g
+        RS_CUDA(launch_scatter_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), Tt, U, nr));
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, 8.0 * L.mvw_Tt);
+        RS_CUDA(launch_matvec<T>(st, L.d_mv_Tt.as<MatvecProb>(), L.d_mv_Tt_blk.as<int64_t>(), L.n_mv_Tt, L.b_mv_Tt,
+                              L.d_T.as<T>(), Tt, U, nr)); }
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
+        RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
+                              L.d_Phi.as<T>(), U, XO, nr)); }
+        RS_CUDA(launch_axpby<T>(st, L.sum_m * nrhs, (T)1, wl, (T)1, XO));   // x' = w + Phi v
+        if (l == d) RS_CUDA(launch_scatter_cm<T, double>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
+        else RS_CUDA(launch_scatter_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), XO, Ph + goff[l + 1] * nrhs, nr));
+    }
+    return RS_OK;
+}
+
+}  // namespace
+
+int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
+              cudaStream_t st, bool profile)
+{
+    const int saved_profile = op->opts.profile;
+    op->opts.profile = profile ? saved_profile : 0;
+    const int rc = op->esz == (int)sizeof(float) ? solve_run_t<float>(op, Ls, ws, fd, xd, nrhs, st)
+                                                 : solve_run_t<double>(op, Ls, ws, fd, xd, nrhs, st);
+    op->opts.profile = saved_profile;
+    return rc;
+}
+
+// One inverse apply with the library's own (growing) workspace; fd, xd device FP64.
+int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st)
+{
+    const SolveLayout Ls = solve_layout(op, nrhs);
+    const size_t e = (size_t)op->esz;
+    RS_CUDA(op->s_w.alloc(e * (size_t)Ls.n_w));
+    RS_CUDA(op->s_g.alloc(e * (size_t)Ls.n_g));
+    RS_CUDA(op->s_phi.alloc(e * (size_t)Ls.n_g));
+    RS_CUDA(op->s_u.alloc(e * (size_t)Ls.n_u));
+    RS_CUDA(op->s_out.alloc(e * (size_t)Ls.n_u));
+    RS_CUDA(op->s_t.alloc(e * (size_t)Ls.n_t));
+    SolveWork ws{op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p};
+    return solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
+}
+
 int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
 {
     const int64_t N = op->N;
     const bool dev_f = is_device_ptr(f), dev_x = is_device_ptr(x);
     if (dev_f != dev_x) return fail(RS_E_INVALID, "f and x must both be device or both be host pointers");
-    // workspace: w, g, phi for all levels; u/v, x', t/y temporaries
-    const SolveLayout Ls = solve_layout(op, nrhs);
-    RS_CUDA(op->s_w.alloc(sizeof(double) * (size_t)Ls.n_w));
-    RS_CUDA(op->s_g.alloc(sizeof(double) * (size_t)Ls.n_g));
-    RS_CUDA(op->s_phi.alloc(sizeof(double) * (size_t)Ls.n_g));
-    RS_CUDA(op->s_u.alloc(sizeof(double) * (size_t)Ls.n_u));
-    RS_CUDA(op->s_out.alloc(sizeof(double) * (size_t)Ls.n_u));
-    RS_CUDA(op->s_t.alloc(sizeof(double) * (size_t)Ls.n_t));
     if (op->opts.profile) {
         op->prof_ms[RS_PROF_SOLVE] = op->prof_work[RS_PROF_SOLVE] = op->prof_bytes[RS_PROF_SOLVE] = 0.0;
         op->prof_n[RS_PROF_SOLVE] = 0;
@@ -588,10 +695,8 @@ int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
         RS_CUDA(op->s_out2.alloc(sizeof(double) * (size_t)(N * nrhs)));
         xd = op->s_out2.as<double>();
     }
-    SolveWork ws{op->s_w.as<double>(), op->s_g.as<double>(), op->s_phi.as<double>(), op->s_u.as<double>(),
-                 op->s_out.as<double>(), op->s_t.as<double>()};
-    int rc = solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
-    if (rc) return rc;
+    int rc = (op->opts.precision == RS_MIXED_FP32) ? refine_solve(op, fd, xd, nrhs, st) : apply_once(op, fd, xd, nrhs, st);
+    if (rc && rc != RS_E_NOT_CONVERGED) return rc;
     if (!dev_x) {
         RS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
         RS_CUDA(cudaStreamSynchronize(st));
@@ -600,79 +705,7 @@ int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
         RS_CUDA(cudaStreamSynchronize(st));
         prof_flush(op);
     }
-    return RS_OK;
-}
-
-// The kernel sequence of the inverse apply, on caller-provided workspace (layout Ls).
-int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
-              cudaStream_t st, bool profile)
-{
-    const int64_t N = op->N;
-    const int d = op->d;
-    const std::vector<int64_t>& woff = Ls.woff;
-    const std::vector<int64_t>& goff = Ls.goff;
-    double* W = ws.w;
-    double* Gb = ws.g;
-    double* Ph = ws.phi;
-    double* U = ws.u;
-    double* XO = ws.out;
-    double* Tt = ws.t;
-    const int saved_profile = op->opts.profile;
-    op->opts.profile = profile ? saved_profile : 0;
-    struct Restore {
-        rs_op* o;
-        int p;
-        ~Restore() { o->opts.profile = p; }
-    } restore{op, saved_profile};
-    const int nr = (int)nrhs;
-    // upward pass
-    for (int l = d; l >= 1; --l) {
-        Level& L = op->lev[l];
-        double* wl = W + woff[l] * nrhs;
-        double* gl = Gb + goff[l] * nrhs;
-        if (l == d) RS_CUDA(launch_gather_cm(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
-        else RS_CUDA(launch_gather_rows(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
-        RS_CUDA(launch_matvec(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
-                              L.d_Phi.as<double>(), U, wl, nr)); }
-        RS_CUDA(launch_gather_rows(st, L.sum_k, L.d_idx_sk.as<int64_t>(), wl, Tt, nr));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, 8.0 * L.mvw_T);
-        RS_CUDA(launch_matvec(st, L.d_mv_T.as<MatvecProb>(), L.d_mv_T_blk.as<int64_t>(), L.n_mv_T, L.b_mv_T,
-                              L.d_T.as<double>(), wl, Tt, nr)); }
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
-        RS_CUDA(launch_matvec(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
-                              L.d_E.as<double>(), Tt, gl, nr)); }
-    }
-    // root
-    {
-        Level& R = op->lev[0];
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, 8.0 * R.mvw_phi);
-        RS_CUDA(launch_matvec(st, R.d_mv_phi.as<MatvecProb>(), R.d_mv_phi_blk.as<int64_t>(), R.n_mv_phi, R.b_mv_phi,
-                              R.d_Phi.as<double>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr)); }
-    }
-    // downward pass
-    for (int l = 1; l <= d; ++l) {
-        Level& L = op->lev[l];
-        double* wl = W + woff[l] * nrhs;
-        double* gl = Gb + goff[l] * nrhs;
-        double* pl = Ph + goff[l] * nrhs;
-        RS_CUDA(cudaMemcpyAsync(Tt, gl, sizeof(double) * (size_t)(L.sum_k * nrhs), cudaMemcpyDeviceToDevice, st));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
-        RS_CUDA(launch_matvec(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
-                              L.d_E.as<double>(), pl, Tt, nr)); }   // beta = 0: Tt = E phi
-        RS_CUDA(launch_axpby(st, L.sum_k * nrhs, -1.0, gl, 1.0, Tt));   // Tt = E phi - g
-        RS_CUDA(launch_scatter_rows(st, L.sum_k, L.d_idx_sk.as<int64_t>(), Tt, U, nr));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, 8.0 * L.mvw_Tt);
-        RS_CUDA(launch_matvec(st, L.d_mv_Tt.as<MatvecProb>(), L.d_mv_Tt_blk.as<int64_t>(), L.n_mv_Tt, L.b_mv_Tt,
-                              L.d_T.as<double>(), Tt, U, nr)); }
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
-        RS_CUDA(launch_matvec(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
-                              L.d_Phi.as<double>(), U, XO, nr)); }
-        RS_CUDA(launch_axpby(st, L.sum_m * nrhs, 1.0, wl, 1.0, XO));   // x' = w + Phi v
-        if (l == d) RS_CUDA(launch_scatter_cm(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
-        else RS_CUDA(launch_scatter_rows(st, L.sum_m, L.d_idx_up.as<int64_t>(), XO, Ph + goff[l + 1] * nrhs, nr));
-    }
-    return RS_OK;
+    return rc;
 }
 
 }  // namespace rs
@@ -753,26 +786,40 @@ int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* o
     return RS_OK;
 }
 
+// Copy n entries of the factor storage (FP64 or FP32) at element offset `off` into doubles.
+static int fetch(const rs_op* op, const DevMem& d, int64_t off, int64_t n, std::vector<double>& out)
+{
+    out.assign((size_t)n, 0.0);
+    if (n == 0) return RS_OK;
+    if (op->esz == (int)sizeof(double)) {
+        RS_CUDA(cudaMemcpy(out.data(), d.as<double>() + off, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> t((size_t)n);
+        RS_CUDA(cudaMemcpy(t.data(), d.as<float>() + off, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < t.size(); ++i) out[i] = t[i];
+    }
+    return RS_OK;
+}
+
 int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out)
 {
     const Level* L = get_level(op, level, box);
     if (!L || !out) return fail(RS_E_INVALID, "level/box out of range");
     const int64_t m = L->m[box], k = L->k[box];
     RS_CUDA(cudaSetDevice(op->device));
+    std::vector<double> t;
+    int rc;
     if (which == 0) {
-        std::vector<double> t((size_t)(k * (m - k)));
-        if (!t.empty()) RS_CUDA(cudaMemcpy(t.data(), L->d_T.as<double>() + L->t_off[box], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        if ((rc = fetch(op, L->d_T, L->t_off[box], k * (m - k), t))) return rc;
         for (int64_t i = 0; i < k; ++i)
             for (int64_t j = 0; j < m - k; ++j) out[i * (m - k) + j] = t[(size_t)(j * k + i)];
     } else if (which == 1) {
-        std::vector<double> t((size_t)(m * m));
-        RS_CUDA(cudaMemcpy(t.data(), L->d_Phi.as<double>() + L->phi_off[box], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        if ((rc = fetch(op, L->d_Phi, L->phi_off[box], m * m, t))) return rc;
         const int32_t* pm = L->perm.data() + L->act_off[box];
         for (int64_t q = 0; q < m; ++q)
             for (int64_t p = 0; p < m; ++p) out[(int64_t)pm[p] * m + pm[q]] = t[(size_t)(q * m + p)];
     } else if (which == 2) {
-        std::vector<double> t((size_t)(k * k));
-        if (!t.empty()) RS_CUDA(cudaMemcpy(t.data(), L->d_E.as<double>() + L->e_off[box], sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+        if ((rc = fetch(op, L->d_E, L->e_off[box], k * k, t))) return rc;
         for (int64_t i = 0; i < k; ++i)
             for (int64_t j = 0; j < k; ++j) out[i * k + j] = t[(size_t)(j * k + i)];
     } else {
@@ -786,9 +833,10 @@ int rs_op_root_matrix(const rs_op* op, double* out)
     if (!op || !out) return fail(RS_E_INVALID, "NULL argument");
     const Level& R = op->lev[0];
     const int64_t m = R.m[0];
-    std::vector<double> t((size_t)(m * m));
     RS_CUDA(cudaSetDevice(op->device));
-    RS_CUDA(cudaMemcpy(t.data(), R.d_Phi.p, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+    std::vector<double> t;
+    const int rc = fetch(op, R.d_Phi, 0, m * m, t);
+    if (rc) return rc;
     for (int64_t q = 0; q < m; ++q)
         for (int64_t p = 0; p < m; ++p) out[p * m + q] = t[(size_t)(q * m + p)];
     return RS_OK;

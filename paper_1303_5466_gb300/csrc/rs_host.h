@@ -93,10 +93,10 @@ struct SolveLayout {
     int64_t total() const { return n_w + 2 * n_g + 2 * n_u + n_t; }
 };
 
-// Workspace pointers of one inverse apply: w (n_w), g and phi (n_g each), u and out (n_u
-// each), t (n_t).
+// Workspace pointers of one inverse apply, in the factor's storage type: w (n_w), g and
+// phi (n_g each), u and out (n_u each), t (n_t).
 struct SolveWork {
-    double *w, *g, *phi, *u, *out, *t;
+    void *w, *g, *phi, *u, *out, *t;
 };
 
 struct ProfRec {
@@ -113,10 +113,15 @@ SolveLayout solve_layout(const rs_op* op, int64_t nrhs);
 int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
               cudaStream_t st, bool profile);
 bool is_device_ptr(const void* p);
+int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st);
+int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st);
+int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
+                   cudaStream_t st);
 }  // namespace rs
 
 struct rs_op {
     int device = 0;
+    int esz = 8;                      // bytes per stored factor entry (8 FP64, 4 mixed FP32)
     int64_t n = 0, N = 0;
     int d = 0;
     rs_kernel_kind kind = RS_LAPLACE;
@@ -130,6 +135,9 @@ struct rs_op {
     // solve workspace (grown on demand)
     rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_in, s_out, s_out2;
     int64_t s_nrhs = 0;
+    // FP64 direct-sum residual (built on first use): offset table, diagonal, permutation,
+    // and refinement workspace
+    rs::DevMem d_ktab, d_diag, d_ing, r_xg, r_yg, r_res, r_dx, r_x, r_norm;
     rs_stats stats{};
     int inflight = 0;
     // profiling (opts.profile): pending event pairs and per-class sums

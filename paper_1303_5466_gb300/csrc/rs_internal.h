@@ -15,10 +15,10 @@ void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
-#define RS_CUDA(call)                                     \
-    do {                                                  \
-        cudaError_t e__ = (call);                         \
-        if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+#define RS_CUDA(...)                                                 \
+    do {                                                             \
+        cudaError_t e__ = (__VA_ARGS__);                             \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #__VA_ARGS__); \
     } while (0)
 
 // Kernel launches made by the library (rs_launch_count).
@@ -64,71 +64,91 @@ struct LaplaceK {
     int n;
 };
 
+// All launchers below are instantiated for T = double (FP64 path) and T = float (the FP32
+// storage of the mixed-precision factor).
+
 // Y for every box of a level: rows = near points then P proxy points, columns = active
 // points, column-major r x m at y_off[b].
+template <class T>
 cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const int64_t* act_off,
                               const int32_t* near, const int64_t* near_off, const double* geo,
-                              const double* ucirc, int P, const int64_t* y_off, double* Y,
-                              LaplaceK K, int max_entries);
+                              const double* ucirc, int P, const int64_t* y_off, T* Y, LaplaceK K,
+                              int max_entries);
 
 // Column-pivoted QR (Eq. 2.1) of every box's Y, G CTAs per box (cooperative when G > 1).
-// Outputs: kout[b], piv[act_off[b] + s] = physical column of pivot s (s < k),
-// diag[act_off[b] + s] = R_ss.  Y is overwritten by the factorisation (rows < k hold R).
-cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off,
-                        const int32_t* nnear, int P, const int64_t* y_off, double* Y, double eps,
-                        int32_t* kout, int32_t* piv, double* diag, unsigned int* bar,
-                        unsigned long long* keys, int* status, long long spin_limit, int max_r,
+// Column norms and pivot choices are FP64 for every T.  Outputs: kout[b],
+// piv[act_off[b] + s] = physical column of pivot s (s < k), diag[act_off[b] + s] = R_ss.
+// Y is overwritten by the factorisation (rows < k hold R).
+template <class T>
+cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
+                        const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
+                        unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
                         int max_m);
-// Largest grid of cpqr_kernel that can be co-resident for these sizes.
+// Largest grid of the cpqr kernel that can be co-resident for these sizes.
+template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G);
-int gj_max_ctas(int max_m, int G);
 
 // T = R11^{-1} R12 for every box, written column-major (k x (m-k)) at t_off[b], rows by
 // sorted skeleton position (skpos[pivot position]) and columns by residual rank.
-cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const int32_t* kk,
-                        const int32_t* nnear, int P, const int64_t* y_off, const double* Y,
-                        const int32_t* piv, const double* diag, const int32_t* skpos,
-                        const int32_t* rscol, const int64_t* t_off, double* T, int max_cols,
+template <class T>
+cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const int32_t* kk, const int32_t* nnear,
+                        int P, const int64_t* y_off, const T* Y, const int32_t* piv, const T* diag,
+                        const int32_t* skpos, const int32_t* rscol, const int64_t* t_off, T* Tout, int max_cols,
                         int max_k);
 
 // F' = Pi^T F Pi for every box (sk-first order given by perm), column-major m x m at
 // phi_off[b].  Leaf: kernel entries with diagonal a_g + self.  Non-leaf: E of the
 // children on the diagonal blocks, kernel entries elsewhere.
-cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act,
-                              const int64_t* act_off, const int32_t* perm, const double* a,
-                              const int64_t* phi_off, double* Phi, const int32_t* child_k,
-                              const int64_t* child_e_off, const double* childE, LaplaceK K,
+template <class T>
+cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act, const int64_t* act_off,
+                              const int32_t* perm, const double* a, const int64_t* phi_off, T* Phi,
+                              const int32_t* child_k, const int64_t* child_e_off, const T* childE, LaplaceK K,
                               int max_m);
 
 // In-place blocked Gauss-Jordan inverse with partial pivoting of nb column-major matrices
 // (sizes m[b], offsets off[b]), G CTAs per matrix (cooperative when G > 1).  ipiv: one int
 // per row (ipiv_off[b]); pivbuf: 2 * gj_panel_width() ints per matrix; bar: one counter per
 // matrix, zeroed before the launch.
-cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off,
-                              double* A, int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf,
-                              unsigned int* bar, int* status, long long spin_limit, int max_m);
+template <class T>
+cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A,
+                              int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf, unsigned int* bar, int* status,
+                              long long spin_limit, int max_m);
+template <class T>
+int gj_max_ctas(int max_m, int G);
 int gj_panel_width();
 
 // Grouped GEMM over `np` problems (device descriptors), total tiles `tiles`.
-cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const double* A,
-                        const double* B, double* C, const double* C0);
+template <class T>
+cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const T* A, const T* B, T* C,
+                        const T* C0);
 
 // Batched matvec(s) over `np` problems, blocks = sum over problems of ceil(out_rows / 64).
-cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np,
-                          int64_t blocks, const double* A, const double* x, double* y, int nrhs);
+template <class T>
+cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np, int64_t blocks,
+                          const T* A, const T* x, T* y, int nrhs);
 
-// Copy rows: dst[dst_off[b] + i * ldd + j] = src[src_off[b] + i * lds + j] style gathers
-// used by the solve: out[p * nrhs + c] = in[idx[p] * nrhs + c] for p < count.
-cudaError_t launch_gather_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
-                               double* out, int nrhs);
-cudaError_t launch_scatter_rows(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
-                                double* out, int nrhs);
-// Column-major N x nrhs (input order) <-> point-major rows at idx.
-cudaError_t launch_gather_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
-                             int64_t N, double* out, int nrhs);
-cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx, const double* in,
-                              int64_t N, double* out, int nrhs);
+// Point-major row gathers/scatters of the solve: out[p * nrhs + c] = in[idx[p] * nrhs + c]
+// (gather) and the reverse (scatter), for p < count.
+template <class T>
+cudaError_t launch_gather_rows(cudaStream_t st, int64_t count, const int64_t* idx, const T* in, T* out, int nrhs);
+template <class T>
+cudaError_t launch_scatter_rows(cudaStream_t st, int64_t count, const int64_t* idx, const T* in, T* out, int nrhs);
+// Column-major N x nrhs FP64 (input order) <-> point-major rows of type T at idx.
+template <class Ti, class To>
+cudaError_t launch_gather_cm(cudaStream_t st, int64_t count, const int64_t* idx, const Ti* in, int64_t N, To* out,
+                             int nrhs);
+template <class Ti, class To>
+cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx, const Ti* in, int64_t N, To* out,
+                              int nrhs);
 // y[i] = a * x[i] + b * y[i]
-cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y);
+template <class T>
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y);
+
+// FP64 direct-sum residual (k_residual.cu): Kt is the (2n-1)^2 offset table of the Laplace
+// kernel; r = f - A x with x, f, r N x nrhs column-major in input order (ing[g] = input index
+// of grid point g), xg, yg grid-order scratch, norms[2c] = |r_c|^2, norms[2c+1] = |f_c|^2.
+cudaError_t launch_laplace_table(cudaStream_t st, int n, double h, double c0, double* Kt);
+cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const double* Kt, const double* dg, const int64_t* ing,
+                            const double* x, const double* f, double* xg, double* yg, double* r, double* norms);
 
 }  // namespace rs

@@ -49,7 +49,8 @@ extern "C" int rs_solve_noalloc(rs_op* op, const void* f, int64_t nrhs, void* x,
 {
     if (!op || !f || !x || nrhs < 1) return fail(RS_E_INVALID, "bad argument");
     if (f == x) return fail(RS_E_INVALID, "x may not alias f");
-    if (op->kind != RS_LAPLACE) return fail(RS_E_INVALID, "only the real (Laplace) operator is supported");
+    if (op->kind != RS_LAPLACE || op->opts.precision != RS_FP64)
+        return fail(RS_E_INVALID, "rs_solve_noalloc covers real FP64 (RS_FP64 Laplace) operators");
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
@@ -64,12 +65,13 @@ extern "C" int rs_solve_noalloc(rs_op* op, const void* f, int64_t nrhs, void* x,
     double* base = nullptr;
     int rc = scratch_address(dev, &base);
     if (rc) return rc;
-    SolveWork ws;
-    ws.w = base;
-    ws.g = ws.w + Ls.n_w;
-    ws.phi = ws.g + Ls.n_g;
-    ws.u = ws.phi + Ls.n_g;
-    ws.out = ws.u + Ls.n_u;
-    ws.t = ws.out + Ls.n_u;
+    // FP64 operator: workspace counts are in doubles
+    double* w = base;
+    double* g = w + Ls.n_w;
+    double* phi = g + Ls.n_g;
+    double* u = phi + Ls.n_g;
+    double* out = u + Ls.n_u;
+    double* t = out + Ls.n_u;
+    SolveWork ws{w, g, phi, u, out, t};
     return solve_run(op, Ls, ws, (const double*)f, (double*)x, nrhs, (cudaStream_t)stream, false);
 }
