@@ -53,6 +53,7 @@ typedef enum { RS_FP64 = 0, RS_MIXED_FP32 = 1, RS_C64_REFINED = 2, RS_C128 = 3 }
 
 typedef struct rs_tree rs_tree;
 typedef struct rs_op rs_op;
+typedef struct rs_server rs_server;
 
 /* Kernel of the integral operator.  b: host, N values of b(x) in input order, or NULL
  * (b = 1); must be > 0 everywhere for RS_HELMHOLTZ (the symmetric form divides by it). */
@@ -116,7 +117,9 @@ int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, dou
  * staged through device memory inside the call).  x may not alias f.  The call returns
  * after x is written (host) or after the work is enqueued on `stream` (device). */
 int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
-void rs_free(rs_op* op);
+/* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of
+ * its requests) still references it; NULL is accepted. */
+int rs_free(rs_op* op);
 
 /* Relative residuals |f_c - A x_c| / |f_c| of nrhs columns by an FP64 direct sum over all N^2
  * pairs (Laplace operators; the off-diagonal entries are tabulated over the (2n-1)^2 integer
@@ -201,6 +204,37 @@ int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out
 /* Root inverse F_root^{-1} (root_m x root_m, active order = skeletons of boxes (1,0) then
  * (1,1)), row-major. */
 int rs_op_root_matrix(const rs_op* op, double* out);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: continuous batching of inverse applies over resident FP64 factorizations.  (The
+ * paper notes that several right-hand sides vectorise, Sec. 5.1.3; the server extends that
+ * to requests of different operators and sizes arriving over time.)
+ * A scheduler thread admits requests in arrival order while fewer than max_inflight are in
+ * flight and their solve workspace fits the device-memory budget, then advances every
+ * in-flight request by one tree level per tick; each stage of a tick is one launch for all
+ * requests in that phase, whatever their operator or nrhs.  A finished request frees its
+ * memory at once and waiting requests join at the next tick.  Results equal rs_solve's.
+ *   ops: RS_FP64 Laplace operators on one device; they stay owned by the caller but cannot be
+ *   freed (rs_free returns RS_E_INVALID) until rs_server_free.
+ *   mem_budget_bytes: device memory reserved for request workspace (allocated once).
+ * --------------------------------------------------------------------------------------- */
+int rs_server_create(rs_op* const* ops, int n_ops, size_t mem_budget_bytes, int max_inflight, rs_server** out);
+/* Queue x = A_op^{-1} f.  f, x: device, N_op x nrhs column-major in the operator's input
+ * order; caller-owned and untouched by the caller until the ticket completes.  Returns a
+ * ticket; RS_E_NOMEM if the request could never fit the budget. */
+int rs_server_submit(rs_server* s, int op_index, const void* f, int64_t nrhs, void* x, uint64_t* ticket);
+/* Non-blocking: up to max completed tickets (completion order) into done_tickets. */
+int rs_server_poll(rs_server* s, uint64_t* done_tickets, int max, int* n_done);
+/* Block until every submitted request completed (RS_E_TIMEOUT after timeout_s seconds). */
+int rs_server_drain(rs_server* s, double timeout_s);
+/* Counters since creation (any output may be NULL). */
+int rs_server_stats(rs_server* s, int64_t* submitted, int64_t* completed, int64_t* rhs_completed, int64_t* ticks,
+                    int64_t* peak_inflight);
+/* Latencies (ms, submission to observed completion) of completed requests in completion
+ * order: up to max values into out_ms, the total count into *n. */
+int rs_server_latencies(rs_server* s, double* out_ms, int64_t max, int64_t* n);
+/* Finish the queued work, stop the scheduler and release the server. */
+void rs_server_free(rs_server* s);
 
 #ifdef __cplusplus
 }

@@ -71,7 +71,14 @@ def lib():
         L.rs_factor.argtypes = [vp, C.POINTER(rs_kernel), dp, C.c_double, C.POINTER(rs_opts), vp, C.POINTER(vp)]
         L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_free.argtypes = [vp]
-        L.rs_free.restype = None
+        L.rs_server_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t, C.c_int, C.POINTER(vp)]
+        L.rs_server_submit.argtypes = [vp, C.c_int, vp, C.c_int64, vp, C.POINTER(C.c_uint64)]
+        L.rs_server_poll.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_int)]
+        L.rs_server_drain.argtypes = [vp, C.c_double]
+        L.rs_server_stats.argtypes = [vp, i64p, i64p, i64p, i64p, i64p]
+        L.rs_server_latencies.argtypes = [vp, dp, C.c_int64, i64p]
+        L.rs_server_free.argtypes = [vp]
+        L.rs_server_free.restype = None
         L.rs_solve_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_residual.argtypes = [vp, vp, vp, C.c_int64, dp, vp]
         L.rs_op_stats.argtypes = [vp, C.POINTER(rs_stats)]
@@ -187,7 +194,50 @@ def rs_residual(op, x, f, nrhs, stream=None):
 
 
 def rs_free(op):
-    lib().rs_free(op)
+    _check(lib().rs_free(op))
+
+
+def rs_server_create(ops, mem_budget_bytes, max_inflight=64):
+    arr = (C.c_void_p * len(ops))(*[o.value if hasattr(o, "value") else o for o in ops])
+    out = C.c_void_p()
+    _check(lib().rs_server_create(arr, len(ops), int(mem_budget_bytes), int(max_inflight), C.byref(out)))
+    return out
+
+
+def rs_server_submit(server, op_index, f, nrhs, x):
+    """Queue x = A^{-1} f (device buffers, N x nrhs column-major); returns the ticket."""
+    t = C.c_uint64()
+    _check(lib().rs_server_submit(server, int(op_index), _ptr(f), int(nrhs), _ptr(x), C.byref(t)))
+    return t.value
+
+
+def rs_server_poll(server, max_tickets=1024):
+    buf = (C.c_uint64 * max_tickets)()
+    n = C.c_int()
+    _check(lib().rs_server_poll(server, buf, max_tickets, C.byref(n)))
+    return list(buf[: n.value])
+
+
+def rs_server_drain(server, timeout_s=600.0):
+    _check(lib().rs_server_drain(server, float(timeout_s)))
+
+
+def rs_server_stats(server):
+    v = [C.c_int64() for _ in range(5)]
+    _check(lib().rs_server_stats(server, *[C.byref(x) for x in v]))
+    return dict(zip(("submitted", "completed", "rhs_completed", "ticks", "peak_inflight"), [x.value for x in v]))
+
+
+def rs_server_latencies(server):
+    n = C.c_int64()
+    _check(lib().rs_server_latencies(server, None, 0, C.byref(n)))
+    out = np.zeros(max(n.value, 1))
+    _check(lib().rs_server_latencies(server, _dp(out), n.value, C.byref(n)))
+    return out[: n.value]
+
+
+def rs_server_free(server):
+    lib().rs_server_free(server)
 
 
 def rs_op_stats(op):

@@ -7,6 +7,7 @@
 #include <float.h>
 
 #include "k_common.cuh"
+#include "k_matvec.cuh"
 
 namespace rs {
 
@@ -307,82 +308,16 @@ cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t 
 }
 
 // ------------------------------------------------------------------ batched matvec(s)
-// Each CTA produces 64 output rows of one problem for all nrhs columns (chunks of 8).
 template <class T>
 __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restrict__ probs,
         const int64_t* __restrict__ blk0, int np, const T* __restrict__ Ab, const T* __restrict__ xb,
         T* __restrict__ yb, int nrhs)
 {
-    constexpr int RB = 64, CH = 8;
-    __shared__ T part[4][RB][CH];
+    __shared__ T part[4][64][8];
     const int64_t t = blockIdx.x;
-    int lo = 0, hi = np - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (blk0[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const MatvecProb P = probs[lo];
-    const int orow0 = (int)(t - blk0[lo]) * RB;
-    const T* A = Ab + P.a_off;
-    const T* x = xb + P.x_off * nrhs;
-    T* y = yb + P.y_off * nrhs;
-    const int out_n = P.trans ? P.cols : P.rows;
-    const int in_n = P.trans ? P.rows : P.cols;
-    for (int c0 = 0; c0 < nrhs; c0 += CH) {
-        const int nc = min(CH, nrhs - c0);
-        T acc[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) acc[c] = 0;
-        if (!P.trans) {
-            const int ri = threadIdx.x & 63, cj = threadIdx.x >> 6;   // 64 rows x 4 column phases
-            const int i = orow0 + ri;
-            if (i < out_n) {
-                for (int j = cj; j < in_n; j += 4) {
-                    const T a = A[(int64_t)j * P.ld + i];
-#pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        if (c < nc) acc[c] = fma(a, x[(int64_t)j * nrhs + c0 + c], acc[c]);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) part[cj][ri][c] = acc[c];
-            __syncthreads();
-            if (threadIdx.x < RB) {
-                const int i2 = orow0 + threadIdx.x;
-                if (i2 < out_n)
-                    for (int c = 0; c < nc; ++c) {
-                        const T s = part[0][threadIdx.x][c] + part[1][threadIdx.x][c] + part[2][threadIdx.x][c] +
-                                    part[3][threadIdx.x][c];
-                        T* yy = y + (int64_t)i2 * nrhs + c0 + c;
-                        *yy = (P.beta == 0.0) ? (T)P.alpha * s : (T)P.alpha * s + (T)P.beta * (*yy);
-                    }
-            }
-            __syncthreads();
-        } else {
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            for (int q = warp; q < RB; q += 8) {
-                const int j = orow0 + q;
-                if (j >= out_n) break;
-                T a2[CH];
-#pragma unroll
-                for (int c = 0; c < CH; ++c) a2[c] = 0;
-                const T* colj = A + (int64_t)j * P.ld;
-                for (int i = lane; i < in_n; i += 32) {
-                    const T a = colj[i];
-#pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        if (c < nc) a2[c] = fma(a, x[(int64_t)i * nrhs + c0 + c], a2[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < CH; ++c) a2[c] = warp_sum(a2[c]);
-                if (lane == 0)
-                    for (int c = 0; c < nc; ++c) {
-                        T* yy = y + (int64_t)j * nrhs + c0 + c;
-                        *yy = (P.beta == 0.0) ? (T)P.alpha * a2[c] : (T)P.alpha * a2[c] + (T)P.beta * (*yy);
-                    }
-            }
-        }
-    }
+    const int pi = find_block(blk0, np, t);
+    const MatvecProb P = probs[pi];
+    matvec_block<T>(P, (int)(t - blk0[pi]) * 64, Ab + P.a_off, xb + P.x_off * nrhs, yb + P.y_off * nrhs, nrhs, part);
 }
 
 template <class T>
@@ -444,7 +379,7 @@ template <class T>
 __global__ void axpby_kernel(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) y[e] = a * x[e] + b * y[e];
+    if (e < n) y[e] = fma(a, x[e], b * y[e]);
 }
 
 static unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }

@@ -734,7 +734,13 @@ int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream)
     return solve_impl(op, f, nrhs, x, (cudaStream_t)stream);
 }
 
-void rs_free(rs_op* op) { delete op; }
+int rs_free(rs_op* op)
+{
+    if (!op) return RS_OK;
+    if (op->inflight.load() > 0) return fail(RS_E_INVALID, "the operator is still referenced by a server");
+    delete op;
+    return RS_OK;
+}
 
 int rs_op_profile(const rs_op* op, int cls, double* ms, double* work, double* bytes, int64_t* launches)
 {

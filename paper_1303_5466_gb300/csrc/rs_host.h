@@ -2,6 +2,7 @@
 #pragma once
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "rs_internal.h"
@@ -139,7 +140,7 @@ struct rs_op {
     // and refinement workspace
     rs::DevMem d_ktab, d_diag, d_ing, r_xg, r_yg, r_res, r_dx, r_x, r_norm;
     rs_stats stats{};
-    int inflight = 0;
+    std::atomic<int> inflight{0};   // references held by servers and their requests
     // profiling (opts.profile): pending event pairs and per-class sums
     std::vector<rs::ProfRec> pending;
     std::vector<cudaEvent_t> ev_pool, ev_all;

@@ -144,6 +144,31 @@ cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx
 template <class T>
 cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y);
 
+// Serving job lists (k_serve.cu).  MvJob: one request's descriptor set of one stage
+// (blocks blk_start .. blk_start + nblk of the launch).  CopyJob: a gather, scatter or axpby
+// over elements e_start .. e_start + count * nrhs (axpby: count elements, nrhs 1).
+struct MvJob {
+    const MatvecProb* probs;
+    const int64_t* blk0;
+    int np, nrhs;
+    int64_t blk_start;
+    const double* A;
+    const double* x;
+    double* y;
+};
+enum { COPY_GATHER_ROWS = 0, COPY_SCATTER_ROWS = 1, COPY_GATHER_CM = 2, COPY_SCATTER_CM = 3, COPY_AXPBY = 4 };
+struct CopyJob {
+    int64_t e_start;
+    int mode, nrhs;
+    int64_t count, N;
+    const int64_t* idx;
+    const double* in;
+    double* out;
+    double a, b;
+};
+cudaError_t launch_mv_jobs(cudaStream_t st, const MvJob* jobs, int nj, int64_t blocks);
+cudaError_t launch_copy_jobs(cudaStream_t st, const CopyJob* jobs, int nj, int64_t total);
+
 // FP64 direct-sum residual (k_residual.cu): Kt is the (2n-1)^2 offset table of the Laplace
 // kernel; r = f - A x with x, f, r N x nrhs column-major in input order (ing[g] = input index
 // of grid point g), xg, yg grid-order scratch, norms[2c] = |r_c|^2, norms[2c+1] = |f_c|^2.
