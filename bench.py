@@ -45,6 +45,9 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD, choices=["laplace_batched", "laplace_n256"],
                    help="laplace_n256 is a quarter-size copy for profiling runs")
+    p.add_argument("--serving-requests", type=int, default=150,
+                   help="requests of the serving stream measured after the main step (0 = skip)")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return p.parse_args()
 
 
@@ -153,6 +156,96 @@ def oracle_sample(n, leaf, eps, a):
             "sample": "oracle factor of the %d finest levels of the %dx%d workload took %.2f s on %d threads; "
                       "those levels are %.1f%% of the factor flops, scaled to the full factor (%.1f s)"
                       % (ORACLE_LEVELS, n, n, dt, cores, 100 * share, est)}
+
+
+SERVING_OPS = ((128, 16), (256, 16), (512, 16))
+
+
+def serving_measure(P, torch, requests, seed=3, load=0.7):
+    """Serving workload: three resident FP64 operators (128^2, 256^2, 512^2 grids, leaves 16^2,
+    eps 1e-10); a seeded stream of requests, each naming an operator uniformly and carrying
+    1-64 RHS ~ N(0,1), arriving as a Poisson process at `load` x the closed-loop capacity
+    measured on a first burst.  Returns p50/p99 latency (submission to completion) and RHS/s."""
+    import numpy as np
+    ops, trees = [], []
+    for n, leaf in SERVING_OPS:
+        t = P.rs_build_tree(W.grid_points(n), leaf)
+        trees.append(t)
+        ops.append(P.rs_factor(t, eps=1e-10))
+    rng = np.random.default_rng(seed)
+    kinds = rng.integers(0, len(SERVING_OPS), requests)
+    nrhs = rng.integers(1, 65, requests)
+    gaps = rng.exponential(1.0, requests)          # scaled by 1/lambda below
+    bufs = []
+    for k, r in zip(kinds, nrhs):
+        n = SERVING_OPS[k][0]
+        F = torch.from_numpy(rng.standard_normal((int(r), n * n))).cuda()
+        bufs.append((F, torch.empty_like(F)))
+    torch.cuda.synchronize()
+    srv = P.rs_server_create(ops, 8 << 30, max_inflight=64)
+    try:
+        # closed loop on the first burst: everything submitted at once
+        burst = min(32, requests)
+        t0 = time.perf_counter()
+        for i in range(burst):
+            P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
+        P.rs_server_drain(srv, 3600.0)
+        cap = burst / (time.perf_counter() - t0)     # requests per second
+        lam = load * cap
+        P.rs_server_latencies(srv)
+        n0 = P.rs_server_stats(srv)["completed"]
+        # open loop: Poisson arrivals at lam
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(burst, requests):
+            t_next += gaps[i] / lam
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
+        P.rs_server_drain(srv, 3600.0)
+        wall = time.perf_counter() - t0
+        lat = P.rs_server_latencies(srv)[n0:]
+        st = P.rs_server_stats(srv)
+        rhs = int(nrhs[burst:].sum())
+        return {"requests": int(requests - burst), "burst_requests": int(burst), "load": load,
+                "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "rhs_per_s": rhs / wall, "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
+                "operators": "%s grids, leaf 16, eps 1e-10, FP64" % ", ".join("%d^2" % n for n, _ in SERVING_OPS),
+                "stream": "seed 3: operator uniform, nrhs uniform 1-64, N(0,1) columns, Exp inter-arrivals"}
+    finally:
+        P.rs_server_free(srv)
+        for o in ops:
+            P.rs_free(o)
+        for t in trees:
+            P.rs_free_tree(t)
+
+
+def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
+    """The same workload with the FP32 factor at eps 1e-6 and FP64-residual refinement to
+    1e-10: factor time, refined solve time, solves made and the final residual."""
+    import numpy as np
+    o = P.rs_opts_default()
+    o.precision = P.RS_MIXED_FP32
+    o.refine_tol = 1e-10
+    f = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    x = torch.empty_like(f)
+    tree = P.rs_build_tree(pts, leaf)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(st)
+    op = P.rs_factor(tree, a=a, eps=1e-6, opts=o, stream=st)
+    e1.record(st)
+    P.rs_solve(op, f, nrhs, x, st)
+    e2.record(st)
+    e2.synchronize()
+    s = P.rs_op_stats(op)
+    rel = P.rs_residual(op, x, f, nrhs, st)
+    out = {"factor_ms": e0.elapsed_time(e1), "refined_solve_ms": e1.elapsed_time(e2), "eps": 1e-6,
+           "refine_solves": s["refine_iters"], "residual": float(rel.max()), "bytes_factors": s["bytes_factors"]}
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+    return out
 
 
 def run_ours(args):
@@ -271,6 +364,18 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    # FP64 residual of the timed solve (direct sum over all pairs)
+    tree, op = step()
+    P.rs_solve(op, f_dev, nrhs, x_dev, st)
+    out["residual_fp64"] = float(P.rs_residual(op, x_dev, f_dev, nrhs, st).max())
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+    if not args.no_mixed:
+        mx = mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st)
+        mx["step_speedup_vs_fp64"] = (factor_ms + solve_ms) / (mx["factor_ms"] + mx["refined_solve_ms"])
+        out["mixed"] = mx
+    if args.serving_requests > 0:
+        out["serving"] = serving_measure(P, torch, args.serving_requests)
     if not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = oracle_sample(n, leaf, eps, a)
     print(json.dumps(out))
