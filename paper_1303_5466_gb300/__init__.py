@@ -150,9 +150,15 @@ def rs_tree_level_sets(tree, level, child_k=None, child_skel=None, proxy_radius_
     return m, act[: int(m.sum())], nn, near[: int(nn.sum())]
 
 
-def rs_factor(tree, kernel=None, a=None, eps=1e-10, opts=None, stream=None):
-    """Factor the operator; `kernel` is an rs_kernel or None (Laplace).  Returns the op handle."""
-    k = kernel if kernel is not None else rs_kernel(RS_LAPLACE, 0.0, None)
+def rs_factor(tree, kernel=None, a=None, eps=1e-10, opts=None, stream=None, kappa=None, b=None):
+    """Factor the operator.  Laplace by default; pass kappa (and b, N values in input order) for
+    the Helmholtz kernel, or a ready rs_kernel as `kernel`.  Returns the op handle."""
+    bv = None
+    if kappa is not None:
+        bv = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        k = rs_kernel(RS_HELMHOLTZ, float(kappa), _dp(bv))
+    else:
+        k = kernel if kernel is not None else rs_kernel(RS_LAPLACE, 0.0, None)
     av = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
     o = opts if opts is not None else rs_opts_default()
     out = C.c_void_p()
@@ -274,29 +280,34 @@ def rs_op_box_indices(op, level, box, which):
     return out[:cnt]
 
 
-def rs_op_box_matrix(op, level, box, which):
+def rs_op_box_matrix(op, level, box, which, cplx=False):
+    """T (which 0), F^{-1} (1) or E (2) of one box; complex operators need cplx=True."""
     m, k, _, _ = rs_op_box_sizes(op, level, box)
     shape = ((k, m - k), (m, m), (k, k))[which]
-    out = np.zeros(max(shape[0] * shape[1], 1))
+    c = 2 if cplx else 1
+    out = np.zeros(max(c * shape[0] * shape[1], 2))
     _check(lib().rs_op_box_matrix(op, level, box, which, _dp(out)))
-    return out[: shape[0] * shape[1]].reshape(shape)
+    out = out[: c * shape[0] * shape[1]]
+    return (out.view(np.complex128) if cplx else out).reshape(shape)
 
 
-def rs_op_root_matrix(op):
+def rs_op_root_matrix(op, cplx=False):
     m = rs_op_stats(op)["root_m"]
-    out = np.zeros(m * m)
+    c = 2 if cplx else 1
+    out = np.zeros(c * m * m)
     _check(lib().rs_op_root_matrix(op, _dp(out)))
-    return out.reshape(m, m)
+    return (out.view(np.complex128) if cplx else out).reshape(m, m)
 
 
 class Solver:
     """Convenience owner of a tree and its factorization (frees both on deletion)."""
 
-    def __init__(self, points, leaf_side, a=None, eps=1e-10, kernel=None, opts=None, stream=None):
+    def __init__(self, points, leaf_side, a=None, eps=1e-10, kernel=None, opts=None, stream=None, kappa=None, b=None):
         self.N = int(np.asarray(points).shape[0])
+        self.complex = kappa is not None
         self.tree = rs_build_tree(points, leaf_side)
         self.op = None
-        self.op = rs_factor(self.tree, kernel=kernel, a=a, eps=eps, opts=opts, stream=stream)
+        self.op = rs_factor(self.tree, kernel=kernel, a=a, eps=eps, opts=opts, stream=stream, kappa=kappa, b=b)
 
     def solve(self, f, stream=None):
         """f: numpy (N,) / (N, nrhs), or torch CUDA (N,) / (nrhs, N).  Returns x of the same kind."""
@@ -307,7 +318,7 @@ class Solver:
             x = torch.empty_like(fc)
             rs_solve(self.op, fc, nrhs, x, stream if stream is not None else torch.cuda.current_stream())
             return x
-        fa = np.asarray(f, dtype=np.float64)
+        fa = np.asarray(f, dtype=np.complex128 if self.complex else np.float64)
         nrhs = 1 if fa.ndim == 1 else fa.shape[1]
         fa = np.asfortranarray(fa)
         x = np.zeros_like(fa, order="F")

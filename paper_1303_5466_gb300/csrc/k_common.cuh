@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "k_scalar.cuh"
 #include "rs_internal.h"
 
 namespace rs {
@@ -18,7 +19,7 @@ template <class T>
 __device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor_(v, o);
     return v;
 }
 

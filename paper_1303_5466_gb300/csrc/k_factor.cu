@@ -8,48 +8,81 @@
 
 namespace rs {
 
-__device__ __forceinline__ void grid_xy(const LaplaceK& K, int g, double& x, double& y)
+__device__ __forceinline__ void grid_xy(const KernelK& K, int g, double& x, double& y)
 {
     const int i1 = g % K.n, i2 = g / K.n;
     x = ((double)i1 + 0.5) * K.h;
     y = ((double)i2 + 0.5) * K.h;
 }
 
-// Off-diagonal Laplace entry -(1/2pi) h^2 log|x - y| = c0 log(|x - y|^2), c0 = -h^2/(4pi),
-// evaluated in the storage precision T (FP32 arithmetic for the mixed-precision factor).
-template <class T>
-__device__ __forceinline__ T lap_entry(const LaplaceK& K, int g, int gp);
-
-template <>
-__device__ __forceinline__ double lap_entry<double>(const LaplaceK& K, int g, int gp)
+// Matrix entries in the storage type S (the arithmetic of the factor's precision).
+//   Laplace (real S): off-diagonal -(1/2pi) h^2 log|x - y| = c0 log(|x - y|^2);
+//   Helmholtz (complex S): s_g (i/4) H0^(1)(kappa r) h^2 s_g' with H0^(1) = J0 + i Y0.
+template <class S>
+__device__ __forceinline__ S hank_row(const KernelK& K, double r)
 {
-    double x, y, xp, yp;
-    grid_xy(K, g, x, y);
-    grid_xy(K, gp, xp, yp);
-    const double dx = x - xp, dy = y - yp;
-    return K.c0 * log(dx * dx + dy * dy);
+    // (i/4) H0^(1)(kappa r) h^2 = (h^2/4) (-Y0 + i J0)
+    using R = typename sc_traits<S>::real;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const float z = (float)(K.kappa * r);
+        const float q = (float)(0.25 * K.h * K.h);
+        return S(-q * y0f(z), q * j0f(z));
+    } else {
+        const double z = K.kappa * r;
+        const double q = 0.25 * K.h * K.h;
+        return S(-q * y0(z), q * j0(z));
+    }
 }
 
-template <>
-__device__ __forceinline__ float lap_entry<float>(const LaplaceK& K, int g, int gp)
+template <class S>
+__device__ __forceinline__ S kentry(const KernelK& K, int g, int gp)
 {
-    const int d1 = g % K.n - gp % K.n, d2 = g / K.n - gp / K.n;
-    const float hf = (float)K.h;
-    const float dx = (float)d1 * hf, dy = (float)d2 * hf;
-    return (float)K.c0 * logf(dx * dx + dy * dy);
+    if constexpr (is_cplx<S>::value) {
+        double x, y, xp, yp;
+        grid_xy(K, g, x, y);
+        grid_xy(K, gp, xp, yp);
+        const double dx = x - xp, dy = y - yp;
+        return rscale<S>(K.s[g] * K.s[gp], hank_row<S>(K, sqrt(dx * dx + dy * dy)));
+    } else if constexpr (sizeof(S) == sizeof(float)) {
+        const int d1 = g % K.n - gp % K.n, d2 = g / K.n - gp / K.n;
+        const float hf = (float)K.h;
+        const float dx = (float)d1 * hf, dy = (float)d2 * hf;
+        return (float)K.c0 * logf(dx * dx + dy * dy);
+    } else {
+        double x, y, xp, yp;
+        grid_xy(K, g, x, y);
+        grid_xy(K, gp, xp, yp);
+        const double dx = x - xp, dy = y - yp;
+        return K.c0 * log(dx * dx + dy * dy);
+    }
 }
 
-template <class T>
-__device__ __forceinline__ T proxy_entry(const LaplaceK& K, double zx, double zy, int g)
+template <class S>
+__device__ __forceinline__ S kdiag(const KernelK& K, const double* a, int g)
+{
+    if constexpr (is_cplx<S>::value) {
+        const double s2 = K.s[g] * K.s[g];
+        return S(a[g] + s2 * K.hs_re, s2 * K.hs_im);
+    } else {
+        return S(a[g] + K.self);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ S kproxy(const KernelK& K, double zx, double zy, int g)
 {
     double x, y;
     grid_xy(K, g, x, y);
-    if (sizeof(T) == sizeof(float)) {
+    if constexpr (is_cplx<S>::value) {
+        const double dx = zx - x, dy = zy - y;
+        return rscale<S>(K.s[g], hank_row<S>(K, sqrt(dx * dx + dy * dy)));
+    } else if constexpr (sizeof(S) == sizeof(float)) {
         const float dx = (float)(zx - x), dy = (float)(zy - y);
-        return (T)((float)K.c0 * logf(dx * dx + dy * dy));
+        return (float)K.c0 * logf(dx * dx + dy * dy);
+    } else {
+        const double dx = zx - x, dy = zy - y;
+        return K.c0 * log(dx * dx + dy * dy);
     }
-    const double dx = zx - x, dy = zy - y;
-    return (T)(K.c0 * log(dx * dx + dy * dy));
 }
 
 // ------------------------------------------------------------------ Y assembly
@@ -58,7 +91,7 @@ __global__ void __launch_bounds__(256) assemble_Y_kernel(const int32_t* __restri
         const int64_t* __restrict__ act_off, const int32_t* __restrict__ near,
         const int64_t* __restrict__ near_off, const double* __restrict__ geo,
         const double* __restrict__ ucirc, int P, const int64_t* __restrict__ y_off,
-        T* __restrict__ Y, LaplaceK K)
+        T* __restrict__ Y, KernelK K)
 {
     const int b = blockIdx.y;
     const int64_t a0 = act_off[b];
@@ -72,11 +105,11 @@ __global__ void __launch_bounds__(256) assemble_Y_kernel(const int32_t* __restri
     const int g = act[a0 + j];
     T v;
     if (i < nn) {
-        v = lap_entry<T>(K, near[n0 + i], g);
+        v = kentry<T>(K, near[n0 + i], g);
     } else {
         const int q = i - nn;
         const double cx = geo[3 * b], cy = geo[3 * b + 1], R = geo[3 * b + 2];
-        v = proxy_entry<T>(K, cx + R * ucirc[q], cy + R * ucirc[P + q], g);
+        v = kproxy<T>(K, cx + R * ucirc[q], cy + R * ucirc[P + q], g);
     }
     Y[y_off[b] + e] = v;
 }
@@ -84,7 +117,7 @@ __global__ void __launch_bounds__(256) assemble_Y_kernel(const int32_t* __restri
 template <class T>
 cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const int64_t* act_off,
                               const int32_t* near, const int64_t* near_off, const double* geo,
-                              const double* ucirc, int P, const int64_t* y_off, T* Y, LaplaceK K,
+                              const double* ucirc, int P, const int64_t* y_off, T* Y, KernelK K,
                               int max_entries)
 {
     if (nb <= 0 || max_entries <= 0) return cudaSuccess;
@@ -136,7 +169,7 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     for (int jj = warp; jj < nown; jj += NW) {
         const T* col = Y + (int64_t)(c0 + jj) * r;
         double s = 0.0;
-        for (int i = lane; i < r; i += 32) { const double x = (double)col[i]; s += x * x; }
+        for (int i = lane; i < r; i += 32) s += abs2d(col[i]);
         s = warp_sum(s);
         if (lane == 0) { nrm[jj] = s; ref[jj] = s; sel[jj] = 0; }
     }
@@ -171,21 +204,27 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
         const T* colp = Y + (int64_t)p * r;
         double part = 0.0;
         for (int i = s + threadIdx.x; i < r; i += NT) {
-            const T x = __ldcg(colp + i);
+            const T x = ldcg_(colp + i);
             v[i] = x;
-            part += (double)x * (double)x;
+            part += abs2d(x);
         }
         const double a2 = block_sum<NT>(part, dred);
         const double alpha = sqrt(a2);
         if (s == 0) alpha0 = alpha;
         if (!(alpha > eps * alpha0)) break;
-        const double x0 = (double)v[s];
-        const double beta = (x0 < 0.0) ? alpha : -alpha;
-        const T tau = (T)(1.0 / (alpha * (alpha + fabs(x0))));   // 2 / ||v||^2
+        using R = typename sc_traits<T>::real;
+        const T x0 = v[s];
+        const double ax0 = absd(x0);
+        // beta = -(x0 / |x0|) alpha (the sign of x0 for real data), so that v_s = x0 - beta
+        // does not cancel
+        T beta;
+        if constexpr (is_cplx<T>::value) beta = (ax0 > 0.0) ? rscale<T>(-alpha / ax0, x0) : T(R(-alpha));
+        else beta = (T)(((double)x0 < 0.0) ? alpha : -alpha);
+        const R tau = (R)(1.0 / (alpha * (alpha + ax0)));   // 2 / ||v||^2
         __syncthreads();
         if (threadIdx.x == 0) {
-            v[s] = (T)(x0 - beta);
-            if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = (T)beta; }
+            v[s] = x0 - beta;
+            if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
         }
         if (threadIdx.x == 0 && p >= c0 && p < c1) sel[p - c0] = 1;
         __syncthreads();
@@ -193,20 +232,20 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             if (sel[jj]) continue;
             T* col = Y + (int64_t)(c0 + jj) * r;
             T w = 0;
-            for (int i = s + lane; i < r; i += 32) w += v[i] * col[i];
+            for (int i = s + lane; i < r; i += 32) w = fma_(conj_(v[i]), col[i], w);
             w = warp_sum(w);
             const T tw = tau * w;
             T rsj = 0;
             for (int i = s + lane; i < r; i += 32) {
-                const T u = col[i] - v[i] * tw;
+                const T u = fma_(-v[i], tw, col[i]);
                 col[i] = u;
                 if (i == s) rsj = u;
             }
-            rsj = __shfl_sync(0xffffffffu, rsj, 0);
-            double nv = nrm[jj] - (double)rsj * (double)rsj;
+            rsj = shfl_(rsj, 0);
+            double nv = nrm[jj] - abs2d(rsj);
             if (nv < 1e-4 * ref[jj]) {
                 double q = 0.0;
-                for (int i = s + 1 + lane; i < r; i += 32) { const double x = (double)col[i]; q += x * x; }
+                for (int i = s + 1 + lane; i < r; i += 32) q += abs2d(col[i]);
                 q = warp_sum(q);
                 nv = q;
                 if (lane == 0) ref[jj] = q;
@@ -304,7 +343,7 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
             const T R = Ra[i];
 #pragma unroll
             for (int q = 0; q < NC; ++q)
-                if (q < nc) ys[q * k + i] -= t[q] * R;
+                if (q < nc) ys[q * k + i] = fma_(-t[q], R, ys[q * k + i]);
         }
     }
 }
@@ -332,7 +371,7 @@ template <class T>
 __global__ void __launch_bounds__(256) assemble_F_kernel(int leaf, const int32_t* __restrict__ act,
         const int64_t* __restrict__ act_off, const int32_t* __restrict__ perm, const double* __restrict__ a,
         const int64_t* __restrict__ phi_off, T* __restrict__ Phi, const int32_t* __restrict__ child_k,
-        const int64_t* __restrict__ child_e_off, const T* __restrict__ childE, LaplaceK K)
+        const int64_t* __restrict__ child_e_off, const T* __restrict__ childE, KernelK K)
 {
     const int b = blockIdx.y;
     const int64_t a0 = act_off[b];
@@ -344,12 +383,12 @@ __global__ void __launch_bounds__(256) assemble_F_kernel(int leaf, const int32_t
     const int gi = act[a0 + i], gj = act[a0 + j];
     T v;
     if (leaf) {
-        v = (i == j) ? (T)(a[gi] + K.self) : lap_entry<T>(K, gi, gj);
+        v = (i == j) ? kdiag<T>(K, a, gi) : kentry<T>(K, gi, gj);
     } else {
         const int k1 = child_k[2 * b], k2 = child_k[2 * b + 1];
         if (i < k1 && j < k1) v = childE[child_e_off[2 * b] + (int64_t)j * k1 + i];
         else if (i >= k1 && j >= k1) v = childE[child_e_off[2 * b + 1] + (int64_t)(j - k1) * k2 + (i - k1)];
-        else v = lap_entry<T>(K, gi, gj);
+        else v = kentry<T>(K, gi, gj);
     }
     Phi[phi_off[b] + e] = v;
 }
@@ -357,7 +396,7 @@ __global__ void __launch_bounds__(256) assemble_F_kernel(int leaf, const int32_t
 template <class T>
 cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act, const int64_t* act_off,
                               const int32_t* perm, const double* a, const int64_t* phi_off, T* Phi,
-                              const int32_t* child_k, const int64_t* child_e_off, const T* childE, LaplaceK K,
+                              const int32_t* child_k, const int64_t* child_e_off, const T* childE, KernelK K,
                               int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
@@ -372,7 +411,7 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
 #define RS_INST_FACTOR(T)                                                                                              \
     template cudaError_t launch_assemble_Y<T>(cudaStream_t, int, const int32_t*, const int64_t*, const int32_t*,     \
                                               const int64_t*, const double*, const double*, int, const int64_t*, T*, \
-                                              LaplaceK, int);                                                        \
+                                              KernelK, int);                                                        \
     template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int64_t*, const int32_t*, int, const int64_t*, \
                                         T*, double, int32_t*, int32_t*, T*, unsigned int*, unsigned long long*,     \
                                         int*, long long, int, int);                                                 \
@@ -382,8 +421,10 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
                                         const int32_t*, const int64_t*, T*, int, int);                              \
     template cudaError_t launch_assemble_F<T>(cudaStream_t, int, bool, const int32_t*, const int64_t*,              \
                                               const int32_t*, const double*, const int64_t*, T*, const int32_t*,     \
-                                              const int64_t*, const T*, LaplaceK, int);
+                                              const int64_t*, const T*, KernelK, int);
 RS_INST_FACTOR(double)
 RS_INST_FACTOR(float)
+RS_INST_FACTOR(cplx<double>)
+RS_INST_FACTOR(cplx<float>)
 
 }  // namespace rs

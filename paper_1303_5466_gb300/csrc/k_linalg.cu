@@ -31,17 +31,18 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
         int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
 {
     constexpr int CB = 32;                 // own columns updated per chunk
+    using W = typename sc_traits<T>::wide;      // FP64 panel arithmetic
     extern __shared__ double sm[];
     __shared__ double dred[NT / 32];
     __shared__ int ired[NT / 32];
     __shared__ int s_piv[NB];
-    __shared__ double s_row[NB];
+    __shared__ W s_row[NB];
     __shared__ T s_aK[NB][CB];
     __shared__ int s_col[CB];
     const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
     const int m = msz[b];
     T* __restrict__ A = Aall + off[b];
-    double* f = sm;                        // m: the current pivot column (panel step)
+    W* f = (W*)sm;                         // m: the current pivot column (panel step)
     int32_t* ip = ipiv + ipiv_off[b];
     int* pb = pivbuf + (int64_t)b * 2 * NB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 double best = -1.0;
                 int bi = m;
                 for (int i = c + threadIdx.x; i < m; i += NT) {
-                    const double a = fabs((double)col[i]);
+                    const double a = absd(col[i]);
                     if (a > best) { best = a; bi = i; }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
@@ -83,22 +84,23 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                     cj[p] = u;
                 }
                 __syncthreads();
-                for (int i = threadIdx.x; i < m; i += NT) f[i] = (double)col[i];
-                if (threadIdx.x < kw) s_row[threadIdx.x] = (double)A[(int64_t)(k0 + threadIdx.x) * m + c];
+                for (int i = threadIdx.x; i < m; i += NT) f[i] = cast_<W>(col[i]);
+                if (threadIdx.x < kw) s_row[threadIdx.x] = cast_<W>(A[(int64_t)(k0 + threadIdx.x) * m + c]);
                 __syncthreads();
-                const double pv = f[c];
-                if (threadIdx.x == 0 && (!(fabs(pv) > 1e3 * 0.5 * DBL_EPSILON * maxpiv) || !isfinite(pv)))
+                const W pv = f[c];
+                const double apv = absd(pv);
+                if (threadIdx.x == 0 && (!(apv > 1e3 * 0.5 * DBL_EPSILON * maxpiv) || !finite_(pv)))
                     atomicOr(status, DEV_SINGULAR);
-                maxpiv = fmax(maxpiv, fabs(pv));
-                const double pinv = (pv != 0.0) ? 1.0 / pv : 0.0;
+                maxpiv = fmax(maxpiv, apv);
+                const W pinv = (apv > 0.0) ? W(1.0) / pv : W(0.0);
                 for (int e = threadIdx.x; e < m * kw; e += NT) {
                     const int jj = e / m, i = e - jj * m;
                     T* cj = A + (int64_t)(k0 + jj) * m;
                     if (k0 + jj == c) {
-                        cj[i] = (T)((i == c) ? pinv : -f[i] * pinv);
+                        cj[i] = cast_<T>((i == c) ? pinv : -f[i] * pinv);
                     } else {
-                        const double aj = s_row[jj] * pinv;
-                        cj[i] = (T)((i == c) ? aj : fma(-f[i], aj, (double)cj[i]));
+                        const W aj = s_row[jj] * pinv;
+                        cj[i] = cast_<T>((i == c) ? aj : fma_(-f[i], aj, cast_<W>(cj[i])));
                     }
                 }
                 __syncthreads();
@@ -142,13 +144,13 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
             for (int i = threadIdx.x; i < m; i += NT) {
                 T P[NB];
 #pragma unroll
-                for (int t = 0; t < NB; ++t) P[t] = (t < kw) ? __ldcg(A + (int64_t)(k0 + t) * m + i) : (T)0;
+                for (int t = 0; t < NB; ++t) P[t] = (t < kw) ? ldcg_(A + (int64_t)(k0 + t) * m + i) : (T)0;
                 const bool inK = (i >= k0) && (i < k0 + kw);
                 for (int jj = 0; jj < nc; ++jj) {
                     T* cj = A + (int64_t)s_col[jj] * m;
                     T v = inK ? (T)0 : cj[i];
 #pragma unroll
-                    for (int t = 0; t < NB; ++t) v = fma(P[t], s_aK[t][jj], v);
+                    for (int t = 0; t < NB; ++t) v = fma_(P[t], s_aK[t][jj], v);
                     cj[i] = v;
                 }
             }
@@ -180,13 +182,14 @@ __global__ void __launch_bounds__(256) gj_unpivot_kernel(const int32_t* __restri
 
 constexpr int GJ_NT = 256, GJ_NB = 8;
 
-static size_t gj_shm(int max_m) { return sizeof(double) * (size_t)max_m + 64; }
+template <class T>
+static size_t gj_shm(int max_m) { return sizeof(typename sc_traits<T>::wide) * (size_t)max_m + 64; }
 
 template <class T>
 int gj_max_ctas(int max_m, int G)
 {
     (void)G;
-    const size_t shm = gj_shm(max_m);
+    const size_t shm = gj_shm<T>(max_m);
     cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -204,7 +207,7 @@ cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, 
                               long long spin_limit, int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
-    const size_t shm = gj_shm(max_m);
+    const size_t shm = gj_shm<T>(max_m);
     cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     if (G == 1) {
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmProb* __restrict__ 
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], bv[w], acc[u][w]);
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma_(a[u], bv[w], acc[u][w]);
         }
         __syncthreads();
     }
@@ -361,7 +364,7 @@ __global__ void gather_cm_kernel(int64_t count, const int64_t* __restrict__ idx,
     if (e >= count * nrhs) return;
     const int64_t p = e / nrhs;
     const int c = (int)(e - p * nrhs);
-    out[e] = (To)in[(int64_t)c * N + idx[p]];
+    out[e] = cast_<To>(in[(int64_t)c * N + idx[p]]);
 }
 
 template <class Ti, class To>
@@ -372,14 +375,14 @@ __global__ void scatter_cm_kernel(int64_t count, const int64_t* __restrict__ idx
     if (e >= count * nrhs) return;
     const int64_t p = e / nrhs;
     const int c = (int)(e - p * nrhs);
-    out[(int64_t)c * N + idx[p]] = (To)in[e];
+    out[(int64_t)c * N + idx[p]] = cast_<To>(in[e]);
 }
 
 template <class T>
 __global__ void axpby_kernel(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) y[e] = fma(a, x[e], b * y[e]);
+    if (e < n) y[e] = fma_(a, x[e], b * y[e]);
 }
 
 static unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -431,6 +434,29 @@ cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y)
     return cudaGetLastError();
 }
 
+// y[c N + i] = s[i]^pw x[c N + i] (pw = +1 or -1), real s, T real or complex
+template <class T>
+__global__ void scale_cm_kernel(int64_t N, int nrhs, const double* __restrict__ sc, int pw, const T* __restrict__ x,
+                                T* __restrict__ y)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * nrhs) return;
+    const int64_t i = e % N;
+    const double f = pw > 0 ? sc[i] : 1.0 / sc[i];
+    y[e] = rscale<T>(f, x[e]);
+}
+
+template <class T>
+cudaError_t launch_scale_cm(cudaStream_t st, int64_t N, int nrhs, const double* sc, int pw, const T* x, T* y)
+{
+    if (N <= 0 || nrhs <= 0) return cudaSuccess;
+    count_launches(1);
+    scale_cm_kernel<T><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, sc, pw, x, y);
+    return cudaGetLastError();
+}
+template cudaError_t launch_scale_cm<cplx<double>>(cudaStream_t, int64_t, int, const double*, int, const cplx<double>*,
+                                                   cplx<double>*);
+
 #define RS_INST_LINALG(T)                                                                                             \
     template int gj_max_ctas<T>(int, int);                                                                          \
     template cudaError_t launch_gj_inverse<T>(cudaStream_t, int, int, const int32_t*, const int64_t*, T*, int32_t*, \
@@ -441,12 +467,16 @@ cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y)
                                           const T*, T*, int);                                                       \
     template cudaError_t launch_gather_rows<T>(cudaStream_t, int64_t, const int64_t*, const T*, T*, int);           \
     template cudaError_t launch_scatter_rows<T>(cudaStream_t, int64_t, const int64_t*, const T*, T*, int);          \
-    template cudaError_t launch_gather_cm<double, T>(cudaStream_t, int64_t, const int64_t*, const double*, int64_t, \
-                                                     T*, int);                                                      \
-    template cudaError_t launch_scatter_cm<T, double>(cudaStream_t, int64_t, const int64_t*, const T*, int64_t,     \
-                                                      double*, int);                                                \
+    template cudaError_t launch_gather_cm<typename sc_traits<T>::io, T>(cudaStream_t, int64_t, const int64_t*,      \
+                                                                      const typename sc_traits<T>::io*, int64_t,  \
+                                                                      T*, int);                                   \
+    template cudaError_t launch_scatter_cm<T, typename sc_traits<T>::io>(cudaStream_t, int64_t, const int64_t*,     \
+                                                                       const T*, int64_t,                         \
+                                                                       typename sc_traits<T>::io*, int);          \
     template cudaError_t launch_axpby<T>(cudaStream_t, int64_t, T, const T*, T, T*);
 RS_INST_LINALG(double)
 RS_INST_LINALG(float)
+RS_INST_LINALG(cplx<double>)
+RS_INST_LINALG(cplx<float>)
 
 }  // namespace rs

@@ -29,7 +29,7 @@ __device__ __forceinline__ void matvec_block(const MatvecProb& P, int orow0, con
                     const T a = A[(int64_t)j * P.ld + i];
 #pragma unroll
                     for (int c = 0; c < CH; ++c)
-                        if (c < nc) acc[c] = fma(a, x[(int64_t)j * nrhs + c0 + c], acc[c]);
+                        if (c < nc) acc[c] = fma_(a, x[(int64_t)j * nrhs + c0 + c], acc[c]);
                 }
             }
 #pragma unroll
@@ -59,7 +59,7 @@ __device__ __forceinline__ void matvec_block(const MatvecProb& P, int orow0, con
                     const T a = colj[i];
 #pragma unroll
                     for (int c = 0; c < CH; ++c)
-                        if (c < nc) a2[c] = fma(a, x[(int64_t)i * nrhs + c0 + c], a2[c]);
+                        if (c < nc) a2[c] = fma_(a, x[(int64_t)i * nrhs + c0 + c], a2[c]);
                 }
 #pragma unroll
                 for (int c = 0; c < CH; ++c) a2[c] = warp_sum(a2[c]);

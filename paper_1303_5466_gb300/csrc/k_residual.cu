@@ -1,5 +1,6 @@
-// k_residual.cu -- FP64 direct-sum residual r = f - A x of the Laplace Nystrom matrix, used by
-// the iterative refinement of the mixed-precision factorization and by rs_residual.
+// k_residual.cu -- FP64 direct-sum residual r = f - A x of the Nystrom matrix (Laplace, or
+// Helmholtz in its original form A = a + kappa^2 b K with complex128 arithmetic), used by the
+// iterative refinement of the low-precision factorizations and by rs_residual.
 //
 // The off-diagonal entries depend only on the integer offset (d1, d2) between two grid points,
 // so they are tabulated once for the (2n-1)^2 offsets; the sum over all N^2 pairs is then one
@@ -20,15 +21,30 @@ __global__ void laplace_table_kernel(int n, double h, double c0, double* __restr
     Kt[e] = (d1 == 0 && d2 == 0) ? 0.0 : c0 * log(dx * dx + dy * dy);
 }
 
+// Kt[...] = (i/4) H0^(1)(kappa |d| h) h^2 = (h^2/4)(-Y0 + i J0), 0 at d1 = d2 = 0.
+__global__ void helmholtz_table_kernel(int n, double h, double kappa, cplx<double>* __restrict__ Kt)
+{
+    const int W = 2 * n - 1;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)W * W) return;
+    const int d1 = (int)(e % W) - (n - 1), d2 = (int)(e / W) - (n - 1);
+    if (d1 == 0 && d2 == 0) { Kt[e] = cplx<double>(0.0, 0.0); return; }
+    const double z = kappa * h * sqrt((double)d1 * d1 + (double)d2 * d2);
+    const double q = 0.25 * h * h;
+    Kt[e] = cplx<double>(-q * y0(z), q * j0(z));
+}
+
 constexpr int DS = 16;          // tile side of targets and sources
 constexpr int DS_RHS = 4;       // right-hand sides per pass
 
-// yg = A xg in grid order: yg[c N + g] = dg[g] xg[c N + g] + sum_{g' != g} K(g - g') xg[c N + g'].
-__global__ void __launch_bounds__(256) direct_sum_kernel(int n, const double* __restrict__ Kt,
-        const double* __restrict__ dg, const double* __restrict__ xg, double* __restrict__ yg, int nrhs)
+// yg = A xg in grid order: yg[c N + g] = dg[g] xg[c N + g] + rs[g] sum_{g' != g} K(g - g') xg[c N + g']
+// (rs = NULL means 1).
+template <class S>
+__global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
+        const double* __restrict__ rs, const S* __restrict__ xg, S* __restrict__ yg, int nrhs)
 {
-    __shared__ double Kw[2 * DS - 1][2 * DS];
-    __shared__ double xs[DS_RHS][DS * DS];
+    __shared__ S Kw[2 * DS - 1][2 * DS];
+    __shared__ S xs[DS_RHS][DS * DS];
     const int64_t N = (int64_t)n * n;
     const int W = 2 * n - 1;
     const int tx0 = blockIdx.x * DS, ty0 = blockIdx.y * DS;
@@ -37,9 +53,9 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const double* __
     const bool tin = ti1 < n && ti2 < n;
     for (int c0 = 0; c0 < nrhs; c0 += DS_RHS) {
         const int nc = min(DS_RHS, nrhs - c0);
-        double acc[DS_RHS];
+        S acc[DS_RHS];
 #pragma unroll
-        for (int c = 0; c < DS_RHS; ++c) acc[c] = 0.0;
+        for (int c = 0; c < DS_RHS; ++c) acc[c] = S(0.0);
         for (int sy0 = 0; sy0 < n; sy0 += DS) {
             for (int sx0 = 0; sx0 < n; sx0 += DS) {
                 __syncthreads();
@@ -48,12 +64,12 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const double* __
                     const int d1 = tx0 - sx0 - (DS - 1) + e1, d2 = ty0 - sy0 - (DS - 1) + e2;
                     Kw[e2][e1] = (d1 > -n && d1 < n && d2 > -n && d2 < n)
                                      ? Kt[(int64_t)(d1 + n - 1) + (int64_t)W * (d2 + n - 1)]
-                                     : 0.0;
+                                     : S(0.0);
                 }
                 for (int e = threadIdx.x; e < nc * DS * DS; e += blockDim.x) {
                     const int c = e / (DS * DS), j = e - c * (DS * DS);
                     const int s1 = sx0 + j % DS, s2 = sy0 + j / DS;
-                    xs[c][j] = (s1 < n && s2 < n) ? xg[(int64_t)(c0 + c) * N + s1 + (int64_t)n * s2] : 0.0;
+                    xs[c][j] = (s1 < n && s2 < n) ? xg[(int64_t)(c0 + c) * N + s1 + (int64_t)n * s2] : S(0.0);
                 }
                 __syncthreads();
                 if (tin) {
@@ -61,10 +77,10 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const double* __
                     for (int j2 = 0; j2 < DS; ++j2) {
 #pragma unroll
                         for (int j1 = 0; j1 < DS; ++j1) {
-                            const double k = Kw[ly - j2 + DS - 1][lx - j1 + DS - 1];
+                            const S k = Kw[ly - j2 + DS - 1][lx - j1 + DS - 1];
 #pragma unroll
                             for (int c = 0; c < DS_RHS; ++c)
-                                if (c < nc) acc[c] = fma(k, xs[c][j2 * DS + j1], acc[c]);
+                                if (c < nc) acc[c] = fma_(k, xs[c][j2 * DS + j1], acc[c]);
                         }
                     }
                 }
@@ -72,15 +88,17 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const double* __
         }
         if (tin) {
             const int64_t g = ti1 + (int64_t)n * ti2;
+            const S sum_scale = rs ? S(rs[g]) : S(1.0);
             for (int c = 0; c < nc; ++c)
-                yg[(int64_t)(c0 + c) * N + g] = fma(dg[g], xg[(int64_t)(c0 + c) * N + g], acc[c]);
+                yg[(int64_t)(c0 + c) * N + g] = fma_(dg[g], xg[(int64_t)(c0 + c) * N + g], sum_scale * acc[c]);
         }
     }
 }
 
 // xg[c N + g] = x[c N + ing[g]]
-__global__ void to_grid_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing, const double* __restrict__ x,
-                               double* __restrict__ xg)
+template <class S>
+__global__ void to_grid_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing, const S* __restrict__ x,
+                               S* __restrict__ xg)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N * nrhs) return;
@@ -89,9 +107,9 @@ __global__ void to_grid_kernel(int64_t N, int nrhs, const int64_t* __restrict__ 
 }
 
 // r[c N + ing[g]] = f[c N + ing[g]] - yg[c N + g]
+template <class S>
 __global__ void residual_finish_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing,
-                                       const double* __restrict__ f, const double* __restrict__ yg,
-                                       double* __restrict__ r)
+                                       const S* __restrict__ f, const S* __restrict__ yg, S* __restrict__ r)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N * nrhs) return;
@@ -100,17 +118,17 @@ __global__ void residual_finish_kernel(int64_t N, int nrhs, const int64_t* __res
     r[i] = f[i] - yg[e];
 }
 
-// out[2c] += sum_i r[c N + i]^2, out[2c + 1] += sum_i f[c N + i]^2
-__global__ void __launch_bounds__(256) colnorm2_kernel(int64_t N, int nrhs, const double* __restrict__ r,
-                                                       const double* __restrict__ f, double* __restrict__ out)
+// out[2c] += sum_i |r[c N + i]|^2, out[2c + 1] += sum_i |f[c N + i]|^2
+template <class S>
+__global__ void __launch_bounds__(256) colnorm2_kernel(int64_t N, int nrhs, const S* __restrict__ r,
+                                                       const S* __restrict__ f, double* __restrict__ out)
 {
     __shared__ double sr[8], sf[8];
     const int c = blockIdx.y;
     double a = 0.0, b = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double u = r[(int64_t)c * N + i], v = f[(int64_t)c * N + i];
-        a = fma(u, u, a);
-        b = fma(v, v, b);
+        a += abs2d(r[(int64_t)c * N + i]);
+        b += abs2d(f[(int64_t)c * N + i]);
     }
     a = warp_sum(a);
     b = warp_sum(b);
@@ -134,20 +152,36 @@ cudaError_t launch_laplace_table(cudaStream_t st, int n, double h, double c0, do
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const double* Kt, const double* dg, const int64_t* ing,
-                            const double* x, const double* f, double* xg, double* yg, double* r, double* norms)
+cudaError_t launch_helmholtz_table(cudaStream_t st, int n, double h, double kappa, cplx<double>* Kt)
+{
+    const int64_t W = 2 * (int64_t)n - 1;
+    count_launches(1);
+    helmholtz_table_kernel<<<nblk(W * W), 256, 0, st>>>(n, h, kappa, Kt);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const S* Kt, const S* dg, const double* rs,
+                            const int64_t* ing, const S* x, const S* f, S* xg, S* yg, S* r, double* norms)
 {
     const int64_t N = (int64_t)n * n;
     count_launches(4);
-    to_grid_kernel<<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, x, xg);
+    to_grid_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, x, xg);
     dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
-    direct_sum_kernel<<<grid, 256, 0, st>>>(n, Kt, dg, xg, yg, nrhs);
-    residual_finish_kernel<<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, f, yg, r);
+    direct_sum_kernel<S><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
+    residual_finish_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, f, yg, r);
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nrhs, st);
     if (e != cudaSuccess) return e;
     dim3 g2((unsigned)std::min<int64_t>(nblk(N), 1024), (unsigned)nrhs);
-    colnorm2_kernel<<<g2, 256, 0, st>>>(N, nrhs, r, f, norms);
+    colnorm2_kernel<S><<<g2, 256, 0, st>>>(N, nrhs, r, f, norms);
     return cudaGetLastError();
 }
+template cudaError_t launch_residual<double>(cudaStream_t, int, int, const double*, const double*, const double*,
+                                             const int64_t*, const double*, const double*, double*, double*, double*,
+                                             double*);
+template cudaError_t launch_residual<cplx<double>>(cudaStream_t, int, int, const cplx<double>*, const cplx<double>*,
+                                                   const double*, const int64_t*, const cplx<double>*,
+                                                   const cplx<double>*, cplx<double>*, cplx<double>*, cplx<double>*,
+                                                   double*);
 
 }  // namespace rs

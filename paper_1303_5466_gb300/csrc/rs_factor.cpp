@@ -514,13 +514,23 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     op->kappa = kernel ? kernel->kappa : 0.0;
     op->eps = eps;
     op->input_of_g = tree->input_of_g;
-    if (op->kind != RS_LAPLACE) return fail(RS_E_INVALID, "only the Laplace kernel is built in this version");
-    if (kernel && kernel->b) return fail(RS_E_INVALID, "b(x) is only used by the Helmholtz kernel");
-    if (op->opts.precision != RS_FP64 && op->opts.precision != RS_MIXED_FP32)
-        return fail(RS_E_INVALID, "Laplace operators are factored in RS_FP64 or RS_MIXED_FP32");
-    op->esz = op->opts.precision == RS_MIXED_FP32 ? (int)sizeof(float) : (int)sizeof(double);
-    if (op->opts.precision == RS_MIXED_FP32 && !(op->opts.refine_tol > 0.0 && op->opts.refine_max_iter >= 1))
-        return fail(RS_E_INVALID, "mixed precision needs refine_tol > 0 and refine_max_iter >= 1");
+    if (op->kind == RS_LAPLACE) {
+        if (kernel && kernel->b) return fail(RS_E_INVALID, "b(x) is only used by the Helmholtz kernel");
+        if (op->opts.precision != RS_FP64 && op->opts.precision != RS_MIXED_FP32)
+            return fail(RS_E_INVALID, "Laplace operators are factored in RS_FP64 or RS_MIXED_FP32");
+        op->esz = op->opts.precision == RS_MIXED_FP32 ? (int)sizeof(float) : (int)sizeof(double);
+    } else if (op->kind == RS_HELMHOLTZ) {
+        if (!(op->kappa > 0.0)) return fail(RS_E_INVALID, "Helmholtz needs kappa > 0");
+        if (op->opts.precision == RS_FP64) op->opts.precision = RS_C128;
+        if (op->opts.precision != RS_C128 && op->opts.precision != RS_C64_REFINED)
+            return fail(RS_E_INVALID, "Helmholtz operators are factored in RS_C128 or RS_C64_REFINED");
+        op->esz = op->opts.precision == RS_C64_REFINED ? 2 * (int)sizeof(float) : 2 * (int)sizeof(double);
+    } else {
+        return fail(RS_E_INVALID, "unknown kernel kind");
+    }
+    if ((op->opts.precision == RS_MIXED_FP32 || op->opts.precision == RS_C64_REFINED) &&
+        !(op->opts.refine_tol > 0.0 && op->opts.refine_max_iter >= 1))
+        return fail(RS_E_INVALID, "refined precisions need refine_tol > 0 and refine_max_iter >= 1");
     if (op->opts.proxy_points < 0 || op->opts.proxy_points > 4096 || !(op->opts.proxy_radius_factor > 0.0))
         return fail(RS_E_INVALID, "bad proxy options");
     if (!(eps >= 0.0) || !(eps < 1.0)) return fail(RS_E_INVALID, "eps must be in [0, 1)");
@@ -532,12 +542,32 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     // diagonal: a_g - (1/2pi) * integral of log|y - x_g| over the h x h cell, whose closed
     // form is h^2 (log h - log(2)/2 - 3/2 + pi/4)
     op->K.self = -(h * h * (std::log(h) - 0.5 * std::log(2.0) - 1.5 + M_PI / 4.0)) / (2.0 * M_PI);
+    op->K.kind = op->kind;
+    op->K.kappa = op->kappa;
     auto t0 = Clock::now();
+    int rc;
+    if (op->kind == RS_HELMHOLTZ) {
+        // (i/4) * integral of H0^(1)(kappa |y - x|) over the h x h cell centred at x
+        double re = 0.0, im = 0.0;
+        helmholtz_cell_integral(h, op->kappa, &re, &im);
+        op->K.hs_re = -0.25 * im;
+        op->K.hs_im = 0.25 * re;
+        // symmetric form of Eq. (5.6): s = kappa sqrt(b), grid order and input order
+        std::vector<double> sg((size_t)op->N), si((size_t)op->N);
+        for (int64_t i = 0; i < op->N; ++i) {
+            const double bi = (kernel && kernel->b) ? kernel->b[i] : 1.0;
+            if (!(bi > 0.0) || !std::isfinite(bi)) return fail(RS_E_INVALID, "b(x) must be positive and finite");
+            si[(size_t)i] = op->kappa * std::sqrt(bi);
+        }
+        for (int64_t g = 0; g < op->N; ++g) sg[(size_t)g] = si[(size_t)op->input_of_g[g]];
+        if ((rc = upload(op->d_s, sg, st))) return rc;
+        if ((rc = upload(op->d_s_in, si, st))) return rc;
+        op->K.s = op->d_s.as<double>();
+    }
     // a in grid order
     std::vector<double> ag(op->N, 1.0);
     if (a)
         for (int64_t g = 0; g < op->N; ++g) ag[g] = a[op->input_of_g[g]];
-    int rc;
     if ((rc = upload(op->d_a, ag, st))) return rc;
     const int P = op->opts.proxy_points;
     std::vector<double> uc(2 * (size_t)P + 1);
@@ -554,7 +584,12 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         op->lev[l].l = l;
         op->lev[l].nb = 1 << l;
     }
-    rc = op->esz == (int)sizeof(float) ? factor_levels<float>(op, st, t0) : factor_levels<double>(op, st, t0);
+    switch (op->opts.precision) {
+        case RS_MIXED_FP32: rc = factor_levels<float>(op, st, t0); break;
+        case RS_C128: rc = factor_levels<cplx<double>>(op, st, t0); break;
+        case RS_C64_REFINED: rc = factor_levels<cplx<float>>(op, st, t0); break;
+        default: rc = factor_levels<double>(op, st, t0); break;
+    }
     if (rc) return rc;
     *out = guard.release();
     return RS_OK;
@@ -585,9 +620,10 @@ namespace {
 // The kernel sequence of the inverse apply (Algorithm 6 as the recursion of Eqs. 2.10-2.12)
 // in storage type T; f (fd) and x (xd) are FP64 N x nrhs column-major in input order.
 template <class T>
-int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
-                cudaStream_t st)
+int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typename sc_traits<T>::io* fd,
+                typename sc_traits<T>::io* xd, int64_t nrhs, cudaStream_t st)
 {
+    using IO = typename sc_traits<T>::io;
     const int64_t N = op->N;
     const int d = op->d;
     const std::vector<int64_t>& woff = Ls.woff;
@@ -604,7 +640,7 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const dou
         Level& L = op->lev[l];
         T* wl = W + woff[l] * nrhs;
         T* gl = Gb + goff[l] * nrhs;
-        if (l == d) RS_CUDA(launch_gather_cm<double, T>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
+        if (l == d) RS_CUDA(launch_gather_cm<IO, T>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
         else RS_CUDA(launch_gather_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
@@ -643,7 +679,7 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const dou
         RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
                               L.d_Phi.as<T>(), U, XO, nr)); }
         RS_CUDA(launch_axpby<T>(st, L.sum_m * nrhs, (T)1, wl, (T)1, XO));   // x' = w + Phi v
-        if (l == d) RS_CUDA(launch_scatter_cm<T, double>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
+        if (l == d) RS_CUDA(launch_scatter_cm<T, IO>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
         else RS_CUDA(launch_scatter_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), XO, Ph + goff[l + 1] * nrhs, nr));
     }
     return RS_OK;
@@ -656,8 +692,13 @@ int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const doubl
 {
     const int saved_profile = op->opts.profile;
     op->opts.profile = profile ? saved_profile : 0;
-    const int rc = op->esz == (int)sizeof(float) ? solve_run_t<float>(op, Ls, ws, fd, xd, nrhs, st)
-                                                 : solve_run_t<double>(op, Ls, ws, fd, xd, nrhs, st);
+    int rc;
+    switch (op->opts.precision) {
+        case RS_MIXED_FP32: rc = solve_run_t<float>(op, Ls, ws, fd, xd, nrhs, st); break;
+        case RS_C128: rc = solve_run_t<cplx<double>>(op, Ls, ws, (const cplx<double>*)fd, (cplx<double>*)xd, nrhs, st); break;
+        case RS_C64_REFINED: rc = solve_run_t<cplx<float>>(op, Ls, ws, (const cplx<double>*)fd, (cplx<double>*)xd, nrhs, st); break;
+        default: rc = solve_run_t<double>(op, Ls, ws, fd, xd, nrhs, st); break;
+    }
     op->opts.profile = saved_profile;
     return rc;
 }
@@ -674,7 +715,15 @@ int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream
     RS_CUDA(op->s_out.alloc(e * (size_t)Ls.n_u));
     RS_CUDA(op->s_t.alloc(e * (size_t)Ls.n_t));
     SolveWork ws{op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p};
-    return solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
+    if (op->kind != RS_HELMHOLTZ) return solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
+    // symmetric form: x = S (S^{-1} A S)^{-1} S^{-1} f, S = diag(kappa sqrt(b))
+    using Z = cplx<double>;
+    RS_CUDA(op->s_fs.alloc(sizeof(Z) * (size_t)(op->N * nrhs)));
+    RS_CUDA(launch_scale_cm<Z>(st, op->N, (int)nrhs, op->d_s_in.as<double>(), -1, (const Z*)fd, op->s_fs.as<Z>()));
+    const int rc = solve_run(op, Ls, ws, op->s_fs.as<double>(), xd, nrhs, st, op->opts.profile != 0);
+    if (rc) return rc;
+    RS_CUDA(launch_scale_cm<Z>(st, op->N, (int)nrhs, op->d_s_in.as<double>(), 1, (const Z*)xd, (Z*)xd));
+    return RS_OK;
 }
 
 int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
@@ -686,19 +735,21 @@ int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
         op->prof_ms[RS_PROF_SOLVE] = op->prof_work[RS_PROF_SOLVE] = op->prof_bytes[RS_PROF_SOLVE] = 0.0;
         op->prof_n[RS_PROF_SOLVE] = 0;
     }
+    const size_t io = op->kind == RS_HELMHOLTZ ? 2 * sizeof(double) : sizeof(double);
     const double* fd = (const double*)f;
     double* xd = (double*)x;
     if (!dev_f) {
-        RS_CUDA(op->s_in.alloc(sizeof(double) * (size_t)(N * nrhs)));
-        RS_CUDA(cudaMemcpyAsync(op->s_in.p, f, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyHostToDevice, st));
+        RS_CUDA(op->s_in.alloc(io * (size_t)(N * nrhs)));
+        RS_CUDA(cudaMemcpyAsync(op->s_in.p, f, io * (size_t)(N * nrhs), cudaMemcpyHostToDevice, st));
         fd = op->s_in.as<double>();
-        RS_CUDA(op->s_out2.alloc(sizeof(double) * (size_t)(N * nrhs)));
+        RS_CUDA(op->s_out2.alloc(io * (size_t)(N * nrhs)));
         xd = op->s_out2.as<double>();
     }
-    int rc = (op->opts.precision == RS_MIXED_FP32) ? refine_solve(op, fd, xd, nrhs, st) : apply_once(op, fd, xd, nrhs, st);
+    const bool refine = op->opts.precision == RS_MIXED_FP32 || op->opts.precision == RS_C64_REFINED;
+    int rc = refine ? refine_solve(op, fd, xd, nrhs, st) : apply_once(op, fd, xd, nrhs, st);
     if (rc && rc != RS_E_NOT_CONVERGED) return rc;
     if (!dev_x) {
-        RS_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaMemcpyAsync(x, xd, io * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
         RS_CUDA(cudaStreamSynchronize(st));
     }
     if (op->opts.profile) {
@@ -797,6 +848,17 @@ static int fetch(const rs_op* op, const DevMem& d, int64_t off, int64_t n, std::
 {
     out.assign((size_t)n, 0.0);
     if (n == 0) return RS_OK;
+    if (op->kind == RS_HELMHOLTZ) {      // complex storage: n counts doubles (re, im pairs)
+        const int64_t e0 = 2 * off;
+        if (op->esz == 2 * (int)sizeof(double)) {
+            RS_CUDA(cudaMemcpy(out.data(), d.as<double>() + e0, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> t((size_t)n);
+            RS_CUDA(cudaMemcpy(t.data(), d.as<float>() + e0, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < t.size(); ++i) out[i] = t[i];
+        }
+        return RS_OK;
+    }
     if (op->esz == (int)sizeof(double)) {
         RS_CUDA(cudaMemcpy(out.data(), d.as<double>() + off, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
     } else {
@@ -812,22 +874,26 @@ int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out
     const Level* L = get_level(op, level, box);
     if (!L || !out) return fail(RS_E_INVALID, "level/box out of range");
     const int64_t m = L->m[box], k = L->k[box];
+    const int c = op->kind == RS_HELMHOLTZ ? 2 : 1;     // doubles per entry
     RS_CUDA(cudaSetDevice(op->device));
     std::vector<double> t;
     int rc;
     if (which == 0) {
-        if ((rc = fetch(op, L->d_T, L->t_off[box], k * (m - k), t))) return rc;
+        if ((rc = fetch(op, L->d_T, L->t_off[box], c * k * (m - k), t))) return rc;
         for (int64_t i = 0; i < k; ++i)
-            for (int64_t j = 0; j < m - k; ++j) out[i * (m - k) + j] = t[(size_t)(j * k + i)];
+            for (int64_t j = 0; j < m - k; ++j)
+                for (int q = 0; q < c; ++q) out[(i * (m - k) + j) * c + q] = t[(size_t)((j * k + i) * c + q)];
     } else if (which == 1) {
-        if ((rc = fetch(op, L->d_Phi, L->phi_off[box], m * m, t))) return rc;
+        if ((rc = fetch(op, L->d_Phi, L->phi_off[box], c * m * m, t))) return rc;
         const int32_t* pm = L->perm.data() + L->act_off[box];
-        for (int64_t q = 0; q < m; ++q)
-            for (int64_t p = 0; p < m; ++p) out[(int64_t)pm[p] * m + pm[q]] = t[(size_t)(q * m + p)];
+        for (int64_t qq = 0; qq < m; ++qq)
+            for (int64_t p = 0; p < m; ++p)
+                for (int q = 0; q < c; ++q) out[((int64_t)pm[p] * m + pm[qq]) * c + q] = t[(size_t)((qq * m + p) * c + q)];
     } else if (which == 2) {
-        if ((rc = fetch(op, L->d_E, L->e_off[box], k * k, t))) return rc;
+        if ((rc = fetch(op, L->d_E, L->e_off[box], c * k * k, t))) return rc;
         for (int64_t i = 0; i < k; ++i)
-            for (int64_t j = 0; j < k; ++j) out[i * k + j] = t[(size_t)(j * k + i)];
+            for (int64_t j = 0; j < k; ++j)
+                for (int q = 0; q < c; ++q) out[(i * k + j) * c + q] = t[(size_t)((j * k + i) * c + q)];
     } else {
         return fail(RS_E_INVALID, "bad `which`");
     }
@@ -839,12 +905,14 @@ int rs_op_root_matrix(const rs_op* op, double* out)
     if (!op || !out) return fail(RS_E_INVALID, "NULL argument");
     const Level& R = op->lev[0];
     const int64_t m = R.m[0];
+    const int c = op->kind == RS_HELMHOLTZ ? 2 : 1;
     RS_CUDA(cudaSetDevice(op->device));
     std::vector<double> t;
-    const int rc = fetch(op, R.d_Phi, 0, m * m, t);
+    const int rc = fetch(op, R.d_Phi, 0, c * m * m, t);
     if (rc) return rc;
-    for (int64_t q = 0; q < m; ++q)
-        for (int64_t p = 0; p < m; ++p) out[p * m + q] = t[(size_t)(q * m + p)];
+    for (int64_t qq = 0; qq < m; ++qq)
+        for (int64_t p = 0; p < m; ++p)
+            for (int q = 0; q < c; ++q) out[(p * m + qq) * c + q] = t[(size_t)((qq * m + p) * c + q)];
     return RS_OK;
 }
 

@@ -118,6 +118,7 @@ int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream
 int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st);
 int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
                    cudaStream_t st);
+void helmholtz_cell_integral(double h, double kappa, double* re, double* im);
 }  // namespace rs
 
 struct rs_op {
@@ -129,7 +130,7 @@ struct rs_op {
     double kappa = 0.0;
     double eps = 0.0;
     rs_opts opts{};
-    rs::LaplaceK K{};
+    rs::KernelK K{};
     std::vector<int64_t> input_of_g;
     std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow;
@@ -138,7 +139,9 @@ struct rs_op {
     int64_t s_nrhs = 0;
     // FP64 direct-sum residual (built on first use): offset table, diagonal, permutation,
     // and refinement workspace
-    rs::DevMem d_ktab, d_diag, d_ing, r_xg, r_yg, r_res, r_dx, r_x, r_norm;
+    rs::DevMem d_ktab, d_diag, d_rs, d_ing, r_xg, r_yg, r_res, r_dx, r_x, r_norm;
+    // Helmholtz symmetric scaling s = kappa sqrt(b): grid order, input order; scaled RHS
+    rs::DevMem d_s, d_s_in, s_fs;
     rs_stats stats{};
     std::atomic<int> inflight{0};   // references held by servers and their requests
     // profiling (opts.profile): pending event pairs and per-class sums

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/rs.h"
+#include "k_scalar.cuh"
 
 namespace rs {
 
@@ -58,21 +59,28 @@ struct MatvecProb {
 // ------------------------------------------------------------------ launchers (kernels.cu)
 // All launchers enqueue on `st`, return cudaError_t of the launch.
 
-// Laplace kernel constants: entry = c0 * log(|x - y|^2), diagonal = a_g + self.
-struct LaplaceK {
+// Kernel constants.  Laplace: off-diagonal c0 log(|x - y|^2) (c0 = -h^2/(4 pi)), diagonal
+// a_g + self.  Helmholtz, in the symmetric form of Eq. (5.6): off-diagonal
+// s_g (i/4) H0(kappa r) h^2 s_g', diagonal a_g + s_g^2 (hs_re + i hs_im), s = kappa sqrt(b)
+// (device array, grid order); the proxy rows are (i/4) H0(kappa |z - x|) h^2 s_g.
+struct KernelK {
     double h, c0, self;
     int n;
+    int kind;
+    double kappa;
+    double hs_re, hs_im;
+    const double* s;
 };
 
-// All launchers below are instantiated for T = double (FP64 path) and T = float (the FP32
-// storage of the mixed-precision factor).
+// All launchers below are instantiated for T = double (FP64 path), float (FP32 storage of the
+// mixed-precision factor), cplx<double> (complex128) and cplx<float> (complex64).
 
 // Y for every box of a level: rows = near points then P proxy points, columns = active
 // points, column-major r x m at y_off[b].
 template <class T>
 cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const int64_t* act_off,
                               const int32_t* near, const int64_t* near_off, const double* geo,
-                              const double* ucirc, int P, const int64_t* y_off, T* Y, LaplaceK K,
+                              const double* ucirc, int P, const int64_t* y_off, T* Y, KernelK K,
                               int max_entries);
 
 // Column-pivoted QR (Eq. 2.1) of every box's Y, G CTAs per box (cooperative when G > 1).
@@ -102,7 +110,7 @@ cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const i
 template <class T>
 cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t* act, const int64_t* act_off,
                               const int32_t* perm, const double* a, const int64_t* phi_off, T* Phi,
-                              const int32_t* child_k, const int64_t* child_e_off, const T* childE, LaplaceK K,
+                              const int32_t* child_k, const int64_t* child_e_off, const T* childE, KernelK K,
                               int max_m);
 
 // In-place blocked Gauss-Jordan inverse with partial pivoting of nb column-major matrices
@@ -143,6 +151,9 @@ cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx
 // y[i] = a * x[i] + b * y[i]
 template <class T>
 cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y);
+// y[c N + i] = s[i]^pw x[c N + i], pw = +1 or -1 (instantiated for cplx<double>)
+template <class T>
+cudaError_t launch_scale_cm(cudaStream_t st, int64_t N, int nrhs, const double* sc, int pw, const T* x, T* y);
 
 // Serving job lists (k_serve.cu).  MvJob: one request's descriptor set of one stage
 // (blocks blk_start .. blk_start + nblk of the launch).  CopyJob: a gather, scatter or axpby
@@ -172,8 +183,12 @@ cudaError_t launch_copy_jobs(cudaStream_t st, const CopyJob* jobs, int nj, int64
 // FP64 direct-sum residual (k_residual.cu): Kt is the (2n-1)^2 offset table of the Laplace
 // kernel; r = f - A x with x, f, r N x nrhs column-major in input order (ing[g] = input index
 // of grid point g), xg, yg grid-order scratch, norms[2c] = |r_c|^2, norms[2c+1] = |f_c|^2.
+// Helmholtz: Kt holds (i/4) H0(kappa |d| h) h^2 (complex), dg = a + kappa^2 b (i/4) int_cell H0 and
+// the off-diagonal sum is scaled per row by rs = kappa^2 b (Laplace: rs = NULL).
 cudaError_t launch_laplace_table(cudaStream_t st, int n, double h, double c0, double* Kt);
-cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const double* Kt, const double* dg, const int64_t* ing,
-                            const double* x, const double* f, double* xg, double* yg, double* r, double* norms);
+cudaError_t launch_helmholtz_table(cudaStream_t st, int n, double h, double kappa, cplx<double>* Kt);
+template <class S>
+cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const S* Kt, const S* dg, const double* rs,
+                            const int64_t* ing, const S* x, const S* f, S* xg, S* yg, S* r, double* norms);
 
 }  // namespace rs

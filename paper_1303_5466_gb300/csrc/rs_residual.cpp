@@ -1,5 +1,6 @@
-// rs_residual.cpp -- FP64 direct-sum residual and the iterative refinement of mixed-precision
-// solves (the paper's one round of refinement, Sec. 5.3/5.4, repeated to a tolerance).
+// rs_residual.cpp -- FP64 direct-sum residual and the iterative refinement of low-precision
+// solves (the paper's round of refinement, Sec. 5.3-5.4, repeated to a tolerance), plus the
+// Helmholtz cell integral used on the diagonal.
 #include <math.h>
 
 #include <algorithm>
@@ -11,42 +12,103 @@
 
 namespace rs {
 
-// Offset table, FP64 diagonal (a_g + self) and the grid -> input permutation, built once.
-static int residual_setup(rs_op* op, cudaStream_t st)
+// Integral of H0^(1)(kappa |y - x|) over the h x h cell centred at x.  In polar coordinates
+// over the eight triangles of the square, with rho(th) = (h/2)/cos th,
+//   int_0^rho r H0(kappa r) dr = (kappa rho H1(kappa rho) + 2i/pi) / kappa^2,
+// and the remaining integral over th in [0, pi/4] is smooth: 48-point Gauss-Legendre.
+void helmholtz_cell_integral(double h, double kappa, double* re, double* im)
+{
+    const int n = 48;
+    std::vector<double> x(n), w(n);
+    for (int i = 0; i < n; ++i) {                 // Legendre roots by Newton's method
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-15) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    double ar = 0.0, ai = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double th = 0.125 * M_PI * (1.0 + x[i]);
+        const double z = kappa * 0.5 * h / std::cos(th);
+        const double wt = 0.125 * M_PI * w[i] / (kappa * kappa);
+        ar += wt * z * j1(z);                      // Re: kappa rho J1
+        ai += wt * (z * y1(z) + 2.0 / M_PI);       // Im: kappa rho Y1 + 2/pi
+    }
+    *re = 8.0 * ar;
+    *im = 8.0 * ai;
+}
+
+namespace {
+
+// Offset table, FP64 diagonal, row scale and the grid -> input permutation, built once.
+int residual_setup(rs_op* op, cudaStream_t st)
 {
     if (op->d_ktab.p) return RS_OK;
     const int n = (int)op->n;
     const int64_t W = 2 * (int64_t)n - 1;
-    RS_CUDA(op->d_ktab.alloc(sizeof(double) * (size_t)(W * W)));
-    RS_CUDA(launch_laplace_table(st, n, op->K.h, op->K.c0, op->d_ktab.as<double>()));
-    RS_CUDA(op->d_diag.alloc(sizeof(double) * (size_t)op->N));
-    // diagonal = a_g + self: a in grid order is already resident; add self on the device
-    std::vector<double> selfv((size_t)op->N, op->K.self);
-    DevMem tmp;
-    RS_CUDA(tmp.alloc(sizeof(double) * (size_t)op->N));
-    RS_CUDA(cudaMemcpyAsync(tmp.p, selfv.data(), sizeof(double) * selfv.size(), cudaMemcpyHostToDevice, st));
-    RS_CUDA(cudaMemcpyAsync(op->d_diag.p, op->d_a.p, sizeof(double) * (size_t)op->N, cudaMemcpyDeviceToDevice, st));
-    RS_CUDA(launch_axpby<double>(st, op->N, 1.0, tmp.as<double>(), 1.0, op->d_diag.as<double>()));
-    RS_CUDA(op->d_ing.alloc(sizeof(int64_t) * (size_t)op->N));
-    RS_CUDA(cudaMemcpyAsync(op->d_ing.p, op->input_of_g.data(), sizeof(int64_t) * (size_t)op->N,
-                            cudaMemcpyHostToDevice, st));
+    const size_t N = (size_t)op->N;
+    std::vector<double> a((size_t)N);
+    RS_CUDA(cudaMemcpy(a.data(), op->d_a.p, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    if (op->kind == RS_HELMHOLTZ) {
+        using Z = cplx<double>;
+        RS_CUDA(op->d_ktab.alloc(sizeof(Z) * (size_t)(W * W)));
+        RS_CUDA(launch_helmholtz_table(st, n, op->K.h, op->kappa, op->d_ktab.as<Z>()));
+        std::vector<double> s(N);
+        RS_CUDA(cudaMemcpy(s.data(), op->d_s.p, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        std::vector<Z> dg(N);
+        std::vector<double> rsv(N);
+        for (size_t g = 0; g < N; ++g) {            // original form: a + kappa^2 b (i/4) int_cell H0
+            const double s2 = s[g] * s[g];
+            dg[g] = Z(a[g] + s2 * op->K.hs_re, s2 * op->K.hs_im);
+            rsv[g] = s2;
+        }
+        RS_CUDA(op->d_diag.alloc(sizeof(Z) * N));
+        RS_CUDA(cudaMemcpy(op->d_diag.p, dg.data(), sizeof(Z) * N, cudaMemcpyHostToDevice));
+        RS_CUDA(op->d_rs.alloc(sizeof(double) * N));
+        RS_CUDA(cudaMemcpy(op->d_rs.p, rsv.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    } else {
+        RS_CUDA(op->d_ktab.alloc(sizeof(double) * (size_t)(W * W)));
+        RS_CUDA(launch_laplace_table(st, n, op->K.h, op->K.c0, op->d_ktab.as<double>()));
+        for (size_t g = 0; g < N; ++g) a[g] += op->K.self;
+        RS_CUDA(op->d_diag.alloc(sizeof(double) * N));
+        RS_CUDA(cudaMemcpy(op->d_diag.p, a.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    }
+    RS_CUDA(op->d_ing.alloc(sizeof(int64_t) * N));
+    RS_CUDA(cudaMemcpyAsync(op->d_ing.p, op->input_of_g.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
     RS_CUDA(cudaStreamSynchronize(st));
     return RS_OK;
 }
 
-// r = f - A x (device, FP64, N x nrhs column-major in input order); rel[c] = |r_c| / |f_c|.
-int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
-                   cudaStream_t st)
+template <class Z>
+int residual_t(rs_op* op, const Z* x, const Z* f, int64_t nrhs, Z* r, double* rel, cudaStream_t st)
 {
     int rc = residual_setup(op, st);
     if (rc) return rc;
-    const size_t bytes = sizeof(double) * (size_t)(op->N * nrhs);
+    const size_t bytes = sizeof(Z) * (size_t)(op->N * nrhs);
     RS_CUDA(op->r_xg.alloc(bytes));
     RS_CUDA(op->r_yg.alloc(bytes));
     RS_CUDA(op->r_norm.alloc(sizeof(double) * 2 * (size_t)nrhs));
-    RS_CUDA(launch_residual(st, (int)op->n, (int)nrhs, op->d_ktab.as<double>(), op->d_diag.as<double>(),
-                            op->d_ing.as<int64_t>(), x, f, op->r_xg.as<double>(), op->r_yg.as<double>(), r,
-                            op->r_norm.as<double>()));
+    RS_CUDA(launch_residual<Z>(st, (int)op->n, (int)nrhs, op->d_ktab.as<Z>(), op->d_diag.as<Z>(),
+                               op->kind == RS_HELMHOLTZ ? op->d_rs.as<double>() : nullptr, op->d_ing.as<int64_t>(), x,
+                               f, op->r_xg.as<Z>(), op->r_yg.as<Z>(), r, op->r_norm.as<double>()));
     std::vector<double> nm(2 * (size_t)nrhs);
     RS_CUDA(cudaMemcpyAsync(nm.data(), op->r_norm.p, sizeof(double) * nm.size(), cudaMemcpyDeviceToHost, st));
     RS_CUDA(cudaStreamSynchronize(st));
@@ -55,11 +117,10 @@ int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, do
     return RS_OK;
 }
 
-// x = 0; repeat: dx = A_eps^{-1} r (the low-precision factors), x += dx, r = f - A x (FP64),
-// until max_c |r_c| / |f_c| <= refine_tol or refine_max_iter solves were made.
-int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st)
+template <class Z>
+int refine_t(rs_op* op, const Z* fd, Z* xd, int64_t nrhs, cudaStream_t st)
 {
-    const size_t bytes = sizeof(double) * (size_t)(op->N * nrhs);
+    const size_t bytes = sizeof(Z) * (size_t)(op->N * nrhs);
     RS_CUDA(op->r_res.alloc(bytes));
     RS_CUDA(op->r_dx.alloc(bytes));
     RS_CUDA(cudaMemsetAsync(xd, 0, bytes, st));
@@ -69,8 +130,8 @@ int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStre
     for (int it = 1; it <= op->opts.refine_max_iter; ++it) {
         int rc = apply_once(op, op->r_res.as<double>(), op->r_dx.as<double>(), nrhs, st);
         if (rc) return rc;
-        RS_CUDA(launch_axpby<double>(st, op->N * nrhs, 1.0, op->r_dx.as<double>(), 1.0, xd));
-        rc = residual_apply(op, xd, fd, nrhs, op->r_res.as<double>(), rel.data(), st);
+        RS_CUDA(launch_axpby<Z>(st, op->N * nrhs, Z(1.0), op->r_dx.as<Z>(), Z(1.0), xd));
+        rc = residual_t<Z>(op, xd, fd, nrhs, op->r_res.as<Z>(), rel.data(), st);
         if (rc) return rc;
         worst = *std::max_element(rel.begin(), rel.end());
         op->stats.refine_iters = it;
@@ -81,6 +142,28 @@ int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStre
                                         std::to_string(op->opts.refine_max_iter) + " solves");
 }
 
+}  // namespace
+
+// r = f - A x (device, N x nrhs column-major in input order, FP64 or complex128 by kernel);
+// rel[c] = |r_c| / |f_c|.
+int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
+                   cudaStream_t st)
+{
+    if (op->kind == RS_HELMHOLTZ)
+        return residual_t<cplx<double>>(op, (const cplx<double>*)x, (const cplx<double>*)f, nrhs, (cplx<double>*)r,
+                                        rel, st);
+    return residual_t<double>(op, x, f, nrhs, r, rel, st);
+}
+
+// x = 0; repeat: dx = A_eps^{-1} r (low-precision factors), x += dx, r = f - A x (FP64),
+// until max_c |r_c| / |f_c| <= refine_tol or refine_max_iter solves were made.
+int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st)
+{
+    if (op->kind == RS_HELMHOLTZ)
+        return refine_t<cplx<double>>(op, (const cplx<double>*)fd, (cplx<double>*)xd, nrhs, st);
+    return refine_t<double>(op, fd, xd, nrhs, st);
+}
+
 }  // namespace rs
 
 using namespace rs;
@@ -88,14 +171,14 @@ using namespace rs;
 extern "C" int rs_residual(rs_op* op, const void* x, const void* f, int64_t nrhs, double* rel_out, void* stream)
 {
     if (!op || !x || !f || nrhs < 1 || !rel_out) return fail(RS_E_INVALID, "bad argument");
-    if (op->kind != RS_LAPLACE) return fail(RS_E_INVALID, "the direct-sum residual covers the Laplace kernel");
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
     cudaStream_t st = (cudaStream_t)stream;
     const bool dx = is_device_ptr(x), df = is_device_ptr(f);
     if (dx != df) return fail(RS_E_INVALID, "x and f must both be device or both be host pointers");
-    const size_t bytes = sizeof(double) * (size_t)(op->N * nrhs);
+    const size_t io = op->kind == RS_HELMHOLTZ ? 2 * sizeof(double) : sizeof(double);
+    const size_t bytes = io * (size_t)(op->N * nrhs);
     DevMem hx, hf, r;
     const double* xd = (const double*)x;
     const double* fd = (const double*)f;
