@@ -38,7 +38,7 @@ def build(force=False, plant=0, out=None):
 class _Opts(C.Structure):
     _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("proxy_points", C.c_int),
                 ("proxy_radius_factor", C.c_double), ("near_all", C.c_int),
-                ("threads", C.c_int), ("max_levels", C.c_int)]
+                ("threads", C.c_int), ("max_levels", C.c_int), ("k_cut", C.c_int), ("hss_leaf", C.c_int)]
 
 
 def load(path):
@@ -86,6 +86,19 @@ def _declare(L):
     L.ro_matvec.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, dp, C.c_int, dp]
     L.ro_matvec_rows.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, dp, C.c_int, i64p, C.c_int, dp]
     L.ro_entry.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, C.c_int64, C.c_int64, dp, dp]
+    L.ro_hss1d_build.argtypes = [C.c_int, dp, C.c_int, ip, C.c_int, C.c_double, C.POINTER(C.c_void_p)]
+    L.ro_hss1d_apply.argtypes = [C.c_void_p, dp, C.c_int, dp]
+    L.ro_hss1d_depth.argtypes = [C.c_void_p]
+    L.ro_hss1d_node.argtypes = [C.c_void_p, C.c_int, C.c_int, ip, ip, ip, ip, ip, dp]
+    L.ro_hss1d_entries.argtypes = [C.c_void_p]
+    L.ro_hss1d_entries.restype = C.c_int64
+    L.ro_hss1d_free.argtypes = [C.c_void_p]
+    L.ro_box_hss.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.ro_box_hss.restype = C.c_void_p
+    L.ro_box_lr_rank.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.ro_box_order.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, ip]
+    L.ro_compressed_entries.argtypes = [C.c_void_p, i64p]
+    L.ro_compressed_entries.restype = C.c_int64
 
 
 def _dp(a):
@@ -147,17 +160,71 @@ def inverse(A):
     return out
 
 
+class HSS1D:
+    """HSS1D form (Sec. 3.2) of an explicit square matrix built by ro_hss1d_build."""
+
+    def __init__(self, M, order=None, leaf=64, eps=1e-10, _handle=None, _owner=None):
+        L = self._L = lib()
+        if _handle is not None:
+            self._p, self._own, self._owner = _handle, False, _owner
+        else:
+            self.cplx = np.iscomplexobj(M)
+            M = np.ascontiguousarray(M, dtype=np.complex128 if self.cplx else np.float64)
+            n = M.shape[0]
+            o = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+            p = C.c_void_p()
+            rc = L.ro_hss1d_build(int(self.cplx), M.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                  None if o is None else o.ctypes.data_as(C.POINTER(C.c_int)), leaf, eps,
+                                  C.byref(p))
+            if rc:
+                raise RuntimeError("ro_hss1d_build failed: %d" % rc)
+            self._p, self._own = p, True
+        self.depth = L.ro_hss1d_depth(self._p)
+
+    def __del__(self):
+        if getattr(self, "_own", False) and getattr(self, "_p", None):
+            self._L.ro_hss1d_free(self._p)
+            self._p = None
+
+    def node(self, level, j):
+        """(lo, hi, a, k, skeleton rows, T) of node (level, j)."""
+        lo, hi, a, k = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        if self._L.ro_hss1d_node(self._p, level, j, C.byref(lo), C.byref(hi), C.byref(a), C.byref(k), None, None):
+            raise IndexError((level, j))
+        sk = np.zeros(max(k.value, 1), dtype=np.int32)
+        dt = np.complex128 if self.cplx else np.float64
+        T = np.zeros(max(k.value * (a.value - k.value), 1), dtype=dt)
+        self._L.ro_hss1d_node(self._p, level, j, None, None, None, None, sk.ctypes.data_as(C.POINTER(C.c_int)),
+                              T.ctypes.data_as(C.POINTER(C.c_double)))
+        return (lo.value, hi.value, a.value, k.value, sk[: k.value],
+                T[: k.value * (a.value - k.value)].reshape(k.value, a.value - k.value))
+
+    def entries(self):
+        return self._L.ro_hss1d_entries(self._p)
+
+    def apply(self, x):
+        x = np.asarray(x)
+        one = x.ndim == 1
+        dt = np.complex128 if self.cplx else np.float64
+        X = np.ascontiguousarray(x.reshape(x.shape[0], -1), dtype=dt)
+        Y = np.zeros_like(X)
+        if self._L.ro_hss1d_apply(self._p, X.ctypes.data_as(C.POINTER(C.c_double)), X.shape[1],
+                                  Y.ctypes.data_as(C.POINTER(C.c_double))):
+            raise RuntimeError("ro_hss1d_apply failed")
+        return Y[:, 0] if one else Y
+
+
 class Factorization:
     """Dense-block HSS inverse built by ro_factor (Algorithm 1)."""
 
     def __init__(self, n, leaf, eps, a=None, b=None, kind=LAPLACE, kappa=0.0, proxy_points=64,
-                 proxy_radius_factor=1.5, near_all=False, threads=0, max_levels=0):
+                 proxy_radius_factor=1.5, near_all=False, threads=0, max_levels=0, k_cut=0, hss_leaf=64):
         L = self._L = lib()
         o = _Opts()
         L.ro_opts_default(C.byref(o))
         o.kind, o.kappa, o.proxy_points = kind, kappa, proxy_points
         o.proxy_radius_factor, o.near_all, o.threads = proxy_radius_factor, int(near_all), threads
-        o.max_levels = max_levels
+        o.max_levels, o.k_cut, o.hss_leaf = max_levels, k_cut, hss_leaf
         self.n, self.leaf, self.eps, self.kind, self.kappa = n, leaf, eps, kind, kappa
         N = n * n
         self.a, self.b = _f64(a, N), _f64(b, N)
@@ -229,6 +296,34 @@ class Factorization:
     def E(self, level, box):
         k = self.sizes(level, box)[1]
         return self._mat("ro_box_E", level, box, (k, k))
+
+    def box_hss(self, level, box, which):
+        """HSS1D form of phi^{sk} (which 0), phi^{rs} (1) or E (2) of a compressed box, or None."""
+        p = self._L.ro_box_hss(self._p, level, box, which)
+        if not p:
+            return None
+        h = HSS1D(None, _handle=C.c_void_p(p), _owner=self)
+        h.cplx = self.cplx
+        return h
+
+    def lr_rank(self, level, box, which):
+        """Rank of the low-rank phi^{s<-r} (0), phi^{r<-s} (1) or T (2) of a compressed box (-1: dense)."""
+        return self._L.ro_box_lr_rank(self._p, level, box, which)
+
+    def order(self, level, box, which):
+        """Sec. 3.1 order: skeleton indices cyclically (which 0) or residual indices along the interface (1)."""
+        m, k, _, _ = self.sizes(level, box)
+        cnt = k if which == 0 else m - k
+        out = np.zeros(max(cnt, 1), dtype=np.int32)
+        if self._L.ro_box_order(self._p, level, box, which, out.ctypes.data_as(C.POINTER(C.c_int))):
+            raise IndexError((level, box))
+        return out[:cnt]
+
+    def compressed_entries(self):
+        """(stored scalars of the compressed forms, scalars the same blocks take densely)."""
+        d = C.c_int64()
+        c = self._L.ro_compressed_entries(self._p, C.byref(d))
+        return c, d.value
 
     def root_inv(self):
         m = self._L.ro_root_size(self._p)

@@ -31,6 +31,40 @@
 #include <omp.h>
 #endif
 
+/* HSS1D form (Sec. 3.2) of an explicit n x n matrix M on a one-dimensional ordering of
+ * its indices: binary tree over runs of the ordering, node (l, j) covering positions
+ * [floor(j n / 2^l), floor((j+1) n / 2^l)); the telescoping factorization of Eq. 2.9
+ * with one ID per node serving its block row and block column. */
+typedef struct {
+    int lo, hi;        /* position range                                        */
+    int a, k;          /* active size, skeleton size                            */
+    int* act;          /* a row indices of M (leaf: positions lo..hi-1; above:
+                          skeleton rows of child 1 then child 2)                */
+    int* sk;           /* k local indices, ascending                            */
+    int* rs;           /* a - k local indices, ascending                        */
+    void* T;           /* k x (a-k) row-major scalars                           */
+} ro_hnode;
+
+struct ro_hss {
+    int cplx, n, depth, leaf;
+    int* order;        /* position -> row of M                                   */
+    ro_hnode** node;   /* node[l][j], l = 1..depth                               */
+    void** B12;        /* internal node (l, j), l < depth, heap index 2^l-1+j:
+                          M(skeleton of child 1, skeleton of child 2)            */
+    void** B21;        /* M(skeleton of child 2, skeleton of child 1)            */
+    void** D;          /* leaf j: M(act, act), a x a row-major; depth 0: D[0] = M */
+};
+
+/* Low-rank form X ~ X(:, sk) [I T] (columns permuted back) of a p x q matrix, from a
+ * column ID of X (Sec. 3.2, low-rank blocks). */
+typedef struct {
+    int p, q, k;
+    int* sk;           /* k column indices, ascending      */
+    int* rs;           /* q - k column indices, ascending  */
+    void* C;           /* X(:, sk), p x k row-major         */
+    void* T;           /* k x (q-k) row-major               */
+} ro_lr;
+
 typedef struct {
     int m, k, r, nnear;
     int64_t* active;   /* m globals                        */
@@ -41,6 +75,14 @@ typedef struct {
     double* T;         /* k x (m-k) scalars                */
     double* Finv;      /* m x m scalars                    */
     double* E;         /* k x k scalars                    */
+    /* extra compression of Sec. 3 (k > k_cut): the blocks of Phi = Pi^T F^{-1} Pi,
+     * E and T in compressed form; the inverse apply then uses these */
+    int hss;
+    ro_hss* H_ss;      /* phi^{sk}, skeleton in cyclic order around the box      */
+    ro_hss* H_rr;      /* phi^{rs}, residual in order along the interface        */
+    ro_hss* H_E;       /* E, cyclic order                                        */
+    ro_lr L_sr, L_rs;  /* phi^{s<-r}, phi^{r<-s}                                 */
+    ro_lr L_T;         /* T                                                      */
 } ro_box;
 
 struct ro_op {
@@ -210,6 +252,72 @@ static uint64_t pivot_key(double v)
     return u & ~((UINT64_C(1) << 40) - 1);
 }
 
+/* ------------------------------------------------------------------ orders of Sec. 3.1 */
+
+/* Skeleton points of box (l, j) ordered cyclically around the box: by angle about the box
+ * centre, counter-clockwise from the positive x1 axis; points on one ray by distance, then
+ * by grid index.  Decided on integer offsets in units of h/2 (exact). */
+typedef struct { int64_t dx, dy, g; int idx; } cyc_key;
+
+static int cyc_cmp(const void* pa, const void* pb)
+{
+    const cyc_key* a = (const cyc_key*)pa;
+    const cyc_key* b = (const cyc_key*)pb;
+    int ha = (a->dy < 0) || (a->dy == 0 && a->dx < 0);
+    int hb = (b->dy < 0) || (b->dy == 0 && b->dx < 0);
+    if (ha != hb) return ha - hb;
+    int64_t cr = a->dx * b->dy - a->dy * b->dx;
+    if (cr != 0) return cr > 0 ? -1 : 1;
+    int64_t ra = a->dx * a->dx + a->dy * a->dy, rb = b->dx * b->dx + b->dy * b->dy;
+    if (ra != rb) return ra < rb ? -1 : 1;
+    return (a->g > b->g) - (a->g < b->g);
+}
+
+static void box_cyclic_order(const ro_op* op, int l, int j, const int64_t* pts, int cnt, int* order)
+{
+    int bx, by, wx, wy;
+    box_int(op->n, l, j, &bx, &by, &wx, &wy);
+    int64_t cx2 = (int64_t)(2 * bx + 1) * wx, cy2 = (int64_t)(2 * by + 1) * wy;
+    cyc_key* key = (cyc_key*)malloc(sizeof(cyc_key) * (size_t)(cnt + 1));
+    for (int i = 0; i < cnt; ++i) {
+        int64_t g = pts[i];
+        key[i].dx = 2 * (g % op->n) + 1 - cx2;
+        key[i].dy = 2 * (g / op->n) + 1 - cy2;
+        key[i].g = g;
+        key[i].idx = i;
+    }
+    qsort(key, (size_t)cnt, sizeof(cyc_key), cyc_cmp);
+    for (int i = 0; i < cnt; ++i) order[i] = key[i].idx;
+    free(key);
+}
+
+/* Residual points of a box of level l ordered along the interface between its children:
+ * a box at even depth is split along x1, so its interface runs along x2 and the points are
+ * ordered by (i2, i1); at odd depth by (i1, i2). */
+typedef struct { int64_t major, minor; int idx; } ifc_key;
+
+static int ifc_cmp(const void* pa, const void* pb)
+{
+    const ifc_key* a = (const ifc_key*)pa;
+    const ifc_key* b = (const ifc_key*)pb;
+    if (a->major != b->major) return a->major < b->major ? -1 : 1;
+    return (a->minor > b->minor) - (a->minor < b->minor);
+}
+
+static void box_interface_order(const ro_op* op, int l, const int64_t* pts, int cnt, int* order)
+{
+    ifc_key* key = (ifc_key*)malloc(sizeof(ifc_key) * (size_t)(cnt + 1));
+    for (int i = 0; i < cnt; ++i) {
+        int64_t i1 = pts[i] % op->n, i2 = pts[i] / op->n;
+        key[i].major = (l % 2 == 0) ? i2 : i1;
+        key[i].minor = (l % 2 == 0) ? i1 : i2;
+        key[i].idx = i;
+    }
+    qsort(key, (size_t)cnt, sizeof(ifc_key), ifc_cmp);
+    for (int i = 0; i < cnt; ++i) order[i] = key[i].idx;
+    free(key);
+}
+
 /* ------------------------------------------------------------------ numeric core x2 */
 
 #define SC double
@@ -251,6 +359,8 @@ void ro_opts_default(ro_opts* o)
     o->near_all = 0;
     o->threads = 0;
     o->max_levels = 0;
+    o->k_cut = 0;
+    o->hss_leaf = 64;
 }
 
 int ro_id(int cplx, const double* Y, int r, int m, double eps, int* k_out, int* perm, double* T)
@@ -335,6 +445,7 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
     if (o.kind != 0 && o.kind != 1) return -1;
     if (o.kind == 0 && b) return -1;
     if (o.proxy_points < 0) return -1;
+    if (o.k_cut > 0 && o.hss_leaf < 1) return -1;
     int64_t N = (int64_t)n * n;
     ro_op* op = (ro_op*)calloc(1, sizeof(ro_op));
     op->n = n; op->leaf = leaf_side; op->d = 2 * L; op->h = 1.0 / n; op->eps = eps; op->opts = o;
@@ -407,6 +518,12 @@ int ro_solve(const ro_op* op, const double* f, int nrhs, double* x)
     return rc;
 }
 
+static void lr_free(ro_lr* L)
+{
+    free(L->sk); free(L->rs); free(L->C); free(L->T);
+    memset(L, 0, sizeof *L);
+}
+
 void ro_free(ro_op* op)
 {
     if (!op) return;
@@ -417,6 +534,8 @@ void ro_free(ro_op* op)
                 ro_box* B = &op->lev[l][j];
                 free(B->active); free(B->near); free(B->skel); free(B->sk_local); free(B->rs_local);
                 free(B->T); free(B->Finv); free(B->E);
+                ro_hss1d_free(B->H_ss); ro_hss1d_free(B->H_rr); ro_hss1d_free(B->H_E);
+                lr_free(&B->L_sr); lr_free(&B->L_rs); lr_free(&B->L_T);
             }
             free(op->lev[l]);
         }
@@ -589,4 +708,132 @@ int ro_matvec(int n, int kind, double kappa, const double* a, const double* b, c
     int rc = ro_matvec_rows(n, kind, kappa, a, b, x, nrhs, rows, (int)N, y);
     free(rows);
     return rc;
+}
+
+/* ------------------------------------------------------------------ HSS1D (Sec. 3) */
+
+int ro_hss1d_build(int cplx, const double* M, int n, const int* order, int leaf, double eps,
+                   ro_hss** out)
+{
+    if (!M || !out || n < 1 || leaf < 1 || eps < 0.0) return -1;
+    if (order) {
+        char* seen = (char*)calloc((size_t)n, 1);
+        for (int p = 0; p < n; ++p) {
+            if (order[p] < 0 || order[p] >= n || seen[order[p]]) { free(seen); return -1; }
+            seen[order[p]] = 1;
+        }
+        free(seen);
+    }
+    ro_hss* h = (ro_hss*)calloc(1, sizeof(ro_hss));
+    int rc = cplx ? hss_build_z((const double complex*)M, n, order, leaf, eps, h)
+                  : hss_build_d(M, n, order, leaf, eps, h);
+    if (rc) { ro_hss1d_free(h); return rc; }
+    *out = h;
+    return 0;
+}
+
+int ro_hss1d_apply(const ro_hss* h, const double* x, int nrhs, double* y)
+{
+    if (!h || !x || !y || nrhs < 1) return -1;
+    if (h->cplx) hss_apply_z(h, (const double complex*)x, nrhs, (double complex*)y);
+    else hss_apply_d(h, x, nrhs, y);
+    return 0;
+}
+
+int ro_hss1d_depth(const ro_hss* h) { return h ? h->depth : -1; }
+
+int ro_hss1d_node(const ro_hss* h, int level, int j, int* lo, int* hi, int* a, int* k,
+                  int* skel_rows, double* T)
+{
+    if (!h || level < 1 || level > h->depth || j < 0 || j >= (1 << level)) return -1;
+    const ro_hnode* q = &h->node[level][j];
+    if (lo) *lo = q->lo;
+    if (hi) *hi = q->hi;
+    if (a) *a = q->a;
+    if (k) *k = q->k;
+    if (skel_rows)
+        for (int s = 0; s < q->k; ++s) skel_rows[s] = q->act[q->sk[s]];
+    if (T) memcpy(T, q->T, (h->cplx ? 2 : 1) * sizeof(double) * (size_t)q->k * (size_t)(q->a - q->k));
+    return 0;
+}
+
+int64_t ro_hss1d_entries(const ro_hss* h)
+{
+    if (!h) return -1;
+    int t = h->depth;
+    if (t == 0) return (int64_t)h->n * h->n;
+    int64_t e = 0;
+    for (int l = 1; l <= t; ++l)
+        for (int j = 0; j < (1 << l); ++j) e += (int64_t)h->node[l][j].k * (h->node[l][j].a - h->node[l][j].k);
+    for (int l = 0; l < t; ++l)
+        for (int j = 0; j < (1 << l); ++j) e += 2 * (int64_t)h->node[l + 1][2 * j].k * h->node[l + 1][2 * j + 1].k;
+    for (int j = 0; j < (1 << t); ++j) e += (int64_t)h->node[t][j].a * h->node[t][j].a;
+    return e;
+}
+
+void ro_hss1d_free(ro_hss* h)
+{
+    if (!h) return;
+    int t = h->depth;
+    if (h->node)
+        for (int l = 1; l <= t; ++l) {
+            if (!h->node[l]) continue;
+            for (int j = 0; j < (1 << l); ++j) {
+                ro_hnode* q = &h->node[l][j];
+                free(q->act); free(q->sk); free(q->rs); free(q->T);
+            }
+            free(h->node[l]);
+        }
+    int nint = (1 << t);
+    if (h->B12) for (int i = 0; i < nint; ++i) free(h->B12[i]);
+    if (h->B21) for (int i = 0; i < nint; ++i) free(h->B21[i]);
+    if (h->D) for (int i = 0; i < nint; ++i) free(h->D[i]);
+    free(h->node); free(h->B12); free(h->B21); free(h->D); free(h->order);
+    free(h);
+}
+
+const ro_hss* ro_box_hss(const ro_op* op, int level, int j, int which)
+{
+    const ro_box* B = getbox(op, level, j);
+    if (!B || !B->hss) return NULL;
+    return which == 0 ? B->H_ss : which == 1 ? B->H_rr : which == 2 ? B->H_E : NULL;
+}
+
+int ro_box_lr_rank(const ro_op* op, int level, int j, int which)
+{
+    const ro_box* B = getbox(op, level, j);
+    if (!B || !B->hss) return -1;
+    return which == 0 ? B->L_sr.k : which == 1 ? B->L_rs.k : which == 2 ? B->L_T.k : -1;
+}
+
+int ro_box_order(const ro_op* op, int level, int j, int which, int* out)
+{
+    const ro_box* B = getbox(op, level, j);
+    if (!B || !out || (which != 0 && which != 1)) return -1;
+    if (which == 0) { box_cyclic_order(op, level, j, B->skel, B->k, out); return 0; }
+    int nr = B->m - B->k;
+    int64_t* rg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nr + 1));
+    for (int c = 0; c < nr; ++c) rg[c] = B->active[B->rs_local[c]];
+    box_interface_order(op, level, rg, nr, out);
+    free(rg);
+    return 0;
+}
+
+static int64_t lr_entries(const ro_lr* L) { return (int64_t)L->p * L->k + (int64_t)L->k * (L->q - L->k); }
+
+int64_t ro_compressed_entries(const ro_op* op, int64_t* dense_entries)
+{
+    if (!op) return -1;
+    int64_t c = 0, d = 0;
+    for (int l = 1; l <= op->d; ++l)
+        for (int j = 0; j < (1 << l); ++j) {
+            const ro_box* B = &op->lev[l][j];
+            if (!B->hss) continue;
+            int64_t m = B->m, k = B->k;
+            d += m * m + k * k + k * (m - k);
+            c += ro_hss1d_entries(B->H_ss) + ro_hss1d_entries(B->H_rr) + ro_hss1d_entries(B->H_E) +
+                 lr_entries(&B->L_sr) + lr_entries(&B->L_rs) + lr_entries(&B->L_T);
+        }
+    if (dense_entries) *dense_entries = d;
+    return c;
 }

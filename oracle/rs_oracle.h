@@ -41,7 +41,14 @@ typedef struct {
     int threads;                 /* OpenMP threads over the boxes of a level (<=0: default) */
     int max_levels;              /* >0: factor only the max_levels finest levels and stop
                                     (a bounded sample for timing; ro_solve then refuses)   */
+    int k_cut;                   /* >0: boxes with k > k_cut keep phi^{sk}, phi^{rs} and E
+                                    in HSS1D form and phi^{s<-r}, phi^{r<-s}, T in low-rank
+                                    form (Sec. 3), compressed at eps from the dense blocks;
+                                    ro_solve uses these forms for those boxes              */
+    int hss_leaf;                /* largest leaf run of the HSS1D trees                    */
 } ro_opts;
+
+typedef struct ro_hss ro_hss;
 
 void ro_opts_default(ro_opts* o);
 
@@ -87,6 +94,37 @@ int ro_box_Finv(const ro_op* op, int level, int box, double* out);  /* m x m    
 int ro_box_E(const ro_op* op, int level, int box, double* out);     /* k x k            */
 int ro_root_size(const ro_op* op);
 int ro_root_inv(const ro_op* op, double* out);
+
+/* HSS1D compression (Sec. 3.2) of an explicit n x n matrix M (row-major; complex:
+ * interleaved) along the ordering order[position] = row (NULL: identity).  The tree halves
+ * runs of positions until they hold at most `leaf`; node (l, j) covers positions
+ * [floor(j n/2^l), floor((j+1) n/2^l)).  Each node's active columns (leaf: its positions;
+ * above: the children's skeletons) get one ID at eps of [M(out, act); M(act, out)^T]
+ * (out = every position outside the node), giving the telescoping form of Eq. 2.9. */
+int ro_hss1d_build(int cplx, const double* M, int n, const int* order, int leaf, double eps,
+                   ro_hss** out);
+/* y = M x through the HSS1D form; x, y: n x nrhs row-major, indexed by row of M. */
+int ro_hss1d_apply(const ro_hss* h, const double* x, int nrhs, double* y);
+int ro_hss1d_depth(const ro_hss* h);
+/* Node (level 1..depth, j): position range, active and skeleton sizes; skel_rows (k rows of
+ * M, ascending local order) and T (k x (a-k) row-major) when non-NULL. */
+int ro_hss1d_node(const ro_hss* h, int level, int j, int* lo, int* hi, int* a, int* k,
+                  int* skel_rows, double* T);
+/* Scalars stored by the form (T blocks, sibling blocks, leaf blocks). */
+int64_t ro_hss1d_entries(const ro_hss* h);
+void ro_hss1d_free(ro_hss* h);
+
+/* Compressed blocks of box (level, j) when the factorization ran with k_cut (NULL / -1
+ * otherwise): which = 0 phi^{sk}, 1 phi^{rs}, 2 E for the HSS1D forms; low-rank ranks
+ * which = 0 phi^{s<-r}, 1 phi^{r<-s}, 2 T. */
+const ro_hss* ro_box_hss(const ro_op* op, int level, int j, int which);
+int ro_box_lr_rank(const ro_op* op, int level, int j, int which);
+/* Orders of Sec. 3.1 for box (level, j): which = 0 skeleton cyclically around the box
+ * (k entries: skeleton index at each position), 1 residual along the interface (m-k). */
+int ro_box_order(const ro_op* op, int level, int j, int which, int* out);
+/* Stored scalars of the compressed boxes' forms; *dense_entries (optional) receives what
+ * the same blocks take densely (m^2 + k^2 + k(m-k) per box). */
+int64_t ro_compressed_entries(const ro_op* op, int64_t* dense_entries);
 
 /* Brute-force y = A x over all N x N entries (nrhs columns, grid order). */
 int ro_matvec(int n, int kind, double kappa, const double* a, const double* b,

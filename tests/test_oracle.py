@@ -325,12 +325,19 @@ def _pins_fail(O):
         _, perm, _ = O.interp_decomp(Z, 1e-14)
         if not np.array_equal(perm[:25], sl.qr(Z, mode="economic", pivoting=True)[2][:25]):
             return True
+        # HSS1D (Sec. 3.2) of a non-symmetric semiseparable matrix reproduces M x to rounding
+        rng = np.random.default_rng(12)
+        u, v, p, q = rng.standard_normal((4, 160))
+        M = np.tril(np.outer(u, v), -1) + np.triu(np.outer(p, q), 1) + np.diag(2 + rng.uniform(0, 1, 160))
+        X = rng.standard_normal((160, 2))
+        if np.linalg.norm(O.HSS1D(M, leaf=16, eps=1e-13).apply(X) - M @ X) > 1e-11 * np.linalg.norm(M @ X):
+            return True
     except Exception:
         return True
     return False
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7])
 def test_planted_mistake_is_caught(oracle_mod, tmp_path, plant):
     path = oracle_mod.build(plant=plant, out=str(tmp_path / ("plant%d.so" % plant)))
     L = oracle_mod.load(path)
