@@ -70,11 +70,17 @@ typedef struct {
     rs_precision precision;      /* arithmetic of the factorization                  [FP64] */
     double refine_tol;           /* target relative residual of the refined solve    [1e-10]*/
     int refine_max_iter;         /* refinement cap; past it RS_E_NOT_CONVERGED        [10]   */
-    int64_t k_cut;               /* skeleton size above which blocks are HSS-compressed
-                                    (paper's remark on k_cut, Sec. 4); 0 = never     [0]    */
+    int64_t k_cut;               /* extra compression of Sec. 3: boxes whose skeleton has
+                                    more than k_cut points keep phi^{sk}, phi^{rs} (the
+                                    diagonal blocks of Pi^T F^{-1} Pi) and E in HSS1D form
+                                    and phi^{s<-r}, phi^{r<-s} and T in low-rank form, each
+                                    compressed at eps from its dense block after the
+                                    factorization; the solve then applies those forms.
+                                    0 = never                                        [0]    */
     int64_t spin_limit;          /* iteration cap of every device-side wait          [2^26] */
     int profile;                 /* 1: time every kernel launch with CUDA events on the
                                     launch stream (rs_op_profile)                     [0]    */
+    int hss_leaf;                /* largest leaf run of the HSS1D trees (k_cut > 0)  [64]   */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);
@@ -168,6 +174,10 @@ typedef struct {
     double ms_inverse;           /* wall time of the inversion phase                       */
     int refine_iters;            /* RS_MIXED_FP32: low-precision solves of the last rs_solve */
     double refine_residual;      /* RS_MIXED_FP32: its final max relative FP64 residual     */
+    int64_t compressed_boxes;    /* boxes in the compressed form of Sec. 3 (opts.k_cut)     */
+    int64_t bytes_compressed;    /* device bytes of their compressed forms                 */
+    int64_t bytes_dense_replaced;/* bytes the same blocks (Phi, E, T) take densely         */
+    double ms_compress;          /* wall time of the compression                           */
 } rs_stats;
 int rs_op_stats(const rs_op* op, rs_stats* out);
 
@@ -198,8 +208,29 @@ int rs_op_box_sizes(const rs_op* op, int level, int box, int64_t* m, int64_t* k,
                     int64_t* nnear);
 /* which: 0 = active set (m), 1 = near rows (nnear), 2 = skeleton ascending in g (k). */
 int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* out);
+/* Orders of Sec. 3.1 used by the extra compression (available for every box): which = 0,
+ * the skeleton (k entries: index into the skeleton ascending in g) by angle about the box
+ * centre, counter-clockwise from the +x1 direction, ties on one ray by distance then g;
+ * which = 1, the residual points (m - k entries: index into the residual in ascending
+ * active position) along the interface between the box's children, i.e. by (i2, i1) when
+ * the level is even and by (i1, i2) when it is odd. */
+int rs_op_box_order(const rs_op* op, int level, int box, int which, int64_t* out);
+/* The same orders for caller-given points of box (level, box) of a tree (no GPU needed):
+ * g: host, cnt grid indices; out: host, cnt entries, out[p] = index into g of the point at
+ * position p.  which = 0 cyclic order, 1 interface order. */
+int rs_tree_box_order(const rs_tree* tree, int level, int box, int which, const int64_t* g, int64_t cnt,
+                      int64_t* out);
+/* Compressed form of one block of a box compressed under opts.k_cut (RS_E_INVALID for other
+ * boxes).  which: 0 phi^{sk}, 1 phi^{rs}, 2 E (HSS1D), 3 phi^{s<-r}, 4 phi^{r<-s}, 5 T (low
+ * rank).  depth: HSS1D tree depth (-1 for a low-rank form); entries: stored scalars.  nodes
+ * (optional; size 4 x (2^(depth+1) - 1), or 4 for a low-rank form): per node in level order
+ * (levels 1..depth, or the single node of a depth-0 tree or a low-rank form) its position
+ * range lo, hi, its active size a and its rank k. */
+int rs_op_box_form(const rs_op* op, int level, int box, int which, int* depth, int64_t* entries,
+                   int64_t* nodes);
 /* which: 0 = T (k x (m-k), rows by skeleton ascending in g, columns by residual in active
- * order), 1 = F^{-1} (m x m, active order), 2 = E (k x k, skeleton order); row-major. */
+ * order), 1 = F^{-1} (m x m, active order), 2 = E (k x k, skeleton order); row-major.
+ * RS_E_INVALID for a level whose dense blocks were released after compression (k_cut). */
 int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out);
 /* Root inverse F_root^{-1} (root_m x root_m, active order = skeletons of boxes (1,0) then
  * (1,1)), row-major. */
@@ -214,8 +245,8 @@ int rs_op_root_matrix(const rs_op* op, double* out);
  * in-flight request by one tree level per tick; each stage of a tick is one launch for all
  * requests in that phase, whatever their operator or nrhs.  A finished request frees its
  * memory at once and waiting requests join at the next tick.  Results equal rs_solve's.
- *   ops: RS_FP64 Laplace operators on one device; they stay owned by the caller but cannot be
- *   freed (rs_free returns RS_E_INVALID) until rs_server_free.
+ *   ops: RS_FP64 Laplace operators on one device, factored without k_cut; they stay owned by
+ *   the caller but cannot be freed (rs_free returns RS_E_INVALID) until rs_server_free.
  *   mem_budget_bytes: device memory reserved for request workspace (allocated once).
  * --------------------------------------------------------------------------------------- */
 int rs_server_create(rs_op* const* ops, int n_ops, size_t mem_budget_bytes, int max_inflight, rs_server** out);
@@ -235,6 +266,37 @@ int rs_server_stats(rs_server* s, int64_t* submitted, int64_t* completed, int64_
 int rs_server_latencies(rs_server* s, double* out_ms, int64_t max, int64_t* n);
 /* Finish the queued work, stop the scheduler and release the server. */
 void rs_server_free(rs_server* s);
+
+/* ---------------------------------------------------------------------------------------
+ * HSS1D form of an explicit matrix (Sec. 3.2: the dense-block HSS compression that the extra
+ * compression of rs_factor uses, exposed on its own).  Positions p = 0..n-1 of the ordering
+ * order[p] (an index of M) are split into halving runs: node (l, j) covers positions
+ * [floor(j n / 2^l), floor((j+1) n / 2^l)) and the tree stops at the first depth whose runs
+ * hold at most `leaf` positions.  Each node's active indices (a leaf's positions; above, the
+ * skeletons of its two children) get one interpolative decomposition at eps (a column-pivoted
+ * QR step is kept while |R_ss| > eps |R_00|) of its block column stacked on its transposed
+ * block row against every index outside the node, so that one skeleton serves both, and M is
+ * held in the telescoping form of Eq. 2.9: interpolation blocks T per node, sibling blocks
+ * between the skeletons of each node's two children, and dense leaf blocks.
+ * --------------------------------------------------------------------------------------- */
+typedef struct rs_hss rs_hss;
+/* M: host or device, n x n column-major, double or (cplx = 1) interleaved complex128.
+ * order: host, n entries forming a permutation of 0..n-1, or NULL (identity).  leaf >= 1,
+ * eps >= 0.  The form lives on the current device until rs_hss1d_free.  Synchronous. */
+int rs_hss1d_build(const void* M, int64_t n, int cplx, const int64_t* order, int leaf, double eps,
+                   void* stream, rs_hss** out);
+/* y = M x through the form; x, y: n x nrhs column-major, both host or both device, y may not
+ * alias x.  Host buffers: returns when y is written; device buffers: when the work is
+ * enqueued on `stream`. */
+int rs_hss1d_apply(rs_hss* h, const void* x, int64_t nrhs, void* y, void* stream);
+/* depth, stored scalars and device bytes of the form (any output may be NULL). */
+int rs_hss1d_info(const rs_hss* h, int* depth, int64_t* entries, int64_t* bytes);
+/* Node (level 1..depth, j < 2^level; a depth-0 tree has the single node (0, 0)): position
+ * range, active size and rank; skel_rows (optional, k entries): the skeleton as indices of M,
+ * ascending in active position. */
+int rs_hss1d_node(const rs_hss* h, int level, int node, int64_t* lo, int64_t* hi, int64_t* a,
+                  int64_t* k, int64_t* skel_rows);
+int rs_hss1d_free(rs_hss* h);
 
 #ifdef __cplusplus
 }

@@ -39,14 +39,15 @@ class rs_kernel(C.Structure):
 class rs_opts(C.Structure):
     _fields_ = [("proxy_points", C.c_int), ("proxy_radius_factor", C.c_double), ("precision", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max_iter", C.c_int), ("k_cut", C.c_int64),
-                ("spin_limit", C.c_int64), ("profile", C.c_int)]
+                ("spin_limit", C.c_int64), ("profile", C.c_int), ("hss_leaf", C.c_int)]
 
 
 class rs_stats(C.Structure):
     _fields_ = [("depth", C.c_int), ("n_side", C.c_int64), ("root_m", C.c_int64), ("bytes_factors", C.c_int64),
                 ("bytes_workspace", C.c_int64), ("flops_factor", C.c_double), ("flops_solve_per_rhs", C.c_double),
                 ("bytes_solve", C.c_double), ("ms_tree", C.c_double), ("ms_inverse", C.c_double),
-                ("refine_iters", C.c_int), ("refine_residual", C.c_double)]
+                ("refine_iters", C.c_int), ("refine_residual", C.c_double), ("compressed_boxes", C.c_int64),
+                ("bytes_compressed", C.c_int64), ("bytes_dense_replaced", C.c_int64), ("ms_compress", C.c_double)]
 
 
 _lib = None
@@ -89,6 +90,14 @@ def lib():
         L.rs_op_profile.argtypes = [vp, C.c_int, dp, dp, dp, i64p]
         L.rs_launch_count.restype = C.c_int64
         L.rs_launch_count.argtypes = []
+        L.rs_op_box_order.argtypes = [vp, C.c_int, C.c_int, C.c_int, i64p]
+        L.rs_tree_box_order.argtypes = [vp, C.c_int, C.c_int, C.c_int, i64p, C.c_int64, i64p]
+        L.rs_op_box_form.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), i64p, i64p]
+        L.rs_hss1d_build.argtypes = [vp, C.c_int64, C.c_int, i64p, C.c_int, C.c_double, vp, C.POINTER(vp)]
+        L.rs_hss1d_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.rs_hss1d_info.argtypes = [vp, C.POINTER(C.c_int), i64p, i64p]
+        L.rs_hss1d_node.argtypes = [vp, C.c_int, C.c_int, i64p, i64p, i64p, i64p, i64p]
+        L.rs_hss1d_free.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -297,6 +306,80 @@ def rs_op_root_matrix(op, cplx=False):
     out = np.zeros(c * m * m)
     _check(lib().rs_op_root_matrix(op, _dp(out)))
     return (out.view(np.complex128) if cplx else out).reshape(m, m)
+
+
+def rs_op_box_order(op, level, box, which):
+    """Sec. 3.1 order of a box: skeleton indices cyclically (which 0), residual indices along
+    the interface (1)."""
+    m, k, _, _ = rs_op_box_sizes(op, level, box)
+    cnt = k if which == 0 else m - k
+    out = np.zeros(max(cnt, 1), dtype=np.int64)
+    _check(lib().rs_op_box_order(op, level, box, which, _i64p(out)))
+    return out[:cnt]
+
+
+def rs_tree_box_order(tree, level, box, which, g):
+    """Sec. 3.1 order of the grid points g of box (level, box): cyclic (which 0) or along the
+    interface (1); returns the index into g at each position."""
+    gv = np.ascontiguousarray(g, dtype=np.int64)
+    out = np.zeros(max(len(gv), 1), dtype=np.int64)
+    _check(lib().rs_tree_box_order(tree, level, box, which, _i64p(gv), len(gv), _i64p(out)))
+    return out[: len(gv)]
+
+
+def rs_op_box_form(op, level, box, which):
+    """Compressed form of a box block (which 0 phi_ss, 1 phi_rr, 2 E, 3 phi_sr, 4 phi_rs, 5 T):
+    (depth, entries, nodes) with nodes an (n, 4) array of (lo, hi, a, k)."""
+    d, e = C.c_int(), C.c_int64()
+    _check(lib().rs_op_box_form(op, level, box, which, C.byref(d), C.byref(e), None))
+    cnt = 1 if d.value <= 0 else (1 << (d.value + 1)) - 2
+    nodes = np.zeros(4 * cnt, dtype=np.int64)
+    _check(lib().rs_op_box_form(op, level, box, which, C.byref(d), C.byref(e), _i64p(nodes)))
+    return d.value, e.value, nodes.reshape(cnt, 4)
+
+
+def rs_hss1d_build(M, order=None, leaf=64, eps=1e-10, stream=None):
+    """HSS1D form of the square matrix M: a numpy array (real or complex), or a torch CUDA
+    tensor whose contiguous storage is M column-major (i.e. the tensor holds M^T).  Returns the
+    handle."""
+    if hasattr(M, "data_ptr"):
+        n = int(M.shape[0])
+        cplx = bool(M.is_complex())
+        ptr = C.c_void_p(M.data_ptr())
+    else:
+        cplx = np.iscomplexobj(M)
+        Mf = np.asfortranarray(M, dtype=np.complex128 if cplx else np.float64)
+        n = Mf.shape[0]
+        ptr = C.c_void_p(Mf.ctypes.data)
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+    out = C.c_void_p()
+    _check(lib().rs_hss1d_build(ptr, n, int(cplx), _i64p(o), int(leaf), float(eps), _stream(stream), C.byref(out)))
+    return out
+
+
+def rs_hss1d_apply(h, x, nrhs, y, stream=None):
+    """y = M x (n x nrhs column-major; both host numpy or both device torch)."""
+    _check(lib().rs_hss1d_apply(h, _ptr(x), int(nrhs), _ptr(y), _stream(stream)))
+
+
+def rs_hss1d_info(h):
+    d, e, b = C.c_int(), C.c_int64(), C.c_int64()
+    _check(lib().rs_hss1d_info(h, C.byref(d), C.byref(e), C.byref(b)))
+    return d.value, e.value, b.value
+
+
+def rs_hss1d_node(h, level, node):
+    """(lo, hi, a, k, skeleton rows) of one node."""
+    v = [C.c_int64() for _ in range(4)]
+    _check(lib().rs_hss1d_node(h, level, node, *[C.byref(x) for x in v], None))
+    k = v[3].value
+    sk = np.zeros(max(k, 1), dtype=np.int64)
+    _check(lib().rs_hss1d_node(h, level, node, None, None, None, None, _i64p(sk)))
+    return v[0].value, v[1].value, v[2].value, k, sk[:k]
+
+
+def rs_hss1d_free(h):
+    _check(lib().rs_hss1d_free(h))
 
 
 class Solver:

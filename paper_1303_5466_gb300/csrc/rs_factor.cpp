@@ -103,9 +103,11 @@ int check_status(rs_op* op, cudaStream_t st)
     return RS_OK;
 }
 
+}  // namespace
+
 // Pick the CTA group size per box for a cooperative kernel: 1 (plain launch) when the boxes
 // alone fill the GPU, otherwise as many CTAs per box as stay co-resident (at most one per
-// 32 columns and 64 in all).
+// 32 columns and 1024 in all).
 int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
 {
     const int gmax = std::max(1, std::min(max_cols / 32, 1024));
@@ -115,6 +117,8 @@ int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
     while (G > 1 && nb * G > capacity(G)) --G;
     return std::max(G, 1);
 }
+
+namespace {
 
 // Workspace of the ID phase, released when rs_factor returns.
 struct IdWork {
@@ -405,6 +409,7 @@ int solve_plan(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     std::vector<int64_t> bphi, bT, bE, bTt;
     int64_t nphi = 0, nT = 0, nE = 0, nTt = 0;
     for (int b = 0; b < nb; ++b) {
+        if (!L.cmp.empty() && L.cmp[b]) continue;   // applied through its compressed forms
         const int m = (int)L.m[b], k = (int)L.k[b];
         add_mv(vphi, bphi, nphi, m, m, m, 0, L.phi_off[b], L.act_off[b], L.act_off[b], 1.0, 0.0);
         if (m - k > 0) add_mv(vT, bT, nT, k, m - k, k, 0, L.t_off[b], L.act_off[b] + k, L.k_off[b], 1.0, 1.0);
@@ -423,8 +428,8 @@ void compute_stats(rs_op* op)
     s.depth = op->d;
     s.n_side = op->n;
     s.root_m = op->lev[0].m[0];
-    double ff = 0.0, fs = 0.0, bs = 0.0;
-    int64_t bytes = 0;
+    double ff = 0.0, sw = 0.0;
+    int64_t bytes = 0, cboxes = 0, replaced = 0;
     for (int l = 1; l <= op->d; ++l) {
         const Level& L = op->lev[l];
         for (int b = 0; b < L.nb; ++b) {
@@ -434,20 +439,30 @@ void compute_stats(rs_op* op)
             ff += 2.0 * m * m * m;                                                // F^{-1}
             ff += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;                  // W, E^{-1}
             ff += 2.0 * k * k * k;                                                // E
-            fs += 2.0 * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
-            bs += op->esz * (2.0 * m * m + 2.0 * k * k + 2.0 * k * (m - k));
+            if (!L.cmp.empty() && L.cmp[b]) {
+                ++cboxes;
+                replaced += (int64_t)(m * m + k * k + k * (m - k)) * op->esz;
+            }
         }
-        bytes += (L.phi_off.back() + L.e_off.back() + L.t_off.back()) * op->esz + L.act_off.back() * 8 + L.nb * 64;
+        // entries read by one apply: Phi, E up and down, T and T^T, dense and compressed parts
+        sw += 2.0 * L.mvw_phi + L.mvw_T + 2.0 * L.mvw_E + L.mvw_Tt;
+        sw += 2.0 * L.p_phi.work + L.p_T.work + 2.0 * L.p_E.work + L.p_Tt.work;
+        if (!L.dense_freed)
+            bytes += (L.phi_off.back() + L.e_off.back() + L.t_off.back()) * op->esz;
+        bytes += L.act_off.back() * 8 + L.nb * 64;
     }
     const double m0 = (double)op->lev[0].m[0];
     ff += 2.0 * m0 * m0 * m0;
-    fs += 2.0 * m0 * m0;
-    bs += op->esz * m0 * m0;
+    sw += m0 * m0;
     bytes += (int64_t)(m0 * m0 * op->esz);
+    bytes += op->cstore_n * op->esz;
     s.flops_factor = ff;
-    s.flops_solve_per_rhs = fs;
-    s.bytes_solve = bs;
+    s.flops_solve_per_rhs = 2.0 * sw;
+    s.bytes_solve = op->esz * sw;
     s.bytes_factors = bytes;
+    s.compressed_boxes = cboxes;
+    s.bytes_compressed = op->cstore_n * op->esz;
+    s.bytes_dense_replaced = replaced;
 }
 
 }  // namespace
@@ -491,6 +506,7 @@ int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
     if ((rc = upload(R.d_perm, R.perm, st))) return rc;
     if ((rc = upload(R.d_m, to32(R.m), st))) return rc;
     if ((rc = inverse_level<T>(op, R, &op->lev[1], st))) return rc;
+    if ((rc = compress_levels<T>(op, st))) return rc;
     for (int l = 0; l <= op->d; ++l)
         if ((rc = solve_plan(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
     RS_CUDA(cudaStreamSynchronize(st));
@@ -535,6 +551,8 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         return fail(RS_E_INVALID, "bad proxy options");
     if (!(eps >= 0.0) || !(eps < 1.0)) return fail(RS_E_INVALID, "eps must be in [0, 1)");
     if (op->opts.spin_limit <= 0) return fail(RS_E_INVALID, "spin_limit must be positive");
+    if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
+    if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     const double h = 1.0 / (double)op->n;
     op->K.n = (int)op->n;
     op->K.h = h;
@@ -612,6 +630,12 @@ SolveLayout solve_layout(const rs_op* op, int64_t nrhs)
     Ls.n_g = Ls.goff[d + 1] * nrhs + 1;
     Ls.n_u = Ls.max_m * nrhs + 1;
     Ls.n_t = Ls.max_k * nrhs + 1;
+    int64_t zr = 0;
+    for (int l = 1; l <= d; ++l) {
+        const Level& L = op->lev[l];
+        zr = std::max({zr, L.p_phi.z_rows, L.p_T.z_rows, L.p_E.z_rows, L.p_Tt.z_rows});
+    }
+    Ls.n_z = zr * nrhs + 1;
     return Ls;
 }
 
@@ -634,7 +658,16 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
     T* U = (T*)ws.u;
     T* XO = (T*)ws.out;
     T* Tt = (T*)ws.t;
+    T* Z = (T*)ws.z;
     const int nr = (int)nrhs;
+    const double esz = (double)sizeof(T);
+    int rc;
+    // compressed boxes (Sec. 3): their part of an apply, from `in` to `out`
+    auto run_cprog = [&](const Program& p, const T* in, T* out) -> int {
+        if (p.st.empty()) return RS_OK;
+        ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * p.work * (double)nrhs, esz * p.work);
+        return run_program<T>(st, p, op->d_cstore.as<T>(), in, out, Z, nr);
+    };
     // upward pass
     for (int l = d; l >= 1; --l) {
         Level& L = op->lev[l];
@@ -642,21 +675,24 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         T* gl = Gb + goff[l] * nrhs;
         if (l == d) RS_CUDA(launch_gather_cm<IO, T>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
         else RS_CUDA(launch_gather_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, esz * L.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
                               L.d_Phi.as<T>(), U, wl, nr)); }
+        if ((rc = run_cprog(L.p_phi, U, wl))) return rc;
         RS_CUDA(launch_gather_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), wl, Tt, nr));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, 8.0 * L.mvw_T);
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, esz * L.mvw_T);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_T.as<MatvecProb>(), L.d_mv_T_blk.as<int64_t>(), L.n_mv_T, L.b_mv_T,
                               L.d_T.as<T>(), wl, Tt, nr)); }
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
+        if ((rc = run_cprog(L.p_T, wl, Tt))) return rc;
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, esz * L.mvw_E);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
                               L.d_E.as<T>(), Tt, gl, nr)); }
+        if ((rc = run_cprog(L.p_E, Tt, gl))) return rc;
     }
     // root
     {
         Level& R = op->lev[0];
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, 8.0 * R.mvw_phi);
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, esz * R.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, R.d_mv_phi.as<MatvecProb>(), R.d_mv_phi_blk.as<int64_t>(), R.n_mv_phi, R.b_mv_phi,
                               R.d_Phi.as<T>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr)); }
     }
@@ -667,17 +703,20 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         T* gl = Gb + goff[l] * nrhs;
         T* pl = Ph + goff[l] * nrhs;
         RS_CUDA(cudaMemcpyAsync(Tt, gl, sizeof(T) * (size_t)(L.sum_k * nrhs), cudaMemcpyDeviceToDevice, st));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, 8.0 * L.mvw_E);
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, esz * L.mvw_E);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
                               L.d_E.as<T>(), pl, Tt, nr)); }   // beta = 0: Tt = E phi
+        if ((rc = run_cprog(L.p_E, pl, Tt))) return rc;
         RS_CUDA(launch_axpby<T>(st, L.sum_k * nrhs, (T)-1, gl, (T)1, Tt));   // Tt = E phi - g
         RS_CUDA(launch_scatter_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), Tt, U, nr));
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, 8.0 * L.mvw_Tt);
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, esz * L.mvw_Tt);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_Tt.as<MatvecProb>(), L.d_mv_Tt_blk.as<int64_t>(), L.n_mv_Tt, L.b_mv_Tt,
                               L.d_T.as<T>(), Tt, U, nr)); }
-        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, 8.0 * L.mvw_phi);
+        if ((rc = run_cprog(L.p_Tt, Tt, U))) return rc;
+        { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, esz * L.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
                               L.d_Phi.as<T>(), U, XO, nr)); }
+        if ((rc = run_cprog(L.p_phi, U, XO))) return rc;
         RS_CUDA(launch_axpby<T>(st, L.sum_m * nrhs, (T)1, wl, (T)1, XO));   // x' = w + Phi v
         if (l == d) RS_CUDA(launch_scatter_cm<T, IO>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));
         else RS_CUDA(launch_scatter_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), XO, Ph + goff[l + 1] * nrhs, nr));
@@ -714,7 +753,8 @@ int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream
     RS_CUDA(op->s_u.alloc(e * (size_t)Ls.n_u));
     RS_CUDA(op->s_out.alloc(e * (size_t)Ls.n_u));
     RS_CUDA(op->s_t.alloc(e * (size_t)Ls.n_t));
-    SolveWork ws{op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p};
+    RS_CUDA(op->s_z.alloc(e * (size_t)Ls.n_z));
+    SolveWork ws{op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p, op->s_z.p};
     if (op->kind != RS_HELMHOLTZ) return solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
     // symmetric form: x = S (S^{-1} A S)^{-1} S^{-1} f, S = diag(kappa sqrt(b))
     using Z = cplx<double>;
@@ -873,6 +913,7 @@ int rs_op_box_matrix(const rs_op* op, int level, int box, int which, double* out
 {
     const Level* L = get_level(op, level, box);
     if (!L || !out) return fail(RS_E_INVALID, "level/box out of range");
+    if (L->dense_freed) return fail(RS_E_INVALID, "the dense blocks of this level were released after compression");
     const int64_t m = L->m[box], k = L->k[box];
     const int c = op->kind == RS_HELMHOLTZ ? 2 : 1;     // doubles per entry
     RS_CUDA(cudaSetDevice(op->device));

@@ -3,6 +3,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <vector>
 
 #include "rs_internal.h"
@@ -58,6 +59,49 @@ struct DevMem {
     template <class T> T* as() const { return (T*)p; }
 };
 
+// ------------------------------------------------------------------ extra compression (Sec. 3)
+// One node of an HSS1D form, or the single node of a low-rank form.
+struct CNode {
+    int lo = 0, hi = 0;          // HSS1D: position range
+    int a = 0, k = 0;            // active and skeleton sizes
+    std::vector<int> act;        // a indices of the matrix, in active order
+    std::vector<int> perm;       // a local indices: skeleton ascending, then residual ascending
+    int64_t t_off = 0;           // T (k x (a-k), column-major, ld k) in the compressed store
+};
+
+// Compressed form of one block, built from the block's explicit dense form.
+//   HSS1D (Sec. 3.2, the telescoping form of Eq. 2.9 on a 1D order): nodes lev[l][j] for
+//     l = 1..depth (depth 0: a single dense node at lev[0][0]); sibling blocks b12/b21 of the
+//     internal nodes (heap index 2^l - 1 + j, levels 0..depth-1) and permuted leaf blocks d_off.
+//   Low rank: X ~ X(:, sk) [I T] Pi^T from a column ID of X: lev[0][0] (a = cols), c_off.
+struct CForm {
+    bool hss = true;
+    int rows = 0, cols = 0, depth = 0;
+    std::vector<int> order;                  // HSS1D: position -> index of the matrix
+    std::vector<std::vector<CNode>> lev;
+    std::vector<int64_t> b12, b21, d_off;
+    int64_t c_off = 0;
+    int64_t entries = 0;                     // stored scalars
+    const void* M = nullptr;                 // dense source (during compression only)
+    int64_t ld = 0;
+};
+
+// One launch of a compressed apply: a row copy between the apply's buffers (0 input,
+// 1 output, 2 scratch), or a batched matvec on the scratch with the compressed store.
+struct ProgStage {
+    int kind = 0;                // 0 copy, 1 matvec
+    int src = 0, dst = 0, add = 0;
+    int64_t count = 0;           // copy: rows; matvec: blocks
+    int np = 0;                  // matvec: problems
+    DevMem a, b;                 // copy: source and destination rows; matvec: problems, first blocks
+    double work = 0.0;           // matvec: sum of rows x cols
+};
+struct Program {
+    std::vector<ProgStage> st;
+    int64_t z_rows = 0;          // scratch rows the program uses
+    double work = 0.0;           // sum of rows x cols of its matvecs
+};
+
 // Everything stored for one tree level (level 0 = root, factored without an ID).
 struct Level {
     int l = 0;
@@ -84,20 +128,27 @@ struct Level {
     int64_t b_mv_phi = 0, b_mv_T = 0, b_mv_E = 0, b_mv_Tt = 0;
     int64_t sum_m = 0, sum_k = 0;
     double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set
+    // extra compression (Sec. 3): boxes with k > k_cut
+    std::vector<char> cmp;                 // per box
+    std::vector<int> cbox;                 // compressed boxes
+    std::vector<CForm> forms;              // 6 per compressed box: phi_ss, phi_rr, E (HSS1D),
+                                           // phi_sr, phi_rs, T (low rank)
+    Program p_phi, p_T, p_E, p_Tt;         // compressed parts of the four solve applies
+    bool dense_freed = false;
 };
 
-// Workspace layout of one inverse apply with nrhs columns (counts in doubles).
+// Workspace layout of one inverse apply with nrhs columns (counts in storage elements).
 struct SolveLayout {
     std::vector<int64_t> woff, goff;   // per-level row offsets of w and of g / phi
     int64_t max_m = 0, max_k = 0;
-    int64_t n_w = 0, n_g = 0, n_u = 0, n_t = 0;
-    int64_t total() const { return n_w + 2 * n_g + 2 * n_u + n_t; }
+    int64_t n_w = 0, n_g = 0, n_u = 0, n_t = 0, n_z = 0;
+    int64_t total() const { return n_w + 2 * n_g + 2 * n_u + n_t + n_z; }
 };
 
 // Workspace pointers of one inverse apply, in the factor's storage type: w (n_w), g and
-// phi (n_g each), u and out (n_u each), t (n_t).
+// phi (n_g each), u and out (n_u each), t (n_t), z (n_z: scratch of the compressed applies).
 struct SolveWork {
-    void *w, *g, *phi, *u, *out, *t;
+    void *w, *g, *phi, *u, *out, *t, *z;
 };
 
 struct ProfRec {
@@ -114,6 +165,43 @@ SolveLayout solve_layout(const rs_op* op, int64_t nrhs);
 int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
               cudaStream_t st, bool profile);
 bool is_device_ptr(const void* p);
+int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity);
+
+// Extra compression (rs_hss1d.cpp).  Orders of Sec. 3.1 for box j of level l of an n x n grid:
+// skeleton points (grid indices g) cyclically around the box, residual points along the
+// interface between its children; both return the index of the point at each position.
+std::vector<int> cyclic_order(int64_t n, int l, int64_t j, const int64_t* g, int cnt);
+std::vector<int> interface_order(int64_t n, int l, const int64_t* g, int cnt);
+// Device status and barrier words of the ID kernels, and their wait limit.
+struct IdCtx {
+    int* status;
+    DevMem* bar;
+    long long spin;
+};
+// Compress every form of `forms` (sources M/ld set; HSS1D forms with their order) at eps with
+// HSS1D leaves of at most `leaf`, into a new store of T elements.
+template <class T>
+int compress_forms(const IdCtx& ctx, cudaStream_t st, std::vector<CForm*>& forms, double eps, int leaf, DevMem& store,
+                   int64_t& store_n);
+// Program builder input: form f applied (trans: X^T for a low-rank form) with input index i at
+// row in_rows[i] of the input buffer and output index i to row out_rows[i] of the output buffer
+// (add: accumulate).
+struct ProgItem {
+    const CForm* f;
+    bool trans;
+    std::vector<int64_t> in_rows, out_rows;
+    bool add;
+};
+int build_program(std::vector<ProgItem>& items, cudaStream_t st, Program& prog);
+template <class T>
+int run_program(cudaStream_t st, const Program& prog, const T* store, const T* in, T* out, T* z, int nrhs);
+}  // namespace rs
+struct rs_op;
+namespace rs {
+// Compress the boxes of every level with k > opts.k_cut (after the dense factorization) and
+// build the levels' apply programs; releases the dense blocks of fully compressed levels.
+template <class T>
+int compress_levels(rs_op* op, cudaStream_t st);
 int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st);
 int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st);
 int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
@@ -135,13 +223,16 @@ struct rs_op {
     std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow;
     // solve workspace (grown on demand)
-    rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_in, s_out, s_out2;
+    rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_z, s_in, s_out, s_out2;
     int64_t s_nrhs = 0;
     // FP64 direct-sum residual (built on first use): offset table, diagonal, permutation,
     // and refinement workspace
     rs::DevMem d_ktab, d_diag, d_rs, d_ing, r_xg, r_yg, r_res, r_dx, r_x, r_norm;
     // Helmholtz symmetric scaling s = kappa sqrt(b): grid order, input order; scaled RHS
     rs::DevMem d_s, d_s_in, s_fs;
+    // compressed store of the Sec. 3 forms (opts.k_cut)
+    rs::DevMem d_cstore;
+    int64_t cstore_n = 0;
     rs_stats stats{};
     std::atomic<int> inflight{0};   // references held by servers and their requests
     // profiling (opts.profile): pending event pairs and per-class sums

@@ -180,6 +180,34 @@ struct CopyJob {
 cudaError_t launch_mv_jobs(cudaStream_t st, const MvJob* jobs, int nj, int64_t blocks);
 cudaError_t launch_copy_jobs(cudaStream_t st, const CopyJob* jobs, int nj, int64_t total);
 
+// Extra compression of Sec. 3 (k_hss1d.cu).
+// ZProb: ID input of one node, column-major r x a at y_off.  mode 0 (HSS1D node):
+// r = 2 nout, rows i < nout are M(out[i], act[:]) and rows nout + i are M(act[:], out[i]);
+// mode 1 (low-rank block): r = nout, rows are M(i, act[:]).  M column-major with ld; act and
+// out are int32 lists at act_off / out_off of the launch's list array.
+struct ZProb {
+    const void* M;
+    int64_t ld;
+    int a, nout, mode;
+    int64_t act_off, out_off, y_off;
+};
+// SubProb: dst[dst_off + i + j rows] = M(row[i], col[j]) (row_off < 0: row[i] = i).
+struct SubProb {
+    const void* M;
+    int64_t ld;
+    int rows, cols;
+    int64_t row_off, col_off, dst_off;
+};
+template <class T>
+cudaError_t launch_zgather(cudaStream_t st, const ZProb* probs, int np, const int32_t* lists, T* Y, int64_t max_el);
+template <class T>
+cudaError_t launch_subgather(cudaStream_t st, const SubProb* probs, int np, const int32_t* lists, T* dst,
+                             int64_t max_el);
+// out[dst[p] * nrhs + c] = in[src[p] * nrhs + c] (add != 0: +=), p < count.
+template <class T>
+cudaError_t launch_copy_rows(cudaStream_t st, int64_t count, const int64_t* src, const int64_t* dst, const T* in, T* out,
+                             int nrhs, int add);
+
 // FP64 direct-sum residual (k_residual.cu): Kt is the (2n-1)^2 offset table of the Laplace
 // kernel; r = f - A x with x, f, r N x nrhs column-major in input order (ing[g] = input index
 // of grid point g), xg, yg grid-order scratch, norms[2c] = |r_c|^2, norms[2c+1] = |f_c|^2.

@@ -72,6 +72,7 @@ extern "C" int rs_solve_noalloc(rs_op* op, const void* f, int64_t nrhs, void* x,
     double* u = phi + Ls.n_g;
     double* out = u + Ls.n_u;
     double* t = out + Ls.n_u;
-    SolveWork ws{w, g, phi, u, out, t};
+    double* z = t + Ls.n_t;
+    SolveWork ws{w, g, phi, u, out, t, z};
     return solve_run(op, Ls, ws, (const double*)f, (double*)x, nrhs, (cudaStream_t)stream, false);
 }

@@ -309,6 +309,10 @@ int rs_server_create(rs_op* const* ops, int n_ops, size_t mem_budget_bytes, int 
             delete s;
             return fail(RS_E_INVALID, "the server batches real FP64 operators");
         }
+        if (ops[i]->cstore_n > 0) {
+            delete s;
+            return fail(RS_E_INVALID, "the server batches dense-block operators (factored without k_cut)");
+        }
         if (i && ops[i]->device != ops[0]->device) {
             delete s;
             return fail(RS_E_INVALID, "all operators must live on one device");

@@ -121,6 +121,7 @@ void rs_opts_default(rs_opts* o)
     o->k_cut = 0;
     o->spin_limit = (int64_t)1 << 26;
     o->profile = 0;
+    o->hss_leaf = 64;
 }
 
 int64_t rs_launch_count(void) { return g_launches.load(); }

@@ -98,3 +98,23 @@ def test_level_bookkeeping_matches_oracle(rs, oracle_mod, n, leaf):
                 np.testing.assert_array_equal(near[no[j]:no[j + 1]], F.near(l, j))
     finally:
         rs.rs_free_tree(t)
+
+
+@pytest.mark.parametrize("n,leaf", [(64, 8), (32, 4)])
+def test_compression_orders_match_oracle(rs, oracle_mod, n, leaf):
+    """Orders of Sec. 3.1 (skeleton around the box, residual along the interface) for the
+    oracle's skeleton and residual points of every box: identical integers on both sides."""
+    F = oracle_mod.Factorization(n, leaf, 1e-10)
+    t = rs.rs_build_tree(W.grid_points(n), leaf)
+    try:
+        for l in range(1, F.depth + 1):
+            for j in range(2 ** l):
+                sk = F.skel(l, j)
+                np.testing.assert_array_equal(rs.rs_tree_box_order(t, l, j, 0, sk), F.order(l, j, 0))
+                sks = set(sk.tolist())
+                rsg = np.array([g for g in F.active(l, j) if g not in sks], dtype=np.int64)
+                np.testing.assert_array_equal(rs.rs_tree_box_order(t, l, j, 1, rsg), F.order(l, j, 1))
+        with pytest.raises(rs.RsError):
+            rs.rs_tree_box_order(t, 1, 0, 0, np.array([n * n], dtype=np.int64))
+    finally:
+        rs.rs_free_tree(t)
