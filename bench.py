@@ -48,6 +48,8 @@ def _args():
     p.add_argument("--serving-requests", type=int, default=150,
                    help="requests of the serving stream measured after the main step (0 = skip)")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    p.add_argument("--k-cut", type=int, default=512,
+                   help="also measure the extra compression of Sec. 3 for boxes with k > K (0: skip)")
     return p.parse_args()
 
 
@@ -248,6 +250,50 @@ def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
     return out
 
 
+def compressed_measure(P, torch, n, leaf, pts, a, F, nrhs, st, eps, k_cut, x_dense, reps=5):
+    """The same workload with the extra compression of Sec. 3 (boxes with k > k_cut): factor
+    time (compression included), solve time, stored bytes against the dense blocks they replace,
+    and the change of the solution against the dense-block factor."""
+    import numpy as np
+    o = P.rs_opts_default()
+    o.k_cut, o.hss_leaf, o.hss_eps, o.profile = k_cut, 64, 1e-12, 1
+    f = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    x = torch.empty_like(f)
+    tree = P.rs_build_tree(pts, leaf)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(st)
+    op = P.rs_factor(tree, a=a, eps=eps, opts=o, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    factor_ms = e0.elapsed_time(e1)
+    P.rs_solve(op, f, nrhs, x, st)      # warm-up (workspace)
+    torch.cuda.synchronize()
+    t = 0.0
+    for _ in range(reps):
+        s0, s1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        s0.record(st)
+        P.rs_solve(op, f, nrhs, x, st)
+        s1.record(st)
+        s1.synchronize()
+        t += s0.elapsed_time(s1)
+    s = P.rs_op_stats(op)
+    sol = P.rs_op_profile(op)["solve"]
+    xd = torch.from_numpy(np.ascontiguousarray(x_dense.T)).cuda()
+    change = float(torch.linalg.norm(x - xd) / torch.linalg.norm(xd))
+    rel = P.rs_residual(op, x, f, nrhs, st)
+    out = {"k_cut": k_cut, "hss_leaf": 64, "hss_eps": 1e-12, "factor_ms": factor_ms, "compress_ms": s["ms_compress"],
+           "solve_ms": t / reps, "compressed_boxes": s["compressed_boxes"],
+           "bytes_compressed": s["bytes_compressed"], "bytes_dense_replaced": s["bytes_dense_replaced"],
+           "bytes_factors": s["bytes_factors"], "bytes_solve": s["bytes_solve"],
+           "flops_solve_per_rhs": s["flops_solve_per_rhs"],
+           "solve_achieved_tflops": sol[1] / (sol[0] * 1e-3) / 1e12 if sol[0] else None,
+           "change_vs_dense": change, "residual_fp64": float(rel.max())}
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -370,6 +416,11 @@ def run_ours(args):
     out["residual_fp64"] = float(P.rs_residual(op, x_dev, f_dev, nrhs, st).max())
     P.rs_free(op)
     P.rs_free_tree(tree)
+    if args.k_cut > 0:
+        out["compressed"] = compressed_measure(P, torch, n, leaf, pts, a, F, nrhs, st, eps, args.k_cut,
+                                               x_dev.cpu().numpy().T.copy())
+        out["compressed"]["dense_solve_ms"] = solve_ms
+        out["compressed"]["dense_bytes_factors"] = last_stats["bytes_factors"]
     if not args.no_mixed:
         mx = mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st)
         mx["step_speedup_vs_fp64"] = (factor_ms + solve_ms) / (mx["factor_ms"] + mx["refined_solve_ms"])

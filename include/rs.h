@@ -81,6 +81,7 @@ typedef struct {
     int profile;                 /* 1: time every kernel launch with CUDA events on the
                                     launch stream (rs_op_profile)                     [0]    */
     int hss_leaf;                /* largest leaf run of the HSS1D trees (k_cut > 0)  [64]   */
+    double hss_eps;              /* ID tolerance of that compression; 0 = eps         [0]    */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);

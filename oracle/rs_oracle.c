@@ -361,6 +361,7 @@ void ro_opts_default(ro_opts* o)
     o->max_levels = 0;
     o->k_cut = 0;
     o->hss_leaf = 64;
+    o->hss_eps = 0.0;
 }
 
 int ro_id(int cplx, const double* Y, int r, int m, double eps, int* k_out, int* perm, double* T)
@@ -445,7 +446,7 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
     if (o.kind != 0 && o.kind != 1) return -1;
     if (o.kind == 0 && b) return -1;
     if (o.proxy_points < 0) return -1;
-    if (o.k_cut > 0 && o.hss_leaf < 1) return -1;
+    if (o.k_cut > 0 && (o.hss_leaf < 1 || !(o.hss_eps >= 0.0))) return -1;
     int64_t N = (int64_t)n * n;
     ro_op* op = (ro_op*)calloc(1, sizeof(ro_op));
     op->n = n; op->leaf = leaf_side; op->d = 2 * L; op->h = 1.0 / n; op->eps = eps; op->opts = o;

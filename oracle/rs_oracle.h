@@ -46,6 +46,7 @@ typedef struct {
                                     form (Sec. 3), compressed at eps from the dense blocks;
                                     ro_solve uses these forms for those boxes              */
     int hss_leaf;                /* largest leaf run of the HSS1D trees                    */
+    double hss_eps;              /* ID tolerance of that compression (0: eps)              */
 } ro_opts;
 
 typedef struct ro_hss ro_hss;

@@ -660,7 +660,8 @@ int compress_levels(rs_op* op, cudaStream_t st)
     }
     if (all.empty()) return RS_OK;
     IdCtx ctx{op->d_status.as<int>(), &op->d_bar, (long long)op->opts.spin_limit};
-    int rc = compress_forms<T>(ctx, st, all, op->eps, op->opts.hss_leaf, op->d_cstore, op->cstore_n);
+    const double eps_c = op->opts.hss_eps > 0.0 ? op->opts.hss_eps : op->eps;
+    int rc = compress_forms<T>(ctx, st, all, eps_c, op->opts.hss_leaf, op->d_cstore, op->cstore_n);
     if (rc) return rc;
     auto rows = [](int64_t base, int64_t n) {
         std::vector<int64_t> v((size_t)n);

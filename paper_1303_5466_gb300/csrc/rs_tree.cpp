@@ -122,6 +122,7 @@ void rs_opts_default(rs_opts* o)
     o->spin_limit = (int64_t)1 << 26;
     o->profile = 0;
     o->hss_leaf = 64;
+    o->hss_eps = 0.0;
 }
 
 int64_t rs_launch_count(void) { return g_launches.load(); }
