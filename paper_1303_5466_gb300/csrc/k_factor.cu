@@ -161,7 +161,10 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     double* nrm = smem;                       // nown: squared norms (FP64 in every precision)
     double* ref = nrm + nown;                 // nown
     int* sel = (int*)(ref + nown);            // nown
-    T* v = (T*)(sel + ((nown + 1) & ~1));     // r: Householder vector
+    int* alist = sel + nown;                  // nown: columns not yet selected (any order)
+    int* apos = alist + nown;                 // nown: position of a column in alist
+    T* v = (T*)(apos + ((nown + 1) & ~1));    // r: Householder vector (8-byte aligned)
+    __shared__ int s_na;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
@@ -171,8 +174,9 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
         double s = 0.0;
         for (int i = lane; i < r; i += 32) s += abs2d(col[i]);
         s = warp_sum(s);
-        if (lane == 0) { nrm[jj] = s; ref[jj] = s; sel[jj] = 0; }
+        if (lane == 0) { nrm[jj] = s; ref[jj] = s; sel[jj] = 0; alist[jj] = jj; apos[jj] = jj; }
     }
+    if (threadIdx.x == 0) s_na = nown;
     __syncthreads();
 
     const int kmax = min(r, m);
@@ -180,22 +184,24 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     double alpha0 = 0.0;
     for (int s = 0; s < kmax; ++s) {
         unsigned long long best = 0;
-        for (int jj = threadIdx.x; jj < nown; jj += NT)
-            if (!sel[jj]) {
-                const unsigned long long q = pivot_key(nrm[jj], c0 + jj);
-                best = q > best ? q : best;
-            }
+        const int na = s_na;
+        for (int t = threadIdx.x; t < na; t += NT) {
+            const int jj = alist[t];
+            const unsigned long long q = pivot_key(nrm[jj], c0 + jj);
+            best = q > best ? q : best;
+        }
         best = block_max_u64<NT>(best, kred);
         if (G > 1) {
             if (threadIdx.x == 0) keys[((int64_t)b * 2 + (s & 1)) * G + gi] = best;
             if (!group_sync(bar + b, (unsigned)(s + 1) * (unsigned)G, status, spin)) return;
-            if (threadIdx.x == 0) {
+            if (warp == 0) {       // the group's keys, read in parallel by one warp
                 unsigned long long t = 0;
-                for (int q = 0; q < G; ++q) {
+                for (int q = lane; q < G; q += 32) {
                     const unsigned long long u = __ldcg(keys + ((int64_t)b * 2 + (s & 1)) * G + q);
                     t = u > t ? u : t;
                 }
-                s_key = t;
+                t = warp_max_u64(t);
+                if (lane == 0) s_key = t;
             }
             __syncthreads();
             best = s_key;
@@ -226,31 +232,86 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             v[s] = x0 - beta;
             if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
         }
-        if (threadIdx.x == 0 && p >= c0 && p < c1) sel[p - c0] = 1;
+        if (threadIdx.x == 0 && p >= c0 && p < c1) {
+            // drop the pivot from the list of open columns (swap with the last)
+            const int jp = p - c0, t = apos[jp], last = alist[s_na - 1];
+            sel[jp] = 1;
+            alist[t] = last;
+            apos[last] = t;
+            s_na = s_na - 1;
+        }
         __syncthreads();
-        for (int jj = warp; jj < nown; jj += NW) {
-            if (sel[jj]) continue;
-            T* col = Y + (int64_t)(c0 + jj) * r;
-            T w = 0;
-            for (int i = s + lane; i < r; i += 32) w = fma_(conj_(v[i]), col[i], w);
-            w = warp_sum(w);
-            const T tw = tau * w;
-            T rsj = 0;
-            for (int i = s + lane; i < r; i += 32) {
-                const T u = fma_(-v[i], tw, col[i]);
-                col[i] = u;
-                if (i == s) rsj = u;
+        // apply the reflector to the open columns, two per warp, with U rows per lane in
+        // flight per column (independent loads keep bytes in flight to cover the memory
+        // latency), then downdate their norms
+        const int nopen = s_na;
+        for (int t = 2 * warp; t < nopen; t += 2 * NW) {
+            const int j0 = alist[t];
+            const bool two = t + 1 < nopen;
+            const int j1 = two ? alist[t + 1] : j0;
+            T* col0 = Y + (int64_t)(c0 + j0) * r;
+            T* col1 = Y + (int64_t)(c0 + j1) * r;
+            constexpr int U = 4;
+            T w0 = 0, w1 = 0;
+            int i = s + lane;
+            for (; i + 32 * (U - 1) < r; i += 32 * U) {
+                T vv[U], a[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    vv[u] = conj_(v[i + 32 * u]);
+                    a[u] = col0[i + 32 * u];
+                    b[u] = col1[i + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    w0 = fma_(vv[u], a[u], w0);
+                    w1 = fma_(vv[u], b[u], w1);
+                }
             }
-            rsj = shfl_(rsj, 0);
-            double nv = nrm[jj] - abs2d(rsj);
-            if (nv < 1e-4 * ref[jj]) {
-                double q = 0.0;
-                for (int i = s + 1 + lane; i < r; i += 32) q += abs2d(col[i]);
-                q = warp_sum(q);
-                nv = q;
-                if (lane == 0) ref[jj] = q;
+            for (; i < r; i += 32) {
+                const T vv = conj_(v[i]);
+                w0 = fma_(vv, col0[i], w0);
+                w1 = fma_(vv, col1[i], w1);
             }
-            if (lane == 0) nrm[jj] = nv;
+            w0 = warp_sum(w0);
+            w1 = warp_sum(w1);
+            const T tw0 = tau * w0, tw1 = tau * w1;
+            i = s + lane;
+            for (; i + 32 * (U - 1) < r; i += 32 * U) {
+                T vv[U], a[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    vv[u] = v[i + 32 * u];
+                    a[u] = col0[i + 32 * u];
+                    b[u] = col1[i + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    col0[i + 32 * u] = fma_(-vv[u], tw0, a[u]);
+                    if (two) col1[i + 32 * u] = fma_(-vv[u], tw1, b[u]);
+                }
+            }
+            for (; i < r; i += 32) {
+                const T vv = v[i];
+                const T a = col0[i], b = col1[i];
+                col0[i] = fma_(-vv, tw0, a);
+                if (two) col1[i] = fma_(-vv, tw1, b);
+            }
+            __syncwarp();
+            for (int c = 0; c < (two ? 2 : 1); ++c) {
+                const int jj = c == 0 ? j0 : j1;
+                const T* col = c == 0 ? col0 : col1;
+                const T rsj = shfl_(lane == 0 ? col[s] : (T)0, 0);
+                double nv = nrm[jj] - abs2d(rsj);
+                if (nv < 1e-4 * ref[jj]) {
+                    double q = 0.0;
+                    for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(col[i2]);
+                    q = warp_sum(q);
+                    nv = q;
+                    if (lane == 0) ref[jj] = q;
+                }
+                if (lane == 0) nrm[jj] = nv;
+            }
         }
         __syncthreads();
         k = s + 1;
@@ -262,7 +323,7 @@ template <class T>
 static size_t cpqr_shm(int max_r, int max_m, int G)
 {
     const int per = (max_m + G - 1) / G;
-    return sizeof(double) * 2 * (size_t)per + sizeof(int) * (size_t)(per + 2) + sizeof(T) * (size_t)max_r + 64;
+    return sizeof(double) * 2 * (size_t)per + sizeof(int) * (size_t)(3 * per + 2) + sizeof(T) * (size_t)max_r + 64;
 }
 
 template <class T>
@@ -294,7 +355,9 @@ int cpqr_max_ctas(int max_r, int max_m, int G)
 {
     constexpr int NT = 256;
     const size_t shm = cpqr_shm<T>(max_r, max_m, G);
-    cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (shm > 227 * 1024) return 0;
+    if (cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
+        return 0;
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -303,16 +366,17 @@ int cpqr_max_ctas(int max_r, int max_m, int G)
 }
 
 // ------------------------------------------------------------------ T = R11^{-1} R12
-// One CTA per (box, group of NC residual columns): back substitution by columns of R11, so
-// each step reads one contiguous column of R.
-template <int NT, int NC, class T>
+// One CTA per (box, group of nc residual columns): back substitution over the columns of R11
+// (a = k-1 .. 0).  The group's right-hand sides live in shared memory; the R11 column of the
+// next step is fetched into a second shared buffer while the current step updates, so each
+// step costs two CTA barriers and no dependent global load.
+template <int NT, class T>
 __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ act_off, const int32_t* __restrict__ kk,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off, const T* __restrict__ Yall,
         const int32_t* __restrict__ piv, const T* __restrict__ diag, const int32_t* __restrict__ skpos,
-        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, T* __restrict__ Tout)
+        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, T* __restrict__ Tout, int NC)
 {
     extern __shared__ double ys_raw[];
-    T* ys = (T*)ys_raw;              // NC x k
     const int b = blockIdx.x;
     const int64_t a0 = act_off[b];
     const int m = (int)(act_off[b + 1] - a0);
@@ -324,28 +388,49 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
     const int r = nnear[b] + P;
     const T* Y = Yall + y_off[b];
     T* Tb = Tout + t_off[b];
-    for (int q = 0; q < nc; ++q) {
+    T* ys = (T*)ys_raw;                 // nc x k right-hand sides, then solutions
+    T* rc = ys + (size_t)NC * k;        // 2 x k: R11 columns of the current and next step
+    __shared__ T tq[64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = NT / 32;
+    for (int q = warp; q < nc; q += NW) {
         const T* col = Y + (int64_t)rscol[a0 + cb + q] * r;
-        for (int a = threadIdx.x; a < k; a += NT) ys[q * k + a] = col[a];
+        for (int i = lane; i < k; i += 32) ys[(size_t)q * k + i] = col[i];
     }
+    {
+        const T* Ra = Y + (int64_t)piv[a0 + k - 1] * r;
+        for (int i = threadIdx.x; i < k; i += NT) rc[(size_t)((k - 1) & 1) * k + i] = Ra[i];
+    }
+    __syncthreads();
     for (int a = k - 1; a >= 0; --a) {
+        const T* cur = rc + (size_t)(a & 1) * k;
+        if (threadIdx.x < nc) {
+            const T t = ys[(size_t)threadIdx.x * k + a] / diag[a0 + a];
+            tq[threadIdx.x] = t;
+            Tb[(int64_t)(cb + threadIdx.x) * k + skpos[a0 + a]] = t;
+        }
+        if (a > 0) {
+            T* nxt = rc + (size_t)((a - 1) & 1) * k;
+            const T* Rn = Y + (int64_t)piv[a0 + a - 1] * r;
+            for (int i = threadIdx.x; i < a - 1 + 1; i += NT) nxt[i] = Rn[i];
+        }
         __syncthreads();
-        const T Raa = diag[a0 + a];
-        T t[NC];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) t[q] = (q < nc) ? ys[q * k + a] / Raa : (T)0;
-        if (threadIdx.x == 0) {
-            const int row = skpos[a0 + a];
-            for (int q = 0; q < nc; ++q) Tb[(int64_t)(cb + q) * k + row] = t[q];
+        for (int q = warp; q < nc; q += NW) {
+            const T t = tq[q];
+            T* yq = ys + (size_t)q * k;
+            for (int i = lane; i < a; i += 32) yq[i] = fma_(-t, cur[i], yq[i]);
         }
-        const T* Ra = Y + (int64_t)piv[a0 + a] * r;
-        for (int i = threadIdx.x; i < a; i += NT) {
-            const T R = Ra[i];
-#pragma unroll
-            for (int q = 0; q < NC; ++q)
-                if (q < nc) ys[q * k + i] = fma_(-t[q], R, ys[q * k + i]);
-        }
+        __syncthreads();
     }
+}
+
+template <class T>
+static int id_T_cols(int max_k)
+{
+    const size_t budget = 160 * 1024;
+    const size_t per = sizeof(T) * (size_t)std::max(max_k, 1);
+    int nc = (int)std::min<size_t>(32, budget / per > 2 ? budget / per - 2 : 1);
+    return std::max(nc, 1);
 }
 
 template <class T>
@@ -354,15 +439,17 @@ cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const i
                         const int32_t* skpos, const int32_t* rscol, const int64_t* t_off, T* Tout, int max_cols,
                         int max_k)
 {
-    constexpr int NT = 128, NC = 4;
+    constexpr int NT = 256;
     if (nb <= 0 || max_cols <= 0 || max_k <= 0) return cudaSuccess;
-    const size_t shm = sizeof(T) * (size_t)NC * (size_t)max_k;
-    cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, NC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const int NC = id_T_cols<T>(max_k);
+    const size_t shm = sizeof(T) * (size_t)(NC + 2) * (size_t)max_k;
+    if (shm > 227 * 1024) return cudaErrorInvalidValue;     // skeleton too large for one CTA's buffers
+    cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)nb, (unsigned)((max_cols + NC - 1) / NC));
     count_launches(1);
-    id_T_kernel<NT, NC, T><<<grid, NT, shm, st>>>(act_off, kk, nnear, P, y_off, Y, piv, diag, skpos, rscol, t_off,
-                                                  Tout);
+    id_T_kernel<NT, T><<<grid, NT, shm, st>>>(act_off, kk, nnear, P, y_off, Y, piv, diag, skpos, rscol, t_off, Tout,
+                                              NC);
     return cudaGetLastError();
 }
 

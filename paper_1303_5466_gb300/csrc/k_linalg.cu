@@ -28,7 +28,7 @@ namespace rs {
 template <int NT, int NB, class T>
 __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
         T* __restrict__ Aall, int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off,
-        int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
+        int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin, int sp)
 {
     constexpr int CB = 32;                 // own columns updated per chunk
     using W = typename sc_traits<T>::wide;      // FP64 panel arithmetic
@@ -43,6 +43,11 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
     const int m = msz[b];
     T* __restrict__ A = Aall + off[b];
     W* f = (W*)sm;                         // m: the current pivot column (panel step)
+    int k0_cur = 0;
+    // sp: the owner factors its panel in shared memory (NB columns of m after f), so the
+    // column steps of the panel -- the serial part of a block step -- touch no global memory
+    T* pan = (T*)(sm + (((size_t)sizeof(W) * m + 15) / 16) * 2);
+    auto pcol = [&](int jj) -> T* { return sp ? pan + (int64_t)jj * m : A + (int64_t)(k0_cur + jj) * m; };
     int32_t* ip = ipiv + ipiv_off[b];
     int* pb = pivbuf + (int64_t)b * 2 * NB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -51,9 +56,14 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
     for (int q = 0; q < npan; ++q) {
         const int k0 = q * NB, kw = min(NB, m - k0);
         if (q % G == gi) {
+            k0_cur = k0;
+            if (sp) {
+                for (int e = threadIdx.x; e < m * kw; e += NT) pan[e] = A[(int64_t)k0 * m + e];
+                __syncthreads();
+            }
             for (int t = 0; t < kw; ++t) {
                 const int c = k0 + t;
-                const T* col = A + (int64_t)c * m;
+                const T* col = pcol(t);
                 double best = -1.0;
                 int bi = m;
                 for (int i = c + threadIdx.x; i < m; i += NT) {
@@ -78,14 +88,14 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 __syncthreads();
                 const int p = s_piv[t];
                 if (threadIdx.x < kw && p != c) {           // swap rows c, p inside the panel
-                    T* cj = A + (int64_t)(k0 + threadIdx.x) * m;
+                    T* cj = pcol(threadIdx.x);
                     const T u = cj[c];
                     cj[c] = cj[p];
                     cj[p] = u;
                 }
                 __syncthreads();
                 for (int i = threadIdx.x; i < m; i += NT) f[i] = cast_<W>(col[i]);
-                if (threadIdx.x < kw) s_row[threadIdx.x] = cast_<W>(A[(int64_t)(k0 + threadIdx.x) * m + c]);
+                if (threadIdx.x < kw) s_row[threadIdx.x] = cast_<W>(pcol(threadIdx.x)[c]);
                 __syncthreads();
                 const W pv = f[c];
                 const double apv = absd(pv);
@@ -95,7 +105,7 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 const W pinv = (apv > 0.0) ? W(1.0) / pv : W(0.0);
                 for (int e = threadIdx.x; e < m * kw; e += NT) {
                     const int jj = e / m, i = e - jj * m;
-                    T* cj = A + (int64_t)(k0 + jj) * m;
+                    T* cj = pcol(jj);
                     if (k0 + jj == c) {
                         cj[i] = cast_<T>((i == c) ? pinv : -f[i] * pinv);
                     } else {
@@ -104,6 +114,9 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                     }
                 }
                 __syncthreads();
+            }
+            if (sp) {
+                for (int e = threadIdx.x; e < m * kw; e += NT) A[(int64_t)k0 * m + e] = pan[e];
             }
             if (threadIdx.x < kw) pb[(q & 1) * NB + threadIdx.x] = s_piv[threadIdx.x];
         }
@@ -182,14 +195,24 @@ __global__ void __launch_bounds__(256) gj_unpivot_kernel(const int32_t* __restri
 
 constexpr int GJ_NT = 256, GJ_NB = 8;
 
+// Dynamic shared memory of the GJ kernel: the pivot column f, and with sp the owner's panel.
 template <class T>
-static size_t gj_shm(int max_m) { return sizeof(typename sc_traits<T>::wide) * (size_t)max_m + 64; }
+static size_t gj_shm(int max_m, bool sp)
+{
+    const size_t fb = ((sizeof(typename sc_traits<T>::wide) * (size_t)max_m + 15) / 16) * 16;
+    return fb + (sp ? sizeof(T) * (size_t)GJ_NB * (size_t)max_m : 0) + 64;
+}
+// Panels go to shared memory for a launch of a single matrix (the root, where the panel steps
+// are the serial part and every SM shares the one matrix) when the CTA stays within 160 KB;
+// with more matrices the smaller CTA keeps more CTAs, and so more panels, resident (measured
+// at 512^2: the root 61 -> 55 ms, the 2- and 4-matrix levels slower with the larger CTA).
+template <class T>
+static bool gj_sp(int max_m, int nb) { return nb == 1 && gj_shm<T>(max_m, true) <= 160 * 1024; }
 
 template <class T>
-int gj_max_ctas(int max_m, int G)
+int gj_max_ctas(int max_m, int nb)
 {
-    (void)G;
-    const size_t shm = gj_shm<T>(max_m);
+    const size_t shm = gj_shm<T>(max_m, gj_sp<T>(max_m, nb));
     cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -207,16 +230,17 @@ cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, 
                               long long spin_limit, int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
-    const size_t shm = gj_shm<T>(max_m);
+    int sp = gj_sp<T>(max_m, nb) ? 1 : 0;
+    const size_t shm = gj_shm<T>(max_m, sp != 0);
     cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     if (G == 1) {
         count_launches(1);
         gj_kernel<GJ_NT, GJ_NB, T><<<nb, GJ_NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status,
-                                                           spin_limit);
+                                                           spin_limit, sp);
     } else {
         void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&pivbuf,
-                        (void*)&bar, (void*)&status, (void*)&spin_limit};
+                        (void*)&bar, (void*)&status, (void*)&spin_limit, (void*)&sp};
         count_launches(1);
         e = cudaLaunchCooperativeKernel((void*)gj_kernel<GJ_NT, GJ_NB, T>, dim3((unsigned)(nb * G)), dim3(GJ_NT), args,
                                         shm, st);

@@ -105,17 +105,20 @@ int check_status(rs_op* op, cudaStream_t st)
 
 }  // namespace
 
-// Pick the CTA group size per box for a cooperative kernel: 1 (plain launch) when the boxes
-// alone fill the GPU, otherwise as many CTAs per box as stay co-resident (at most one per
-// 32 columns and 1024 in all).
+// Pick the CTA group size per box for a cooperative kernel (capacity(G): co-resident CTAs
+// when each box takes G CTAs, 0 if such a CTA does not fit on an SM).  Start from the smallest
+// G whose CTAs fit; keep it when the boxes alone fill the GPU, otherwise take as many CTAs per
+// box as stay co-resident (at most one per 32 columns and 1024 in all).
 int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
 {
     const int gmax = std::max(1, std::min(max_cols / 32, 1024));
-    const int cap1 = capacity(1);
-    if (gmax == 1 || nb >= cap1) return 1;
-    int G = std::min(gmax, cap1 / std::max(nb, 1));
-    while (G > 1 && nb * G > capacity(G)) --G;
-    return std::max(G, 1);
+    int g0 = 1;
+    while (g0 < gmax && capacity(g0) <= 0) ++g0;
+    const int cap0 = capacity(g0);
+    if (cap0 <= 0 || g0 == gmax || nb * g0 >= cap0) return g0;
+    int G = std::min(gmax, cap0 / std::max(nb, 1));
+    while (G > g0 && nb * G > capacity(G)) --G;
+    return std::max(G, g0);
 }
 
 namespace {
@@ -139,7 +142,7 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
     RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
     // one CTA per panel of columns at most
-    const int G = choose_group(nb, max_m * 32 / gj_panel_width(), [&](int g) { return gj_max_ctas<T>(max_m, g); });
+    const int G = choose_group(nb, max_m * 32 / gj_panel_width(), [&](int) { return gj_max_ctas<T>(max_m, nb); });
     double work = 0.0;
     for (int b = 0; b < nb; ++b) work += 2.0 * (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
     ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb]);

@@ -121,8 +121,9 @@ template <class T>
 cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A,
                               int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf, unsigned int* bar, int* status,
                               long long spin_limit, int max_m);
+// Co-resident CTAs of the GJ kernel for a launch of nb matrices of size <= max_m.
 template <class T>
-int gj_max_ctas(int max_m, int G);
+int gj_max_ctas(int max_m, int nb);
 int gj_panel_width();
 
 // Grouped GEMM over `np` problems (device descriptors), total tiles `tiles`.
