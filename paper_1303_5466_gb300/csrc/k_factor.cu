@@ -128,22 +128,29 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 }
 
 // ------------------------------------------------------------------ column-pivoted QR
-// One group of G CTAs per box; CTA gi owns columns [c0, c1) of the box's Y (column-major,
-// ld = r).  Columns never move: the pivot order is recorded in piv[], and R is read back
-// from the physical columns (rows < k) with its diagonal in diag[].  Each step:
-//   1. every CTA finds the best pivot key among its unselected columns; the group max
-//      (via `keys` and one barrier when G > 1) names the pivot column p;
-//   2. every CTA builds the Householder vector of column p (rows s..r-1) in shared memory;
-//   3. every CTA applies the reflector to its unselected columns (one warp per column, lanes
-//      over rows, shuffle reductions) and downdates their squared norms, recomputing a norm
-//      from the data once it falls below 1e-4 of the value it was last computed from.
-// The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step.
+// One group of G CTAs per box (cooperative when G > 1); Y is column-major with ld = r.
+// Columns never move: the pivot order is recorded in piv[], and R is read back from the
+// physical columns (rows < k) with its diagonal in diag[].  The squared column norms live in
+// global memory (nrm, ref: act_off-indexed), and every CTA keeps the same list of open
+// (unselected) columns, updated identically from the same pivot each step; step s splits the
+// list evenly over the group's CTAs, so the work stays balanced however the pivots fall.
+// Each step:
+//   1. the group's best pivot key (computed by every CTA for its share at the end of the
+//      previous step) is read from `keys` after one group barrier and names the pivot p;
+//   2. every CTA drops p from its list and builds the Householder vector of column p
+//      (rows s..r-1) in shared memory;
+//   3. every CTA applies the reflector to its share of the open columns (two per warp, four
+//      rows in flight per lane), downdates their squared norms (recomputed from the data once
+//      below 1e-4 of the value they were last computed from) and takes the best key of its
+//      share for the next step.
+// The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step (every CTA
+// computes alpha from the same data in the same order).
 template <int NT, class T>
 __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
         T* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
         T* __restrict__ diag, unsigned int* __restrict__ bar, unsigned long long* __restrict__ keys,
-        int* __restrict__ status, long long spin)
+        int* __restrict__ status, long long spin, double* __restrict__ nrm_all, double* __restrict__ ref_all)
 {
     extern __shared__ double smem[];
     __shared__ double dred[NT / 32];
@@ -155,58 +162,58 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     const int m = (int)(act_off[b + 1] - a0);
     const int r = nnear[b] + P;
     T* __restrict__ Y = Yall + y_off[b];
-    const int per = (m + G - 1) / G;
-    const int c0 = min(m, gi * per), c1 = min(m, c0 + per);
-    const int nown = c1 - c0;
-    double* nrm = smem;                       // nown: squared norms (FP64 in every precision)
-    double* ref = nrm + nown;                 // nown
-    int* sel = (int*)(ref + nown);            // nown
-    int* alist = sel + nown;                  // nown: columns not yet selected (any order)
-    int* apos = alist + nown;                 // nown: position of a column in alist
-    T* v = (T*)(apos + ((nown + 1) & ~1));    // r: Householder vector (8-byte aligned)
-    __shared__ int s_na;
+    double* __restrict__ nrm = nrm_all + a0;
+    double* __restrict__ ref = ref_all + a0;
+    int* alist = (int*)smem;                  // m: open columns (same order in every CTA)
+    int* apos = alist + m;                    // m: position of a column in alist
+    T* v = (T*)(apos + m);                    // r: Householder vector (2m ints keep it 8-byte aligned)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
+    unsigned long long* kb = keys + (int64_t)b * 2 * G;   // [2][G], by step parity
 
-    for (int jj = warp; jj < nown; jj += NW) {
-        const T* col = Y + (int64_t)(c0 + jj) * r;
-        double s = 0.0;
-        for (int i = lane; i < r; i += 32) s += abs2d(col[i]);
-        s = warp_sum(s);
-        if (lane == 0) { nrm[jj] = s; ref[jj] = s; sel[jj] = 0; alist[jj] = jj; apos[jj] = jj; }
+    for (int j = threadIdx.x; j < m; j += NT) { alist[j] = j; apos[j] = j; }
+    {
+        // initial norms of this CTA's share, and its best key for step 0
+        const int lo = (int)(((int64_t)gi * m) / G), hi = (int)(((int64_t)(gi + 1) * m) / G);
+        unsigned long long best = 0;
+        for (int j = lo + warp; j < hi; j += NW) {
+            const T* col = Y + (int64_t)j * r;
+            double q = 0.0;
+            for (int i = lane; i < r; i += 32) q += abs2d(col[i]);
+            q = warp_sum(q);
+            if (lane == 0) { nrm[j] = q; ref[j] = q; }
+            const unsigned long long kq = pivot_key(q, j);
+            best = kq > best ? kq : best;
+        }
+        best = block_max_u64<NT>(best, kred);
+        if (threadIdx.x == 0) kb[gi] = best;
     }
-    if (threadIdx.x == 0) s_na = nown;
-    __syncthreads();
-
+    int nopen = m;
     const int kmax = min(r, m);
     int k = 0;
     double alpha0 = 0.0;
     for (int s = 0; s < kmax; ++s) {
-        unsigned long long best = 0;
-        const int na = s_na;
-        for (int t = threadIdx.x; t < na; t += NT) {
-            const int jj = alist[t];
-            const unsigned long long q = pivot_key(nrm[jj], c0 + jj);
-            best = q > best ? q : best;
-        }
-        best = block_max_u64<NT>(best, kred);
+        // 1. the group's pivot
         if (G > 1) {
-            if (threadIdx.x == 0) keys[((int64_t)b * 2 + (s & 1)) * G + gi] = best;
             if (!group_sync(bar + b, (unsigned)(s + 1) * (unsigned)G, status, spin)) return;
-            if (warp == 0) {       // the group's keys, read in parallel by one warp
-                unsigned long long t = 0;
-                for (int q = lane; q < G; q += 32) {
-                    const unsigned long long u = __ldcg(keys + ((int64_t)b * 2 + (s & 1)) * G + q);
-                    t = u > t ? u : t;
-                }
-                t = warp_max_u64(t);
-                if (lane == 0) s_key = t;
-            }
+        } else {
             __syncthreads();
-            best = s_key;
         }
+        if (warp == 0) {
+            unsigned long long t = 0;
+            for (int q = lane; q < G; q += 32) {
+                const unsigned long long u = G > 1 ? __ldcg(kb + (s & 1) * G + q) : kb[(s & 1) * G + q];
+                t = u > t ? u : t;
+            }
+            t = warp_max_u64(t);
+            if (lane == 0) s_key = t;
+        }
+        __syncthreads();
+        const unsigned long long best = s_key;
         const int p = (int)(KEY_MASK - (best & KEY_MASK));
+        if (p < 0 || p >= m) { if (threadIdx.x == 0) atomicOr(status, DEV_BADSIZE); break; }
+        // 2. drop p from the open list (every CTA the same way), Householder vector
         const T* colp = Y + (int64_t)p * r;
         double part = 0.0;
         for (int i = s + threadIdx.x; i < r; i += NT) {
@@ -214,7 +221,13 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             v[i] = x;
             part += abs2d(x);
         }
-        const double a2 = block_sum<NT>(part, dred);
+        const double a2 = block_sum<NT>(part, dred);    // its barriers also order the loads above
+        if (threadIdx.x == 0) {
+            const int t = apos[p], last = alist[nopen - 1];
+            alist[t] = last;
+            apos[last] = t;
+        }
+        --nopen;
         const double alpha = sqrt(a2);
         if (s == 0) alpha0 = alpha;
         if (!(alpha > eps * alpha0)) break;
@@ -232,40 +245,31 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             v[s] = x0 - beta;
             if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
         }
-        if (threadIdx.x == 0 && p >= c0 && p < c1) {
-            // drop the pivot from the list of open columns (swap with the last)
-            const int jp = p - c0, t = apos[jp], last = alist[s_na - 1];
-            sel[jp] = 1;
-            alist[t] = last;
-            apos[last] = t;
-            s_na = s_na - 1;
-        }
         __syncthreads();
-        // apply the reflector to the open columns, two per warp, with U rows per lane in
-        // flight per column (independent loads keep bytes in flight to cover the memory
-        // latency), then downdate their norms
-        const int nopen = s_na;
-        for (int t = 2 * warp; t < nopen; t += 2 * NW) {
+        // 3. this CTA's share of the open columns
+        const int lo = (int)(((int64_t)gi * nopen) / G), hi = (int)(((int64_t)(gi + 1) * nopen) / G);
+        unsigned long long wbest = 0;
+        for (int t = lo + 2 * warp; t < hi; t += 2 * NW) {
             const int j0 = alist[t];
-            const bool two = t + 1 < nopen;
+            const bool two = t + 1 < hi;
             const int j1 = two ? alist[t + 1] : j0;
-            T* col0 = Y + (int64_t)(c0 + j0) * r;
-            T* col1 = Y + (int64_t)(c0 + j1) * r;
+            T* col0 = Y + (int64_t)j0 * r;
+            T* col1 = Y + (int64_t)j1 * r;
             constexpr int U = 4;
             T w0 = 0, w1 = 0;
             int i = s + lane;
             for (; i + 32 * (U - 1) < r; i += 32 * U) {
-                T vv[U], a[U], b[U];
+                T vv[U], xa[U], xb[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     vv[u] = conj_(v[i + 32 * u]);
-                    a[u] = col0[i + 32 * u];
-                    b[u] = col1[i + 32 * u];
+                    xa[u] = col0[i + 32 * u];
+                    xb[u] = col1[i + 32 * u];
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    w0 = fma_(vv[u], a[u], w0);
-                    w1 = fma_(vv[u], b[u], w1);
+                    w0 = fma_(vv[u], xa[u], w0);
+                    w1 = fma_(vv[u], xb[u], w1);
                 }
             }
             for (; i < r; i += 32) {
@@ -278,32 +282,32 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             const T tw0 = tau * w0, tw1 = tau * w1;
             i = s + lane;
             for (; i + 32 * (U - 1) < r; i += 32 * U) {
-                T vv[U], a[U], b[U];
+                T vv[U], xa[U], xb[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     vv[u] = v[i + 32 * u];
-                    a[u] = col0[i + 32 * u];
-                    b[u] = col1[i + 32 * u];
+                    xa[u] = col0[i + 32 * u];
+                    xb[u] = col1[i + 32 * u];
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    col0[i + 32 * u] = fma_(-vv[u], tw0, a[u]);
-                    if (two) col1[i + 32 * u] = fma_(-vv[u], tw1, b[u]);
+                    col0[i + 32 * u] = fma_(-vv[u], tw0, xa[u]);
+                    if (two) col1[i + 32 * u] = fma_(-vv[u], tw1, xb[u]);
                 }
             }
             for (; i < r; i += 32) {
                 const T vv = v[i];
-                const T a = col0[i], b = col1[i];
-                col0[i] = fma_(-vv, tw0, a);
-                if (two) col1[i] = fma_(-vv, tw1, b);
+                const T xa = col0[i], xb = col1[i];
+                col0[i] = fma_(-vv, tw0, xa);
+                if (two) col1[i] = fma_(-vv, tw1, xb);
             }
             __syncwarp();
             for (int c = 0; c < (two ? 2 : 1); ++c) {
                 const int jj = c == 0 ? j0 : j1;
                 const T* col = c == 0 ? col0 : col1;
                 const T rsj = shfl_(lane == 0 ? col[s] : (T)0, 0);
-                double nv = nrm[jj] - abs2d(rsj);
-                if (nv < 1e-4 * ref[jj]) {
+                double nv = ldcg_(nrm + jj) - abs2d(rsj);
+                if (nv < 1e-4 * ldcg_(ref + jj)) {
                     double q = 0.0;
                     for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(col[i2]);
                     q = warp_sum(q);
@@ -311,9 +315,12 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
                     if (lane == 0) ref[jj] = q;
                 }
                 if (lane == 0) nrm[jj] = nv;
+                const unsigned long long kq = pivot_key(nv, jj);
+                wbest = kq > wbest ? kq : wbest;
             }
         }
-        __syncthreads();
+        wbest = block_max_u64<NT>(wbest, kred);
+        if (threadIdx.x == 0) kb[((s + 1) & 1) * G + gi] = wbest;
         k = s + 1;
     }
     if (gi == 0 && threadIdx.x == 0) kout[b] = k;
@@ -322,15 +329,15 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
 template <class T>
 static size_t cpqr_shm(int max_r, int max_m, int G)
 {
-    const int per = (max_m + G - 1) / G;
-    return sizeof(double) * 2 * (size_t)per + sizeof(int) * (size_t)(3 * per + 2) + sizeof(T) * (size_t)max_r + 64;
+    (void)G;
+    return sizeof(int) * (size_t)(2 * max_m + 2) + sizeof(T) * (size_t)max_r + 64;
 }
 
 template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
                         const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
-                        int max_m)
+                        int max_m, double* nrm, double* ref)
 {
     constexpr int NT = 256;
     if (nb <= 0) return cudaSuccess;
@@ -340,12 +347,12 @@ cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, 
     if (G == 1) {
         count_launches(1);
         cpqr_kernel<NT, T><<<nb, NT, shm, st>>>(G, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys,
-                                                status, spin_limit);
+                                                status, spin_limit, nrm, ref);
         return cudaGetLastError();
     }
     void* args[] = {(void*)&G, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y, (void*)&eps,
                     (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
-                    (void*)&spin_limit};
+                    (void*)&spin_limit, (void*)&nrm, (void*)&ref};
     count_launches(1);
     return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, T>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
 }
@@ -501,7 +508,7 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
                                               KernelK, int);                                                        \
     template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int64_t*, const int32_t*, int, const int64_t*, \
                                         T*, double, int32_t*, int32_t*, T*, unsigned int*, unsigned long long*,     \
-                                        int*, long long, int, int);                                                 \
+                                        int*, long long, int, int, double*, double*);                               \
     template int cpqr_max_ctas<T>(int, int, int);                                                                    \
     template cudaError_t launch_id_T<T>(cudaStream_t, int, const int64_t*, const int32_t*, const int32_t*, int,      \
                                         const int64_t*, const T*, const int32_t*, const T*, const int32_t*,         \

@@ -25,10 +25,10 @@ namespace rs {
 // sets DEV_SINGULAR; the loop still finishes.  The panel arithmetic (pivot values and the
 // panel's own elimination) runs in FP64 for every storage type T; the rank-NB trailing update
 // runs in T.
-template <int NT, int NB, class T>
+template <int NT, int NB, bool SP, class T>
 __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict__ msz, const int64_t* __restrict__ off,
         T* __restrict__ Aall, int32_t* __restrict__ ipiv, const int64_t* __restrict__ ipiv_off,
-        int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin, int sp)
+        int* __restrict__ pivbuf, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
 {
     constexpr int CB = 32;                 // own columns updated per chunk
     using W = typename sc_traits<T>::wide;      // FP64 panel arithmetic
@@ -43,11 +43,9 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
     const int m = msz[b];
     T* __restrict__ A = Aall + off[b];
     W* f = (W*)sm;                         // m: the current pivot column (panel step)
-    int k0_cur = 0;
-    // sp: the owner factors its panel in shared memory (NB columns of m after f), so the
+    // SP: the owner factors its panel in shared memory (NB columns of m after f), so the
     // column steps of the panel -- the serial part of a block step -- touch no global memory
     T* pan = (T*)(sm + (((size_t)sizeof(W) * m + 15) / 16) * 2);
-    auto pcol = [&](int jj) -> T* { return sp ? pan + (int64_t)jj * m : A + (int64_t)(k0_cur + jj) * m; };
     int32_t* ip = ipiv + ipiv_off[b];
     int* pb = pivbuf + (int64_t)b * 2 * NB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -56,14 +54,14 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
     for (int q = 0; q < npan; ++q) {
         const int k0 = q * NB, kw = min(NB, m - k0);
         if (q % G == gi) {
-            k0_cur = k0;
-            if (sp) {
+            T* pbase = SP ? pan : A + (int64_t)k0 * m;      // panel column jj at pbase + jj m
+            if (SP) {
                 for (int e = threadIdx.x; e < m * kw; e += NT) pan[e] = A[(int64_t)k0 * m + e];
                 __syncthreads();
             }
             for (int t = 0; t < kw; ++t) {
                 const int c = k0 + t;
-                const T* col = pcol(t);
+                const T* col = pbase + (int64_t)t * m;
                 double best = -1.0;
                 int bi = m;
                 for (int i = c + threadIdx.x; i < m; i += NT) {
@@ -88,14 +86,14 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 __syncthreads();
                 const int p = s_piv[t];
                 if (threadIdx.x < kw && p != c) {           // swap rows c, p inside the panel
-                    T* cj = pcol(threadIdx.x);
+                    T* cj = pbase + (int64_t)threadIdx.x * m;
                     const T u = cj[c];
                     cj[c] = cj[p];
                     cj[p] = u;
                 }
                 __syncthreads();
                 for (int i = threadIdx.x; i < m; i += NT) f[i] = cast_<W>(col[i]);
-                if (threadIdx.x < kw) s_row[threadIdx.x] = cast_<W>(pcol(threadIdx.x)[c]);
+                if (threadIdx.x < kw) s_row[threadIdx.x] = cast_<W>(pbase[(int64_t)threadIdx.x * m + c]);
                 __syncthreads();
                 const W pv = f[c];
                 const double apv = absd(pv);
@@ -105,7 +103,7 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 const W pinv = (apv > 0.0) ? W(1.0) / pv : W(0.0);
                 for (int e = threadIdx.x; e < m * kw; e += NT) {
                     const int jj = e / m, i = e - jj * m;
-                    T* cj = pcol(jj);
+                    T* cj = pbase + (int64_t)jj * m;
                     if (k0 + jj == c) {
                         cj[i] = cast_<T>((i == c) ? pinv : -f[i] * pinv);
                     } else {
@@ -115,7 +113,7 @@ __global__ void __launch_bounds__(NT) gj_kernel(int G, const int32_t* __restrict
                 }
                 __syncthreads();
             }
-            if (sp) {
+            if (SP) {
                 for (int e = threadIdx.x; e < m * kw; e += NT) A[(int64_t)k0 * m + e] = pan[e];
             }
             if (threadIdx.x < kw) pb[(q & 1) * NB + threadIdx.x] = s_piv[threadIdx.x];
@@ -209,20 +207,49 @@ static size_t gj_shm(int max_m, bool sp)
 template <class T>
 static bool gj_sp(int max_m, int nb) { return nb == 1 && gj_shm<T>(max_m, true) <= 160 * 1024; }
 
-template <class T>
-int gj_max_ctas(int max_m, int nb)
+template <bool SP, class T>
+static int gj_capacity(size_t shm)
 {
-    const size_t shm = gj_shm<T>(max_m, gj_sp<T>(max_m, nb));
-    cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, SP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) !=
+        cudaSuccess)
+        return 0;
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<GJ_NT, GJ_NB, T>, GJ_NT, shm) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_kernel<GJ_NT, GJ_NB, SP, T>, GJ_NT, shm) != cudaSuccess)
         return 0;
     return per_sm * sms;
 }
 
+template <class T>
+int gj_max_ctas(int max_m, int nb)
+{
+    const bool sp = gj_sp<T>(max_m, nb);
+    const size_t shm = gj_shm<T>(max_m, sp);
+    return sp ? gj_capacity<true, T>(shm) : gj_capacity<false, T>(shm);
+}
+
 int gj_panel_width() { return GJ_NB; }
+
+template <bool SP, class T>
+static cudaError_t launch_gj_t(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A,
+                               int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf, unsigned int* bar, int* status,
+                               long long spin_limit, size_t shm)
+{
+    cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, SP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shm);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    if (G == 1) {
+        gj_kernel<GJ_NT, GJ_NB, SP, T><<<nb, GJ_NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status,
+                                                               spin_limit);
+        return cudaGetLastError();
+    }
+    void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&pivbuf,
+                    (void*)&bar, (void*)&status, (void*)&spin_limit};
+    return cudaLaunchCooperativeKernel((void*)gj_kernel<GJ_NT, GJ_NB, SP, T>, dim3((unsigned)(nb * G)), dim3(GJ_NT),
+                                       args, shm, st);
+}
 
 template <class T>
 cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A,
@@ -230,22 +257,12 @@ cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, 
                               long long spin_limit, int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
-    int sp = gj_sp<T>(max_m, nb) ? 1 : 0;
-    const size_t shm = gj_shm<T>(max_m, sp != 0);
-    cudaError_t e = cudaFuncSetAttribute(gj_kernel<GJ_NT, GJ_NB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const bool sp = gj_sp<T>(max_m, nb);
+    const size_t shm = gj_shm<T>(max_m, sp);
+    cudaError_t e = sp ? launch_gj_t<true, T>(st, nb, G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status, spin_limit, shm)
+                       : launch_gj_t<false, T>(st, nb, G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status, spin_limit,
+                                               shm);
     if (e != cudaSuccess) return e;
-    if (G == 1) {
-        count_launches(1);
-        gj_kernel<GJ_NT, GJ_NB, T><<<nb, GJ_NT, shm, st>>>(G, m, off, A, ipiv, ipiv_off, pivbuf, bar, status,
-                                                           spin_limit, sp);
-    } else {
-        void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&ipiv, (void*)&ipiv_off, (void*)&pivbuf,
-                        (void*)&bar, (void*)&status, (void*)&spin_limit, (void*)&sp};
-        count_launches(1);
-        e = cudaLaunchCooperativeKernel((void*)gj_kernel<GJ_NT, GJ_NB, T>, dim3((unsigned)(nb * G)), dim3(GJ_NT), args,
-                                        shm, st);
-        if (e != cudaSuccess) return e;
-    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launches(1);

@@ -100,6 +100,7 @@ int check_status(rs_op* op, cudaStream_t st)
     RS_CUDA(cudaMemcpy(&s, op->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (s & DEV_TIMEOUT) return fail(RS_E_TIMEOUT, "a device-side wait exceeded spin_limit");
     if (s & DEV_SINGULAR) return fail(RS_E_SINGULAR, "pivot below 1e3 unit roundoff times the largest earlier pivot");
+    if (s & DEV_BADSIZE) return fail(RS_E_CUDA, "a kernel found an out-of-range index and stopped");
     return RS_OK;
 }
 
@@ -125,7 +126,7 @@ namespace {
 
 // Workspace of the ID phase, released when rs_factor returns.
 struct IdWork {
-    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys;
+    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms;
 };
 
 template <class T>
@@ -201,15 +202,18 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
     const int max_r = L.max_r, max_m = L.max_m;
-    const int G = choose_group(nb, max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
+    // the open columns are re-split every step, so a group may take one CTA per 16 columns
+    const int G = choose_group(nb, 2 * max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
     RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * 2 * (size_t)nb * G));
+    RS_CUDA(w.norms.alloc(sizeof(double) * 2 * (size_t)(sum_m + 1)));
     {
     // the rank is known only afterwards: the work is added once k is read back
     ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0);
     RS_CUDA(launch_cpqr<T>(st, nb, G, L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
                         w.Y.as<T>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<T>(),
                         op->d_bar.as<unsigned int>(), w.keys.as<unsigned long long>(), op->d_status.as<int>(),
-                        (long long)op->opts.spin_limit, max_r, max_m));
+                        (long long)op->opts.spin_limit, max_r, max_m, w.norms.as<double>(),
+                        w.norms.as<double>() + sum_m + 1));
     }
     if ((rc = check_status(op, st))) return rc;
     std::vector<int32_t> k32(nb), piv(sum_m);

@@ -84,6 +84,7 @@ int check_ctx(const IdCtx& ctx, cudaStream_t st)
     RS_CUDA(cudaMemcpy(&s, ctx.status, sizeof(int), cudaMemcpyDeviceToHost));
     if (s & DEV_TIMEOUT) return fail(RS_E_TIMEOUT, "a device-side wait exceeded spin_limit");
     if (s & DEV_SINGULAR) return fail(RS_E_SINGULAR, "pivot below 1e3 unit roundoff times the largest earlier pivot");
+    if (s & DEV_BADSIZE) return fail(RS_E_CUDA, "a kernel found an out-of-range index and stopped");
     return RS_OK;
 }
 
@@ -213,7 +214,7 @@ int compress_forms(const IdCtx& ctx, cudaStream_t st, std::vector<CForm*>& forms
             max_m = std::max(max_m, jb.q->a);
             max_el = std::max<int64_t>(max_el, (int64_t)jb.r * jb.q->a);
         }
-        DevMem d_lists, d_zp, d_act_off, d_y_off, d_nn, Y, piv, diag, kk, keys;
+        DevMem d_lists, d_zp, d_act_off, d_y_off, d_nn, Y, piv, diag, kk, keys, norms;
         int rc;
         if ((rc = upload_vec(d_lists, lists, st))) return rc;
         if ((rc = upload_vec(d_zp, zp, st))) return rc;
@@ -232,10 +233,11 @@ int compress_forms(const IdCtx& ctx, cudaStream_t st, std::vector<CForm*>& forms
         RS_CUDA(cudaMemsetAsync(ctx.bar->p, 0, sizeof(unsigned int) * (size_t)nb, st));
         const int G = choose_group(nb, max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
         RS_CUDA(keys.alloc(sizeof(unsigned long long) * 2 * (size_t)nb * G));
+        RS_CUDA(norms.alloc(sizeof(double) * 2 * (size_t)(sum_a + 1)));
         RS_CUDA(launch_cpqr<T>(st, nb, G, d_act_off.as<int64_t>(), d_nn.as<int32_t>(), 0, d_y_off.as<int64_t>(),
                                Y.as<T>(), eps, kk.as<int32_t>(), piv.as<int32_t>(), diag.as<T>(),
                                ctx.bar->as<unsigned int>(), keys.as<unsigned long long>(), ctx.status, ctx.spin,
-                               max_r, max_m));
+                               max_r, max_m, norms.as<double>(), norms.as<double>() + sum_a + 1));
         if ((rc = check_ctx(ctx, st))) return rc;
         std::vector<int32_t> k32(nb), ph((size_t)sum_a);
         RS_CUDA(cudaMemcpy(k32.data(), kk.p, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));

@@ -84,14 +84,15 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
                               int max_entries);
 
 // Column-pivoted QR (Eq. 2.1) of every box's Y, G CTAs per box (cooperative when G > 1).
-// Column norms and pivot choices are FP64 for every T.  Outputs: kout[b],
+// Column norms and pivot choices are FP64 for every T; nrm and ref are FP64 work arrays of
+// act_off[nb] entries each (the squared column norms, shared by the group's CTAs).  Outputs: kout[b],
 // piv[act_off[b] + s] = physical column of pivot s (s < k), diag[act_off[b] + s] = R_ss.
 // Y is overwritten by the factorisation (rows < k hold R).
 template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
                         const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
-                        int max_m);
+                        int max_m, double* nrm, double* ref);
 // Largest grid of the cpqr kernel that can be co-resident for these sizes.
 template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G);
