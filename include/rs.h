@@ -110,7 +110,7 @@ int rs_tree_level_sets(const rs_tree* tree, int level, const int64_t* child_k,
                        const int64_t* child_skel, double proxy_radius_factor,
                        int64_t* m, int64_t* act, int64_t* nnear, int64_t* near);
 
-/* Factor (Algorithm 1; Algorithm 2 line 9 for E).  kernel: see rs_kernel.  a: host, N
+/* Factor (Algorithm 1; Algorithm 2 for E).  kernel: see rs_kernel.  a: host, N
  * values of a(x) in input order, or NULL (a = 1).  eps: ID tolerance; a CPQR step is kept
  * while |R_ss| > eps |R_00| (Eq. 2.1).  opts: NULL = defaults.  stream: cudaStream_t or
  * NULL (legacy default stream).  The factors stay resident on the current device until

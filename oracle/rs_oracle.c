@@ -13,7 +13,7 @@
  *     near rows: neighbours' active points strictly inside the proxy circle, in
  *     (neighbour, active) order; proxy: P points c + R(cos 2 pi j/P, sin 2 pi j/P) with
  *     R = factor x the larger half-width (Sec. 2.2, equivalent densities);
- *   - E_i = (R_i F_i^{-1} L_i)^{-1} as in Algorithm 1 line 11 (the "E = R F^{-1} L" of
+ *   - E_i = (R_i F_i^{-1} L_i)^{-1} as in Algorithm 1 (the "E = R F^{-1} L" of
  *     Sec. 2.4 contradicts Algorithm 1 and the derivation of Eq. 2.11);
  *   - the Helmholtz kernel is +(i/4) H0 and the system is put in the symmetric form
  *     of Eq. (5.6) by the diagonal similarity S = diag(kappa sqrt(b)).

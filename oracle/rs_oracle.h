@@ -15,7 +15,7 @@
  *                  factored in the symmetric form of Eq. (5.6), S^{-1} A S with
  *                  S = diag(kappa sqrt(b)); ro_solve takes and returns the unscaled f, x
  *   - binary tree by alternating bisection (Sec. 2.2), proxy-accelerated IDs (Sec. 2.2,
- *     Eq. 2.1), the HSS inversion of Algorithm 1 with the E formula of Algorithm 2 line 9,
+ *     Eq. 2.1), the HSS inversion of Algorithm 1 with the E formula of Algorithm 2,
  *     and the inverse apply of Algorithm 6 restated from Eqs. (2.10)-(2.12).
  *
  * All arrays are host memory, caller-owned unless stated.  Complex values are interleaved

@@ -3,7 +3,7 @@
 //   assemble_Y : Y_i = [ K(near_i, I_i) ; K(proxy_i, I_i) ]  (Sec. 2.2, equivalent densities)
 //   cpqr       : Householder QR with column pivoting of Y_i  (Sec. 2.1, Eq. 2.1)
 //   id_T       : T_i = R11^{-1} R12                           (Eq. 2.1)
-//   assemble_F : F_i = D_i (+ diag(E_c1, E_c2))                (Algorithm 1, lines 2-6)
+//   assemble_F : F_i = D_i (+ diag(E_c1, E_c2))                (Algorithm 1)
 #include "k_common.cuh"
 
 namespace rs {

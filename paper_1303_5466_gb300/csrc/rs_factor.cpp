@@ -278,7 +278,7 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     return check_status(op, st);
 }
 
-// Inversion phase of one level (Algorithm 1 lines 3-11 with the E of Algorithm 2 line 9).
+// Inversion phase of one level (Algorithm 1 with the E of Algorithm 2).
 template <class T>
 int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
 {

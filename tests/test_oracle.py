@@ -271,7 +271,7 @@ def test_helmholtz_proxy_factor_vs_dense(oracle_mod):
 
 
 def test_E_equals_four_term_formula(oracle_mod):
-    """E_i^{-1} = Phi_ss + T Phi_rs + Phi_sr T^T + T Phi_rr T^T (Algorithm 2, line 9)."""
+    """E_i^{-1} = Phi_ss + T Phi_rs + Phi_sr T^T + T Phi_rr T^T (Algorithm 2)."""
     n, leaf = 32, 8
     F = oracle_mod.Factorization(n, leaf, 1e-10)
     for l, j in [(F.depth, 5), (2, 1)]:
