@@ -82,6 +82,12 @@ typedef struct {
                                     launch stream (rs_op_profile)                     [0]    */
     int hss_leaf;                /* largest leaf run of the HSS1D trees (k_cut > 0)  [64]   */
     double hss_eps;              /* ID tolerance of that compression; 0 = eps         [0]    */
+    int spd_inverse;             /* 1: invert F, E and the root of a real symmetric kernel
+                                    (RS_LAPLACE) by the symmetric sweep without pivoting
+                                    (half the flops of Gauss-Jordan); a level whose pivots
+                                    show a block that is not positive definite to working
+                                    accuracy is redone with pivoted Gauss-Jordan
+                                    (rs_stats.spd_fallbacks).  0: always pivoted GJ  [1]    */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);
@@ -179,6 +185,7 @@ typedef struct {
     int64_t bytes_compressed;    /* device bytes of their compressed forms                 */
     int64_t bytes_dense_replaced;/* bytes the same blocks (Phi, E, T) take densely         */
     double ms_compress;          /* wall time of the compression                           */
+    int spd_fallbacks;           /* inversions redone with pivoted Gauss-Jordan (opts.spd_inverse) */
 } rs_stats;
 int rs_op_stats(const rs_op* op, rs_stats* out);
 
@@ -189,10 +196,10 @@ enum {
     RS_PROF_CPQR = 1,         /* column-pivoted QR of Y (flops 4rmk - 2k^2(r+m) + 4k^3/3)       */
     RS_PROF_ID_T = 2,         /* T = R11^{-1} R12 (flops k^2 (m-k))                             */
     RS_PROF_ASSEMBLE_F = 3,   /* F (work unit: entries)                                         */
-    RS_PROF_INV_F = 4,        /* Gauss-Jordan F^{-1} (flops 2 m^3)                              */
+    RS_PROF_INV_F = 4,        /* F^{-1}: flops m^3 by the symmetric sweep, 2 m^3 by Gauss-Jordan  */
     RS_PROF_GEMM_E = 5,       /* W = F^{-1} L, E^{-1} = R W (flops 2m(m-k)k + 2k(m-k)k)          */
-    RS_PROF_INV_E = 6,        /* Gauss-Jordan E (flops 2 k^3)                                   */
-    RS_PROF_INV_ROOT = 7,     /* root F^{-1} (flops 2 m^3)                                      */
+    RS_PROF_INV_E = 6,        /* E: flops k^3 by the sweep, 2 k^3 by Gauss-Jordan                 */
+    RS_PROF_INV_ROOT = 7,     /* root F^{-1}: flops m^3 by the sweep, 2 m^3 by Gauss-Jordan       */
     RS_PROF_SOLVE = 8,        /* inverse apply (flops per RHS 2(2m^2 + 2k^2 + 2k(m-k)))         */
     RS_PROF_COUNT = 9
 };

@@ -40,7 +40,7 @@ class rs_opts(C.Structure):
     _fields_ = [("proxy_points", C.c_int), ("proxy_radius_factor", C.c_double), ("precision", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max_iter", C.c_int), ("k_cut", C.c_int64),
                 ("spin_limit", C.c_int64), ("profile", C.c_int), ("hss_leaf", C.c_int),
-                ("hss_eps", C.c_double)]
+                ("hss_eps", C.c_double), ("spd_inverse", C.c_int)]
 
 
 class rs_stats(C.Structure):
@@ -48,7 +48,8 @@ class rs_stats(C.Structure):
                 ("bytes_workspace", C.c_int64), ("flops_factor", C.c_double), ("flops_solve_per_rhs", C.c_double),
                 ("bytes_solve", C.c_double), ("ms_tree", C.c_double), ("ms_inverse", C.c_double),
                 ("refine_iters", C.c_int), ("refine_residual", C.c_double), ("compressed_boxes", C.c_int64),
-                ("bytes_compressed", C.c_int64), ("bytes_dense_replaced", C.c_int64), ("ms_compress", C.c_double)]
+                ("bytes_compressed", C.c_int64), ("bytes_dense_replaced", C.c_int64), ("ms_compress", C.c_double),
+                ("spd_fallbacks", C.c_int)]
 
 
 _lib = None

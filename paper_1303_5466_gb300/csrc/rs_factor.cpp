@@ -153,6 +153,56 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
     return check_status(op, st);
 }
 
+// Symmetric sweep inverse of a level's SPD blocks (real kernels only).  *not_spd is set, and
+// the status word cleared, when a block is not positive definite to working accuracy: the
+// blocks are then partly swept and the caller rebuilds them for run_gj.
+template <class T>
+int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, T* A,
+              const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls,
+              bool* not_spd)
+{
+    *not_spd = false;
+    if (max_m <= 0) return RS_OK;
+    if constexpr (is_cplx<T>::value) {
+        return fail(RS_E_INVALID, "the symmetric sweep is for real kernels");
+    } else {
+        const int NB = sweep_panel_width();
+        std::vector<int64_t> pb_off(nb);
+        for (int b = 0; b < nb; ++b) pb_off[b] = 2 * (int64_t)NB * size_off[b];
+        DevMem d_pboff;
+        int rc;
+        if ((rc = upload(d_pboff, pb_off, st))) return rc;
+        RS_CUDA(op->d_pb.alloc(sizeof(T) * 2 * (size_t)NB * (size_t)(size_off[nb] + 1)));
+        RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
+        RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
+        // panels are dealt back and forth, so a group of G CTAs wants at least 2G panels
+        const int cap = sweep_max_ctas<T>();
+        const int G = choose_group(nb, max_m * 16 / NB, [&](int) { return cap; });
+        double work = 0.0;
+        for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
+        {
+            ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb]);
+            RS_CUDA(launch_sweep_inverse<T>(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_pb.as<T>(),
+                                            d_pboff.as<int64_t>(), op->d_bar.as<unsigned int>(),
+                                            op->d_status.as<int>(), (long long)op->opts.spin_limit, max_m));
+        }
+        RS_CUDA(cudaStreamSynchronize(st));
+        prof_flush(op);
+        int s = 0;
+        RS_CUDA(cudaMemcpy(&s, op->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (s & DEV_NOT_SPD) {
+            RS_CUDA(cudaMemsetAsync(op->d_status.p, 0, sizeof(int), st));
+            op->stats.spd_fallbacks += 1;
+            *not_spd = true;
+            return RS_OK;
+        }
+        return check_status(op, st);
+    }
+}
+
+// Whether the inverses of this operator go through the symmetric sweep first.
+bool use_sweep(const rs_op* op) { return op->kind == RS_LAPLACE && op->opts.spd_inverse != 0; }
+
 // ID phase of one level (Sec. 2.2 proxy ID, Eq. 2.1).
 template <class T>
 int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st)
@@ -295,15 +345,24 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     if ((rc = upload(L.d_phi_off, L.phi_off, st))) return rc;
     RS_CUDA(L.d_Phi.alloc(sizeof(T) * (size_t)(L.phi_off[nb] + 1)));
     const bool leaf = (L.l == op->d);
-    {
-    ProfScope ps(op, RS_PROF_ASSEMBLE_F, st, (double)L.phi_off[nb], sizeof(T) * (double)L.phi_off[nb]);
-    RS_CUDA(launch_assemble_F<T>(st, nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), L.d_perm.as<int32_t>(),
-                              op->d_a.as<double>(), L.d_phi_off.as<int64_t>(), L.d_Phi.as<T>(),
-                              child ? child->d_k.as<int32_t>() : nullptr, child ? child->d_e_off.as<int64_t>() : nullptr,
-                              child ? child->d_E.as<T>() : nullptr, op->K, L.max_m));
+    auto assemble = [&]() -> int {
+        ProfScope ps(op, RS_PROF_ASSEMBLE_F, st, (double)L.phi_off[nb], sizeof(T) * (double)L.phi_off[nb]);
+        RS_CUDA(launch_assemble_F<T>(st, nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(),
+                                     L.d_perm.as<int32_t>(), op->d_a.as<double>(), L.d_phi_off.as<int64_t>(),
+                                     L.d_Phi.as<T>(), child ? child->d_k.as<int32_t>() : nullptr,
+                                     child ? child->d_e_off.as<int64_t>() : nullptr,
+                                     child ? child->d_E.as<T>() : nullptr, op->K, L.max_m));
+        return RS_OK;
+    };
+    if ((rc = assemble())) return rc;
+    const int cls_f = L.l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F;
+    bool redo = true;
+    if (use_sweep(op)) {
+        if ((rc = run_sweep<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f, &redo)))
+            return rc;
+        if (redo && (rc = assemble())) return rc;
     }
-    if ((rc = run_gj<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m,
-                     L.l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F)))
+    if (redo && (rc = run_gj<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f)))
         return rc;
     if (L.l == 0) return RS_OK;
     // W = Phi[:, :k] + Phi[:, k:] T^T ;  E^{-1} = W[:k, :] + T W[k:, :]
@@ -351,6 +410,16 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     RS_CUDA(cudaStreamSynchronize(st));
     DevMem d_k32;
     if ((rc = upload(d_k32, to32(L.k), st))) return rc;
+    redo = true;
+    if (use_sweep(op)) {
+        if ((rc = run_sweep<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E,
+                               &redo)))
+            return rc;
+        if (redo && !p1.empty())     // E^{-1} again from W (the sweep overwrote it)
+            RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
+                                   L.d_E.as<T>(), W.as<T>()));
+    }
+    if (!redo) return RS_OK;
     return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E);
 }
 
@@ -436,6 +505,8 @@ void compute_stats(rs_op* op)
     s.n_side = op->n;
     s.root_m = op->lev[0].m[0];
     double ff = 0.0, sw = 0.0;
+    // an SPD inverse by the symmetric sweep does m^3 flops, Gauss-Jordan 2 m^3
+    const double inv = (use_sweep(op) && s.spd_fallbacks == 0) ? 1.0 : 2.0;
     int64_t bytes = 0, cboxes = 0, replaced = 0;
     for (int l = 1; l <= op->d; ++l) {
         const Level& L = op->lev[l];
@@ -443,9 +514,9 @@ void compute_stats(rs_op* op)
             const double m = (double)L.m[b], k = (double)L.k[b], r = (double)L.r[b];
             ff += 4.0 * r * m * k - 2.0 * k * k * (r + m) + 4.0 * k * k * k / 3.0;   // CPQR, k steps
             ff += k * k * (m - k);                                                // T = R11^{-1} R12
-            ff += 2.0 * m * m * m;                                                // F^{-1}
+            ff += inv * m * m * m;                                                // F^{-1}
             ff += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;                  // W, E^{-1}
-            ff += 2.0 * k * k * k;                                                // E
+            ff += inv * k * k * k;                                                // E
             if (!L.cmp.empty() && L.cmp[b]) {
                 ++cboxes;
                 replaced += (int64_t)(m * m + k * k + k * (m - k)) * op->esz;
@@ -459,7 +530,7 @@ void compute_stats(rs_op* op)
         bytes += L.act_off.back() * 8 + L.nb * 64;
     }
     const double m0 = (double)op->lev[0].m[0];
-    ff += 2.0 * m0 * m0 * m0;
+    ff += inv * m0 * m0 * m0;
     sw += m0 * m0;
     bytes += (int64_t)(m0 * m0 * op->esz);
     bytes += op->cstore_n * op->esz;

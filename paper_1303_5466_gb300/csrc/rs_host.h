@@ -221,7 +221,7 @@ struct rs_op {
     rs::KernelK K{};
     std::vector<int64_t> input_of_g;
     std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
-    rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow;
+    rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // solve workspace (grown on demand)
     rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_z, s_in, s_out, s_out2;
     int64_t s_nrhs = 0;

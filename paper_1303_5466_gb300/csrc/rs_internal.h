@@ -26,7 +26,7 @@ int cuda_fail(cudaError_t e, const char* what);
 void count_launches(int n);
 
 // Device status word bits written by kernels (never a trap): the host maps them to RS_E_*.
-enum : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2, DEV_BADSIZE = 4 };
+enum : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2, DEV_BADSIZE = 4, DEV_NOT_SPD = 8 };
 
 // Pivot key of the column-pivoted QR: the squared column norm with its 40 low mantissa bits
 // cleared (relative step 2^-12), and the low bits holding (2^40-1 - column index), so that the
@@ -126,6 +126,20 @@ cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, 
 template <class T>
 int gj_max_ctas(int max_m, int nb);
 int gj_panel_width();
+
+// In-place inverse of nb symmetric positive definite matrices (real T) by the symmetric sweep
+// (k_sweep.cu), G CTAs per matrix (cooperative when G > 1): sizes m[b], offsets off[b]; Pb: 2 *
+// sweep_panel_width() * m[b] elements per matrix at pb_off[b] (16-byte aligned); bar: one
+// counter per matrix, zeroed before the launch.  Reads the lower triangle, writes the full
+// inverse.  A matrix that is not SPD to working accuracy sets DEV_NOT_SPD and is left partly
+// swept.
+template <class T>
+cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A, T* Pb,
+                                 const int64_t* pb_off, unsigned int* bar, int* status, long long spin_limit,
+                                 int max_m);
+template <class T>
+int sweep_max_ctas();
+int sweep_panel_width();
 
 // Grouped GEMM over `np` problems (device descriptors), total tiles `tiles`.
 template <class T>

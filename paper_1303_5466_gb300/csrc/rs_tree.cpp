@@ -122,6 +122,7 @@ void rs_opts_default(rs_opts* o)
     o->spin_limit = (int64_t)1 << 26;
     o->profile = 0;
     o->hss_leaf = 64;
+    o->spd_inverse = 1;
     o->hss_eps = 0.0;
 }
 
