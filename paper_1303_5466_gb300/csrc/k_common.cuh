@@ -33,7 +33,9 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Block-wide sum with a fixed reduction order (same result in every CTA for the same data).
+// Block-wide sum with a fixed reduction order (same result in every CTA for the same data);
+// scratch holds NT / 32 + 1 doubles.  Warp 0 adds the warp sums, so the FP64 pipe sees one
+// short butterfly rather than every thread adding them all.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* scratch)
 {
@@ -42,10 +44,14 @@ __device__ __forceinline__ double block_sum(double v, double* scratch)
     __syncthreads();
     if (l == 0) scratch[w] = v;
     __syncthreads();
-    double t = 0.0;
+    if (w == 0) {
+        double t = l < NT / 32 ? scratch[l] : 0.0;
 #pragma unroll
-    for (int q = 0; q < NT / 32; ++q) t += scratch[q];
-    return t;
+        for (int o = NT / 64; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (l == 0) scratch[NT / 32] = t;
+    }
+    __syncthreads();
+    return scratch[NT / 32];
 }
 
 template <int NT>

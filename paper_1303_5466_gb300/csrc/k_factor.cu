@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
         int* __restrict__ status, long long spin, double* __restrict__ nrm_all, double* __restrict__ ref_all)
 {
     extern __shared__ double smem[];
-    __shared__ double dred[NT / 32];
+    __shared__ double dred[NT / 32 + 1];
     __shared__ unsigned long long kred[NT / 32];
     __shared__ unsigned long long s_key;
 
@@ -246,9 +246,10 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
         }
         __syncthreads();
-        // 3. this CTA's share of the open columns
+        // 3. this CTA's share of the open columns, two per warp
         const int lo = (int)(((int64_t)gi * nopen) / G), hi = (int)(((int64_t)(gi + 1) * nopen) / G);
         unsigned long long wbest = 0;
+        const bool lo16 = lane < 16;       // paired bookkeeping: lanes 0-15 column j0, 16-31 j1
         for (int t = lo + 2 * warp; t < hi; t += 2 * NW) {
             const int j0 = alist[t];
             const bool two = t + 1 < hi;
@@ -263,8 +264,8 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     vv[u] = conj_(v[i + 32 * u]);
-                    xa[u] = col0[i + 32 * u];
-                    xb[u] = col1[i + 32 * u];
+                    xa[u] = ldcg_(col0 + i + 32 * u);
+                    xb[u] = ldcg_(col1 + i + 32 * u);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -274,50 +275,61 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             }
             for (; i < r; i += 32) {
                 const T vv = conj_(v[i]);
-                w0 = fma_(vv, col0[i], w0);
-                w1 = fma_(vv, col1[i], w1);
+                w0 = fma_(vv, ldcg_(col0 + i), w0);
+                w1 = fma_(vv, ldcg_(col1 + i), w1);
             }
-            w0 = warp_sum(w0);
-            w1 = warp_sum(w1);
-            const T tw0 = tau * w0, tw1 = tau * w1;
+            // both sums in one butterfly: lanes 0-15 end with w0's, 16-31 with w1's
+            T wp = (lo16 ? w0 : w1) + shfl_xor_(lo16 ? w1 : w0, 16);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) wp += shfl_xor_(wp, o);
+            const T twp = tau * wp;
+            const T tw0 = shfl_(twp, 0), tw1 = shfl_(twp, 16);
+            T rs0 = 0, rs1 = 0;                // row s after the update (lane 0)
             i = s + lane;
             for (; i + 32 * (U - 1) < r; i += 32 * U) {
                 T vv[U], xa[U], xb[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     vv[u] = v[i + 32 * u];
-                    xa[u] = col0[i + 32 * u];
-                    xb[u] = col1[i + 32 * u];
+                    xa[u] = ldcg_(col0 + i + 32 * u);
+                    xb[u] = ldcg_(col1 + i + 32 * u);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    col0[i + 32 * u] = fma_(-vv[u], tw0, xa[u]);
-                    if (two) col1[i + 32 * u] = fma_(-vv[u], tw1, xb[u]);
+                    xa[u] = fma_(-vv[u], tw0, xa[u]);
+                    xb[u] = fma_(-vv[u], tw1, xb[u]);
+                    col0[i + 32 * u] = xa[u];
+                    if (two) col1[i + 32 * u] = xb[u];
                 }
+                if (i == s) { rs0 = xa[0]; rs1 = xb[0]; }
             }
             for (; i < r; i += 32) {
                 const T vv = v[i];
-                const T xa = col0[i], xb = col1[i];
-                col0[i] = fma_(-vv, tw0, xa);
-                if (two) col1[i] = fma_(-vv, tw1, xb);
+                const T xa = fma_(-vv, tw0, ldcg_(col0 + i)), xb = fma_(-vv, tw1, ldcg_(col1 + i));
+                col0[i] = xa;
+                if (two) col1[i] = xb;
+                if (i == s) { rs0 = xa; rs1 = xb; }
             }
-            __syncwarp();
-            for (int c = 0; c < (two ? 2 : 1); ++c) {
-                const int jj = c == 0 ? j0 : j1;
-                const T* col = c == 0 ? col0 : col1;
-                const T rsj = shfl_(lane == 0 ? col[s] : (T)0, 0);
-                double nv = ldcg_(nrm + jj) - abs2d(rsj);
-                if (nv < 1e-4 * ldcg_(ref + jj)) {
+            // downdated squared norms of both columns at once (R_sj is row s of column j)
+            const T r0 = shfl_(rs0, 0), r1 = shfl_(rs1, 0);
+            const int jj = lo16 ? j0 : j1;
+            double nv = ldcg_(nrm + jj) - abs2d(lo16 ? r0 : r1);
+            const unsigned need = __ballot_sync(0xffffffffu, nv < 1e-4 * ldcg_(ref + jj));
+            if (need & 0x00010001u) {
+                __syncwarp();                  // the recomputation reads the warp's stores
+                for (int c = 0; c < (two ? 2 : 1); ++c) {
+                    if (!(need & (1u << (16 * c)))) continue;
+                    const T* col = c == 0 ? col0 : col1;
                     double q = 0.0;
-                    for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(col[i2]);
+                    for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(ldcg_(col + i2));
                     q = warp_sum(q);
-                    nv = q;
-                    if (lane == 0) ref[jj] = q;
+                    if (!two || (lane >> 4) == c) nv = q;
+                    if (lane == 16 * c) ref[jj] = q;
                 }
-                if (lane == 0) nrm[jj] = nv;
-                const unsigned long long kq = pivot_key(nv, jj);
-                wbest = kq > wbest ? kq : wbest;
             }
+            if (lane == 0 || (lane == 16 && two)) nrm[jj] = nv;
+            const unsigned long long kq = pivot_key(nv, jj);
+            wbest = kq > wbest ? kq : wbest;
         }
         wbest = block_max_u64<NT>(wbest, kred);
         if (threadIdx.x == 0) kb[((s + 1) & 1) * G + gi] = wbest;

@@ -108,8 +108,10 @@ int check_status(rs_op* op, cudaStream_t st)
 
 // Pick the CTA group size per box for a cooperative kernel (capacity(G): co-resident CTAs
 // when each box takes G CTAs, 0 if such a CTA does not fit on an SM).  Start from the smallest
-// G whose CTAs fit; keep it when the boxes alone fill the GPU, otherwise take as many CTAs per
-// box as stay co-resident (at most one per 32 columns and 1024 in all).
+// G whose CTAs fit; keep it when the boxes alone fill the GPU.  Otherwise take up to
+// max_cols / 32 CTAs per box (and 1024), as many as stay co-resident, preferring a total
+// that loads every SM with the same number of CTAs: a group runs at the pace of its slowest
+// CTA, so CTAs that share an SM with one more neighbour than the others hold back the group.
 int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
 {
     const int gmax = std::max(1, std::min(max_cols / 32, 1024));
@@ -119,7 +121,20 @@ int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
     if (cap0 <= 0 || g0 == gmax || nb * g0 >= cap0) return g0;
     int G = std::min(gmax, cap0 / std::max(nb, 1));
     while (G > g0 && nb * G > capacity(G)) --G;
-    return std::max(G, g0);
+    G = std::max(G, g0);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms <= 0)
+        return G;
+    // evenness of the per-SM load of T CTAs: T / (sms * ceil(T / sms))
+    auto even = [&](int g) {
+        const double T = (double)nb * g;
+        return T / (sms * std::ceil(T / sms));
+    };
+    int best = G;
+    for (int g = G - 1; g >= g0 && g >= G / 2; --g)
+        if (even(g) > even(best) + 0.02) best = g;
+    return best;
 }
 
 namespace {
