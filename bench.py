@@ -247,7 +247,8 @@ def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
     s = P.rs_op_stats(op)
     rel = P.rs_residual(op, x, f, nrhs, st)
     out = {"factor_ms": e0.elapsed_time(e1), "refined_solve_ms": e1.elapsed_time(e2), "eps": 1e-6,
-           "refine_solves": s["refine_iters"], "residual": float(rel.max()), "bytes_factors": s["bytes_factors"]}
+           "refine_solves": s["refine_iters"], "refine_fp64_direct_sums": s["refine_fp64_sums"],
+           "residual": float(rel.max()), "bytes_factors": s["bytes_factors"]}
     P.rs_free(op)
     P.rs_free_tree(tree)
     return out

@@ -186,6 +186,9 @@ typedef struct {
     int64_t bytes_dense_replaced;/* bytes the same blocks (Phi, E, T) take densely         */
     double ms_compress;          /* wall time of the compression                           */
     int spd_fallbacks;           /* inversions redone with pivoted Gauss-Jordan (opts.spd_inverse) */
+    int refine_fp64_sums;        /* refined precisions: FP64 direct sums of the last rs_solve (the
+                                    first residual, and each confirmation of the tolerance;
+                                    the other corrections' products run in FP32)            */
 } rs_stats;
 int rs_op_stats(const rs_op* op, rs_stats* out);
 

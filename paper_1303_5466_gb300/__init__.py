@@ -49,7 +49,7 @@ class rs_stats(C.Structure):
                 ("bytes_solve", C.c_double), ("ms_tree", C.c_double), ("ms_inverse", C.c_double),
                 ("refine_iters", C.c_int), ("refine_residual", C.c_double), ("compressed_boxes", C.c_int64),
                 ("bytes_compressed", C.c_int64), ("bytes_dense_replaced", C.c_int64), ("ms_compress", C.c_double),
-                ("spd_fallbacks", C.c_int)]
+                ("spd_fallbacks", C.c_int), ("refine_fp64_sums", C.c_int)]
 
 
 _lib = None

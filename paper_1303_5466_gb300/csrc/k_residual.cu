@@ -1,6 +1,7 @@
 // k_residual.cu -- FP64 direct-sum residual r = f - A x of the Nystrom matrix (Laplace, or
 // Helmholtz in its original form A = a + kappa^2 b K with complex128 arithmetic), used by the
-// iterative refinement of the low-precision factorizations and by rs_residual.
+// iterative refinement of the low-precision factorizations and by rs_residual, and the update
+// r <- r - A dx of a residual by a small correction dx, whose product runs in FP32 (complex64).
 //
 // The off-diagonal entries depend only on the integer offset (d1, d2) between two grid points,
 // so they are tabulated once for the (2n-1)^2 offsets; the sum over all N^2 pairs is then one
@@ -38,10 +39,12 @@ constexpr int DS = 16;          // tile side of targets and sources
 constexpr int DS_RHS = 4;       // right-hand sides per pass
 
 // yg = A xg in grid order: yg[c N + g] = dg[g] xg[c N + g] + rs[g] sum_{g' != g} K(g - g') xg[c N + g']
-// (rs = NULL means 1).
-template <class S>
+// (rs = NULL means 1).  Products and the sum over one 16 x 16 source tile run in S; the tile
+// sums are added in A (A = S for the FP64 residual; A = FP64 for an FP32 product, so that the
+// FP32 rounding stays that of 256-term sums however large the grid).
+template <class S, class A>
 __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
-        const double* __restrict__ rs, const S* __restrict__ xg, S* __restrict__ yg, int nrhs)
+        const double* __restrict__ rs, const S* __restrict__ xg, A* __restrict__ yg, int nrhs)
 {
     __shared__ S Kw[2 * DS - 1][2 * DS];
     __shared__ S xs[DS_RHS][DS * DS];
@@ -53,9 +56,9 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restr
     const bool tin = ti1 < n && ti2 < n;
     for (int c0 = 0; c0 < nrhs; c0 += DS_RHS) {
         const int nc = min(DS_RHS, nrhs - c0);
-        S acc[DS_RHS];
+        A acc[DS_RHS];
 #pragma unroll
-        for (int c = 0; c < DS_RHS; ++c) acc[c] = S(0.0);
+        for (int c = 0; c < DS_RHS; ++c) acc[c] = A(0.0);
         for (int sy0 = 0; sy0 < n; sy0 += DS) {
             for (int sx0 = 0; sx0 < n; sx0 += DS) {
                 __syncthreads();
@@ -73,6 +76,9 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restr
                 }
                 __syncthreads();
                 if (tin) {
+                    S t[DS_RHS];
+#pragma unroll
+                    for (int c = 0; c < DS_RHS; ++c) t[c] = S(0.0);
 #pragma unroll 4
                     for (int j2 = 0; j2 < DS; ++j2) {
 #pragma unroll
@@ -80,17 +86,20 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restr
                             const S k = Kw[ly - j2 + DS - 1][lx - j1 + DS - 1];
 #pragma unroll
                             for (int c = 0; c < DS_RHS; ++c)
-                                if (c < nc) acc[c] = fma_(k, xs[c][j2 * DS + j1], acc[c]);
+                                if (c < nc) t[c] = fma_(k, xs[c][j2 * DS + j1], t[c]);
                         }
                     }
+#pragma unroll
+                    for (int c = 0; c < DS_RHS; ++c) acc[c] += cast_<A>(t[c]);
                 }
             }
         }
         if (tin) {
             const int64_t g = ti1 + (int64_t)n * ti2;
-            const S sum_scale = rs ? S(rs[g]) : S(1.0);
+            const A sum_scale = rs ? A(rs[g]) : A(1.0);
             for (int c = 0; c < nc; ++c)
-                yg[(int64_t)(c0 + c) * N + g] = fma_(dg[g], xg[(int64_t)(c0 + c) * N + g], sum_scale * acc[c]);
+                yg[(int64_t)(c0 + c) * N + g] =
+                    fma_(cast_<A>(dg[g]), cast_<A>(xg[(int64_t)(c0 + c) * N + g]), sum_scale * acc[c]);
         }
     }
 }
@@ -168,7 +177,7 @@ cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const S* Kt, const
     count_launches(4);
     to_grid_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, x, xg);
     dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
-    direct_sum_kernel<S><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
+    direct_sum_kernel<S, S><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
     residual_finish_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, f, yg, r);
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nrhs, st);
     if (e != cudaSuccess) return e;
@@ -176,6 +185,73 @@ cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const S* Kt, const
     colnorm2_kernel<S><<<g2, 256, 0, st>>>(N, nrhs, r, f, norms);
     return cudaGetLastError();
 }
+// Low-precision copy of a table or diagonal: out[i] = (L) in[i].
+template <class S, class L>
+__global__ void narrow_kernel(int64_t n, const S* __restrict__ in, L* __restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = cast_<L>(in[e]);
+}
+
+// xg[c N + g] = (L) dx[c N + ing[g]]
+template <class S, class L>
+__global__ void to_grid_narrow_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing, const S* __restrict__ x,
+                                      L* __restrict__ xg)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * nrhs) return;
+    const int64_t c = e / N, g = e - c * N;
+    xg[e] = cast_<L>(x[c * N + ing[g]]);
+}
+
+// r[c N + ing[g]] -= yg[c N + g]
+template <class S>
+__global__ void residual_sub_kernel(int64_t N, int nrhs, const int64_t* __restrict__ ing, const S* __restrict__ yg,
+                                    S* __restrict__ r)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * nrhs) return;
+    const int64_t c = e / N, g = e - c * N;
+    const int64_t i = c * N + ing[g];
+    r[i] = r[i] - yg[e];
+}
+
+template <class S, class L>
+cudaError_t launch_narrow(cudaStream_t st, int64_t n, const S* in, L* out)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    narrow_kernel<S, L><<<nblk(n), 256, 0, st>>>(n, in, out);
+    return cudaGetLastError();
+}
+
+template <class S, class L>
+cudaError_t launch_residual_update(cudaStream_t st, int n, int nrhs, const L* Kt, const L* dg, const double* rs,
+                                   const int64_t* ing, const S* dx, S* r, L* xg, S* yg, double* norms)
+{
+    const int64_t N = (int64_t)n * n;
+    count_launches(4);
+    to_grid_narrow_kernel<S, L><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, dx, xg);
+    dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
+    direct_sum_kernel<L, S><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
+    residual_sub_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, yg, r);
+    cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nrhs, st);
+    if (e != cudaSuccess) return e;
+    dim3 g2((unsigned)std::min<int64_t>(nblk(N), 1024), (unsigned)nrhs);
+    colnorm2_kernel<S><<<g2, 256, 0, st>>>(N, nrhs, r, r, norms);
+    return cudaGetLastError();
+}
+template cudaError_t launch_narrow<double, float>(cudaStream_t, int64_t, const double*, float*);
+template cudaError_t launch_narrow<cplx<double>, cplx<float>>(cudaStream_t, int64_t, const cplx<double>*,
+                                                              cplx<float>*);
+template cudaError_t launch_residual_update<double, float>(cudaStream_t, int, int, const float*, const float*,
+                                                           const double*, const int64_t*, const double*, double*,
+                                                           float*, double*, double*);
+template cudaError_t launch_residual_update<cplx<double>, cplx<float>>(cudaStream_t, int, int, const cplx<float>*,
+                                                                       const cplx<float>*, const double*,
+                                                                       const int64_t*, const cplx<double>*,
+                                                                       cplx<double>*, cplx<float>*, cplx<double>*,
+                                                                       double*);
 template cudaError_t launch_residual<double>(cudaStream_t, int, int, const double*, const double*, const double*,
                                              const int64_t*, const double*, const double*, double*, double*, double*,
                                              double*);

@@ -228,6 +228,9 @@ struct rs_op {
     // FP64 direct-sum residual (built on first use): offset table, diagonal, permutation,
     // and refinement workspace
     rs::DevMem d_ktab, d_diag, d_rs, d_ing, r_xg, r_yg, r_res, r_dx, r_x, r_norm;
+    // FP32 (complex64) copies of the table and diagonal, and grid scratch, for the products of
+    // the refinement's corrections
+    rs::DevMem d_ktab_lo, d_diag_lo, r_xg_lo;
     // Helmholtz symmetric scaling s = kappa sqrt(b): grid order, input order; scaled RHS
     rs::DevMem d_s, d_s_in, s_fs;
     // compressed store of the Sec. 3 forms (opts.k_cut)

@@ -234,5 +234,14 @@ cudaError_t launch_helmholtz_table(cudaStream_t st, int n, double h, double kapp
 template <class S>
 cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const S* Kt, const S* dg, const double* rs,
                             const int64_t* ing, const S* x, const S* f, S* xg, S* yg, S* r, double* norms);
+// out = (L) in, n entries (L = float or cplx<float> copies of the table and diagonal)
+template <class S, class L>
+cudaError_t launch_narrow(cudaStream_t st, int64_t n, const S* in, L* out);
+// r <- r - A dx with the products of A dx in L, each 256-term tile sum added in S (table Kt
+// and diagonal dg in L; dx, r in S, N x nrhs column-major in input order; xg (L) and yg (S)
+// grid-order scratch); norms[2c] = norms[2c + 1] = |r_c|^2.
+template <class S, class L>
+cudaError_t launch_residual_update(cudaStream_t st, int n, int nrhs, const L* Kt, const L* dg, const double* rs,
+                                   const int64_t* ing, const S* dx, S* r, L* xg, S* yg, double* norms);
 
 }  // namespace rs
