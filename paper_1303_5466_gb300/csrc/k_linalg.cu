@@ -352,25 +352,36 @@ cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t 
 }
 
 // ------------------------------------------------------------------ batched matvec(s)
-template <class T>
+template <class T, int RB>
 __global__ void __launch_bounds__(256) matvec_kernel(const MatvecProb* __restrict__ probs,
         const int64_t* __restrict__ blk0, int np, const T* __restrict__ Ab, const T* __restrict__ xb,
         T* __restrict__ yb, int nrhs)
 {
-    __shared__ T part[4][64][8];
+    __shared__ T part[256 * 8];
     const int64_t t = blockIdx.x;
     const int pi = find_block(blk0, np, t);
     const MatvecProb P = probs[pi];
-    matvec_block<T>(P, (int)(t - blk0[pi]) * 64, Ab + P.a_off, xb + P.x_off * nrhs, yb + P.y_off * nrhs, nrhs, part);
+    matvec_block<T, RB>(P, (int)(t - blk0[pi]) * RB, Ab + P.a_off, xb + P.x_off * nrhs, yb + P.y_off * nrhs, nrhs,
+                        part);
+}
+
+int matvec_rows_per_block(int64_t blocks64)
+{
+    // enough blocks for four CTAs per SM, else smaller blocks (more column phases per row)
+    if (blocks64 >= 608) return 64;
+    if (2 * blocks64 >= 608) return 32;
+    return 16;
 }
 
 template <class T>
 cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np, int64_t blocks,
-                          const T* A, const T* x, T* y, int nrhs)
+                          const T* A, const T* x, T* y, int nrhs, int rb)
 {
     if (np <= 0 || blocks <= 0) return cudaSuccess;
     count_launches(1);
-    matvec_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
+    if (rb == 16) matvec_kernel<T, 16><<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
+    else if (rb == 32) matvec_kernel<T, 32><<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
+    else matvec_kernel<T, 64><<<(unsigned)blocks, 256, 0, st>>>(probs, blk0, np, A, x, y, nrhs);
     return cudaGetLastError();
 }
 
@@ -505,7 +516,7 @@ template cudaError_t launch_scale_cm<cplx<double>>(cudaStream_t, int64_t, int, c
     template cudaError_t launch_gemm<T>(cudaStream_t, const GemmProb*, int, int64_t, const T*, const T*, T*,        \
                                         const T*);                                                                  \
     template cudaError_t launch_matvec<T>(cudaStream_t, const MatvecProb*, const int64_t*, int, int64_t, const T*,  \
-                                          const T*, T*, int);                                                       \
+                                          const T*, T*, int, int);                                                  \
     template cudaError_t launch_gather_rows<T>(cudaStream_t, int64_t, const int64_t*, const T*, T*, int);           \
     template cudaError_t launch_scatter_rows<T>(cudaStream_t, int64_t, const int64_t*, const T*, T*, int);          \
     template cudaError_t launch_gather_cm<typename sc_traits<T>::io, T>(cudaStream_t, int64_t, const int64_t*,      \

@@ -20,15 +20,20 @@ __device__ __forceinline__ int find_job(const J* __restrict__ jobs, int nj, int6
 
 __global__ void __launch_bounds__(256) mv_jobs_kernel(const MvJob* __restrict__ jobs, int nj)
 {
-    __shared__ double part[4][64][8];
+    __shared__ double part[256 * 8];
     const int64_t t = blockIdx.x;
     const int j = find_job(jobs, nj, t, &MvJob::blk_start);
     const MvJob J = jobs[j];
     const int64_t lt = t - J.blk_start;
     const int pi = find_block(J.blk0, J.np, lt);
     const MatvecProb P = J.probs[pi];
-    matvec_block<double>(P, (int)(lt - J.blk0[pi]) * 64, J.A + P.a_off, J.x + P.x_off * J.nrhs,
-                         J.y + P.y_off * J.nrhs, J.nrhs, part);
+    const int row0 = (int)(lt - J.blk0[pi]) * J.rb;
+    const double* A = J.A + P.a_off;
+    const double* x = J.x + P.x_off * J.nrhs;
+    double* y = J.y + P.y_off * J.nrhs;
+    if (J.rb == 16) matvec_block<double, 16>(P, row0, A, x, y, J.nrhs, part);
+    else if (J.rb == 32) matvec_block<double, 32>(P, row0, A, x, y, J.nrhs, part);
+    else matvec_block<double, 64>(P, row0, A, x, y, J.nrhs, part);
 }
 
 __global__ void __launch_bounds__(256) copy_jobs_kernel(const CopyJob* __restrict__ jobs, int nj, int64_t total)

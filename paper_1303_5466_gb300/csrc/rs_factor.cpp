@@ -451,11 +451,18 @@ void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk
     nblk += (out_n + 63) / 64;
 }
 
-int upload_mv(DevMem& d, DevMem& db, int& n, int64_t& nblk, std::vector<MatvecProb>& v, std::vector<int64_t>& blk,
-              int64_t total, cudaStream_t st, double* work = nullptr)
+// Upload a descriptor set, with blocks of rb output entries (matvec_rows_per_block of its
+// 64-entry block count: small sets get smaller blocks, so the launch still fills the GPU).
+int upload_mv(DevMem& d, DevMem& db, int& n, int64_t& nblk, int& rb, std::vector<MatvecProb>& v,
+              std::vector<int64_t>& blk, int64_t total, cudaStream_t st, double* work = nullptr)
 {
     n = (int)v.size();
-    nblk = total;
+    rb = matvec_rows_per_block(total);
+    nblk = 0;
+    for (size_t i = 0; i < v.size(); ++i) {
+        blk[i] = nblk;
+        nblk += ((v[i].trans ? v[i].cols : v[i].rows) + rb - 1) / rb;
+    }
     if (work) {
         *work = 0.0;
         for (const MatvecProb& p : v) *work += (double)p.rows * (double)p.cols;
@@ -490,7 +497,7 @@ int solve_plan(rs_op* op, Level& L, const Level* child, cudaStream_t st)
         std::vector<int64_t> blk;
         int64_t n = 0;
         add_mv(v, blk, n, (int)L.m[0], (int)L.m[0], (int)L.m[0], 0, 0, 0, 0, 1.0, 0.0);
-        return upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, v, blk, n, st, &L.mvw_phi);
+        return upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, v, blk, n, st, &L.mvw_phi);
     }
     std::vector<int64_t> isk(L.sum_k);
     for (int b = 0; b < nb; ++b)
@@ -507,10 +514,12 @@ int solve_plan(rs_op* op, Level& L, const Level* child, cudaStream_t st)
         add_mv(vE, bE, nE, k, k, k, 0, L.e_off[b], L.k_off[b], L.k_off[b], 1.0, 0.0);
         if (m - k > 0) add_mv(vTt, bTt, nTt, k, m - k, k, 1, L.t_off[b], L.k_off[b], L.act_off[b] + k, 1.0, 0.0);
     }
-    if ((rc = upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, vphi, bphi, nphi, st, &L.mvw_phi))) return rc;
-    if ((rc = upload_mv(L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, vT, bT, nT, st, &L.mvw_T))) return rc;
-    if ((rc = upload_mv(L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, vE, bE, nE, st, &L.mvw_E))) return rc;
-    return upload_mv(L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, vTt, bTt, nTt, st, &L.mvw_Tt);
+    if ((rc = upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, vphi, bphi, nphi, st,
+                        &L.mvw_phi)))
+        return rc;
+    if ((rc = upload_mv(L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.rb_T, vT, bT, nT, st, &L.mvw_T))) return rc;
+    if ((rc = upload_mv(L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, vE, bE, nE, st, &L.mvw_E))) return rc;
+    return upload_mv(L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.rb_Tt, vTt, bTt, nTt, st, &L.mvw_Tt);
 }
 
 void compute_stats(rs_op* op)
@@ -771,16 +780,16 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         else RS_CUDA(launch_gather_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, esz * L.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
-                              L.d_Phi.as<T>(), U, wl, nr)); }
+                              L.d_Phi.as<T>(), U, wl, nr, L.rb_phi)); }
         if ((rc = run_cprog(L.p_phi, U, wl))) return rc;
         RS_CUDA(launch_gather_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), wl, Tt, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, esz * L.mvw_T);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_T.as<MatvecProb>(), L.d_mv_T_blk.as<int64_t>(), L.n_mv_T, L.b_mv_T,
-                              L.d_T.as<T>(), wl, Tt, nr)); }
+                              L.d_T.as<T>(), wl, Tt, nr, L.rb_T)); }
         if ((rc = run_cprog(L.p_T, wl, Tt))) return rc;
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, esz * L.mvw_E);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
-                              L.d_E.as<T>(), Tt, gl, nr)); }
+                              L.d_E.as<T>(), Tt, gl, nr, L.rb_E)); }
         if ((rc = run_cprog(L.p_E, Tt, gl))) return rc;
     }
     // root
@@ -788,7 +797,7 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         Level& R = op->lev[0];
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, esz * R.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, R.d_mv_phi.as<MatvecProb>(), R.d_mv_phi_blk.as<int64_t>(), R.n_mv_phi, R.b_mv_phi,
-                              R.d_Phi.as<T>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr)); }
+                              R.d_Phi.as<T>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr, R.rb_phi)); }
     }
     // downward pass
     for (int l = 1; l <= d; ++l) {
@@ -799,17 +808,17 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         RS_CUDA(cudaMemcpyAsync(Tt, gl, sizeof(T) * (size_t)(L.sum_k * nrhs), cudaMemcpyDeviceToDevice, st));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, esz * L.mvw_E);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
-                              L.d_E.as<T>(), pl, Tt, nr)); }   // beta = 0: Tt = E phi
+                              L.d_E.as<T>(), pl, Tt, nr, L.rb_E)); }   // beta = 0: Tt = E phi
         if ((rc = run_cprog(L.p_E, pl, Tt))) return rc;
         RS_CUDA(launch_axpby<T>(st, L.sum_k * nrhs, (T)-1, gl, (T)1, Tt));   // Tt = E phi - g
         RS_CUDA(launch_scatter_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), Tt, U, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, esz * L.mvw_Tt);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_Tt.as<MatvecProb>(), L.d_mv_Tt_blk.as<int64_t>(), L.n_mv_Tt, L.b_mv_Tt,
-                              L.d_T.as<T>(), Tt, U, nr)); }
+                              L.d_T.as<T>(), Tt, U, nr, L.rb_Tt)); }
         if ((rc = run_cprog(L.p_Tt, Tt, U))) return rc;
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, esz * L.mvw_phi);
         RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
-                              L.d_Phi.as<T>(), U, XO, nr)); }
+                              L.d_Phi.as<T>(), U, XO, nr, L.rb_phi)); }
         if ((rc = run_cprog(L.p_phi, U, XO))) return rc;
         RS_CUDA(launch_axpby<T>(st, L.sum_m * nrhs, (T)1, wl, (T)1, XO));   // x' = w + Phi v
         if (l == d) RS_CUDA(launch_scatter_cm<T, IO>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));

@@ -125,6 +125,7 @@ struct Level {
     DevMem d_idx_sk;      // row act_off + a for each skeleton position a (k_off order)
     DevMem d_mv_phi, d_mv_phi_blk, d_mv_T, d_mv_T_blk, d_mv_E, d_mv_E_blk, d_mv_Tt, d_mv_Tt_blk;
     int n_mv_phi = 0, n_mv_T = 0, n_mv_E = 0, n_mv_Tt = 0;
+    int rb_phi = 64, rb_T = 64, rb_E = 64, rb_Tt = 64;     // output entries per block
     int64_t b_mv_phi = 0, b_mv_T = 0, b_mv_E = 0, b_mv_Tt = 0;
     int64_t sum_m = 0, sum_k = 0;
     double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set

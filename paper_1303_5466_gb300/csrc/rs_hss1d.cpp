@@ -593,7 +593,8 @@ int run_program(cudaStream_t st, const Program& prog, const T* store, const T* i
             T* dst = s.dst == BUF_Z ? z : out;
             RS_CUDA(launch_copy_rows<T>(st, s.count, s.a.as<int64_t>(), s.b.as<int64_t>(), src, dst, nrhs, s.add));
         } else {
-            RS_CUDA(launch_matvec<T>(st, s.a.as<MatvecProb>(), s.b.as<int64_t>(), s.np, s.count, store, z, z, nrhs));
+            RS_CUDA(launch_matvec<T>(st, s.a.as<MatvecProb>(), s.b.as<int64_t>(), s.np, s.count, store, z, z, nrhs,
+                                     64));
         }
     }
     return RS_OK;

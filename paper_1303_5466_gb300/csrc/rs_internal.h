@@ -146,10 +146,13 @@ template <class T>
 cudaError_t launch_gemm(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const T* A, const T* B, T* C,
                         const T* C0);
 
-// Batched matvec(s) over `np` problems, blocks = sum over problems of ceil(out_rows / 64).
+// Batched matvec(s) over `np` problems, blocks = sum over problems of ceil(out_rows / rb) with
+// rb = 16, 32 or 64 output entries per block (blk0[p]: first block of problem p).
 template <class T>
 cudaError_t launch_matvec(cudaStream_t st, const MatvecProb* probs, const int64_t* blk0, int np, int64_t blocks,
-                          const T* A, const T* x, T* y, int nrhs);
+                          const T* A, const T* x, T* y, int nrhs, int rb);
+// Block size (rb) of a descriptor set whose problems give blocks64 blocks of 64 outputs.
+int matvec_rows_per_block(int64_t blocks64);
 
 // Point-major row gathers/scatters of the solve: out[p * nrhs + c] = in[idx[p] * nrhs + c]
 // (gather) and the reverse (scatter), for p < count.
@@ -177,7 +180,7 @@ cudaError_t launch_scale_cm(cudaStream_t st, int64_t N, int nrhs, const double* 
 struct MvJob {
     const MatvecProb* probs;
     const int64_t* blk0;
-    int np, nrhs;
+    int np, nrhs, rb;
     int64_t blk_start;
     const double* A;
     const double* x;

@@ -121,11 +121,11 @@ struct StageJobs {
     std::vector<MvJob> mv;
     std::vector<CopyJob> cp;
     int64_t mv_blocks = 0, cp_elems = 0;
-    void add_mv(const Level& L, const DevMem& probs, const DevMem& blk0, int np, int64_t nblk, const double* A,
-                const double* x, double* y, int64_t nrhs)
+    void add_mv(const Level& L, const DevMem& probs, const DevMem& blk0, int np, int64_t nblk, int rb,
+                const double* A, const double* x, double* y, int64_t nrhs)
     {
         if (np <= 0 || nblk <= 0) return;
-        MvJob j{probs.as<MatvecProb>(), blk0.as<int64_t>(), np, (int)nrhs, mv_blocks, A, x, y};
+        MvJob j{probs.as<MatvecProb>(), blk0.as<int64_t>(), np, (int)nrhs, rb, mv_blocks, A, x, y};
         (void)L;
         mv.push_back(j);
         mv_blocks += nblk;
@@ -151,7 +151,7 @@ void build_jobs(rs_server* s, std::vector<StageJobs>& S)
         const int d = op->d;
         if (r->phase == 1) {
             const Level& R = op->lev[0];
-            S[RT].add_mv(R, R.d_mv_phi, R.d_mv_phi_blk, R.n_mv_phi, R.b_mv_phi, R.d_Phi.as<double>(),
+            S[RT].add_mv(R, R.d_mv_phi, R.d_mv_phi_blk, R.n_mv_phi, R.b_mv_phi, R.rb_phi, R.d_Phi.as<double>(),
                          r->g + r->Ls.goff[1] * nr, r->phi + r->Ls.goff[1] * nr, nr);
             continue;
         }
@@ -163,16 +163,16 @@ void build_jobs(rs_server* s, std::vector<StageJobs>& S)
         if (r->phase == 0) {
             if (l == d) S[U1].add_cp(COPY_GATHER_CM, L.sum_m, nr, op->N, L.d_idx_leaf.as<int64_t>(), r->f, r->u);
             else S[U1].add_cp(COPY_GATHER_ROWS, L.sum_m, nr, 0, L.d_idx_up.as<int64_t>(), r->g + r->Ls.goff[l + 1] * nr, r->u);
-            S[U2].add_mv(L, L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.d_Phi.as<double>(), r->u, wl, nr);
+            S[U2].add_mv(L, L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, L.d_Phi.as<double>(), r->u, wl, nr);
             S[U3].add_cp(COPY_GATHER_ROWS, L.sum_k, nr, 0, L.d_idx_sk.as<int64_t>(), wl, r->t);
-            S[U4].add_mv(L, L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.d_T.as<double>(), wl, r->t, nr);
-            S[U5].add_mv(L, L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.d_E.as<double>(), r->t, gl, nr);
+            S[U4].add_mv(L, L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.rb_T, L.d_T.as<double>(), wl, r->t, nr);
+            S[U5].add_mv(L, L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, L.d_E.as<double>(), r->t, gl, nr);
         } else {
-            S[D1].add_mv(L, L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.d_E.as<double>(), pl, r->t, nr);
+            S[D1].add_mv(L, L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, L.d_E.as<double>(), pl, r->t, nr);
             S[D2].add_cp(COPY_AXPBY, L.sum_k * nr, 1, 0, nullptr, gl, r->t, -1.0, 1.0);
             S[D3].add_cp(COPY_SCATTER_ROWS, L.sum_k, nr, 0, L.d_idx_sk.as<int64_t>(), r->t, r->u);
-            S[D4].add_mv(L, L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.d_T.as<double>(), r->t, r->u, nr);
-            S[D5].add_mv(L, L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.d_Phi.as<double>(), r->u, r->out, nr);
+            S[D4].add_mv(L, L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.rb_Tt, L.d_T.as<double>(), r->t, r->u, nr);
+            S[D5].add_mv(L, L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, L.d_Phi.as<double>(), r->u, r->out, nr);
             S[D6].add_cp(COPY_AXPBY, L.sum_m * nr, 1, 0, nullptr, wl, r->out, 1.0, 1.0);
             if (l == d) S[D7].add_cp(COPY_SCATTER_CM, L.sum_m, nr, op->N, L.d_idx_leaf.as<int64_t>(), r->out, r->x);
             else S[D7].add_cp(COPY_SCATTER_ROWS, L.sum_m, nr, 0, L.d_idx_up.as<int64_t>(), r->out,
