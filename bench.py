@@ -33,6 +33,8 @@ WORKLOAD = "laplace_batched"
 # FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26 TFLOP/s, the 1.25
 # TFLOP/s FP64 figure of the profiling recipe (a register-only FMA probe measured 1.203).
 PEAK_FP64_TFLOPS = 1.25
+# FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
 # factor kernels and the profile classes (rs_op_profile) whose launches they are
 KERNEL_CLASSES = {"gj_kernel": ("inv_F", "inv_E", "inv_root"), "cpqr_kernel": ("cpqr",),
@@ -195,7 +197,8 @@ def serving_measure(P, torch, requests, seed=3, load=0.7):
         for i in range(burst):
             P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
         P.rs_server_drain(srv, 3600.0)
-        cap = burst / (time.perf_counter() - t0)     # requests per second
+        burst_s = time.perf_counter() - t0
+        cap = burst / burst_s                        # requests per second
         lam = load * cap
         P.rs_server_latencies(srv)
         n0 = P.rs_server_stats(srv)["completed"]
@@ -213,7 +216,18 @@ def serving_measure(P, torch, requests, seed=3, load=0.7):
         lat = P.rs_server_latencies(srv)[n0:]
         st = P.rs_server_stats(srv)
         rhs = int(nrhs[burst:].sum())
+        # the same burst, one rs_solve per request in submission order (no cross-request batching)
+        cs = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for i in range(burst):
+            P.rs_solve(ops[int(kinds[i])], bufs[i][0], int(nrhs[i]), bufs[i][1], cs)
+        torch.cuda.synchronize()
+        seq_s = time.perf_counter() - t1
+        burst_rhs = int(nrhs[:burst].sum())
         return {"requests": int(requests - burst), "burst_requests": int(burst), "load": load,
+                "burst_rhs_per_s": burst_rhs / burst_s, "sequential_rhs_per_s": burst_rhs / seq_s,
+                "burst_speedup_vs_sequential": seq_s / burst_s,
                 "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "rhs_per_s": rhs / wall, "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
                 "operators": "%s grids, leaf 16, eps 1e-10, FP64" % ", ".join("%d^2" % n for n, _ in SERVING_OPS),
@@ -233,6 +247,7 @@ def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
     o = P.rs_opts_default()
     o.precision = P.RS_MIXED_FP32
     o.refine_tol = 1e-10
+    o.profile = 1
     f = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
     x = torch.empty_like(f)
     tree = P.rs_build_tree(pts, leaf)
@@ -245,8 +260,13 @@ def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
     e2.record(st)
     e2.synchronize()
     s = P.rs_op_stats(op)
+    prof = P.rs_op_profile(op)
     rel = P.rs_residual(op, x, f, nrhs, st)
     out = {"factor_ms": e0.elapsed_time(e1), "refined_solve_ms": e1.elapsed_time(e2), "eps": 1e-6,
+           "factor_profile_ms": {k: v[0] for k, v in prof.items() if k != "solve"},
+           "factor_profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items()
+                                     if k != "solve" and v[0] > 0 and v[1] > 0},
+           "fp32_peak_tflops": PEAK_FP32_TFLOPS,
            "refine_solves": s["refine_iters"], "refine_fp64_direct_sums": s["refine_fp64_sums"],
            "residual": float(rel.max()), "bytes_factors": s["bytes_factors"]}
     P.rs_free(op)
@@ -410,6 +430,10 @@ def run_ours(args):
                            "achieved_gbs": sol[2] / (sol[0] * 1e-3) / 1e9 if sol[0] else None},
         "profile_ms_per_step": {k: v[0] / K for k, v in prof.items()},
         "profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items() if v[0] > 0 and v[1] > 0},
+        "roofline_by_kernel": {k: {"achieved_tflops": kern[k][1] / (kern[k][0] * 1e-3) / 1e12,
+                                   "frac_fp64": kern[k][1] / (kern[k][0] * 1e-3) / 1e12 / PEAK_FP64_TFLOPS,
+                                   "ms_per_step": kern[k][0] / K}
+                               for k in kern if kern[k][0] > 0},
         "e2e": {"value": world * N / e2e_s, "unit": "unknowns/s (build + factor + 4-RHS solve, host buffers)",
                 "h2d_bytes_per_step": N * 2 * 8 + N * 8 + N * nrhs * 8, "d2h_bytes_per_step": N * nrhs * 8},
         "gpu_launches": launches,

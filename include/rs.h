@@ -82,6 +82,10 @@ typedef struct {
                                     launch stream (rs_op_profile)                     [0]    */
     int hss_leaf;                /* largest leaf run of the HSS1D trees (k_cut > 0)  [64]   */
     double hss_eps;              /* ID tolerance of that compression; 0 = eps         [0]    */
+    int solve_graph;             /* 1: rs_solve of RS_FP64 / RS_C128 operators replays a CUDA
+                                    graph of the whole inverse apply, captured once per nrhs
+                                    (inputs staged through library buffers); 0: launch the
+                                    kernels one by one                                [1]    */
     int spd_inverse;             /* 1: invert F, E and the root of a real symmetric kernel
                                     (RS_LAPLACE) by the symmetric sweep without pivoting
                                     (half the flops of Gauss-Jordan); a level whose pivots

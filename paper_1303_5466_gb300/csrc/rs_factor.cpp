@@ -845,10 +845,11 @@ int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const doubl
     return rc;
 }
 
-// One inverse apply with the library's own (growing) workspace; fd, xd device FP64.
-int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st)
+// Workspace of one inverse apply with nrhs columns (grown on demand); bumps op->ws_gen when a
+// buffer moves, which retires the solve graphs captured against the old addresses.
+int solve_workspace(rs_op* op, int64_t nrhs, SolveLayout& Ls, SolveWork& ws)
 {
-    const SolveLayout Ls = solve_layout(op, nrhs);
+    Ls = solve_layout(op, nrhs);
     const size_t e = (size_t)op->esz;
     RS_CUDA(op->s_w.alloc(e * (size_t)Ls.n_w));
     RS_CUDA(op->s_g.alloc(e * (size_t)Ls.n_g));
@@ -857,15 +858,98 @@ int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream
     RS_CUDA(op->s_out.alloc(e * (size_t)Ls.n_u));
     RS_CUDA(op->s_t.alloc(e * (size_t)Ls.n_t));
     RS_CUDA(op->s_z.alloc(e * (size_t)Ls.n_z));
-    SolveWork ws{op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p, op->s_z.p};
-    if (op->kind != RS_HELMHOLTZ) return solve_run(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
+    if (op->kind == RS_HELMHOLTZ) RS_CUDA(op->s_fs.alloc(2 * sizeof(double) * (size_t)(op->N * nrhs)));
+    ws = SolveWork{op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p, op->s_z.p};
+    const void* now[9] = {op->s_w.p, op->s_g.p, op->s_phi.p, op->s_u.p, op->s_out.p, op->s_t.p, op->s_z.p,
+                          op->s_fs.p, nullptr};
+    if (memcmp(now, op->ws_ptrs, sizeof(now)) != 0) {
+        memcpy(op->ws_ptrs, now, sizeof(now));
+        ++op->ws_gen;
+    }
+    return RS_OK;
+}
+
+// The launches of one inverse apply (no allocation, no host synchronisation).
+int apply_launch(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
+                 cudaStream_t st, bool profile)
+{
+    if (op->kind != RS_HELMHOLTZ) return solve_run(op, Ls, ws, fd, xd, nrhs, st, profile);
     // symmetric form: x = S (S^{-1} A S)^{-1} S^{-1} f, S = diag(kappa sqrt(b))
     using Z = cplx<double>;
-    RS_CUDA(op->s_fs.alloc(sizeof(Z) * (size_t)(op->N * nrhs)));
     RS_CUDA(launch_scale_cm<Z>(st, op->N, (int)nrhs, op->d_s_in.as<double>(), -1, (const Z*)fd, op->s_fs.as<Z>()));
-    const int rc = solve_run(op, Ls, ws, op->s_fs.as<double>(), xd, nrhs, st, op->opts.profile != 0);
+    const int rc = solve_run(op, Ls, ws, op->s_fs.as<double>(), xd, nrhs, st, profile);
     if (rc) return rc;
     RS_CUDA(launch_scale_cm<Z>(st, op->N, (int)nrhs, op->d_s_in.as<double>(), 1, (const Z*)xd, (Z*)xd));
+    return RS_OK;
+}
+
+// One inverse apply with the library's own (growing) workspace; fd, xd device FP64.
+int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st)
+{
+    SolveLayout Ls;
+    SolveWork ws;
+    int rc = solve_workspace(op, nrhs, Ls, ws);
+    if (rc) return rc;
+    return apply_launch(op, Ls, ws, fd, xd, nrhs, st, op->opts.profile != 0);
+}
+
+// One inverse apply replayed from a CUDA graph (captured on first use for this nrhs and
+// workspace): f is copied into the staging buffer the graph reads, x out of the one it writes.
+int apply_graph(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st)
+{
+    SolveLayout Ls;
+    SolveWork ws;
+    int rc = solve_workspace(op, nrhs, Ls, ws);
+    if (rc) return rc;
+    const size_t io = (op->kind == RS_HELMHOLTZ ? 2 : 1) * sizeof(double) * (size_t)(op->N * nrhs);
+    const void* gin0 = op->g_in.p;
+    const void* gout0 = op->g_out.p;
+    RS_CUDA(op->g_in.alloc(io));
+    RS_CUDA(op->g_out.alloc(io));
+    if (op->g_in.p != gin0 || op->g_out.p != gout0) ++op->ws_gen;
+    RS_CUDA(cudaMemcpyAsync(op->g_in.p, fd, io, cudaMemcpyDeviceToDevice, st));
+    rs_op::SolveGraph* g = nullptr;
+    for (auto it = op->graphs.begin(); it != op->graphs.end();) {
+        if (it->gen != op->ws_gen) {                    // captured against buffers since moved
+            cudaGraphExecDestroy(it->exec);
+            it = op->graphs.erase(it);
+            continue;
+        }
+        if (it->nrhs == nrhs) g = &*it;
+        ++it;
+    }
+    if (!g) {
+        if (op->graphs.size() >= 16) {
+            for (auto& e : op->graphs) cudaGraphExecDestroy(e.exec);
+            op->graphs.clear();
+        }
+        if (!op->cap_stream) RS_CUDA(cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking));
+        const int64_t l0 = rs_launch_count();
+        RS_CUDA(cudaStreamBeginCapture(op->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = apply_launch(op, Ls, ws, op->g_in.as<double>(), op->g_out.as<double>(), nrhs, op->cap_stream, false);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(op->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture (inverse apply)");
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate (inverse apply)");
+        // the launches were recorded, not made: the count is taken on every replay instead
+        const int64_t nl = rs_launch_count() - l0;
+        count_launches((int)-nl);
+        op->graphs.push_back({nrhs, op->ws_gen, exec, nl});
+        g = &op->graphs.back();
+    }
+    {
+        ProfScope ps(op, RS_PROF_SOLVE, st, op->stats.flops_solve_per_rhs * (double)nrhs, op->stats.bytes_solve);
+        RS_CUDA(cudaGraphLaunch(g->exec, st));
+    }
+    count_launches((int)g->launches);
+    RS_CUDA(cudaMemcpyAsync(xd, op->g_out.p, io, cudaMemcpyDeviceToDevice, st));
     return RS_OK;
 }
 
@@ -889,7 +973,8 @@ int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
         xd = op->s_out2.as<double>();
     }
     const bool refine = op->opts.precision == RS_MIXED_FP32 || op->opts.precision == RS_C64_REFINED;
-    int rc = refine ? refine_solve(op, fd, xd, nrhs, st) : apply_once(op, fd, xd, nrhs, st);
+    int rc = refine ? refine_solve(op, fd, xd, nrhs, st)
+                    : op->opts.solve_graph ? apply_graph(op, fd, xd, nrhs, st) : apply_once(op, fd, xd, nrhs, st);
     if (rc && rc != RS_E_NOT_CONVERGED) return rc;
     if (!dev_x) {
         RS_CUDA(cudaMemcpyAsync(x, xd, io * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));

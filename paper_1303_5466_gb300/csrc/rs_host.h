@@ -239,6 +239,20 @@ struct rs_op {
     int64_t cstore_n = 0;
     rs_stats stats{};
     std::atomic<int> inflight{0};   // references held by servers and their requests
+    // CUDA graphs of the inverse apply (opts.solve_graph), one per nrhs, captured on a private
+    // stream with the staging buffers g_in / g_out; ws_gen counts workspace reallocations, and
+    // a graph captured under an older workspace is dropped
+    struct SolveGraph {
+        int64_t nrhs;
+        uint64_t gen;
+        cudaGraphExec_t exec;
+        int64_t launches;
+    };
+    std::vector<SolveGraph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    uint64_t ws_gen = 0;
+    const void* ws_ptrs[9] = {};
+    rs::DevMem g_in, g_out;
     // profiling (opts.profile): pending event pairs and per-class sums
     std::vector<rs::ProfRec> pending;
     std::vector<cudaEvent_t> ev_pool, ev_all;
@@ -247,5 +261,7 @@ struct rs_op {
     ~rs_op()
     {
         for (cudaEvent_t e : ev_all) cudaEventDestroy(e);
+        for (SolveGraph& g : graphs) cudaGraphExecDestroy(g.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
