@@ -146,7 +146,8 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 // The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step (every CTA
 // computes alpha from the same data in the same order).
 template <int NT, class T>
-__global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restrict__ act_off,
+__global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restrict__ cta_off,
+        const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
         T* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
         T* __restrict__ diag, unsigned int* __restrict__ bar, unsigned long long* __restrict__ keys,
@@ -157,7 +158,23 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
     __shared__ unsigned long long kred[NT / 32];
     __shared__ unsigned long long s_key;
 
-    const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
+    // box and rank in its group: G0 CTAs per box, or (cta_off given) G0 boxes, box b owning CTAs
+    // cta_off[b] .. cta_off[b+1]
+    int b, gi, G;
+    if (cta_off) {
+        int lo = 0, hi = G0 - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        b = lo;
+        gi = (int)blockIdx.x - cta_off[b];
+        G = cta_off[b + 1] - cta_off[b];
+    } else {
+        G = G0;
+        b = blockIdx.x / G;
+        gi = blockIdx.x - b * G;
+    }
     const int64_t a0 = act_off[b];
     const int m = (int)(act_off[b + 1] - a0);
     const int r = nnear[b] + P;
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
-    unsigned long long* kb = keys + (int64_t)b * 2 * G;   // [2][G], by step parity
+    unsigned long long* kb = keys + 2 * (cta_off ? (int64_t)cta_off[b] : (int64_t)b * G);   // [2][G], by parity
 
     for (int j = threadIdx.x; j < m; j += NT) { alist[j] = j; apos[j] = j; }
     {
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
             T* col0 = Y + (int64_t)j0 * r;
             T* col1 = Y + (int64_t)j1 * r;
             constexpr int U = 4;
-            T w0 = 0, w1 = 0;
+            T w0 = 0, w1 = 0, w0b = 0, w1b = 0;      // two accumulators per column: shorter FMA chains
             int i = s + lane;
             for (; i + 32 * (U - 1) < r; i += 32 * U) {
                 T vv[U], xa[U], xb[U];
@@ -268,9 +285,11 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
                     xb[u] = ldcg_(col1 + i + 32 * u);
                 }
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
+                for (int u = 0; u < U; u += 2) {
                     w0 = fma_(vv[u], xa[u], w0);
                     w1 = fma_(vv[u], xb[u], w1);
+                    w0b = fma_(vv[u + 1], xa[u + 1], w0b);
+                    w1b = fma_(vv[u + 1], xb[u + 1], w1b);
                 }
             }
             for (; i < r; i += 32) {
@@ -278,6 +297,8 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G, const int64_t* __restri
                 w0 = fma_(vv, ldcg_(col0 + i), w0);
                 w1 = fma_(vv, ldcg_(col1 + i), w1);
             }
+            w0 += w0b;
+            w1 += w1b;
             // both sums in one butterfly: lanes 0-15 end with w0's, 16-31 with w1's
             T wp = (lo16 ? w0 : w1) + shfl_xor_(lo16 ? w1 : w0, 16);
 #pragma unroll
@@ -346,7 +367,8 @@ static size_t cpqr_shm(int max_r, int max_m, int G)
 }
 
 template <class T>
-cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
+cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int64_t* act_off,
+                        const int32_t* nnear, int P,
                         const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
                         int max_m, double* nrm, double* ref)
@@ -356,17 +378,20 @@ cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, 
     const size_t shm = cpqr_shm<T>(max_r, max_m, G);
     cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
-    if (G == 1) {
+    if (!cta_off && G == 1) {
         count_launches(1);
-        cpqr_kernel<NT, T><<<nb, NT, shm, st>>>(G, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys,
-                                                status, spin_limit, nrm, ref);
+        cpqr_kernel<NT, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
+                                                keys, status, spin_limit, nrm, ref);
         return cudaGetLastError();
     }
-    void* args[] = {(void*)&G, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y, (void*)&eps,
-                    (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
+    void* args[] = {(void*)&G, (void*)&cta_off, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y,
+                    (void*)&eps, (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
                     (void*)&spin_limit, (void*)&nrm, (void*)&ref};
     count_launches(1);
-    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, T>, dim3((unsigned)(nb * G)), dim3(NT), args, shm, st);
+    int g0 = cta_off ? nb : G;
+    args[0] = (void*)&g0;
+    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, T>, dim3((unsigned)(cta_off ? ctas : nb * G)), dim3(NT),
+                                       args, shm, st);
 }
 
 template <class T>
@@ -518,7 +543,8 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
     template cudaError_t launch_assemble_Y<T>(cudaStream_t, int, const int32_t*, const int64_t*, const int32_t*,     \
                                               const int64_t*, const double*, const double*, int, const int64_t*, T*, \
                                               KernelK, int);                                                        \
-    template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int64_t*, const int32_t*, int, const int64_t*, \
+    template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int32_t*, int, const int64_t*, const int32_t*, \
+                                        int, const int64_t*,                                                        \
                                         T*, double, int32_t*, int32_t*, T*, unsigned int*, unsigned long long*,     \
                                         int*, long long, int, int, double*, double*);                               \
     template int cpqr_max_ctas<T>(int, int, int);                                                                    \

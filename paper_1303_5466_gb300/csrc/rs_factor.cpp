@@ -141,7 +141,7 @@ namespace {
 
 // Workspace of the ID phase, released when rs_factor returns.
 struct IdWork {
-    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms;
+    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms, cta_off;
 };
 
 template <class T>
@@ -269,12 +269,49 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     const int max_r = L.max_r, max_m = L.max_m;
     // the open columns are re-split every step, so a group may take one CTA per 16 columns
     const int G = choose_group(nb, 2 * max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
-    RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * 2 * (size_t)nb * G));
+    // The boxes of a level differ in work (boundary boxes have fewer near rows, ranks differ),
+    // and a group runs at its own pace: deal the same CTA total in proportion to each box's
+    // work, r m^2, so the groups finish together (at least one CTA, at most one per 16 columns).
+    std::vector<int32_t> cta_off;
+    if (G > 1 && nb > 1) {
+        const int total = nb * G;
+        std::vector<double> wgt(nb);
+        double W = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            wgt[b] = (double)L.r[b] * (double)L.m[b] * (double)L.m[b];
+            W += wgt[b];
+        }
+        std::vector<int> gb(nb);
+        int used = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int cap_b = std::max(1, (int)(2 * L.m[b] / 32));
+            gb[b] = std::max(1, std::min(cap_b, (int)std::floor(total * wgt[b] / W)));
+            used += gb[b];
+        }
+        while (used < total) {              // the rest to the boxes with the most work per CTA
+            int best = -1;
+            for (int b = 0; b < nb; ++b)
+                if (gb[b] < std::max(1, (int)(2 * L.m[b] / 32)) && (best < 0 || wgt[b] / gb[b] > wgt[best] / gb[best]))
+                    best = b;
+            if (best < 0) break;
+            ++gb[best];
+            ++used;
+        }
+        cta_off.assign(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) cta_off[b + 1] = cta_off[b] + gb[b];
+    }
+    const int ctas = cta_off.empty() ? nb * G : cta_off[nb];
+    if (!cta_off.empty()) {
+        int rc2;
+        if ((rc2 = upload(w.cta_off, cta_off, st))) return rc2;
+    }
+    RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * 2 * (size_t)ctas));
     RS_CUDA(w.norms.alloc(sizeof(double) * 2 * (size_t)(sum_m + 1)));
     {
     // the rank is known only afterwards: the work is added once k is read back
     ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0);
-    RS_CUDA(launch_cpqr<T>(st, nb, G, L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
+    RS_CUDA(launch_cpqr<T>(st, nb, G, cta_off.empty() ? nullptr : w.cta_off.as<int32_t>(), ctas,
+                        L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
                         w.Y.as<T>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<T>(),
                         op->d_bar.as<unsigned int>(), w.keys.as<unsigned long long>(), op->d_status.as<int>(),
                         (long long)op->opts.spin_limit, max_r, max_m, w.norms.as<double>(),

@@ -88,8 +88,11 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 // act_off[nb] entries each (the squared column norms, shared by the group's CTAs).  Outputs: kout[b],
 // piv[act_off[b] + s] = physical column of pivot s (s < k), diag[act_off[b] + s] = R_ss.
 // Y is overwritten by the factorisation (rows < k hold R).
+// Group sizes: G CTAs for every box, or (cta_off != NULL, device, nb + 1 entries) box b takes
+// CTAs cta_off[b] .. cta_off[b+1], ctas = cta_off[nb] in all.
 template <class T>
-cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int64_t* act_off, const int32_t* nnear, int P,
+cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int64_t* act_off,
+                        const int32_t* nnear, int P,
                         const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
                         int max_m, double* nrm, double* ref);
