@@ -36,8 +36,9 @@ PEAK_FP64_TFLOPS = 1.25
 # FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
-# factor kernels and the profile classes (rs_op_profile) whose launches they are
-KERNEL_CLASSES = {"gj_kernel": ("inv_F", "inv_E", "inv_root"), "cpqr_kernel": ("cpqr",),
+# factor kernels and the profile classes (rs_op_profile) whose launches they are (the inverse
+# classes run the symmetric sweep on the Laplace workload)
+KERNEL_CLASSES = {"sweep_kernel": ("inv_F", "inv_E", "inv_root"), "cpqr_kernel": ("cpqr",),
                   "gemm_kernel": ("gemm_E",), "id_T_kernel": ("id_T",)}
 
 

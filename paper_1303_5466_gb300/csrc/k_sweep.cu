@@ -80,7 +80,8 @@ __device__ __forceinline__ void write_panel_rows(const T* __restrict__ A, int m,
 //   4. the owner of panel q + 1 copies its panel's rows into the other buffer.
 // The result is -S^{-1} in the lower triangle; sweep_finish_kernel negates and mirrors it.
 template <int NT, int NB, class T>
-__global__ void __launch_bounds__(NT) sweep_kernel(int G, const int32_t* __restrict__ msz,
+__global__ void __launch_bounds__(NT) sweep_kernel(int G0, const int32_t* __restrict__ cta_off,
+        const int32_t* __restrict__ msz,
         const int64_t* __restrict__ off, T* __restrict__ Aall, T* __restrict__ Pball,
         const int64_t* __restrict__ pb_off, unsigned int* __restrict__ bar, int* __restrict__ status, long long spin)
 {
@@ -92,7 +93,23 @@ __global__ void __launch_bounds__(NT) sweep_kernel(int G, const int32_t* __restr
     __shared__ int s_col[CB];
     __shared__ int s_fail;
 
-    const int b = blockIdx.x / G, gi = blockIdx.x - (blockIdx.x / G) * G;
+    // matrix and rank in its group: G0 CTAs per matrix, or (cta_off given) G0 matrices, matrix b
+    // owning CTAs cta_off[b] .. cta_off[b+1]
+    int b, gi, G;
+    if (cta_off) {
+        int lo = 0, hi = G0 - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        b = lo;
+        gi = (int)blockIdx.x - cta_off[b];
+        G = cta_off[b + 1] - cta_off[b];
+    } else {
+        G = G0;
+        b = blockIdx.x / G;
+        gi = blockIdx.x - b * G;
+    }
     const int m = msz[b];
     if (m <= 0) return;                    // the whole group returns
     T* __restrict__ A = Aall + off[b];
@@ -190,10 +207,32 @@ __global__ void __launch_bounds__(NT) sweep_kernel(int G, const int32_t* __restr
                 if (i >= k0 && i < k0 + kw) continue;
                 T P[NB];
                 load_row<NB>(pb + (int64_t)i * NB, P);
-                for (int jj = 0; jj < nc; ++jj) {
-                    const int j = s_col[jj];
-                    if (j > i) break;                          // columns ascend
-                    T* cp = A + (int64_t)j * m + i;
+                // the chunk's columns with j <= i (lower triangle): a prefix, the columns ascend
+                int nv = 0;
+                for (int step = CB / 2; step > 0; step >>= 1)
+                    if (nv + step <= nc && s_col[nv + step - 1] <= i) nv += step;
+                if (nv < nc && s_col[nv] <= i) ++nv;
+                int jj = 0;
+                for (; jj + 3 < nv; jj += 4) {           // four independent FMA chains
+                    T* c0 = A + (int64_t)s_col[jj] * m + i;
+                    T* c1 = A + (int64_t)s_col[jj + 1] * m + i;
+                    T* c2 = A + (int64_t)s_col[jj + 2] * m + i;
+                    T* c3 = A + (int64_t)s_col[jj + 3] * m + i;
+                    T v0 = ldcg_(c0), v1 = ldcg_(c1), v2 = ldcg_(c2), v3 = ldcg_(c3);
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) {
+                        v0 = fma_(P[t], s_c[t][jj], v0);
+                        v1 = fma_(P[t], s_c[t][jj + 1], v1);
+                        v2 = fma_(P[t], s_c[t][jj + 2], v2);
+                        v3 = fma_(P[t], s_c[t][jj + 3], v3);
+                    }
+                    *c0 = v0;
+                    *c1 = v1;
+                    *c2 = v2;
+                    *c3 = v3;
+                }
+                for (; jj < nv; ++jj) {
+                    T* cp = A + (int64_t)s_col[jj] * m + i;
                     T v = ldcg_(cp);
 #pragma unroll
                     for (int t = 0; t < NB; ++t) v = fma_(P[t], s_c[t][jj], v);
@@ -286,19 +325,22 @@ int sweep_max_ctas()
 }
 
 template <class T>
-cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A, T* Pb,
-                                 const int64_t* pb_off, unsigned int* bar, int* status, long long spin_limit,
-                                 int max_m)
+cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int32_t* m,
+                                 const int64_t* off, T* A, T* Pb, const int64_t* pb_off, unsigned int* bar,
+                                 int* status, long long spin_limit, int max_m)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
     count_launches(1);
-    if (G == 1) {
-        sweep_kernel<SW_NT, SW_NB, T><<<nb, SW_NT, 0, st>>>(G, m, off, A, Pb, pb_off, bar, status, spin_limit);
+    if (!cta_off && G == 1) {
+        sweep_kernel<SW_NT, SW_NB, T><<<nb, SW_NT, 0, st>>>(1, nullptr, m, off, A, Pb, pb_off, bar, status,
+                                                            spin_limit);
     } else {
-        void* args[] = {(void*)&G, (void*)&m, (void*)&off, (void*)&A, (void*)&Pb, (void*)&pb_off, (void*)&bar,
-                        (void*)&status, (void*)&spin_limit};
-        cudaError_t e = cudaLaunchCooperativeKernel((void*)sweep_kernel<SW_NT, SW_NB, T>, dim3((unsigned)(nb * G)),
-                                                    dim3(SW_NT), args, 0, st);
+        int g0 = cta_off ? nb : G;
+        void* args[] = {(void*)&g0, (void*)&cta_off, (void*)&m, (void*)&off, (void*)&A, (void*)&Pb, (void*)&pb_off,
+                        (void*)&bar, (void*)&status, (void*)&spin_limit};
+        cudaError_t e = cudaLaunchCooperativeKernel((void*)sweep_kernel<SW_NT, SW_NB, T>,
+                                                    dim3((unsigned)(cta_off ? ctas : nb * G)), dim3(SW_NT), args, 0,
+                                                    st);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaGetLastError();
@@ -311,8 +353,9 @@ cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* 
 
 #define RS_INST_SWEEP(T)                                                                                              \
     template int sweep_max_ctas<T>();                                                                               \
-    template cudaError_t launch_sweep_inverse<T>(cudaStream_t, int, int, const int32_t*, const int64_t*, T*, T*,   \
-                                                 const int64_t*, unsigned int*, int*, long long, int);
+    template cudaError_t launch_sweep_inverse<T>(cudaStream_t, int, int, const int32_t*, int, const int32_t*,       \
+                                                 const int64_t*, T*, T*, const int64_t*, unsigned int*, int*,       \
+                                                 long long, int);
 RS_INST_SWEEP(double)
 RS_INST_SWEEP(float)
 

@@ -137,6 +137,30 @@ int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity)
     return best;
 }
 
+std::vector<int32_t> proportional_groups(int total, const std::vector<double>& work, const std::vector<int>& cap)
+{
+    const int nb = (int)work.size();
+    double W = 0.0;
+    for (double w : work) W += w;
+    std::vector<int> gb(nb);
+    int used = 0;
+    for (int b = 0; b < nb; ++b) {
+        gb[b] = std::max(1, std::min(cap[b], W > 0.0 ? (int)std::floor(total * work[b] / W) : 1));
+        used += gb[b];
+    }
+    while (used < total) {              // the rest to the groups with the most work per CTA
+        int best = -1;
+        for (int b = 0; b < nb; ++b)
+            if (gb[b] < cap[b] && (best < 0 || work[b] / gb[b] > work[best] / gb[best])) best = b;
+        if (best < 0) break;
+        ++gb[best];
+        ++used;
+    }
+    std::vector<int32_t> off(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + gb[b];
+    return off;
+}
+
 namespace {
 
 // Workspace of the ID phase, released when rs_factor returns.
@@ -195,11 +219,26 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
         const int G = choose_group(nb, max_m * 16 / NB, [&](int) { return cap; });
         double work = 0.0;
         for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
+        // matrices of one launch differ in size: CTAs in proportion to m^3, at most m / 16 each
+        std::vector<int32_t> cta_off;
+        DevMem d_cta;
+        if (G > 1 && nb > 1) {
+            std::vector<double> wgt(nb);
+            std::vector<int> capb(nb);
+            for (int b = 0; b < nb; ++b) {
+                wgt[b] = (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
+                capb[b] = std::max(1, (int)(sizes[b] / (2 * NB)));
+            }
+            cta_off = proportional_groups(nb * G, wgt, capb);
+            if ((rc = upload(d_cta, cta_off, st))) return rc;
+        }
         {
             ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb]);
-            RS_CUDA(launch_sweep_inverse<T>(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_pb.as<T>(),
-                                            d_pboff.as<int64_t>(), op->d_bar.as<unsigned int>(),
-                                            op->d_status.as<int>(), (long long)op->opts.spin_limit, max_m));
+            RS_CUDA(launch_sweep_inverse<T>(st, nb, G, cta_off.empty() ? nullptr : d_cta.as<int32_t>(),
+                                            cta_off.empty() ? nb * G : cta_off[nb], dm.as<int32_t>(),
+                                            doff.as<int64_t>(), A, op->d_pb.as<T>(), d_pboff.as<int64_t>(),
+                                            op->d_bar.as<unsigned int>(), op->d_status.as<int>(),
+                                            (long long)op->opts.spin_limit, max_m));
         }
         RS_CUDA(cudaStreamSynchronize(st));
         prof_flush(op);
@@ -271,34 +310,16 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     const int G = choose_group(nb, 2 * max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
     // The boxes of a level differ in work (boundary boxes have fewer near rows, ranks differ),
     // and a group runs at its own pace: deal the same CTA total in proportion to each box's
-    // work, r m^2, so the groups finish together (at least one CTA, at most one per 16 columns).
+    // work, r m^2, so the groups finish together (at most one CTA per 16 columns).
     std::vector<int32_t> cta_off;
     if (G > 1 && nb > 1) {
-        const int total = nb * G;
         std::vector<double> wgt(nb);
-        double W = 0.0;
+        std::vector<int> cap(nb);
         for (int b = 0; b < nb; ++b) {
             wgt[b] = (double)L.r[b] * (double)L.m[b] * (double)L.m[b];
-            W += wgt[b];
+            cap[b] = std::max(1, (int)(2 * L.m[b] / 32));
         }
-        std::vector<int> gb(nb);
-        int used = 0;
-        for (int b = 0; b < nb; ++b) {
-            const int cap_b = std::max(1, (int)(2 * L.m[b] / 32));
-            gb[b] = std::max(1, std::min(cap_b, (int)std::floor(total * wgt[b] / W)));
-            used += gb[b];
-        }
-        while (used < total) {              // the rest to the boxes with the most work per CTA
-            int best = -1;
-            for (int b = 0; b < nb; ++b)
-                if (gb[b] < std::max(1, (int)(2 * L.m[b] / 32)) && (best < 0 || wgt[b] / gb[b] > wgt[best] / gb[best]))
-                    best = b;
-            if (best < 0) break;
-            ++gb[best];
-            ++used;
-        }
-        cta_off.assign(nb + 1, 0);
-        for (int b = 0; b < nb; ++b) cta_off[b + 1] = cta_off[b] + gb[b];
+        cta_off = proportional_groups(nb * G, wgt, cap);
     }
     const int ctas = cta_off.empty() ? nb * G : cta_off[nb];
     if (!cta_off.empty()) {

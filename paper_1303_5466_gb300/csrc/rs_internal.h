@@ -125,6 +125,9 @@ template <class T>
 cudaError_t launch_gj_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A,
                               int32_t* ipiv, const int64_t* ipiv_off, int* pivbuf, unsigned int* bar, int* status,
                               long long spin_limit, int max_m);
+// Deal `total` CTAs to nb groups in proportion to their work (at least one each, at most
+// cap[b]); returns the prefix (nb + 1 entries).
+std::vector<int32_t> proportional_groups(int total, const std::vector<double>& work, const std::vector<int>& cap);
 // Co-resident CTAs of the GJ kernel for a launch of nb matrices of size <= max_m.
 template <class T>
 int gj_max_ctas(int max_m, int nb);
@@ -136,10 +139,11 @@ int gj_panel_width();
 // counter per matrix, zeroed before the launch.  Reads the lower triangle, writes the full
 // inverse.  A matrix that is not SPD to working accuracy sets DEV_NOT_SPD and is left partly
 // swept.
+// Group sizes as for launch_cpqr: G per matrix, or the device prefix cta_off (ctas in all).
 template <class T>
-cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* m, const int64_t* off, T* A, T* Pb,
-                                 const int64_t* pb_off, unsigned int* bar, int* status, long long spin_limit,
-                                 int max_m);
+cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int32_t* m,
+                                 const int64_t* off, T* A, T* Pb, const int64_t* pb_off, unsigned int* bar,
+                                 int* status, long long spin_limit, int max_m);
 template <class T>
 int sweep_max_ctas();
 int sweep_panel_width();
