@@ -145,7 +145,7 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 //      share for the next step.
 // The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step (every CTA
 // computes alpha from the same data in the same order).
-template <int NT, class T>
+template <int NT, int U, class T>
 __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restrict__ cta_off,
         const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
@@ -273,7 +273,6 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
             const int j1 = two ? alist[t + 1] : j0;
             T* col0 = Y + (int64_t)j0 * r;
             T* col1 = Y + (int64_t)j1 * r;
-            constexpr int U = 4;
             T w0 = 0, w1 = 0, w0b = 0, w1b = 0;      // two accumulators per column: shorter FMA chains
             int i = s + lane;
             for (; i + 32 * (U - 1) < r; i += 32 * U) {
@@ -366,46 +365,57 @@ static size_t cpqr_shm(int max_r, int max_m, int G)
     return sizeof(int) * (size_t)(2 * max_m + 2) + sizeof(T) * (size_t)max_r + 64;
 }
 
-template <class T>
-cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int64_t* act_off,
-                        const int32_t* nnear, int P,
-                        const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
-                        unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
-                        int max_m, double* nrm, double* ref)
+template <int U, class T>
+static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas,
+                                 const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y,
+                                 double eps, int32_t* kout, int32_t* piv, T* diag, unsigned int* bar,
+                                 unsigned long long* keys, int* status, long long spin_limit, size_t shm, double* nrm,
+                                 double* ref)
 {
     constexpr int NT = 256;
-    if (nb <= 0) return cudaSuccess;
-    const size_t shm = cpqr_shm<T>(max_r, max_m, G);
-    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, U, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
+    count_launches(1);
     if (!cta_off && G == 1) {
-        count_launches(1);
-        cpqr_kernel<NT, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                                                keys, status, spin_limit, nrm, ref);
+        cpqr_kernel<NT, U, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
+                                                   keys, status, spin_limit, nrm, ref);
         return cudaGetLastError();
     }
-    void* args[] = {(void*)&G, (void*)&cta_off, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y,
+    int g0 = cta_off ? nb : G;
+    void* args[] = {(void*)&g0, (void*)&cta_off, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y,
                     (void*)&eps, (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
                     (void*)&spin_limit, (void*)&nrm, (void*)&ref};
-    count_launches(1);
-    int g0 = cta_off ? nb : G;
-    args[0] = (void*)&g0;
-    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, T>, dim3((unsigned)(cta_off ? ctas : nb * G)), dim3(NT),
-                                       args, shm, st);
+    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, U, T>, dim3((unsigned)(cta_off ? ctas : nb * G)),
+                                       dim3(NT), args, shm, st);
 }
 
 template <class T>
-int cpqr_max_ctas(int max_r, int max_m, int G)
+cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, int deep,
+                        const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y, double eps,
+                        int32_t* kout, int32_t* piv, T* diag, unsigned int* bar, unsigned long long* keys,
+                        int* status, long long spin_limit, int max_r, int max_m, double* nrm, double* ref)
+{
+    if (nb <= 0) return cudaSuccess;
+    const size_t shm = cpqr_shm<T>(max_r, max_m, G);
+    if (deep)
+        return launch_cpqr_u<8, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
+                                   keys, status, spin_limit, shm, nrm, ref);
+    return launch_cpqr_u<4, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
+                               keys, status, spin_limit, shm, nrm, ref);
+}
+
+template <class T>
+int cpqr_max_ctas(int max_r, int max_m, int G, int deep)
 {
     constexpr int NT = 256;
     const size_t shm = cpqr_shm<T>(max_r, max_m, G);
     if (shm > 227 * 1024) return 0;
-    if (cudaFuncSetAttribute(cpqr_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
-        return 0;
+    const void* fn = deep ? (const void*)cpqr_kernel<NT, 8, T> : (const void*)cpqr_kernel<NT, 4, T>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel<NT, T>, NT, shm) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, shm) != cudaSuccess) return 0;
     return per_sm * sms;
 }
 
@@ -543,11 +553,11 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
     template cudaError_t launch_assemble_Y<T>(cudaStream_t, int, const int32_t*, const int64_t*, const int32_t*,     \
                                               const int64_t*, const double*, const double*, int, const int64_t*, T*, \
                                               KernelK, int);                                                        \
-    template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int32_t*, int, const int64_t*, const int32_t*, \
-                                        int, const int64_t*,                                                        \
-                                        T*, double, int32_t*, int32_t*, T*, unsigned int*, unsigned long long*,     \
-                                        int*, long long, int, int, double*, double*);                               \
-    template int cpqr_max_ctas<T>(int, int, int);                                                                    \
+    template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int32_t*, int, int, const int64_t*,            \
+                                        const int32_t*, int, const int64_t*, T*, double, int32_t*, int32_t*, T*,    \
+                                        unsigned int*, unsigned long long*, int*, long long, int, int, double*,     \
+                                        double*);                                                                   \
+    template int cpqr_max_ctas<T>(int, int, int, int);                                                               \
     template cudaError_t launch_id_T<T>(cudaStream_t, int, const int64_t*, const int32_t*, const int32_t*, int,      \
                                         const int64_t*, const T*, const int32_t*, const T*, const int32_t*,         \
                                         const int32_t*, const int64_t*, T*, int, int);                              \

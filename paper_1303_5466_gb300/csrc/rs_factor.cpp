@@ -331,7 +331,12 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     {
     // the rank is known only afterwards: the work is added once k is read back
     ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0);
-    RS_CUDA(launch_cpqr<T>(st, nb, G, cta_off.empty() ? nullptr : w.cta_off.as<int32_t>(), ctas,
+    // few CTAs per SM: each warp keeps twice the rows in flight
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int deep = (G > 1 && ctas <= 2 * sms && ctas <= cpqr_max_ctas<T>(max_r, max_m, G, 1)) ? 1 : 0;
+    RS_CUDA(launch_cpqr<T>(st, nb, G, cta_off.empty() ? nullptr : w.cta_off.as<int32_t>(), ctas, deep,
                         L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
                         w.Y.as<T>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<T>(),
                         op->d_bar.as<unsigned int>(), w.keys.as<unsigned long long>(), op->d_status.as<int>(),

@@ -234,7 +234,7 @@ int compress_forms(const IdCtx& ctx, cudaStream_t st, std::vector<CForm*>& forms
         const int G = choose_group(nb, max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
         RS_CUDA(keys.alloc(sizeof(unsigned long long) * 2 * (size_t)nb * G));
         RS_CUDA(norms.alloc(sizeof(double) * 2 * (size_t)(sum_a + 1)));
-        RS_CUDA(launch_cpqr<T>(st, nb, G, nullptr, 0, d_act_off.as<int64_t>(), d_nn.as<int32_t>(), 0, d_y_off.as<int64_t>(),
+        RS_CUDA(launch_cpqr<T>(st, nb, G, nullptr, 0, 0, d_act_off.as<int64_t>(), d_nn.as<int32_t>(), 0, d_y_off.as<int64_t>(),
                                Y.as<T>(), eps, kk.as<int32_t>(), piv.as<int32_t>(), diag.as<T>(),
                                ctx.bar->as<unsigned int>(), keys.as<unsigned long long>(), ctx.status, ctx.spin,
                                max_r, max_m, norms.as<double>(), norms.as<double>() + sum_a + 1));
