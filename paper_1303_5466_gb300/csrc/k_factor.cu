@@ -37,6 +37,12 @@ __device__ __forceinline__ S hank_row(const KernelK& K, double r)
 template <class S>
 __device__ __forceinline__ S kentry(const KernelK& K, int g, int gp)
 {
+    if (K.tab) {
+        const int d1 = g % K.n - gp % K.n, d2 = g / K.n - gp / K.n;
+        const S t = ((const S*)K.tab)[(d1 + K.n - 1) + (int64_t)(2 * K.n - 1) * (d2 + K.n - 1)];
+        if constexpr (is_cplx<S>::value) return rscale<S>(K.s[g] * K.s[gp], t);
+        else return t;
+    }
     if constexpr (is_cplx<S>::value) {
         double x, y, xp, yp;
         grid_xy(K, g, x, y);

@@ -753,6 +753,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (a)
         for (int64_t g = 0; g < op->N; ++g) ag[g] = a[op->input_of_g[g]];
     if ((rc = upload(op->d_a, ag, st))) return rc;
+    if ((rc = kernel_tables(op, st))) return rc;
     const int P = op->opts.proxy_points;
     std::vector<double> uc(2 * (size_t)P + 1);
     for (int q = 0; q < P; ++q) {

@@ -207,6 +207,7 @@ int apply_once(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream
 int refine_solve(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStream_t st);
 int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
                    cudaStream_t st);
+int kernel_tables(rs_op* op, cudaStream_t st);
 void helmholtz_cell_integral(double h, double kappa, double* re, double* im);
 }  // namespace rs
 

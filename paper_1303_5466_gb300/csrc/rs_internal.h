@@ -70,6 +70,10 @@ struct KernelK {
     double kappa;
     double hs_re, hs_im;
     const double* s;
+    // the off-diagonal entries on the grid depend only on the offset (d1, d2): when set, a
+    // (2n-1)^2 table of K(d1 h, d2 h) in the factor's storage type (Helmholtz: without the
+    // s_g s_g' scaling), read at (d1 + n - 1) + (2n - 1)(d2 + n - 1)
+    const void* tab;
 };
 
 // All launchers below are instantiated for T = double (FP64 path), float (FP32 storage of the

@@ -200,6 +200,31 @@ int refine_t(rs_op* op, const Z* fd, Z* xd, int64_t nrhs, cudaStream_t st)
 
 }  // namespace
 
+// Offset tables of the kernel for the factorization's entries (and the residual): FP64 or
+// complex128, plus the FP32 / complex64 copy for the reduced precisions; sets op->K.tab.
+int kernel_tables(rs_op* op, cudaStream_t st)
+{
+    RS_CUDA(cudaStreamSynchronize(st));          // a(x) and the scaling were uploaded on st
+    int rc;
+    if (op->kind == RS_HELMHOLTZ) {
+        if (op->opts.precision == RS_C64_REFINED) {
+            if ((rc = residual_setup_lo<cplx<double>, cplx<float>>(op, st))) return rc;
+            op->K.tab = op->d_ktab_lo.p;
+        } else {
+            if ((rc = residual_setup(op, st))) return rc;
+            op->K.tab = op->d_ktab.p;
+        }
+    } else if (op->opts.precision == RS_MIXED_FP32) {
+        if ((rc = residual_setup_lo<double, float>(op, st))) return rc;
+        op->K.tab = op->d_ktab_lo.p;
+    } else {
+        if ((rc = residual_setup(op, st))) return rc;
+        op->K.tab = op->d_ktab.p;
+    }
+    RS_CUDA(cudaStreamSynchronize(st));
+    return RS_OK;
+}
+
 // r = f - A x (device, N x nrhs column-major in input order, FP64 or complex128 by kernel);
 // rel[c] = |r_c| / |f_c|.
 int residual_apply(rs_op* op, const double* x, const double* f, int64_t nrhs, double* r, double* rel,
