@@ -269,14 +269,14 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
             if (gi == 0) { piv[a0 + s] = p; diag[a0 + s] = beta; }
         }
         __syncthreads();
-        // 3. this CTA's share of the open columns, two per warp
+        // 3. this CTA's share of the open columns.  Its warps take contiguous runs of equal
+        // length (within one column), two columns at a time and a single column at the end
+        // of an odd run, so a warp never waits for a neighbour by more than one column.
         const int lo = (int)(((int64_t)gi * nopen) / G), hi = (int)(((int64_t)(gi + 1) * nopen) / G);
         unsigned long long wbest = 0;
         const bool lo16 = lane < 16;       // paired bookkeeping: lanes 0-15 column j0, 16-31 j1
-        for (int t = lo + 2 * warp; t < hi; t += 2 * NW) {
-            const int j0 = alist[t];
-            const bool two = t + 1 < hi;
-            const int j1 = two ? alist[t + 1] : j0;
+        auto columns = [&](auto two_c, int j0, int j1) {
+            constexpr bool TWO = decltype(two_c)::value;
             T* col0 = Y + (int64_t)j0 * r;
             T* col1 = Y + (int64_t)j1 * r;
             T w0 = 0, w1 = 0, w0b = 0, w1b = 0;      // two accumulators per column: shorter FMA chains
@@ -287,29 +287,37 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
                 for (int u = 0; u < U; ++u) {
                     vv[u] = conj_(v[i + 32 * u]);
                     xa[u] = ldcg_(col0 + i + 32 * u);
-                    xb[u] = ldcg_(col1 + i + 32 * u);
+                    if constexpr (TWO) xb[u] = ldcg_(col1 + i + 32 * u);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u += 2) {
                     w0 = fma_(vv[u], xa[u], w0);
-                    w1 = fma_(vv[u], xb[u], w1);
                     w0b = fma_(vv[u + 1], xa[u + 1], w0b);
-                    w1b = fma_(vv[u + 1], xb[u + 1], w1b);
+                    if constexpr (TWO) {
+                        w1 = fma_(vv[u], xb[u], w1);
+                        w1b = fma_(vv[u + 1], xb[u + 1], w1b);
+                    }
                 }
             }
             for (; i < r; i += 32) {
                 const T vv = conj_(v[i]);
                 w0 = fma_(vv, ldcg_(col0 + i), w0);
-                w1 = fma_(vv, ldcg_(col1 + i), w1);
+                if constexpr (TWO) w1 = fma_(vv, ldcg_(col1 + i), w1);
             }
             w0 += w0b;
-            w1 += w1b;
-            // both sums in one butterfly: lanes 0-15 end with w0's, 16-31 with w1's
-            T wp = (lo16 ? w0 : w1) + shfl_xor_(lo16 ? w1 : w0, 16);
+            T tw0, tw1 = 0;
+            if constexpr (TWO) {
+                w1 += w1b;
+                // both sums in one butterfly: lanes 0-15 end with w0's, 16-31 with w1's
+                T wp = (lo16 ? w0 : w1) + shfl_xor_(lo16 ? w1 : w0, 16);
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) wp += shfl_xor_(wp, o);
-            const T twp = tau * wp;
-            const T tw0 = shfl_(twp, 0), tw1 = shfl_(twp, 16);
+                for (int o = 8; o > 0; o >>= 1) wp += shfl_xor_(wp, o);
+                const T twp = tau * wp;
+                tw0 = shfl_(twp, 0);
+                tw1 = shfl_(twp, 16);
+            } else {
+                tw0 = tau * warp_sum(w0);
+            }
             T rs0 = 0, rs1 = 0;                // row s after the update (lane 0)
             i = s + lane;
             for (; i + 32 * (U - 1) < r; i += 32 * U) {
@@ -318,44 +326,62 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
                 for (int u = 0; u < U; ++u) {
                     vv[u] = v[i + 32 * u];
                     xa[u] = ldcg_(col0 + i + 32 * u);
-                    xb[u] = ldcg_(col1 + i + 32 * u);
+                    if constexpr (TWO) xb[u] = ldcg_(col1 + i + 32 * u);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     xa[u] = fma_(-vv[u], tw0, xa[u]);
-                    xb[u] = fma_(-vv[u], tw1, xb[u]);
                     col0[i + 32 * u] = xa[u];
-                    if (two) col1[i + 32 * u] = xb[u];
+                    if constexpr (TWO) {
+                        xb[u] = fma_(-vv[u], tw1, xb[u]);
+                        col1[i + 32 * u] = xb[u];
+                    }
                 }
-                if (i == s) { rs0 = xa[0]; rs1 = xb[0]; }
+                if (i == s) {
+                    rs0 = xa[0];
+                    if constexpr (TWO) rs1 = xb[0];
+                }
             }
             for (; i < r; i += 32) {
                 const T vv = v[i];
-                const T xa = fma_(-vv, tw0, ldcg_(col0 + i)), xb = fma_(-vv, tw1, ldcg_(col1 + i));
+                const T xa = fma_(-vv, tw0, ldcg_(col0 + i));
                 col0[i] = xa;
-                if (two) col1[i] = xb;
-                if (i == s) { rs0 = xa; rs1 = xb; }
+                if (i == s) rs0 = xa;
+                if constexpr (TWO) {
+                    const T xb = fma_(-vv, tw1, ldcg_(col1 + i));
+                    col1[i] = xb;
+                    if (i == s) rs1 = xb;
+                }
             }
-            // downdated squared norms of both columns at once (R_sj is row s of column j)
-            const T r0 = shfl_(rs0, 0), r1 = shfl_(rs1, 0);
-            const int jj = lo16 ? j0 : j1;
-            double nv = ldcg_(nrm + jj) - abs2d(lo16 ? r0 : r1);
+            // downdated squared norms (R_sj is row s of column j): both columns in one
+            // instruction when there are two
+            const T r0 = shfl_(rs0, 0);
+            const T r1 = TWO ? shfl_(rs1, 0) : r0;
+            const int jj = (TWO && !lo16) ? j1 : j0;
+            double nv = ldcg_(nrm + jj) - abs2d((TWO && !lo16) ? r1 : r0);
             const unsigned need = __ballot_sync(0xffffffffu, nv < 1e-4 * ldcg_(ref + jj));
             if (need & 0x00010001u) {
                 __syncwarp();                  // the recomputation reads the warp's stores
-                for (int c = 0; c < (two ? 2 : 1); ++c) {
+                for (int c = 0; c < (TWO ? 2 : 1); ++c) {
                     if (!(need & (1u << (16 * c)))) continue;
                     const T* col = c == 0 ? col0 : col1;
                     double q = 0.0;
                     for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(ldcg_(col + i2));
                     q = warp_sum(q);
-                    if (!two || (lane >> 4) == c) nv = q;
+                    if (!TWO || (lane >> 4) == c) nv = q;
                     if (lane == 16 * c) ref[jj] = q;
                 }
             }
-            if (lane == 0 || (lane == 16 && two)) nrm[jj] = nv;
+            if (lane == 0 || (TWO && lane == 16)) nrm[jj] = nv;
             const unsigned long long kq = pivot_key(nv, jj);
             wbest = kq > wbest ? kq : wbest;
+        };
+        {
+            const int C = hi - lo;
+            const int wlo = lo + (int)(((int64_t)warp * C) / NW), whi = lo + (int)(((int64_t)(warp + 1) * C) / NW);
+            int t = wlo;
+            for (; t + 1 < whi; t += 2) columns(std::true_type{}, alist[t], alist[t + 1]);
+            if (t < whi) columns(std::false_type{}, alist[t], alist[t]);
         }
         wbest = block_max_u64<NT>(wbest, kred);
         if (threadIdx.x == 0) kb[((s + 1) & 1) * G + gi] = wbest;

@@ -83,15 +83,34 @@ int level_sets(int64_t n, int d, int l, const int64_t* child_k, const int64_t* c
     nnear.assign(nb, 0);
     near_off.assign(nb + 1, 0);
     nearv.clear();
+    // the level's boxes tile the grid: index them by position, so each box finds its (at most
+    // eight) neighbours directly, then visits them in ascending box index
+    std::vector<BoxInt> boxes(nb);
+    int64_t nbx = 0, nby = 0;
     for (int64_t j = 0; j < nb; ++j) {
-        const BoxInt b = box_int(n, l, j);
+        boxes[j] = box_int(n, l, j);
+        nbx = std::max(nbx, boxes[j].bx + 1);
+        nby = std::max(nby, boxes[j].by + 1);
+    }
+    std::vector<int64_t> at((size_t)(nbx * nby), -1);
+    for (int64_t j = 0; j < nb; ++j) at[(size_t)(boxes[j].bx + nbx * boxes[j].by)] = j;
+    for (int64_t j = 0; j < nb; ++j) {
+        const BoxInt b = boxes[j];
         const int64_t cx = (2 * b.bx + 1) * b.wx, cy = (2 * b.by + 1) * b.wy;
         const double R = rfac * (double)std::max(b.wx, b.wy);
         const double R2 = R * R;
-        for (int64_t q = 0; q < nb; ++q) {
-            if (q == j) continue;
-            const BoxInt o = box_int(n, l, q);
-            if (std::llabs(o.bx - b.bx) > 1 || std::llabs(o.by - b.by) > 1) continue;
+        int64_t nbr[8];
+        int cnt = 0;
+        for (int64_t ey = -1; ey <= 1; ++ey)
+            for (int64_t ex = -1; ex <= 1; ++ex) {
+                const int64_t x = b.bx + ex, y = b.by + ey;
+                if ((ex == 0 && ey == 0) || x < 0 || y < 0 || x >= nbx || y >= nby) continue;
+                const int64_t q = at[(size_t)(x + nbx * y)];
+                if (q >= 0) nbr[cnt++] = q;
+            }
+        std::sort(nbr, nbr + cnt);
+        for (int c = 0; c < cnt; ++c) {
+            const int64_t q = nbr[c];
             for (int64_t p = act_off[q]; p < act_off[q + 1]; ++p) {
                 const int64_t g = act[p];
                 const int64_t dx = 2 * (g % n) + 1 - cx, dy = 2 * (g / n) + 1 - cy;
