@@ -214,8 +214,35 @@ enum {
  * bytes: algorithmic bytes the class must move (solve: factor bytes read).  Any output may be
  * NULL.  Returns RS_E_INVALID for an unknown class. */
 int rs_op_profile(const rs_op* op, int cls, double* ms, double* work, double* bytes, int64_t* launches);
+/* ms: summed event time of the class's launches at tree level `level` (factor classes; the
+ * root is level 0), 0 if none. */
+int rs_op_profile_level(const rs_op* op, int cls, int level, double* ms);
 /* Kernel launches made by this library in this process so far (all threads). */
 int64_t rs_launch_count(void);
+
+/* Autotuner (launch shapes; no counterpart in the paper).  Launch shapes -- the CTA-group size
+ * of the CPQR and sweep kernels and the CPQR variant -- are chosen per level from the counts
+ * of boxes and columns.  rs_autotune factors the given operator once with the current table
+ * and once per candidate setting (each forced on every level, with per-level CUDA-event
+ * timing), then records for every level's launch shape the fastest candidate of each kernel
+ * in a process-wide table that later rs_factor calls consult; the table is written to `path`
+ * as JSON unless path is NULL.  Choices never change what is computed: the CPQR variants
+ * differ only in rounding order.  report may be NULL.  The table is shared by all threads;
+ * while rs_autotune runs, its candidates apply to factorizations on the calling thread only.
+ * rs_tune_load merges a file written by rs_tune_save into the table (RS_E_INVALID on any
+ * malformed entry, leaving the table unchanged); rs_tune_clear empties it. */
+typedef struct {
+    int candidates;              /* settings timed                                         */
+    int keys_set;                /* table entries written                                  */
+    double default_factor_ms;    /* factor wall time with the table as it was              */
+    double tuned_factor_ms;      /* factor wall time with the new table                    */
+} rs_tune_report;
+int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps, const rs_opts* opts,
+                void* stream, const char* path, rs_tune_report* report);
+int rs_tune_save(const char* path);
+int rs_tune_load(const char* path);
+int rs_tune_clear(void);
+int rs_tune_count(void);
 
 /* Per-box inspection (copies from the device).  level 1..d, box 0..2^level-1.
  * sizes: m (active points), k (skeleton), r (ID rows), nnear (near rows). */

@@ -53,6 +53,11 @@ class rs_stats(C.Structure):
                 ("spd_fallbacks", C.c_int), ("refine_fp64_sums", C.c_int)]
 
 
+class rs_tune_report(C.Structure):
+    _fields_ = [("candidates", C.c_int), ("keys_set", C.c_int), ("default_factor_ms", C.c_double),
+                ("tuned_factor_ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -101,6 +106,13 @@ def lib():
         L.rs_hss1d_info.argtypes = [vp, C.POINTER(C.c_int), i64p, i64p]
         L.rs_hss1d_node.argtypes = [vp, C.c_int, C.c_int, i64p, i64p, i64p, i64p, i64p]
         L.rs_hss1d_free.argtypes = [vp]
+        L.rs_op_profile_level.argtypes = [vp, C.c_int, C.c_int, dp]
+        L.rs_autotune.argtypes = [vp, C.POINTER(rs_kernel), dp, C.c_double, C.POINTER(rs_opts), vp, C.c_char_p,
+                                  C.POINTER(rs_tune_report)]
+        L.rs_tune_save.argtypes = [C.c_char_p]
+        L.rs_tune_load.argtypes = [C.c_char_p]
+        L.rs_tune_clear.argtypes = []
+        L.rs_tune_count.argtypes = []
         _lib = L
     return _lib
 
@@ -272,6 +284,45 @@ def rs_op_profile(op):
         _check(lib().rs_op_profile(op, cls, C.byref(ms), C.byref(w), C.byref(b), C.byref(n)))
         out[name] = (ms.value, w.value, b.value, n.value)
     return out
+
+
+def rs_op_profile_level(op, cls_name, level):
+    """Event time (ms) of one profile class at one tree level (opts.profile)."""
+    ms = C.c_double()
+    _check(lib().rs_op_profile_level(op, PROF_CLASSES.index(cls_name), int(level), C.byref(ms)))
+    return ms.value
+
+
+def rs_autotune(tree, kernel=None, a=None, eps=1e-10, opts=None, stream=None, path=None, kappa=None, b=None):
+    """Time the candidate launch settings on this operator and fill the tuning table (and
+    `path`, JSON, if given).  Returns the report as a dict."""
+    if kappa is not None:
+        bv = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        k = rs_kernel(RS_HELMHOLTZ, float(kappa), _dp(bv))
+    else:
+        k = kernel if kernel is not None else rs_kernel(RS_LAPLACE, 0.0, None)
+    av = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    o = opts if opts is not None else rs_opts_default()
+    rep = rs_tune_report()
+    _check(lib().rs_autotune(tree, C.byref(k), _dp(av), float(eps), C.byref(o), _stream(stream),
+                             None if path is None else str(path).encode(), C.byref(rep)))
+    return {name: getattr(rep, name) for name, _ in rs_tune_report._fields_}
+
+
+def rs_tune_save(path):
+    _check(lib().rs_tune_save(str(path).encode()))
+
+
+def rs_tune_load(path):
+    _check(lib().rs_tune_load(str(path).encode()))
+
+
+def rs_tune_clear():
+    _check(lib().rs_tune_clear())
+
+
+def rs_tune_count():
+    return int(lib().rs_tune_count())
 
 
 def rs_launch_count():

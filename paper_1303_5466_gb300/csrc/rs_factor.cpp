@@ -48,6 +48,7 @@ struct ProfScope {
     int cls;
     cudaStream_t st;
     double work, bytes;
+    int level;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     static cudaEvent_t take(rs_op* o)
     {
@@ -61,7 +62,8 @@ struct ProfScope {
         o->ev_all.push_back(e);
         return e;
     }
-    ProfScope(rs_op* o, int c, cudaStream_t s, double w, double b = 0.0) : op(o), cls(c), st(s), work(w), bytes(b)
+    ProfScope(rs_op* o, int c, cudaStream_t s, double w, double b = 0.0, int lvl = -1)
+        : op(o), cls(c), st(s), work(w), bytes(b), level(lvl)
     {
         if (!op->opts.profile) return;
         e0 = take(op);
@@ -72,7 +74,7 @@ struct ProfScope {
     {
         if (!e0 || !e1) return;
         cudaEventRecord(e1, st);
-        op->pending.push_back({cls, e0, e1, work, bytes});
+        op->pending.push_back({cls, level, e0, e1, work, bytes});
     }
 };
 
@@ -85,6 +87,11 @@ void prof_flush(rs_op* op)
             op->prof_work[r.cls] += r.work;
             op->prof_bytes[r.cls] += r.bytes;
             op->prof_n[r.cls] += 1;
+            if (r.level >= 0) {
+                std::vector<double>& v = op->prof_level_ms[r.cls];
+                if ((int)v.size() <= r.level) v.resize(r.level + 1, 0.0);
+                v[r.level] += ms;
+            }
         }
         op->ev_pool.push_back(r.e0);
         op->ev_pool.push_back(r.e1);
@@ -170,7 +177,7 @@ struct IdWork {
 
 template <class T>
 int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, T* A,
-           const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls)
+           const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls, int level)
 {
     if (max_m <= 0) return RS_OK;
     DevMem d_ipoff;
@@ -185,7 +192,7 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
     const int G = choose_group(nb, max_m * 32 / gj_panel_width(), [&](int) { return gj_max_ctas<T>(max_m, nb); });
     double work = 0.0;
     for (int b = 0; b < nb; ++b) work += 2.0 * (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
-    ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb]);
+    ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb], level);
     RS_CUDA(launch_gj_inverse<T>(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_ipiv.as<int32_t>(),
                               d_ipoff.as<int64_t>(), op->d_pivrow.as<int>(), op->d_bar.as<unsigned int>(),
                               op->d_status.as<int>(), (long long)op->opts.spin_limit, max_m));
@@ -198,7 +205,7 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
 template <class T>
 int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, T* A,
               const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls,
-              bool* not_spd)
+              int level, bool* not_spd)
 {
     *not_spd = false;
     if (max_m <= 0) return RS_OK;
@@ -216,7 +223,12 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
         RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
         // panels are dealt back and forth, so a group of G CTAs wants at least 2G panels
         const int cap = sweep_max_ctas<T>();
-        const int G = choose_group(nb, max_m * 16 / NB, [&](int) { return cap; });
+        int G = choose_group(nb, max_m * 16 / NB, [&](int) { return cap; });
+        // the autotuner's group scale for this launch shape (or the candidate being timed)
+        const double gs = g_trial.sweep_gscale >= 0.0
+                              ? g_trial.sweep_gscale
+                              : tune_get(tune_key("sweep", (int)sizeof(T), nb, max_m, 0) + ".gscale", 1.0);
+        if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
         double work = 0.0;
         for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
         // matrices of one launch differ in size: CTAs in proportion to m^3, at most m / 16 each
@@ -233,7 +245,7 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
             if ((rc = upload(d_cta, cta_off, st))) return rc;
         }
         {
-            ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb]);
+            ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb], level);
             RS_CUDA(launch_sweep_inverse<T>(st, nb, G, cta_off.empty() ? nullptr : d_cta.as<int32_t>(),
                                             cta_off.empty() ? nb * G : cta_off[nb], dm.as<int32_t>(),
                                             doff.as<int64_t>(), A, op->d_pb.as<T>(), d_pboff.as<int64_t>(),
@@ -307,7 +319,12 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
     const int max_r = L.max_r, max_m = L.max_m;
     // the open columns are re-split every step, so a group may take one CTA per 16 columns
-    const int G = choose_group(nb, 2 * max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
+    int G = choose_group(nb, 2 * max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
+    // the autotuner's settings for this launch shape (or the candidate being timed)
+    const std::string tkey = tune_key("cpqr", (int)sizeof(T), nb, max_m, max_r);
+    const double gs = g_trial.cpqr_gscale >= 0.0 ? g_trial.cpqr_gscale : tune_get(tkey + ".gscale", 1.0);
+    const int deep_set = g_trial.cpqr_deep >= 0 ? g_trial.cpqr_deep : (int)tune_get(tkey + ".deep", -1.0);
+    if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
     // The boxes of a level differ in work (boundary boxes have fewer near rows, ranks differ),
     // and a group runs at its own pace: deal the same CTA total in proportion to each box's
     // work, r m^2, so the groups finish together (at most one CTA per 16 columns).
@@ -330,12 +347,14 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     RS_CUDA(w.norms.alloc(sizeof(double) * 2 * (size_t)(sum_m + 1)));
     {
     // the rank is known only afterwards: the work is added once k is read back
-    ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0);
+    ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0, L.l);
     // few CTAs per SM: each warp keeps twice the rows in flight
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int deep = (G > 1 && ctas <= 2 * sms && ctas <= cpqr_max_ctas<T>(max_r, max_m, G, 1)) ? 1 : 0;
+    int deep = (G > 1 && ctas <= 2 * sms) ? 1 : 0;
+    if (deep_set >= 0) deep = deep_set;
+    if (deep && ctas > cpqr_max_ctas<T>(max_r, max_m, G, 1)) deep = 0;     // must stay co-resident
     RS_CUDA(launch_cpqr<T>(st, nb, G, cta_off.empty() ? nullptr : w.cta_off.as<int32_t>(), ctas, deep,
                         L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
                         w.Y.as<T>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<T>(),
@@ -436,11 +455,12 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     const int cls_f = L.l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F;
     bool redo = true;
     if (use_sweep(op)) {
-        if ((rc = run_sweep<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f, &redo)))
+        if ((rc = run_sweep<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f, L.l,
+                               &redo)))
             return rc;
         if (redo && (rc = assemble())) return rc;
     }
-    if (redo && (rc = run_gj<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f)))
+    if (redo && (rc = run_gj<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f, L.l)))
         return rc;
     if (L.l == 0) return RS_OK;
     // W = Phi[:, :k] + Phi[:, k:] T^T ;  E^{-1} = W[:k, :] + T W[k:, :]
@@ -491,14 +511,14 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     redo = true;
     if (use_sweep(op)) {
         if ((rc = run_sweep<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E,
-                               &redo)))
+                               L.l, &redo)))
             return rc;
         if (redo && !p1.empty())     // E^{-1} again from W (the sweep overwrote it)
             RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
                                    L.d_E.as<T>(), W.as<T>()));
     }
     if (!redo) return RS_OK;
-    return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E);
+    return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E, L.l);
 }
 
 void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk, int rows, int cols, int ld, int trans,
@@ -1082,6 +1102,122 @@ int rs_free(rs_op* op)
     if (!op) return RS_OK;
     if (op->inflight.load() > 0) return fail(RS_E_INVALID, "the operator is still referenced by a server");
     delete op;
+    return RS_OK;
+}
+
+int rs_op_profile_level(const rs_op* op, int cls, int level, double* ms)
+{
+    if (!op || !ms || cls < 0 || cls >= RS_PROF_COUNT || level < 0) return fail(RS_E_INVALID, "bad argument");
+    const std::vector<double>& v = op->prof_level_ms[cls];
+    *ms = level < (int)v.size() ? v[level] : 0.0;
+    return RS_OK;
+}
+
+// Autotuner: time whole factorizations under each candidate setting and keep, for every
+// level's launch shape, the fastest candidate of each kernel (the levels are independent
+// launches, so their choices combine).
+int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, double eps, const rs_opts* opts,
+                void* stream, const char* path, rs_tune_report* report)
+{
+    if (!tree) return fail(RS_E_INVALID, "tree is NULL");
+    rs_opts o;
+    if (opts) o = *opts; else rs_opts_default(&o);
+    o.profile = 1;
+    o.k_cut = 0;
+    const cudaStream_t st = (cudaStream_t)stream;
+    // candidates (CPQR group scale, CPQR deep variant, sweep group scale): every CPQR pair and
+    // every sweep scale appears once
+    const TuneTrial trials[] = {{1.0, 0, 1.0}, {1.0, 1, 0.5}, {0.5, 0, 0.25}, {0.5, 1, 1.0}};
+    constexpr int NTR = 4;
+    auto timed_factor = [&](rs_op** op, double* ms) -> int {
+        auto t0 = std::chrono::steady_clock::now();
+        int rc = factor_impl(tree, kernel, a, eps, &o, st, op);
+        if (rc) return rc;
+        RS_CUDA(cudaStreamSynchronize(st));
+        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return RS_OK;
+    };
+    struct Shape {
+        int nb;
+        int64_t m, r, k;
+    };
+    std::vector<Shape> shapes;
+    std::vector<std::vector<double>> t_cpqr(NTR), t_f(NTR), t_e(NTR);
+    double base_ms = 0.0;
+    g_trial = TuneTrial();
+    {
+        rs_op* op = nullptr;
+        int rc = timed_factor(&op, &base_ms);
+        if (rc) return rc;
+        for (int l = 0; l <= op->d; ++l) {
+            const Level& L = op->lev[l];
+            shapes.push_back({L.nb, (int64_t)L.max_m, (int64_t)L.max_r, (int64_t)L.max_k});
+        }
+        rs_free(op);
+    }
+    for (int t = 0; t < NTR; ++t) {
+        g_trial = trials[t];
+        rs_op* op = nullptr;
+        double ms = 0.0;
+        const int rc = timed_factor(&op, &ms);
+        g_trial = TuneTrial();
+        if (rc) return rc;
+        const int d = op->d;
+        t_cpqr[t].assign(d + 1, 0.0);
+        t_f[t].assign(d + 1, 0.0);
+        t_e[t].assign(d + 1, 0.0);
+        for (int l = 0; l <= d; ++l) {
+            double v = 0.0;
+            rs_op_profile_level(op, RS_PROF_CPQR, l, &v);
+            t_cpqr[t][l] = v;
+            rs_op_profile_level(op, l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F, l, &v);
+            t_f[t][l] = v;
+            rs_op_profile_level(op, RS_PROF_INV_E, l, &v);
+            t_e[t][l] = v;
+        }
+        rs_free(op);
+    }
+    int keys = 0;
+    const int esz = (o.precision == RS_MIXED_FP32) ? 4 : (o.precision == RS_C64_REFINED) ? 8
+                    : (kernel && kernel->kind == RS_HELMHOLTZ) ? 16 : 8;
+    for (size_t l = 0; l < shapes.size(); ++l) {
+        const Shape& S = shapes[l];
+        auto best_of = [&](const std::vector<std::vector<double>>& tt) {
+            int b = 0;
+            for (int t = 1; t < NTR; ++t)
+                if (l < tt[t].size() && tt[t][l] < tt[b][l]) b = t;
+            return b;
+        };
+        if (l >= 1) {
+            const int b = best_of(t_cpqr);
+            const std::string k = tune_key("cpqr", esz, S.nb, S.m, S.r);
+            tune_set(k + ".gscale", trials[b].cpqr_gscale);
+            tune_set(k + ".deep", trials[b].cpqr_deep);
+            const int be = best_of(t_e);
+            tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".gscale", trials[be].sweep_gscale);
+            keys += 3;
+        }
+        const int bf = best_of(t_f);
+        tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", trials[bf].sweep_gscale);
+        keys += 1;
+    }
+    double tuned_ms = 0.0;
+    {
+        rs_op* op = nullptr;
+        int rc = timed_factor(&op, &tuned_ms);
+        if (rc) return rc;
+        rs_free(op);
+    }
+    if (path) {
+        int rc = rs_tune_save(path);
+        if (rc) return rc;
+    }
+    if (report) {
+        report->candidates = NTR;
+        report->keys_set = keys;
+        report->default_factor_ms = base_ms;
+        report->tuned_factor_ms = tuned_ms;
+    }
     return RS_OK;
 }
 

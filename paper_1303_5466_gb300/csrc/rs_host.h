@@ -153,10 +153,23 @@ struct SolveWork {
 };
 
 struct ProfRec {
-    int cls;
+    int cls, level;
     cudaEvent_t e0, e1;
     double work, bytes;
 };
+
+// Autotuner table (rs_tune.cpp).  Keys: tune_key(kernel, scalar bytes, boxes, largest m, r).
+std::string tune_key(const char* what, int esz, int nb, int64_t m, int64_t r);
+double tune_get(const std::string& key, double dflt);
+void tune_set(const std::string& key, double v);
+int tune_count();
+// Settings forced on every level by rs_autotune while it times one candidate (negative: none).
+struct TuneTrial {
+    double cpqr_gscale = -1.0;
+    int cpqr_deep = -1;
+    double sweep_gscale = -1.0;
+};
+extern thread_local TuneTrial g_trial;
 
 }  // namespace rs
 
@@ -258,6 +271,7 @@ struct rs_op {
     std::vector<rs::ProfRec> pending;
     std::vector<cudaEvent_t> ev_pool, ev_all;
     double prof_ms[RS_PROF_COUNT] = {}, prof_work[RS_PROF_COUNT] = {}, prof_bytes[RS_PROF_COUNT] = {};
+    std::vector<double> prof_level_ms[RS_PROF_COUNT];     // by tree level (factor classes)
     int64_t prof_n[RS_PROF_COUNT] = {};
     ~rs_op()
     {
