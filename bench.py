@@ -385,6 +385,8 @@ def run_ours(args):
                 for i in range(4):
                     p[i] += v[i]
             last_stats = P.rs_op_stats(op)
+            by_level = {c: [round(P.rs_op_profile_level(op, c, l), 2) for l in range(last_stats["depth"], -1, -1)]
+                        for c in ("cpqr", "inv_F", "inv_E")}
             # residual check of the timed solve on sampled rows (outside the timing)
             x_last = x_dev.cpu().numpy().T.copy()
             P.rs_free(op)
@@ -441,6 +443,7 @@ def run_ours(args):
                            "frac": (sol[1] / (sol[0] * 1e-3) / 1e12) / PEAK_FP64_TFLOPS if sol[0] else None,
                            "achieved_gbs": sol[2] / (sol[0] * 1e-3) / 1e9 if sol[0] else None},
         "profile_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+        "profile_ms_by_level": {"levels": "finest .. root (root: inv_F holds the root inverse)", **by_level},
         "profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items() if v[0] > 0 and v[1] > 0},
         "roofline_by_kernel": {k: {"achieved_tflops": kern[k][1] / (kern[k][0] * 1e-3) / 1e12,
                                    "frac_fp64": kern[k][1] / (kern[k][0] * 1e-3) / 1e12 / PEAK_FP64_TFLOPS,

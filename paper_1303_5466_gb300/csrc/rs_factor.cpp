@@ -180,7 +180,7 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
            const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls, int level)
 {
     if (max_m <= 0) return RS_OK;
-    DevMem d_ipoff;
+    DevMem& d_ipoff = op->t_ipoff;      // kept by the op: a freed buffer would synchronise the device
     RS_CUDA(d_ipoff.alloc(sizeof(int64_t) * nb));
     RS_CUDA(cudaMemcpyAsync(d_ipoff.p, size_off.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
     const int64_t tot = size_off[nb];
@@ -215,7 +215,7 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
         const int NB = sweep_panel_width();
         std::vector<int64_t> pb_off(nb);
         for (int b = 0; b < nb; ++b) pb_off[b] = 2 * (int64_t)NB * size_off[b];
-        DevMem d_pboff;
+        DevMem& d_pboff = op->t_pboff;
         int rc;
         if ((rc = upload(d_pboff, pb_off, st))) return rc;
         RS_CUDA(op->d_pb.alloc(sizeof(T) * 2 * (size_t)NB * (size_t)(size_off[nb] + 1)));
@@ -233,7 +233,7 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
         for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
         // matrices of one launch differ in size: CTAs in proportion to m^3, at most m / 16 each
         std::vector<int32_t> cta_off;
-        DevMem d_cta;
+        DevMem& d_cta = op->t_cta;
         if (G > 1 && nb > 1) {
             std::vector<double> wgt(nb);
             std::vector<int> capb(nb);
@@ -317,50 +317,91 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     RS_CUDA(L.d_k.alloc(sizeof(int32_t) * nb));
     RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
     RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
-    const int max_r = L.max_r, max_m = L.max_m;
-    // the open columns are re-split every step, so a group may take one CTA per 16 columns
-    int G = choose_group(nb, 2 * max_m, [&](int g) { return cpqr_max_ctas<T>(max_r, max_m, g); });
-    // the autotuner's settings for this launch shape (or the candidate being timed)
-    const std::string tkey = tune_key("cpqr", (int)sizeof(T), nb, max_m, max_r);
+    // The autotuner's settings for this level (or the candidate being timed).  With a batch
+    // budget, boxes whose Y fit together in that many 96 MB units go to one launch each, and
+    // each launch takes the whole GPU: the passes of a step then stream from L2 rather than
+    // HBM (all boxes of a big level at once spill L2 and re-read every trailing matrix from HBM
+    // at every step), at the price of fewer CTAs per box.  Untuned: one launch per level.
+    const std::string tkey = tune_key("cpqr", (int)sizeof(T), nb, L.max_m, L.max_r);
     const double gs = g_trial.cpqr_gscale >= 0.0 ? g_trial.cpqr_gscale : tune_get(tkey + ".gscale", 1.0);
     const int deep_set = g_trial.cpqr_deep >= 0 ? g_trial.cpqr_deep : (int)tune_get(tkey + ".deep", -1.0);
-    if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
-    // The boxes of a level differ in work (boundary boxes have fewer near rows, ranks differ),
-    // and a group runs at its own pace: deal the same CTA total in proportion to each box's
-    // work, r m^2, so the groups finish together (at most one CTA per 16 columns).
-    std::vector<int32_t> cta_off;
-    if (G > 1 && nb > 1) {
-        std::vector<double> wgt(nb);
-        std::vector<int> cap(nb);
-        for (int b = 0; b < nb; ++b) {
-            wgt[b] = (double)L.r[b] * (double)L.m[b] * (double)L.m[b];
-            cap[b] = std::max(1, (int)(2 * L.m[b] / 32));
-        }
-        cta_off = proportional_groups(nb * G, wgt, cap);
+    const double batch_bytes =
+        96.0 * (1 << 20) * (g_trial.cpqr_batch >= 0.0 ? g_trial.cpqr_batch : tune_get(tkey + ".batch", 0.0));
+    std::vector<int> b_start(1, 0);
+    if (batch_bytes > 0.0) {
+        double tot = 0.0;
+        for (int b = 0; b < nb; ++b) tot += (double)sizeof(T) * (double)L.r[b] * (double)L.m[b];
+        const int nbat = std::max(1, std::min(nb, (int)std::ceil(tot / batch_bytes)));
+        for (int q = 1; q < nbat; ++q) b_start.push_back((int)(((int64_t)q * nb) / nbat));
     }
-    const int ctas = cta_off.empty() ? nb * G : cta_off[nb];
-    if (!cta_off.empty()) {
-        int rc2;
-        if ((rc2 = upload(w.cta_off, cta_off, st))) return rc2;
-    }
-    RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * 2 * (size_t)ctas));
-    RS_CUDA(w.norms.alloc(sizeof(double) * 2 * (size_t)(sum_m + 1)));
-    {
-    // the rank is known only afterwards: the work is added once k is read back
-    ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0, L.l);
-    // few CTAs per SM: each warp keeps twice the rows in flight
+    b_start.push_back(nb);
+    const int nbat = (int)b_start.size() - 1;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int deep = (G > 1 && ctas <= 2 * sms) ? 1 : 0;
-    if (deep_set >= 0) deep = deep_set;
-    if (deep && ctas > cpqr_max_ctas<T>(max_r, max_m, G, 1)) deep = 0;     // must stay co-resident
-    RS_CUDA(launch_cpqr<T>(st, nb, G, cta_off.empty() ? nullptr : w.cta_off.as<int32_t>(), ctas, deep,
-                        L.d_act_off.as<int64_t>(), w.nn.as<int32_t>(), P, w.y_off.as<int64_t>(),
-                        w.Y.as<T>(), op->eps, L.d_k.as<int32_t>(), w.piv.as<int32_t>(), w.diag.as<T>(),
-                        op->d_bar.as<unsigned int>(), w.keys.as<unsigned long long>(), op->d_status.as<int>(),
-                        (long long)op->opts.spin_limit, max_r, max_m, w.norms.as<double>(),
-                        w.norms.as<double>() + sum_m + 1));
+    struct Batch {
+        int b0, nb, G, ctas, deep, max_r, max_m;
+        size_t cta_pos;
+    };
+    std::vector<Batch> bats;
+    std::vector<int32_t> cta_all;
+    size_t max_keys = 1;
+    for (int q = 0; q < nbat; ++q) {
+        Batch B{};
+        B.b0 = b_start[q];
+        B.nb = b_start[q + 1] - b_start[q];
+        for (int b = B.b0; b < B.b0 + B.nb; ++b) {
+            B.max_r = std::max<int>(B.max_r, (int)L.r[b]);
+            B.max_m = std::max<int>(B.max_m, (int)L.m[b]);
+        }
+        // the open columns are re-split every step, so a group may take one CTA per 16 columns
+        int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g); });
+        if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
+        B.G = G;
+        // The boxes of a batch differ in work (boundary boxes have fewer near rows, ranks
+        // differ), and a group runs at its own pace: deal the same CTA total in proportion to
+        // each box's work, r m^2, so the groups finish together (at most one CTA per 16 columns).
+        B.cta_pos = cta_all.size();
+        if (G > 1 && B.nb > 1) {
+            std::vector<double> wgt(B.nb);
+            std::vector<int> cap(B.nb);
+            for (int b = 0; b < B.nb; ++b) {
+                wgt[b] = (double)L.r[B.b0 + b] * (double)L.m[B.b0 + b] * (double)L.m[B.b0 + b];
+                cap[b] = std::max(1, (int)(2 * L.m[B.b0 + b] / 32));
+            }
+            const std::vector<int32_t> off = proportional_groups(B.nb * G, wgt, cap);
+            cta_all.insert(cta_all.end(), off.begin(), off.end());
+            B.ctas = off[B.nb];
+        } else {
+            B.cta_pos = (size_t)-1;
+            B.ctas = B.nb * G;
+        }
+        // few CTAs per SM: each warp keeps twice the rows in flight
+        B.deep = (G > 1 && B.ctas <= 2 * sms) ? 1 : 0;
+        if (deep_set >= 0) B.deep = deep_set;
+        if (B.deep && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, 1)) B.deep = 0;   // must stay co-resident
+        max_keys = std::max(max_keys, (size_t)(2 * B.ctas));
+        bats.push_back(B);
+    }
+    if (!cta_all.empty()) {
+        int rc2;
+        if ((rc2 = upload(w.cta_off, cta_all, st))) return rc2;
+    }
+    RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * max_keys));
+    RS_CUDA(w.norms.alloc(sizeof(double) * 2 * (size_t)(sum_m + 1)));
+    {
+        // the rank is known only afterwards: the work is added once k is read back
+        ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0, L.l);
+        for (const Batch& B : bats) {
+            RS_CUDA(launch_cpqr<T>(st, B.nb, B.G,
+                                   B.cta_pos == (size_t)-1 ? nullptr : w.cta_off.as<int32_t>() + B.cta_pos, B.ctas,
+                                   B.deep, L.d_act_off.as<int64_t>() + B.b0, w.nn.as<int32_t>() + B.b0, P,
+                                   w.y_off.as<int64_t>() + B.b0, w.Y.as<T>(), op->eps, L.d_k.as<int32_t>() + B.b0,
+                                   w.piv.as<int32_t>(), w.diag.as<T>(), op->d_bar.as<unsigned int>() + B.b0,
+                                   w.keys.as<unsigned long long>(), op->d_status.as<int>(),
+                                   (long long)op->opts.spin_limit, B.max_r, B.max_m, w.norms.as<double>(),
+                                   w.norms.as<double>() + sum_m + 1));
+        }
     }
     if ((rc = check_status(op, st))) return rc;
     std::vector<int32_t> k32(nb), piv(sum_m);
@@ -422,7 +463,9 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
                         w.skpos.as<int32_t>(), w.rscol.as<int32_t>(), L.d_t_off.as<int64_t>(), L.d_T.as<T>(),
                         max_res, L.max_k));
     }
-    return check_status(op, st);
+    // no synchronisation: the next level's CPQR status check covers this launch too
+    RS_CUDA(cudaGetLastError());
+    return RS_OK;
 }
 
 // Inversion phase of one level (Algorithm 1 with the E of Algorithm 2).
@@ -466,7 +509,10 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     // W = Phi[:, :k] + Phi[:, k:] T^T ;  E^{-1} = W[:k, :] + T W[k:, :]
     if ((rc = upload(L.d_e_off, L.e_off, st))) return rc;
     RS_CUDA(L.d_E.alloc(sizeof(T) * (size_t)(L.e_off[nb] + 1)));
-    DevMem W, d_p1, d_p2;
+    // scratch kept by the op across levels (freeing it would synchronise the device)
+    DevMem& W = op->t_W;
+    DevMem& d_p1 = op->t_p1;
+    DevMem& d_p2 = op->t_p2;
     RS_CUDA(W.alloc(sizeof(T) * (size_t)(L.w_off[nb] + 1)));
     std::vector<GemmProb> p1, p2;
     int64_t t1 = 0, t2 = 0;
@@ -505,8 +551,7 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
         RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
                                L.d_E.as<T>(), W.as<T>()));
     }
-    RS_CUDA(cudaStreamSynchronize(st));
-    DevMem d_k32;
+    DevMem& d_k32 = op->t_k32;
     if ((rc = upload(d_k32, to32(L.k), st))) return rc;
     redo = true;
     if (use_sweep(op)) {
@@ -1127,8 +1172,11 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     const cudaStream_t st = (cudaStream_t)stream;
     // candidates (CPQR group scale, CPQR deep variant, sweep group scale): every CPQR pair and
     // every sweep scale appears once
-    const TuneTrial trials[] = {{1.0, 0, 1.0}, {1.0, 1, 0.5}, {0.5, 0, 0.25}, {0.5, 1, 1.0}};
-    constexpr int NTR = 4;
+    // candidates: (CPQR group scale, CPQR deep variant, sweep group scale, CPQR batch budget);
+    // every sweep scale appears, and the CPQR settings are picked per level as one triple
+    const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
+                                {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0}};
+    constexpr int NTR = 6;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);
@@ -1193,9 +1241,10 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
             const std::string k = tune_key("cpqr", esz, S.nb, S.m, S.r);
             tune_set(k + ".gscale", trials[b].cpqr_gscale);
             tune_set(k + ".deep", trials[b].cpqr_deep);
+            tune_set(k + ".batch", trials[b].cpqr_batch);
             const int be = best_of(t_e);
             tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".gscale", trials[be].sweep_gscale);
-            keys += 3;
+            keys += 4;
         }
         const int bf = best_of(t_f);
         tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", trials[bf].sweep_gscale);

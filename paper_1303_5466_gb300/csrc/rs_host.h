@@ -31,31 +31,43 @@ int level_sets(int64_t n, int d, int l, const int64_t* child_k, const int64_t* c
 // Owned device allocation.
 struct DevMem {
     void* p = nullptr;
-    size_t bytes = 0;
+    size_t bytes = 0, cap = 0;
     DevMem() = default;
     DevMem(const DevMem&) = delete;
     DevMem& operator=(const DevMem&) = delete;
-    DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes), cap(o.cap) { o.p = nullptr; o.bytes = o.cap = 0; }
     DevMem& operator=(DevMem&& o) noexcept
     {
         if (this != &o) {
             if (p) cudaFree(p);
-            p = o.p; bytes = o.bytes;
-            o.p = nullptr; o.bytes = 0;
+            p = o.p; bytes = o.bytes; cap = o.cap;
+            o.p = nullptr; o.bytes = o.cap = 0;
         }
         return *this;
     }
     ~DevMem() { if (p) cudaFree(p); }
+    // Grow-only; a growing buffer takes 1.25x the request (cap), so a sequence of slowly
+    // growing requests (the levels of a factorization) reallocates -- and synchronises -- less
+    // often.  `bytes` is the request of the last reallocation.
     cudaError_t alloc(size_t b)
     {
-        if (b <= bytes && p) return cudaSuccess;
+        if (b <= cap && p) return cudaSuccess;
         if (p) cudaFree(p);
         p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&p, b ? b : 16);
-        if (e == cudaSuccess) bytes = b;
+        bytes = cap = 0;
+        const size_t want = bytes_hint(b);
+        cudaError_t e = cudaMalloc(&p, want ? want : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            e = cudaMalloc(&p, b ? b : 16);          // without the headroom
+            if (e == cudaSuccess) bytes = cap = b;
+            return e;
+        }
+        bytes = b;
+        cap = want;
         return e;
     }
+    static size_t bytes_hint(size_t b) { return b < (size_t)1 << 20 ? b : b + b / 4; }
     template <class T> T* as() const { return (T*)p; }
 };
 
@@ -168,6 +180,7 @@ struct TuneTrial {
     double cpqr_gscale = -1.0;
     int cpqr_deep = -1;
     double sweep_gscale = -1.0;
+    double cpqr_batch = -1.0;      // L2 batch budget of the CPQR launches, in units of 96 MB (0: none)
 };
 extern thread_local TuneTrial g_trial;
 
@@ -237,6 +250,8 @@ struct rs_op {
     std::vector<int64_t> input_of_g;
     std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
+    // factor-time scratch reused across levels, released with the op
+    rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32;
     // solve workspace (grown on demand)
     rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_z, s_in, s_out, s_out2;
     int64_t s_nrhs = 0;

@@ -34,7 +34,7 @@ def test_autotune_fills_table_and_keeps_results(rs, tmp_path):
     finally:
         rs.rs_free_tree(tree)
     d = S0.stats()["depth"]
-    assert rep["candidates"] == 4 and rep["keys_set"] >= d
+    assert rep["candidates"] >= 4 and rep["keys_set"] >= d
     assert rep["default_factor_ms"] > 0 and rep["tuned_factor_ms"] > 0
     assert rs.rs_tune_count() > 0 and path.exists()
     S1 = rs.Solver(W.grid_points(n), leaf, a=a, eps=eps)
