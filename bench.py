@@ -33,6 +33,9 @@ WORKLOAD = "laplace_batched"
 # FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26 TFLOP/s, the 1.25
 # TFLOP/s FP64 figure of the profiling recipe (a register-only FMA probe measured 1.203).
 PEAK_FP64_TFLOPS = 1.25
+# DRAM bytes per cpqr_kernel launch measured by ncu at this workload with one launch per level
+# (profiles/cpqr_kernel_dram_laplace_batched.md); to be re-taken whenever the kernel changes
+CPQR_TRAFFIC_BYTES_PER_LAUNCH = 143.8e9
 # FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
@@ -433,7 +436,10 @@ def run_ours(args):
         "flops_factor": last_stats["flops_factor"], "bytes_factors": last_stats["bytes_factors"],
         "root_m": last_stats["root_m"],
         "roofline": {"kernel": dom, "classes": list(KERNEL_CLASSES[dom]), "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
+                     "traffic": CPQR_TRAFFIC_BYTES_PER_LAUNCH if dom == "cpqr_kernel" else None,
+                     "traffic_note": "ncu DRAM read+write bytes per launch, one launch per level (no autotuner "
+                                     "batching), profiles/cpqr_kernel_dram_laplace_batched.md",
                      "launches": nl, "avg_launch_ms": ms / max(nl, 1),
                      "peak_note": "FP64 ALU peak 152 SMs x 4 flop/clk x 2.07 GHz (recipe figure; no FP64 entry "
                                   "in the measured peaks)"},
