@@ -58,6 +58,7 @@ def _args():
                    help="requests of the serving stream measured after the main step (0 = skip)")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     p.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner before the steps")
+    p.add_argument("--no-per-box", action="store_true", help="skip the one-box-per-launch comparison")
     p.add_argument("--k-cut", type=int, default=512,
                    help="also measure the extra compression of Sec. 3 for boxes with k > K (0: skip)")
     return p.parse_args()
@@ -279,6 +280,38 @@ def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
     return out
 
 
+def per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps):
+    """The same FP64 step with every factor and solve kernel launched for one box at a time
+    (opts.per_box): the unbatched GPU form the per-level launches are compared with."""
+    import numpy as np
+    o = P.rs_opts_default()
+    o.per_box = 1
+    f = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    x = torch.empty_like(f)
+    tree = P.rs_build_tree(pts, leaf)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(st)
+    op = P.rs_factor(tree, a=a, eps=eps, opts=o, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    P.rs_solve(op, f, nrhs, x, st)           # captures the solve graph
+    torch.cuda.synchronize()
+    launches0 = P.rs_launch_count()
+    s0, s1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    s0.record(st)
+    P.rs_solve(op, f, nrhs, x, st)
+    s1.record(st)
+    s1.synchronize()
+    factor_ms, solve_ms = e0.elapsed_time(e1), s0.elapsed_time(s1)
+    out = {"factor_ms": factor_ms, "solve_ms": solve_ms,
+           "step_ms": factor_ms + solve_ms, "solve_launches": P.rs_launch_count() - launches0,
+           "residual_fp64": float(P.rs_residual(op, x, f, nrhs, st).max())}
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+    return out
+
+
 def compressed_measure(P, torch, n, leaf, pts, a, F, nrhs, st, eps, k_cut, x_dense, reps=5):
     """The same workload with the extra compression of Sec. 3 (boxes with k > k_cut): factor
     time (compression included), solve time, stored bytes against the dense blocks they replace,
@@ -472,9 +505,14 @@ def run_ours(args):
                                                x_dev.cpu().numpy().T.copy())
         out["compressed"]["dense_solve_ms"] = solve_ms
         out["compressed"]["dense_bytes_factors"] = last_stats["bytes_factors"]
+    if not args.no_per_box:
+        out["per_box_fp64"] = per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps)
+        out["per_box_fp64"]["batched_step_speedup"] = out["per_box_fp64"]["step_ms"] / (factor_ms + solve_ms)
     if not args.no_mixed:
         mx = mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st)
         mx["step_speedup_vs_fp64"] = (factor_ms + solve_ms) / (mx["factor_ms"] + mx["refined_solve_ms"])
+        if "per_box_fp64" in out:
+            mx["step_speedup_vs_per_box_fp64"] = out["per_box_fp64"]["step_ms"] / (mx["factor_ms"] + mx["refined_solve_ms"])
         out["mixed"] = mx
     if args.serving_requests > 0:
         out["serving"] = serving_measure(P, torch, args.serving_requests)

@@ -86,6 +86,10 @@ typedef struct {
                                     graph of the whole inverse apply, captured once per nrhs
                                     (inputs staged through library buffers); 0: launch the
                                     kernels one by one                                [1]    */
+    int per_box;                 /* 1: launch every factor and solve kernel for one box at a
+                                    time (each box gets the whole GPU), the unbatched form
+                                    that the per-level launches are measured against; same
+                                    arithmetic up to rounding order                   [0]    */
     int spd_inverse;             /* 1: invert F, E and the root of a real symmetric kernel
                                     (RS_LAPLACE) by the symmetric sweep without pivoting
                                     (half the flops of Gauss-Jordan); a level whose pivots

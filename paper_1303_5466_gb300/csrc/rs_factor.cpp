@@ -193,6 +193,19 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
     double work = 0.0;
     for (int b = 0; b < nb; ++b) work += 2.0 * (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
     ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb], level);
+    if (op->opts.per_box) {                 // one matrix per launch, each with the whole GPU
+        for (int b = 0; b < nb; ++b) {
+            const int mb = (int)sizes[b];
+            if (mb <= 0) continue;
+            const int Gb = choose_group(1, mb * 32 / gj_panel_width(), [&](int) { return gj_max_ctas<T>(mb, 1); });
+            RS_CUDA(launch_gj_inverse<T>(st, 1, Gb, dm.as<int32_t>() + b, doff.as<int64_t>() + b, A,
+                                         op->d_ipiv.as<int32_t>(), d_ipoff.as<int64_t>() + b,
+                                         op->d_pivrow.as<int>() + 2 * (int64_t)gj_panel_width() * b,
+                                         op->d_bar.as<unsigned int>() + b, op->d_status.as<int>(),
+                                         (long long)op->opts.spin_limit, mb));
+        }
+        return check_status(op, st);
+    }
     RS_CUDA(launch_gj_inverse<T>(st, nb, G, dm.as<int32_t>(), doff.as<int64_t>(), A, op->d_ipiv.as<int32_t>(),
                               d_ipoff.as<int64_t>(), op->d_pivrow.as<int>(), op->d_bar.as<unsigned int>(),
                               op->d_status.as<int>(), (long long)op->opts.spin_limit, max_m));
@@ -244,7 +257,18 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
             cta_off = proportional_groups(nb * G, wgt, capb);
             if ((rc = upload(d_cta, cta_off, st))) return rc;
         }
-        {
+        if (op->opts.per_box) {             // one matrix per launch, each with the whole GPU
+            ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb], level);
+            for (int b = 0; b < nb; ++b) {
+                const int mb = (int)sizes[b];
+                if (mb <= 0) continue;
+                const int Gb = choose_group(1, mb * 16 / NB, [&](int) { return cap; });
+                RS_CUDA(launch_sweep_inverse<T>(st, 1, Gb, nullptr, Gb, dm.as<int32_t>() + b, doff.as<int64_t>() + b,
+                                                A, op->d_pb.as<T>(), d_pboff.as<int64_t>() + b,
+                                                op->d_bar.as<unsigned int>() + b, op->d_status.as<int>(),
+                                                (long long)op->opts.spin_limit, mb));
+            }
+        } else {
             ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb], level);
             RS_CUDA(launch_sweep_inverse<T>(st, nb, G, cta_off.empty() ? nullptr : d_cta.as<int32_t>(),
                                             cta_off.empty() ? nb * G : cta_off[nb], dm.as<int32_t>(),
@@ -307,9 +331,14 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     RS_CUDA(w.Y.alloc(sizeof(T) * (size_t)(y_off[nb] + 1)));
     {
     ProfScope ps(op, RS_PROF_ASSEMBLE_Y, st, (double)y_off[nb], sizeof(T) * (double)y_off[nb]);
-    RS_CUDA(launch_assemble_Y<T>(st, nb, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(), w.near.as<int32_t>(),
-                                 w.near_off.as<int64_t>(), w.geo.as<double>(), op->d_ucirc.as<double>(), P,
-                                 w.y_off.as<int64_t>(), w.Y.as<T>(), op->K, (int)max_entries));
+    const bool pb = op->opts.per_box != 0;
+    for (int b0 = 0; b0 < nb; b0 += pb ? 1 : nb) {
+        const int cnt = pb ? 1 : nb;
+        RS_CUDA(launch_assemble_Y<T>(st, cnt, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>() + b0,
+                                     w.near.as<int32_t>(), w.near_off.as<int64_t>() + b0, w.geo.as<double>() + 3 * b0,
+                                     op->d_ucirc.as<double>(), P, w.y_off.as<int64_t>() + b0, w.Y.as<T>(), op->K,
+                                     pb ? (int)(L.r[b0] * L.m[b0]) : (int)max_entries));
+    }
     }
     const int64_t sum_m = L.act_off[nb];
     RS_CUDA(w.piv.alloc(sizeof(int32_t) * (sum_m + 1)));
@@ -328,7 +357,9 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     const double batch_bytes =
         96.0 * (1 << 20) * (g_trial.cpqr_batch >= 0.0 ? g_trial.cpqr_batch : tune_get(tkey + ".batch", 0.0));
     std::vector<int> b_start(1, 0);
-    if (batch_bytes > 0.0) {
+    if (op->opts.per_box) {
+        for (int b = 1; b < nb; ++b) b_start.push_back(b);
+    } else if (batch_bytes > 0.0) {
         double tot = 0.0;
         for (int b = 0; b < nb; ++b) tot += (double)sizeof(T) * (double)L.r[b] * (double)L.m[b];
         const int nbat = std::max(1, std::min(nb, (int)std::ceil(tot / batch_bytes)));
@@ -458,10 +489,15 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     RS_CUDA(L.d_T.alloc(sizeof(T) * (size_t)(L.t_off[nb] + 1)));
     {
     ProfScope ps(op, RS_PROF_ID_T, st, t_work, sizeof(T) * (double)L.t_off[nb]);
-    RS_CUDA(launch_id_T<T>(st, nb, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(), w.nn.as<int32_t>(), P,
-                        w.y_off.as<int64_t>(), w.Y.as<T>(), w.piv.as<int32_t>(), w.diag.as<T>(),
-                        w.skpos.as<int32_t>(), w.rscol.as<int32_t>(), L.d_t_off.as<int64_t>(), L.d_T.as<T>(),
-                        max_res, L.max_k));
+    const bool pb = op->opts.per_box != 0;
+    for (int b0 = 0; b0 < nb; b0 += pb ? 1 : nb) {
+        const int cnt = pb ? 1 : nb;
+        RS_CUDA(launch_id_T<T>(st, cnt, L.d_act_off.as<int64_t>() + b0, L.d_k.as<int32_t>() + b0,
+                               w.nn.as<int32_t>() + b0, P, w.y_off.as<int64_t>() + b0, w.Y.as<T>(),
+                               w.piv.as<int32_t>(), w.diag.as<T>(), w.skpos.as<int32_t>(), w.rscol.as<int32_t>(),
+                               L.d_t_off.as<int64_t>() + b0, L.d_T.as<T>(),
+                               pb ? (int)(L.m[b0] - L.k[b0]) : max_res, pb ? (int)L.k[b0] : L.max_k));
+    }
     }
     // no synchronisation: the next level's CPQR status check covers this launch too
     RS_CUDA(cudaGetLastError());
@@ -487,11 +523,16 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     const bool leaf = (L.l == op->d);
     auto assemble = [&]() -> int {
         ProfScope ps(op, RS_PROF_ASSEMBLE_F, st, (double)L.phi_off[nb], sizeof(T) * (double)L.phi_off[nb]);
-        RS_CUDA(launch_assemble_F<T>(st, nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>(),
-                                     L.d_perm.as<int32_t>(), op->d_a.as<double>(), L.d_phi_off.as<int64_t>(),
-                                     L.d_Phi.as<T>(), child ? child->d_k.as<int32_t>() : nullptr,
-                                     child ? child->d_e_off.as<int64_t>() : nullptr,
-                                     child ? child->d_E.as<T>() : nullptr, op->K, L.max_m));
+        const bool pb = op->opts.per_box != 0;
+        for (int b0 = 0; b0 < nb; b0 += pb ? 1 : nb) {
+            RS_CUDA(launch_assemble_F<T>(st, pb ? 1 : nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>() + b0,
+                                         L.d_perm.as<int32_t>(), op->d_a.as<double>(),
+                                         L.d_phi_off.as<int64_t>() + b0, L.d_Phi.as<T>(),
+                                         child ? child->d_k.as<int32_t>() + 2 * b0 : nullptr,
+                                         child ? child->d_e_off.as<int64_t>() + 2 * b0 : nullptr,
+                                         child ? child->d_E.as<T>() : nullptr, op->K,
+                                         pb ? (int)L.m[b0] : L.max_m));
+        }
         return RS_OK;
     };
     if ((rc = assemble())) return rc;
@@ -546,10 +587,24 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
         }
         ProfScope ps(op, RS_PROF_GEMM_E, st, work,
                      sizeof(T) * (double)(L.phi_off[nb] + 2 * L.w_off[nb] + L.e_off[nb]));
-        RS_CUDA(launch_gemm<T>(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<T>(), L.d_T.as<T>(),
-                               W.as<T>(), L.d_Phi.as<T>()));
-        RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
-                               L.d_E.as<T>(), W.as<T>()));
+        if (op->opts.per_box) {             // one box per launch: descriptors starting at tile 0
+            std::vector<GemmProb> q1 = p1, q2 = p2;
+            for (auto& g : q1) g.tile0 = 0;
+            for (auto& g : q2) g.tile0 = 0;
+            if ((rc = upload(op->t_q1, q1, st))) return rc;
+            if ((rc = upload(op->t_q2, q2, st))) return rc;
+            for (size_t i = 0; i < q1.size(); ++i) {
+                RS_CUDA(launch_gemm<T>(st, op->t_q1.as<GemmProb>() + i, 1, (int64_t)q1[i].tiles_m * q1[i].tiles_n,
+                                       L.d_Phi.as<T>(), L.d_T.as<T>(), W.as<T>(), L.d_Phi.as<T>()));
+                RS_CUDA(launch_gemm<T>(st, op->t_q2.as<GemmProb>() + i, 1, (int64_t)q2[i].tiles_m * q2[i].tiles_n,
+                                       L.d_T.as<T>(), W.as<T>(), L.d_E.as<T>(), W.as<T>()));
+            }
+        } else {
+            RS_CUDA(launch_gemm<T>(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<T>(), L.d_T.as<T>(),
+                                   W.as<T>(), L.d_Phi.as<T>()));
+            RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
+                                   L.d_E.as<T>(), W.as<T>()));
+        }
     }
     DevMem& d_k32 = op->t_k32;
     if ((rc = upload(d_k32, to32(L.k), st))) return rc;
@@ -582,7 +637,8 @@ void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk
 // Upload a descriptor set, with blocks of rb output entries (matvec_rows_per_block of its
 // 64-entry block count: small sets get smaller blocks, so the launch still fills the GPU).
 int upload_mv(DevMem& d, DevMem& db, int& n, int64_t& nblk, int& rb, std::vector<MatvecProb>& v,
-              std::vector<int64_t>& blk, int64_t total, cudaStream_t st, double* work = nullptr)
+              std::vector<int64_t>& blk, int64_t total, cudaStream_t st, double* work = nullptr,
+              std::vector<int64_t>* keep = nullptr)
 {
     n = (int)v.size();
     rb = matvec_rows_per_block(total);
@@ -597,6 +653,10 @@ int upload_mv(DevMem& d, DevMem& db, int& n, int64_t& nblk, int& rb, std::vector
     }
     int rc;
     if ((rc = upload(d, v, st))) return rc;
+    if (keep) {
+        *keep = blk;
+        keep->push_back(nblk);
+    }
     return upload(db, blk, st);
 }
 
@@ -625,7 +685,8 @@ int solve_plan(rs_op* op, Level& L, const Level* child, cudaStream_t st)
         std::vector<int64_t> blk;
         int64_t n = 0;
         add_mv(v, blk, n, (int)L.m[0], (int)L.m[0], (int)L.m[0], 0, 0, 0, 0, 1.0, 0.0);
-        return upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, v, blk, n, st, &L.mvw_phi);
+        return upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, v, blk, n, st, &L.mvw_phi,
+                         &L.h_blk_phi);
     }
     std::vector<int64_t> isk(L.sum_k);
     for (int b = 0; b < nb; ++b)
@@ -643,11 +704,14 @@ int solve_plan(rs_op* op, Level& L, const Level* child, cudaStream_t st)
         if (m - k > 0) add_mv(vTt, bTt, nTt, k, m - k, k, 1, L.t_off[b], L.k_off[b], L.act_off[b] + k, 1.0, 0.0);
     }
     if ((rc = upload_mv(L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, vphi, bphi, nphi, st,
-                        &L.mvw_phi)))
+                        &L.mvw_phi, &L.h_blk_phi)))
         return rc;
-    if ((rc = upload_mv(L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.rb_T, vT, bT, nT, st, &L.mvw_T))) return rc;
-    if ((rc = upload_mv(L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, vE, bE, nE, st, &L.mvw_E))) return rc;
-    return upload_mv(L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.rb_Tt, vTt, bTt, nTt, st, &L.mvw_Tt);
+    if ((rc = upload_mv(L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.rb_T, vT, bT, nT, st, &L.mvw_T, &L.h_blk_T)))
+        return rc;
+    if ((rc = upload_mv(L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, vE, bE, nE, st, &L.mvw_E, &L.h_blk_E)))
+        return rc;
+    return upload_mv(L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.rb_Tt, vTt, bTt, nTt, st, &L.mvw_Tt,
+                     &L.h_blk_Tt);
 }
 
 void compute_stats(rs_op* op)
@@ -828,6 +892,8 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     }
     if ((rc = upload(op->d_ucirc, uc, st))) return rc;
     RS_CUDA(op->d_status.alloc(sizeof(int)));
+    RS_CUDA(op->d_zero.alloc(sizeof(int64_t)));
+    RS_CUDA(cudaMemsetAsync(op->d_zero.p, 0, sizeof(int64_t), st));
     RS_CUDA(cudaMemsetAsync(op->d_status.p, 0, sizeof(int), st));
     op->lev.resize(op->d + 1);
     for (int l = 0; l <= op->d; ++l) {
@@ -894,6 +960,19 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
     const int nr = (int)nrhs;
     const double esz = (double)sizeof(T);
     int rc;
+    // one descriptor set: one launch, or (opts.per_box) one launch per box
+    auto mv = [&](const Level& L, const DevMem& probs, const DevMem& blk0, int np, int64_t nblk, int rb,
+                  const std::vector<int64_t>& hblk, const T* A, const T* x, T* y) -> int {
+        if (!op->opts.per_box || np <= 1) {
+            RS_CUDA(launch_matvec<T>(st, probs.as<MatvecProb>(), blk0.as<int64_t>(), np, nblk, A, x, y, nr, rb));
+            return RS_OK;
+        }
+        (void)L;
+        for (int i = 0; i < np; ++i)
+            RS_CUDA(launch_matvec<T>(st, probs.as<MatvecProb>() + i, op->d_zero.as<int64_t>(), 1, hblk[i + 1] - hblk[i],
+                                     A, x, y, nr, rb));
+        return RS_OK;
+    };
     // compressed boxes (Sec. 3): their part of an apply, from `in` to `out`
     auto run_cprog = [&](const Program& p, const T* in, T* out) -> int {
         if (p.st.empty()) return RS_OK;
@@ -908,25 +987,25 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         if (l == d) RS_CUDA(launch_gather_cm<IO, T>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), fd, N, U, nr));
         else RS_CUDA(launch_gather_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, esz * L.mvw_phi);
-        RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
-                              L.d_Phi.as<T>(), U, wl, nr, L.rb_phi)); }
+        if ((rc = mv(L, L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, L.h_blk_phi,
+                     L.d_Phi.as<T>(), U, wl))) return rc; }
         if ((rc = run_cprog(L.p_phi, U, wl))) return rc;
         RS_CUDA(launch_gather_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), wl, Tt, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_T * (double)nrhs, esz * L.mvw_T);
-        RS_CUDA(launch_matvec<T>(st, L.d_mv_T.as<MatvecProb>(), L.d_mv_T_blk.as<int64_t>(), L.n_mv_T, L.b_mv_T,
-                              L.d_T.as<T>(), wl, Tt, nr, L.rb_T)); }
+        if ((rc = mv(L, L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.rb_T, L.h_blk_T,
+                     L.d_T.as<T>(), wl, Tt))) return rc; }
         if ((rc = run_cprog(L.p_T, wl, Tt))) return rc;
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, esz * L.mvw_E);
-        RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
-                              L.d_E.as<T>(), Tt, gl, nr, L.rb_E)); }
+        if ((rc = mv(L, L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, L.h_blk_E,
+                     L.d_E.as<T>(), Tt, gl))) return rc; }
         if ((rc = run_cprog(L.p_E, Tt, gl))) return rc;
     }
     // root
     {
         Level& R = op->lev[0];
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * R.mvw_phi * (double)nrhs, esz * R.mvw_phi);
-        RS_CUDA(launch_matvec<T>(st, R.d_mv_phi.as<MatvecProb>(), R.d_mv_phi_blk.as<int64_t>(), R.n_mv_phi, R.b_mv_phi,
-                              R.d_Phi.as<T>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr, R.rb_phi)); }
+        if ((rc = mv(R, R.d_mv_phi, R.d_mv_phi_blk, R.n_mv_phi, R.b_mv_phi, R.rb_phi, R.h_blk_phi,
+                     R.d_Phi.as<T>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs))) return rc; }
     }
     // downward pass
     for (int l = 1; l <= d; ++l) {
@@ -936,18 +1015,18 @@ int solve_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typ
         T* pl = Ph + goff[l] * nrhs;
         RS_CUDA(cudaMemcpyAsync(Tt, gl, sizeof(T) * (size_t)(L.sum_k * nrhs), cudaMemcpyDeviceToDevice, st));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_E * (double)nrhs, esz * L.mvw_E);
-        RS_CUDA(launch_matvec<T>(st, L.d_mv_E.as<MatvecProb>(), L.d_mv_E_blk.as<int64_t>(), L.n_mv_E, L.b_mv_E,
-                              L.d_E.as<T>(), pl, Tt, nr, L.rb_E)); }   // beta = 0: Tt = E phi
+        if ((rc = mv(L, L.d_mv_E, L.d_mv_E_blk, L.n_mv_E, L.b_mv_E, L.rb_E, L.h_blk_E,
+                     L.d_E.as<T>(), pl, Tt))) return rc; }   // beta = 0: Tt = E phi
         if ((rc = run_cprog(L.p_E, pl, Tt))) return rc;
         RS_CUDA(launch_axpby<T>(st, L.sum_k * nrhs, (T)-1, gl, (T)1, Tt));   // Tt = E phi - g
         RS_CUDA(launch_scatter_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), Tt, U, nr));
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_Tt * (double)nrhs, esz * L.mvw_Tt);
-        RS_CUDA(launch_matvec<T>(st, L.d_mv_Tt.as<MatvecProb>(), L.d_mv_Tt_blk.as<int64_t>(), L.n_mv_Tt, L.b_mv_Tt,
-                              L.d_T.as<T>(), Tt, U, nr, L.rb_Tt)); }
+        if ((rc = mv(L, L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.rb_Tt, L.h_blk_Tt,
+                     L.d_T.as<T>(), Tt, U))) return rc; }
         if ((rc = run_cprog(L.p_Tt, Tt, U))) return rc;
         { ProfScope ps(op, RS_PROF_SOLVE, st, 2.0 * L.mvw_phi * (double)nrhs, esz * L.mvw_phi);
-        RS_CUDA(launch_matvec<T>(st, L.d_mv_phi.as<MatvecProb>(), L.d_mv_phi_blk.as<int64_t>(), L.n_mv_phi, L.b_mv_phi,
-                              L.d_Phi.as<T>(), U, XO, nr, L.rb_phi)); }
+        if ((rc = mv(L, L.d_mv_phi, L.d_mv_phi_blk, L.n_mv_phi, L.b_mv_phi, L.rb_phi, L.h_blk_phi,
+                     L.d_Phi.as<T>(), U, XO))) return rc; }
         if ((rc = run_cprog(L.p_phi, U, XO))) return rc;
         RS_CUDA(launch_axpby<T>(st, L.sum_m * nrhs, (T)1, wl, (T)1, XO));   // x' = w + Phi v
         if (l == d) RS_CUDA(launch_scatter_cm<T, IO>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), XO, N, xd, nr));

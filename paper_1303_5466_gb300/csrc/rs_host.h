@@ -138,6 +138,7 @@ struct Level {
     DevMem d_mv_phi, d_mv_phi_blk, d_mv_T, d_mv_T_blk, d_mv_E, d_mv_E_blk, d_mv_Tt, d_mv_Tt_blk;
     int n_mv_phi = 0, n_mv_T = 0, n_mv_E = 0, n_mv_Tt = 0;
     int rb_phi = 64, rb_T = 64, rb_E = 64, rb_Tt = 64;     // output entries per block
+    std::vector<int64_t> h_blk_phi, h_blk_T, h_blk_E, h_blk_Tt;  // first block of each problem, then the total
     int64_t b_mv_phi = 0, b_mv_T = 0, b_mv_E = 0, b_mv_Tt = 0;
     int64_t sum_m = 0, sum_k = 0;
     double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set
@@ -251,7 +252,8 @@ struct rs_op {
     std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // factor-time scratch reused across levels, released with the op
-    rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32;
+    rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2;
+    rs::DevMem d_zero;                // one int64 zero: the first block of a one-problem launch
     // solve workspace (grown on demand)
     rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_z, s_in, s_out, s_out2;
     int64_t s_nrhs = 0;
