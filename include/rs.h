@@ -96,6 +96,13 @@ typedef struct {
                                     show a block that is not positive definite to working
                                     accuracy is redone with pivoted Gauss-Jordan
                                     (rs_stats.spd_fallbacks).  0: always pivoted GJ  [1]    */
+    int cpqr_variant;            /* form of the column-pivoted QR (Eq. 2.1) on every level:
+                                    0 = two passes over the open columns per step, 4 rows
+                                    per lane in flight; 1 = the same with 8; 2 = look-ahead
+                                    (one pass per step: the update of step s fused with the
+                                    dot products of step s+1); -1 = the autotuner's table
+                                    (rs_autotune), else 0 or 1 by occupancy. Same result up
+                                    to rounding order                                [-1]   */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);

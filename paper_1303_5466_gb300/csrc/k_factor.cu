@@ -425,9 +425,14 @@ template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, int deep,
                         const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y, double eps,
                         int32_t* kout, int32_t* piv, T* diag, unsigned int* bar, unsigned long long* keys,
-                        int* status, long long spin_limit, int max_r, int max_m, double* nrm, double* ref)
+                        int* status, long long spin_limit, int max_r, int max_m, double* nrm, double* ref, T* wv)
 {
     if (nb <= 0) return cudaSuccess;
+    if (deep == 2) {
+        if (!wv) return cudaErrorInvalidValue;
+        return launch_cpqr_la<T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
+                                 keys, status, spin_limit, max_r, max_m, nrm, ref, wv);
+    }
     const size_t shm = cpqr_shm<T>(max_r, max_m, G);
     if (deep)
         return launch_cpqr_u<8, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
@@ -440,6 +445,7 @@ template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G, int deep)
 {
     constexpr int NT = 256;
+    if (deep == 2) return cpqr_la_max_ctas<T>(max_r, max_m);
     const size_t shm = cpqr_shm<T>(max_r, max_m, G);
     if (shm > 227 * 1024) return 0;
     const void* fn = deep ? (const void*)cpqr_kernel<NT, 8, T> : (const void*)cpqr_kernel<NT, 4, T>;
@@ -588,7 +594,7 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
     template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int32_t*, int, int, const int64_t*,            \
                                         const int32_t*, int, const int64_t*, T*, double, int32_t*, int32_t*, T*,    \
                                         unsigned int*, unsigned long long*, int*, long long, int, int, double*,     \
-                                        double*);                                                                   \
+                                        double*, T*);                                                               \
     template int cpqr_max_ctas<T>(int, int, int, int);                                                               \
     template cudaError_t launch_id_T<T>(cudaStream_t, int, const int64_t*, const int32_t*, const int32_t*, int,      \
                                         const int64_t*, const T*, const int32_t*, const T*, const int32_t*,         \

@@ -353,7 +353,9 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     // at every step), at the price of fewer CTAs per box.  Untuned: one launch per level.
     const std::string tkey = tune_key("cpqr", (int)sizeof(T), nb, L.max_m, L.max_r);
     const double gs = g_trial.cpqr_gscale >= 0.0 ? g_trial.cpqr_gscale : tune_get(tkey + ".gscale", 1.0);
-    const int deep_set = g_trial.cpqr_deep >= 0 ? g_trial.cpqr_deep : (int)tune_get(tkey + ".deep", -1.0);
+    const int deep_set = g_trial.cpqr_deep >= 0         ? g_trial.cpqr_deep
+                         : op->opts.cpqr_variant >= 0 ? op->opts.cpqr_variant
+                                                      : (int)tune_get(tkey + ".deep", -1.0);
     const double batch_bytes =
         96.0 * (1 << 20) * (g_trial.cpqr_batch >= 0.0 ? g_trial.cpqr_batch : tune_get(tkey + ".batch", 0.0));
     std::vector<int> b_start(1, 0);
@@ -386,7 +388,9 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
             B.max_m = std::max<int>(B.max_m, (int)L.m[b]);
         }
         // the open columns are re-split every step, so a group may take one CTA per 16 columns
-        int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g); });
+        // (sized for the co-residency of the variant when one is set)
+        const int var = deep_set >= 0 ? deep_set : 0;
+        int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g, var); });
         if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
         B.G = G;
         // The boxes of a batch differ in work (boundary boxes have fewer near rows, ranks
@@ -410,7 +414,7 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
         // few CTAs per SM: each warp keeps twice the rows in flight
         B.deep = (G > 1 && B.ctas <= 2 * sms) ? 1 : 0;
         if (deep_set >= 0) B.deep = deep_set;
-        if (B.deep && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, 1)) B.deep = 0;   // must stay co-resident
+        if (B.deep && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, B.deep)) B.deep = 0;   // must stay co-resident
         max_keys = std::max(max_keys, (size_t)(2 * B.ctas));
         bats.push_back(B);
     }
@@ -419,7 +423,9 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
         if ((rc2 = upload(w.cta_off, cta_all, st))) return rc2;
     }
     RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * max_keys));
-    RS_CUDA(w.norms.alloc(sizeof(double) * 2 * (size_t)(sum_m + 1)));
+    // squared norms, their references, and (look-ahead variant) the dot products v^H y_j
+    const size_t nrm_dbl = 2 * (size_t)(sum_m + 1), wv_dbl = ((size_t)(sum_m + 1) * sizeof(T) + 7) / 8;
+    RS_CUDA(w.norms.alloc(sizeof(double) * (nrm_dbl + wv_dbl)));
     {
         // the rank is known only afterwards: the work is added once k is read back
         ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0, L.l);
@@ -431,7 +437,7 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
                                    w.piv.as<int32_t>(), w.diag.as<T>(), op->d_bar.as<unsigned int>() + B.b0,
                                    w.keys.as<unsigned long long>(), op->d_status.as<int>(),
                                    (long long)op->opts.spin_limit, B.max_r, B.max_m, w.norms.as<double>(),
-                                   w.norms.as<double>() + sum_m + 1));
+                                   w.norms.as<double>() + sum_m + 1, (T*)(w.norms.as<double>() + nrm_dbl)));
         }
     }
     if ((rc = check_status(op, st))) return rc;
@@ -848,6 +854,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
+    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 2) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 2");
     const double h = 1.0 / (double)op->n;
     op->K.n = (int)op->n;
     op->K.h = h;
@@ -1249,13 +1256,13 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     o.profile = 1;
     o.k_cut = 0;
     const cudaStream_t st = (cudaStream_t)stream;
-    // candidates (CPQR group scale, CPQR deep variant, sweep group scale): every CPQR pair and
-    // every sweep scale appears once
-    // candidates: (CPQR group scale, CPQR deep variant, sweep group scale, CPQR batch budget);
-    // every sweep scale appears, and the CPQR settings are picked per level as one triple
+    // candidates: (CPQR group scale, CPQR variant (4 rows, 8 rows, look-ahead), sweep group
+    // scale, CPQR batch budget); every sweep scale appears, and the CPQR settings are picked
+    // per level as one triple
     const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
-                                {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0}};
-    constexpr int NTR = 6;
+                                {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0},
+                                {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}};
+    constexpr int NTR = 8;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);

@@ -94,17 +94,26 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 // Y is overwritten by the factorisation (rows < k hold R).
 // Group sizes: G CTAs for every box, or (cta_off != NULL, device, nb + 1 entries) box b takes
 // CTAs cta_off[b] .. cta_off[b+1], ctas = cta_off[nb] in all.
-// deep: eight rows per lane in flight instead of four (more registers; for launches with few
-// CTAs per SM, where each warp must hide more memory latency by itself).
+// deep (the variant): 0 = four rows per lane in flight; 1 = eight (more registers; for
+// launches with few CTAs per SM, where each warp must hide more memory latency by itself);
+// 2 = the look-ahead form (k_cpqr_la.cu: one read and one write of each open column per step
+// instead of two reads and a write), which needs wv, a work array of act_off[nb] entries.
 template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, int deep,
                         const int64_t* act_off, const int32_t* nnear, int P,
                         const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
-                        int max_m, double* nrm, double* ref);
-// Largest grid of the cpqr kernel (deep or not) that can be co-resident for these sizes.
+                        int max_m, double* nrm, double* ref, T* wv = nullptr);
+// Largest grid of the cpqr kernel (of the given variant) that can be co-resident for these sizes.
 template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G, int deep = 0);
+template <class T>
+cudaError_t launch_cpqr_la(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int64_t* act_off,
+                           const int32_t* nnear, int P, const int64_t* y_off, T* Y, double eps, int32_t* kout,
+                           int32_t* piv, T* diag, unsigned int* bar, unsigned long long* keys, int* status,
+                           long long spin_limit, int max_r, int max_m, double* nrm, double* ref, T* wv);
+template <class T>
+int cpqr_la_max_ctas(int max_r, int max_m);
 
 // T = R11^{-1} R12 for every box, written column-major (k x (m-k)) at t_off[b], rows by
 // sorted skeleton position (skpos[pivot position]) and columns by residual rank.

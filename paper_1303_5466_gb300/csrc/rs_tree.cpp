@@ -142,6 +142,7 @@ void rs_opts_default(rs_opts* o)
     o->profile = 0;
     o->hss_leaf = 64;
     o->spd_inverse = 1;
+    o->cpqr_variant = -1;
     o->solve_graph = 1;
     o->per_box = 0;
     o->hss_eps = 0.0;
