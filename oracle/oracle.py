@@ -39,7 +39,7 @@ class _Opts(C.Structure):
     _fields_ = [("kind", C.c_int), ("kappa", C.c_double), ("proxy_points", C.c_int),
                 ("proxy_radius_factor", C.c_double), ("near_all", C.c_int),
                 ("threads", C.c_int), ("max_levels", C.c_int), ("k_cut", C.c_int), ("hss_leaf", C.c_int),
-                ("hss_eps", C.c_double)]
+                ("hss_eps", C.c_double), ("ti", C.c_int)]
 
 
 def load(path):
@@ -220,13 +220,14 @@ class Factorization:
 
     def __init__(self, n, leaf, eps, a=None, b=None, kind=LAPLACE, kappa=0.0, proxy_points=64,
                  proxy_radius_factor=1.5, near_all=False, threads=0, max_levels=0, k_cut=0, hss_leaf=64,
-                 hss_eps=0.0):
+                 hss_eps=0.0, ti=False):
         L = self._L = lib()
         o = _Opts()
         L.ro_opts_default(C.byref(o))
         o.kind, o.kappa, o.proxy_points = kind, kappa, proxy_points
         o.proxy_radius_factor, o.near_all, o.threads = proxy_radius_factor, int(near_all), threads
         o.max_levels, o.k_cut, o.hss_leaf, o.hss_eps = max_levels, k_cut, hss_leaf, hss_eps
+        o.ti = int(ti)
         self.n, self.leaf, self.eps, self.kind, self.kappa = n, leaf, eps, kind, kappa
         N = n * n
         self.a, self.b = _f64(a, N), _f64(b, N)

@@ -242,6 +242,19 @@ static double complex proxy_entry_z(const ro_op* op, double zx, double zy, int64
     return k * op->s[g];
 }
 
+/* Translation-invariant mode: the entry between a lattice point outside the grid at (x, y)
+ * (a translate of a grid point) and grid point g.  It is the off-diagonal formula; in the
+ * Helmholtz form the outside point takes the constant scaling s of the grid. */
+static double outside_entry_d(const ro_op* op, double x, double y, int64_t g)
+{
+    return proxy_entry_d(op, x, y, g);
+}
+
+static double complex outside_entry_z(const ro_op* op, double x, double y, int64_t g)
+{
+    return op->s[0] * proxy_entry_z(op, x, y, g);
+}
+
 /* Pivot key of the column-pivoted QR: the squared norm with its 40 low mantissa bits
  * cleared (a monotone map of non-negative doubles onto a grid of relative step 2^-12). */
 static uint64_t pivot_key(double v)
@@ -362,6 +375,7 @@ void ro_opts_default(ro_opts* o)
     o->k_cut = 0;
     o->hss_leaf = 64;
     o->hss_eps = 0.0;
+    o->ti = 0;
 }
 
 int ro_id(int cplx, const double* Y, int r, int m, double eps, int* k_out, int* perm, double* T)
@@ -448,6 +462,11 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
     if (o.proxy_points < 0) return -1;
     if (o.k_cut > 0 && (o.hss_leaf < 1 || !(o.hss_eps >= 0.0))) return -1;
     int64_t N = (int64_t)n * n;
+    if (o.ti) {                  /* translation invariance needs constant a and b */
+        if (o.k_cut > 0 || o.near_all) return -1;
+        for (int64_t g = 1; g < N; ++g)
+            if ((a && a[g] != a[0]) || (b && b[g] != b[0])) return -1;
+    }
     ro_op* op = (ro_op*)calloc(1, sizeof(ro_op));
     op->n = n; op->leaf = leaf_side; op->d = 2 * L; op->h = 1.0 / n; op->eps = eps; op->opts = o;
 #ifdef _OPENMP
@@ -485,6 +504,10 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
         level_bookkeeping(op, l);
         int nb = 1 << l;
         int err = 0;
+        if (o.ti) {
+            rc = (o.kind == 0) ? factor_ti_level_d(op, l) : factor_ti_level_z(op, l);
+            continue;
+        }
         #pragma omp parallel for schedule(dynamic) num_threads(op->nthreads)
         for (int j = 0; j < nb; ++j) {
             int e = (o.kind == 0) ? factor_box_d(op, l, j) : factor_box_z(op, l, j);
@@ -586,7 +609,7 @@ int ro_box_skel(const ro_op* op, int l, int j, int64_t* out)
 int ro_box_near(const ro_op* op, int l, int j, int64_t* out)
 {
     const ro_box* B = getbox(op, l, j);
-    if (!B) return -1;
+    if (!B || !B->near) return -1;           /* translation-invariant mode: no per-box list */
     memcpy(out, B->near, sizeof(int64_t) * (size_t)B->nnear);
     return 0;
 }

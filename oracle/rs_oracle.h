@@ -47,6 +47,10 @@ typedef struct {
                                     ro_solve uses these forms for those boxes              */
     int hss_leaf;                /* largest leaf run of the HSS1D trees                    */
     double hss_eps;              /* ID tolerance of that compression (0: eps)              */
+    int ti;                      /* 1: translation-invariant mode (a and b constant): one
+                                    ID and one set of blocks per level, taken on box 0
+                                    with all eight neighbours present (Sec. 5, one set of
+                                    matrices per level) and copied to every box           */
 } ro_opts;
 
 typedef struct ro_hss ro_hss;
