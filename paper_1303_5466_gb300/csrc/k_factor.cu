@@ -34,13 +34,16 @@ __device__ __forceinline__ S hank_row(const KernelK& K, double r)
     }
 }
 
+// Helmholtz scaling s_g of the symmetric form (per grid point, or the constant s0)
+__device__ __forceinline__ double kscale(const KernelK& K, int g) { return K.s ? K.s[g] : K.s0; }
+
 template <class S>
 __device__ __forceinline__ S kentry(const KernelK& K, int g, int gp)
 {
     if (K.tab) {
         const int d1 = g % K.n - gp % K.n, d2 = g / K.n - gp / K.n;
         const S t = ((const S*)K.tab)[(d1 + K.n - 1) + (int64_t)(2 * K.n - 1) * (d2 + K.n - 1)];
-        if constexpr (is_cplx<S>::value) return rscale<S>(K.s[g] * K.s[gp], t);
+        if constexpr (is_cplx<S>::value) return rscale<S>(kscale(K, g) * kscale(K, gp), t);
         else return t;
     }
     if constexpr (is_cplx<S>::value) {
@@ -48,7 +51,7 @@ __device__ __forceinline__ S kentry(const KernelK& K, int g, int gp)
         grid_xy(K, g, x, y);
         grid_xy(K, gp, xp, yp);
         const double dx = x - xp, dy = y - yp;
-        return rscale<S>(K.s[g] * K.s[gp], hank_row<S>(K, sqrt(dx * dx + dy * dy)));
+        return rscale<S>(kscale(K, g) * kscale(K, gp), hank_row<S>(K, sqrt(dx * dx + dy * dy)));
     } else if constexpr (sizeof(S) == sizeof(float)) {
         const int d1 = g % K.n - gp % K.n, d2 = g / K.n - gp / K.n;
         const float hf = (float)K.h;
@@ -67,7 +70,7 @@ template <class S>
 __device__ __forceinline__ S kdiag(const KernelK& K, const double* a, int g)
 {
     if constexpr (is_cplx<S>::value) {
-        const double s2 = K.s[g] * K.s[g];
+        const double s2 = kscale(K, g) * kscale(K, g);
         return S(a[g] + s2 * K.hs_re, s2 * K.hs_im);
     } else {
         return S(a[g] + K.self);
@@ -81,7 +84,7 @@ __device__ __forceinline__ S kproxy(const KernelK& K, double zx, double zy, int 
     grid_xy(K, g, x, y);
     if constexpr (is_cplx<S>::value) {
         const double dx = zx - x, dy = zy - y;
-        return rscale<S>(K.s[g], hank_row<S>(K, sqrt(dx * dx + dy * dy)));
+        return rscale<S>(kscale(K, g), hank_row<S>(K, sqrt(dx * dx + dy * dy)));
     } else if constexpr (sizeof(S) == sizeof(float)) {
         const float dx = (float)(zx - x), dy = (float)(zy - y);
         return (float)K.c0 * logf(dx * dx + dy * dy);

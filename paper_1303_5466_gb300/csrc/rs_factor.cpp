@@ -294,17 +294,17 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
 bool use_sweep(const rs_op* op) { return op->kind == RS_LAPLACE && op->opts.spd_inverse != 0; }
 
 // ID phase of one level (Sec. 2.2 proxy ID, Eq. 2.1).
+// The ID phase of one level whose index sets (L.m, act, nn, nearv and their offsets) are
+// filled: Y assembly with kernel K and proxy circles geo (centre x, y, radius per box),
+// column-pivoted QR, skeleton bookkeeping and T.
 template <class T>
-int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st)
+int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, const std::vector<double>& geo)
 {
     const int P = op->opts.proxy_points;
-    int rc = level_sets(op->n, op->d, L.l, child ? child->k.data() : nullptr, child ? child->skel.data() : nullptr,
-                        op->opts.proxy_radius_factor, L.m, L.act, L.act_off, L.nn, L.nearv, L.near_off);
-    if (rc) return rc;
+    int rc;
     const int nb = L.nb;
     L.r.resize(nb);
     std::vector<int64_t> y_off(nb + 1, 0);
-    std::vector<double> geo(3 * nb);
     int64_t max_entries = 0;
     L.max_m = L.max_r = 0;
     for (int b = 0; b < nb; ++b) {
@@ -313,11 +313,6 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
         max_entries = std::max(max_entries, L.r[b] * L.m[b]);
         L.max_m = std::max<int>(L.max_m, (int)L.m[b]);
         L.max_r = std::max<int>(L.max_r, (int)L.r[b]);
-        const BoxInt bi = box_int(op->n, L.l, b);
-        const double hh = 0.5 * op->K.h;
-        geo[3 * b] = (double)((2 * bi.bx + 1) * bi.wx) * hh;
-        geo[3 * b + 1] = (double)((2 * bi.by + 1) * bi.wy) * hh;
-        geo[3 * b + 2] = (op->opts.proxy_radius_factor * (double)std::max(bi.wx, bi.wy)) * hh;
     }
     if (max_entries > (int64_t)INT32_MAX) return fail(RS_E_INVALID, "box too large");
     if ((rc = upload(L.d_act, to32(L.act), st))) return rc;
@@ -336,7 +331,7 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
         const int cnt = pb ? 1 : nb;
         RS_CUDA(launch_assemble_Y<T>(st, cnt, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>() + b0,
                                      w.near.as<int32_t>(), w.near_off.as<int64_t>() + b0, w.geo.as<double>() + 3 * b0,
-                                     op->d_ucirc.as<double>(), P, w.y_off.as<int64_t>() + b0, w.Y.as<T>(), op->K,
+                                     op->d_ucirc.as<double>(), P, w.y_off.as<int64_t>() + b0, w.Y.as<T>(), K,
                                      pb ? (int)(L.r[b0] * L.m[b0]) : (int)max_entries));
     }
     }
@@ -510,6 +505,114 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     return RS_OK;
 }
 
+// Proxy circle of every box of level L (centre x, y and radius; Sec. 2.2).
+std::vector<double> box_geo(const rs_op* op, const Level& L)
+{
+    std::vector<double> geo(3 * (size_t)L.nb);
+    const double hh = 0.5 * op->K.h;
+    for (int b = 0; b < L.nb; ++b) {
+        const BoxInt bi = box_int(op->n, L.l, b);
+        geo[3 * b] = (double)((2 * bi.bx + 1) * bi.wx) * hh;
+        geo[3 * b + 1] = (double)((2 * bi.by + 1) * bi.wy) * hh;
+        geo[3 * b + 2] = (op->opts.proxy_radius_factor * (double)std::max(bi.wx, bi.wy)) * hh;
+    }
+    return geo;
+}
+
+// Translation-invariant mode (a and b constant; Sec. 5, one set of matrix blocks per level):
+// every box of the level is a translate of box 0, its active set translated point by point.
+// The level's ID is taken once, on box 0 with all eight same-level neighbours present --
+// translates of its active set in the order (dy, dx) = (-1,-1), (-1,0), (-1,1), (0,-1),
+// (0,1), (1,-1), (1,0), (1,1), also where they fall outside the unit square, their points
+// strictly inside the proxy circle as near rows.  Every box's real near rows are rows of this
+// Y (translated) and its proxy rows the same, so the skeleton positions and T serve all boxes.
+// The template lives on an extended lattice of side 3n, box 0 shifted by (n, n): the entries
+// depend only on offsets, so the grid kernels evaluate it unchanged (no offset table; the
+// Helmholtz scaling is the constant s0).
+template <class T>
+int id_level_ti(rs_op* op, Level& L, IdWork& w, cudaStream_t st)
+{
+    const int64_t n = op->n, ne = 3 * n;
+    const int nb = L.nb;
+    Level& TL = op->ti_lev[L.l];
+    TL.l = L.l;
+    TL.nb = 1;
+    const int64_t m = L.m[0];
+    const BoxInt bi = box_int(n, L.l, 0);
+    TL.m = {m};
+    TL.act.resize(m);
+    for (int64_t p = 0; p < m; ++p) {
+        const int64_t g = L.act[p];
+        TL.act[p] = (g % n + n) + ne * (g / n + n);
+    }
+    TL.act_off = {0, m};
+    const int64_t cx2 = (2 * bi.bx + 1) * bi.wx, cy2 = (2 * bi.by + 1) * bi.wy;     // units of h/2
+    const double R2 = op->opts.proxy_radius_factor * (double)std::max(bi.wx, bi.wy);
+    TL.nearv.clear();
+    for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+            if (ox == 0 && oy == 0) continue;
+            for (int64_t p = 0; p < m; ++p) {
+                const int64_t i1 = L.act[p] % n + ox * bi.wx, i2 = L.act[p] / n + oy * bi.wy;
+                const int64_t dx = 2 * i1 + 1 - cx2, dy = 2 * i2 + 1 - cy2;
+                if (!((double)(dx * dx + dy * dy) < R2 * R2)) continue;
+                TL.nearv.push_back((i1 + n) + ne * (i2 + n));
+            }
+        }
+    TL.nn = {(int64_t)TL.nearv.size()};
+    TL.near_off = {0, (int64_t)TL.nearv.size()};
+    std::vector<double> geo = box_geo(op, TL);
+    geo[0] += (double)n * op->K.h;
+    geo[1] += (double)n * op->K.h;
+    KernelK Kx = op->K;
+    Kx.n = (int)ne;
+    Kx.tab = nullptr;
+    Kx.s = nullptr;
+    Kx.s0 = op->ti_s0;
+    int rc = id_core<T>(op, TL, w, st, Kx, geo);
+    if (rc) return rc;
+    // every box: the template's rank, skeleton positions and T (offset 0 for all boxes)
+    const int64_t k = TL.k[0];
+    L.r.assign(nb, TL.r[0]);
+    L.nn.assign(nb, TL.nn[0]);
+    L.k.assign(nb, k);
+    L.k_off.resize(nb + 1);
+    for (int b = 0; b <= nb; ++b) L.k_off[b] = (int64_t)b * k;
+    L.perm.resize((size_t)nb * m);
+    L.skel.resize((size_t)nb * k);
+    for (int b = 0; b < nb; ++b) {
+        if (L.m[b] != m) return fail(RS_E_CUDA, "translation-invariant mode: boxes of a level differ in size");
+        const int64_t a0 = L.act_off[b], sh = L.act[a0] - L.act[0];
+        for (int64_t p = 0; p < m; ++p) {
+            if (L.act[a0 + p] - L.act[p] != sh) return fail(RS_E_CUDA, "translation-invariant mode: not a translate");
+            L.perm[a0 + p] = TL.perm[p];
+        }
+        for (int64_t a = 0; a < k; ++a) L.skel[b * k + a] = L.act[a0 + TL.perm[a]];
+    }
+    L.t_off.assign(nb + 1, 0);
+    L.t_off[nb] = k * (m - k);
+    L.max_m = (int)m;
+    L.max_k = (int)k;
+    L.max_r = TL.max_r;
+    if ((rc = upload(L.d_act, to32(L.act), st))) return rc;
+    if ((rc = upload(L.d_act_off, L.act_off, st))) return rc;
+    if ((rc = upload(L.d_m, to32(L.m), st))) return rc;
+    if ((rc = upload(L.d_k, to32(L.k), st))) return rc;
+    if ((rc = upload(L.d_perm, L.perm, st))) return rc;
+    if ((rc = upload(L.d_k_off, L.k_off, st))) return rc;
+    return upload(L.d_t_off, L.t_off, st);
+}
+
+template <class T>
+int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st)
+{
+    int rc = level_sets(op->n, op->d, L.l, child ? child->k.data() : nullptr, child ? child->skel.data() : nullptr,
+                        op->opts.proxy_radius_factor, L.m, L.act, L.act_off, L.nn, L.nearv, L.near_off);
+    if (rc) return rc;
+    if (op->opts.translation_invariant) return id_level_ti<T>(op, L, w, st);
+    return id_core<T>(op, L, w, st, op->K, box_geo(op, L));
+}
+
 // Inversion phase of one level (Algorithm 1 with the E of Algorithm 2).
 template <class T>
 int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
@@ -627,6 +730,32 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E, L.l);
 }
 
+// Translation-invariant mode: the inversion phase on the level's template (one box), its F
+// assembled from box 0's own active points, then shared by every box (all offsets 0).
+template <class T>
+int inverse_level_ti(rs_op* op, int l, cudaStream_t st)
+{
+    Level& L = op->lev[l];
+    Level& TL = op->ti_lev[l];
+    const int nb = L.nb;
+    const int64_t m = TL.m[0], k = TL.k[0];
+    TL.act.assign(L.act.begin(), L.act.begin() + m);
+    int rc;
+    if ((rc = upload(TL.d_act, to32(TL.act), st))) return rc;
+    if ((rc = inverse_level<T>(op, TL, l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    L.phi_off.assign(nb + 1, 0);
+    L.phi_off[nb] = m * m;
+    L.e_off.assign(nb + 1, 0);
+    L.e_off[nb] = k * k;
+    L.w_off.assign(nb + 1, 0);
+    L.w_off[nb] = m * k;
+    L.d_Phi = std::move(TL.d_Phi);
+    L.d_E = std::move(TL.d_E);
+    L.d_T = std::move(TL.d_T);
+    if ((rc = upload(L.d_phi_off, L.phi_off, st))) return rc;
+    return upload(L.d_e_off, L.e_off, st);
+}
+
 void add_mv(std::vector<MatvecProb>& v, std::vector<int64_t>& blk, int64_t& nblk, int rows, int cols, int ld, int trans,
             int64_t a_off, int64_t x_off, int64_t y_off, double alpha, double beta)
 {
@@ -732,8 +861,10 @@ void compute_stats(rs_op* op)
     int64_t bytes = 0, cboxes = 0, replaced = 0;
     for (int l = 1; l <= op->d; ++l) {
         const Level& L = op->lev[l];
+        const int nf = op->opts.translation_invariant ? 1 : L.nb;   // boxes factored
         for (int b = 0; b < L.nb; ++b) {
             const double m = (double)L.m[b], k = (double)L.k[b], r = (double)L.r[b];
+            if (b >= nf) continue;
             ff += 4.0 * r * m * k - 2.0 * k * k * (r + m) + 4.0 * k * k * k / 3.0;   // CPQR, k steps
             ff += k * k * (m - k);                                                // T = R11^{-1} R12
             ff += inv * m * m * m;                                                // F^{-1}
@@ -789,8 +920,12 @@ int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
     }
     op->stats.ms_tree = ms_since(t0);
     auto t1 = Clock::now();
-    for (int l = op->d; l >= 1; --l)
-        if ((rc = inverse_level<T>(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    for (int l = op->d; l >= 1; --l) {
+        const Level* child = l < op->d ? &op->lev[l + 1] : nullptr;
+        rc = op->opts.translation_invariant ? inverse_level_ti<T>(op, l, st)
+                                            : inverse_level<T>(op, op->lev[l], child, st);
+        if (rc) return rc;
+    }
     // root: active set = skeletons of (1,0) then (1,1), natural order
     Level& R = op->lev[0];
     const Level& L1 = op->lev[1];
@@ -855,6 +990,13 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
     if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 2) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 2");
+    if (op->opts.translation_invariant) {
+        if (op->opts.k_cut > 0) return fail(RS_E_INVALID, "translation_invariant does not combine with k_cut");
+        if (9 * op->N > (int64_t)INT32_MAX) return fail(RS_E_INVALID, "translation_invariant: grid too large");
+        for (int64_t i = 1; i < op->N; ++i)
+            if ((a && a[i] != a[0]) || (kernel && kernel->b && kernel->b[i] != kernel->b[0]))
+                return fail(RS_E_INVALID, "translation_invariant needs constant a(x) and b(x)");
+    }
     const double h = 1.0 / (double)op->n;
     op->K.n = (int)op->n;
     op->K.h = h;
@@ -883,6 +1025,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         if ((rc = upload(op->d_s, sg, st))) return rc;
         if ((rc = upload(op->d_s_in, si, st))) return rc;
         op->K.s = op->d_s.as<double>();
+        op->ti_s0 = si[0];
     }
     // a in grid order
     std::vector<double> ag(op->N, 1.0);
@@ -903,6 +1046,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     RS_CUDA(cudaMemsetAsync(op->d_zero.p, 0, sizeof(int64_t), st));
     RS_CUDA(cudaMemsetAsync(op->d_status.p, 0, sizeof(int), st));
     op->lev.resize(op->d + 1);
+    if (op->opts.translation_invariant) op->ti_lev.resize(op->d + 1);
     for (int l = 0; l <= op->d; ++l) {
         op->lev[l].l = l;
         op->lev[l].nb = 1 << l;
@@ -1397,6 +1541,8 @@ int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* o
     if (which == 0) {
         std::copy(L->act.begin() + L->act_off[box], L->act.begin() + L->act_off[box + 1], out);
     } else if (which == 1) {
+        if (op->opts.translation_invariant)      // the level's near rows are its template's
+            return fail(RS_E_INVALID, "no per-box near list in translation-invariant mode");
         std::copy(L->nearv.begin() + L->near_off[box], L->nearv.begin() + L->near_off[box + 1], out);
     } else if (which == 2) {
         std::copy(L->skel.begin() + L->k_off[box], L->skel.begin() + L->k_off[box + 1], out);

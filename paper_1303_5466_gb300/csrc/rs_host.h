@@ -250,6 +250,11 @@ struct rs_op {
     rs::KernelK K{};
     std::vector<int64_t> input_of_g;
     std::vector<rs::Level> lev;       // lev[0] = root, lev[l] for l = 1..d
+    // translation-invariant mode (opts.translation_invariant): the one-box template of each
+    // level (its ID on an extended lattice, then its F, F^{-1} and E), whose factors every box
+    // of lev[l] shares
+    std::vector<rs::Level> ti_lev;
+    double ti_s0 = 1.0;               // the constant Helmholtz scaling s = kappa sqrt(b) there
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // factor-time scratch reused across levels, released with the op
     rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2;

@@ -69,7 +69,8 @@ struct KernelK {
     int kind;
     double kappa;
     double hs_re, hs_im;
-    const double* s;
+    const double* s;        // Helmholtz s_g per grid point, or NULL: the constant s0
+    double s0;
     // the off-diagonal entries on the grid depend only on the offset (d1, d2): when set, a
     // (2n-1)^2 table of K(d1 h, d2 h) in the factor's storage type (Helmholtz: without the
     // s_g s_g' scaling), read at (d1 + n - 1) + (2n - 1)(d2 + n - 1)
