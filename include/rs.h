@@ -103,14 +103,18 @@ typedef struct {
                                     dot products of step s+1); -1 = the autotuner's table
                                     (rs_autotune), else 0 or 1 by occupancy. Same result up
                                     to rounding order                                [-1]   */
-    int translation_invariant;   /* 1: a(x) (and b(x)) constant, so A depends only on the
+    int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the
                                     offset between grid points (Sec. 5: one set of matrix
-                                    blocks per level).  Each level's ID is taken once, on
+                                    blocks per level).  1: each level's ID is taken once, on
                                     box 0 with all eight same-level neighbours present (also
                                     where they fall outside the unit square), and its T,
                                     F^{-1} and E are stored once and shared by every box of
-                                    the level.  Refused with varying a or b, with k_cut > 0,
-                                    and for 9 N > 2^31 - 1                            [0]    */
+                                    the level.  2: boxes whose active points, near points
+                                    and children are translates of one another share one
+                                    factored box (the per-box result, each distinct box
+                                    factored once: ~13-24 per level at any grid size).
+                                    Refused with varying a or b, with k_cut > 0, and for
+                                    9 N > 2^31 - 1 (mode 1)                           [0]    */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);
@@ -267,7 +271,7 @@ int rs_tune_count(void);
  * sizes: m (active points), k (skeleton), r (ID rows), nnear (near rows). */
 int rs_op_box_sizes(const rs_op* op, int level, int box, int64_t* m, int64_t* k, int64_t* r,
                     int64_t* nnear);
-/* which: 0 = active set (m), 1 = near rows (nnear; refused in translation-invariant mode,
+/* which: 0 = active set (m), 1 = near rows (nnear; refused in translation-invariant mode 1,
  * whose near rows belong to the level's template), 2 = skeleton ascending in g (k). */
 int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* out);
 /* Orders of Sec. 3.1 used by the extra compression (available for every box): which = 0,

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <chrono>
 #include <cmath>
 #include <functional>
@@ -519,80 +520,144 @@ std::vector<double> box_geo(const rs_op* op, const Level& L)
     return geo;
 }
 
-// Translation-invariant mode (a and b constant; Sec. 5, one set of matrix blocks per level):
-// every box of the level is a translate of box 0, its active set translated point by point.
-// The level's ID is taken once, on box 0 with all eight same-level neighbours present --
-// translates of its active set in the order (dy, dx) = (-1,-1), (-1,0), (-1,1), (0,-1),
-// (0,1), (1,-1), (1,0), (1,1), also where they fall outside the unit square, their points
-// strictly inside the proxy circle as near rows.  Every box's real near rows are rows of this
-// Y (translated) and its proxy rows the same, so the skeleton positions and T serve all boxes.
-// The template lives on an extended lattice of side 3n, box 0 shifted by (n, n): the entries
-// depend only on offsets, so the grid kernels evaluate it unchanged (no offset table; the
-// Helmholtz scaling is the constant s0).
+// Translation-invariant modes (a and b constant, so A depends only on the offset between grid
+// points; Sec. 5, one set of matrix blocks per level).  The level's ID phase runs on a few
+// "factored" boxes, and every box of the level takes the rank, skeleton positions and T of
+// its class (L.ti_cls, representatives L.ti_rep).
+//   Mode 1 (the paper's one set per level): one template, box 0 with all eight same-level
+//     neighbours present -- translates of its active set in the order (dy, dx) = (-1,-1),
+//     (-1,0), (-1,1), (0,-1), (0,1), (1,-1), (1,0), (1,1), also where they fall outside the
+//     unit square, their points strictly inside the proxy circle as near rows.  Every box's
+//     real near rows are rows of this Y (translated) and its proxy rows the same, so the
+//     skeleton positions and T serve all boxes.  The template lives on an extended lattice of
+//     side 3n, box 0 shifted by (n, n): the entries depend only on offsets, so the grid kernels
+//     evaluate it unchanged (no offset table; the Helmholtz scaling is the constant s0).
+//   Mode 2 (the per-box factorization without its repeats): boxes whose active points, near
+//     points and children's classes are translates of one another have translated Y and F,
+//     hence the same ID, F^{-1} and E; one box per class is factored (with its real rows).
 template <class T>
-int id_level_ti(rs_op* op, Level& L, IdWork& w, cudaStream_t st)
+int id_level_ti(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st)
 {
-    const int64_t n = op->n, ne = 3 * n;
+    const int64_t n = op->n;
     const int nb = L.nb;
     Level& TL = op->ti_lev[L.l];
     TL.l = L.l;
-    TL.nb = 1;
-    const int64_t m = L.m[0];
-    const BoxInt bi = box_int(n, L.l, 0);
-    TL.m = {m};
-    TL.act.resize(m);
-    for (int64_t p = 0; p < m; ++p) {
-        const int64_t g = L.act[p];
-        TL.act[p] = (g % n + n) + ne * (g / n + n);
-    }
-    TL.act_off = {0, m};
-    const int64_t cx2 = (2 * bi.bx + 1) * bi.wx, cy2 = (2 * bi.by + 1) * bi.wy;     // units of h/2
-    const double R2 = op->opts.proxy_radius_factor * (double)std::max(bi.wx, bi.wy);
-    TL.nearv.clear();
-    for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-            if (ox == 0 && oy == 0) continue;
-            for (int64_t p = 0; p < m; ++p) {
-                const int64_t i1 = L.act[p] % n + ox * bi.wx, i2 = L.act[p] / n + oy * bi.wy;
-                const int64_t dx = 2 * i1 + 1 - cx2, dy = 2 * i2 + 1 - cy2;
-                if (!((double)(dx * dx + dy * dy) < R2 * R2)) continue;
-                TL.nearv.push_back((i1 + n) + ne * (i2 + n));
-            }
-        }
-    TL.nn = {(int64_t)TL.nearv.size()};
-    TL.near_off = {0, (int64_t)TL.nearv.size()};
-    std::vector<double> geo = box_geo(op, TL);
-    geo[0] += (double)n * op->K.h;
-    geo[1] += (double)n * op->K.h;
-    KernelK Kx = op->K;
-    Kx.n = (int)ne;
-    Kx.tab = nullptr;
-    Kx.s = nullptr;
-    Kx.s0 = op->ti_s0;
-    int rc = id_core<T>(op, TL, w, st, Kx, geo);
-    if (rc) return rc;
-    // every box: the template's rank, skeleton positions and T (offset 0 for all boxes)
-    const int64_t k = TL.k[0];
-    L.r.assign(nb, TL.r[0]);
-    L.nn.assign(nb, TL.nn[0]);
-    L.k.assign(nb, k);
-    L.k_off.resize(nb + 1);
-    for (int b = 0; b <= nb; ++b) L.k_off[b] = (int64_t)b * k;
-    L.perm.resize((size_t)nb * m);
-    L.skel.resize((size_t)nb * k);
-    for (int b = 0; b < nb; ++b) {
-        if (L.m[b] != m) return fail(RS_E_CUDA, "translation-invariant mode: boxes of a level differ in size");
-        const int64_t a0 = L.act_off[b], sh = L.act[a0] - L.act[0];
+    std::vector<double> geo;
+    KernelK K = op->K;
+    if (op->opts.translation_invariant == 1) {
+        const int64_t ne = 3 * n;
+        const int64_t m = L.m[0];
+        const BoxInt bi = box_int(n, L.l, 0);
+        L.ti_cls.assign(nb, 0);
+        L.ti_rep = {0};
+        TL.nb = 1;
+        TL.m = {m};
+        TL.act.resize(m);
         for (int64_t p = 0; p < m; ++p) {
-            if (L.act[a0 + p] - L.act[p] != sh) return fail(RS_E_CUDA, "translation-invariant mode: not a translate");
-            L.perm[a0 + p] = TL.perm[p];
+            const int64_t g = L.act[p];
+            TL.act[p] = (g % n + n) + ne * (g / n + n);
         }
-        for (int64_t a = 0; a < k; ++a) L.skel[b * k + a] = L.act[a0 + TL.perm[a]];
+        TL.act_off = {0, m};
+        const int64_t cx2 = (2 * bi.bx + 1) * bi.wx, cy2 = (2 * bi.by + 1) * bi.wy;     // units of h/2
+        const double R2 = op->opts.proxy_radius_factor * (double)std::max(bi.wx, bi.wy);
+        TL.nearv.clear();
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                if (ox == 0 && oy == 0) continue;
+                for (int64_t p = 0; p < m; ++p) {
+                    const int64_t i1 = L.act[p] % n + ox * bi.wx, i2 = L.act[p] / n + oy * bi.wy;
+                    const int64_t dx = 2 * i1 + 1 - cx2, dy = 2 * i2 + 1 - cy2;
+                    if (!((double)(dx * dx + dy * dy) < R2 * R2)) continue;
+                    TL.nearv.push_back((i1 + n) + ne * (i2 + n));
+                }
+            }
+        TL.nn = {(int64_t)TL.nearv.size()};
+        TL.near_off = {0, (int64_t)TL.nearv.size()};
+        geo = box_geo(op, TL);
+        geo[0] += (double)n * op->K.h;
+        geo[1] += (double)n * op->K.h;
+        K.n = (int)ne;
+        K.tab = nullptr;
+        K.s = nullptr;
+        K.s0 = op->ti_s0;
+    } else {
+        // classes: the active and near points relative to the box's first active point, and
+        // the children's classes (exact keys: equal keys mean translated Y and F)
+        std::map<std::vector<int64_t>, int> key_of;
+        L.ti_cls.assign(nb, 0);
+        L.ti_rep.clear();
+        std::vector<int64_t> key;
+        for (int b = 0; b < nb; ++b) {
+            const int64_t a0 = L.act_off[b], a1 = L.act_off[b + 1], g0 = L.act[a0];
+            key.clear();
+            key.push_back(a1 - a0);
+            key.push_back(L.near_off[b + 1] - L.near_off[b]);
+            if (child) {
+                key.push_back(child->ti_cls[2 * b]);
+                key.push_back(child->ti_cls[2 * b + 1]);
+            }
+            for (int64_t p = a0; p < a1; ++p) key.push_back(L.act[p] - g0);
+            for (int64_t q = L.near_off[b]; q < L.near_off[b + 1]; ++q) key.push_back(L.nearv[q] - g0);
+            auto it = key_of.find(key);
+            if (it == key_of.end()) {
+                it = key_of.emplace(key, (int)L.ti_rep.size()).first;
+                L.ti_rep.push_back(b);
+            }
+            L.ti_cls[b] = it->second;
+        }
+        const int nc = (int)L.ti_rep.size();
+        TL.nb = nc;
+        TL.m.resize(nc);
+        TL.nn.resize(nc);
+        TL.act_off.assign(nc + 1, 0);
+        TL.near_off.assign(nc + 1, 0);
+        TL.act.clear();
+        TL.nearv.clear();
+        const std::vector<double> g_all = box_geo(op, L);
+        geo.resize(3 * (size_t)nc);
+        for (int c = 0; c < nc; ++c) {
+            const int b = L.ti_rep[c];
+            TL.m[c] = L.m[b];
+            TL.nn[c] = L.nn[b];
+            TL.act.insert(TL.act.end(), L.act.begin() + L.act_off[b], L.act.begin() + L.act_off[b + 1]);
+            TL.nearv.insert(TL.nearv.end(), L.nearv.begin() + L.near_off[b], L.nearv.begin() + L.near_off[b + 1]);
+            TL.act_off[c + 1] = (int64_t)TL.act.size();
+            TL.near_off[c + 1] = (int64_t)TL.nearv.size();
+            for (int q = 0; q < 3; ++q) geo[3 * c + q] = g_all[3 * b + q];
+        }
     }
+    int rc = id_core<T>(op, TL, w, st, K, geo);
+    if (rc) return rc;
+    // every box: its class's rank, skeleton positions and T
+    L.r.resize(nb);
+    L.k.resize(nb);
+    L.k_off.assign(nb + 1, 0);
     L.t_off.assign(nb + 1, 0);
-    L.t_off[nb] = k * (m - k);
-    L.max_m = (int)m;
-    L.max_k = (int)k;
+    for (int b = 0; b < nb; ++b) {
+        const int c = L.ti_cls[b];
+        L.r[b] = TL.r[c];
+        if (op->opts.translation_invariant == 1) L.nn[b] = TL.nn[c];
+        L.k[b] = TL.k[c];
+        L.k_off[b + 1] = L.k_off[b] + L.k[b];
+        L.t_off[b] = TL.t_off[c];
+    }
+    L.t_off[nb] = TL.t_off[TL.nb];
+    L.perm.resize(L.act.size());
+    L.skel.resize(L.k_off[nb]);
+    for (int b = 0; b < nb; ++b) {
+        const int c = L.ti_cls[b];
+        const int64_t a0 = L.act_off[b], m = L.m[b], t0 = TL.act_off[c];
+        if (m != TL.m[c]) return fail(RS_E_CUDA, "translation-invariant mode: boxes of a class differ in size");
+        const int64_t sh = L.act[a0] - L.act[L.act_off[L.ti_rep[c]]];
+        for (int64_t p = 0; p < m; ++p) {
+            if (op->opts.translation_invariant == 2 && L.act[a0 + p] - TL.act[t0 + p] != sh)
+                return fail(RS_E_CUDA, "translation-invariant mode: not a translate");
+            L.perm[a0 + p] = TL.perm[t0 + p];
+        }
+        for (int64_t a = 0; a < L.k[b]; ++a) L.skel[L.k_off[b] + a] = L.act[a0 + TL.perm[t0 + a]];
+    }
+    L.max_m = TL.max_m;
+    L.max_k = TL.max_k;
     L.max_r = TL.max_r;
     if ((rc = upload(L.d_act, to32(L.act), st))) return rc;
     if ((rc = upload(L.d_act_off, L.act_off, st))) return rc;
@@ -609,13 +674,21 @@ int id_level(rs_op* op, Level& L, const Level* child, IdWork& w, cudaStream_t st
     int rc = level_sets(op->n, op->d, L.l, child ? child->k.data() : nullptr, child ? child->skel.data() : nullptr,
                         op->opts.proxy_radius_factor, L.m, L.act, L.act_off, L.nn, L.nearv, L.near_off);
     if (rc) return rc;
-    if (op->opts.translation_invariant) return id_level_ti<T>(op, L, w, st);
+    if (op->opts.translation_invariant) return id_level_ti<T>(op, L, child, w, st);
     return id_core<T>(op, L, w, st, op->K, box_geo(op, L));
 }
 
+// What F assembly reads of the child level: per box b of the level being inverted, the rank
+// and E offset of its children at 2b and 2b + 1, and the children's E storage.
+struct ChildRef {
+    const int32_t* k = nullptr;
+    const int64_t* e_off = nullptr;
+    const void* E = nullptr;
+};
+
 // Inversion phase of one level (Algorithm 1 with the E of Algorithm 2).
 template <class T>
-int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
+int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
 {
     const int nb = L.nb;
     L.phi_off.assign(nb + 1, 0);
@@ -637,9 +710,9 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
             RS_CUDA(launch_assemble_F<T>(st, pb ? 1 : nb, leaf, L.d_act.as<int32_t>(), L.d_act_off.as<int64_t>() + b0,
                                          L.d_perm.as<int32_t>(), op->d_a.as<double>(),
                                          L.d_phi_off.as<int64_t>() + b0, L.d_Phi.as<T>(),
-                                         child ? child->d_k.as<int32_t>() + 2 * b0 : nullptr,
-                                         child ? child->d_e_off.as<int64_t>() + 2 * b0 : nullptr,
-                                         child ? child->d_E.as<T>() : nullptr, op->K,
+                                         cref.k ? cref.k + 2 * b0 : nullptr,
+                                         cref.e_off ? cref.e_off + 2 * b0 : nullptr,
+                                         (const T*)cref.E, op->K,
                                          pb ? (int)L.m[b0] : L.max_m));
         }
         return RS_OK;
@@ -730,25 +803,66 @@ int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
     return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E, L.l);
 }
 
-// Translation-invariant mode: the inversion phase on the level's template (one box), its F
-// assembled from box 0's own active points, then shared by every box (all offsets 0).
+ChildRef child_ref(const Level* child)
+{
+    ChildRef c;
+    if (child) {
+        c.k = child->d_k.as<int32_t>();
+        c.e_off = child->d_e_off.as<int64_t>();
+        c.E = child->d_E.p;
+    }
+    return c;
+}
+
+template <class T>
+int inverse_level(rs_op* op, Level& L, const Level* child, cudaStream_t st)
+{
+    return inverse_level<T>(op, L, child_ref(child), st);
+}
+
+// Translation-invariant modes: the inversion phase on the level's factored boxes (the
+// template, or one box per class), each F assembled from its representative's own active
+// points and children; then every box takes its class's F^{-1}, E and T offsets.
 template <class T>
 int inverse_level_ti(rs_op* op, int l, cudaStream_t st)
 {
     Level& L = op->lev[l];
     Level& TL = op->ti_lev[l];
-    const int nb = L.nb;
-    const int64_t m = TL.m[0], k = TL.k[0];
-    TL.act.assign(L.act.begin(), L.act.begin() + m);
+    const int nb = L.nb, nc = TL.nb;
     int rc;
-    if ((rc = upload(TL.d_act, to32(TL.act), st))) return rc;
-    if ((rc = inverse_level<T>(op, TL, l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
+    if (op->opts.translation_invariant == 1) {      // the template's Y was on the extended lattice
+        TL.act.assign(L.act.begin(), L.act.begin() + TL.m[0]);
+        if ((rc = upload(TL.d_act, to32(TL.act), st))) return rc;
+    }
+    ChildRef cref;
+    if (l < op->d) {
+        const Level& C = op->lev[l + 1];
+        std::vector<int32_t> ck(2 * (size_t)nc);
+        std::vector<int64_t> ce(2 * (size_t)nc);
+        for (int c = 0; c < nc; ++c)
+            for (int i = 0; i < 2; ++i) {
+                const int cb = 2 * L.ti_rep[c] + i;
+                ck[2 * c + i] = (int32_t)C.k[cb];
+                ce[2 * c + i] = C.e_off[cb];
+            }
+        if ((rc = upload(op->t_ck, ck, st))) return rc;
+        if ((rc = upload(op->t_ce, ce, st))) return rc;
+        cref.k = op->t_ck.as<int32_t>();
+        cref.e_off = op->t_ce.as<int64_t>();
+        cref.E = C.d_E.p;
+    }
+    if ((rc = inverse_level<T>(op, TL, cref, st))) return rc;
     L.phi_off.assign(nb + 1, 0);
-    L.phi_off[nb] = m * m;
     L.e_off.assign(nb + 1, 0);
-    L.e_off[nb] = k * k;
     L.w_off.assign(nb + 1, 0);
-    L.w_off[nb] = m * k;
+    for (int b = 0; b < nb; ++b) {
+        L.phi_off[b] = TL.phi_off[L.ti_cls[b]];
+        L.e_off[b] = TL.e_off[L.ti_cls[b]];
+        L.w_off[b] = TL.w_off[L.ti_cls[b]];
+    }
+    L.phi_off[nb] = TL.phi_off[nc];
+    L.e_off[nb] = TL.e_off[nc];
+    L.w_off[nb] = TL.w_off[nc];
     L.d_Phi = std::move(TL.d_Phi);
     L.d_E = std::move(TL.d_E);
     L.d_T = std::move(TL.d_T);
@@ -861,10 +975,14 @@ void compute_stats(rs_op* op)
     int64_t bytes = 0, cboxes = 0, replaced = 0;
     for (int l = 1; l <= op->d; ++l) {
         const Level& L = op->lev[l];
-        const int nf = op->opts.translation_invariant ? 1 : L.nb;   // boxes factored
+        std::vector<char> fac(L.nb, 1);                 // boxes factored (one per class)
+        if (op->opts.translation_invariant) {
+            fac.assign(L.nb, 0);
+            for (int b : L.ti_rep) fac[b] = 1;
+        }
         for (int b = 0; b < L.nb; ++b) {
             const double m = (double)L.m[b], k = (double)L.k[b], r = (double)L.r[b];
-            if (b >= nf) continue;
+            if (!fac[b]) continue;
             ff += 4.0 * r * m * k - 2.0 * k * k * (r + m) + 4.0 * k * k * k / 3.0;   // CPQR, k steps
             ff += k * k * (m - k);                                                // T = R11^{-1} R12
             ff += inv * m * m * m;                                                // F^{-1}
@@ -990,9 +1108,12 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
     if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 2) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 2");
+    if (op->opts.translation_invariant < 0 || op->opts.translation_invariant > 2)
+        return fail(RS_E_INVALID, "translation_invariant must be 0, 1 or 2");
     if (op->opts.translation_invariant) {
         if (op->opts.k_cut > 0) return fail(RS_E_INVALID, "translation_invariant does not combine with k_cut");
-        if (9 * op->N > (int64_t)INT32_MAX) return fail(RS_E_INVALID, "translation_invariant: grid too large");
+        if (op->opts.translation_invariant == 1 && 9 * op->N > (int64_t)INT32_MAX)
+            return fail(RS_E_INVALID, "translation_invariant: grid too large");
         for (int64_t i = 1; i < op->N; ++i)
             if ((a && a[i] != a[0]) || (kernel && kernel->b && kernel->b[i] != kernel->b[0]))
                 return fail(RS_E_INVALID, "translation_invariant needs constant a(x) and b(x)");
@@ -1541,7 +1662,7 @@ int rs_op_box_indices(const rs_op* op, int level, int box, int which, int64_t* o
     if (which == 0) {
         std::copy(L->act.begin() + L->act_off[box], L->act.begin() + L->act_off[box + 1], out);
     } else if (which == 1) {
-        if (op->opts.translation_invariant)      // the level's near rows are its template's
+        if (op->opts.translation_invariant == 1)  // the level's near rows are its template's
             return fail(RS_E_INVALID, "no per-box near list in translation-invariant mode");
         std::copy(L->nearv.begin() + L->near_off[box], L->nearv.begin() + L->near_off[box + 1], out);
     } else if (which == 2) {

@@ -142,6 +142,9 @@ struct Level {
     int64_t b_mv_phi = 0, b_mv_T = 0, b_mv_E = 0, b_mv_Tt = 0;
     int64_t sum_m = 0, sum_k = 0;
     double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set
+    // translation-invariant modes: class of every box and the box factored for each class
+    std::vector<int32_t> ti_cls;
+    std::vector<int> ti_rep;
     // extra compression (Sec. 3): boxes with k > k_cut
     std::vector<char> cmp;                 // per box
     std::vector<int> cbox;                 // compressed boxes
@@ -257,7 +260,7 @@ struct rs_op {
     double ti_s0 = 1.0;               // the constant Helmholtz scaling s = kappa sqrt(b) there
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // factor-time scratch reused across levels, released with the op
-    rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2;
+    rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2, t_ck, t_ce;
     rs::DevMem d_zero;                // one int64 zero: the first block of a one-problem launch
     // solve workspace (grown on demand)
     rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_z, s_in, s_out, s_out2;

@@ -1,9 +1,11 @@
-"""Translation-invariant mode (opts.translation_invariant; Sec. 5, one set of matrix blocks per
-level) on the GPU against the oracle's translation-invariant mode: identical ranks and
-skeleton sets at every level, T, F^{-1} and E of the template within the tolerances of the
-per-box path, solutions within 1e-9 (FP64 and complex128) and refined solutions to 1e-10
-(mixed FP32, complex64); every box reads the one stored set; the full-size 512^2 grid with
-a = 1 at sampled rows; and the inputs the mode must refuse."""
+"""Translation-invariant modes (opts.translation_invariant; Sec. 5, one set of matrix blocks per
+level) on the GPU.  Mode 1 (one template per level) against the oracle's translation-invariant
+mode; mode 2 (each class of translated boxes factored once) against the oracle's per-box
+factorization, whose results it reproduces.  Identical ranks and skeleton sets at every level,
+T, F^{-1} and E within the tolerances of the per-box path, solutions within 1e-9 (FP64 and
+complex128) and refined solutions to 1e-10 (mixed FP32, complex64); storage and factor flops
+below the per-box path's; the full-size 512^2 grid with a = 1 at sampled rows; and the inputs
+the modes must refuse."""
 import numpy as np
 import pytest
 
@@ -23,9 +25,9 @@ def rs():
     return P
 
 
-def _opts(rs, precision=None, **kw):
+def _opts(rs, precision=None, mode=1, **kw):
     o = rs.rs_opts_default()
-    o.translation_invariant = 1
+    o.translation_invariant = mode
     if precision is not None:
         o.precision = precision
     for k, v in kw.items():
@@ -149,6 +151,102 @@ def test_ti_full_size_sampled_residual(rs, oracle_mod):
     finally:
         rs.rs_free_tree(tree)
     rows = np.random.default_rng(4).choice(n * n, 128, replace=False)
+    Ax = oracle_mod.matvec_rows(n, x, rows)
+    for c in range(F.shape[1]):
+        assert np.linalg.norm(Ax[:, c] - F[rows, c]) / np.linalg.norm(F[rows, c]) <= 10 * eps
+
+
+# ------------------------------------------------------------------ mode 2
+
+
+@pytest.mark.parametrize("n,leaf,eps", [(32, 8, 1e-10), (64, 8, 1e-10), (64, 16, 1e-5), (128, 16, 1e-10)])
+def test_mode2_matches_per_box_oracle(rs, oracle_mod, n, leaf, eps):
+    F = oracle_mod.Factorization(n, leaf, eps)
+    S = rs.Solver(W.grid_points(n), leaf, eps=eps, opts=_opts(rs, mode=2))
+    mism = []
+    for l in range(F.depth, 0, -1):
+        for j in range(2 ** l):
+            assert rs.rs_op_box_sizes(S.op, l, j) == F.sizes(l, j), (l, j)
+            np.testing.assert_array_equal(rs.rs_op_box_indices(S.op, l, j, 0), F.active(l, j))
+            np.testing.assert_array_equal(rs.rs_op_box_indices(S.op, l, j, 1), F.near(l, j))
+            if not np.array_equal(rs.rs_op_box_indices(S.op, l, j, 2), F.skel(l, j)):
+                mism.append((l, j))
+    assert not mism, "skeleton sets differ at %s" % mism[:10]
+    if n <= 64:
+        ttol = max(1e-10, 1e-16 / max(eps, 1e-16)) * 100
+        rng = np.random.default_rng(1)
+        for l in range(F.depth, 0, -1):
+            for j in set(rng.choice(2 ** l, min(4, 2 ** l), replace=False).tolist()):
+                t = rs.rs_op_box_matrix(S.op, l, j, 0)
+                assert np.linalg.norm(t - F.T(l, j)) <= ttol * max(np.linalg.norm(t), 1.0)
+                fi = rs.rs_op_box_matrix(S.op, l, j, 1)
+                assert np.linalg.norm(fi - F.Finv(l, j)) <= 1e-6 * np.linalg.norm(fi)
+                e = rs.rs_op_box_matrix(S.op, l, j, 2)
+                assert np.linalg.norm(e - F.E(l, j)) <= 1e-6 * np.linalg.norm(e)
+    f = W.rhs_normal(n, 4, nrhs=2)
+    tol = 1e-9 if eps <= 1e-10 else 1e-3
+    assert _rel(S.solve(f), F.solve(f)) <= tol
+
+
+def test_mode2_factors_each_class_once(rs):
+    n, leaf = 128, 16
+    S2 = rs.Solver(W.grid_points(n), leaf, eps=1e-10, opts=_opts(rs, mode=2))
+    S0 = rs.Solver(W.grid_points(n), leaf, eps=1e-10)
+    s2, s0 = rs.rs_op_stats(S2.op), rs.rs_op_stats(S0.op)
+    assert s2["bytes_factors"] < s0["bytes_factors"]
+    assert s2["flops_factor"] < s0["flops_factor"]
+    d = s0["depth"]
+    for l in range(d, 0, -1):
+        for j in range(2 ** l):
+            assert rs.rs_op_box_sizes(S2.op, l, j) == rs.rs_op_box_sizes(S0.op, l, j)
+    f = W.rhs_normal(n, 2, nrhs=2)
+    assert _rel(S2.solve(f), S0.solve(f)) <= 1e-11
+
+
+def test_mode2_helmholtz_and_refined(rs, oracle_mod):
+    n, leaf, kappa = 32, 8, 25.0
+    F = oracle_mod.Factorization(n, leaf, 1e-10, kind=1, kappa=kappa)
+    S = rs.Solver(W.grid_points(n), leaf, eps=1e-10, kappa=kappa, opts=_opts(rs, rs.RS_C128, mode=2))
+    for l in range(F.depth, 0, -1):
+        for j in range(2 ** l):
+            assert rs.rs_op_box_sizes(S.op, l, j) == F.sizes(l, j), (l, j)
+    f = W.rhs_plane_wave(n, kappa)
+    assert _rel(S.solve(f), F.solve(f)) <= 1e-9
+    S32 = rs.Solver(W.grid_points(n), leaf, eps=1e-5, kappa=kappa,
+                    opts=_opts(rs, rs.RS_C64_REFINED, mode=2, refine_max_iter=12))
+    x = S32.solve(f)
+    assert _rel(oracle_mod.matvec(n, x, kind=1, kappa=kappa), f) <= 1e-10 * 1.01
+    n = 64
+    Sm = rs.Solver(W.grid_points(n), 8, eps=1e-6, opts=_opts(rs, rs.RS_MIXED_FP32, mode=2))
+    fm = W.rhs_uniform(n, 3)
+    assert _rel(oracle_mod.matvec(n, Sm.solve(fm)), fm) <= 1e-10 * 1.01
+
+
+def test_mode_out_of_range_is_refused(rs):
+    with pytest.raises(RuntimeError):
+        rs.Solver(W.grid_points(16), 4, eps=1e-10, opts=_opts(rs, mode=3))
+
+
+@pytest.mark.slow
+def test_mode2_full_size_sampled_residual(rs, oracle_mod):
+    import torch
+    n, leaf, eps = 512, 16, 1e-10
+    F = W.rhs_normal(n, 1, nrhs=2)
+    st = torch.cuda.current_stream()
+    tree = rs.rs_build_tree(W.grid_points(n), leaf)
+    try:
+        op = rs.rs_factor(tree, eps=eps, opts=_opts(rs, mode=2), stream=st)
+        try:
+            f_dev = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+            x_dev = torch.empty_like(f_dev)
+            rs.rs_solve(op, f_dev, 2, x_dev, st)
+            torch.cuda.synchronize()
+            x = x_dev.cpu().numpy().T.copy()
+        finally:
+            rs.rs_free(op)
+    finally:
+        rs.rs_free_tree(tree)
+    rows = np.random.default_rng(5).choice(n * n, 128, replace=False)
     Ax = oracle_mod.matvec_rows(n, x, rows)
     for c in range(F.shape[1]):
         assert np.linalg.norm(Ax[:, c] - F[rows, c]) / np.linalg.norm(F[rows, c]) <= 10 * eps
