@@ -59,6 +59,7 @@ def _args():
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     p.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner before the steps")
     p.add_argument("--no-per-box", action="store_true", help="skip the one-box-per-launch comparison")
+    p.add_argument("--no-ti", action="store_true", help="skip the translation-invariant comparison (a = 1)")
     p.add_argument("--k-cut", type=int, default=512,
                    help="also measure the extra compression of Sec. 3 for boxes with k > K (0: skip)")
     return p.parse_args()
@@ -312,6 +313,43 @@ def per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps):
     return out
 
 
+def ti_measure(P, torch, leaf, pts, F, nrhs, st, eps):
+    """The translation-invariant modes (Sec. 5: one set of matrix blocks per level) on the same
+    grid with a = 1, against the per-box-result factorization of that operator: factor and
+    solve time, stored bytes, root size and the FP64 direct-sum residual for each mode."""
+    import numpy as np
+    f = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    x = torch.empty_like(f)
+    tree = P.rs_build_tree(pts, leaf)
+    out = {"a": "1 (constant)"}
+    for mode in (0, 1, 2):
+        o = P.rs_opts_default()
+        o.translation_invariant = mode
+        torch.cuda.synchronize()
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(st)
+        op = P.rs_factor(tree, eps=eps, opts=o, stream=st)
+        e1.record(st)
+        e1.synchronize()
+        P.rs_solve(op, f, nrhs, x, st)
+        torch.cuda.synchronize()
+        s0, s1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        s0.record(st)
+        P.rs_solve(op, f, nrhs, x, st)
+        s1.record(st)
+        s1.synchronize()
+        stt = P.rs_op_stats(op)
+        out["mode%d" % mode] = {"factor_ms": e0.elapsed_time(e1), "solve_ms": s0.elapsed_time(s1),
+                                "bytes_factors": stt["bytes_factors"], "root_m": stt["root_m"],
+                                "flops_factor": stt["flops_factor"],
+                                "residual_fp64": float(P.rs_residual(op, x, f, nrhs, st).max())}
+        P.rs_free(op)
+    P.rs_free_tree(tree)
+    for mode in (1, 2):
+        out["mode%d" % mode]["factor_speedup_vs_per_box"] = out["mode0"]["factor_ms"] / out["mode%d" % mode]["factor_ms"]
+    return out
+
+
 def compressed_measure(P, torch, n, leaf, pts, a, F, nrhs, st, eps, k_cut, x_dense, reps=5):
     """The same workload with the extra compression of Sec. 3 (boxes with k > k_cut): factor
     time (compression included), solve time, stored bytes against the dense blocks they replace,
@@ -505,6 +543,8 @@ def run_ours(args):
                                                x_dev.cpu().numpy().T.copy())
         out["compressed"]["dense_solve_ms"] = solve_ms
         out["compressed"]["dense_bytes_factors"] = last_stats["bytes_factors"]
+    if not args.no_ti:
+        out["translation_invariant"] = ti_measure(P, torch, leaf, pts, F, nrhs, st, eps)
     if not args.no_per_box:
         out["per_box_fp64"] = per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps)
         out["per_box_fp64"]["batched_step_speedup"] = out["per_box_fp64"]["step_ms"] / (factor_ms + solve_ms)
