@@ -75,6 +75,7 @@ def _declare(L):
     L.ro_inverse.argtypes = [C.c_int, dp, C.c_int, dp]
     L.ro_factor.argtypes = [C.c_int, C.c_int, dp, dp, C.c_double, C.POINTER(_Opts), C.POINTER(C.c_void_p)]
     L.ro_solve.argtypes = [C.c_void_p, dp, C.c_int, dp]
+    L.ro_fwd_apply.argtypes = [C.c_void_p, dp, C.c_int, dp]
     L.ro_free.argtypes = [C.c_void_p]
     L.ro_depth.argtypes = [C.c_void_p]
     L.ro_box_sizes.argtypes = [C.c_void_p, C.c_int, C.c_int, ip, ip, ip, ip]
@@ -261,6 +262,22 @@ class Factorization:
         if rc:
             raise RuntimeError("ro_solve failed: %d" % rc)
         return X[:, 0] if one else np.ascontiguousarray(X)
+
+    def fwd_apply(self, x):
+        """y = A x through the HSS form the factorization's IDs define (O(N), error ~ eps).
+        x: (N,) or (N, nrhs) in grid order."""
+        N = self.n * self.n
+        x = np.asarray(x)
+        one = x.ndim == 1
+        X = x.reshape(N, -1)
+        dt = np.complex128 if self.cplx else np.float64
+        Xc = np.asfortranarray(X.astype(dt))
+        Y = np.zeros_like(Xc)
+        rc = self._L.ro_fwd_apply(self._p, Xc.ctypes.data_as(C.POINTER(C.c_double)), X.shape[1],
+                                  Y.ctypes.data_as(C.POINTER(C.c_double)))
+        if rc:
+            raise RuntimeError("ro_fwd_apply failed: %d" % rc)
+        return Y[:, 0] if one else np.ascontiguousarray(Y)
 
     def sizes(self, level, box):
         m, k, r, nn = C.c_int(), C.c_int(), C.c_int(), C.c_int()

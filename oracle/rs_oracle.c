@@ -525,6 +525,23 @@ int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps
     return 0;
 }
 
+int ro_fwd_apply(const ro_op* op, const double* x, int nrhs, double* y)
+{
+    if (!op || !x || !y || nrhs < 1 || op->partial || op->opts.k_cut > 0) return -1;
+    if (op->opts.kind == 0) return fwd_sym_d(op, x, nrhs, y);
+    int64_t N = (int64_t)op->n * op->n;
+    const double complex* xz = (const double complex*)x;
+    double complex* yz = (double complex*)y;
+    double complex* xs = (double complex*)malloc(sizeof(double complex) * (size_t)N * nrhs);
+    for (int c = 0; c < nrhs; ++c)
+        for (int64_t g = 0; g < N; ++g) xs[(size_t)c * N + g] = xz[(size_t)c * N + g] / op->s[g];
+    int rc = fwd_sym_z(op, xs, nrhs, yz);     /* A = S A_s S^{-1} (the symmetric form) */
+    for (int c = 0; c < nrhs; ++c)
+        for (int64_t g = 0; g < N; ++g) yz[(size_t)c * N + g] *= op->s[g];
+    free(xs);
+    return rc;
+}
+
 int ro_solve(const ro_op* op, const double* f, int nrhs, double* x)
 {
     if (!op || !f || !x || nrhs < 1 || op->partial) return -1;

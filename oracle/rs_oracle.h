@@ -81,6 +81,11 @@ int ro_inverse(int cplx, const double* A, int m, double* Ainv);
  * or NULL (= 1). */
 int ro_factor(int n, int leaf_side, const double* a, const double* b, double eps,
               const ro_opts* opts, ro_op** out);
+/* y = A x through the HSS form of A that the factorization's IDs define (skeleton
+ * interactions between siblings at every level, the IDs' T on both sides, dense leaf blocks):
+ * the O(N) forward operator of the compressed matrix.  Its error against A x is of the order
+ * of eps.  Refused for a partial factorization and with k_cut > 0.  x, y as for ro_solve. */
+int ro_fwd_apply(const ro_op* op, const double* x, int nrhs, double* y);
 /* Inverse apply (Algorithm 6).  f, x: N x nrhs column-major in grid order. */
 int ro_solve(const ro_op* op, const double* f, int nrhs, double* x);
 void ro_free(ro_op* op);

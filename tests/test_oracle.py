@@ -319,6 +319,9 @@ def _pins_fail(O):
         Ft = O.Factorization(n, leaf, 1e-10, ti=True)       # translation-invariant mode
         if np.linalg.norm(Ft.solve(f) - xd) > 1e-9 * np.linalg.norm(xd):
             return True
+        Af = D.laplace(n) @ f                                # forward HSS apply
+        if np.linalg.norm(Fp.fwd_apply(f) - Af) > 1e-9 * np.linalg.norm(Af):
+            return True
         rng = np.random.default_rng(7)
         Y, _ = _lowrank(rng, 70, 60)
         k, perm, T = O.interp_decomp(Y, 1e-8)
@@ -340,7 +343,7 @@ def _pins_fail(O):
     return False
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_planted_mistake_is_caught(oracle_mod, tmp_path, plant):
     path = oracle_mod.build(plant=plant, out=str(tmp_path / ("plant%d.so" % plant)))
     L = oracle_mod.load(path)
