@@ -157,6 +157,17 @@ int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, dou
  * staged through device memory inside the call).  x may not alias f.  The call returns
  * after x is written (host) or after the work is enqueued on `stream` (device). */
 int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
+/* Forward apply y = A x through the HSS form of A that the factorization's IDs define: the
+ * off-diagonal blocks A(I_i, I_j) ~ L_i A(sk_i, sk_j) R_j (Sec. 2.2, the ID of Eq. 2.1 on both
+ * sides), nested level by level (the telescoping form of Eq. 2.9), with the two children's
+ * mutual blocks at every level and the leaves' diagonal blocks generated on the fly.  O(N) work
+ * and no storage beyond the factor's T; its error against A x is of the order of eps (for
+ * Helmholtz, in the symmetric form), and rs_solve inverts it to rounding.  x, y: as f, x of
+ * rs_solve (y may not alias x).  RS_E_INVALID for operators with compressed boxes
+ * (opts.k_cut > 0).  The call returns after y is written (host) or after the work is
+ * enqueued on `stream` (device); it shares the operator's solve workspace, so it must not
+ * run concurrently with rs_solve on the same operator. */
+int rs_fwd_apply(rs_op* op, const void* x, int64_t nrhs, void* y, void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of
  * its requests) still references it; NULL is accepted. */
 int rs_free(rs_op* op);

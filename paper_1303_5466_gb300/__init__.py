@@ -80,6 +80,7 @@ def lib():
         L.rs_tree_level_sets.argtypes = [vp, C.c_int, i64p, i64p, C.c_double, i64p, i64p, i64p, i64p]
         L.rs_factor.argtypes = [vp, C.POINTER(rs_kernel), dp, C.c_double, C.POINTER(rs_opts), vp, C.POINTER(vp)]
         L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.rs_fwd_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_free.argtypes = [vp]
         L.rs_server_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t, C.c_int, C.POINTER(vp)]
         L.rs_server_submit.argtypes = [vp, C.c_int, vp, C.c_int64, vp, C.POINTER(C.c_uint64)]
@@ -209,6 +210,12 @@ def rs_solve(op, f, nrhs, x, stream=None):
     """x = A^{-1} f; f and x are both host (numpy) or both device (torch CUDA) buffers holding
     N x nrhs column-major values in input order."""
     _check(lib().rs_solve(op, _ptr(f), int(nrhs), _ptr(x), _stream(stream)))
+
+
+def rs_fwd_apply(op, x, nrhs, y, stream=None):
+    """y = A x through the HSS form the factorization's IDs define (O(N); x, y: both host or
+    both device, N x nrhs column-major in input order)."""
+    _check(lib().rs_fwd_apply(op, _ptr(x), int(nrhs), _ptr(y), _stream(stream)))
 
 
 def rs_solve_noalloc(op, f, nrhs, x, stream=None):
@@ -462,6 +469,14 @@ class Solver:
         x = np.zeros_like(fa, order="F")
         rs_solve(self.op, fa, nrhs, x, stream)
         return x
+
+    def fwd_apply(self, v):
+        """A v through the HSS form of the factorization (numpy (N,) / (N, nrhs))."""
+        va = np.asfortranarray(np.asarray(v, dtype=np.complex128 if self.complex else np.float64))
+        nrhs = 1 if va.ndim == 1 else va.shape[1]
+        y = np.zeros_like(va, order="F")
+        rs_fwd_apply(self.op, va, nrhs, y)
+        return y
 
     def stats(self):
         return rs_op_stats(self.op)

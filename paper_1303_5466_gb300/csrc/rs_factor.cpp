@@ -1433,6 +1433,172 @@ int apply_graph(rs_op* op, const double* fd, double* xd, int64_t nrhs, cudaStrea
     return RS_OK;
 }
 
+// ------------------------------------------------------------------ forward apply
+// y = A x through the HSS form of A that the factorization's IDs define: the off-diagonal
+// blocks A(I_i, I_j) ~ L_i A(sk_i, sk_j) R_j (Sec. 2.2, the ID of Eq. 2.1 on both sides of the
+// symmetric form), nested level by level as in the telescoping form of Eq. 2.9:
+//   up:   xh_i = u_i(sk) + T_i u_i(rs), u_i = x(I_i) at a leaf and [xh_c1; xh_c2] above;
+//   root: yh of the two level-1 boxes = [A(sk_1, sk_2) xh_2; A(sk_2, sk_1) xh_1];
+//   down: z_i = L_i yh_i (z(sk) = yh_i, z(rs) = T_i^T yh_i); above the leaves z_i plus the
+//         children's mutual blocks gives yh_c1, yh_c2; at a leaf y(I_i) = A(I_i, I_i) x + z_i.
+// The T products reuse the solve's descriptors; the blocks of A are generated on the fly.
+
+int fw_plan(rs_op* op, cudaStream_t st)
+{
+    if (op->fw_built) return RS_OK;
+    const int RB = kblock_rows_per_block();
+    auto add = [&](std::vector<KbProb>& v, std::vector<int64_t>& blk, int64_t& nblk, int64_t rows, int64_t cols,
+                   int64_t r_off, int64_t c_off, int64_t x_off, int64_t y_off) {
+        if (rows <= 0 || cols <= 0) return;
+        KbProb p{};
+        p.rows = (int)rows; p.cols = (int)cols;
+        p.r_off = r_off; p.c_off = c_off; p.x_off = x_off; p.y_off = y_off;
+        v.push_back(p);
+        blk.push_back(nblk);
+        nblk += (rows + RB - 1) / RB;
+    };
+    int rc;
+    for (int l = 0; l < op->d; ++l) {
+        Level& P = op->lev[l];
+        const Level& C = op->lev[l + 1];
+        std::vector<KbProb> v;
+        std::vector<int64_t> blk;
+        int64_t nblk = 0;
+        for (int b = 0; b < P.nb; ++b) {
+            const int c1 = 2 * b, c2 = 2 * b + 1;
+            add(v, blk, nblk, C.k[c1], C.k[c2], C.k_off[c1], C.k_off[c2], C.k_off[c2], C.k_off[c1]);
+            add(v, blk, nblk, C.k[c2], C.k[c1], C.k_off[c2], C.k_off[c1], C.k_off[c1], C.k_off[c2]);
+        }
+        if ((rc = upload(P.d_fw_pts, to32(C.skel), st))) return rc;
+        if ((rc = upload(P.d_fw_sib, v, st))) return rc;
+        if ((rc = upload(P.d_fw_sib_blk, blk, st))) return rc;
+        P.n_fw_sib = (int)v.size();
+        P.b_fw_sib = nblk;
+    }
+    Level& L = op->lev[op->d];
+    std::vector<int64_t> pts(L.act.size());
+    std::vector<KbProb> v;
+    std::vector<int64_t> blk;
+    int64_t nblk = 0;
+    for (int b = 0; b < L.nb; ++b) {
+        const int64_t a0 = L.act_off[b], m = L.m[b];
+        for (int64_t p = 0; p < m; ++p) pts[a0 + p] = L.act[a0 + L.perm[a0 + p]];
+        add(v, blk, nblk, m, m, a0, a0, a0, a0);
+    }
+    if ((rc = upload(L.d_fw_leaf_pts, to32(pts), st))) return rc;
+    if ((rc = upload(L.d_fw_leaf, v, st))) return rc;
+    if ((rc = upload(L.d_fw_leaf_blk, blk, st))) return rc;
+    L.n_fw_leaf = (int)v.size();
+    L.b_fw_leaf = nblk;
+    op->fw_built = true;
+    return RS_OK;
+}
+
+template <class T>
+int fwd_run_t(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const typename sc_traits<T>::io* xd,
+              typename sc_traits<T>::io* yd, int64_t nrhs, cudaStream_t st)
+{
+    using IO = typename sc_traits<T>::io;
+    const int64_t N = op->N;
+    const int d = op->d;
+    const std::vector<int64_t>& goff = Ls.goff;
+    T* Gb = (T*)ws.g;
+    T* Ph = (T*)ws.phi;
+    T* U = (T*)ws.u;
+    T* Z = (T*)ws.out;
+    T* Ud = (T*)ws.w + Ls.woff[d] * nrhs;          // the leaf values of x, kept for the leaf blocks
+    const int nr = (int)nrhs;
+    const double* a = op->d_a.as<double>();
+    auto mv = [&](const DevMem& probs, const DevMem& blk0, int np, int64_t nblk, int rb, const T* A, const T* x,
+                  T* y) -> int {
+        RS_CUDA(launch_matvec<T>(st, probs.as<MatvecProb>(), blk0.as<int64_t>(), np, nblk, A, x, y, nr, rb));
+        return RS_OK;
+    };
+    int rc;
+    for (int l = d; l >= 1; --l) {
+        Level& L = op->lev[l];
+        T* ul = U;
+        if (l == d) {
+            RS_CUDA(launch_gather_cm<IO, T>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), xd, N, Ud, nr));
+            ul = Ud;
+        } else {
+            RS_CUDA(launch_gather_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Gb + goff[l + 1] * nrhs, U, nr));
+        }
+        T* gl = Gb + goff[l] * nrhs;
+        RS_CUDA(launch_gather_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), ul, gl, nr));
+        if ((rc = mv(L.d_mv_T, L.d_mv_T_blk, L.n_mv_T, L.b_mv_T, L.rb_T, L.d_T.as<T>(), ul, gl))) return rc;
+    }
+    {
+        Level& R = op->lev[0];
+        RS_CUDA(cudaMemsetAsync(Ph + goff[1] * nrhs, 0, sizeof(T) * (size_t)(op->lev[1].sum_k * nrhs), st));
+        RS_CUDA(launch_kblock_mv<T>(st, R.d_fw_sib.as<KbProb>(), R.d_fw_sib_blk.as<int64_t>(), R.n_fw_sib, R.b_fw_sib,
+                                    R.d_fw_pts.as<int32_t>(), Gb + goff[1] * nrhs, Ph + goff[1] * nrhs, nr, op->K, a));
+    }
+    for (int l = 1; l <= d; ++l) {
+        Level& L = op->lev[l];
+        T* pl = Ph + goff[l] * nrhs;
+        RS_CUDA(launch_scatter_rows<T>(st, L.sum_k, L.d_idx_sk.as<int64_t>(), pl, Z, nr));
+        if ((rc = mv(L.d_mv_Tt, L.d_mv_Tt_blk, L.n_mv_Tt, L.b_mv_Tt, L.rb_Tt, L.d_T.as<T>(), pl, Z))) return rc;
+        if (l < d) {
+            T* pc = Ph + goff[l + 1] * nrhs;
+            RS_CUDA(launch_scatter_rows<T>(st, L.sum_m, L.d_idx_up.as<int64_t>(), Z, pc, nr));
+            RS_CUDA(launch_kblock_mv<T>(st, L.d_fw_sib.as<KbProb>(), L.d_fw_sib_blk.as<int64_t>(), L.n_fw_sib,
+                                        L.b_fw_sib, L.d_fw_pts.as<int32_t>(), Gb + goff[l + 1] * nrhs, pc, nr,
+                                        op->K, a));
+        } else {
+            RS_CUDA(launch_kblock_mv<T>(st, L.d_fw_leaf.as<KbProb>(), L.d_fw_leaf_blk.as<int64_t>(), L.n_fw_leaf,
+                                        L.b_fw_leaf, L.d_fw_leaf_pts.as<int32_t>(), Ud, Z, nr, op->K, a));
+            RS_CUDA(launch_scatter_cm<T, IO>(st, L.sum_m, L.d_idx_leaf.as<int64_t>(), Z, N, yd, nr));
+        }
+    }
+    return RS_OK;
+}
+
+int fwd_impl(rs_op* op, const void* x, int64_t nrhs, void* y, cudaStream_t st)
+{
+    const int64_t N = op->N;
+    for (int l = 1; l <= op->d; ++l)
+        if (!op->lev[l].cmp.empty())
+            for (char c : op->lev[l].cmp)
+                if (c) return fail(RS_E_INVALID, "the forward apply needs the dense T of every box (k_cut = 0)");
+    const bool dev_x = is_device_ptr(x), dev_y = is_device_ptr(y);
+    if (dev_x != dev_y) return fail(RS_E_INVALID, "x and y must both be device or both be host pointers");
+    const size_t io = op->kind == RS_HELMHOLTZ ? 2 * sizeof(double) : sizeof(double);
+    const double* xd = (const double*)x;
+    double* yd = (double*)y;
+    if (!dev_x) {
+        RS_CUDA(op->s_in.alloc(io * (size_t)(N * nrhs)));
+        RS_CUDA(cudaMemcpyAsync(op->s_in.p, x, io * (size_t)(N * nrhs), cudaMemcpyHostToDevice, st));
+        xd = op->s_in.as<double>();
+        RS_CUDA(op->s_out2.alloc(io * (size_t)(N * nrhs)));
+        yd = op->s_out2.as<double>();
+    }
+    int rc = fw_plan(op, st);
+    if (rc) return rc;
+    SolveLayout Ls;
+    SolveWork ws;
+    if ((rc = solve_workspace(op, nrhs, Ls, ws))) return rc;
+    using Zc = cplx<double>;
+    if (op->kind == RS_HELMHOLTZ) {      // A = S A_s S^{-1}: the symmetric form between two scalings
+        RS_CUDA(launch_scale_cm<Zc>(st, N, (int)nrhs, op->d_s_in.as<double>(), -1, (const Zc*)xd, op->s_fs.as<Zc>()));
+        xd = op->s_fs.as<double>();
+    }
+    switch (op->opts.precision) {
+        case RS_MIXED_FP32: rc = fwd_run_t<float>(op, Ls, ws, xd, yd, nrhs, st); break;
+        case RS_C128: rc = fwd_run_t<cplx<double>>(op, Ls, ws, (const Zc*)xd, (Zc*)yd, nrhs, st); break;
+        case RS_C64_REFINED: rc = fwd_run_t<cplx<float>>(op, Ls, ws, (const Zc*)xd, (Zc*)yd, nrhs, st); break;
+        default: rc = fwd_run_t<double>(op, Ls, ws, xd, yd, nrhs, st); break;
+    }
+    if (rc) return rc;
+    if (op->kind == RS_HELMHOLTZ)
+        RS_CUDA(launch_scale_cm<Zc>(st, N, (int)nrhs, op->d_s_in.as<double>(), 1, (const Zc*)yd, (Zc*)yd));
+    if (!dev_x) {
+        RS_CUDA(cudaMemcpyAsync(y, yd, io * (size_t)(N * nrhs), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+    }
+    return RS_OK;
+}
+
 int solve_impl(rs_op* op, const void* f, int64_t nrhs, void* x, cudaStream_t st)
 {
     const int64_t N = op->N;
@@ -1480,6 +1646,17 @@ int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, dou
     *out = nullptr;
     if (!tree) return fail(RS_E_INVALID, "tree is NULL");
     return factor_impl(tree, kernel, a, eps, opts, (cudaStream_t)stream, out);
+}
+
+int rs_fwd_apply(rs_op* op, const void* x, int64_t nrhs, void* y, void* stream)
+{
+    if (!op || !x || !y || nrhs < 1) return fail(RS_E_INVALID, "bad argument");
+    if (nrhs > (int64_t)1 << 20) return fail(RS_E_INVALID, "nrhs too large");
+    if (x == y) return fail(RS_E_INVALID, "y may not alias x");
+    int dev = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
+    return fwd_impl(op, x, nrhs, y, (cudaStream_t)stream);
 }
 
 int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream)

@@ -142,6 +142,12 @@ struct Level {
     int64_t b_mv_phi = 0, b_mv_T = 0, b_mv_E = 0, b_mv_Tt = 0;
     int64_t sum_m = 0, sum_k = 0;
     double mvw_phi = 0, mvw_T = 0, mvw_E = 0, mvw_Tt = 0;   // sum of rows * cols per descriptor set
+    // forward apply (rs_fwd_apply), built on first use: the mutual blocks of each box's two
+    // children (points: the child level's skeletons, in k_off order) and, at the leaf level,
+    // the diagonal blocks (points: the leaf points in the permuted order)
+    DevMem d_fw_pts, d_fw_sib, d_fw_sib_blk, d_fw_leaf, d_fw_leaf_blk, d_fw_leaf_pts;
+    int n_fw_sib = 0, n_fw_leaf = 0;
+    int64_t b_fw_sib = 0, b_fw_leaf = 0;
     // translation-invariant modes: class of every box and the box factored for each class
     std::vector<int32_t> ti_cls;
     std::vector<int> ti_rep;
@@ -258,6 +264,7 @@ struct rs_op {
     // of lev[l] shares
     std::vector<rs::Level> ti_lev;
     double ti_s0 = 1.0;               // the constant Helmholtz scaling s = kappa sqrt(b) there
+    bool fw_built = false;            // forward-apply block lists uploaded
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // factor-time scratch reused across levels, released with the op
     rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2, t_ck, t_ce;

@@ -56,6 +56,13 @@ struct MatvecProb {
     double alpha, beta;
 };
 
+// One block product of the forward apply: y(y_off + i) += sum_j A(pts[r_off + i], pts[c_off + j])
+// x(x_off + j), i < rows, j < cols (vectors row-major with nrhs columns).
+struct KbProb {
+    int rows, cols;
+    int64_t r_off, c_off, x_off, y_off;
+};
+
 // ------------------------------------------------------------------ launchers (kernels.cu)
 // All launchers enqueue on `st`, return cudaError_t of the launch.
 
@@ -194,6 +201,14 @@ cudaError_t launch_scatter_cm(cudaStream_t st, int64_t count, const int64_t* idx
 template <class T>
 cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T* x, T b, T* y);
 // y[c N + i] = s[i]^pw x[c N + i], pw = +1 or -1 (instantiated for cplx<double>)
+// Block products of the forward apply (k_forward.cu): problem p owns blocks blk0[p] ..
+// of kblock_rows_per_block() rows each, nblk in all; entries from K (diagonal a_g + self where
+// a row and a column are the same point).
+template <class T>
+cudaError_t launch_kblock_mv(cudaStream_t st, const KbProb* probs, const int64_t* blk0, int np, int64_t nblk,
+                             const int32_t* pts, const T* x, T* y, int nrhs, const KernelK& K, const double* a);
+int kblock_rows_per_block();
+
 template <class T>
 cudaError_t launch_scale_cm(cudaStream_t st, int64_t N, int nrhs, const double* sc, int pw, const T* x, T* y);
 
