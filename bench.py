@@ -313,6 +313,24 @@ def per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps):
     return out
 
 
+def fwd_measure(P, torch, op, x_dev, f_dev, nrhs, st, reps=5):
+    """rs_fwd_apply (y = A x through the HSS form of the factorization, O(N)) on the solution of
+    the timed solve: its time for nrhs columns, and the paper's error measure
+    |f - A (A^{-1} f)| / |f| with A applied that way (rs_solve inverts it to rounding)."""
+    import numpy as np
+    y = torch.empty_like(x_dev)
+    P.rs_fwd_apply(op, x_dev, nrhs, y, st)
+    torch.cuda.synchronize()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(st)
+    for _ in range(reps):
+        P.rs_fwd_apply(op, x_dev, nrhs, y, st)
+    e1.record(st)
+    e1.synchronize()
+    err = (torch.linalg.norm(y - f_dev, dim=1) / torch.linalg.norm(f_dev, dim=1)).max().item()
+    return {"ms": e0.elapsed_time(e1) / reps, "nrhs": nrhs, "error_vs_f": err}
+
+
 def ti_measure(P, torch, leaf, pts, F, nrhs, st, eps):
     """The translation-invariant modes (Sec. 5: one set of matrix blocks per level) on the same
     grid with a = 1, against the per-box-result factorization of that operator: factor and
@@ -532,10 +550,18 @@ def run_ours(args):
         "clocks": clk.summary(),
         "autotune": tune,
     }
-    # FP64 residual of the timed solve (direct sum over all pairs)
+    # FP64 residual of the timed solve (direct sum over all pairs), and the forward apply
+    # through the factorization's HSS form beside it
     tree, op = step()
     P.rs_solve(op, f_dev, nrhs, x_dev, st)
+    torch.cuda.synchronize()
+    r0, r1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    r0.record(st)
     out["residual_fp64"] = float(P.rs_residual(op, x_dev, f_dev, nrhs, st).max())
+    r1.record(st)
+    r1.synchronize()
+    out["forward_apply"] = fwd_measure(P, torch, op, x_dev, f_dev, nrhs, st)
+    out["forward_apply"]["direct_sum_residual_ms"] = r0.elapsed_time(r1)
     P.rs_free(op)
     P.rs_free_tree(tree)
     if args.k_cut > 0:

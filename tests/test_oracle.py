@@ -287,8 +287,11 @@ def test_E_equals_four_term_formula(oracle_mod):
 
 
 def test_error_measure_consistent_with_paper_table(oracle_mod):
-    """Table 5.3 prints E <= 1.8e-14 for N <= 3136 at eps = 1e-10; our true residual at the
-    nearest sizes (N = 1024, 4096) stays within 100x of the printed error."""
+    """Table 5.3 prints E <= 1.8e-14 for N <= 3136 at eps = 1e-10.  With A the compressed
+    forward operator (the HSS form of the factorization's IDs, Factorization.fwd_apply), the
+    paper's measure E = |v - A A^{-1} v| / |v| at the nearest sizes (N = 1024, 4096) is at or
+    below the printed value: the dense-block inverse is exact for that operator.  The true
+    residual (brute-force A) stays within 100x of it."""
     rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_inverse_apply_error.txt"))
     for n, leaf in ((32, 8), (64, 8)):
         N = n * n
@@ -296,6 +299,8 @@ def test_error_measure_consistent_with_paper_table(oracle_mod):
         F = oracle_mod.Factorization(n, leaf, 1e-10)
         f = W.rhs_uniform(n, 0)
         x = F.solve(f)
+        E = np.linalg.norm(F.fwd_apply(x) - f) / np.linalg.norm(f)
+        assert E <= ref
         res = np.linalg.norm(oracle_mod.matvec(n, x) - f) / np.linalg.norm(f)
         assert res <= 100 * ref
 
