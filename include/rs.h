@@ -115,6 +115,11 @@ typedef struct {
                                     factored once: ~13-24 per level at any grid size).
                                     Refused with varying a or b, with k_cut > 0, and for
                                     9 N > 2^31 - 1 (mode 1)                           [0]    */
+    int forward_only;            /* 1: the tree build alone (the IDs of every level, Sec. 2.2):
+                                    the operator serves rs_fwd_apply (the compressed forward
+                                    operator), rs_residual and rs_bicgstab's matvec, not
+                                    rs_solve.  Not with translation_invariant, k_cut or
+                                    per_box                                           [0]    */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);
@@ -168,6 +173,18 @@ int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
  * enqueued on `stream` (device); it shares the operator's solve workspace, so it must not
  * run concurrently with rs_solve on the same operator. */
 int rs_fwd_apply(rs_op* op, const void* x, int64_t nrhs, void* y, void* stream);
+/* The preconditioned iterative solver of Sec. 5.4: BiCGstab on A x = f with the right
+ * preconditioner M^{-1} (A M^{-1} y = f, x = M^{-1} y), one right-hand side.  A is applied
+ * through its HSS form (rs_fwd_apply; a forward_only operator gives the tree build alone), M^{-1}
+ * through rs_solve(M) -- e.g. A the Lippmann-Schwinger operator (Helmholtz, b varying) and M
+ * the translation-invariant Helmholtz operator (b = 1).  f, x: device pointers, N values in
+ * input order (double, or interleaved complex128 for Helmholtz); x may not alias f.  Stops when
+ * the recursive residual |f - A x| / |f| (with A the HSS form) is at most tol; iters and
+ * rel_res (host) report the iterations and that residual.  RS_E_NOT_CONVERGED after max_iter
+ * iterations or on a breakdown (x then holds the last iterate).  Synchronous.  A and M must
+ * share N and the kernel kind; M must be factored (not forward_only). */
+int rs_bicgstab(rs_op* A, rs_op* M, const void* f, void* x, double tol, int max_iter, int* iters, double* rel_res,
+                void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of
  * its requests) still references it; NULL is accepted. */
 int rs_free(rs_op* op);

@@ -42,7 +42,7 @@ class rs_opts(C.Structure):
                 ("spin_limit", C.c_int64), ("profile", C.c_int), ("hss_leaf", C.c_int),
                 ("hss_eps", C.c_double), ("solve_graph", C.c_int),
                 ("per_box", C.c_int), ("spd_inverse", C.c_int), ("cpqr_variant", C.c_int),
-                ("translation_invariant", C.c_int)]
+                ("translation_invariant", C.c_int), ("forward_only", C.c_int)]
 
 
 class rs_stats(C.Structure):
@@ -81,6 +81,8 @@ def lib():
         L.rs_factor.argtypes = [vp, C.POINTER(rs_kernel), dp, C.c_double, C.POINTER(rs_opts), vp, C.POINTER(vp)]
         L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_fwd_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.rs_bicgstab.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double), vp]
         L.rs_free.argtypes = [vp]
         L.rs_server_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t, C.c_int, C.POINTER(vp)]
         L.rs_server_submit.argtypes = [vp, C.c_int, vp, C.c_int64, vp, C.POINTER(C.c_uint64)]
@@ -216,6 +218,16 @@ def rs_fwd_apply(op, x, nrhs, y, stream=None):
     """y = A x through the HSS form the factorization's IDs define (O(N); x, y: both host or
     both device, N x nrhs column-major in input order)."""
     _check(lib().rs_fwd_apply(op, _ptr(x), int(nrhs), _ptr(y), _stream(stream)))
+
+
+def rs_bicgstab(A, M, f, x, tol=1e-10, max_iter=100, stream=None):
+    """x = A^{-1} f by BiCGstab with the right preconditioner M^{-1} (Sec. 5.4); f, x device
+    buffers (torch CUDA, N values).  Returns (iterations, relative residual).  Raises RsError
+    (RS_E_NOT_CONVERGED) when max_iter is reached."""
+    it, rel = C.c_int(), C.c_double()
+    _check(lib().rs_bicgstab(A, M, _ptr(f), _ptr(x), float(tol), int(max_iter), C.byref(it), C.byref(rel),
+                             _stream(stream)))
+    return it.value, rel.value
 
 
 def rs_solve_noalloc(op, f, nrhs, x, stream=None):

@@ -985,6 +985,7 @@ void compute_stats(rs_op* op)
             if (!fac[b]) continue;
             ff += 4.0 * r * m * k - 2.0 * k * k * (r + m) + 4.0 * k * k * k / 3.0;   // CPQR, k steps
             ff += k * k * (m - k);                                                // T = R11^{-1} R12
+            if (op->opts.forward_only) continue;
             ff += inv * m * m * m;                                                // F^{-1}
             ff += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;                  // W, E^{-1}
             ff += inv * k * k * k;                                                // E
@@ -1001,9 +1002,11 @@ void compute_stats(rs_op* op)
         bytes += L.act_off.back() * 8 + L.nb * 64;
     }
     const double m0 = (double)op->lev[0].m[0];
-    ff += inv * m0 * m0 * m0;
-    sw += m0 * m0;
-    bytes += (int64_t)(m0 * m0 * op->esz);
+    if (!op->opts.forward_only) {
+        ff += inv * m0 * m0 * m0;
+        sw += m0 * m0;
+        bytes += (int64_t)(m0 * m0 * op->esz);
+    }
     bytes += op->cstore_n * op->esz;
     s.flops_factor = ff;
     s.flops_solve_per_rhs = 2.0 * sw;
@@ -1038,8 +1041,16 @@ int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
     }
     op->stats.ms_tree = ms_since(t0);
     auto t1 = Clock::now();
+    const bool fwd_only = op->opts.forward_only != 0;
     for (int l = op->d; l >= 1; --l) {
         const Level* child = l < op->d ? &op->lev[l + 1] : nullptr;
+        if (fwd_only) {             // the tree build alone: no F^{-1}, no E
+            Level& L = op->lev[l];
+            L.phi_off.assign(L.nb + 1, 0);
+            L.e_off.assign(L.nb + 1, 0);
+            L.w_off.assign(L.nb + 1, 0);
+            continue;
+        }
         rc = op->opts.translation_invariant ? inverse_level_ti<T>(op, l, st)
                                             : inverse_level<T>(op, op->lev[l], child, st);
         if (rc) return rc;
@@ -1058,7 +1069,8 @@ int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
     if ((rc = upload(R.d_act_off, R.act_off, st))) return rc;
     if ((rc = upload(R.d_perm, R.perm, st))) return rc;
     if ((rc = upload(R.d_m, to32(R.m), st))) return rc;
-    if ((rc = inverse_level<T>(op, R, &op->lev[1], st))) return rc;
+    if (fwd_only) R.phi_off = {0, 0};
+    else if ((rc = inverse_level<T>(op, R, &op->lev[1], st))) return rc;
     if ((rc = compress_levels<T>(op, st))) return rc;
     for (int l = 0; l <= op->d; ++l)
         if ((rc = solve_plan(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;
@@ -1108,6 +1120,8 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
     if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 2) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 2");
+    if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))
+        return fail(RS_E_INVALID, "forward_only combines with none of translation_invariant, k_cut, per_box");
     if (op->opts.translation_invariant < 0 || op->opts.translation_invariant > 2)
         return fail(RS_E_INVALID, "translation_invariant must be 0, 1 or 2");
     if (op->opts.translation_invariant) {
@@ -1664,6 +1678,7 @@ int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream)
     if (!op || !f || !x || nrhs < 1) return fail(RS_E_INVALID, "bad argument");
     if (nrhs > (int64_t)1 << 20) return fail(RS_E_INVALID, "nrhs too large");
     if (f == x) return fail(RS_E_INVALID, "x may not alias f");
+    if (op->opts.forward_only) return fail(RS_E_INVALID, "a forward-only operator has no inverse");
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");

@@ -209,6 +209,15 @@ cudaError_t launch_kblock_mv(cudaStream_t st, const KbProb* probs, const int64_t
                              const int32_t* pts, const T* x, T* y, int nrhs, const KernelK& K, const double* a);
 int kblock_rows_per_block();
 
+// Vector kernels of BiCGstab (k_krylov.cu), T = double or cplx<double>: *out = sum conj(a_i) b_i
+// (part: dot_partials() scratch entries; fixed summation order), y = c0 x0 + c1 x1 + c2 x2.
+template <class T>
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const T* a, const T* b, T* part, T* out);
+int dot_partials();
+template <class T>
+cudaError_t launch_lincomb(cudaStream_t st, int64_t n, T c0, const T* x0, T c1, const T* x1, T c2, const T* x2,
+                           T* y);
+
 template <class T>
 cudaError_t launch_scale_cm(cudaStream_t st, int64_t N, int nrhs, const double* sc, int pw, const T* x, T* y);
 

@@ -49,8 +49,8 @@ extern "C" int rs_solve_noalloc(rs_op* op, const void* f, int64_t nrhs, void* x,
 {
     if (!op || !f || !x || nrhs < 1) return fail(RS_E_INVALID, "bad argument");
     if (f == x) return fail(RS_E_INVALID, "x may not alias f");
-    if (op->kind != RS_LAPLACE || op->opts.precision != RS_FP64)
-        return fail(RS_E_INVALID, "rs_solve_noalloc covers real FP64 (RS_FP64 Laplace) operators");
+    if (op->kind != RS_LAPLACE || op->opts.precision != RS_FP64 || op->opts.forward_only)
+        return fail(RS_E_INVALID, "rs_solve_noalloc covers real FP64 (RS_FP64 Laplace) factored operators");
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");

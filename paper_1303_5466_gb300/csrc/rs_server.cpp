@@ -305,9 +305,9 @@ int rs_server_create(rs_op* const* ops, int n_ops, size_t mem_budget_bytes, int 
     rs_server* s = new (std::nothrow) rs_server();
     if (!s) return fail(RS_E_NOMEM, "host allocation");
     for (int i = 0; i < n_ops; ++i) {
-        if (!ops[i] || ops[i]->kind != RS_LAPLACE || ops[i]->opts.precision != RS_FP64) {
+        if (!ops[i] || ops[i]->kind != RS_LAPLACE || ops[i]->opts.precision != RS_FP64 || ops[i]->opts.forward_only) {
             delete s;
-            return fail(RS_E_INVALID, "the server batches real FP64 operators");
+            return fail(RS_E_INVALID, "the server batches real FP64 factored operators");
         }
         if (ops[i]->cstore_n > 0) {
             delete s;

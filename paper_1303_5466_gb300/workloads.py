@@ -12,6 +12,9 @@ grid order g = i1 + n*i2):
   laplace_mixed   n=1024, leaf 16, eps 1e-6 (FP32 factor) + FP64 refinement, f ~ U[-1,1] (seed 2)
   serving         n = 128, 256, 512, leaf 16, eps 1e-10; Poisson stream of 10k requests (seed 3)
   helmholtz_ls    n=256,  leaf 16, kappa 25, b = exp(-40 |x - (1/2,1/2)|^2), f = exp(i kappa x1)
+  helmholtz_ls_plateau  n=256, leaf 16, kappa 25, the test problem's b of Sec. 5.4 (a plateau
+                  b = 1 with a tanh fall-off at the boundary; coeff_b_plateau), f = exp(i kappa x1):
+                  the iterative solver with the b = 1 preconditioner
 """
 import numpy as np
 
@@ -22,6 +25,7 @@ WORKLOADS = {
     # a quarter-size copy of laplace_batched for profiling runs (same leaf, eps, a, RHS recipe)
     "laplace_n256": dict(n=256, leaf=16, eps=1e-10, nrhs=4, seed=1),
     "helmholtz_ls": dict(n=256, leaf=16, eps=1e-5, nrhs=1, seed=None, kappa=25.0),
+    "helmholtz_ls_plateau": dict(n=256, leaf=16, eps=1e-10, nrhs=1, seed=None, kappa=25.0),
 }
 
 
@@ -44,6 +48,16 @@ def coeff_b_gaussian(n, width=40.0):
     """b(x) = exp(-width |x - (1/2, 1/2)|^2) on the grid (the Lippmann-Schwinger workload)."""
     p = grid_points(n)
     return np.exp(-width * ((p[:, 0] - 0.5) ** 2 + (p[:, 1] - 0.5) ** 2))
+
+
+def coeff_b_plateau(n, D=20.0, e=0.1):
+    """The scatterer of the Lippmann-Schwinger test problem of Sec. 5.4, without its k^2 factor
+    (the kernel carries kappa^2): b = (1/4)(1 + tanh D(1 - e - |xi1|))(1 + tanh D(1 - e - |xi2|))
+    with xi = 2x - 1 mapping [0,1]^2 onto the paper's [-1,1]^2.  b is 1 on most of the square and
+    falls off in a layer at its boundary (D and e are not given in the paper)."""
+    p = grid_points(n)
+    xi1, xi2 = 2.0 * p[:, 0] - 1.0, 2.0 * p[:, 1] - 1.0
+    return 0.25 * (1.0 + np.tanh(D * (1.0 - e - np.abs(xi1)))) * (1.0 + np.tanh(D * (1.0 - e - np.abs(xi2))))
 
 
 def rhs_uniform(n, seed, nrhs=1):
