@@ -331,6 +331,57 @@ def fwd_measure(P, torch, op, x_dev, f_dev, nrhs, st, reps=5):
     return {"ms": e0.elapsed_time(e1) / reps, "nrhs": nrhs, "error_vs_f": err}
 
 
+def ls_measure(P, torch, st):
+    """The Lippmann-Schwinger test problem of Sec. 5.4 (plateau scatterer, kappa 25, 256^2) two
+    ways: the iterative route (tree build of A alone, the translation-invariant Helmholtz
+    inverse as right preconditioner, BiCGstab with A through its HSS form) and the direct route
+    (complex64 factor at eps 1e-5 refined to 1e-10 with the complex128 direct sum).  Times,
+    iterations and the true residuals."""
+    import numpy as np
+    from paper_1303_5466_gb300 import workloads as W
+    cfg = W.WORKLOADS["helmholtz_ls_plateau"]
+    n, leaf, kappa = cfg["n"], cfg["leaf"], cfg["kappa"]
+    b = W.coeff_b_plateau(n)
+    f = W.rhs_plane_wave(n, kappa)
+    fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    xd = torch.zeros_like(fd)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    tree = P.rs_build_tree(W.grid_points(n), leaf)
+    out = {"n": n, "kappa": kappa, "scatterer": "plateau (coeff_b_plateau)"}
+    oa = P.rs_opts_default(); oa.precision = P.RS_C128; oa.forward_only = 1
+    om = P.rs_opts_default(); om.precision = P.RS_C128; om.translation_invariant = 2
+    torch.cuda.synchronize()
+    e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+    e0.record(st)
+    A = P.rs_factor(tree, eps=cfg["eps"], opts=oa, stream=st, kappa=kappa, b=b)
+    e1.record(st)
+    M = P.rs_factor(tree, eps=cfg["eps"], opts=om, stream=st, kappa=kappa)
+    e2.record(st)
+    it, rel = P.rs_bicgstab(A, M, fd, xd, tol=1e-10, max_iter=200, stream=st)
+    e3.record(st)
+    e3.synchronize()
+    res = float(P.rs_residual(A, xd.cpu().numpy(), f, 1)[0])
+    out["iterative"] = {"tree_build_ms": e0.elapsed_time(e1), "preconditioner_factor_ms": e1.elapsed_time(e2),
+                        "bicgstab_ms": e2.elapsed_time(e3), "iterations": it, "hss_residual": rel,
+                        "true_residual_fp64": res}
+    od = P.rs_opts_default(); od.precision = P.RS_C64_REFINED; od.refine_max_iter = 12
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(st)
+    D = P.rs_factor(tree, eps=1e-5, opts=od, stream=st, kappa=kappa, b=b)
+    e1.record(st)
+    xd2 = torch.zeros_like(fd)
+    P.rs_solve(D, fd, 1, xd2, st)
+    e2.record(st)
+    e2.synchronize()
+    st_d = P.rs_op_stats(D)
+    out["direct_refined"] = {"factor_ms": e0.elapsed_time(e1), "refined_solve_ms": e1.elapsed_time(e2),
+                             "refine_iters": st_d["refine_iters"], "true_residual_fp64": st_d["refine_residual"]}
+    for op in (A, M, D):
+        P.rs_free(op)
+    P.rs_free_tree(tree)
+    return out
+
+
 def ti_measure(P, torch, leaf, pts, F, nrhs, st, eps):
     """The translation-invariant modes (Sec. 5: one set of matrix blocks per level) on the same
     grid with a = 1, against the per-box-result factorization of that operator: factor and
@@ -571,6 +622,7 @@ def run_ours(args):
         out["compressed"]["dense_bytes_factors"] = last_stats["bytes_factors"]
     if not args.no_ti:
         out["translation_invariant"] = ti_measure(P, torch, leaf, pts, F, nrhs, st, eps)
+        out["lippmann_schwinger"] = ls_measure(P, torch, st)
     if not args.no_per_box:
         out["per_box_fp64"] = per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps)
         out["per_box_fp64"]["batched_step_speedup"] = out["per_box_fp64"]["step_ms"] / (factor_ms + solve_ms)
