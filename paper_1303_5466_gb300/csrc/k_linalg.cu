@@ -287,7 +287,16 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmProb* __restrict__ 
     }
     const GemmProb P = probs[lo];
     const int64_t lt = t - P.tile0;
-    const int tm = (int)(lt % P.tiles_m), tn = (int)(lt / P.tiles_m);
+    int tm, tn;
+    if (P.lower) {           // row-by-row enumeration of the lower triangle of tiles
+        tm = (int)((sqrt(8.0 * (double)lt + 1.0) - 1.0) * 0.5);
+        while ((int64_t)tm * (tm + 1) / 2 > lt) --tm;
+        while ((int64_t)(tm + 1) * (tm + 2) / 2 <= lt) ++tm;
+        tn = (int)(lt - (int64_t)tm * (tm + 1) / 2);
+    } else {
+        tm = (int)(lt % P.tiles_m);
+        tn = (int)(lt / P.tiles_m);
+    }
     const int row0 = tm * BM, col0 = tn * BN;
     const T* A = Ab + P.a_off;
     const T* B = Bb + P.b_off;

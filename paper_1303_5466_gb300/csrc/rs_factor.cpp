@@ -737,8 +737,11 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
     DevMem& d_p1 = op->t_p1;
     DevMem& d_p2 = op->t_p2;
     RS_CUDA(W.alloc(sizeof(T) * (size_t)(L.w_off[nb] + 1)));
-    std::vector<GemmProb> p1, p2;
-    int64_t t1 = 0, t2 = 0;
+    // with the symmetric sweep, E^{-1} (symmetric) is needed on and below the diagonal only:
+    // p2l takes those tiles; p2 (all tiles) serves the Gauss-Jordan path and its fallback
+    const bool sym = use_sweep(op);
+    std::vector<GemmProb> p1, p2, p2l;
+    int64_t t1 = 0, t2 = 0, t2l = 0;
     for (int b = 0; b < nb; ++b) {
         const int m = (int)L.m[b], k = (int)L.k[b];
         if (k == 0) continue;
@@ -758,33 +761,40 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
         h.tiles_m = (k + 63) / 64; h.tiles_n = (k + 63) / 64; h.tile0 = t2;
         t2 += (int64_t)h.tiles_m * h.tiles_n;
         p2.push_back(h);
+        GemmProb hl = h;
+        hl.lower = 1;
+        hl.tile0 = t2l;
+        t2l += (int64_t)h.tiles_m * (h.tiles_m + 1) / 2;
+        p2l.push_back(hl);
     }
     if (!p1.empty()) {
         if ((rc = upload(d_p1, p1, st))) return rc;
-        if ((rc = upload(d_p2, p2, st))) return rc;
+        if ((rc = upload(d_p2, sym ? p2l : p2, st))) return rc;
         double work = 0.0;
         for (int b = 0; b < nb; ++b) {
             const double m = (double)L.m[b], k = (double)L.k[b];
-            work += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;
+            work += 2.0 * m * (m - k) * k + (sym ? k * (k + 1.0) * (m - k) : 2.0 * k * (m - k) * k);
         }
         ProfScope ps(op, RS_PROF_GEMM_E, st, work,
                      sizeof(T) * (double)(L.phi_off[nb] + 2 * L.w_off[nb] + L.e_off[nb]));
         if (op->opts.per_box) {             // one box per launch: descriptors starting at tile 0
-            std::vector<GemmProb> q1 = p1, q2 = p2;
+            std::vector<GemmProb> q1 = p1, q2 = sym ? p2l : p2;
             for (auto& g : q1) g.tile0 = 0;
             for (auto& g : q2) g.tile0 = 0;
             if ((rc = upload(op->t_q1, q1, st))) return rc;
             if ((rc = upload(op->t_q2, q2, st))) return rc;
             for (size_t i = 0; i < q1.size(); ++i) {
+                const int64_t n2 = q2[i].lower ? (int64_t)q2[i].tiles_m * (q2[i].tiles_m + 1) / 2
+                                               : (int64_t)q2[i].tiles_m * q2[i].tiles_n;
                 RS_CUDA(launch_gemm<T>(st, op->t_q1.as<GemmProb>() + i, 1, (int64_t)q1[i].tiles_m * q1[i].tiles_n,
                                        L.d_Phi.as<T>(), L.d_T.as<T>(), W.as<T>(), L.d_Phi.as<T>()));
-                RS_CUDA(launch_gemm<T>(st, op->t_q2.as<GemmProb>() + i, 1, (int64_t)q2[i].tiles_m * q2[i].tiles_n,
-                                       L.d_T.as<T>(), W.as<T>(), L.d_E.as<T>(), W.as<T>()));
+                RS_CUDA(launch_gemm<T>(st, op->t_q2.as<GemmProb>() + i, 1, n2, L.d_T.as<T>(), W.as<T>(),
+                                       L.d_E.as<T>(), W.as<T>()));
             }
         } else {
             RS_CUDA(launch_gemm<T>(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<T>(), L.d_T.as<T>(),
                                    W.as<T>(), L.d_Phi.as<T>()));
-            RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
+            RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), sym ? t2l : t2, L.d_T.as<T>(), W.as<T>(),
                                    L.d_E.as<T>(), W.as<T>()));
         }
     }
@@ -795,9 +805,11 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
         if ((rc = run_sweep<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E,
                                L.l, &redo)))
             return rc;
-        if (redo && !p1.empty())     // E^{-1} again from W (the sweep overwrote it)
+        if (redo && !p1.empty()) {   // E^{-1} again from W, all tiles (the sweep overwrote it)
+            if ((rc = upload(d_p2, p2, st))) return rc;
             RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
                                    L.d_E.as<T>(), W.as<T>()));
+        }
     }
     if (!redo) return RS_OK;
     return run_gj<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E, L.l);
@@ -987,7 +999,8 @@ void compute_stats(rs_op* op)
             ff += k * k * (m - k);                                                // T = R11^{-1} R12
             if (op->opts.forward_only) continue;
             ff += inv * m * m * m;                                                // F^{-1}
-            ff += 2.0 * m * (m - k) * k + 2.0 * k * (m - k) * k;                  // W, E^{-1}
+            ff += 2.0 * m * (m - k) * k;                                          // W
+            ff += (inv == 1.0) ? k * (k + 1.0) * (m - k) : 2.0 * k * (m - k) * k;  // E^{-1} (lower only if SPD)
             ff += inv * k * k * k;                                                // E
             if (!L.cmp.empty() && L.cmp[b]) {
                 ++cboxes;

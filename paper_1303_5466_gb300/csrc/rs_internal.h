@@ -45,6 +45,7 @@ struct GemmProb {
     double alpha, beta;
     int tiles_m, tiles_n;
     int64_t tile0;         // first tile index of this problem in the launch
+    int lower;             // 1: only the tiles on and below the diagonal (M = N; tiles_m (tiles_m + 1) / 2)
 };
 
 // Batched matrix-vector(s) descriptor: y = alpha * op(A) x + beta * y, A column-major
