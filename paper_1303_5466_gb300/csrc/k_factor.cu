@@ -424,10 +424,10 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
             for (int i = threadIdx.x; i < a - 1 + 1; i += NT) nxt[i] = Rn[i];
         }
         __syncthreads();
-        for (int q = warp; q < nc; q += NW) {
-            const T t = tq[q];
-            T* yq = ys + (size_t)q * k;
-            for (int i = lane; i < a; i += 32) yq[i] = fma_(-t, cur[i], yq[i]);
+        // every thread takes rows i of all nc columns (no warp idles when nc < NW)
+        for (int i = threadIdx.x; i < a; i += NT) {
+            const T c = cur[i];
+            for (int q = 0; q < nc; ++q) ys[(size_t)q * k + i] = fma_(-tq[q], c, ys[(size_t)q * k + i]);
         }
         __syncthreads();
     }
@@ -450,7 +450,15 @@ cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const i
 {
     constexpr int NT = 256;
     if (nb <= 0 || max_cols <= 0 || max_k <= 0) return cudaSuccess;
-    const int NC = id_T_cols<T>(max_k);
+    // columns per CTA: as many as shared memory allows, fewer when that leaves the launch short of
+    // about four CTAs per SM (the top levels: few boxes, long back substitutions)
+    int NC = id_T_cols<T>(max_k);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = 4 * (int64_t)std::max(sms, 1);
+    const int64_t nc_fill = ((int64_t)nb * max_cols + want - 1) / want;
+    NC = (int)std::max<int64_t>(1, std::min<int64_t>(NC, nc_fill));
     const size_t shm = sizeof(T) * (size_t)(NC + 2) * (size_t)max_k;
     if (shm > 227 * 1024) return cudaErrorInvalidValue;     // skeleton too large for one CTA's buffers
     cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
