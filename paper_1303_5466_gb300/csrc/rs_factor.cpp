@@ -388,6 +388,17 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         const int var = deep_set >= 0 ? deep_set : 0;
         int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g, var); });
         if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
+        // gs > 1 (large boxes, few per launch): more CTAs than one per 16 columns, so that more
+        // warps -- and more loads in flight -- share each SM, within co-residency
+        double cap_scale = 1.0;
+        if (G > 1 && gs > 1.0) {
+            const int capc = cpqr_max_ctas<T>(B.max_r, B.max_m, G, var);
+            const int G2 = std::min((int)std::lround(G * gs), capc / std::max(B.nb, 1));
+            if (G2 > G) {
+                cap_scale = (double)G2 / (double)G;
+                G = G2;
+            }
+        }
         B.G = G;
         // The boxes of a batch differ in work (boundary boxes have fewer near rows, ranks
         // differ), and a group runs at its own pace: deal the same CTA total in proportion to
@@ -398,7 +409,7 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
             std::vector<int> cap(B.nb);
             for (int b = 0; b < B.nb; ++b) {
                 wgt[b] = (double)L.r[B.b0 + b] * (double)L.m[B.b0 + b] * (double)L.m[B.b0 + b];
-                cap[b] = std::max(1, (int)(2 * L.m[B.b0 + b] / 32));
+                cap[b] = std::max(1, (int)(cap_scale * (double)(2 * L.m[B.b0 + b] / 32)));
             }
             const std::vector<int32_t> off = proportional_groups(B.nb * G, wgt, cap);
             cta_all.insert(cta_all.end(), off.begin(), off.end());
@@ -1731,8 +1742,8 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     // per level as one triple
     const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
                                 {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0},
-                                {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}};
-    constexpr int NTR = 8;
+                                {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}, {2.0, 1, 1.0, 0.0}, {3.0, 0, 0.5, 0.0}};
+    constexpr int NTR = 10;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);
