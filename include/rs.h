@@ -100,9 +100,11 @@ typedef struct {
                                     0 = two passes over the open columns per step, 4 rows
                                     per lane in flight; 1 = the same with 8; 2 = look-ahead
                                     (one pass per step: the update of step s fused with the
-                                    dot products of step s+1); -1 = the autotuner's table
-                                    (rs_autotune), else 0 or 1 by occupancy. Same result up
-                                    to rounding order                                [-1]   */
+                                    dot products of step s+1); 3 = 0 with the lists of open
+                                    columns in global memory (taken by 0 and 1 by themselves
+                                    for boxes whose lists do not fit shared memory); -1 = the
+                                    autotuner's table (rs_autotune), else 0 or 1 by
+                                    occupancy. Same result up to rounding order       [-1]   */
     int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the
                                     offset between grid points (Sec. 5: one set of matrix
                                     blocks per level).  1: each level's ID is taken once, on

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
         T* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
         T* __restrict__ diag, unsigned int* __restrict__ bar, unsigned long long* __restrict__ keys,
-        int* __restrict__ status, long long spin, double* __restrict__ nrm_all, double* __restrict__ ref_all)
+        int* __restrict__ status, long long spin, double* __restrict__ nrm_all, double* __restrict__ ref_all,
+        int* __restrict__ gwork, int gstride)
 {
     extern __shared__ double smem[];
     __shared__ double dred[NT / 32 + 1];
@@ -104,9 +105,12 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
     T* __restrict__ Y = Yall + y_off[b];
     double* __restrict__ nrm = nrm_all + a0;
     double* __restrict__ ref = ref_all + a0;
-    int* alist = (int*)smem;                  // m: open columns (same order in every CTA)
-    int* apos = alist + m;                    // m: position of a column in alist
-    T* v = (T*)(apos + m);                    // r: Householder vector (2m ints keep it 8-byte aligned)
+    // open-column list (m: same order in every CTA), positions in it (m), Householder vector (r):
+    // all in shared memory, or (gwork: boxes too large for that) the two lists in this CTA's
+    // slice of global memory
+    int* alist = gwork ? gwork + (int64_t)blockIdx.x * gstride : (int*)smem;
+    int* apos = alist + m;
+    T* v = gwork ? (T*)smem : (T*)(apos + m);   // (2m ints keep it 8-byte aligned)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
@@ -308,10 +312,23 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
 }
 
 template <class T>
-static size_t cpqr_shm(int max_r, int max_m, int G)
+static size_t cpqr_shm(int max_r, int max_m, bool global_lists)
 {
-    (void)G;
-    return sizeof(int) * (size_t)(2 * max_m + 2) + sizeof(T) * (size_t)max_r + 64;
+    return (global_lists ? 0 : sizeof(int) * (size_t)(2 * max_m + 2)) + sizeof(T) * (size_t)max_r + 64;
+}
+
+// The open-column lists go to global memory when asked (variant 3) or when shared memory cannot
+// hold them with the Householder vector.
+template <class T>
+static bool cpqr_global(int max_r, int max_m, int deep)
+{
+    return deep == 3 || cpqr_shm<T>(max_r, max_m, false) > 227 * 1024;
+}
+
+template <class T>
+size_t cpqr_gwork_ints(int max_r, int max_m, int deep, int ctas)
+{
+    return cpqr_global<T>(max_r, max_m, deep) ? (size_t)ctas * (size_t)(2 * max_m + 2) : 0;
 }
 
 template <int U, class T>
@@ -319,7 +336,7 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
                                  const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y,
                                  double eps, int32_t* kout, int32_t* piv, T* diag, unsigned int* bar,
                                  unsigned long long* keys, int* status, long long spin_limit, size_t shm, double* nrm,
-                                 double* ref)
+                                 double* ref, int* gwork, int gstride)
 {
     constexpr int NT = 256;
     cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, U, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -327,13 +344,13 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
     count_launches(1);
     if (!cta_off && G == 1) {
         cpqr_kernel<NT, U, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                                                   keys, status, spin_limit, nrm, ref);
+                                                   keys, status, spin_limit, nrm, ref, gwork, gstride);
         return cudaGetLastError();
     }
     int g0 = cta_off ? nb : G;
     void* args[] = {(void*)&g0, (void*)&cta_off, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y,
                     (void*)&eps, (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
-                    (void*)&spin_limit, (void*)&nrm, (void*)&ref};
+                    (void*)&spin_limit, (void*)&nrm, (void*)&ref, (void*)&gwork, (void*)&gstride};
     return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, U, T>, dim3((unsigned)(cta_off ? ctas : nb * G)),
                                        dim3(NT), args, shm, st);
 }
@@ -342,7 +359,8 @@ template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, int deep,
                         const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y, double eps,
                         int32_t* kout, int32_t* piv, T* diag, unsigned int* bar, unsigned long long* keys,
-                        int* status, long long spin_limit, int max_r, int max_m, double* nrm, double* ref, T* wv)
+                        int* status, long long spin_limit, int max_r, int max_m, double* nrm, double* ref, T* wv,
+                        int* gwork)
 {
     if (nb <= 0) return cudaSuccess;
     if (deep == 2) {
@@ -350,22 +368,28 @@ cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, 
         return launch_cpqr_la<T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
                                  keys, status, spin_limit, max_r, max_m, nrm, ref, wv);
     }
-    const size_t shm = cpqr_shm<T>(max_r, max_m, G);
-    if (deep)
+    const bool glob = cpqr_global<T>(max_r, max_m, deep);
+    if (glob && !gwork) return cudaErrorInvalidValue;
+    const size_t shm = cpqr_shm<T>(max_r, max_m, glob);
+    if (shm > 227 * 1024) return cudaErrorInvalidValue;     // the Householder vector alone does not fit
+    int* gw = glob ? gwork : nullptr;
+    const int gstride = 2 * max_m + 2;
+    if (deep == 1)
         return launch_cpqr_u<8, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                                   keys, status, spin_limit, shm, nrm, ref);
+                                   keys, status, spin_limit, shm, nrm, ref, gw, gstride);
     return launch_cpqr_u<4, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                               keys, status, spin_limit, shm, nrm, ref);
+                               keys, status, spin_limit, shm, nrm, ref, gw, gstride);
 }
 
 template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G, int deep)
 {
     constexpr int NT = 256;
+    (void)G;
     if (deep == 2) return cpqr_la_max_ctas<T>(max_r, max_m);
-    const size_t shm = cpqr_shm<T>(max_r, max_m, G);
+    const size_t shm = cpqr_shm<T>(max_r, max_m, cpqr_global<T>(max_r, max_m, deep));
     if (shm > 227 * 1024) return 0;
-    const void* fn = deep ? (const void*)cpqr_kernel<NT, 8, T> : (const void*)cpqr_kernel<NT, 4, T>;
+    const void* fn = deep == 1 ? (const void*)cpqr_kernel<NT, 8, T> : (const void*)cpqr_kernel<NT, 4, T>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -383,7 +407,8 @@ template <int NT, class T>
 __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ act_off, const int32_t* __restrict__ kk,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off, const T* __restrict__ Yall,
         const int32_t* __restrict__ piv, const T* __restrict__ diag, const int32_t* __restrict__ skpos,
-        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, T* __restrict__ Tout, int NC)
+        const int32_t* __restrict__ rscol, const int64_t* __restrict__ t_off, T* __restrict__ Tout, int NC,
+        int rglobal)
 {
     extern __shared__ double ys_raw[];
     const int b = blockIdx.x;
@@ -398,7 +423,8 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
     const T* Y = Yall + y_off[b];
     T* Tb = Tout + t_off[b];
     T* ys = (T*)ys_raw;                 // nc x k right-hand sides, then solutions
-    T* rc = ys + (size_t)NC * k;        // 2 x k: R11 columns of the current and next step
+    T* rc = ys + (size_t)NC * k;        // 2 x k: R11 columns of the current and next step (none
+                                        // when rglobal: the columns are read from Y in place)
     __shared__ T tq[64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
@@ -406,19 +432,19 @@ __global__ void __launch_bounds__(NT) id_T_kernel(const int64_t* __restrict__ ac
         const T* col = Y + (int64_t)rscol[a0 + cb + q] * r;
         for (int i = lane; i < k; i += 32) ys[(size_t)q * k + i] = col[i];
     }
-    {
+    if (!rglobal) {
         const T* Ra = Y + (int64_t)piv[a0 + k - 1] * r;
         for (int i = threadIdx.x; i < k; i += NT) rc[(size_t)((k - 1) & 1) * k + i] = Ra[i];
     }
     __syncthreads();
     for (int a = k - 1; a >= 0; --a) {
-        const T* cur = rc + (size_t)(a & 1) * k;
+        const T* cur = rglobal ? Y + (int64_t)piv[a0 + a] * r : rc + (size_t)(a & 1) * k;
         if (threadIdx.x < nc) {
             const T t = ys[(size_t)threadIdx.x * k + a] / diag[a0 + a];
             tq[threadIdx.x] = t;
             Tb[(int64_t)(cb + threadIdx.x) * k + skpos[a0 + a]] = t;
         }
-        if (a > 0) {
+        if (a > 0 && !rglobal) {
             T* nxt = rc + (size_t)((a - 1) & 1) * k;
             const T* Rn = Y + (int64_t)piv[a0 + a - 1] * r;
             for (int i = threadIdx.x; i < a - 1 + 1; i += NT) nxt[i] = Rn[i];
@@ -459,14 +485,20 @@ cudaError_t launch_id_T(cudaStream_t st, int nb, const int64_t* act_off, const i
     const int64_t want = 4 * (int64_t)std::max(sms, 1);
     const int64_t nc_fill = ((int64_t)nb * max_cols + want - 1) / want;
     NC = (int)std::max<int64_t>(1, std::min<int64_t>(NC, nc_fill));
-    const size_t shm = sizeof(T) * (size_t)(NC + 2) * (size_t)max_k;
+    // a skeleton too large for the two R11 column buffers: the columns are read from Y in place
+    int rglobal = 0;
+    size_t shm = sizeof(T) * (size_t)(NC + 2) * (size_t)max_k;
+    if (shm > 227 * 1024) {
+        rglobal = 1;
+        shm = sizeof(T) * (size_t)NC * (size_t)max_k;
+    }
     if (shm > 227 * 1024) return cudaErrorInvalidValue;     // skeleton too large for one CTA's buffers
     cudaError_t e = cudaFuncSetAttribute(id_T_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)nb, (unsigned)((max_cols + NC - 1) / NC));
     count_launches(1);
     id_T_kernel<NT, T><<<grid, NT, shm, st>>>(act_off, kk, nnear, P, y_off, Y, piv, diag, skpos, rscol, t_off, Tout,
-                                              NC);
+                                              NC, rglobal);
     return cudaGetLastError();
 }
 
@@ -519,8 +551,9 @@ cudaError_t launch_assemble_F(cudaStream_t st, int nb, bool leaf, const int32_t*
     template cudaError_t launch_cpqr<T>(cudaStream_t, int, int, const int32_t*, int, int, const int64_t*,            \
                                         const int32_t*, int, const int64_t*, T*, double, int32_t*, int32_t*, T*,    \
                                         unsigned int*, unsigned long long*, int*, long long, int, int, double*,     \
-                                        double*, T*);                                                               \
+                                        double*, T*, int*);                                                         \
     template int cpqr_max_ctas<T>(int, int, int, int);                                                               \
+    template size_t cpqr_gwork_ints<T>(int, int, int, int);                                                          \
     template cudaError_t launch_id_T<T>(cudaStream_t, int, const int64_t*, const int32_t*, const int32_t*, int,      \
                                         const int64_t*, const T*, const int32_t*, const T*, const int32_t*,         \
                                         const int32_t*, const int64_t*, T*, int, int);                              \

@@ -173,7 +173,7 @@ namespace {
 
 // Workspace of the ID phase, released when rs_factor returns.
 struct IdWork {
-    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms, cta_off;
+    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms, cta_off, gwork;
 };
 
 template <class T>
@@ -430,6 +430,9 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         if ((rc2 = upload(w.cta_off, cta_all, st))) return rc2;
     }
     RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * max_keys));
+    size_t gw_ints = 0;        // open-column lists in global memory (boxes too large for shared)
+    for (const Batch& B : bats) gw_ints = std::max(gw_ints, cpqr_gwork_ints<T>(B.max_r, B.max_m, B.deep, B.ctas));
+    if (gw_ints) RS_CUDA(w.gwork.alloc(sizeof(int) * gw_ints));
     // squared norms, their references, and (look-ahead variant) the dot products v^H y_j
     const size_t nrm_dbl = 2 * (size_t)(sum_m + 1), wv_dbl = ((size_t)(sum_m + 1) * sizeof(T) + 7) / 8;
     RS_CUDA(w.norms.alloc(sizeof(double) * (nrm_dbl + wv_dbl)));
@@ -444,7 +447,8 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
                                    w.piv.as<int32_t>(), w.diag.as<T>(), op->d_bar.as<unsigned int>() + B.b0,
                                    w.keys.as<unsigned long long>(), op->d_status.as<int>(),
                                    (long long)op->opts.spin_limit, B.max_r, B.max_m, w.norms.as<double>(),
-                                   w.norms.as<double>() + sum_m + 1, (T*)(w.norms.as<double>() + nrm_dbl)));
+                                   w.norms.as<double>() + sum_m + 1, (T*)(w.norms.as<double>() + nrm_dbl),
+                                   gw_ints ? w.gwork.as<int>() : nullptr));
         }
     }
     if ((rc = check_status(op, st))) return rc;
@@ -1143,7 +1147,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
-    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 2) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 2");
+    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 3) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 3");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))
         return fail(RS_E_INVALID, "forward_only combines with none of translation_invariant, k_cut, per_box");
     if (op->opts.translation_invariant < 0 || op->opts.translation_invariant > 2)

@@ -106,13 +106,18 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 // deep (the variant): 0 = four rows per lane in flight; 1 = eight (more registers; for
 // launches with few CTAs per SM, where each warp must hide more memory latency by itself);
 // 2 = the look-ahead form (k_cpqr_la.cu: one read and one write of each open column per step
-// instead of two reads and a write), which needs wv, a work array of act_off[nb] entries.
+// instead of two reads and a write), which needs wv, a work array of act_off[nb] entries;
+// 3 = variant 0 with the open-column lists in global memory (gwork), which variants 0 and 1
+// also take when shared memory cannot hold them: gwork then needs cpqr_gwork_ints() ints.
 template <class T>
 cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, int deep,
                         const int64_t* act_off, const int32_t* nnear, int P,
                         const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag,
                         unsigned int* bar, unsigned long long* keys, int* status, long long spin_limit, int max_r,
-                        int max_m, double* nrm, double* ref, T* wv = nullptr);
+                        int max_m, double* nrm, double* ref, T* wv = nullptr, int* gwork = nullptr);
+// ints of global scratch a launch of `ctas` CTAs needs for its open-column lists (0: none)
+template <class T>
+size_t cpqr_gwork_ints(int max_r, int max_m, int deep, int ctas);
 // Largest grid of the cpqr kernel (of the given variant) that can be co-resident for these sizes.
 template <class T>
 int cpqr_max_ctas(int max_r, int max_m, int G, int deep = 0);

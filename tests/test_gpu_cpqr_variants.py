@@ -1,6 +1,7 @@
-"""The three forms of the column-pivoted QR of Eq. 2.1 (opts.cpqr_variant): two passes per step
-with 4 or 8 rows per lane in flight, and the look-ahead form (one pass per step, the update of
-step s fused with the dot products of step s+1).  Each is forced on every level and checked
+"""The forms of the column-pivoted QR of Eq. 2.1 (opts.cpqr_variant): two passes per step with
+4 or 8 rows per lane in flight, the look-ahead form (one pass per step, the update of step s
+fused with the dot products of step s+1), and the form that keeps the open-column lists in
+global memory (taken by itself for boxes too large for shared memory).  Each is forced on every level and checked
 against the oracle: identical ranks and skeleton sets, solutions within the 1e-9 bound of the
 FP64 path.  The cases cover several CTAs per box (64^2 grids and up), boxes whose rank test
 stops the factorisation before min(r, m) (eps = 1e-5, and the extra group barrier the
@@ -13,7 +14,7 @@ from paper_1303_5466_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [0, 1, 2]
+VARIANTS = [0, 1, 2, 3]
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +60,7 @@ def test_variant_matches_oracle_laplace(rs, oracle_mod, variant, n, leaf, eps):
     assert _rel(x, xo) <= tol
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_variant_matches_default_128(rs, variant):
     """128^2 grid, leaves 16^2: Y blocks of several hundred rows and columns, so every loop
     of the kernels (full blocks of rows, leftover rows, paired and single columns) runs."""
@@ -108,7 +109,7 @@ def test_look_ahead_mixed_fp32(rs, oracle_mod):
 
 
 def test_bad_variant_is_rejected(rs):
-    o = _opts(rs, 3)
+    o = _opts(rs, 4)
     with pytest.raises(RuntimeError):
         rs.Solver(W.grid_points(16), 4, eps=1e-10, opts=o)
 
