@@ -60,6 +60,9 @@ def _args():
     p.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner before the steps")
     p.add_argument("--no-per-box", action="store_true", help="skip the one-box-per-launch comparison")
     p.add_argument("--no-ti", action="store_true", help="skip the translation-invariant comparison (a = 1)")
+    p.add_argument("--large-grid", type=int, default=0,
+                   help="instead of the benchmark: factor and solve an n x n grid (a = 1, translation-invariant "
+                        "mode 2) and print its own JSON line")
     p.add_argument("--k-cut", type=int, default=512,
                    help="also measure the extra compression of Sec. 3 for boxes with k > K (0: skip)")
     return p.parse_args()
@@ -673,10 +676,58 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_large_grid(args):
+    """--large-grid n: one factorization and solve of an n x n grid with a = 1 in the
+    translation-invariant mode 2 (FP64, leaf 16, eps 1e-10), with the residual on 32 sampled
+    rows computed entry by entry by the oracle.  Prints one JSON line (not the benchmark line)."""
+    import numpy as np
+    import torch
+    import paper_1303_5466_gb300 as P
+    from paper_1303_5466_gb300 import workloads as W
+    from oracle import oracle as O
+    n = args.large_grid
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream()
+    o = P.rs_opts_default()
+    o.translation_invariant = 2
+    o.profile = 1
+    tree = P.rs_build_tree(W.grid_points(n), 16)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    op = P.rs_factor(tree, eps=1e-10, opts=o, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    factor_ms = e0.elapsed_time(e1)
+    f = torch.from_numpy(W.rhs_uniform(n, 2)[None, :].copy()).cuda()
+    x = torch.empty_like(f)
+    P.rs_solve(op, f, 1, x, st)
+    torch.cuda.synchronize()
+    e0.record(st)
+    P.rs_solve(op, f, 1, x, st)
+    e1.record(st)
+    e1.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    s = P.rs_op_stats(op)
+    rows = np.random.default_rng(0).choice(n * n, 32, replace=False)
+    xs = x.cpu().numpy()[0]
+    fr = f.cpu().numpy()[0][rows]
+    res = float(np.linalg.norm(np.ravel(O.matvec_rows(n, xs, rows)) - fr) / np.linalg.norm(fr))
+    print(json.dumps({"large_grid": {"n": n, "N": n * n, "factor_ms": factor_ms, "solve_ms": solve_ms,
+                                     "unknowns_per_s": n * n / (factor_ms * 1e-3), "root_m": s["root_m"],
+                                     "bytes_factors": s["bytes_factors"], "flops_factor": s["flops_factor"],
+                                     "sampled_residual": res, "residual_rows": 32,
+                                     "profile_ms": {k: v[0] for k, v in P.rs_op_profile(op).items()}}}))
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.large_grid:
+        run_large_grid(args)
     else:
         run_ours(args)
 
