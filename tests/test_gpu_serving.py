@@ -138,3 +138,39 @@ def test_host_side_failures(env):
             P.rs_server_submit(srv, 0, np.zeros(32 * 32), 1, np.zeros(32 * 32))   # host buffers
     finally:
         P.rs_server_free(srv)
+
+
+def test_translation_invariant_operators_in_the_mix(env):
+    """Operators factored in the translation-invariant modes (their boxes share one stored set
+    of blocks per class or per level) are served like any other: same results as rs_solve."""
+    import torch
+    P, _ = env
+    trees, ops = [], []
+    try:
+        for mode, (n, leaf) in zip((1, 2, 0), SPECS):
+            t = P.rs_build_tree(W.grid_points(n), leaf)
+            trees.append(t)
+            o = P.rs_opts_default()
+            o.translation_invariant = mode
+            ops.append(P.rs_factor(t, eps=1e-10, opts=o))
+        reqs = _requests(24, 5)
+        ref = _alone(P, ops, reqs)
+        srv = P.rs_server_create(ops, 256 << 20, max_inflight=8)
+        try:
+            fs = [torch.from_numpy(F).cuda() for _, _, F in reqs]
+            xs = [torch.full_like(f, np.nan) for f in fs]
+            torch.cuda.synchronize()
+            for i, (k, nrhs, _) in enumerate(reqs):
+                P.rs_server_submit(srv, k, fs[i], nrhs, xs[i])
+            P.rs_server_drain(srv, 120.0)
+            torch.cuda.synchronize()
+            for i in range(len(reqs)):
+                x = xs[i].cpu().numpy()
+                assert np.linalg.norm(x - ref[i]) <= 1e-13 * np.linalg.norm(ref[i])
+        finally:
+            P.rs_server_free(srv)
+    finally:
+        for o in ops:
+            P.rs_free(o)
+        for t in trees:
+            P.rs_free_tree(t)
