@@ -68,7 +68,7 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 //      share for the next step.
 // The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step (every CTA
 // computes alpha from the same data in the same order).
-template <int NT, int U, class T>
+template <int NT, int U, bool GL, class T>
 __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restrict__ cta_off,
         const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
@@ -106,11 +106,12 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
     double* __restrict__ nrm = nrm_all + a0;
     double* __restrict__ ref = ref_all + a0;
     // open-column list (m: same order in every CTA), positions in it (m), Householder vector (r):
-    // all in shared memory, or (gwork: boxes too large for that) the two lists in this CTA's
-    // slice of global memory
-    int* alist = gwork ? gwork + (int64_t)blockIdx.x * gstride : (int*)smem;
+    // all in shared memory, or (GL: boxes too large for that) the two lists in this CTA's slice of
+    // global memory; the vector's address is formed from the shared base either way, so its
+    // reads in the hot loops stay shared-memory loads
+    int* alist = GL ? gwork + (int64_t)blockIdx.x * gstride : (int*)smem;
     int* apos = alist + m;
-    T* v = gwork ? (T*)smem : (T*)(apos + m);   // (2m ints keep it 8-byte aligned)
+    T* v = (T*)((int*)smem + (GL ? 0 : 2 * m));    // (2m ints keep it 8-byte aligned)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
@@ -331,7 +332,7 @@ size_t cpqr_gwork_ints(int max_r, int max_m, int deep, int ctas)
     return cpqr_global<T>(max_r, max_m, deep) ? (size_t)ctas * (size_t)(2 * max_m + 2) : 0;
 }
 
-template <int U, class T>
+template <int U, bool GL, class T>
 static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas,
                                  const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y,
                                  double eps, int32_t* kout, int32_t* piv, T* diag, unsigned int* bar,
@@ -339,11 +340,11 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
                                  double* ref, int* gwork, int gstride)
 {
     constexpr int NT = 256;
-    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, U, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, U, GL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     count_launches(1);
     if (!cta_off && G == 1) {
-        cpqr_kernel<NT, U, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
+        cpqr_kernel<NT, U, GL, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
                                                    keys, status, spin_limit, nrm, ref, gwork, gstride);
         return cudaGetLastError();
     }
@@ -351,7 +352,7 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
     void* args[] = {(void*)&g0, (void*)&cta_off, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y,
                     (void*)&eps, (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
                     (void*)&spin_limit, (void*)&nrm, (void*)&ref, (void*)&gwork, (void*)&gstride};
-    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, U, T>, dim3((unsigned)(cta_off ? ctas : nb * G)),
+    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, U, GL, T>, dim3((unsigned)(cta_off ? ctas : nb * G)),
                                        dim3(NT), args, shm, st);
 }
 
@@ -374,11 +375,18 @@ cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, 
     if (shm > 227 * 1024) return cudaErrorInvalidValue;     // the Householder vector alone does not fit
     int* gw = glob ? gwork : nullptr;
     const int gstride = 2 * max_m + 2;
+    if (glob) {
+        if (deep == 1)
+            return launch_cpqr_u<8, true, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv,
+                                             diag, bar, keys, status, spin_limit, shm, nrm, ref, gw, gstride);
+        return launch_cpqr_u<4, true, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag,
+                                         bar, keys, status, spin_limit, shm, nrm, ref, gw, gstride);
+    }
     if (deep == 1)
-        return launch_cpqr_u<8, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                                   keys, status, spin_limit, shm, nrm, ref, gw, gstride);
-    return launch_cpqr_u<4, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                               keys, status, spin_limit, shm, nrm, ref, gw, gstride);
+        return launch_cpqr_u<8, false, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag,
+                                          bar, keys, status, spin_limit, shm, nrm, ref, nullptr, gstride);
+    return launch_cpqr_u<4, false, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag,
+                                      bar, keys, status, spin_limit, shm, nrm, ref, nullptr, gstride);
 }
 
 template <class T>
@@ -387,9 +395,12 @@ int cpqr_max_ctas(int max_r, int max_m, int G, int deep)
     constexpr int NT = 256;
     (void)G;
     if (deep == 2) return cpqr_la_max_ctas<T>(max_r, max_m);
-    const size_t shm = cpqr_shm<T>(max_r, max_m, cpqr_global<T>(max_r, max_m, deep));
+    const bool glob = cpqr_global<T>(max_r, max_m, deep);
+    const size_t shm = cpqr_shm<T>(max_r, max_m, glob);
     if (shm > 227 * 1024) return 0;
-    const void* fn = deep == 1 ? (const void*)cpqr_kernel<NT, 8, T> : (const void*)cpqr_kernel<NT, 4, T>;
+    const void* fn;
+    if (glob) fn = deep == 1 ? (const void*)cpqr_kernel<NT, 8, true, T> : (const void*)cpqr_kernel<NT, 4, true, T>;
+    else fn = deep == 1 ? (const void*)cpqr_kernel<NT, 8, false, T> : (const void*)cpqr_kernel<NT, 4, false, T>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);

@@ -1762,7 +1762,20 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     };
     std::vector<Shape> shapes;
     std::vector<std::vector<double>> t_cpqr(NTR), t_f(NTR), t_e(NTR);
+    // per-level event times (CPQR, F^{-1} or root, E) of one factorization
+    auto level_times = [&](rs_op* op, std::vector<double>& c, std::vector<double>& f, std::vector<double>& e) {
+        const int d = op->d;
+        c.assign(d + 1, 0.0);
+        f.assign(d + 1, 0.0);
+        e.assign(d + 1, 0.0);
+        for (int l = 0; l <= d; ++l) {
+            rs_op_profile_level(op, RS_PROF_CPQR, l, &c[l]);
+            rs_op_profile_level(op, l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F, l, &f[l]);
+            rs_op_profile_level(op, RS_PROF_INV_E, l, &e[l]);
+        }
+    };
     double base_ms = 0.0;
+    std::vector<double> b_cpqr, b_f, b_e;
     g_trial = TuneTrial();
     {
         rs_op* op = nullptr;
@@ -1772,6 +1785,7 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
             const Level& L = op->lev[l];
             shapes.push_back({L.nb, (int64_t)L.max_m, (int64_t)L.max_r, (int64_t)L.max_k});
         }
+        level_times(op, b_cpqr, b_f, b_e);
         rs_free(op);
     }
     for (int t = 0; t < NTR; ++t) {
@@ -1781,19 +1795,7 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         const int rc = timed_factor(&op, &ms);
         g_trial = TuneTrial();
         if (rc) return rc;
-        const int d = op->d;
-        t_cpqr[t].assign(d + 1, 0.0);
-        t_f[t].assign(d + 1, 0.0);
-        t_e[t].assign(d + 1, 0.0);
-        for (int l = 0; l <= d; ++l) {
-            double v = 0.0;
-            rs_op_profile_level(op, RS_PROF_CPQR, l, &v);
-            t_cpqr[t][l] = v;
-            rs_op_profile_level(op, l == 0 ? RS_PROF_INV_ROOT : RS_PROF_INV_F, l, &v);
-            t_f[t][l] = v;
-            rs_op_profile_level(op, RS_PROF_INV_E, l, &v);
-            t_e[t][l] = v;
-        }
+        level_times(op, t_cpqr[t], t_f[t], t_e[t]);
         rs_free(op);
     }
     int keys = 0;
@@ -1820,6 +1822,29 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         const int bf = best_of(t_f);
         tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", trials[bf].sweep_gscale);
         keys += 1;
+    }
+    // Each candidate was timed once: check the picks in one factorization on the new table, and
+    // give the built-in setting back to every level whose kernel came out more than 3% slower
+    // than in the first factorization (a pick that owed its place to a lucky timing).
+    {
+        rs_op* op = nullptr;
+        double ms = 0.0;
+        int rc = timed_factor(&op, &ms);
+        if (rc) return rc;
+        std::vector<double> v_cpqr, v_f, v_e;
+        level_times(op, v_cpqr, v_f, v_e);
+        rs_free(op);
+        for (size_t l = 0; l < shapes.size() && l < v_cpqr.size() && l < b_cpqr.size(); ++l) {
+            const Shape& S = shapes[l];
+            if (l >= 1 && v_cpqr[l] > 1.03 * b_cpqr[l]) {
+                const std::string k = tune_key("cpqr", esz, S.nb, S.m, S.r);
+                tune_set(k + ".gscale", 1.0);
+                tune_set(k + ".deep", -1.0);
+                tune_set(k + ".batch", 0.0);
+            }
+            if (l >= 1 && v_e[l] > 1.03 * b_e[l]) tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".gscale", 1.0);
+            if (v_f[l] > 1.03 * b_f[l]) tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", 1.0);
+        }
     }
     double tuned_ms = 0.0;
     {
