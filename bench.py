@@ -186,11 +186,12 @@ def oracle_sample(n, leaf, eps, a):
 SERVING_OPS = ((128, 16), (256, 16), (512, 16))
 
 
-def serving_measure(P, torch, requests, seed=3, load=0.7):
+def serving_measure(P, torch, requests, seed=3, load=0.7, other_loads=(0.5, 0.9)):
     """Serving workload: three resident FP64 operators (128^2, 256^2, 512^2 grids, leaves 16^2,
     eps 1e-10); a seeded stream of requests, each naming an operator uniformly and carrying
     1-64 RHS ~ N(0,1), arriving as a Poisson process at `load` x the closed-loop capacity
-    measured on a first burst.  Returns p50/p99 latency (submission to completion) and RHS/s."""
+    measured on a first burst (and the same stream again at each of `other_loads`).  Returns
+    p50/p99 latency (submission to completion) and RHS/s."""
     import numpy as np
     ops, trees = [], []
     for n, leaf in SERVING_OPS:
@@ -217,23 +218,33 @@ def serving_measure(P, torch, requests, seed=3, load=0.7):
         P.rs_server_drain(srv, 3600.0)
         burst_s = time.perf_counter() - t0
         cap = burst / burst_s                        # requests per second
-        lam = load * cap
         P.rs_server_latencies(srv)
-        n0 = P.rs_server_stats(srv)["completed"]
-        # open loop: Poisson arrivals at lam
-        t0 = time.perf_counter()
-        t_next = t0
-        for i in range(burst, requests):
-            t_next += gaps[i] / lam
-            delay = t_next - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
-        P.rs_server_drain(srv, 3600.0)
-        wall = time.perf_counter() - t0
-        lat = P.rs_server_latencies(srv)[n0:]
-        st = P.rs_server_stats(srv)
         rhs = int(nrhs[burst:].sum())
+
+        def open_loop(ld):
+            # Poisson arrivals at ld x capacity; latencies of this phase only
+            lam_ = ld * cap
+            n0_ = P.rs_server_stats(srv)["completed"]
+            t0_ = time.perf_counter()
+            t_next = t0_
+            for i in range(burst, requests):
+                t_next += gaps[i] / lam_
+                delay = t_next - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
+            P.rs_server_drain(srv, 3600.0)
+            wall_ = time.perf_counter() - t0_
+            lat_ = P.rs_server_latencies(srv)[n0_:]
+            return lam_, wall_, lat_
+
+        lam, wall, lat = open_loop(load)
+        st = P.rs_server_stats(srv)
+        others = {}
+        for ld in other_loads:
+            lam2, wall2, lat2 = open_loop(ld)
+            others["%.1f" % ld] = {"lambda_per_s": lam2, "p50_ms": float(np.percentile(lat2, 50)),
+                                   "p99_ms": float(np.percentile(lat2, 99)), "rhs_per_s": rhs / wall2}
         # the same burst, one rs_solve per request in submission order (no cross-request batching)
         cs = torch.cuda.current_stream()
         torch.cuda.synchronize()
@@ -248,6 +259,7 @@ def serving_measure(P, torch, requests, seed=3, load=0.7):
                 "burst_speedup_vs_sequential": seq_s / burst_s,
                 "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "rhs_per_s": rhs / wall, "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
+                "other_loads": others,
                 "operators": "%s grids, leaf 16, eps 1e-10, FP64" % ", ".join("%d^2" % n for n, _ in SERVING_OPS),
                 "stream": "seed 3: operator uniform, nrhs uniform 1-64, N(0,1) columns, Exp inter-arrivals"}
     finally:
