@@ -117,6 +117,10 @@ typedef struct {
                                     factored once: ~13-24 per level at any grid size).
                                     Refused with varying a or b, with k_cut > 0, and for
                                     9 N > 2^31 - 1 (mode 1)                           [0]    */
+    int sweep_panel;             /* panel width of the symmetric sweep (spd_inverse): 8 or
+                                    16 columns per step (16: twice the FMAs per element
+                                    loaded, half the steps); 0 = the autotuner's table,
+                                    else 8                                            [0]    */
     int forward_only;            /* 1: the tree build alone (the IDs of every level, Sec. 2.2):
                                     the operator serves rs_fwd_apply (the compressed forward
                                     operator), rs_residual and rs_bicgstab's matvec, not

@@ -313,13 +313,20 @@ constexpr int SW_NT = 256, SW_NB = 8;
 
 int sweep_panel_width() { return SW_NB; }
 
+// The kernel for panel width nbw (8 or 16: twice the FMAs per element loaded, half the steps).
 template <class T>
-int sweep_max_ctas()
+static const void* sweep_fn(int nbw)
+{
+    return nbw == 16 ? (const void*)sweep_kernel<SW_NT, 16, T> : (const void*)sweep_kernel<SW_NT, SW_NB, T>;
+}
+
+template <class T>
+int sweep_max_ctas(int nbw)
 {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<SW_NT, SW_NB, T>, SW_NT, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn<T>(nbw), SW_NT, 0) != cudaSuccess)
         return 0;
     return per_sm * sms;
 }
@@ -327,20 +334,23 @@ int sweep_max_ctas()
 template <class T>
 cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int32_t* m,
                                  const int64_t* off, T* A, T* Pb, const int64_t* pb_off, unsigned int* bar,
-                                 int* status, long long spin_limit, int max_m)
+                                 int* status, long long spin_limit, int max_m, int nbw)
 {
     if (nb <= 0 || max_m <= 0) return cudaSuccess;
+    if (nbw != SW_NB && nbw != 16) return cudaErrorInvalidValue;
     count_launches(1);
     if (!cta_off && G == 1) {
-        sweep_kernel<SW_NT, SW_NB, T><<<nb, SW_NT, 0, st>>>(1, nullptr, m, off, A, Pb, pb_off, bar, status,
-                                                            spin_limit);
+        if (nbw == 16)
+            sweep_kernel<SW_NT, 16, T><<<nb, SW_NT, 0, st>>>(1, nullptr, m, off, A, Pb, pb_off, bar, status, spin_limit);
+        else
+            sweep_kernel<SW_NT, SW_NB, T><<<nb, SW_NT, 0, st>>>(1, nullptr, m, off, A, Pb, pb_off, bar, status,
+                                                                spin_limit);
     } else {
         int g0 = cta_off ? nb : G;
         void* args[] = {(void*)&g0, (void*)&cta_off, (void*)&m, (void*)&off, (void*)&A, (void*)&Pb, (void*)&pb_off,
                         (void*)&bar, (void*)&status, (void*)&spin_limit};
-        cudaError_t e = cudaLaunchCooperativeKernel((void*)sweep_kernel<SW_NT, SW_NB, T>,
-                                                    dim3((unsigned)(cta_off ? ctas : nb * G)), dim3(SW_NT), args, 0,
-                                                    st);
+        cudaError_t e = cudaLaunchCooperativeKernel(sweep_fn<T>(nbw), dim3((unsigned)(cta_off ? ctas : nb * G)),
+                                                    dim3(SW_NT), args, 0, st);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaGetLastError();
@@ -352,10 +362,10 @@ cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* 
 }
 
 #define RS_INST_SWEEP(T)                                                                                              \
-    template int sweep_max_ctas<T>();                                                                               \
+    template int sweep_max_ctas<T>(int);                                                                            \
     template cudaError_t launch_sweep_inverse<T>(cudaStream_t, int, int, const int32_t*, int, const int32_t*,       \
                                                  const int64_t*, T*, T*, const int64_t*, unsigned int*, int*,       \
-                                                 long long, int);
+                                                 long long, int, int);
 RS_INST_SWEEP(double)
 RS_INST_SWEEP(float)
 

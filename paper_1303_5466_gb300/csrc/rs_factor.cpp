@@ -226,7 +226,11 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
     if constexpr (is_cplx<T>::value) {
         return fail(RS_E_INVALID, "the symmetric sweep is for real kernels");
     } else {
-        const int NB = sweep_panel_width();
+        // panel width: the autotuner's for this launch shape (or the candidate being timed)
+        const std::string skey = tune_key("sweep", (int)sizeof(T), nb, max_m, 0);
+        const int NB = g_trial.sweep_nb > 0       ? g_trial.sweep_nb
+                       : op->opts.sweep_panel > 0 ? op->opts.sweep_panel
+                                                  : (int)tune_get(skey + ".nb", (double)sweep_panel_width());
         std::vector<int64_t> pb_off(nb);
         for (int b = 0; b < nb; ++b) pb_off[b] = 2 * (int64_t)NB * size_off[b];
         DevMem& d_pboff = op->t_pboff;
@@ -236,12 +240,10 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
         RS_CUDA(op->d_bar.alloc(sizeof(unsigned int) * nb));
         RS_CUDA(cudaMemsetAsync(op->d_bar.p, 0, sizeof(unsigned int) * nb, st));
         // panels are dealt back and forth, so a group of G CTAs wants at least 2G panels
-        const int cap = sweep_max_ctas<T>();
+        const int cap = sweep_max_ctas<T>(NB);
         int G = choose_group(nb, max_m * 16 / NB, [&](int) { return cap; });
         // the autotuner's group scale for this launch shape (or the candidate being timed)
-        const double gs = g_trial.sweep_gscale >= 0.0
-                              ? g_trial.sweep_gscale
-                              : tune_get(tune_key("sweep", (int)sizeof(T), nb, max_m, 0) + ".gscale", 1.0);
+        const double gs = g_trial.sweep_gscale >= 0.0 ? g_trial.sweep_gscale : tune_get(skey + ".gscale", 1.0);
         if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
         double work = 0.0;
         for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
@@ -267,7 +269,7 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
                 RS_CUDA(launch_sweep_inverse<T>(st, 1, Gb, nullptr, Gb, dm.as<int32_t>() + b, doff.as<int64_t>() + b,
                                                 A, op->d_pb.as<T>(), d_pboff.as<int64_t>() + b,
                                                 op->d_bar.as<unsigned int>() + b, op->d_status.as<int>(),
-                                                (long long)op->opts.spin_limit, mb));
+                                                (long long)op->opts.spin_limit, mb, NB));
             }
         } else {
             ProfScope ps(op, cls, st, work, 2.0 * sizeof(T) * (double)size_off[nb], level);
@@ -275,7 +277,7 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
                                             cta_off.empty() ? nb * G : cta_off[nb], dm.as<int32_t>(),
                                             doff.as<int64_t>(), A, op->d_pb.as<T>(), d_pboff.as<int64_t>(),
                                             op->d_bar.as<unsigned int>(), op->d_status.as<int>(),
-                                            (long long)op->opts.spin_limit, max_m));
+                                            (long long)op->opts.spin_limit, max_m, NB));
         }
         RS_CUDA(cudaStreamSynchronize(st));
         prof_flush(op);
@@ -1148,6 +1150,8 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
     if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 3) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 3");
+    if (op->opts.sweep_panel != 0 && op->opts.sweep_panel != 8 && op->opts.sweep_panel != 16)
+        return fail(RS_E_INVALID, "sweep_panel must be 0, 8 or 16");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))
         return fail(RS_E_INVALID, "forward_only combines with none of translation_invariant, k_cut, per_box");
     if (op->opts.translation_invariant < 0 || op->opts.translation_invariant > 2)
@@ -1742,12 +1746,13 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     o.k_cut = 0;
     const cudaStream_t st = (cudaStream_t)stream;
     // candidates: (CPQR group scale, CPQR variant (4 rows, 8 rows, look-ahead), sweep group
-    // scale, CPQR batch budget); every sweep scale appears, and the CPQR settings are picked
-    // per level as one triple
+    // scale, CPQR batch budget, sweep panel width); every sweep scale appears, and the CPQR
+    // settings are picked per level as one triple, the sweep's as one pair
     const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
                                 {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0},
-                                {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}, {2.0, 1, 1.0, 0.0}, {3.0, 0, 0.5, 0.0}};
-    constexpr int NTR = 10;
+                                {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}, {2.0, 1, 1.0, 0.0}, {3.0, 0, 0.5, 0.0},
+                                {1.0, 0, 1.0, 0.0, 16}, {1.0, 1, 0.5, 0.0, 16}};
+    constexpr int NTR = 12;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);
@@ -1816,12 +1821,16 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
             tune_set(k + ".deep", trials[b].cpqr_deep);
             tune_set(k + ".batch", trials[b].cpqr_batch);
             const int be = best_of(t_e);
-            tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".gscale", trials[be].sweep_gscale);
-            keys += 4;
+            const std::string ke = tune_key("sweep", esz, S.nb, S.k, 0);
+            tune_set(ke + ".gscale", trials[be].sweep_gscale);
+            tune_set(ke + ".nb", trials[be].sweep_nb > 0 ? trials[be].sweep_nb : sweep_panel_width());
+            keys += 5;
         }
         const int bf = best_of(t_f);
-        tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", trials[bf].sweep_gscale);
-        keys += 1;
+        const std::string kf = tune_key("sweep", esz, S.nb, S.m, 0);
+        tune_set(kf + ".gscale", trials[bf].sweep_gscale);
+        tune_set(kf + ".nb", trials[bf].sweep_nb > 0 ? trials[bf].sweep_nb : sweep_panel_width());
+        keys += 2;
     }
     // Each candidate was timed once: check the picks in one factorization on the new table, and
     // give the built-in setting back to every level whose kernel came out more than 3% slower
@@ -1842,8 +1851,14 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
                 tune_set(k + ".deep", -1.0);
                 tune_set(k + ".batch", 0.0);
             }
-            if (l >= 1 && v_e[l] > 1.03 * b_e[l]) tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".gscale", 1.0);
-            if (v_f[l] > 1.03 * b_f[l]) tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", 1.0);
+            if (l >= 1 && v_e[l] > 1.03 * b_e[l]) {
+                tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".gscale", 1.0);
+                tune_set(tune_key("sweep", esz, S.nb, S.k, 0) + ".nb", sweep_panel_width());
+            }
+            if (v_f[l] > 1.03 * b_f[l]) {
+                tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".gscale", 1.0);
+                tune_set(tune_key("sweep", esz, S.nb, S.m, 0) + ".nb", sweep_panel_width());
+            }
         }
     }
     double tuned_ms = 0.0;

@@ -191,6 +191,7 @@ struct TuneTrial {
     int cpqr_deep = -1;
     double sweep_gscale = -1.0;
     double cpqr_batch = -1.0;      // L2 batch budget of the CPQR launches, in units of 96 MB (0: none)
+    int sweep_nb = -1;             // panel width of the sweep (8 or 16)
 };
 extern thread_local TuneTrial g_trial;
 

@@ -163,8 +163,9 @@ int gj_max_ctas(int max_m, int nb);
 int gj_panel_width();
 
 // In-place inverse of nb symmetric positive definite matrices (real T) by the symmetric sweep
-// (k_sweep.cu), G CTAs per matrix (cooperative when G > 1): sizes m[b], offsets off[b]; Pb: 2 *
-// sweep_panel_width() * m[b] elements per matrix at pb_off[b] (16-byte aligned); bar: one
+// (k_sweep.cu), G CTAs per matrix (cooperative when G > 1), panels of nbw columns (8 =
+// sweep_panel_width(), or 16): sizes m[b], offsets off[b]; Pb: 2 * nbw * m[b] elements per
+// matrix at pb_off[b] (16-byte aligned); bar: one
 // counter per matrix, zeroed before the launch.  Reads the lower triangle, writes the full
 // inverse.  A matrix that is not SPD to working accuracy sets DEV_NOT_SPD and is left partly
 // swept.
@@ -172,9 +173,9 @@ int gj_panel_width();
 template <class T>
 cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, const int32_t* m,
                                  const int64_t* off, T* A, T* Pb, const int64_t* pb_off, unsigned int* bar,
-                                 int* status, long long spin_limit, int max_m);
+                                 int* status, long long spin_limit, int max_m, int nbw);
 template <class T>
-int sweep_max_ctas();
+int sweep_max_ctas(int nbw);
 int sweep_panel_width();
 
 // Grouped GEMM over `np` problems (device descriptors), total tiles `tiles`.

@@ -144,6 +144,7 @@ void rs_opts_default(rs_opts* o)
     o->spd_inverse = 1;
     o->cpqr_variant = -1;
     o->translation_invariant = 0;
+    o->sweep_panel = 0;
     o->forward_only = 0;
     o->solve_graph = 1;
     o->per_box = 0;

@@ -29,16 +29,19 @@ def _rel(x, y):
     return np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)
 
 
-def _factor(rs, n, leaf, eps, a, spd):
+def _factor(rs, n, leaf, eps, a, spd, panel=0):
     o = rs.rs_opts_default()
     o.spd_inverse = spd
+    o.sweep_panel = panel
     return rs.Solver(W.grid_points(n), leaf, a=a, eps=eps, opts=o)
 
 
+@pytest.mark.parametrize("panel", [8, 16])
 @pytest.mark.parametrize("n,leaf,eps", [(32, 8, 1e-10), (64, 8, 1e-10), (64, 16, 1e-6), (8, 2, 0.0)])
-def test_sweep_matches_pivoted_gauss_jordan(rs, n, leaf, eps):
+def test_sweep_matches_pivoted_gauss_jordan(rs, n, leaf, eps, panel):
+    """Panels of 8 and of 16 columns (a block of 8 x 8 or 16 x 16 pivots per step)."""
     a = W.coeff_a_batched(n)
-    S1 = _factor(rs, n, leaf, eps, a, 1)
+    S1 = _factor(rs, n, leaf, eps, a, 1, panel)
     S0 = _factor(rs, n, leaf, eps, a, 0)
     assert S1.stats()["spd_fallbacks"] == 0
     d = S1.stats()["depth"]
@@ -80,3 +83,8 @@ def test_indefinite_level_falls_back(rs, oracle_mod):
     f = W.rhs_uniform(n, 6)
     xo = oracle_mod.Factorization(n, leaf, eps, a=a).solve(f)
     assert _rel(S.solve(f), xo) <= 1e-9
+
+
+def test_bad_panel_width_is_refused(rs):
+    with pytest.raises(RuntimeError):
+        _factor(rs, 16, 4, 1e-10, None, 1, 12)
