@@ -35,7 +35,7 @@ WORKLOAD = "laplace_batched"
 PEAK_FP64_TFLOPS = 1.25
 # DRAM bytes per cpqr_kernel launch measured by ncu at this workload with one launch per level
 # (profiles/cpqr_kernel_dram_laplace_batched.md); to be re-taken whenever the kernel changes
-CPQR_TRAFFIC_BYTES_PER_LAUNCH = 143.8e9
+CPQR_TRAFFIC_BYTES_PER_LAUNCH = 143.5e9
 # FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
