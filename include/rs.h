@@ -191,6 +191,12 @@ int rs_fwd_apply(rs_op* op, const void* x, int64_t nrhs, void* y, void* stream);
  * share N and the kernel kind; M must be factored (not forward_only). */
 int rs_bicgstab(rs_op* A, rs_op* M, const void* f, void* x, double tol, int max_iter, int* iters, double* rel_res,
                 void* stream);
+/* Check of the bounded device-side waits: one CTA enters the group barrier of the cooperative
+ * kernels with a target that can never be reached.  The wait must end after `limit` polls and
+ * the call returns RS_E_TIMEOUT (the expected outcome; RS_E_CUDA if the wait returned without
+ * the timeout flag), with the CUDA context left usable.  stream: cudaStream_t or NULL.
+ * Synchronous. */
+int rs_wait_check(int64_t limit, void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of
  * its requests) still references it; NULL is accepted. */
 int rs_free(rs_op* op);

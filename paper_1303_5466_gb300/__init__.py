@@ -81,6 +81,7 @@ def lib():
         L.rs_factor.argtypes = [vp, C.POINTER(rs_kernel), dp, C.c_double, C.POINTER(rs_opts), vp, C.POINTER(vp)]
         L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_fwd_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.rs_wait_check.argtypes = [C.c_int64, vp]
         L.rs_bicgstab.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                                   C.POINTER(C.c_double), vp]
         L.rs_free.argtypes = [vp]
@@ -228,6 +229,12 @@ def rs_bicgstab(A, M, f, x, tol=1e-10, max_iter=100, stream=None):
     _check(lib().rs_bicgstab(A, M, _ptr(f), _ptr(x), float(tol), int(max_iter), C.byref(it), C.byref(rel),
                              _stream(stream)))
     return it.value, rel.value
+
+
+def rs_wait_check(limit, stream=None):
+    """A device-side wait that cannot complete, bounded by `limit` polls: raises RsError with
+    code RS_E_TIMEOUT, the expected outcome."""
+    _check(lib().rs_wait_check(int(limit), _stream(stream)))
 
 
 def rs_solve_noalloc(op, f, nrhs, x, stream=None):

@@ -216,6 +216,10 @@ cudaError_t launch_kblock_mv(cudaStream_t st, const KbProb* probs, const int64_t
                              const int32_t* pts, const T* x, T* y, int nrhs, const KernelK& K, const double* a);
 int kblock_rows_per_block();
 
+// One CTA waiting at a group barrier that can never complete (k_wait.cu): the bounded wait
+// must end after `limit` polls with DEV_TIMEOUT in *status.  ctr: one zeroed counter.
+cudaError_t launch_wait_check(cudaStream_t st, unsigned int* ctr, int* status, long long limit);
+
 // Vector kernels of BiCGstab (k_krylov.cu), T = double or cplx<double>: *out = sum conj(a_i) b_i
 // (part: dot_partials() scratch entries; fixed summation order), y = c0 x0 + c1 x1 + c2 x2.
 template <class T>
