@@ -139,6 +139,17 @@ def _dist():
     return world, rank, local
 
 
+def _init_group(backend, device=None, timeout_s=900.0):
+    """Process group of the replicas.  A rank that dies or never reaches a collective ends the
+    others' next collective with an error after timeout_s, instead of leaving them waiting."""
+    import datetime
+    import torch.distributed as dist
+    kw = {"timeout": datetime.timedelta(seconds=timeout_s)}
+    if device is not None:
+        kw["device_id"] = device
+    dist.init_process_group(backend, **kw)
+
+
 def _max_over_ranks(vals, world):
     """Element-wise max of per-rank values over all ranks (the slowest replica sets the time);
     the tensor lives where the process group's backend wants it (NCCL: the GPU, gloo: host)."""
@@ -493,8 +504,7 @@ def run_ours(args):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        _init_group("nccl", torch.device("cuda", local))
     import paper_1303_5466_gb300 as P
     from paper_1303_5466_gb300 import build as B
     B.build()
