@@ -168,13 +168,15 @@ def _replica_rate(world, units_per_rank, max_seconds):
     return world * units_per_rank / max_seconds
 
 
-def sample_share():
-    """Share of the factor flops in the ORACLE_LEVELS finest levels, from the per-level counts
-    that oracle/level_flops.py wrote from a full oracle factorization of this workload."""
+def sample_share(levels=None):
+    """Share of the factor flops in the `levels` (default ORACLE_LEVELS) finest levels, from the
+    per-level counts that oracle/level_flops.py wrote from a full oracle factorization of this
+    workload."""
+    levels = ORACLE_LEVELS if levels is None else levels
     with open(os.path.join(ROOT, "oracle", "laplace_batched_level_flops.json")) as fh:
         fl = {int(k): v for k, v in json.load(fh).items()}
     d = max(fl)
-    return sum(fl[l] for l in range(d - ORACLE_LEVELS + 1, d + 1)) / sum(fl.values())
+    return sum(fl[l] for l in range(d - levels + 1, d + 1)) / sum(fl.values())
 
 
 def oracle_sample(n, leaf, eps, a):
@@ -188,10 +190,25 @@ def oracle_sample(n, leaf, eps, a):
     dt = time.perf_counter() - t
     share = sample_share()
     est = dt / share
+    # one thread as well: the finest level of the 128 x 128 grid of the same a(x) (64 leaves of
+    # the same 16 x 16 size), scaled by the leaf count to this grid's finest level, then by
+    # that level's share of the flops -- a sample of a few seconds
+    ns = 128
+    a_s = W.coeff_a_batched(ns)
+    t = time.perf_counter()
+    O.Factorization(ns, leaf, eps, a=a_s, max_levels=1, threads=1)
+    dt1 = (time.perf_counter() - t) * (n // ns) ** 2
+    share1 = sample_share(1)
+    est1 = dt1 / share1
     return {"value": n * n / est, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
             "sample": "oracle factor of the %d finest levels of the %dx%d workload took %.2f s on %d threads; "
                       "those levels are %.1f%% of the factor flops, scaled to the full factor (%.1f s)"
-                      % (ORACLE_LEVELS, n, n, dt, cores, 100 * share, est)}
+                      % (ORACLE_LEVELS, n, n, dt, cores, 100 * share, est),
+            "single_thread": {"value": n * n / est1, "unit": "unknowns/s", "cores": 1,
+                              "sample": "the finest level (%d leaves of the %dx%d grid, scaled by leaf count to "
+                                        "%d) on 1 thread: %.2f s; %.1f%% of the factor flops, scaled to the full "
+                                        "factor (%.1f s)" % ((ns // leaf) ** 2, ns, ns, (n // leaf) ** 2, dt1,
+                                                            100 * share1, est1)}}
 
 
 SERVING_OPS = ((128, 16), (256, 16), (512, 16))
