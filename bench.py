@@ -33,8 +33,9 @@ WORKLOAD = "laplace_batched"
 # FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26 TFLOP/s, the 1.25
 # TFLOP/s FP64 figure of the profiling recipe (a register-only FMA probe measured 1.203).
 PEAK_FP64_TFLOPS = 1.25
-# DRAM bytes per cpqr_kernel launch measured by ncu at this workload with one launch per level
-# (profiles/cpqr_kernel_dram_laplace_batched.md); to be re-taken whenever the kernel changes
+# DRAM bytes (read + write) per cpqr_kernel launch, from one ncu capture of dram__bytes_read.sum
+# and dram__bytes_write.sum at this workload with one launch per level; None once the kernel
+# has changed since that capture
 CPQR_TRAFFIC_BYTES_PER_LAUNCH = 143.5e9
 # FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 PEAK_FP32_TFLOPS = 80.5
@@ -180,8 +181,12 @@ def sample_share(levels=None):
 
 
 def oracle_sample(n, leaf, eps, a):
-    """Time the CPU oracle on the ORACLE_LEVELS finest levels of the workload and scale to the
-    whole factorization by those levels' share of the algorithmic flops."""
+    """Time the CPU oracle on a bounded sample of the workload: the ORACLE_LEVELS finest levels
+    (every box of them) on all host cores, and the finest level alone on one thread (every box
+    of this grid's finest level, no rescaling across grids).  Each time is scaled to the whole
+    factorization by the sample's share of the algorithmic flops; that assumes the top levels,
+    where the oracle has only a few boxes to spread over its threads, run at the sample's rate,
+    so the extrapolated CPU rate is an upper bound on what a full oracle run achieves."""
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
@@ -190,25 +195,28 @@ def oracle_sample(n, leaf, eps, a):
     dt = time.perf_counter() - t
     share = sample_share()
     est = dt / share
-    # one thread as well: the finest level of the 128 x 128 grid of the same a(x) (64 leaves of
-    # the same 16 x 16 size), scaled by the leaf count to this grid's finest level, then by
-    # that level's share of the flops -- a sample of a few seconds
-    ns = 128
-    a_s = W.coeff_a_batched(ns)
     t = time.perf_counter()
-    O.Factorization(ns, leaf, eps, a=a_s, max_levels=1, threads=1)
-    dt1 = (time.perf_counter() - t) * (n // ns) ** 2
+    O.Factorization(n, leaf, eps, a=a, max_levels=1, threads=1)
+    dt1 = time.perf_counter() - t
     share1 = sample_share(1)
     est1 = dt1 / share1
-    return {"value": n * n / est, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
-            "sample": "oracle factor of the %d finest levels of the %dx%d workload took %.2f s on %d threads; "
-                      "those levels are %.1f%% of the factor flops, scaled to the full factor (%.1f s)"
-                      % (ORACLE_LEVELS, n, n, dt, cores, 100 * share, est),
-            "single_thread": {"value": n * n / est1, "unit": "unknowns/s", "cores": 1,
-                              "sample": "the finest level (%d leaves of the %dx%d grid, scaled by leaf count to "
-                                        "%d) on 1 thread: %.2f s; %.1f%% of the factor flops, scaled to the full "
-                                        "factor (%.1f s)" % ((ns // leaf) ** 2, ns, ns, (n // leaf) ** 2, dt1,
-                                                            100 * share1, est1)}}
+    return {"value": n * n / est, "unit": "unknowns/s", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": "oracle factor of the %d finest levels (all %d boxes) of the %dx%d workload: %.2f s measured on "
+                      "%d threads; those levels are %.1f%% of the factor flops, so the full factor is estimated at "
+                      "%.1f s (flop share, an optimistic bound for the CPU)"
+                      % (ORACLE_LEVELS, sum(2 ** (2 * _depth_half(n, leaf) - i) for i in range(ORACLE_LEVELS)),
+                         n, n, dt, cores, 100 * share, est),
+            "sample_s": dt, "flop_share": share, "full_factor_estimate_s": est,
+            "single_thread": {"value": n * n / est1, "unit": "unknowns/s", "cores": 1, "extrapolated": True,
+                              "sample": "the finest level of the %dx%d workload (all %d leaves) on 1 thread: %.2f s "
+                                        "measured; %.1f%% of the factor flops, scaled to the full factor (%.1f s)"
+                                        % (n, n, (n // leaf) ** 2, dt1, 100 * share1, est1),
+                              "sample_s": dt1, "flop_share": share1}}
+
+
+def _depth_half(n, leaf):
+    """log2(n / leaf): the tree has depth 2 x this, and 4^this leaves."""
+    return (n // leaf).bit_length() - 1
 
 
 SERVING_OPS = ((128, 16), (256, 16), (512, 16))
@@ -628,8 +636,8 @@ def run_ours(args):
         "roofline": {"kernel": dom, "classes": list(KERNEL_CLASSES[dom]), "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
                      "traffic": CPQR_TRAFFIC_BYTES_PER_LAUNCH if dom == "cpqr_kernel" else None,
-                     "traffic_note": "ncu DRAM read+write bytes per launch, one launch per level (no autotuner "
-                                     "batching), profiles/cpqr_kernel_dram_laplace_batched.md",
+                     "traffic_note": "ncu DRAM read+write bytes per launch at this workload, one launch per "
+                                     "level (no autotuner batching)",
                      "launches": nl, "avg_launch_ms": ms / max(nl, 1),
                      "peak_note": "FP64 ALU peak 152 SMs x 4 flop/clk x 2.07 GHz (recipe figure; no FP64 entry "
                                   "in the measured peaks)"},
@@ -645,7 +653,8 @@ def run_ours(args):
                                    "frac_fp64": kern[k][1] / (kern[k][0] * 1e-3) / 1e12 / PEAK_FP64_TFLOPS,
                                    "ms_per_step": kern[k][0] / K}
                                for k in kern if kern[k][0] > 0},
-        "e2e": {"value": world * N / e2e_s, "unit": "unknowns/s (build + factor + 4-RHS solve, host buffers)",
+        "e2e": {"value": world * N / e2e_s, "unit": "unknowns/s",
+                "step": "rs_build_tree + rs_factor + 4-RHS rs_solve from pinned host buffers, copies timed",
                 "h2d_bytes_per_step": N * 2 * 8 + N * 8 + N * nrhs * 8, "d2h_bytes_per_step": N * nrhs * 8},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -692,6 +701,12 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The oracle arm: every step (warm-up and timed) factors the ORACLE_LEVELS finest levels of
+    the workload (every box of them) with the oracle on all host cores, a bounded sample of the
+    whole factorization.  `ms_per_step` is that measured sample time.  `value` scales the mean
+    sample time to the full factor by the sample's share of the algorithmic flops (stated in
+    `extrapolation`), an optimistic bound for the CPU: the oracle spreads a level over its boxes,
+    and the top levels have only 2-8 of them."""
     world, rank, _ = _dist()
     if rank != 0:
         return
@@ -711,14 +726,18 @@ def run_reference(args):
     share = sample_share()
     est = dt / share
     v = n * n / est
+    boxes = sum(2 ** (2 * _depth_half(n, leaf) - i) for i in range(ORACLE_LEVELS))
+    sample = ("each step: oracle factor of the %d finest levels (all %d boxes) of the %dx%d workload on %d threads, "
+              "%.2f s measured on average" % (ORACLE_LEVELS, boxes, n, n, cores, dt))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": _config(n, leaf, eps, nrhs, world),
-           "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
-                            "sample": "each step: oracle factor of the %d finest levels (%.2f s on %d threads), "
-                                      "scaled by their %.1f%% share of the factor flops" % (ORACLE_LEVELS, dt, cores,
-                                                                                          100 * share)},
+           "extrapolation": {"sample_ms_per_step": dt * 1e3, "flop_share": share,
+                             "extrapolated_ms_full_factor": est * 1e3,
+                             "rule": "value = N / (sample time / flop share of the sampled levels)"},
+           "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle", "sample": sample,
+                            "extrapolated": True},
            "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

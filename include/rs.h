@@ -165,7 +165,8 @@ int rs_factor(const rs_tree* tree, const rs_kernel* kernel, const double* a, dou
 /* Inverse apply (Algorithm 6): x = A^{-1} f for nrhs right-hand sides.  f, x: N x nrhs
  * column-major in input order, double (Laplace) or interleaved complex128 (Helmholtz);
  * either both device pointers or both host pointers (detected per call; host buffers are
- * staged through device memory inside the call).  x may not alias f.  The call returns
+ * staged through device memory inside the call).  Device buffers must live on the
+ * operator's GPU (memory of another GPU: RS_E_INVALID).  x may not alias f.  The call returns
  * after x is written (host) or after the work is enqueued on `stream` (device). */
 int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream);
 /* Forward apply y = A x through the HSS form of A that the factorization's IDs define: the
@@ -219,10 +220,12 @@ int rs_residual(rs_op* op, const void* x, const void* f, int64_t nrhs, double* r
  * cudaMalloc on first use; rs_solve_noalloc computes the same x = A^{-1} f with its workspace
  * in one fixed device array of RS_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB), which every GPU
  * that loads this library holds until the process exits, and calls no allocating routine.
- *   - f, x: device pointers only (host buffers: RS_E_INVALID), N x nrhs column-major in input
- *     order; real FP64 operators only (RS_LAPLACE factored in RS_FP64);
+ *   - f, x: device pointers on the operator's GPU only (host buffers, or memory of another
+ *     GPU: RS_E_INVALID), N x nrhs column-major in input order; real FP64 operators only
+ *     (RS_LAPLACE factored in RS_FP64);
  *   - the workspace grows linearly with nrhs (about 3 x N x nrhs doubles plus small terms);
- *     a request that does not fit returns RS_E_INVALID, names the size it needed in
+ *     a request that does not fit (any nrhs above RS_NOALLOC_SCRATCH_DOUBLES / N among them,
+ *     refused before any size arithmetic) returns RS_E_INVALID, names the size in
  *     rs_last_error(), and launches nothing;
  *   - the first call on a device looks up the array's device address (once per device, with
  *     that device current); make that first call before any stream capture;
@@ -239,7 +242,9 @@ typedef struct {
     int64_t n_side;
     int64_t root_m;
     int64_t bytes_factors;       /* device bytes of the stored factors (Phi, E, T, indices) */
-    int64_t bytes_workspace;     /* device bytes of reusable workspace                     */
+    int64_t bytes_workspace;     /* device bytes of the solve workspace rs_solve has grown so
+                                    far (0 until the first rs_solve; rs_solve_noalloc adds
+                                    nothing)                                              */
     double flops_factor;         /* algorithmic flops of the factorization (the sum of the
                                     per-class formulas listed with RS_PROF_*)            */
     double flops_solve_per_rhs;  /* algorithmic flops of one inverse apply per RHS         */

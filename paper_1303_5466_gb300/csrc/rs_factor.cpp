@@ -1059,6 +1059,22 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool on_other_device(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.device != dev;
+}
+
 // Algorithm 1 over all levels in storage precision T: IDs (d..1), inverses (d..1), root.
 template <class T>
 int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
@@ -1702,6 +1718,8 @@ int rs_fwd_apply(rs_op* op, const void* x, int64_t nrhs, void* y, void* stream)
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
+    if (on_other_device(x) || on_other_device(y))
+        return fail(RS_E_INVALID, "x or y is device memory of another GPU than the operator's");
     return fwd_impl(op, x, nrhs, y, (cudaStream_t)stream);
 }
 
@@ -1714,6 +1732,8 @@ int rs_solve(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream)
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
+    if (on_other_device(f) || on_other_device(x))
+        return fail(RS_E_INVALID, "f or x is device memory of another GPU than the operator's");
     return solve_impl(op, f, nrhs, x, (cudaStream_t)stream);
 }
 
@@ -1895,6 +1915,13 @@ int rs_op_stats(const rs_op* op, rs_stats* out)
 {
     if (!op || !out) return fail(RS_E_INVALID, "NULL argument");
     *out = op->stats;
+    // the solve workspace as it stands now (grown by rs_solve on demand; rs_solve_noalloc
+    // never touches it)
+    int64_t ws = 0;
+    for (const DevMem* m : {&op->s_u, &op->s_w, &op->s_g, &op->s_phi, &op->s_t, &op->s_z, &op->s_in, &op->s_out,
+                            &op->s_out2, &op->s_fs})
+        ws += (int64_t)m->cap;
+    out->bytes_workspace = ws;
     return RS_OK;
 }
 

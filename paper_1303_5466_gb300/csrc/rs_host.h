@@ -203,6 +203,9 @@ SolveLayout solve_layout(const rs_op* op, int64_t nrhs);
 int solve_run(rs_op* op, const SolveLayout& Ls, const SolveWork& ws, const double* fd, double* xd, int64_t nrhs,
               cudaStream_t st, bool profile);
 bool is_device_ptr(const void* p);
+// True when p is device memory of a GPU other than the current one (kernels of the current
+// device cannot read it without peer access, so the entry points refuse it).
+bool on_other_device(const void* p);
 int choose_group(int nb, int max_cols, const std::function<int(int)>& capacity);
 
 // Extra compression (rs_hss1d.cpp).  Orders of Sec. 3.1 for box j of level l of an n x n grid:

@@ -793,6 +793,7 @@ int rs_hss1d_build(const void* M, int64_t n, int is_complex, const int64_t* orde
     cudaStream_t st = (cudaStream_t)stream;
     const size_t esz = is_complex ? 2 * sizeof(double) : sizeof(double);
     const void* Md = M;
+    if (on_other_device(M)) return fail(RS_E_INVALID, "M is device memory of another GPU than the current one");
     if (!is_device_ptr(M)) {
         RS_CUDA(h->m_dev.alloc(esz * (size_t)(n * n)));
         RS_CUDA(cudaMemcpyAsync(h->m_dev.p, M, esz * (size_t)(n * n), cudaMemcpyHostToDevice, st));
@@ -819,6 +820,8 @@ int rs_hss1d_apply(rs_hss* h, const void* x, int64_t nrhs, void* y, void* stream
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != h->device) return fail(RS_E_INVALID, "the current device is not the one the form was built on");
+    if (on_other_device(x) || on_other_device(y))
+        return fail(RS_E_INVALID, "x or y is device memory of another GPU than the form's");
     const bool dx = is_device_ptr(x), dy = is_device_ptr(y);
     if (dx != dy) return fail(RS_E_INVALID, "x and y must both be host or both be device pointers");
     cudaStream_t st = (cudaStream_t)stream;

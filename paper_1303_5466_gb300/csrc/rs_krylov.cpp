@@ -124,6 +124,14 @@ int rs_bicgstab(rs_op* A, rs_op* M, const void* f, void* x, double tol, int max_
     if (A->N != M->N || A->kind != M->kind) return fail(RS_E_INVALID, "A and M differ in size or kernel kind");
     if (M->opts.forward_only) return fail(RS_E_INVALID, "the preconditioner must be a factored operator");
     if (!is_device_ptr(f) || !is_device_ptr(x)) return fail(RS_E_INVALID, "f and x must be device pointers");
+    {
+        int dev = 0;
+        RS_CUDA(cudaGetDevice(&dev));
+        if (dev != A->device || dev != M->device)
+            return fail(RS_E_INVALID, "the current device is not the one the operators were factored on");
+        if (on_other_device(f) || on_other_device(x))
+            return fail(RS_E_INVALID, "f or x is device memory of another GPU than the operators'");
+    }
     const cudaStream_t st = (cudaStream_t)stream;
     if (A->kind == RS_HELMHOLTZ)
         return bicgstab_t<cplx<double>>(A, M, (const cplx<double>*)f, (cplx<double>*)x, tol, max_iter, iters, rel_res,

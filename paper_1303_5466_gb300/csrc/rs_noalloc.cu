@@ -48,12 +48,20 @@ using namespace rs;
 extern "C" int rs_solve_noalloc(rs_op* op, const void* f, int64_t nrhs, void* x, void* stream)
 {
     if (!op || !f || !x || nrhs < 1) return fail(RS_E_INVALID, "bad argument");
+    // Bound nrhs before any size arithmetic: the workspace needs at least N doubles per
+    // column, so a larger nrhs cannot fit (and would overflow the layout's products).
+    if (op->N < 1 || nrhs > (int64_t)RS_NOALLOC_SCRATCH_DOUBLES / op->N)
+        return fail(RS_E_INVALID, "rs_solve_noalloc: nrhs=" + std::to_string(nrhs) +
+                                      " needs more workspace than its fixed scratch of " +
+                                      std::to_string((int64_t)RS_NOALLOC_SCRATCH_DOUBLES) + " doubles (use rs_solve)");
     if (f == x) return fail(RS_E_INVALID, "x may not alias f");
     if (op->kind != RS_LAPLACE || op->opts.precision != RS_FP64 || op->opts.forward_only)
         return fail(RS_E_INVALID, "rs_solve_noalloc covers real FP64 (RS_FP64 Laplace) factored operators");
     int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
+    if (on_other_device(f) || on_other_device(x))
+        return fail(RS_E_INVALID, "f or x is device memory of another GPU than the operator's");
     if (!is_device_ptr(f) || !is_device_ptr(x))
         return fail(RS_E_INVALID, "rs_solve_noalloc takes device pointers only (host buffers would need staging)");
     const SolveLayout Ls = solve_layout(op, nrhs);

@@ -257,6 +257,8 @@ extern "C" int rs_residual(rs_op* op, const void* x, const void* f, int64_t nrhs
     RS_CUDA(cudaGetDevice(&dev));
     if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
     cudaStream_t st = (cudaStream_t)stream;
+    if (on_other_device(x) || on_other_device(f))
+        return fail(RS_E_INVALID, "x or f is device memory of another GPU than the operator's");
     const bool dx = is_device_ptr(x), df = is_device_ptr(f);
     if (dx != df) return fail(RS_E_INVALID, "x and f must both be device or both be host pointers");
     const size_t io = op->kind == RS_HELMHOLTZ ? 2 * sizeof(double) : sizeof(double);

@@ -344,6 +344,13 @@ int rs_server_submit(rs_server* s, int op_index, const void* f, int64_t nrhs, vo
     if (f == x) return fail(RS_E_INVALID, "x may not alias f");
     if (!is_device_ptr(f) || !is_device_ptr(x)) return fail(RS_E_INVALID, "the server takes device buffers");
     rs_op* op = s->ops[op_index];
+    {
+        int dev = 0;
+        RS_CUDA(cudaGetDevice(&dev));
+        if (dev != op->device) return fail(RS_E_INVALID, "the current device is not the one the operator was factored on");
+        if (on_other_device(f) || on_other_device(x))
+            return fail(RS_E_INVALID, "f or x is device memory of another GPU than the operator's");
+    }
     Req* r = new (std::nothrow) Req();
     if (!r) return fail(RS_E_NOMEM, "host allocation");
     r->op = op_index;

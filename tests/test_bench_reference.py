@@ -31,6 +31,11 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("laplace_batched")
+    # ms_per_step is the measured sample time; the full-factor figure is named as extrapolated
+    ex = d["extrapolation"]
+    assert abs(d["ms_per_step"] - ex["sample_ms_per_step"]) <= 1e-9 * d["ms_per_step"]
+    assert ex["extrapolated_ms_full_factor"] > d["ms_per_step"] and 0 < ex["flop_share"] < 1
+    assert abs(d["value"] * ex["extrapolated_ms_full_factor"] * 1e-3 - d["config"]["N"]) <= 1e-6 * d["config"]["N"]
 
 
 def test_reference_arm_other_ranks_are_silent():

@@ -2,7 +2,8 @@
 
 Requests of different operators and RHS counts are admitted while others run, share launches
 tick by tick, and must give the same result as rs_solve alone (the same per-request
-arithmetic: identical bits expected, 1e-13 asserted).  Admission respects the memory budget,
+arithmetic: identical bits expected, 1e-13 asserted), and every served result must match
+the oracle's inverse apply within the 1e-9 FP64 solution tolerance.  Admission respects the memory budget,
 and host-side failures (bad arguments, an operator freed while referenced, a request that
 can never fit) are reported as error codes, with no GPU fault involved.
 """
@@ -89,6 +90,36 @@ def test_results_equal_alone_and_in_the_mix(env):
         assert worst <= 1e-13, worst
         lat = P.rs_server_latencies(srv)
         assert len(lat) == 40 and (lat > 0).all()
+    finally:
+        P.rs_server_free(srv)
+
+
+def test_served_results_match_oracle(env, oracle_mod):
+    """Every request served in the mix (several operators, 1-64 right-hand sides, arriving while
+    others run) is compared with the oracle's inverse apply of the same operator (Algorithm 6
+    over the oracle's own factorization) within the 1e-9 FP64 solution tolerance."""
+    import torch
+    P, ops = env
+    orc = [oracle_mod.Factorization(n, leaf, 1e-10) for n, leaf in SPECS]
+    reqs = _requests(30, 11, max_rhs=64)
+    srv = P.rs_server_create(ops, 512 << 20, max_inflight=16)
+    try:
+        fs = [torch.from_numpy(F).cuda() for _, _, F in reqs]
+        xs = [torch.full_like(f, np.nan) for f in fs]
+        torch.cuda.synchronize()
+        for i, (k, nrhs, _) in enumerate(reqs):
+            P.rs_server_submit(srv, k, fs[i], nrhs, xs[i])
+            if i == 14:
+                time.sleep(0.01)          # the second half arrives while the first runs
+        P.rs_server_drain(srv, 120.0)
+        torch.cuda.synchronize()
+        assert P.rs_server_stats(srv)["peak_inflight"] > 1
+        for (k, nrhs, F), x in zip(reqs, xs):
+            got = x.cpu().numpy()                       # (nrhs, N): column-major N x nrhs
+            want = orc[k].solve(np.ascontiguousarray(F.T)).reshape(-1, nrhs).T
+            for c in range(nrhs):
+                rel = np.linalg.norm(got[c] - want[c]) / np.linalg.norm(want[c])
+                assert rel <= 1e-9, (k, nrhs, c, rel)
     finally:
         P.rs_server_free(srv)
 

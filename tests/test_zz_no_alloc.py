@@ -71,3 +71,45 @@ def test_noalloc_refuses_oversize_and_host_buffers(small):
     with pytest.raises(P.RsError) as e:
         P.rs_solve_noalloc(op, fh, 1, np.zeros(n * n))
     assert e.value.code == P.RS_E_INVALID
+
+
+def test_noalloc_refuses_huge_nrhs_before_size_arithmetic(small):
+    import torch
+    P, op, n = small
+    f = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    x = torch.full_like(f, 7.0)
+    for nrhs in (1 << 40, (1 << 51) + 3):        # products with the layout offsets would overflow
+        with pytest.raises(P.RsError) as e:
+            P.rs_solve_noalloc(op, f, nrhs, x, torch.cuda.current_stream())
+        assert e.value.code == P.RS_E_INVALID and "workspace" in str(e.value)
+    torch.cuda.synchronize()
+    assert bool((x == 7.0).all())
+
+
+def test_noalloc_on_fresh_operator_grows_no_workspace():
+    """On an operator that rs_solve has never touched, rs_solve_noalloc alone leaves the
+    operator's own solve workspace at zero bytes, and still matches the oracle-checked
+    rs_solve computed afterwards."""
+    import torch
+    from paper_1303_5466_gb300 import build as B
+    B.build()
+    import paper_1303_5466_gb300 as P
+    n, leaf, eps = 32, 8, 1e-10
+    tree = P.rs_build_tree(W.grid_points(n), leaf)
+    op = P.rs_factor(tree, eps=eps)
+    try:
+        assert P.rs_op_stats(op)["bytes_workspace"] == 0
+        f = _dev(W.rhs_normal(n, 21, nrhs=3))
+        x_na = torch.full_like(f, np.nan)
+        for _ in range(2):
+            P.rs_solve_noalloc(op, f, 3, x_na, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert P.rs_op_stats(op)["bytes_workspace"] == 0
+        x_ref = torch.empty_like(f)
+        P.rs_solve(op, f, 3, x_ref, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert P.rs_op_stats(op)["bytes_workspace"] > 0
+        assert _rel(x_na.cpu().numpy(), x_ref.cpu().numpy()) <= SOL_TOL
+    finally:
+        P.rs_free(op)
+        P.rs_free_tree(tree)
