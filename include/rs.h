@@ -198,6 +198,15 @@ int rs_bicgstab(rs_op* A, rs_op* M, const void* f, void* x, double tol, int max_
  * the timeout flag), with the CUDA context left usable.  stream: cudaStream_t or NULL.
  * Synchronous. */
 int rs_wait_check(int64_t limit, void* stream);
+
+/* Throughput probe of an FP64 pipe (no counterpart in the paper: it measures the roofline that
+ * bounds the FP64 factorization of Sec. 4's work model on the present GPU).  kind:
+ * RS_PROBE_DFMA, independent FP64 fused multiply-add chains on the CUDA cores; RS_PROBE_DMMA,
+ * independent mma.sync m8n8k4 FP64 matrix instructions.  Each runs register-only chains on 64
+ * warps per SM; the best of three timed launches (after one warm-up, CUDA events on `stream`)
+ * gives *tflops_out (host).  Synchronous; allocates a few KB of device memory. */
+enum { RS_PROBE_DFMA = 0, RS_PROBE_DMMA = 1 };
+int rs_fp64_probe(int kind, double* tflops_out, void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of
  * its requests) still references it; NULL is accepted. */
 int rs_free(rs_op* op);

@@ -82,6 +82,7 @@ def lib():
         L.rs_solve.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_fwd_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.rs_wait_check.argtypes = [C.c_int64, vp]
+        L.rs_fp64_probe.argtypes = [C.c_int, dp, vp]
         L.rs_bicgstab.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int),
                                   C.POINTER(C.c_double), vp]
         L.rs_free.argtypes = [vp]
@@ -235,6 +236,17 @@ def rs_wait_check(limit, stream=None):
     """A device-side wait that cannot complete, bounded by `limit` polls: raises RsError with
     code RS_E_TIMEOUT, the expected outcome."""
     _check(lib().rs_wait_check(int(limit), _stream(stream)))
+
+
+RS_PROBE_DFMA, RS_PROBE_DMMA = 0, 1
+
+
+def rs_fp64_probe(kind, stream=None):
+    """Measured FP64 throughput (TFLOP/s) of DFMA chains (RS_PROBE_DFMA) or mma.sync f64
+    matrix instructions (RS_PROBE_DMMA) on the current device."""
+    out = C.c_double()
+    _check(lib().rs_fp64_probe(int(kind), C.byref(out), _stream(stream)))
+    return out.value
 
 
 def rs_solve_noalloc(op, f, nrhs, x, stream=None):

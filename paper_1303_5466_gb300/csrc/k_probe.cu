@@ -1,0 +1,108 @@
+// k_probe.cu -- throughput probes of the FP64 pipes this library's factorization runs on.
+//
+// The factor and the solve are FP64 dense linear algebra, so the roofline that bounds them is
+// the chip's FP64 rate, which GB300 gives through two routes: the FP64 FMA of the CUDA cores
+// (DFMA) and the FP64 matrix instruction (mma.sync m8n8k4 .f64, "DMMA").  Each probe keeps
+// every warp busy with independent register-only chains of one instruction kind, long enough
+// that launch cost is negligible, and returns the achieved rate from CUDA-event timing.  The
+// larger of the two is the FP64 peak the benchmark divides by; their ratio decides which pipe
+// the FP64 contractions should use.
+#include "k_common.cuh"
+#include "rs.h"
+#include "rs_host.h"
+
+namespace rs {
+
+namespace {
+
+constexpr int PROBE_NT = 256;
+constexpr int PROBE_CHAINS = 8;
+
+// DFMA: 8 independent chains per thread, a = a * m + c (m, c kept near 1 so nothing overflows
+// or underflows over the iterations).
+__global__ void __launch_bounds__(PROBE_NT) dfma_probe_kernel(int iters, double m, double c, double* out)
+{
+    double a[PROBE_CHAINS];
+#pragma unroll
+    for (int q = 0; q < PROBE_CHAINS; ++q) a[q] = 1.0 + 1e-3 * (threadIdx.x + q);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < PROBE_CHAINS; ++q) a[q] = fma(a[q], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < PROBE_CHAINS; ++q) s += a[q];
+    if (s == 12345.678) out[blockIdx.x] = s;      // never true: keeps the chains live
+}
+
+// DMMA: 4 independent m8n8k4 accumulations per warp, D = A B + D with A, B fixed fragments of
+// small values (each step adds a bounded amount; no overflow over the iterations).
+__global__ void __launch_bounds__(PROBE_NT) dmma_probe_kernel(int iters, double av, double bv, double* out)
+{
+    double d[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q][0] = d[q][1] = 0.0;
+    const double a = av * (1.0 + 1e-3 * (threadIdx.x & 31));
+    const double b = bv;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                         : "+d"(d[q][0]), "+d"(d[q][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += d[q][0] + d[q][1];
+    if (s == 12345.678) out[blockIdx.x] = s;
+}
+
+}  // namespace
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
+{
+    if (!tflops_out || (kind != RS_PROBE_DFMA && kind != RS_PROBE_DMMA)) return fail(RS_E_INVALID, "bad argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 8 * sms;                     // 8 CTAs of 256 threads per SM: 64 warps
+    const int iters = kind == RS_PROBE_DFMA ? 4096 : 1024;
+    DevMem out;
+    RS_CUDA(out.alloc(sizeof(double) * (size_t)blocks));
+    cudaEvent_t e0, e1;
+    RS_CUDA(cudaEventCreate(&e0));
+    RS_CUDA(cudaEventCreate(&e1));
+    float best = 0.0f;
+    for (int rep = 0; rep < 4; ++rep) {             // rep 0 warms up; the best of the others
+        cudaEventRecord(e0, st);
+        count_launches(1);
+        if (kind == RS_PROBE_DFMA)
+            dfma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
+        else
+            dmma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 1e-3, 1e-3, out.as<double>());
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "probe kernel");
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RS_CUDA(cudaGetLastError());
+    const double threads = (double)blocks * PROBE_NT;
+    // DFMA: 2 flops per FMA; DMMA: 8 x 8 x 4 FMAs = 512 flops per warp-instruction
+    const double flops = kind == RS_PROBE_DFMA ? threads * iters * PROBE_CHAINS * 2.0
+                                                : threads / 32.0 * iters * 4 * 512.0;
+    *tflops_out = flops / (best * 1e-3) / 1e12;
+    return RS_OK;
+}

@@ -8,7 +8,7 @@ is loaded), against the oracle's factorization of the same workload over the who
 - every box of every level: sizes (m, k, r, near rows), active sets and skeleton sets
   identical (integer results, bit-exact);
 - factor blocks on sampled boxes of every level (every box of levels 1-2) and the root
-  inverse, within the block tolerances derived in test_gpu_parity;
+  inverse, within the block tolerances derived in test_blocks_match_oracle_on_every_level;
 - the 4-RHS solution within the 1e-9 FP64 tolerance of the oracle's solution;
 - the true residual on sampled rows (computed entry by entry by the oracle) within 10 eps.
 """
@@ -58,21 +58,39 @@ def test_every_level_matches_oracle(full):
 
 
 def test_blocks_match_oracle_on_every_level(full):
+    """Block tolerances.  A leaf's F^{-1} involves no T: 1e-11 (as in test_gpu_parity).  T =
+    R11^{-1} R12 with |R_kk| / |R_11| ~ eps carries rounding differences of R amplified by up
+    to 1/eps: 100 u / eps = 1e-4.  E, F^{-1} above the leaves and the root inverse are built
+    from the children's T and E, so they carry those differences too; at this size their
+    condition numbers reach 1e4 (|F^{-1}| ~ 4e3 at level 1) and the small-grid bound of 1e-6
+    no longer holds, so they are held to T's bound, 1e-4.  The solution itself is held to
+    1e-9 below.  The largest observed difference per kind is printed."""
     P, op, orc, d = full["P"], full["op"], full["orc"], full["d"]
     rng = np.random.default_rng(0)
+    worst = {"Finv_leaf": 0.0, "Finv": 0.0, "E": 0.0, "T": 0.0}
+    bad = []
+
+    def rel(a, b, floor=0.0):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(a), floor))
+
     for l in range(d, 0, -1):
         boxes = range(2 ** l) if l <= 2 else rng.choice(2 ** l, 3, replace=False)
         for j in boxes:
-            fi = P.rs_op_box_matrix(op, l, j, 1)
-            ftol = 1e-11 if l == d else 1e-6                                      # see test_gpu_parity
-            assert np.linalg.norm(fi - orc.Finv(l, j)) <= ftol * np.linalg.norm(fi), ("Finv", l, j)
-            e = P.rs_op_box_matrix(op, l, j, 2)
-            assert np.linalg.norm(e - orc.E(l, j)) <= 1e-6 * np.linalg.norm(e), ("E", l, j)
+            kf = "Finv_leaf" if l == d else "Finv"
+            checks = [(kf, rel(P.rs_op_box_matrix(op, l, j, 1), orc.Finv(l, j)), 1e-11 if l == d else 1e-4),
+                      ("E", rel(P.rs_op_box_matrix(op, l, j, 2), orc.E(l, j)), 1e-4)]
             t = P.rs_op_box_matrix(op, l, j, 0)
             if t.size:
-                assert np.linalg.norm(t - orc.T(l, j)) <= 1e-4 * max(np.linalg.norm(t), 1.0), ("T", l, j)
+                checks.append(("T", rel(t, orc.T(l, j), 1.0), 1e-4))
+            for kind, v, tol in checks:
+                worst[kind] = max(worst[kind], v)
+                if not v <= tol:
+                    bad.append((kind, l, int(j), v))
     r = P.rs_op_root_matrix(op)
-    assert np.linalg.norm(r - orc.root_inv()) <= 1e-6 * np.linalg.norm(r)
+    root = rel(r, orc.root_inv())
+    print("largest relative block differences:", worst, "root inverse %.2e" % root)
+    assert not bad, bad[:10]
+    assert root <= 1e-4
 
 
 def test_solution_matches_oracle(full):
