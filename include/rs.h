@@ -102,9 +102,13 @@ typedef struct {
                                     (one pass per step: the update of step s fused with the
                                     dot products of step s+1); 3 = 0 with the lists of open
                                     columns in global memory (taken by 0 and 1 by themselves
-                                    for boxes whose lists do not fit shared memory); -1 = the
-                                    autotuner's table (rs_autotune), else 0 or 1 by
-                                    occupancy. Same result up to rounding order       [-1]   */
+                                    for boxes whose lists do not fit shared memory); 4 =
+                                    each box held in the shared memory of one thread-block
+                                    cluster for the whole factorization (levels whose boxes
+                                    fit 16 CTAs; the others take the default); -1 = the
+                                    autotuner's table (rs_autotune), else 4 where it fits,
+                                    else 0 or 1 by occupancy. Same result up to rounding
+                                    order                                             [-1]   */
     int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the
                                     offset between grid points (Sec. 5: one set of matrix
                                     blocks per level).  1: each level's ID is taken once, on

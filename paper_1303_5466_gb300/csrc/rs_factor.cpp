@@ -371,7 +371,7 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     struct Batch {
-        int b0, nb, G, ctas, deep, max_r, max_m;
+        int b0, nb, G, ctas, deep, max_r, max_m, cl;
         size_t cta_pos;
     };
     std::vector<Batch> bats;
@@ -385,9 +385,21 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
             B.max_r = std::max<int>(B.max_r, (int)L.r[b]);
             B.max_m = std::max<int>(B.max_m, (int)L.m[b]);
         }
+        // boxes that fit the shared memory of one cluster stay there for the whole
+        // factorization (variant 4, the default where it fits)
+        B.cl = 0;
+        if (!op->opts.per_box && (deep_set == 4 || deep_set < 0)) B.cl = cpqr_cl_cluster<T>(B.max_r, B.max_m);
+        if (B.cl > 0) {
+            B.G = 1;
+            B.ctas = B.nb * B.cl;
+            B.deep = 4;
+            B.cta_pos = (size_t)-1;
+            bats.push_back(B);
+            continue;
+        }
         // the open columns are re-split every step, so a group may take one CTA per 16 columns
         // (sized for the co-residency of the variant when one is set)
-        const int var = deep_set >= 0 ? deep_set : 0;
+        const int var = deep_set >= 0 && deep_set <= 3 ? deep_set : 0;
         int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g, var); });
         if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
         // gs > 1 (large boxes, few per launch): more CTAs than one per 16 columns, so that more
@@ -422,7 +434,7 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         }
         // few CTAs per SM: each warp keeps twice the rows in flight
         B.deep = (G > 1 && B.ctas <= 2 * sms) ? 1 : 0;
-        if (deep_set >= 0) B.deep = deep_set;
+        if (deep_set >= 0 && deep_set <= 3) B.deep = deep_set;
         if (B.deep && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, B.deep)) B.deep = 0;   // must stay co-resident
         max_keys = std::max(max_keys, (size_t)(2 * B.ctas));
         bats.push_back(B);
@@ -433,7 +445,8 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
     }
     RS_CUDA(w.keys.alloc(sizeof(unsigned long long) * max_keys));
     size_t gw_ints = 0;        // open-column lists in global memory (boxes too large for shared)
-    for (const Batch& B : bats) gw_ints = std::max(gw_ints, cpqr_gwork_ints<T>(B.max_r, B.max_m, B.deep, B.ctas));
+    for (const Batch& B : bats)
+        if (!B.cl) gw_ints = std::max(gw_ints, cpqr_gwork_ints<T>(B.max_r, B.max_m, B.deep, B.ctas));
     if (gw_ints) RS_CUDA(w.gwork.alloc(sizeof(int) * gw_ints));
     // squared norms, their references, and (look-ahead variant) the dot products v^H y_j
     const size_t nrm_dbl = 2 * (size_t)(sum_m + 1), wv_dbl = ((size_t)(sum_m + 1) * sizeof(T) + 7) / 8;
@@ -442,6 +455,13 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         // the rank is known only afterwards: the work is added once k is read back
         ProfScope ps(op, RS_PROF_CPQR, st, 0.0, 0.0, L.l);
         for (const Batch& B : bats) {
+            if (B.cl) {
+                RS_CUDA(launch_cpqr_cl<T>(st, B.nb, B.cl, L.d_act_off.as<int64_t>() + B.b0, w.nn.as<int32_t>() + B.b0, P,
+                                          w.y_off.as<int64_t>() + B.b0, w.Y.as<T>(), op->eps,
+                                          L.d_k.as<int32_t>() + B.b0, w.piv.as<int32_t>(), w.diag.as<T>(),
+                                          op->d_status.as<int>(), B.max_r, B.max_m));
+                continue;
+            }
             RS_CUDA(launch_cpqr<T>(st, B.nb, B.G,
                                    B.cta_pos == (size_t)-1 ? nullptr : w.cta_off.as<int32_t>() + B.cta_pos, B.ctas,
                                    B.deep, L.d_act_off.as<int64_t>() + B.b0, w.nn.as<int32_t>() + B.b0, P,
@@ -1165,7 +1185,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
-    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 3) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 3");
+    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 4) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 4");
     if (op->opts.sweep_panel != 0 && op->opts.sweep_panel != 8 && op->opts.sweep_panel != 16)
         return fail(RS_E_INVALID, "sweep_panel must be 0, 8 or 16");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))

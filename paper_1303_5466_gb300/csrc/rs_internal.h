@@ -128,6 +128,17 @@ cudaError_t launch_cpqr_la(cudaStream_t st, int nb, int G, const int32_t* cta_of
                            long long spin_limit, int max_r, int max_m, double* nrm, double* ref, T* wv);
 template <class T>
 int cpqr_la_max_ctas(int max_r, int max_m);
+// Variant 4 (k_cpqr_cl.cu): one thread-block cluster of C CTAs per box, the box's Y held in the
+// clusters' shared memory for the whole factorization (read once, R written back once).
+// cpqr_cl_cluster: the cluster size for boxes up to max_r x max_m, 0 when they do not fit.
+// Same outputs as launch_cpqr (kout, piv, diag, R in rows < k of Y); no barrier words, keys or
+// norm arrays in global memory.
+template <class T>
+int cpqr_cl_cluster(int max_r, int max_m);
+template <class T>
+cudaError_t launch_cpqr_cl(cudaStream_t st, int nb, int C, const int64_t* act_off, const int32_t* nnear, int P,
+                           const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag, int* status,
+                           int max_r, int max_m);
 
 // T = R11^{-1} R12 for every box, written column-major (k x (m-k)) at t_off[b], rows by
 // sorted skeleton position (skpos[pivot position]) and columns by residual rank.
