@@ -30,9 +30,10 @@ from paper_1303_5466_gb300 import workloads as W  # noqa: E402
 
 METRIC = "factor unknowns/sec and solve RHS/sec at 1e-10 residual; serving p50/p99 latency"
 WORKLOAD = "laplace_batched"
-# FP64 ALU peak of one GB300: 152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26 TFLOP/s, the 1.25
-# TFLOP/s FP64 figure of the profiling recipe (a register-only FMA probe measured 1.203).
-PEAK_FP64_TFLOPS = 1.25
+# Nominal FP64 rate of one GB300 (152 SMs x 4 FP64 flop/clk x 2.07 GHz = 1.26 TFLOP/s; 1.25 in
+# NVIDIA's figures).  The roofline divides by the rate the library's FP64 probes measure in
+# the same run (the better of DFMA chains and mma.sync f64), and reports this one beside it.
+PEAK_FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per cpqr_kernel launch, from one ncu capture of dram__bytes_read.sum
 # and dram__bytes_write.sum at this workload with one launch per level; None once the kernel
 # has changed since that capture
@@ -340,6 +341,47 @@ def mixed_measure(P, torch, n, leaf, pts, a, F, nrhs, st):
     return out
 
 
+def mixed_1024_measure(P, torch, st):
+    """The mixed-precision workload as configured: 1024 x 1024 grid (N = 1048576), leaves 16 x 16,
+    a = 1, one RHS ~ U[-1, 1] (seed 2); FP32 factor at eps 1e-6 refined to 1e-10 with the FP64
+    direct-sum residual, beside the FP64 factor at eps 1e-10 and its solve on the same grid.
+    Times: CUDA events on the launch stream; the FP64 residual of each solution by the direct
+    sum (outside the timings)."""
+    import numpy as np
+    cfg = W.WORKLOADS["laplace_mixed"]
+    n, leaf = cfg["n"], cfg["leaf"]
+    f = torch.from_numpy(W.rhs_uniform(n, cfg["seed"])[None, :].copy()).cuda()
+    x = torch.empty_like(f)
+    tree = P.rs_build_tree(W.grid_points(n), leaf)
+    out = {"n": n, "N": n * n, "nrhs": 1}
+    try:
+        for name, prec, eps in (("mixed", P.RS_MIXED_FP32, cfg["eps"]), ("fp64", P.RS_FP64, 1e-10)):
+            o = P.rs_opts_default()
+            o.precision = prec
+            o.refine_tol = 1e-10
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(st)
+            op = P.rs_factor(tree, eps=eps, opts=o, stream=st)
+            e1.record(st)
+            P.rs_solve(op, f, 1, x, st)
+            e2.record(st)
+            e2.synchronize()
+            s = P.rs_op_stats(op)
+            rel = float(P.rs_residual(op, x, f, 1, st)[0])
+            out[name] = {"eps": eps, "factor_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2),
+                         "step_ms": e0.elapsed_time(e2), "residual_fp64": rel, "bytes_factors": s["bytes_factors"],
+                         "root_m": s["root_m"]}
+            if prec == P.RS_MIXED_FP32:
+                out[name]["refine_solves"] = s["refine_iters"]
+                out[name]["refine_fp64_direct_sums"] = s["refine_fp64_sums"]
+            P.rs_free(op)
+    finally:
+        P.rs_free_tree(tree)
+    out["step_speedup_mixed_vs_fp64"] = out["fp64"]["step_ms"] / out["mixed"]["step_ms"]
+    return out
+
+
 def per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps):
     """The same FP64 step with every factor and solve kernel launched for one box at a time
     (opts.per_box): the unbatched GPU form the per-level launches are compared with."""
@@ -541,6 +583,9 @@ def run_ours(args):
     opts = P.rs_opts_default()
     opts.profile = 1
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    # the FP64 pipe's measured rate: the roofline peak of every FP64 kernel below
+    probe = {"dfma_tflops": P.rs_fp64_probe(P.RS_PROBE_DFMA, st), "dmma_tflops": P.rs_fp64_probe(P.RS_PROBE_DMMA, st)}
+    peak64 = max(probe.values())
 
     def step():
         tree = P.rs_build_tree(pts, leaf)
@@ -633,24 +678,27 @@ def run_ours(args):
         "sampled_residual": res,
         "flops_factor": last_stats["flops_factor"], "bytes_factors": last_stats["bytes_factors"],
         "root_m": last_stats["root_m"],
-        "roofline": {"kernel": dom, "classes": list(KERNEL_CLASSES[dom]), "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
+        "roofline": {"kernel": dom, "classes": list(KERNEL_CLASSES[dom]), "bound": "alu", "achieved": achieved, "peak": peak64,
+                     "unit": "TFLOP/s", "frac": achieved / peak64,
+                     "peak_nominal": PEAK_FP64_NOMINAL_TFLOPS, "frac_of_nominal": achieved / PEAK_FP64_NOMINAL_TFLOPS,
                      "traffic": CPQR_TRAFFIC_BYTES_PER_LAUNCH if dom == "cpqr_kernel" else None,
                      "traffic_note": "ncu DRAM read+write bytes per launch at this workload, one launch per "
                                      "level (no autotuner batching)",
                      "launches": nl, "avg_launch_ms": ms / max(nl, 1),
-                     "peak_note": "FP64 ALU peak 152 SMs x 4 flop/clk x 2.07 GHz (recipe figure; no FP64 entry "
-                                  "in the measured peaks)"},
+                     "peak_note": "of measured: the better of the library's FP64 probes in this run (DFMA chains "
+                                  "%.3f, mma.sync f64 %.3f TFLOP/s); nominal 152 SMs x 4 flop/clk x 2.07 GHz"
+                                  % (probe["dfma_tflops"], probe["dmma_tflops"])},
+        "fp64_probe": probe,
         "roofline_solve": {"kernel": "solve matvec", "bound": "alu",
                            "achieved": sol[1] / (sol[0] * 1e-3) / 1e12 if sol[0] else None,
-                           "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                           "frac": (sol[1] / (sol[0] * 1e-3) / 1e12) / PEAK_FP64_TFLOPS if sol[0] else None,
+                           "peak": peak64, "unit": "TFLOP/s",
+                           "frac": (sol[1] / (sol[0] * 1e-3) / 1e12) / peak64 if sol[0] else None,
                            "achieved_gbs": sol[2] / (sol[0] * 1e-3) / 1e9 if sol[0] else None},
         "profile_ms_per_step": {k: v[0] / K for k, v in prof.items()},
         "profile_ms_by_level": {"levels": "finest .. root (root: inv_F holds the root inverse)", **by_level},
         "profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items() if v[0] > 0 and v[1] > 0},
         "roofline_by_kernel": {k: {"achieved_tflops": kern[k][1] / (kern[k][0] * 1e-3) / 1e12,
-                                   "frac_fp64": kern[k][1] / (kern[k][0] * 1e-3) / 1e12 / PEAK_FP64_TFLOPS,
+                                   "frac_fp64": kern[k][1] / (kern[k][0] * 1e-3) / 1e12 / peak64,
                                    "ms_per_step": kern[k][0] / K}
                                for k in kern if kern[k][0] > 0},
         "e2e": {"value": world * N / e2e_s, "unit": "unknowns/s",
@@ -691,6 +739,7 @@ def run_ours(args):
         if "per_box_fp64" in out:
             mx["step_speedup_vs_per_box_fp64"] = out["per_box_fp64"]["step_ms"] / (mx["factor_ms"] + mx["refined_solve_ms"])
         out["mixed"] = mx
+        out["mixed_1024"] = mixed_1024_measure(P, torch, st)
     if args.serving_requests > 0:
         out["serving"] = serving_measure(P, torch, args.serving_requests)
     if not args.no_cpu_baseline and args.workload == WORKLOAD:

@@ -106,9 +106,8 @@ typedef struct {
                                     each box held in the shared memory of one thread-block
                                     cluster for the whole factorization (levels whose boxes
                                     fit 16 CTAs; the others take the default); -1 = the
-                                    autotuner's table (rs_autotune), else 4 where it fits,
-                                    else 0 or 1 by occupancy. Same result up to rounding
-                                    order                                             [-1]   */
+                                    autotuner's table (rs_autotune), else 0 or 1 by
+                                    occupancy. Same result up to rounding order       [-1]   */
     int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the
                                     offset between grid points (Sec. 5: one set of matrix
                                     blocks per level).  1: each level's ID is taken once, on
@@ -204,11 +203,12 @@ int rs_bicgstab(rs_op* A, rs_op* M, const void* f, void* x, double tol, int max_
 int rs_wait_check(int64_t limit, void* stream);
 
 /* Throughput probe of an FP64 pipe (no counterpart in the paper: it measures the roofline that
- * bounds the FP64 factorization of Sec. 4's work model on the present GPU).  kind:
+ * bounds the FP64 factorization of the work model of Sec. 4 on the present GPU).  kind:
  * RS_PROBE_DFMA, independent FP64 fused multiply-add chains on the CUDA cores; RS_PROBE_DMMA,
- * independent mma.sync m8n8k4 FP64 matrix instructions.  Each runs register-only chains on 64
- * warps per SM; the best of three timed launches (after one warm-up, CUDA events on `stream`)
- * gives *tflops_out (host).  Synchronous; allocates a few KB of device memory. */
+ * independent mma.sync m8n8k4 FP64 matrix instructions.  Each runs register-only chains on 16,
+ * 32 and 64 warps per SM; the best rate of three timed launches per shape (after one warm-up,
+ * CUDA events on `stream`) gives *tflops_out (host).  Synchronous; allocates a few KB of
+ * device memory. */
 enum { RS_PROBE_DFMA = 0, RS_PROBE_DMMA = 1 };
 int rs_fp64_probe(int kind, double* tflops_out, void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of

@@ -32,7 +32,7 @@ namespace rs {
 // Shared-memory layout of one CTA (bytes), for at most `ncmax` columns of stride `ld`.
 template <class T>
 struct ClLayout {
-    size_t y, v, part, tw, nrm, ref, open, pos, total;
+    size_t y, v, part, tw, nrm, ref, open, pos, rec, total;
     __host__ __device__ ClLayout(int ncmax, int ld, int nt)
     {
         size_t o = 0;
@@ -45,6 +45,7 @@ struct ClLayout {
         ref = take(sizeof(double) * (size_t)ncmax);
         open = take(sizeof(int) * (size_t)ncmax);
         pos = take(sizeof(int) * (size_t)ncmax);
+        rec = take(sizeof(int) * (size_t)ncmax);
         total = o;
     }
 };
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
     __shared__ unsigned long long kred[NT / 32];
     __shared__ double dred[NT / 32 + 1];
     __shared__ unsigned long long s_key;
+    __shared__ int s_nrec;                            // columns whose norm is recomputed
 
     cg::cluster_group cluster = cg::this_cluster();
     const int c = (int)cluster.block_rank();
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
     double* __restrict__ ref = (double*)(smraw + Lo.ref);
     int* __restrict__ open = (int*)(smraw + Lo.open);
     int* __restrict__ pos = (int*)(smraw + Lo.pos);
+    int* __restrict__ rec = (int*)(smraw + Lo.rec);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = NT / 32;
     using R = typename sc_traits<T>::real;
@@ -178,17 +181,19 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
         const int jl = act ? open[slot] : 0;
         T* __restrict__ col = Ys + (int64_t)jl * ld;
         if (act) {
-            T w0 = T(0), w1 = T(0);
+            T w0 = T(0), w1 = T(0), w2 = T(0), w3 = T(0);
             int i = rlo;
-            for (; i + 1 < rhi; i += 2) {
+            for (; i + 3 < rhi; i += 4) {
                 w0 = fma_(conj_(v[i]), col[i], w0);
                 w1 = fma_(conj_(v[i + 1]), col[i + 1], w1);
+                w2 = fma_(conj_(v[i + 2]), col[i + 2], w2);
+                w3 = fma_(conj_(v[i + 3]), col[i + 3], w3);
             }
-            if (i < rhi) w0 = fma_(conj_(v[i]), col[i], w0);
-            part[rg * NS + slot] = w0 + w1;
+            for (; i < rhi; ++i) w0 = fma_(conj_(v[i]), col[i], w0);
+            part[rg * NS + slot] = (w0 + w1) + (w2 + w3);
         }
+        if (threadIdx.x == 0) s_nrec = 0;
         __syncthreads();
-        bool recompute = false;
         if (nopen > 0 && threadIdx.x < nopen) {
             T w = part[threadIdx.x];
             for (int q = 1; q < RG; ++q) w += part[q * NS + threadIdx.x];
@@ -198,31 +203,42 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
             const T rsj = fma_(-v[s], t, Ys[(int64_t)jq * ld + s]);   // row s after the update
             const double nv = nrm[jq] - abs2d(rsj);
             nrm[jq] = nv;
-            recompute = nv < 1e-4 * ref[jq];
+            if (nv < 1e-4 * ref[jq]) rec[atomicAdd(&s_nrec, 1)] = jq;
         }
         __syncthreads();
         if (act) {
             const T t = tw[slot];
             int i = rlo;
-            for (; i + 1 < rhi; i += 2) {
+            for (; i + 3 < rhi; i += 4) {
                 const T y0 = fma_(-v[i], t, col[i]);
                 const T y1 = fma_(-v[i + 1], t, col[i + 1]);
+                const T y2 = fma_(-v[i + 2], t, col[i + 2]);
+                const T y3 = fma_(-v[i + 3], t, col[i + 3]);
                 col[i] = y0;
                 col[i + 1] = y1;
+                col[i + 2] = y2;
+                col[i + 3] = y3;
             }
-            if (i < rhi) col[i] = fma_(-v[i], t, col[i]);
+            for (; i < rhi; ++i) col[i] = fma_(-v[i], t, col[i]);
         }
         __syncthreads();
+        // norms that fell below 1e-4 of their reference: recomputed from the updated rows
+        // s+1..r-1, one warp per column
+        const int nrec = s_nrec;
+        if (nrec > 0) {
+            for (int q = warp; q < nrec; q += NW) {
+                const int jq = rec[q];
+                const T* cq = Ys + (int64_t)jq * ld;
+                double acc = 0.0;
+                for (int i = s + 1 + lane; i < r; i += 32) acc += abs2d(cq[i]);
+                acc = warp_sum(acc);
+                if (lane == 0) { nrm[jq] = acc; ref[jq] = acc; }
+            }
+            __syncthreads();
+        }
         best = 0;
         if (nopen > 0 && threadIdx.x < nopen) {
             const int jq = open[threadIdx.x];
-            if (recompute) {
-                const T* cq = Ys + (int64_t)jq * ld;
-                double q = 0.0;
-                for (int i = s + 1; i < r; ++i) q += abs2d(cq[i]);
-                nrm[jq] = q;
-                ref[jq] = q;
-            }
             best = pivot_key(nrm[jq], j0 + jq);
         }
         best = block_max_u64<NT>(best, kred);

@@ -4,9 +4,12 @@
 // the chip's FP64 rate, which GB300 gives through two routes: the FP64 FMA of the CUDA cores
 // (DFMA) and the FP64 matrix instruction (mma.sync m8n8k4 .f64, "DMMA").  Each probe keeps
 // every warp busy with independent register-only chains of one instruction kind, long enough
-// that launch cost is negligible, and returns the achieved rate from CUDA-event timing.  The
+// that launch cost is negligible, at 16, 32 and 64 warps per SM, and returns the best rate
+// from CUDA-event timing.  The
 // larger of the two is the FP64 peak the benchmark divides by; their ratio decides which pipe
 // the FP64 contractions should use.
+#include <algorithm>
+
 #include "k_common.cuh"
 #include "rs.h"
 #include "rs_host.h"
@@ -70,39 +73,44 @@ extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
     int dev = 0, sms = 0;
     RS_CUDA(cudaGetDevice(&dev));
     RS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = 8 * sms;                     // 8 CTAs of 256 threads per SM: 64 warps
-    const int iters = kind == RS_PROBE_DFMA ? 4096 : 1024;
     DevMem out;
-    RS_CUDA(out.alloc(sizeof(double) * (size_t)blocks));
+    RS_CUDA(out.alloc(sizeof(double) * (size_t)(8 * sms)));
     cudaEvent_t e0, e1;
     RS_CUDA(cudaEventCreate(&e0));
     RS_CUDA(cudaEventCreate(&e1));
-    float best = 0.0f;
-    for (int rep = 0; rep < 4; ++rep) {             // rep 0 warms up; the best of the others
-        cudaEventRecord(e0, st);
-        count_launches(1);
-        if (kind == RS_PROBE_DFMA)
-            dfma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
-        else
-            dmma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 1e-3, 1e-3, out.as<double>());
-        cudaEventRecord(e1, st);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(e, "probe kernel");
+    // 2, 4 and 8 CTAs of 256 threads per SM (16 to 64 warps); the best rate of three timed
+    // launches of each, after one warm-up launch
+    double best_rate = 0.0;
+    for (int per_sm = 2; per_sm <= 8; per_sm *= 2) {
+        const int blocks = per_sm * sms;
+        const int iters = (kind == RS_PROBE_DFMA ? 32768 : 8192) / per_sm;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, st);
+            count_launches(1);
+            if (kind == RS_PROBE_DFMA)
+                dfma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
+            else
+                dmma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 1e-3, 1e-3, out.as<double>());
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(e, "probe kernel");
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 0 || ms <= 0.0f) continue;
+            const double threads = (double)blocks * PROBE_NT;
+            // DFMA: 2 flops per FMA; DMMA: 8 x 8 x 4 FMAs = 512 flops per warp-instruction
+            const double flops = kind == RS_PROBE_DFMA ? threads * iters * PROBE_CHAINS * 2.0
+                                                        : threads / 32.0 * iters * 4 * 512.0;
+            best_rate = std::max(best_rate, flops / (ms * 1e-3) / 1e12);
         }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     RS_CUDA(cudaGetLastError());
-    const double threads = (double)blocks * PROBE_NT;
-    // DFMA: 2 flops per FMA; DMMA: 8 x 8 x 4 FMAs = 512 flops per warp-instruction
-    const double flops = kind == RS_PROBE_DFMA ? threads * iters * PROBE_CHAINS * 2.0
-                                                : threads / 32.0 * iters * 4 * 512.0;
-    *tflops_out = flops / (best * 1e-3) / 1e12;
+    *tflops_out = best_rate;
     return RS_OK;
 }

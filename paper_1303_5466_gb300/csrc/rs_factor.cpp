@@ -385,10 +385,10 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
             B.max_r = std::max<int>(B.max_r, (int)L.r[b]);
             B.max_m = std::max<int>(B.max_m, (int)L.m[b]);
         }
-        // boxes that fit the shared memory of one cluster stay there for the whole
-        // factorization (variant 4, the default where it fits)
+        // variant 4: boxes that fit the shared memory of one cluster stay there for the whole
+        // factorization (when asked for, or picked by the autotuner)
         B.cl = 0;
-        if (!op->opts.per_box && (deep_set == 4 || deep_set < 0)) B.cl = cpqr_cl_cluster<T>(B.max_r, B.max_m);
+        if (!op->opts.per_box && deep_set == 4) B.cl = cpqr_cl_cluster<T>(B.max_r, B.max_m);
         if (B.cl > 0) {
             B.G = 1;
             B.ctas = B.nb * B.cl;
@@ -1791,8 +1791,8 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
                                 {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0},
                                 {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}, {2.0, 1, 1.0, 0.0}, {3.0, 0, 0.5, 0.0},
-                                {1.0, 0, 1.0, 0.0, 16}, {1.0, 1, 0.5, 0.0, 16}};
-    constexpr int NTR = 12;
+                                {1.0, 0, 1.0, 0.0, 16}, {1.0, 1, 0.5, 0.0, 16}, {1.0, 4, 1.0, 0.0}};
+    constexpr int NTR = 13;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);
@@ -1857,9 +1857,11 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
         if (l >= 1) {
             const int b = best_of(t_cpqr);
             const std::string k = tune_key("cpqr", esz, S.nb, S.m, S.r);
-            tune_set(k + ".gscale", trials[b].cpqr_gscale);
-            tune_set(k + ".deep", trials[b].cpqr_deep);
-            tune_set(k + ".batch", trials[b].cpqr_batch);
+            // the built-in setting competes too
+            const bool keep = l < b_cpqr.size() && l < t_cpqr[b].size() && b_cpqr[l] <= t_cpqr[b][l];
+            tune_set(k + ".gscale", keep ? 1.0 : trials[b].cpqr_gscale);
+            tune_set(k + ".deep", keep ? -1.0 : trials[b].cpqr_deep);
+            tune_set(k + ".batch", keep ? 0.0 : trials[b].cpqr_batch);
             const int be = best_of(t_e);
             const std::string ke = tune_key("sweep", esz, S.nb, S.k, 0);
             tune_set(ke + ".gscale", trials[be].sweep_gscale);
