@@ -56,8 +56,11 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD, choices=["laplace_batched", "laplace_n256"],
                    help="laplace_n256 is a quarter-size copy for profiling runs")
-    p.add_argument("--serving-requests", type=int, default=150,
+    p.add_argument("--serving-requests", type=int, default=600,
                    help="requests of the serving stream measured after the main step (0 = skip)")
+    p.add_argument("--serving-only", action="store_true",
+                   help="instead of the benchmark: only the serving stream (e.g. --serving-requests 10000), "
+                        "printed as its own JSON line")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     p.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner before the steps")
     p.add_argument("--no-per-box", action="store_true", help="skip the one-box-per-launch comparison")
@@ -223,12 +226,17 @@ def _depth_half(n, leaf):
 SERVING_OPS = ((128, 16), (256, 16), (512, 16))
 
 
-def serving_measure(P, torch, requests, seed=3, load=0.7, other_loads=(0.5, 0.9)):
+def serving_measure(P, torch, requests, seed=3, load=0.7, other_loads=(0.5, 0.9), slots=128):
     """Serving workload: three resident FP64 operators (128^2, 256^2, 512^2 grids, leaves 16^2,
     eps 1e-10); a seeded stream of requests, each naming an operator uniformly and carrying
     1-64 RHS ~ N(0,1), arriving as a Poisson process at `load` x the closed-loop capacity
     measured on a first burst (and the same stream again at each of `other_loads`).  Returns
-    p50/p99 latency (submission to completion) and RHS/s."""
+    p50/p99 latency (submission to completion) and RHS/s.
+
+    Device buffers are reused so that long streams fit: the right-hand sides of a request are
+    the first nrhs of 64 fixed N(0,1) columns of its operator (inputs are only read), and its
+    solution goes to one of `slots` output buffers, taken in turn once its previous request has
+    completed."""
     import numpy as np
     ops, trees = [], []
     for n, leaf in SERVING_OPS:
@@ -239,23 +247,38 @@ def serving_measure(P, torch, requests, seed=3, load=0.7, other_loads=(0.5, 0.9)
     kinds = rng.integers(0, len(SERVING_OPS), requests)
     nrhs = rng.integers(1, 65, requests)
     gaps = rng.exponential(1.0, requests)          # scaled by 1/lambda below
-    bufs = []
-    for k, r in zip(kinds, nrhs):
-        n = SERVING_OPS[k][0]
-        F = torch.from_numpy(rng.standard_normal((int(r), n * n))).cuda()
-        bufs.append((F, torch.empty_like(F)))
+    fin = [torch.from_numpy(rng.standard_normal((64, n * n))).cuda() for n, _ in SERVING_OPS]
+    nmax = max(n * n for n, _ in SERVING_OPS)
+    xout = [torch.empty((64 * nmax,), dtype=torch.float64, device="cuda") for _ in range(slots)]
     torch.cuda.synchronize()
+    fl = [P.rs_op_stats(o)["flops_solve_per_rhs"] for o in ops]
+    owner = [0] * slots                            # ticket whose output a slot holds (0: none)
+    done = set()
     srv = P.rs_server_create(ops, 8 << 30, max_inflight=64)
+
+    def args_of(i):
+        k, r = int(kinds[i]), int(nrhs[i])
+        return k, fin[k], r, xout[i % slots]
+
+    def submit(i):
+        q = i % slots
+        while owner[q] and owner[q] not in done:   # the slot's previous request must be complete
+            done.update(P.rs_server_poll(srv, 4096))
+            if owner[q] not in done:
+                time.sleep(1e-4)
+        k, f, r, x = args_of(i)
+        owner[q] = P.rs_server_submit(srv, k, f, r, x)
+
     try:
         # closed loop on the first burst: everything submitted at once
         burst = min(32, requests)
         t0 = time.perf_counter()
         for i in range(burst):
-            P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
+            submit(i)
         P.rs_server_drain(srv, 3600.0)
         burst_s = time.perf_counter() - t0
+        done.update(P.rs_server_poll(srv, 1 << 16))
         cap = burst / burst_s                        # requests per second
-        P.rs_server_latencies(srv)
         rhs = int(nrhs[burst:].sum())
 
         def open_loop(ld):
@@ -269,9 +292,10 @@ def serving_measure(P, torch, requests, seed=3, load=0.7, other_loads=(0.5, 0.9)
                 delay = t_next - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-                P.rs_server_submit(srv, int(kinds[i]), bufs[i][0], int(nrhs[i]), bufs[i][1])
-            P.rs_server_drain(srv, 3600.0)
+                submit(i)
+            P.rs_server_drain(srv, 36000.0)
             wall_ = time.perf_counter() - t0_
+            done.update(P.rs_server_poll(srv, 1 << 20))
             lat_ = P.rs_server_latencies(srv)[n0_:]
             return lam_, wall_, lat_
 
@@ -287,13 +311,16 @@ def serving_measure(P, torch, requests, seed=3, load=0.7, other_loads=(0.5, 0.9)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         for i in range(burst):
-            P.rs_solve(ops[int(kinds[i])], bufs[i][0], int(nrhs[i]), bufs[i][1], cs)
+            k, f, r, x = args_of(i)
+            P.rs_solve(ops[k], f, r, x, cs)
         torch.cuda.synchronize()
         seq_s = time.perf_counter() - t1
         burst_rhs = int(nrhs[:burst].sum())
+        burst_flops = float(sum(fl[int(kinds[i])] * int(nrhs[i]) for i in range(burst)))
         return {"requests": int(requests - burst), "burst_requests": int(burst), "load": load,
                 "burst_rhs_per_s": burst_rhs / burst_s, "sequential_rhs_per_s": burst_rhs / seq_s,
                 "burst_speedup_vs_sequential": seq_s / burst_s,
+                "burst_tflops": burst_flops / burst_s / 1e12, "sequential_tflops": burst_flops / seq_s / 1e12,
                 "lambda_per_s": lam, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "rhs_per_s": rhs / wall, "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
                 "other_loads": others,
@@ -480,6 +507,46 @@ def ls_measure(P, torch, st):
     for op in (A, M, D):
         P.rs_free(op)
     P.rs_free_tree(tree)
+    return out
+
+
+def helmholtz_measure(P, torch, st):
+    """The Lippmann-Schwinger workload as configured: 256 x 256 grid, kappa 25, b = exp(-40 |x -
+    (1/2,1/2)|^2), f = exp(i kappa x1), leaves 16 x 16; complex64 factor at eps 1e-5 refined to
+    1e-10 with the complex128 direct-sum residual, beside the complex128 factor at eps 1e-10 and
+    its solve.  CUDA-event times on the launch stream."""
+    import numpy as np
+    cfg = W.WORKLOADS["helmholtz_ls"]
+    n, leaf, kappa = cfg["n"], cfg["leaf"], cfg["kappa"]
+    b = W.coeff_b_gaussian(n)
+    f = torch.from_numpy(np.ascontiguousarray(W.rhs_plane_wave(n, kappa))).cuda()
+    x = torch.zeros_like(f)
+    tree = P.rs_build_tree(W.grid_points(n), leaf)
+    out = {"n": n, "kappa": kappa, "scatterer": "Gaussian exp(-40|x-c|^2)"}
+    try:
+        for name, prec, eps in (("c64_refined", P.RS_C64_REFINED, cfg["eps"]), ("c128", P.RS_C128, 1e-10)):
+            o = P.rs_opts_default()
+            o.precision = prec
+            o.refine_tol = 1e-10
+            o.refine_max_iter = 12
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(st)
+            op = P.rs_factor(tree, eps=eps, opts=o, stream=st, kappa=kappa, b=b)
+            e1.record(st)
+            P.rs_solve(op, f, 1, x, st)
+            e2.record(st)
+            e2.synchronize()
+            s = P.rs_op_stats(op)
+            res = float(P.rs_residual(op, x, f, 1, st)[0])
+            out[name] = {"eps": eps, "factor_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2),
+                         "step_ms": e0.elapsed_time(e2), "residual_c128": res, "bytes_factors": s["bytes_factors"]}
+            if prec == P.RS_C64_REFINED:
+                out[name]["refine_solves"] = s["refine_iters"]
+            P.rs_free(op)
+    finally:
+        P.rs_free_tree(tree)
+    out["step_speedup_c64_refined_vs_c128"] = out["c128"]["step_ms"] / out["c64_refined"]["step_ms"]
     return out
 
 
@@ -730,6 +797,7 @@ def run_ours(args):
     if not args.no_ti:
         out["translation_invariant"] = ti_measure(P, torch, leaf, pts, F, nrhs, st, eps)
         out["lippmann_schwinger"] = ls_measure(P, torch, st)
+        out["helmholtz_gaussian"] = helmholtz_measure(P, torch, st)
     if not args.no_per_box:
         out["per_box_fp64"] = per_box_measure(P, torch, leaf, pts, a, F, nrhs, st, eps)
         out["per_box_fp64"]["batched_step_speedup"] = out["per_box_fp64"]["step_ms"] / (factor_ms + solve_ms)
@@ -837,12 +905,28 @@ def run_large_grid(args):
     P.rs_free_tree(tree)
 
 
+def run_serving_only(args):
+    """--serving-only: the serving stream alone (three resident operators, Poisson arrivals at
+    0.5, 0.7 and 0.9 x the measured capacity); prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_1303_5466_gb300 as P
+    from paper_1303_5466_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    out = serving_measure(P, torch, args.serving_requests)
+    out["wall_s"] = time.perf_counter() - t0
+    print(json.dumps({"serving": out}))
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
     elif args.large_grid:
         run_large_grid(args)
+    elif args.serving_only:
+        run_serving_only(args)
     else:
         run_ours(args)
 

@@ -105,7 +105,10 @@ typedef struct {
                                     for boxes whose lists do not fit shared memory); 4 =
                                     each box held in the shared memory of one thread-block
                                     cluster for the whole factorization (levels whose boxes
-                                    fit 16 CTAs; the others take the default); -1 = the
+                                    fit 16 CTAs; the others take the default); 5 = 0 with
+                                    eight columns per warp pass, their dot products summed
+                                    by recursive halving across the lanes and the per-column
+                                    bookkeeping done once per column; -1 = the
                                     autotuner's table (rs_autotune), else 0 or 1 by
                                     occupancy. Same result up to rounding order       [-1]   */
     int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the
@@ -206,9 +209,10 @@ int rs_wait_check(int64_t limit, void* stream);
  * bounds the FP64 factorization of the work model of Sec. 4 on the present GPU).  kind:
  * RS_PROBE_DFMA, independent FP64 fused multiply-add chains on the CUDA cores; RS_PROBE_DMMA,
  * independent mma.sync m8n8k4 FP64 matrix instructions.  Each runs register-only chains on 16,
- * 32 and 64 warps per SM; the best rate of three timed launches per shape (after one warm-up,
- * CUDA events on `stream`) gives *tflops_out (host).  Synchronous; allocates a few KB of
- * device memory. */
+ * 32 and 64 warps per SM (DFMA: three chain layouts, eight chains sharing their operands or
+ * four or two with their own); the best rate of three timed launches per shape (after one
+ * warm-up, CUDA events on `stream`) gives *tflops_out (host).  Synchronous; allocates a few
+ * KB of device memory. */
 enum { RS_PROBE_DFMA = 0, RS_PROBE_DMMA = 1 };
 int rs_fp64_probe(int kind, double* tflops_out, void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of

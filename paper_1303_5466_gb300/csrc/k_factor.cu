@@ -68,7 +68,7 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 //      share for the next step.
 // The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step (every CTA
 // computes alpha from the same data in the same order).
-template <int NT, int U, bool GL, class T>
+template <int NT, int U, bool GL, class T, bool BT = false>
 __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restrict__ cta_off,
         const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
@@ -298,12 +298,126 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
             const unsigned long long kq = pivot_key(nv, jj);
             wbest = kq > wbest ? kq : wbest;
         };
+        // BT: eight columns per warp pass.  The lanes' partial dot products of the eight are
+        // summed by recursive halving (lane l ends with column (l >> 2) & 7: 9 FP64 adds for
+        // eight columns instead of 5 per pair), and the per-column bookkeeping (tau w, row s of
+        // R, the norm downdate, the key) runs once per column on lanes 0, 4, .., 28, so the
+        // FP64 pipe spends its time on the dot-product and update FMAs.
+        auto group8 = [&](int t0, int ng) {
+            T* cp[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cp[c] = Y + (int64_t)alist[t0 + (c < ng ? c : 0)] * r;
+            T acc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = T(0);
+            int i = s + lane;
+            for (; i + 32 < r; i += 64) {
+                const T va = conj_(v[i]), vb = conj_(v[i + 32]);
+                T xa[8], xb[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    xa[c] = c < ng ? ldcg_(cp[c] + i) : T(0);
+                    xb[c] = c < ng ? ldcg_(cp[c] + i + 32) : T(0);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] = fma_(vb, xb[c], fma_(va, xa[c], acc[c]));
+            }
+            if (i < r) {
+                const T va = conj_(v[i]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < ng) acc[c] = fma_(va, ldcg_(cp[c] + i), acc[c]);
+            }
+            // recursive halving over lanes 16, 8, 4, then the last two levels
+            const bool h4 = (lane >> 4) & 1, h3 = (lane >> 3) & 1, h2 = (lane >> 2) & 1;
+            T q4[4], q2[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T snd = h4 ? acc[q] : acc[4 + q];
+                q4[q] = (h4 ? acc[4 + q] : acc[q]) + shfl_xor_(snd, 16);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const T snd = h3 ? q4[q] : q4[2 + q];
+                q2[q] = (h3 ? q4[2 + q] : q4[q]) + shfl_xor_(snd, 8);
+            }
+            T w = (h2 ? q2[1] : q2[0]) + shfl_xor_(h2 ? q2[0] : q2[1], 4);
+            w += shfl_xor_(w, 2);
+            w += shfl_xor_(w, 1);
+            const int cme = (lane >> 2) & 7;
+            const bool book = (lane & 3) == 0 && cme < ng;
+            const T twm = tau * w;
+            T tw[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) tw[c] = shfl_(twm, c << 2);
+            // row s of R for this lane's column (the update below computes the same value)
+            int jme = 0;
+            double nv = 0.0;
+            bool need = false;
+            if (book) {
+                jme = alist[t0 + cme];
+                const T rsj = fma_(-v[s], twm, ldcg_(Y + (int64_t)jme * r + s));
+                nv = ldcg_(nrm + jme) - abs2d(rsj);
+                need = nv < 1e-4 * ldcg_(ref + jme);
+            }
+            // the update of the eight columns
+            i = s + lane;
+            for (; i + 32 < r; i += 64) {
+                const T va = v[i], vb = v[i + 32];
+                T xa[8], xb[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    xa[c] = c < ng ? ldcg_(cp[c] + i) : T(0);
+                    xb[c] = c < ng ? ldcg_(cp[c] + i + 32) : T(0);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < ng) {
+                        cp[c][i] = fma_(-va, tw[c], xa[c]);
+                        cp[c][i + 32] = fma_(-vb, tw[c], xb[c]);
+                    }
+            }
+            if (i < r) {
+                const T va = v[i];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < ng) cp[c][i] = fma_(-va, tw[c], ldcg_(cp[c] + i));
+            }
+            // norms that fell below 1e-4 of their reference: recomputed from the updated rows,
+            // the whole warp on each such column in turn
+            unsigned rec = __ballot_sync(0xffffffffu, need);
+            if (rec) {
+                __syncwarp();                  // the recomputation reads the warp's stores
+                while (rec) {
+                    const int src = __ffs(rec) - 1;
+                    rec &= rec - 1;
+                    const int jq = __shfl_sync(0xffffffffu, jme, src);
+                    const T* col = Y + (int64_t)jq * r;
+                    double q = 0.0;
+                    for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(ldcg_(col + i2));
+                    q = warp_sum(q);
+                    if (lane == src) {
+                        nv = q;
+                        ref[jq] = q;
+                    }
+                }
+            }
+            if (book) {
+                nrm[jme] = nv;
+                const unsigned long long kq = pivot_key(nv, jme);
+                wbest = kq > wbest ? kq : wbest;
+            }
+        };
         {
             const int C = hi - lo;
             const int wlo = lo + (int)(((int64_t)warp * C) / NW), whi = lo + (int)(((int64_t)(warp + 1) * C) / NW);
-            int t = wlo;
-            for (; t + 1 < whi; t += 2) columns(std::true_type{}, alist[t], alist[t + 1]);
-            if (t < whi) columns(std::false_type{}, alist[t], alist[t]);
+            if constexpr (BT) {
+                for (int t = wlo; t < whi; t += 8) group8(t, min(8, whi - t));
+            } else {
+                int t = wlo;
+                for (; t + 1 < whi; t += 2) columns(std::true_type{}, alist[t], alist[t + 1]);
+                if (t < whi) columns(std::false_type{}, alist[t], alist[t]);
+            }
         }
         wbest = block_max_u64<NT>(wbest, kred);
         if (threadIdx.x == 0) kb[((s + 1) & 1) * G + gi] = wbest;
@@ -332,7 +446,7 @@ size_t cpqr_gwork_ints(int max_r, int max_m, int deep, int ctas)
     return cpqr_global<T>(max_r, max_m, deep) ? (size_t)ctas * (size_t)(2 * max_m + 2) : 0;
 }
 
-template <int U, bool GL, class T>
+template <int U, bool GL, class T, bool BT>
 static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas,
                                  const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y,
                                  double eps, int32_t* kout, int32_t* piv, T* diag, unsigned int* bar,
@@ -340,20 +454,31 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
                                  double* ref, int* gwork, int gstride)
 {
     constexpr int NT = 256;
-    cudaError_t e = cudaFuncSetAttribute(cpqr_kernel<NT, U, GL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    auto fn = cpqr_kernel<NT, U, GL, T, BT>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     count_launches(1);
     if (!cta_off && G == 1) {
-        cpqr_kernel<NT, U, GL, T><<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar,
-                                                   keys, status, spin_limit, nrm, ref, gwork, gstride);
+        fn<<<nb, NT, shm, st>>>(1, nullptr, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys, status,
+                                spin_limit, nrm, ref, gwork, gstride);
         return cudaGetLastError();
     }
     int g0 = cta_off ? nb : G;
     void* args[] = {(void*)&g0, (void*)&cta_off, (void*)&act_off, (void*)&nnear, (void*)&P, (void*)&y_off, (void*)&Y,
                     (void*)&eps, (void*)&kout, (void*)&piv, (void*)&diag, (void*)&bar, (void*)&keys, (void*)&status,
                     (void*)&spin_limit, (void*)&nrm, (void*)&ref, (void*)&gwork, (void*)&gstride};
-    return cudaLaunchCooperativeKernel((void*)cpqr_kernel<NT, U, GL, T>, dim3((unsigned)(cta_off ? ctas : nb * G)),
-                                       dim3(NT), args, shm, st);
+    return cudaLaunchCooperativeKernel((void*)fn, dim3((unsigned)(cta_off ? ctas : nb * G)), dim3(NT), args, shm, st);
+}
+
+// The kernel instance of a variant: deep 0 (U = 4), 1 (U = 8), 3 (global lists) and 5 (eight
+// columns per warp pass, U unused) of cpqr_kernel.
+template <class T>
+static const void* cpqr_fn(int deep, bool glob)
+{
+    constexpr int NT = 256;
+    if (deep == 5) return glob ? (const void*)cpqr_kernel<NT, 4, true, T, true> : (const void*)cpqr_kernel<NT, 4, false, T, true>;
+    if (glob) return deep == 1 ? (const void*)cpqr_kernel<NT, 8, true, T> : (const void*)cpqr_kernel<NT, 4, true, T>;
+    return deep == 1 ? (const void*)cpqr_kernel<NT, 8, false, T> : (const void*)cpqr_kernel<NT, 4, false, T>;
 }
 
 template <class T>
@@ -375,18 +500,14 @@ cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, 
     if (shm > 227 * 1024) return cudaErrorInvalidValue;     // the Householder vector alone does not fit
     int* gw = glob ? gwork : nullptr;
     const int gstride = 2 * max_m + 2;
-    if (glob) {
-        if (deep == 1)
-            return launch_cpqr_u<8, true, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv,
-                                             diag, bar, keys, status, spin_limit, shm, nrm, ref, gw, gstride);
-        return launch_cpqr_u<4, true, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag,
-                                         bar, keys, status, spin_limit, shm, nrm, ref, gw, gstride);
-    }
-    if (deep == 1)
-        return launch_cpqr_u<8, false, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag,
-                                          bar, keys, status, spin_limit, shm, nrm, ref, nullptr, gstride);
-    return launch_cpqr_u<4, false, T>(st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag,
-                                      bar, keys, status, spin_limit, shm, nrm, ref, nullptr, gstride);
+#define RS_CPQR_ARGS st, nb, G, cta_off, ctas, act_off, nnear, P, y_off, Y, eps, kout, piv, diag, bar, keys, status, \
+                     spin_limit, shm, nrm, ref, gw, gstride
+    if (deep == 5)
+        return glob ? launch_cpqr_u<4, true, T, true>(RS_CPQR_ARGS) : launch_cpqr_u<4, false, T, true>(RS_CPQR_ARGS);
+    if (glob)
+        return deep == 1 ? launch_cpqr_u<8, true, T, false>(RS_CPQR_ARGS) : launch_cpqr_u<4, true, T, false>(RS_CPQR_ARGS);
+    return deep == 1 ? launch_cpqr_u<8, false, T, false>(RS_CPQR_ARGS) : launch_cpqr_u<4, false, T, false>(RS_CPQR_ARGS);
+#undef RS_CPQR_ARGS
 }
 
 template <class T>
@@ -398,9 +519,7 @@ int cpqr_max_ctas(int max_r, int max_m, int G, int deep)
     const bool glob = cpqr_global<T>(max_r, max_m, deep);
     const size_t shm = cpqr_shm<T>(max_r, max_m, glob);
     if (shm > 227 * 1024) return 0;
-    const void* fn;
-    if (glob) fn = deep == 1 ? (const void*)cpqr_kernel<NT, 8, true, T> : (const void*)cpqr_kernel<NT, 4, true, T>;
-    else fn = deep == 1 ? (const void*)cpqr_kernel<NT, 8, false, T> : (const void*)cpqr_kernel<NT, 4, false, T>;
+    const void* fn = cpqr_fn<T>(deep, glob);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);

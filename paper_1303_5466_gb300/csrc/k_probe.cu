@@ -38,6 +38,28 @@ __global__ void __launch_bounds__(PROBE_NT) dfma_probe_kernel(int iters, double 
     if (s == 12345.678) out[blockIdx.x] = s;      // never true: keeps the chains live
 }
 
+// DFMA with CH independent chains whose multiplier and addend are per-chain registers
+// (a = a * b_q + c_q).
+template <int CH>
+__global__ void __launch_bounds__(PROBE_NT) dfma_probe2_kernel(int iters, double m, double c, double* out)
+{
+    double a[CH], bq[CH], cq[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+        a[q] = 1.0 + 1e-3 * (threadIdx.x + q);
+        bq[q] = m * (1.0 - 1e-9 * q);
+        cq[q] = c * (1.0 + 1e-3 * q);
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < CH; ++q) a[q] = fma(a[q], bq[q], cq[q]);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < CH; ++q) s += a[q];
+    if (s == 12345.678) out[blockIdx.x] = s;
+}
+
 // DMMA: 4 independent m8n8k4 accumulations per warp, D = A B + D with A, B fixed fragments of
 // small values (each step adds a bounded amount; no overflow over the iterations).
 __global__ void __launch_bounds__(PROBE_NT) dmma_probe_kernel(int iters, double av, double bv, double* out)
@@ -81,14 +103,23 @@ extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
     // 2, 4 and 8 CTAs of 256 threads per SM (16 to 64 warps); the best rate of three timed
     // launches of each, after one warm-up launch
     double best_rate = 0.0;
+    // DFMA forms: 0 = eight chains sharing their multiplier and addend, 1 = four and 2 = two
+    // chains with their own
+    const int forms = kind == RS_PROBE_DFMA ? 3 : 1;
+    for (int form = 0; form < forms; ++form)
     for (int per_sm = 2; per_sm <= 8; per_sm *= 2) {
         const int blocks = per_sm * sms;
-        const int iters = (kind == RS_PROBE_DFMA ? 32768 : 8192) / per_sm;
+        const int chains = kind != RS_PROBE_DFMA ? 1 : form == 0 ? PROBE_CHAINS : form == 1 ? 4 : 2;
+        const int iters = kind == RS_PROBE_DFMA ? 32768 * PROBE_CHAINS / chains / per_sm : 8192 / per_sm;
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, st);
             count_launches(1);
-            if (kind == RS_PROBE_DFMA)
+            if (kind == RS_PROBE_DFMA && form == 0)
                 dfma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
+            else if (kind == RS_PROBE_DFMA && form == 1)
+                dfma_probe2_kernel<4><<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
+            else if (kind == RS_PROBE_DFMA)
+                dfma_probe2_kernel<2><<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
             else
                 dmma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 1e-3, 1e-3, out.as<double>());
             cudaEventRecord(e1, st);
@@ -103,7 +134,7 @@ extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
             if (rep == 0 || ms <= 0.0f) continue;
             const double threads = (double)blocks * PROBE_NT;
             // DFMA: 2 flops per FMA; DMMA: 8 x 8 x 4 FMAs = 512 flops per warp-instruction
-            const double flops = kind == RS_PROBE_DFMA ? threads * iters * PROBE_CHAINS * 2.0
+            const double flops = kind == RS_PROBE_DFMA ? threads * iters * chains * 2.0
                                                         : threads / 32.0 * iters * 4 * 512.0;
             best_rate = std::max(best_rate, flops / (ms * 1e-3) / 1e12);
         }

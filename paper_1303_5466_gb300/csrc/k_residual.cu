@@ -41,66 +41,204 @@ constexpr int DS_RHS = 4;       // right-hand sides per pass
 // yg = A xg in grid order: yg[c N + g] = dg[g] xg[c N + g] + rs[g] sum_{g' != g} K(g - g') xg[c N + g']
 // (rs = NULL means 1).  Products and the sum over one 16 x 16 source tile run in S; the tile
 // sums are added in A (A = S for the FP64 residual; A = FP64 for an FP32 product, so that the
-// FP32 rounding stays that of 256-term sums however large the grid).
-template <class S, class A>
-__global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
-        const double* __restrict__ rs, const S* __restrict__ xg, A* __restrict__ yg, int nrhs)
+// FP32 rounding stays that of 256-term sums however large the grid).  Each pass takes NC
+// right-hand sides, NC fixed at compile time, so no FMA is issued for absent columns.
+template <class S, class A, int NC>
+__device__ __forceinline__ void direct_sum_pass(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
+        const double* __restrict__ rs, const S* __restrict__ xg, A* __restrict__ yg, int c0,
+        S (*Kw)[2 * DS], S (*xs)[DS * DS])
 {
-    __shared__ S Kw[2 * DS - 1][2 * DS];
-    __shared__ S xs[DS_RHS][DS * DS];
     const int64_t N = (int64_t)n * n;
     const int W = 2 * n - 1;
     const int tx0 = blockIdx.x * DS, ty0 = blockIdx.y * DS;
     const int lx = threadIdx.x % DS, ly = threadIdx.x / DS;
     const int ti1 = tx0 + lx, ti2 = ty0 + ly;
     const bool tin = ti1 < n && ti2 < n;
-    for (int c0 = 0; c0 < nrhs; c0 += DS_RHS) {
-        const int nc = min(DS_RHS, nrhs - c0);
-        A acc[DS_RHS];
+    A acc[NC];
 #pragma unroll
-        for (int c = 0; c < DS_RHS; ++c) acc[c] = A(0.0);
-        for (int sy0 = 0; sy0 < n; sy0 += DS) {
-            for (int sx0 = 0; sx0 < n; sx0 += DS) {
-                __syncthreads();
-                for (int e = threadIdx.x; e < (2 * DS - 1) * (2 * DS - 1); e += blockDim.x) {
-                    const int e1 = e % (2 * DS - 1), e2 = e / (2 * DS - 1);
-                    const int d1 = tx0 - sx0 - (DS - 1) + e1, d2 = ty0 - sy0 - (DS - 1) + e2;
-                    Kw[e2][e1] = (d1 > -n && d1 < n && d2 > -n && d2 < n)
-                                     ? Kt[(int64_t)(d1 + n - 1) + (int64_t)W * (d2 + n - 1)]
-                                     : S(0.0);
-                }
-                for (int e = threadIdx.x; e < nc * DS * DS; e += blockDim.x) {
-                    const int c = e / (DS * DS), j = e - c * (DS * DS);
-                    const int s1 = sx0 + j % DS, s2 = sy0 + j / DS;
-                    xs[c][j] = (s1 < n && s2 < n) ? xg[(int64_t)(c0 + c) * N + s1 + (int64_t)n * s2] : S(0.0);
-                }
-                __syncthreads();
-                if (tin) {
-                    S t[DS_RHS];
+    for (int c = 0; c < NC; ++c) acc[c] = A(0.0);
+    for (int sy0 = 0; sy0 < n; sy0 += DS) {
+        for (int sx0 = 0; sx0 < n; sx0 += DS) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < (2 * DS - 1) * (2 * DS - 1); e += blockDim.x) {
+                const int e1 = e % (2 * DS - 1), e2 = e / (2 * DS - 1);
+                const int d1 = tx0 - sx0 - (DS - 1) + e1, d2 = ty0 - sy0 - (DS - 1) + e2;
+                Kw[e2][e1] = (d1 > -n && d1 < n && d2 > -n && d2 < n)
+                                 ? Kt[(int64_t)(d1 + n - 1) + (int64_t)W * (d2 + n - 1)]
+                                 : S(0.0);
+            }
+            for (int e = threadIdx.x; e < NC * DS * DS; e += blockDim.x) {
+                const int c = e / (DS * DS), j = e - c * (DS * DS);
+                const int s1 = sx0 + j % DS, s2 = sy0 + j / DS;
+                xs[c][j] = (s1 < n && s2 < n) ? xg[(int64_t)(c0 + c) * N + s1 + (int64_t)n * s2] : S(0.0);
+            }
+            __syncthreads();
+            if (tin) {
+                S t[NC];
 #pragma unroll
-                    for (int c = 0; c < DS_RHS; ++c) t[c] = S(0.0);
+                for (int c = 0; c < NC; ++c) t[c] = S(0.0);
 #pragma unroll 4
-                    for (int j2 = 0; j2 < DS; ++j2) {
+                for (int j2 = 0; j2 < DS; ++j2) {
 #pragma unroll
-                        for (int j1 = 0; j1 < DS; ++j1) {
-                            const S k = Kw[ly - j2 + DS - 1][lx - j1 + DS - 1];
+                    for (int j1 = 0; j1 < DS; ++j1) {
+                        const S k = Kw[ly - j2 + DS - 1][lx - j1 + DS - 1];
 #pragma unroll
-                            for (int c = 0; c < DS_RHS; ++c)
-                                if (c < nc) t[c] = fma_(k, xs[c][j2 * DS + j1], t[c]);
-                        }
+                        for (int c = 0; c < NC; ++c) t[c] = fma_(k, xs[c][j2 * DS + j1], t[c]);
                     }
-#pragma unroll
-                    for (int c = 0; c < DS_RHS; ++c) acc[c] += cast_<A>(t[c]);
                 }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[c] += cast_<A>(t[c]);
             }
         }
-        if (tin) {
+    }
+    if (tin) {
+        const int64_t g = ti1 + (int64_t)n * ti2;
+        const A sum_scale = rs ? A(rs[g]) : A(1.0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            yg[(int64_t)(c0 + c) * N + g] =
+                fma_(cast_<A>(dg[g]), cast_<A>(xg[(int64_t)(c0 + c) * N + g]), sum_scale * acc[c]);
+    }
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) direct_sum_kernel(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
+        const double* __restrict__ rs, const S* __restrict__ xg, A* __restrict__ yg, int nrhs)
+{
+    __shared__ S Kw[2 * DS - 1][2 * DS];
+    __shared__ S xs[DS_RHS][DS * DS];
+    for (int c0 = 0; c0 < nrhs; c0 += DS_RHS) {
+        switch (min(DS_RHS, nrhs - c0)) {
+            case 1: direct_sum_pass<S, A, 1>(n, Kt, dg, rs, xg, yg, c0, Kw, xs); break;
+            case 2: direct_sum_pass<S, A, 2>(n, Kt, dg, rs, xg, yg, c0, Kw, xs); break;
+            case 3: direct_sum_pass<S, A, 3>(n, Kt, dg, rs, xg, yg, c0, Kw, xs); break;
+            default: direct_sum_pass<S, A, 4>(n, Kt, dg, rs, xg, yg, c0, Kw, xs); break;
+        }
+    }
+}
+
+// The same sum with 32 x 32 target tiles, four targets per thread (column lx, rows ly + 8q),
+// against 32 x 32 source tiles: the 63 x 63 table window and the sources are staged once per
+// source tile for four times the products of the 16 x 16 form, so the staging and the two
+// CTA barriers per tile stay small beside the FMAs even at one right-hand side.  The products
+// of each 8-row band of a source tile (256 terms) are summed in S and the band sums added in
+// A, the rounding structure of the 16 x 16 form.  Taken when the grid has at least three
+// 32 x 32 target tiles per SM (1024 x 1024 and up on 152 SMs; fewer tiles would leave SMs
+// with uneven shares) and for scalars of at most 8 bytes (its static shared memory holds
+// 63 x 64 + 2 x 1024 scalars, within the 48 KB static limit).
+constexpr int DT = 32;          // tile side of the large form
+constexpr int DT_RHS = 2;       // right-hand sides per pass of the large form
+
+// One pass of the large form over NC (compile-time, so no FMA is issued for absent columns)
+// right-hand sides c0 .. c0 + NC.
+template <class S, class A, int NC>
+__device__ __forceinline__ void direct_sum32_pass(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
+        const double* __restrict__ rs, const S* __restrict__ xg, A* __restrict__ yg, int c0,
+        S (*Kw)[2 * DT], S (*xs)[DT * DT])
+{
+    const int64_t N = (int64_t)n * n;
+    const int W = 2 * n - 1;
+    const int tx0 = blockIdx.x * DT, ty0 = blockIdx.y * DT;
+    const int lx = threadIdx.x % DT, ly = threadIdx.x / DT;          // ly in 0..7
+    const int ti1 = tx0 + lx;
+    A acc[4][NC];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[q][c] = A(0.0);
+    for (int sy0 = 0; sy0 < n; sy0 += DT) {
+        for (int sx0 = 0; sx0 < n; sx0 += DT) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < (2 * DT - 1) * (2 * DT - 1); e += blockDim.x) {
+                const int e1 = e % (2 * DT - 1), e2 = e / (2 * DT - 1);
+                const int d1 = tx0 - sx0 - (DT - 1) + e1, d2 = ty0 - sy0 - (DT - 1) + e2;
+                Kw[e2][e1] = (d1 > -n && d1 < n && d2 > -n && d2 < n)
+                                 ? Kt[(int64_t)(d1 + n - 1) + (int64_t)W * (d2 + n - 1)]
+                                 : S(0.0);
+            }
+            for (int e = threadIdx.x; e < NC * DT * DT; e += blockDim.x) {
+                const int c = e / (DT * DT), j = e - c * (DT * DT);
+                const int s1 = sx0 + j % DT, s2 = sy0 + j / DT;
+                xs[c][j] = (s1 < n && s2 < n) ? xg[(int64_t)(c0 + c) * N + s1 + (int64_t)n * s2] : S(0.0);
+            }
+            __syncthreads();
+            for (int jb = 0; jb < DT; jb += 8) {                 // bands of 8 source rows
+                S t[4][NC];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) t[q][c] = S(0.0);
+#pragma unroll 2
+                for (int j2 = jb; j2 < jb + 8; ++j2) {
+#pragma unroll 8
+                    for (int j1 = 0; j1 < DT; ++j1) {
+                        S xv[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) xv[c] = xs[c][j2 * DT + j1];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const S k = Kw[ly + 8 * q - j2 + DT - 1][lx - j1 + DT - 1];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) t[q][c] = fma_(k, xv[c], t[q][c]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[q][c] += cast_<A>(t[q][c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int ti2 = ty0 + ly + 8 * q;
+        if (ti1 < n && ti2 < n) {
             const int64_t g = ti1 + (int64_t)n * ti2;
             const A sum_scale = rs ? A(rs[g]) : A(1.0);
-            for (int c = 0; c < nc; ++c)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
                 yg[(int64_t)(c0 + c) * N + g] =
-                    fma_(cast_<A>(dg[g]), cast_<A>(xg[(int64_t)(c0 + c) * N + g]), sum_scale * acc[c]);
+                    fma_(cast_<A>(dg[g]), cast_<A>(xg[(int64_t)(c0 + c) * N + g]), sum_scale * acc[q][c]);
         }
+    }
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(256) direct_sum32_kernel(int n, const S* __restrict__ Kt, const S* __restrict__ dg,
+        const double* __restrict__ rs, const S* __restrict__ xg, A* __restrict__ yg, int nrhs)
+{
+    __shared__ S Kw[2 * DT - 1][2 * DT];
+    __shared__ S xs[DT_RHS][DT * DT];
+    for (int c0 = 0; c0 < nrhs; c0 += DT_RHS) {
+        if (nrhs - c0 >= 2) direct_sum32_pass<S, A, 2>(n, Kt, dg, rs, xg, yg, c0, Kw, xs);
+        else direct_sum32_pass<S, A, 1>(n, Kt, dg, rs, xg, yg, c0, Kw, xs);
+    }
+}
+
+// One direct sum, by the form that suits the grid.
+template <class S, class A>
+static void launch_direct_sum(cudaStream_t st, int n, const S* Kt, const S* dg, const double* rs, const S* xg, A* yg,
+                              int nrhs)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    const int64_t tiles32 = (int64_t)((n + DT - 1) / DT) * ((n + DT - 1) / DT);
+    if constexpr (sizeof(S) <= 8) {
+        if (tiles32 >= 3 * (int64_t)sms) {
+            dim3 grid((unsigned)((n + DT - 1) / DT), (unsigned)((n + DT - 1) / DT));
+            direct_sum32_kernel<S, A><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
+            return;
+        }
+    }
+    {
+        dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
+        direct_sum_kernel<S, A><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
     }
 }
 
@@ -176,8 +314,7 @@ cudaError_t launch_residual(cudaStream_t st, int n, int nrhs, const S* Kt, const
     const int64_t N = (int64_t)n * n;
     count_launches(4);
     to_grid_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, x, xg);
-    dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
-    direct_sum_kernel<S, S><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
+    launch_direct_sum<S, S>(st, n, Kt, dg, rs, xg, yg, nrhs);
     residual_finish_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, f, yg, r);
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nrhs, st);
     if (e != cudaSuccess) return e;
@@ -232,8 +369,7 @@ cudaError_t launch_residual_update(cudaStream_t st, int n, int nrhs, const L* Kt
     const int64_t N = (int64_t)n * n;
     count_launches(4);
     to_grid_narrow_kernel<S, L><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, dx, xg);
-    dim3 grid((unsigned)((n + DS - 1) / DS), (unsigned)((n + DS - 1) / DS));
-    direct_sum_kernel<L, S><<<grid, 256, 0, st>>>(n, Kt, dg, rs, xg, yg, nrhs);
+    launch_direct_sum<L, S>(st, n, Kt, dg, rs, xg, yg, nrhs);
     residual_sub_kernel<S><<<nblk(N * nrhs), 256, 0, st>>>(N, nrhs, ing, yg, r);
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nrhs, st);
     if (e != cudaSuccess) return e;

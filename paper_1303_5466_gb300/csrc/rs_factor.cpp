@@ -399,7 +399,8 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         }
         // the open columns are re-split every step, so a group may take one CTA per 16 columns
         // (sized for the co-residency of the variant when one is set)
-        const int var = deep_set >= 0 && deep_set <= 3 ? deep_set : 0;
+        const bool streaming = deep_set >= 0 && deep_set != 4;      // variants 0-3 and 5
+        const int var = streaming ? deep_set : 0;
         int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g, var); });
         if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
         // gs > 1 (large boxes, few per launch): more CTAs than one per 16 columns, so that more
@@ -434,7 +435,7 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         }
         // few CTAs per SM: each warp keeps twice the rows in flight
         B.deep = (G > 1 && B.ctas <= 2 * sms) ? 1 : 0;
-        if (deep_set >= 0 && deep_set <= 3) B.deep = deep_set;
+        if (streaming) B.deep = deep_set;
         if (B.deep && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, B.deep)) B.deep = 0;   // must stay co-resident
         max_keys = std::max(max_keys, (size_t)(2 * B.ctas));
         bats.push_back(B);
@@ -1185,7 +1186,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
-    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 4) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 4");
+    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 5) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 5");
     if (op->opts.sweep_panel != 0 && op->opts.sweep_panel != 8 && op->opts.sweep_panel != 16)
         return fail(RS_E_INVALID, "sweep_panel must be 0, 8 or 16");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))

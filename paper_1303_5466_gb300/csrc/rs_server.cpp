@@ -7,9 +7,14 @@
 //      level of the upward pass, the root, or one level of the downward pass;
 //   3. issues each stage of that step as a single launch whose job list holds every request
 //      in that phase, across operators, levels and RHS counts;
-//   4. after the stream drains, retires finished requests (freeing their memory at once).
-// Requests that arrive while others run join at the next tick.  The per-request kernels do
-// the same arithmetic as rs_solve, so results do not depend on the batch.
+//   4. waits for the previous tick (not this one) and retires the requests it finished
+//      (freeing their memory at once).
+// Two ticks are in flight at a time: the host builds and enqueues tick t+1 while the GPU runs
+// tick t (the steps of a request are known in advance, and stream order keeps each request's
+// stages in sequence), so the GPU does not idle while the host prepares job lists.  Job lists
+// are staged through two buffers, one per tick in flight.  Requests that arrive while others
+// run join at the next tick.  The per-request kernels do the same arithmetic as rs_solve, so
+// results do not depend on the batch.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -79,6 +84,7 @@ struct Req {
     SolveLayout Ls;
     int phase = 0;      // 0 up, 1 root, 2 down
     int level = 0;
+    int64_t done_tick = -1;   // the tick that issues its last stage (retired once it completes)
     Clock::time_point t_submit;
     // workspace (device)
     double *w = nullptr, *g = nullptr, *phi = nullptr, *u = nullptr, *out = nullptr, *t = nullptr;
@@ -108,10 +114,11 @@ struct rs_server {
     int error = RS_OK;
     std::string error_msg;
     std::thread worker;
-    // job staging
-    rs::DevMem d_mv, d_cp;
-    void* h_stage = nullptr;
-    size_t h_stage_bytes = 0;
+    // job staging: one set per tick in flight
+    rs::DevMem d_mv[2], d_cp[2];
+    void* h_stage[2] = {nullptr, nullptr};
+    size_t h_stage_bytes[2] = {0, 0};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
 namespace rs {
@@ -146,6 +153,7 @@ enum { U1, U2, U3, U4, U5, RT, D1, D2, D3, D4, D5, D6, D7, NSTAGE };
 void build_jobs(rs_server* s, std::vector<StageJobs>& S)
 {
     for (Req* r : s->inflight) {
+        if (r->done_tick >= 0) continue;          // finished in a tick still in flight
         rs_op* op = s->ops[r->op];
         const int64_t nr = r->nrhs;
         const int d = op->d;
@@ -181,24 +189,28 @@ void build_jobs(rs_server* s, std::vector<StageJobs>& S)
     }
 }
 
-int run_tick(rs_server* s)
+// Enqueue one tick through staging set `slot` (whose previous tick has completed) and record
+// its completion event; no host synchronisation.
+int run_tick(rs_server* s, int slot)
 {
     std::vector<StageJobs> S(NSTAGE);
     build_jobs(s, S);
     size_t nmv = 0, ncp = 0;
     for (const StageJobs& j : S) { nmv += j.mv.size(); ncp += j.cp.size(); }
     const size_t bmv = nmv * sizeof(MvJob), bcp = ncp * sizeof(CopyJob);
-    if (bmv + bcp > s->h_stage_bytes) {
-        if (s->h_stage) cudaFreeHost(s->h_stage);
-        s->h_stage = nullptr;
-        s->h_stage_bytes = 0;
-        RS_CUDA(cudaMallocHost(&s->h_stage, 2 * (bmv + bcp) + 4096));
-        s->h_stage_bytes = 2 * (bmv + bcp) + 4096;
+    if (bmv + bcp > s->h_stage_bytes[slot]) {
+        if (s->h_stage[slot]) cudaFreeHost(s->h_stage[slot]);
+        s->h_stage[slot] = nullptr;
+        s->h_stage_bytes[slot] = 0;
+        RS_CUDA(cudaMallocHost(&s->h_stage[slot], 2 * (bmv + bcp) + 4096));
+        s->h_stage_bytes[slot] = 2 * (bmv + bcp) + 4096;
     }
-    RS_CUDA(s->d_mv.alloc(bmv + 64));
-    RS_CUDA(s->d_cp.alloc(bcp + 64));
-    MvJob* hm = (MvJob*)s->h_stage;
-    CopyJob* hc = (CopyJob*)((char*)s->h_stage + bmv);
+    DevMem& dmv = s->d_mv[slot];
+    DevMem& dcp = s->d_cp[slot];
+    RS_CUDA(dmv.alloc(bmv + 64));
+    RS_CUDA(dcp.alloc(bcp + 64));
+    MvJob* hm = (MvJob*)s->h_stage[slot];
+    CopyJob* hc = (CopyJob*)((char*)s->h_stage[slot] + bmv);
     std::vector<size_t> mv_at(NSTAGE), cp_at(NSTAGE);
     size_t im = 0, ic = 0;
     for (int k = 0; k < NSTAGE; ++k) {
@@ -209,13 +221,13 @@ int run_tick(rs_server* s)
         im += S[k].mv.size();
         ic += S[k].cp.size();
     }
-    if (bmv) RS_CUDA(cudaMemcpyAsync(s->d_mv.p, hm, bmv, cudaMemcpyHostToDevice, s->st));
-    if (bcp) RS_CUDA(cudaMemcpyAsync(s->d_cp.p, hc, bcp, cudaMemcpyHostToDevice, s->st));
+    if (bmv) RS_CUDA(cudaMemcpyAsync(dmv.p, hm, bmv, cudaMemcpyHostToDevice, s->st));
+    if (bcp) RS_CUDA(cudaMemcpyAsync(dcp.p, hc, bcp, cudaMemcpyHostToDevice, s->st));
     for (int k = 0; k < NSTAGE; ++k) {
-        RS_CUDA(launch_copy_jobs(s->st, s->d_cp.as<CopyJob>() + cp_at[k], (int)S[k].cp.size(), S[k].cp_elems));
-        RS_CUDA(launch_mv_jobs(s->st, s->d_mv.as<MvJob>() + mv_at[k], (int)S[k].mv.size(), S[k].mv_blocks));
+        RS_CUDA(launch_copy_jobs(s->st, dcp.as<CopyJob>() + cp_at[k], (int)S[k].cp.size(), S[k].cp_elems));
+        RS_CUDA(launch_mv_jobs(s->st, dmv.as<MvJob>() + mv_at[k], (int)S[k].mv.size(), S[k].mv_blocks));
     }
-    RS_CUDA(cudaStreamSynchronize(s->st));
+    RS_CUDA(cudaEventRecord(s->ev[slot], s->st));
     return RS_OK;
 }
 
@@ -223,6 +235,17 @@ void worker_main(rs_server* s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    int64_t enq = -1, waited = -1;       // last tick enqueued, last tick known complete
+    auto fail_all = [&](int rc) {
+        s->error = rc;
+        s->error_msg = rs_last_error();
+        for (Req* r : s->inflight) {
+            s->ops[r->op]->inflight -= 1;
+            delete r;
+        }
+        s->inflight.clear();
+        s->cv_done.notify_all();
+    };
     while (true) {
         // admission: arrival order, in-flight cap, memory budget
         while (!s->pending.empty() && (int)s->inflight.size() < s->max_inflight) {
@@ -243,49 +266,68 @@ void worker_main(rs_server* s)
             s->inflight.push_back(r);
         }
         s->peak_inflight = std::max<int64_t>(s->peak_inflight, (int64_t)s->inflight.size());
-        if (s->inflight.empty()) {
+        bool active = false;
+        for (Req* r : s->inflight) active = active || r->done_tick < 0;
+        if (!active && enq == waited) {
             if (s->stop) break;
             s->cv_work.wait(lk);
             continue;
         }
-        lk.unlock();
-        const int rc = run_tick(s);
-        lk.lock();
-        ++s->ticks;
-        if (rc) {
-            s->error = rc;
-            s->error_msg = rs_last_error();
-            for (Req* r : s->inflight) delete r;
-            s->inflight.clear();
-            s->cv_done.notify_all();
-            break;
-        }
-        const auto now = Clock::now();
-        std::vector<Req*> keep;
-        for (Req* r : s->inflight) {
-            const int d = s->ops[r->op]->d;
-            bool fin = false;
-            if (r->phase == 0) {
-                if (r->level == 1) r->phase = 1; else --r->level;
-            } else if (r->phase == 1) {
-                r->phase = 2;
-                r->level = 1;
-            } else if (r->level == d) {
-                fin = true;
-            } else {
-                ++r->level;
+        if (active) {
+            const int slot = (int)((enq + 1) & 1);       // its previous tick (enq - 1) has completed
+            lk.unlock();
+            const int rc = run_tick(s, slot);
+            lk.lock();
+            if (rc) {
+                fail_all(rc);
+                break;
             }
-            if (!fin) { keep.push_back(r); continue; }
-            s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
-            s->done_q.push_back(r->ticket);
-            ++s->completed;
-            s->rhs_completed += r->nrhs;
-            s->arena.release(r->off, r->bytes);
-            s->ops[r->op]->inflight -= 1;
-            delete r;
+            ++enq;
+            ++s->ticks;
+            for (Req* r : s->inflight) {
+                if (r->done_tick >= 0) continue;
+                const int d = s->ops[r->op]->d;
+                if (r->phase == 0) {
+                    if (r->level == 1) r->phase = 1; else --r->level;
+                } else if (r->phase == 1) {
+                    r->phase = 2;
+                    r->level = 1;
+                } else if (r->level == d) {
+                    r->done_tick = enq;
+                } else {
+                    ++r->level;
+                }
+            }
         }
-        s->inflight.swap(keep);
-        s->cv_done.notify_all();
+        // wait for the older tick in flight (the newest one too when nothing new was issued)
+        const int64_t target = active ? enq - 1 : enq;
+        if (target > waited) {
+            lk.unlock();
+            const cudaError_t e = cudaEventSynchronize(s->ev[target & 1]);
+            lk.lock();
+            if (e != cudaSuccess) {
+                fail_all(cuda_fail(e, "server tick"));
+                break;
+            }
+            waited = target;
+            const auto now = Clock::now();
+            std::vector<Req*> keep;
+            for (Req* r : s->inflight) {
+                if (r->done_tick < 0 || r->done_tick > waited) {
+                    keep.push_back(r);
+                    continue;
+                }
+                s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+                s->done_q.push_back(r->ticket);
+                ++s->completed;
+                s->rhs_completed += r->nrhs;
+                s->arena.release(r->off, r->bytes);
+                s->ops[r->op]->inflight -= 1;
+                delete r;
+            }
+            s->inflight.swap(keep);
+            s->cv_done.notify_all();
+        }
     }
 }
 
@@ -323,9 +365,12 @@ int rs_server_create(rs_op* const* ops, int n_ops, size_t mem_budget_bytes, int 
     s->max_inflight = max_inflight;
     cudaError_t e = cudaSetDevice(s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&s->ev[q], cudaEventDisableTiming);
     if (e == cudaSuccess) e = s->pool.alloc(mem_budget_bytes);
     if (e != cudaSuccess) {
         const int rc = cuda_fail(e, "server setup");
+        for (int q = 0; q < 2; ++q)
+            if (s->ev[q]) cudaEventDestroy(s->ev[q]);
         if (s->st) cudaStreamDestroy(s->st);
         delete s;
         return rc;
@@ -438,10 +483,19 @@ void rs_server_free(rs_server* s)
         s->ops[r->op]->inflight -= 1;
         delete r;
     }
-    for (Req* r : s->inflight) delete r;
+    for (Req* r : s->inflight) {
+        s->ops[r->op]->inflight -= 1;
+        delete r;
+    }
     for (rs_op* op : s->ops) op->inflight -= 1;
-    if (s->st) cudaStreamDestroy(s->st);
-    if (s->h_stage) cudaFreeHost(s->h_stage);
+    if (s->st) {
+        cudaStreamSynchronize(s->st);
+        cudaStreamDestroy(s->st);
+    }
+    for (int q = 0; q < 2; ++q) {
+        if (s->ev[q]) cudaEventDestroy(s->ev[q]);
+        if (s->h_stage[q]) cudaFreeHost(s->h_stage[q]);
+    }
     delete s;
 }
 

@@ -3,7 +3,8 @@
 fused with the dot products of step s+1), and the form that keeps the open-column lists in
 global memory (taken by itself for boxes too large for shared memory), and the form that keeps
 each box in the shared memory of one thread-block cluster (variant 4; levels whose boxes do not
-fit 16 CTAs take the default).  Each is forced on every level and checked
+fit 16 CTAs take the default), and the form that processes eight columns per warp pass with
+one reduction and one bookkeeping pass per eight (variant 5).  Each is forced on every level and checked
 against the oracle: identical ranks and skeleton sets, solutions within the 1e-9 bound of the
 FP64 path.  The cases cover several CTAs per box (64^2 grids and up), boxes whose rank test
 stops the factorisation before min(r, m) (eps = 1e-5, and the extra group barrier the
@@ -16,7 +17,7 @@ from paper_1303_5466_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [0, 1, 2, 3, 4]
+VARIANTS = [0, 1, 2, 3, 4, 5]
 
 
 @pytest.fixture(scope="module")
@@ -62,7 +63,7 @@ def test_variant_matches_oracle_laplace(rs, oracle_mod, variant, n, leaf, eps):
     assert _rel(x, xo) <= tol
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 def test_variant_matches_default_128(rs, variant):
     """128^2 grid, leaves 16^2: Y blocks of several hundred rows and columns, so every loop
     of the kernels (full blocks of rows, leftover rows, paired and single columns) runs."""
@@ -100,12 +101,13 @@ def test_look_ahead_helmholtz_c128_and_c64(rs, oracle_mod):
     assert res <= 1e-10 * 1.01
 
 
+@pytest.mark.parametrize("variant", [4, 5])
 @pytest.mark.parametrize("n,leaf", [(32, 8), (64, 16)])
-def test_cluster_form_helmholtz_c128_and_c64(rs, oracle_mod, n, leaf):
+def test_variant_helmholtz_c128_and_c64(rs, oracle_mod, n, leaf, variant):
     kappa = 25.0
     b = W.coeff_b_gaussian(n)
     F = oracle_mod.Factorization(n, leaf, 1e-10, b=b, kind=1, kappa=kappa)
-    S = rs.Solver(W.grid_points(n), leaf, eps=1e-10, kappa=kappa, b=b, opts=_opts(rs, 4, rs.RS_C128))
+    S = rs.Solver(W.grid_points(n), leaf, eps=1e-10, kappa=kappa, b=b, opts=_opts(rs, variant, rs.RS_C128))
     mism = []
     for l in range(F.depth, 0, -1):
         for j in range(2 ** l):
@@ -115,7 +117,7 @@ def test_cluster_form_helmholtz_c128_and_c64(rs, oracle_mod, n, leaf):
     assert not mism
     f = W.rhs_plane_wave(n, kappa)
     assert _rel(S.solve(f), F.solve(f)) <= 1e-9
-    o = _opts(rs, 4, rs.RS_C64_REFINED)
+    o = _opts(rs, variant, rs.RS_C64_REFINED)
     o.refine_max_iter = 12
     S32 = rs.Solver(W.grid_points(n), leaf, eps=1e-5, kappa=kappa, b=b, opts=o)
     x = S32.solve(f)
@@ -123,7 +125,7 @@ def test_cluster_form_helmholtz_c128_and_c64(rs, oracle_mod, n, leaf):
     assert res <= 1e-10 * 1.01
 
 
-@pytest.mark.parametrize("variant", [2, 4])
+@pytest.mark.parametrize("variant", [2, 4, 5])
 def test_variant_mixed_fp32(rs, oracle_mod, variant):
     n, leaf = 64, 8
     a = W.coeff_a_batched(n)
@@ -135,7 +137,7 @@ def test_variant_mixed_fp32(rs, oracle_mod, variant):
 
 
 def test_bad_variant_is_rejected(rs):
-    o = _opts(rs, 5)
+    o = _opts(rs, 6)
     with pytest.raises(RuntimeError):
         rs.Solver(W.grid_points(16), 4, eps=1e-10, opts=o)
 

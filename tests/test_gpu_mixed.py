@@ -7,6 +7,8 @@ oracle's.  Both sides refine to their own residual bound; two solutions with rel
 residuals r1, r2 differ by at most cond(A) (r1 + r2), and cond(A) ~ 1.13 here, so with
 r_gpu <= 1e-10 and r_oracle <= 1e-12 the tolerance is 1e-9.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -116,7 +118,15 @@ def test_mixed_multi_rhs_device_and_nonconvergence(P):
 @pytest.mark.slow
 def test_mixed_full_size_sampled_residual(P, oracle_mod):
     """The mixed workload at full size: 1024 x 1024 grid (N = 1048576), leaves 16 x 16,
-    eps 1e-6 FP32 factor, refinement to 1e-10, f ~ U[-1,1] (seed 2)."""
+    eps 1e-6 FP32 factor, refinement to 1e-10, f ~ U[-1,1] (seed 2).
+
+    Checked against the oracle's FP64 solution of the same problem (eps 1e-10, stored for 2048
+    sampled rows by tests/golden/make_laplace_mixed_sample.py, which calls only the oracle):
+    two solutions with residuals r1, r2 differ by at most |A^{-1}| (r1 + r2) |f|, and A =
+    I + (a positive operator) has |A^{-1}| <= 1, so with r1 <= 1e-10 (the refinement target)
+    and the oracle's r2 (stated in the file, ~1e-13) the sampled relative difference is held to
+    1e-9.  The true residual on 128 of those rows, computed entry by entry by the oracle, is
+    held to the 1e-10 target itself."""
     import torch
     cfg = W.WORKLOADS["laplace_mixed"]
     n, leaf = cfg["n"], cfg["leaf"]
@@ -130,9 +140,14 @@ def test_mixed_full_size_sampled_residual(P, oracle_mod):
         st = P.rs_op_stats(op)
         assert st["refine_residual"] <= 1e-10
         x = xd.cpu().numpy()
-        rows = np.random.default_rng(2).choice(n * n, 128, replace=False)
-        r = oracle_mod.matvec_rows(n, x, rows) - f[rows]
-        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(f[rows]) * 10
+        gold = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "laplace_mixed_1024_oracle_sample.txt"))
+        rows = gold[:, 0].astype(np.int64)
+        xo = gold[:, 1]
+        diff = np.linalg.norm(x[rows] - xo) / np.linalg.norm(xo)
+        assert diff <= 1e-9, diff
+        sub = rows[:128]
+        r = oracle_mod.matvec_rows(n, x, sub) - f[sub]
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(f[sub])
     finally:
         P.rs_free(op)
         P.rs_free_tree(tree)
