@@ -58,6 +58,10 @@ def _args():
                    help="laplace_n256 is a quarter-size copy for profiling runs")
     p.add_argument("--serving-requests", type=int, default=600,
                    help="requests of the serving stream measured after the main step (0 = skip)")
+    p.add_argument("--full-factor", action="store_true",
+                   help="with --impl reference: time one full oracle factorization and 4-RHS solve of the "
+                        "workload at all host cores and on one thread's sample level, printed as its own "
+                        "JSON line (not the benchmark line)")
     p.add_argument("--serving-only", action="store_true",
                    help="instead of the benchmark: only the serving stream (e.g. --serving-requests 10000), "
                         "printed as its own JSON line")
@@ -817,6 +821,24 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_reference_full(args):
+    """--impl reference --full-factor: the oracle's whole factorization (every level, the root)
+    and its 4-RHS solve of the batched Laplace workload on all host cores, timed once; the
+    measured counterpart of the arm's extrapolated figure."""
+    n, leaf, eps, nrhs, pts, a, F = _inputs()
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    S = O.Factorization(n, leaf, eps, a=a, threads=cores)
+    t1 = time.perf_counter()
+    S.solve(F)
+    t2 = time.perf_counter()
+    print(json.dumps({"oracle_full": {"workload": _config(n, leaf, eps, nrhs, 1)["workload"], "cores": cores,
+                                      "factor_s": t1 - t0, "solve_4rhs_s": t2 - t1,
+                                      "factor_unknowns_per_s": n * n / (t1 - t0)}}))
+
+
 def run_reference(args):
     """The oracle arm: every step (warm-up and timed) factors the ORACLE_LEVELS finest levels of
     the workload (every box of them) with the oracle on all host cores, a bounded sample of the
@@ -921,7 +943,9 @@ def run_serving_only(args):
 
 def main():
     args = _args()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.full_factor:
+        run_reference_full(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.large_grid:
         run_large_grid(args)

@@ -361,3 +361,16 @@ def test_planted_mistake_is_caught(oracle_mod, tmp_path, plant):
 
 def test_unplanted_oracle_passes_the_same_pins(oracle_mod):
     assert not _pins_fail(oracle_mod)
+
+
+def test_mixed_golden_sample_is_consistent():
+    """The stored oracle sample of the 1024 x 1024 mixed workload: its rows are the ones the
+    writing script draws (default_rng(2), 2048 without replacement, sorted), its solution
+    values are finite and of the size |f| ~ 1 implies, and its stored residuals are at
+    rounding level (the oracle's eps = 1e-10 solution of a well-conditioned operator)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "laplace_mixed_1024_oracle_sample.txt")
+    g = np.loadtxt(path)
+    rows = np.sort(np.random.default_rng(2).choice(1024 * 1024, 2048, replace=False))
+    np.testing.assert_array_equal(g[:, 0].astype(np.int64), rows)
+    assert np.isfinite(g[:, 1]).all() and 0.05 < np.abs(g[:, 1]).mean() < 2.0
+    assert np.linalg.norm(g[:, 2]) <= 1e-10 * np.sqrt(2048 / 3.0)      # |f_i| ~ U[-1,1]: rms 1/sqrt(3)
