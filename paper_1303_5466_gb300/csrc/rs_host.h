@@ -105,6 +105,7 @@ struct ProgStage {
     int src = 0, dst = 0, add = 0;
     int64_t count = 0;           // copy: rows; matvec: blocks
     int np = 0;                  // matvec: problems
+    int rb = 64;                 // matvec: output rows per block (16, 32 or 64, by problem size)
     DevMem a, b;                 // copy: source and destination rows; matvec: problems, first blocks
     double work = 0.0;           // matvec: sum of rows x cols
 };

@@ -564,12 +564,18 @@ int build_program(std::vector<ProgItem>& items, cudaStream_t st, Program& prog)
             if ((rc = upload_vec(s.b, sl.d, st))) return rc;
         } else {
             if (sl.mv.empty()) continue;
+            // blocks of 16, 32 or 64 output rows: the HSS1D nodes are small (a few tens of
+            // rows), and a block taller than its problem leaves most of its threads idle
+            double outs = 0.0;
+            for (const MatvecProb& p : sl.mv) outs += (double)(p.trans ? p.cols : p.rows);
+            const double mean_out = outs / (double)sl.mv.size();
+            s.rb = mean_out <= 24.0 ? 16 : mean_out <= 48.0 ? 32 : 64;
             std::vector<int64_t> blk(sl.mv.size());
             int64_t nblk = 0;
             for (size_t i = 0; i < sl.mv.size(); ++i) {
                 const MatvecProb& p = sl.mv[i];
                 blk[i] = nblk;
-                nblk += ((p.trans ? p.cols : p.rows) + 63) / 64;
+                nblk += ((p.trans ? p.cols : p.rows) + s.rb - 1) / s.rb;
                 s.work += (double)p.rows * (double)p.cols;
             }
             s.count = nblk;
@@ -594,7 +600,7 @@ int run_program(cudaStream_t st, const Program& prog, const T* store, const T* i
             RS_CUDA(launch_copy_rows<T>(st, s.count, s.a.as<int64_t>(), s.b.as<int64_t>(), src, dst, nrhs, s.add));
         } else {
             RS_CUDA(launch_matvec<T>(st, s.a.as<MatvecProb>(), s.b.as<int64_t>(), s.np, s.count, store, z, z, nrhs,
-                                     64));
+                                     s.rb));
         }
     }
     return RS_OK;
