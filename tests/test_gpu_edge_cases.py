@@ -68,7 +68,7 @@ def test_ragged_rhs_counts_on_device(rs, oracle_mod, nrhs):
     xd = torch.full_like(fd, np.nan)
     rs.rs_solve(S.op, fd, nrhs, xd, torch.cuda.current_stream())
     torch.cuda.synchronize()
-    x = xd.cpu().numpy().T
+    x = xd.cpu().numpy().T.reshape(n * n, nrhs)
     xo = F.solve(f).reshape(n * n, nrhs)
     for c in range(nrhs):
         assert _rel(x[:, c], xo[:, c]) <= SOL_TOL, c
