@@ -62,6 +62,14 @@ def _args():
                    help="with --impl reference: time one full oracle factorization and 4-RHS solve of the "
                         "workload at all host cores and on one thread's sample level, printed as its own "
                         "JSON line (not the benchmark line)")
+    p.add_argument("--residual-grid", type=int, default=0,
+                   help="instead of the benchmark: the FP64 direct-sum residual (1 RHS) of an n x n grid's "
+                        "operator (tree build alone), timed, as its own JSON line")
+    p.add_argument("--factor-grid", type=int, default=0,
+                   help="instead of the benchmark: one factorization of an n x n grid of the batched Laplace "
+                        "workload (leaf 16), timed with its per-class profile, as its own JSON line")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                   help="--factor-grid: FP64 at eps 1e-10, or FP32 at eps 1e-6")
     p.add_argument("--serving-only", action="store_true",
                    help="instead of the benchmark: only the serving stream (e.g. --serving-requests 10000), "
                         "printed as its own JSON line")
@@ -927,6 +935,69 @@ def run_large_grid(args):
     P.rs_free_tree(tree)
 
 
+def run_residual_grid(args):
+    """--residual-grid n: the FP64 direct-sum residual of one right-hand side on an n x n grid
+    (the refinement's residual kernel), on an operator built by the tree build alone
+    (opts.forward_only), timed with CUDA events; prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_1303_5466_gb300 as P
+    from paper_1303_5466_gb300 import build as B
+    B.build()
+    n = args.residual_grid
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream()
+    tree = P.rs_build_tree(W.grid_points(n), 16)
+    o = P.rs_opts_default()
+    o.forward_only = 1
+    op = P.rs_factor(tree, eps=1e-10, opts=o, stream=st)
+    f = torch.from_numpy(W.rhs_uniform(n, 2)[None, :].copy()).cuda()
+    x = torch.from_numpy(W.rhs_uniform(n, 3)[None, :].copy()).cuda()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    rel = float(P.rs_residual(op, x, f, 1, st)[0])
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"residual_grid": {"n": n, "nrhs": 1, "ms": ms, "pair_terms": float(n) ** 4,
+                                        "tflops": 2.0 * float(n) ** 4 / (ms * 1e-3) / 1e12, "rel": rel}}))
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+
+
+def run_factor_grid(args):
+    """--factor-grid n: one factorization of the n x n batched Laplace workload (leaf 16,
+    a = 1 + 0.5 sin(2 pi x1) cos(2 pi x2)) in FP64 at eps 1e-10 or FP32 at eps 1e-6, timed, with
+    its per-class profile; prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_1303_5466_gb300 as P
+    from paper_1303_5466_gb300 import build as B
+    B.build()
+    n = args.factor_grid
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream()
+    tree = P.rs_build_tree(W.grid_points(n), 16)
+    o = P.rs_opts_default()
+    o.profile = 1
+    eps = 1e-10
+    if args.precision == "fp32":
+        o.precision = P.RS_MIXED_FP32
+        eps = 1e-6
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    op = P.rs_factor(tree, a=W.coeff_a_batched(n), eps=eps, opts=o, stream=st)
+    e1.record(st)
+    e1.synchronize()
+    prof = P.rs_op_profile(op)
+    print(json.dumps({"factor_grid": {"n": n, "precision": args.precision, "eps": eps, "factor_ms": e0.elapsed_time(e1),
+                                      "profile_ms": {k: v[0] for k, v in prof.items()},
+                                      "profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items()
+                                                         if v[0] > 0 and v[1] > 0}}}))
+    P.rs_free(op)
+    P.rs_free_tree(tree)
+
+
 def run_serving_only(args):
     """--serving-only: the serving stream alone (three resident operators, Poisson arrivals at
     0.5, 0.7 and 0.9 x the measured capacity); prints one JSON line (not the benchmark line)."""
@@ -951,6 +1022,10 @@ def main():
         run_large_grid(args)
     elif args.serving_only:
         run_serving_only(args)
+    elif args.residual_grid:
+        run_residual_grid(args)
+    elif args.factor_grid:
+        run_factor_grid(args)
     else:
         run_ours(args)
 

@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
     unsigned long long best = 0;
     if (fits) {
         for (int jl = warp; jl < nc; jl += NW) {
-            double q = sumsq_strided<T>(lane, r, 32, [&](int i) { return Ys[(int64_t)jl * ld + i]; });
+            double q = 0.0;
+            for (int i = lane; i < r; i += 32) q += abs2d(Ys[(int64_t)jl * ld + i]);
             q = warp_sum(q);
             if (lane == 0) { nrm[jl] = q; ref[jl] = q; }
             const unsigned long long kq = pivot_key(q, j0 + jl);
@@ -144,8 +145,11 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
         // 2. the Householder vector from the owner's copy of column p (rows s..r-1)
         const T* colp = cluster.map_shared_rank(Ys + (int64_t)lp * ld, owner);
         double part2 = 0.0;
-        for (int i = s + threadIdx.x; i < r; i += NT) v[i] = colp[i];
-        part2 = sumsq_strided<T>(s + threadIdx.x, r, NT, [&](int i) { return v[i]; });
+        for (int i = s + threadIdx.x; i < r; i += NT) {
+            const T x = colp[i];
+            v[i] = x;
+            part2 += abs2d(x);
+        }
         if (owner == c && threadIdx.x == 0) {
             const int t = pos[lp], last = open[nopen - 1];
             open[t] = last;
@@ -225,7 +229,8 @@ __global__ void __launch_bounds__(NT) cpqr_cl_kernel(int C, const int64_t* __res
             for (int q = warp; q < nrec; q += NW) {
                 const int jq = rec[q];
                 const T* cq = Ys + (int64_t)jq * ld;
-                double acc = sumsq_strided<T>(s + 1 + lane, r, 32, [&](int i) { return cq[i]; });
+                double acc = 0.0;
+                for (int i = s + 1 + lane; i < r; i += 32) acc += abs2d(cq[i]);
                 acc = warp_sum(acc);
                 if (lane == 0) { nrm[jq] = acc; ref[jq] = acc; }
             }

@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(NT) cpqr_la_kernel(int G0, const int32_t* __re
                 const T* col = c == 0 ? col0 : col1;
                 const T dc = shfl_(d, 16 * c);
                 const T td = tau * dc;
-                double q = sumsq_strided<T>(from + lane, r, 32,
-                                            [&](int i2) { return fma_(-vv[i2], td, ldcg_(col + i2)); });
+                double q = 0.0;
+                for (int i2 = from + lane; i2 < r; i2 += 32) q += abs2d(fma_(-vv[i2], td, ldcg_(col + i2)));
                 q = warp_sum(q);
                 if (!TWO || (lane >> 4) == c) nv = q;
                 if (lane == 16 * c) ref[jj] = q;
@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(NT) cpqr_la_kernel(int G0, const int32_t* __re
         unsigned long long best = 0;
         for (int j = lo + warp; j < hi; j += NW) {
             const T* col = Y + (int64_t)j * r;
-            double q = sumsq_strided<T>(lane, r, 32, [&](int i) { return col[i]; });
+            double q = 0.0;
+            for (int i = lane; i < r; i += 32) q += abs2d(col[i]);
             q = warp_sum(q);
             if (lane == 0) { nrm[j] = q; ref[j] = q; }
             const unsigned long long kq = pivot_key(q, j);
@@ -154,8 +155,12 @@ __global__ void __launch_bounds__(NT) cpqr_la_kernel(int G0, const int32_t* __re
         const int p = group_pivot(0);
         if (p < 0 || p >= m) { if (threadIdx.x == 0) atomicOr(status, DEV_BADSIZE); goto done; }
         const T* colp = Y + (int64_t)p * r;
-        for (int i = threadIdx.x; i < r; i += NT) va[i] = ldcg_(colp + i);
-        const double part = sumsq_strided<T>(threadIdx.x, r, NT, [&](int i) { return va[i]; });
+        double part = 0.0;
+        for (int i = threadIdx.x; i < r; i += NT) {
+            const T x = ldcg_(colp + i);
+            va[i] = x;
+            part += abs2d(x);
+        }
         const double a2 = block_sum<NT>(part, dred);
         T beta;
         alpha0 = householder(va, 0, a2, beta, tau_a);
@@ -243,8 +248,12 @@ __global__ void __launch_bounds__(NT) cpqr_la_kernel(int G0, const int32_t* __re
             if (p < 0 || p >= m) { if (threadIdx.x == 0) atomicOr(status, DEV_BADSIZE); goto done; }
             const T* colp = Y + (int64_t)p * r;
             const T tw = tau_a * ldcg_(wv + p);
-            for (int i = s + 1 + threadIdx.x; i < r; i += NT) vb[i] = fma_(-va[i], tw, ldcg_(colp + i));
-            const double part = sumsq_strided<T>(s + 1 + threadIdx.x, r, NT, [&](int i) { return vb[i]; });
+            double part = 0.0;
+            for (int i = s + 1 + threadIdx.x; i < r; i += NT) {
+                const T x = fma_(-va[i], tw, ldcg_(colp + i));
+                vb[i] = x;
+                part += abs2d(x);
+            }
             const double a2 = block_sum<NT>(part, dred);
             T beta;
             const double alpha = householder(vb, s + 1, a2, beta, tau_b);

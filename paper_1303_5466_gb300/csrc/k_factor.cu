@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
         unsigned long long best = 0;
         for (int j = lo + warp; j < hi; j += NW) {
             const T* col = Y + (int64_t)j * r;
-            double q = sumsq_strided<T>(lane, r, 32, [&](int i) { return col[i]; });
+            double q = 0.0;
+            for (int i = lane; i < r; i += 32) q += abs2d(col[i]);
             q = warp_sum(q);
             if (lane == 0) { nrm[j] = q; ref[j] = q; }
             const unsigned long long kq = pivot_key(q, j);
@@ -160,23 +161,10 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
         // 2. drop p from the open list (every CTA the same way), Householder vector
         const T* colp = Y + (int64_t)p * r;
         double part = 0.0;
-        {
-            // |x|^2 summed in FP64 (FP64 data), or in runs of 16 in the storage precision added
-            // in FP64 (reduced precision: no FP64 multiply per element)
-            using Rr = typename sc_traits<T>::real;
-            Rr pr = Rr(0);
-            int cnt = 0;
-            for (int i = s + threadIdx.x; i < r; i += NT) {
-                const T x = ldcg_(colp + i);
-                v[i] = x;
-                if constexpr (std::is_same<Rr, double>::value) {
-                    part += abs2d(x);
-                } else {
-                    pr += abs2s(x);
-                    if (++cnt == 16) { part += (double)pr; pr = Rr(0); cnt = 0; }
-                }
-            }
-            if constexpr (!std::is_same<Rr, double>::value) part += (double)pr;
+        for (int i = s + threadIdx.x; i < r; i += NT) {
+            const T x = ldcg_(colp + i);
+            v[i] = x;
+            part += abs2d(x);
         }
         const double a2 = block_sum<NT>(part, dred);    // its barriers also order the loads above
         if (threadIdx.x == 0) {
@@ -299,7 +287,8 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
                 for (int c = 0; c < (TWO ? 2 : 1); ++c) {
                     if (!(need & (1u << (16 * c)))) continue;
                     const T* col = c == 0 ? col0 : col1;
-                    double q = sumsq_strided<T>(s + 1 + lane, r, 32, [&](int i2) { return ldcg_(col + i2); });
+                    double q = 0.0;
+                    for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(ldcg_(col + i2));
                     q = warp_sum(q);
                     if (!TWO || (lane >> 4) == c) nv = q;
                     if (lane == 16 * c) ref[jj] = q;
@@ -404,7 +393,8 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
                     rec &= rec - 1;
                     const int jq = __shfl_sync(0xffffffffu, jme, src);
                     const T* col = Y + (int64_t)jq * r;
-                    double q = sumsq_strided<T>(s + 1 + lane, r, 32, [&](int i2) { return ldcg_(col + i2); });
+                    double q = 0.0;
+                    for (int i2 = s + 1 + lane; i2 < r; i2 += 32) q += abs2d(ldcg_(col + i2));
                     q = warp_sum(q);
                     if (lane == src) {
                         nv = q;

@@ -69,33 +69,6 @@ template <class R> __host__ __device__ inline double abs2d(cplx<R> a)
     return (double)a.re * (double)a.re + (double)a.im * (double)a.im;
 }
 template <class S> __host__ __device__ inline double absd(S a) { return sqrt(abs2d(a)); }
-// |a|^2 in the real type of a (the storage precision)
-__host__ __device__ inline double abs2s(double a) { return a * a; }
-__host__ __device__ inline float abs2s(float a) { return a * a; }
-template <class R> __host__ __device__ inline R abs2s(cplx<R> a) { return a.re * a.re + a.im * a.im; }
-
-// Sum of |x_i|^2 for i = i0, i0 + stride, ... < n, with x_i = ld(i), returned in FP64.  FP64
-// data: one FP64 sum in index order.  Reduced-precision data (FP32, complex64): partial sums
-// of 16 terms in the storage precision, added in FP64, so the FP64 pipe (64 times slower than
-// the FP32 one on this GPU) sees one add per 16 elements instead of a multiply-add per element,
-// while each partial carries at most 16 roundings of the storage precision.
-template <class T, class Ld>
-__host__ __device__ inline double sumsq_strided(int i0, int n, int stride, Ld ld)
-{
-    using R = typename sc_traits<T>::real;
-    double q = 0.0;
-    if constexpr (std::is_same<R, double>::value) {
-        for (int i = i0; i < n; i += stride) q += abs2d(ld(i));
-    } else {
-        int i = i0;
-        while (i < n) {
-            R p = R(0);
-            for (int c = 0; c < 16 && i < n; ++c, i += stride) p += abs2s(ld(i));
-            q += (double)p;
-        }
-    }
-    return q;
-}
 __host__ __device__ inline double absd(double a) { return fabs(a); }
 __host__ __device__ inline double absd(float a) { return fabs((double)a); }
 __host__ __device__ inline bool finite_(double a) { return isfinite(a); }
