@@ -757,6 +757,7 @@ def run_ours(args):
         "sampled_residual": res,
         "flops_factor": last_stats["flops_factor"], "bytes_factors": last_stats["bytes_factors"],
         "root_m": last_stats["root_m"],
+        "host_wall_ms": {"id_phase": last_stats["ms_tree"], "inverse_phase": last_stats["ms_inverse"]},
         "roofline": {"kernel": dom, "classes": list(KERNEL_CLASSES[dom]), "bound": "alu", "achieved": achieved, "peak": peak64,
                      "unit": "TFLOP/s", "frac": achieved / peak64,
                      "peak_nominal": PEAK_FP64_NOMINAL_TFLOPS, "frac_of_nominal": achieved / PEAK_FP64_NOMINAL_TFLOPS,

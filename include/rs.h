@@ -92,10 +92,13 @@ typedef struct {
                                     arithmetic up to rounding order                   [0]    */
     int spd_inverse;             /* 1: invert F, E and the root of a real symmetric kernel
                                     (RS_LAPLACE) by the symmetric sweep without pivoting
-                                    (half the flops of Gauss-Jordan); a level whose pivots
-                                    show a block that is not positive definite to working
-                                    accuracy is redone with pivoted Gauss-Jordan
-                                    (rs_stats.spd_fallbacks).  0: always pivoted GJ  [1]    */
+                                    (half the flops of Gauss-Jordan); when the pivots show
+                                    a block that is not positive definite to working
+                                    accuracy, the inversions are redone with pivoted
+                                    Gauss-Jordan (all of them with the per-level launches,
+                                    whose status is read once after the root; the failing
+                                    level's in the per-box and translation-invariant modes;
+                                    rs_stats.spd_fallbacks).  0: always pivoted GJ  [1]    */
     int cpqr_variant;            /* form of the column-pivoted QR (Eq. 2.1) on every level:
                                     0 = two passes over the open columns per step, 4 rows
                                     per lane in flight; 1 = the same with 8; 2 = look-ahead
@@ -274,7 +277,11 @@ typedef struct {
     int64_t bytes_compressed;    /* device bytes of their compressed forms                 */
     int64_t bytes_dense_replaced;/* bytes the same blocks (Phi, E, T) take densely         */
     double ms_compress;          /* wall time of the compression                           */
-    int spd_fallbacks;           /* inversions redone with pivoted Gauss-Jordan (opts.spd_inverse) */
+    int spd_fallbacks;           /* inversions redone with pivoted Gauss-Jordan (opts.spd_inverse):
+                                    with the per-level launches, a block found not SPD
+                                    anywhere reruns every inversion of the factorization
+                                    (2 x depth + 1); in the per-box and translation-invariant
+                                    modes, those of the failing levels               */
     int refine_fp64_sums;        /* refined precisions: FP64 direct sums of the last rs_solve (the
                                     first residual, and each confirmation of the tolerance;
                                     the other corrections' products run in FP32)            */

@@ -215,7 +215,9 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
 
 // Symmetric sweep inverse of a level's SPD blocks (real kernels only).  *not_spd is set, and
 // the status word cleared, when a block is not positive definite to working accuracy: the
-// blocks are then partly swept and the caller rebuilds them for run_gj.
+// blocks are then partly swept and the caller rebuilds them for run_gj.  While op->defer_spd
+// is set the launch returns without waiting: the status word is read once after the whole
+// inverse phase, which is redone with Gauss-Jordan if any sweep found a block not SPD.
 template <class T>
 int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, T* A,
               const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls,
@@ -279,6 +281,7 @@ int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem
                                             op->d_bar.as<unsigned int>(), op->d_status.as<int>(),
                                             (long long)op->opts.spin_limit, max_m, NB));
         }
+        if (op->defer_spd) return RS_OK;
         RS_CUDA(cudaStreamSynchronize(st));
         prof_flush(op);
         int s = 0;
@@ -1109,6 +1112,9 @@ int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
     op->stats.ms_tree = ms_since(t0);
     auto t1 = Clock::now();
     const bool fwd_only = op->opts.forward_only != 0;
+    // the per-box inverse phase runs without a host round trip per sweep: one status check
+    // after the root, and a rerun with pivoted Gauss-Jordan if a block was not SPD
+    op->defer_spd = use_sweep(op) && !op->opts.per_box && !op->opts.translation_invariant && !fwd_only;
     for (int l = op->d; l >= 1; --l) {
         const Level* child = l < op->d ? &op->lev[l + 1] : nullptr;
         if (fwd_only) {             // the tree build alone: no F^{-1}, no E
@@ -1138,6 +1144,26 @@ int factor_levels(rs_op* op, cudaStream_t st, Clock::time_point t0)
     if ((rc = upload(R.d_m, to32(R.m), st))) return rc;
     if (fwd_only) R.phi_off = {0, 0};
     else if ((rc = inverse_level<T>(op, R, &op->lev[1], st))) return rc;
+    if (op->defer_spd) {
+        op->defer_spd = false;
+        RS_CUDA(cudaStreamSynchronize(st));
+        prof_flush(op);
+        int s = 0;
+        RS_CUDA(cudaMemcpy(&s, op->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (s & DEV_NOT_SPD) {
+            // every inversion of the phase again, by pivoted Gauss-Jordan (each level's F is
+            // rebuilt from the children's new E)
+            RS_CUDA(cudaMemsetAsync(op->d_status.p, 0, sizeof(int), st));
+            op->opts.spd_inverse = 0;
+            for (int l = op->d; l >= 1 && !rc; --l)
+                rc = inverse_level<T>(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st);
+            if (!rc) rc = inverse_level<T>(op, R, &op->lev[1], st);
+            op->opts.spd_inverse = 1;
+            if (rc) return rc;
+            op->stats.spd_fallbacks = 2 * op->d + 1;
+        }
+        if ((rc = check_status(op, st))) return rc;
+    }
     if ((rc = compress_levels<T>(op, st))) return rc;
     for (int l = 0; l <= op->d; ++l)
         if ((rc = solve_plan(op, op->lev[l], l < op->d ? &op->lev[l + 1] : nullptr, st))) return rc;

@@ -270,6 +270,8 @@ struct rs_op {
     std::vector<rs::Level> ti_lev;
     double ti_s0 = 1.0;               // the constant Helmholtz scaling s = kappa sqrt(b) there
     bool fw_built = false;            // forward-apply block lists uploaded
+    bool defer_spd = false;           // sweeps of the inverse phase launch without a host check
+                                      // of their status (checked once after the root)
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // factor-time scratch reused across levels, released with the op
     rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2, t_ck, t_ce;
