@@ -111,7 +111,9 @@ typedef struct {
                                     fit 16 CTAs; the others take the default); 5 = 0 with
                                     eight columns per warp pass, their dot products summed
                                     by recursive halving across the lanes and the per-column
-                                    bookkeeping done once per column; -1 = the
+                                    bookkeeping done once per column; 6 = 0 with 2 rows per
+                                    lane in flight and registers capped for five CTAs per SM;
+                                    -1 = the
                                     autotuner's table (rs_autotune), else 0 or 1 by
                                     occupancy. Same result up to rounding order       [-1]   */
     int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the

@@ -68,8 +68,8 @@ cudaError_t launch_assemble_Y(cudaStream_t st, int nb, const int32_t* act, const
 //      share for the next step.
 // The rank test |R_ss| > eps |R_00| ends the loop in all CTAs at the same step (every CTA
 // computes alpha from the same data in the same order).
-template <int NT, int U, bool GL, class T, bool BT = false>
-__global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restrict__ cta_off,
+template <int NT, int U, bool GL, class T, bool BT>
+__device__ __forceinline__ void cpqr_body(int G0, const int32_t* __restrict__ cta_off,
         const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ nnear, int P, const int64_t* __restrict__ y_off,
         T* __restrict__ Yall, double eps, int32_t* __restrict__ kout, int32_t* __restrict__ piv,
@@ -426,6 +426,28 @@ __global__ void __launch_bounds__(NT) cpqr_kernel(int G0, const int32_t* __restr
     if (gi == 0 && threadIdx.x == 0) kout[b] = k;
 }
 
+#define RS_CPQR_PARAMS                                                                                               \
+    int G0, const int32_t *__restrict__ cta_off, const int64_t *__restrict__ act_off,                                \
+        const int32_t *__restrict__ nnear, int P, const int64_t *__restrict__ y_off, T *__restrict__ Yall, double eps, \
+        int32_t *__restrict__ kout, int32_t *__restrict__ piv, T *__restrict__ diag, unsigned int *__restrict__ bar, \
+        unsigned long long *__restrict__ keys, int *__restrict__ status, long long spin,                            \
+        double *__restrict__ nrm_all, double *__restrict__ ref_all, int *__restrict__ gwork, int gstride
+#define RS_CPQR_PASS G0, cta_off, act_off, nnear, P, y_off, Yall, eps, kout, piv, diag, bar, keys, status, spin, \
+                     nrm_all, ref_all, gwork, gstride
+
+template <int NT, int U, bool GL, class T, bool BT = false>
+__global__ void __launch_bounds__(NT) cpqr_kernel(RS_CPQR_PARAMS)
+{
+    cpqr_body<NT, U, GL, T, BT>(RS_CPQR_PASS);
+}
+
+// The same body with registers capped for five CTAs per SM (variant 6).
+template <int NT, int U, bool GL, class T>
+__global__ void __launch_bounds__(NT, 5) cpqr_occ_kernel(RS_CPQR_PARAMS)
+{
+    cpqr_body<NT, U, GL, T, false>(RS_CPQR_PASS);
+}
+
 template <class T>
 static size_t cpqr_shm(int max_r, int max_m, bool global_lists)
 {
@@ -446,7 +468,7 @@ size_t cpqr_gwork_ints(int max_r, int max_m, int deep, int ctas)
     return cpqr_global<T>(max_r, max_m, deep) ? (size_t)ctas * (size_t)(2 * max_m + 2) : 0;
 }
 
-template <int U, bool GL, class T, bool BT>
+template <int U, bool GL, class T, bool BT, bool OCC = false>
 static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas,
                                  const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y,
                                  double eps, int32_t* kout, int32_t* piv, T* diag, unsigned int* bar,
@@ -454,7 +476,7 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
                                  double* ref, int* gwork, int gstride)
 {
     constexpr int NT = 256;
-    auto fn = cpqr_kernel<NT, U, GL, T, BT>;
+    auto fn = OCC ? cpqr_occ_kernel<NT, U, GL, T> : cpqr_kernel<NT, U, GL, T, BT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
     count_launches(1);
@@ -470,13 +492,15 @@ static cudaError_t launch_cpqr_u(cudaStream_t st, int nb, int G, const int32_t* 
     return cudaLaunchCooperativeKernel((void*)fn, dim3((unsigned)(cta_off ? ctas : nb * G)), dim3(NT), args, shm, st);
 }
 
-// The kernel instance of a variant: deep 0 (U = 4), 1 (U = 8), 3 (global lists) and 5 (eight
-// columns per warp pass, U unused) of cpqr_kernel.
+// The kernel instance of a variant: deep 0 (U = 4), 1 (U = 8), 3 (global lists), 5 (eight
+// columns per warp pass, U unused) and 6 (U = 2, registers capped for five CTAs per SM: more
+// boxes in flight per SM to cover each one's per-step latency) of cpqr_kernel.
 template <class T>
 static const void* cpqr_fn(int deep, bool glob)
 {
     constexpr int NT = 256;
     if (deep == 5) return glob ? (const void*)cpqr_kernel<NT, 4, true, T, true> : (const void*)cpqr_kernel<NT, 4, false, T, true>;
+    if (deep == 6) return glob ? (const void*)cpqr_occ_kernel<NT, 2, true, T> : (const void*)cpqr_occ_kernel<NT, 2, false, T>;
     if (glob) return deep == 1 ? (const void*)cpqr_kernel<NT, 8, true, T> : (const void*)cpqr_kernel<NT, 4, true, T>;
     return deep == 1 ? (const void*)cpqr_kernel<NT, 8, false, T> : (const void*)cpqr_kernel<NT, 4, false, T>;
 }
@@ -504,6 +528,8 @@ cudaError_t launch_cpqr(cudaStream_t st, int nb, int G, const int32_t* cta_off, 
                      spin_limit, shm, nrm, ref, gw, gstride
     if (deep == 5)
         return glob ? launch_cpqr_u<4, true, T, true>(RS_CPQR_ARGS) : launch_cpqr_u<4, false, T, true>(RS_CPQR_ARGS);
+    if (deep == 6)
+        return glob ? launch_cpqr_u<2, true, T, false, true>(RS_CPQR_ARGS) : launch_cpqr_u<2, false, T, false, true>(RS_CPQR_ARGS);
     if (glob)
         return deep == 1 ? launch_cpqr_u<8, true, T, false>(RS_CPQR_ARGS) : launch_cpqr_u<4, true, T, false>(RS_CPQR_ARGS);
     return deep == 1 ? launch_cpqr_u<8, false, T, false>(RS_CPQR_ARGS) : launch_cpqr_u<4, false, T, false>(RS_CPQR_ARGS);

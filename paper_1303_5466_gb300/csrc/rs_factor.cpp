@@ -1212,7 +1212,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
-    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 5) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 5");
+    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 6) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 6");
     if (op->opts.sweep_panel != 0 && op->opts.sweep_panel != 8 && op->opts.sweep_panel != 16)
         return fail(RS_E_INVALID, "sweep_panel must be 0, 8 or 16");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))
@@ -1818,8 +1818,9 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
                                 {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0},
                                 {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}, {2.0, 1, 1.0, 0.0}, {3.0, 0, 0.5, 0.0},
-                                {1.0, 0, 1.0, 0.0, 16}, {1.0, 1, 0.5, 0.0, 16}, {1.0, 4, 1.0, 0.0}};
-    constexpr int NTR = 13;
+                                {1.0, 0, 1.0, 0.0, 16}, {1.0, 1, 0.5, 0.0, 16}, {1.0, 4, 1.0, 0.0},
+                                {1.0, 6, 1.0, 0.0}};
+    constexpr int NTR = 14;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);
