@@ -34,16 +34,16 @@ WORKLOAD = "laplace_batched"
 # NVIDIA's figures).  The roofline divides by the rate the library's FP64 probes measure in
 # the same run (the better of DFMA chains and mma.sync f64), and reports this one beside it.
 PEAK_FP64_NOMINAL_TFLOPS = 1.25
-# DRAM bytes (read + write) per cpqr_kernel launch, from one ncu capture of dram__bytes_read.sum
-# and dram__bytes_write.sum at this workload with one launch per level; None once the kernel
-# has changed since that capture
-CPQR_TRAFFIC_BYTES_PER_LAUNCH = 143.5e9
+# DRAM bytes (read + write) per launch of the CPQR class (cpqr_kernel and cpqr_bl_kernel), from
+# one ncu capture of dram__bytes_read.sum and dram__bytes_write.sum at this workload with one
+# launch per level; None once a kernel has changed since that capture
+CPQR_TRAFFIC_BYTES_PER_LAUNCH = None
 # FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
 # factor kernels and the profile classes (rs_op_profile) whose launches they are (the inverse
 # classes run the symmetric sweep on the Laplace workload)
-KERNEL_CLASSES = {"sweep_kernel": ("inv_F", "inv_E", "inv_root"), "cpqr_kernel": ("cpqr",),
+KERNEL_CLASSES = {"sweep_kernel": ("inv_F", "inv_E", "inv_root"), "cpqr_kernel+cpqr_bl_kernel": ("cpqr",),
                   "gemm_kernel": ("gemm_E",), "id_T_kernel": ("id_T",)}
 
 
@@ -68,6 +68,9 @@ def _args():
     p.add_argument("--factor-grid", type=int, default=0,
                    help="instead of the benchmark: one factorization of an n x n grid of the batched Laplace "
                         "workload (leaf 16), timed with its per-class profile, as its own JSON line")
+    p.add_argument("--cpqr-variant", type=int, default=-1,
+                   help="--factor-grid: the column-pivoted QR form forced on every level (opts.cpqr_variant; "
+                        "-1 = the built-in choice per level)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                    help="--factor-grid: FP64 at eps 1e-10, or FP32 at eps 1e-6")
     p.add_argument("--serving-only", action="store_true",
@@ -761,7 +764,7 @@ def run_ours(args):
         "roofline": {"kernel": dom, "classes": list(KERNEL_CLASSES[dom]), "bound": "alu", "achieved": achieved, "peak": peak64,
                      "unit": "TFLOP/s", "frac": achieved / peak64,
                      "peak_nominal": PEAK_FP64_NOMINAL_TFLOPS, "frac_of_nominal": achieved / PEAK_FP64_NOMINAL_TFLOPS,
-                     "traffic": CPQR_TRAFFIC_BYTES_PER_LAUNCH if dom == "cpqr_kernel" else None,
+                     "traffic": CPQR_TRAFFIC_BYTES_PER_LAUNCH if dom.startswith("cpqr") else None,
                      "traffic_note": "ncu DRAM read+write bytes per launch at this workload, one launch per "
                                      "level (no autotuner batching)",
                      "launches": nl, "avg_launch_ms": ms / max(nl, 1),
@@ -969,7 +972,8 @@ def run_residual_grid(args):
 def run_factor_grid(args):
     """--factor-grid n: one factorization of the n x n batched Laplace workload (leaf 16,
     a = 1 + 0.5 sin(2 pi x1) cos(2 pi x2)) in FP64 at eps 1e-10 or FP32 at eps 1e-6, timed, with
-    its per-class profile; prints one JSON line (not the benchmark line)."""
+    its per-class profile and the CPQR time of every level (finest first), the CPQR form given by
+    --cpqr-variant; prints one JSON line (not the benchmark line)."""
     import torch
     import paper_1303_5466_gb300 as P
     from paper_1303_5466_gb300 import build as B
@@ -980,6 +984,7 @@ def run_factor_grid(args):
     tree = P.rs_build_tree(W.grid_points(n), 16)
     o = P.rs_opts_default()
     o.profile = 1
+    o.cpqr_variant = args.cpqr_variant
     eps = 1e-10
     if args.precision == "fp32":
         o.precision = P.RS_MIXED_FP32
@@ -991,7 +996,10 @@ def run_factor_grid(args):
     e1.record(st)
     e1.synchronize()
     prof = P.rs_op_profile(op)
-    print(json.dumps({"factor_grid": {"n": n, "precision": args.precision, "eps": eps, "factor_ms": e0.elapsed_time(e1),
+    depth = P.rs_op_stats(op)["depth"]
+    print(json.dumps({"factor_grid": {"n": n, "precision": args.precision, "eps": eps, "cpqr_variant": args.cpqr_variant,
+                                      "factor_ms": e0.elapsed_time(e1),
+                                      "cpqr_ms_by_level": [P.rs_op_profile_level(op, "cpqr", l) for l in range(depth, 0, -1)],
                                       "profile_ms": {k: v[0] for k, v in prof.items()},
                                       "profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items()
                                                          if v[0] > 0 and v[1] > 0}}}))

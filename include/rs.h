@@ -113,7 +113,10 @@ typedef struct {
                                     by recursive halving across the lanes and the per-column
                                     bookkeeping done once per column; 6 = 0 with 2 rows per
                                     lane in flight and registers capped for five CTAs per SM;
-                                    -1 = the
+                                    7 / 8 = blocked: the trailing updates deferred over
+                                    panels of 16 / 8 steps, so a step reads each open column
+                                    once (real scalars and boxes whose lists fit shared
+                                    memory; the others take the default); -1 = the
                                     autotuner's table (rs_autotune), else 0 or 1 by
                                     occupancy. Same result up to rounding order       [-1]   */
     int translation_invariant;   /* a(x) (and b(x)) constant, so A depends only on the

@@ -542,6 +542,7 @@ int cpqr_max_ctas(int max_r, int max_m, int G, int deep)
     constexpr int NT = 256;
     (void)G;
     if (deep == 2) return cpqr_la_max_ctas<T>(max_r, max_m);
+    if (deep == 7 || deep == 8) return cpqr_bl_max_ctas<T>(max_r, max_m, deep == 7 ? 16 : 8);
     const bool glob = cpqr_global<T>(max_r, max_m, deep);
     const size_t shm = cpqr_shm<T>(max_r, max_m, glob);
     if (shm > 227 * 1024) return 0;

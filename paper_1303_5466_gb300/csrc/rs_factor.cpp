@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <map>
 #include <chrono>
 #include <cmath>
@@ -173,7 +174,7 @@ namespace {
 
 // Workspace of the ID phase, released when rs_factor returns.
 struct IdWork {
-    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms, cta_off, gwork;
+    DevMem near, near_off, geo, y_off, nn, piv, diag, skpos, rscol, Y, keys, norms, cta_off, gwork, blk;
 };
 
 template <class T>
@@ -354,9 +355,11 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
     // at every step), at the price of fewer CTAs per box.  Untuned: one launch per level.
     const std::string tkey = tune_key("cpqr", (int)sizeof(T), nb, L.max_m, L.max_r);
     const double gs = g_trial.cpqr_gscale >= 0.0 ? g_trial.cpqr_gscale : tune_get(tkey + ".gscale", 1.0);
-    const int deep_set = g_trial.cpqr_deep >= 0         ? g_trial.cpqr_deep
-                         : op->opts.cpqr_variant >= 0 ? op->opts.cpqr_variant
-                                                      : (int)tune_get(tkey + ".deep", -1.0);
+    int deep_set = g_trial.cpqr_deep >= 0         ? g_trial.cpqr_deep
+                   : op->opts.cpqr_variant >= 0 ? op->opts.cpqr_variant
+                                                : (int)tune_get(tkey + ".deep", -1.0);
+    // the blocked forms (7, 8) take real scalars and boxes whose lists fit shared memory
+    if ((deep_set == 7 || deep_set == 8) && !cpqr_bl_fits<T>(L.max_r, L.max_m)) deep_set = -1;
     const double batch_bytes =
         96.0 * (1 << 20) * (g_trial.cpqr_batch >= 0.0 ? g_trial.cpqr_batch : tune_get(tkey + ".batch", 0.0));
     std::vector<int> b_start(1, 0);
@@ -402,7 +405,7 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
         }
         // the open columns are re-split every step, so a group may take one CTA per 16 columns
         // (sized for the co-residency of the variant when one is set)
-        const bool streaming = deep_set >= 0 && deep_set != 4;      // variants 0-3 and 5
+        const bool streaming = deep_set >= 0 && deep_set != 4;      // variants 0-3 and 5-8
         const int var = streaming ? deep_set : 0;
         int G = choose_group(B.nb, 2 * B.max_m, [&](int g) { return cpqr_max_ctas<T>(B.max_r, B.max_m, g, var); });
         if (G > 1 && gs > 0.0 && gs < 1.0) G = std::max(1, (int)std::lround(G * gs));
@@ -436,10 +439,16 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
             B.cta_pos = (size_t)-1;
             B.ctas = B.nb * G;
         }
-        // few CTAs per SM: each warp keeps twice the rows in flight
+        // few CTAs per SM: each warp keeps twice the rows in flight.  FP64 levels of many
+        // small boxes (one or two CTAs each) take the blocked form with panels of 8 steps:
+        // measured 9-19% faster there at 512^2, slower where a box spreads over more CTAs (its
+        // two group barriers per step then wait on the slowest of them) and in FP32
         B.deep = (G > 1 && B.ctas <= 2 * sms) ? 1 : 0;
+        if (std::is_same<T, double>::value && G <= 2 && B.max_r <= 704 && cpqr_bl_fits<T>(B.max_r, B.max_m)) B.deep = 8;
         if (streaming) B.deep = deep_set;
-        if (B.deep && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, B.deep)) B.deep = 0;   // must stay co-resident
+        // a group of several CTAs must stay co-resident
+        if (B.deep && (G > 1 || B.cta_pos != (size_t)-1) && B.ctas > cpqr_max_ctas<T>(B.max_r, B.max_m, G, B.deep))
+            B.deep = 0;
         max_keys = std::max(max_keys, (size_t)(2 * B.ctas));
         bats.push_back(B);
     }
@@ -452,6 +461,11 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
     for (const Batch& B : bats)
         if (!B.cl) gw_ints = std::max(gw_ints, cpqr_gwork_ints<T>(B.max_r, B.max_m, B.deep, B.ctas));
     if (gw_ints) RS_CUDA(w.gwork.alloc(sizeof(int) * gw_ints));
+    size_t bl_bytes = 0;       // V, F and group partials of the blocked forms
+    for (const Batch& B : bats)
+        if (!B.cl && (B.deep == 7 || B.deep == 8))
+            bl_bytes = std::max(bl_bytes, cpqr_bl_bytes<T>(B.nb, B.max_r, sum_m, B.ctas, B.deep == 7 ? 16 : 8));
+    if (bl_bytes) RS_CUDA(w.blk.alloc(bl_bytes));
     // squared norms, their references, and (look-ahead variant) the dot products v^H y_j
     const size_t nrm_dbl = 2 * (size_t)(sum_m + 1), wv_dbl = ((size_t)(sum_m + 1) * sizeof(T) + 7) / 8;
     RS_CUDA(w.norms.alloc(sizeof(double) * (nrm_dbl + wv_dbl)));
@@ -464,6 +478,17 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
                                           w.y_off.as<int64_t>() + B.b0, w.Y.as<T>(), op->eps,
                                           L.d_k.as<int32_t>() + B.b0, w.piv.as<int32_t>(), w.diag.as<T>(),
                                           op->d_status.as<int>(), B.max_r, B.max_m));
+                continue;
+            }
+            if (B.deep == 7 || B.deep == 8) {
+                RS_CUDA(launch_cpqr_bl<T>(st, B.nb, B.G,
+                                          B.cta_pos == (size_t)-1 ? nullptr : w.cta_off.as<int32_t>() + B.cta_pos,
+                                          B.ctas, B.deep == 7 ? 16 : 8, L.d_act_off.as<int64_t>() + B.b0,
+                                          w.nn.as<int32_t>() + B.b0, P, w.y_off.as<int64_t>() + B.b0, w.Y.as<T>(),
+                                          op->eps, L.d_k.as<int32_t>() + B.b0, w.piv.as<int32_t>(), w.diag.as<T>(),
+                                          op->d_bar.as<unsigned int>() + B.b0, w.keys.as<unsigned long long>(),
+                                          op->d_status.as<int>(), (long long)op->opts.spin_limit, B.max_r, B.max_m,
+                                          sum_m, w.norms.as<double>(), w.norms.as<double>() + sum_m + 1, w.blk.p));
                 continue;
             }
             RS_CUDA(launch_cpqr<T>(st, B.nb, B.G,
@@ -1212,7 +1237,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut < 0) return fail(RS_E_INVALID, "k_cut must be >= 0");
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
-    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 6) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 6");
+    if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 8) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 8");
     if (op->opts.sweep_panel != 0 && op->opts.sweep_panel != 8 && op->opts.sweep_panel != 16)
         return fail(RS_E_INVALID, "sweep_panel must be 0, 8 or 16");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))
@@ -1812,15 +1837,16 @@ int rs_autotune(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     o.profile = 1;
     o.k_cut = 0;
     const cudaStream_t st = (cudaStream_t)stream;
-    // candidates: (CPQR group scale, CPQR variant (4 rows, 8 rows, look-ahead), sweep group
+    // candidates: (CPQR group scale, CPQR variant (4 rows, 8 rows, look-ahead, cluster-resident,
+    // register-capped, blocked), sweep group
     // scale, CPQR batch budget, sweep panel width); every sweep scale appears, and the CPQR
     // settings are picked per level as one triple, the sweep's as one pair
     const TuneTrial trials[] = {{1.0, 0, 1.0, 0.0}, {1.0, 1, 0.5, 0.0}, {1.0, 0, 0.25, 1.0},
                                 {1.0, 1, 1.0, 1.0}, {0.5, 1, 0.5, 2.0}, {1.0, 1, 1.0, 2.0},
                                 {1.0, 2, 1.0, 0.0}, {1.0, 2, 0.5, 1.0}, {2.0, 1, 1.0, 0.0}, {3.0, 0, 0.5, 0.0},
                                 {1.0, 0, 1.0, 0.0, 16}, {1.0, 1, 0.5, 0.0, 16}, {1.0, 4, 1.0, 0.0},
-                                {1.0, 6, 1.0, 0.0}};
-    constexpr int NTR = 14;
+                                {1.0, 6, 1.0, 0.0}, {1.0, 8, 1.0, 0.0}};
+    constexpr int NTR = 15;
     auto timed_factor = [&](rs_op** op, double* ms) -> int {
         auto t0 = std::chrono::steady_clock::now();
         int rc = factor_impl(tree, kernel, a, eps, &o, st, op);

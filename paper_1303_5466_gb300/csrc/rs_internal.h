@@ -140,6 +140,23 @@ cudaError_t launch_cpqr_cl(cudaStream_t st, int nb, int C, const int64_t* act_of
                            const int64_t* y_off, T* Y, double eps, int32_t* kout, int32_t* piv, T* diag, int* status,
                            int max_r, int max_m);
 
+// Variants 7 and 8 (k_cpqr_bl.cu): the trailing updates deferred over panels of nbp = 16 or 8
+// steps; real scalars only.  Same arguments and outputs as launch_cpqr, plus sum_m (the level's
+// act_off[nb] of all boxes, which F is indexed by) and scratch: cpqr_bl_bytes() bytes of
+// device memory (V, F and the group partials).
+template <class T>
+bool cpqr_bl_fits(int max_r, int max_m);
+template <class T>
+int cpqr_bl_max_ctas(int max_r, int max_m, int nbp);
+template <class T>
+size_t cpqr_bl_bytes(int nb, int max_r, int64_t sum_m, int ctas, int nbp);
+template <class T>
+cudaError_t launch_cpqr_bl(cudaStream_t st, int nb, int G, const int32_t* cta_off, int ctas, int nbp,
+                           const int64_t* act_off, const int32_t* nnear, int P, const int64_t* y_off, T* Y,
+                           double eps, int32_t* kout, int32_t* piv, T* diag, unsigned int* bar,
+                           unsigned long long* keys, int* status, long long spin_limit, int max_r, int max_m,
+                           int64_t sum_m, double* nrm, double* ref, void* scratch);
+
 // T = R11^{-1} R12 for every box, written column-major (k x (m-k)) at t_off[b], rows by
 // sorted skeleton position (skpos[pivot position]) and columns by residual rank.
 template <class T>

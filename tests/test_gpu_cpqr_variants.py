@@ -4,8 +4,10 @@ fused with the dot products of step s+1), and the form that keeps the open-colum
 global memory (taken by itself for boxes too large for shared memory), and the form that keeps
 each box in the shared memory of one thread-block cluster (variant 4; levels whose boxes do not
 fit 16 CTAs take the default), and the form that processes eight columns per warp pass with
-one reduction and one bookkeeping pass per eight (variant 5), and the two-rows-in-flight form
-capped at the registers of five CTAs per SM (variant 6).  Each is forced on every level and checked
+one reduction and one bookkeeping pass per eight (variant 5), the two-rows-in-flight form
+capped at the registers of five CTAs per SM (variant 6), and the blocked forms that defer the
+trailing updates over panels of 16 or 8 steps (variants 7, 8; real scalars, complex operators
+take the default form).  Each is forced on every level and checked
 against the oracle: identical ranks and skeleton sets, solutions within the 1e-9 bound of the
 FP64 path.  The cases cover several CTAs per box (64^2 grids and up), boxes whose rank test
 stops the factorisation before min(r, m) (eps = 1e-5, and the extra group barrier the
@@ -18,7 +20,7 @@ from paper_1303_5466_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [0, 1, 2, 3, 4, 5, 6]
+VARIANTS = [0, 1, 2, 3, 4, 5, 6, 7, 8]
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +66,7 @@ def test_variant_matches_oracle_laplace(rs, oracle_mod, variant, n, leaf, eps):
     assert _rel(x, xo) <= tol
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_variant_matches_default_128(rs, variant):
     """128^2 grid, leaves 16^2: Y blocks of several hundred rows and columns, so every loop
     of the kernels (full blocks of rows, leftover rows, paired and single columns) runs."""
@@ -102,7 +104,7 @@ def test_look_ahead_helmholtz_c128_and_c64(rs, oracle_mod):
     assert res <= 1e-10 * 1.01
 
 
-@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("variant", [4, 5, 7])
 @pytest.mark.parametrize("n,leaf", [(32, 8), (64, 16)])
 def test_variant_helmholtz_c128_and_c64(rs, oracle_mod, n, leaf, variant):
     kappa = 25.0
@@ -126,7 +128,7 @@ def test_variant_helmholtz_c128_and_c64(rs, oracle_mod, n, leaf, variant):
     assert res <= 1e-10 * 1.01
 
 
-@pytest.mark.parametrize("variant", [2, 4, 5])
+@pytest.mark.parametrize("variant", [2, 4, 5, 7, 8])
 def test_variant_mixed_fp32(rs, oracle_mod, variant):
     n, leaf = 64, 8
     a = W.coeff_a_batched(n)
@@ -138,7 +140,7 @@ def test_variant_mixed_fp32(rs, oracle_mod, variant):
 
 
 def test_bad_variant_is_rejected(rs):
-    o = _opts(rs, 7)
+    o = _opts(rs, 9)
     with pytest.raises(RuntimeError):
         rs.Solver(W.grid_points(16), 4, eps=1e-10, opts=o)
 
