@@ -37,7 +37,7 @@ PEAK_FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch of the CPQR class (cpqr_kernel and cpqr_bl_kernel), from
 # one ncu capture of dram__bytes_read.sum and dram__bytes_write.sum at this workload with one
 # launch per level; None once a kernel has changed since that capture
-CPQR_TRAFFIC_BYTES_PER_LAUNCH = None
+CPQR_TRAFFIC_BYTES_PER_LAUNCH = 136.3e9
 # FP32 FMA peak (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
