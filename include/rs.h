@@ -140,6 +140,11 @@ typedef struct {
                                     operator), rs_residual and rs_bicgstab's matvec, not
                                     rs_solve.  Not with translation_invariant, k_cut or
                                     per_box                                           [0]    */
+    int gemm_form;               /* products forming E (Algorithm 1) of RS_FP64 operators:
+                                    1 = exact products of 7-bit digit slices on the bf16
+                                    tensor cores, summed in integers (one rounding per
+                                    entry; parts below 2^-56 of the row and column maxima
+                                    left out); 0 = FP64 FMA tiles                     [1]    */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);

@@ -42,7 +42,8 @@ class rs_opts(C.Structure):
                 ("spin_limit", C.c_int64), ("profile", C.c_int), ("hss_leaf", C.c_int),
                 ("hss_eps", C.c_double), ("solve_graph", C.c_int),
                 ("per_box", C.c_int), ("spd_inverse", C.c_int), ("cpqr_variant", C.c_int),
-                ("translation_invariant", C.c_int), ("sweep_panel", C.c_int), ("forward_only", C.c_int)]
+                ("translation_invariant", C.c_int), ("sweep_panel", C.c_int), ("forward_only", C.c_int),
+                ("gemm_form", C.c_int)]
 
 
 class rs_stats(C.Structure):

@@ -1,0 +1,253 @@
+// k_gemm_oz.cu -- FP64 grouped GEMM from exact products of 7-bit digit slices on the bf16 tensor
+// cores (the E products of Algorithm 1: W = Phi_{:,r} T^T + Phi_{:,s}, E^{-1} = T W_r + W_s).
+//
+// This GPU runs FP64 FMAs at 1.2 TFLOP/s and bf16 tensor-core products (mma.sync, FP32
+// accumulation) at 0.6 PFLOP/s.  Each FP64 entry is written as a sum of eight signed 7-bit
+// digits against a power of two shared by its row of A (or column of B): x = sum_s q_s 2^(E-7-7s),
+// |q_s| <= 127, exact up to the 56th bit below the row's largest entry.  A digit is an integer
+// that bf16 holds exactly, and so is the product of two; a K-chunk of 128 of them, summed over
+// the at most 8 digit pairs (i, j) of one level l = i + j, stays below 2^24 and is therefore exact
+// in the tensor core's FP32 accumulator.  The eight level sums of a chunk are combined in int64
+// (W_A = sum_{l<4} S_l 2^(7(3-l)), W_B the same for l = 4..7) and summed over the chunks exactly,
+// so C = 2^(EA+EB-35) (W_A + 2^-28 W_B) carries one rounding, against K roundings of a chain of
+// FP64 FMAs.  Levels above 7 (products below 2^-56 of the row and column maxima) are left out:
+// the result differs from the exact product by at most about K 2^-56 max|A_i,:| max|B_:,j|.
+//
+// Launch: one warp per row of A and per column of B finds its exponent first; then one CTA of
+// 8 warps per 64 x 32 tile of C, the warps 16 x 16 each (two m16n8k16 tiles), K in stages of
+// 32 digits staged in shared memory (split on the fly from the FP64 operands).
+#include <algorithm>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "k_common.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr int OZ_BM = 64, OZ_BN = 32, OZ_BK = 32, OZ_NT = 256;
+constexpr int OZ_S = 8;               // digit slices per entry
+constexpr int OZ_CHUNK = 128;         // K per exact FP32 level sum
+constexpr int OZ_LD = OZ_BK + 8;      // padded row of a slice tile (bf16), conflict-free fragments
+
+__device__ __forceinline__ double oz_a(const GemmProb& P, const double* A, int i, int k)
+{
+    return P.ta ? A[(int64_t)i * P.lda + k] : A[(int64_t)k * P.lda + i];
+}
+__device__ __forceinline__ double oz_b(const GemmProb& P, const double* B, int k, int j)
+{
+    return P.tb ? B[(int64_t)k * P.ldb + j] : B[(int64_t)j * P.ldb + k];
+}
+
+// Exponent E of every row of A and column of B: max |x| < 2^E (0 for an all-zero line).
+__global__ void __launch_bounds__(256) oz_exp_kernel(const GemmProb* __restrict__ probs, int np,
+        const int64_t* __restrict__ eoff, int64_t nlines, const double* __restrict__ Ab,
+        const double* __restrict__ Bb, int* __restrict__ ex)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nlines) return;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (eoff[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const GemmProb P = probs[lo];
+    const int idx = (int)(w - eoff[lo]);
+    double mx = 0.0;
+    if (idx < P.M) {
+        const double* A = Ab + P.a_off;
+        for (int k = lane; k < P.K; k += 32) mx = fmax(mx, fabs(oz_a(P, A, idx, k)));
+    } else {
+        const double* B = Bb + P.b_off;
+        for (int k = lane; k < P.K; k += 32) mx = fmax(mx, fabs(oz_b(P, B, k, idx - P.M)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        int e = 0;
+        if (mx > 0.0) frexp(mx, &e);
+        ex[w] = e;
+    }
+}
+
+// The eight signed digits of x against 2^E: |x| 2^(56-E) truncated to an integer Z < 2^56, digit s
+// the bits 49-7s .. 55-7s of Z, with the sign of x.
+__device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16* out, int stride)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((u >> 52) & 0x7ff);
+    unsigned long long Z = 0;
+    if (ef != 0) {                                   // zeros and subnormals: no digits
+        const unsigned long long mt = (u & ((1ull << 52) - 1)) | (1ull << 52);
+        const int sh = (ef - 1023) + 4 - E;          // |x| < 2^E, so sh <= 3
+        if (sh >= 0) Z = mt << sh;
+        else if (sh > -64) Z = mt >> (-sh);
+    }
+    const bool neg = (u >> 63) != 0;
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        const int d = (int)((Z >> (49 - 7 * s)) & 127ull);
+        out[s * stride] = __float2bfloat16_rn((float)(neg ? -d : d));
+    }
+}
+
+__device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __restrict__ probs, int np,
+        const int64_t* __restrict__ eoff, const int* __restrict__ ex, const double* __restrict__ Ab,
+        const double* __restrict__ Bb, double* Cb, const double* C0b)
+{
+    extern __shared__ __align__(16) unsigned char oz_smem[];
+    auto As = reinterpret_cast<__nv_bfloat16 (*)[OZ_BM][OZ_LD]>(oz_smem);
+    auto Bs = reinterpret_cast<__nv_bfloat16 (*)[OZ_BN][OZ_LD]>(oz_smem + sizeof(__nv_bfloat16) * OZ_S * OZ_BM * OZ_LD);
+    __shared__ int eA[OZ_BM], eB[OZ_BN];
+    const int64_t t = blockIdx.x;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const GemmProb P = probs[lo];
+    const int64_t lt = t - P.tile0;
+    const int tm = (int)(lt % P.tiles_m), tn = (int)(lt / P.tiles_m);
+    const int row0 = tm * OZ_BM, col0 = tn * OZ_BN;
+    if (P.lower && col0 > row0 + OZ_BM - 1) return;          // wholly above the diagonal
+    const double* A = Ab + P.a_off;
+    const double* B = Bb + P.b_off;
+    const int* exA = ex + eoff[lo];
+    const int* exB = exA + P.M;
+    for (int e = threadIdx.x; e < OZ_BM; e += OZ_NT) eA[e] = row0 + e < P.M ? exA[row0 + e] : 0;
+    for (int e = threadIdx.x; e < OZ_BN; e += OZ_NT) eB[e] = col0 + e < P.N ? exB[col0 + e] : 0;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp & 3) * 16, wn = (warp >> 2) * 16;   // the warp's 16 x 16 block of the tile
+    const int g = lane >> 2, q = lane & 3;
+    float S[OZ_S][2][4];                                      // level sums of the chunk, two n8 tiles
+    long long WA[2][4], WB[2][4];
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) WA[n][e] = WB[n][e] = 0;
+    auto zeroS = [&]() {
+#pragma unroll
+        for (int l = 0; l < OZ_S; ++l)
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) S[l][n][e] = 0.0f;
+    };
+    auto flush = [&]() {                                      // the chunk's level sums into int64
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                long long a = 0, b = 0;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) a = a * 128 + (long long)__float2int_rz(S[l][n][e]);
+#pragma unroll
+                for (int l = 4; l < 8; ++l) b = b * 128 + (long long)__float2int_rz(S[l][n][e]);
+                WA[n][e] += a;
+                WB[n][e] += b;
+            }
+    };
+    zeroS();
+    __syncthreads();
+    for (int k0 = 0; k0 < P.K; k0 += OZ_BK) {
+        // stage the digits of the A (64 x 32) and B (32 x 32) tiles
+        for (int e = threadIdx.x; e < OZ_BM * OZ_BK; e += OZ_NT) {
+            const int i = P.ta ? e / OZ_BK : e % OZ_BM, kk = P.ta ? e % OZ_BK : e / OZ_BM;
+            const int gi = row0 + i, gk = k0 + kk;
+            const double x = (gi < P.M && gk < P.K) ? oz_a(P, A, gi, gk) : 0.0;
+            oz_split(x, eA[i], &As[0][i][kk], OZ_BM * OZ_LD);
+        }
+        for (int e = threadIdx.x; e < OZ_BN * OZ_BK; e += OZ_NT) {
+            const int j = P.tb ? e % OZ_BN : e / OZ_BK, kk = P.tb ? e / OZ_BN : e % OZ_BK;
+            const int gj = col0 + j, gk = k0 + kk;
+            const double x = (gj < P.N && gk < P.K) ? oz_b(P, B, gk, gj) : 0.0;
+            oz_split(x, eB[j], &Bs[0][j][kk], OZ_BN * OZ_LD);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < OZ_BK; ks += 16) {
+#pragma unroll
+            for (int i = 0; i < OZ_S; ++i) {
+                uint32_t a[4];
+                a[0] = *(const uint32_t*)&As[i][wm + g][ks + 2 * q];
+                a[1] = *(const uint32_t*)&As[i][wm + g + 8][ks + 2 * q];
+                a[2] = *(const uint32_t*)&As[i][wm + g][ks + 2 * q + 8];
+                a[3] = *(const uint32_t*)&As[i][wm + g + 8][ks + 2 * q + 8];
+#pragma unroll
+                for (int j = 0; j + i < OZ_S; ++j) {
+#pragma unroll
+                    for (int n = 0; n < 2; ++n) {
+                        const uint32_t b0 = *(const uint32_t*)&Bs[j][wn + 8 * n + g][ks + 2 * q];
+                        const uint32_t b1 = *(const uint32_t*)&Bs[j][wn + 8 * n + g][ks + 2 * q + 8];
+                        oz_mma(S[i + j][n], a, b0, b1);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if ((k0 + OZ_BK) % OZ_CHUNK == 0 || k0 + OZ_BK >= P.K) {
+            flush();
+            zeroS();
+        }
+    }
+    // C = alpha 2^(EA+EB-35) (W_A + 2^-28 W_B) + beta C0
+    double* C = Cb + P.c_off;
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int li = wm + g + (e >= 2 ? 8 : 0), lj = wn + 8 * n + 2 * q + (e & 1);
+            const int gi = row0 + li, gj = col0 + lj;
+            if (gi >= P.M || gj >= P.N) continue;
+            const double v = fma((double)WB[n][e], 0x1p-28, (double)WA[n][e]);
+            const double val = ldexp(v, eA[li] + eB[lj] - 35);
+            const double c0 = (P.beta == 0.0) ? 0.0 : C0b[P.c0_off + (int64_t)gj * P.ldc0 + gi];
+            C[(int64_t)gj * P.ldc + gi] = P.alpha * val + P.beta * c0;
+        }
+}
+
+}  // namespace
+
+int64_t gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff)
+{
+    int64_t tiles = 0;
+    eoff.assign(probs.size() + 1, 0);
+    for (size_t p = 0; p < probs.size(); ++p) {
+        GemmProb& g = probs[p];
+        g.tiles_m = (g.M + OZ_BM - 1) / OZ_BM;
+        g.tiles_n = (g.N + OZ_BN - 1) / OZ_BN;
+        g.tile0 = tiles;
+        tiles += (int64_t)g.tiles_m * g.tiles_n;
+        eoff[p + 1] = eoff[p] + g.M + g.N;
+    }
+    return tiles;
+}
+
+cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const int64_t* eoff,
+                           int64_t nlines, int* ex, const double* A, const double* B, double* C, const double* C0)
+{
+    if (np <= 0 || tiles <= 0) return cudaSuccess;
+    count_launches(2);
+    oz_exp_kernel<<<(unsigned)((nlines * 32 + 255) / 256), 256, 0, st>>>(probs, np, eoff, nlines, A, B, ex);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int shm = (int)(sizeof(__nv_bfloat16) * OZ_S * (OZ_BM + OZ_BN) * OZ_LD);
+    e = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+    if (e != cudaSuccess) return e;
+    gemm_oz_kernel<<<(unsigned)tiles, OZ_NT, shm, st>>>(probs, np, eoff, ex, A, B, C, C0);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

@@ -806,6 +806,25 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
     // with the symmetric sweep, E^{-1} (symmetric) is needed on and below the diagonal only:
     // p2l takes those tiles; p2 (all tiles) serves the Gauss-Jordan path and its fallback
     const bool sym = use_sweep(op);
+    // FP64: the products from digit slices on the tensor cores (opts.gemm_form), batched launches
+    const bool use_oz = std::is_same<T, double>::value && op->opts.gemm_form == 1 && !op->opts.per_box;
+    auto run_oz = [&](std::vector<GemmProb> q, DevMem& dq, DevMem& de, const T* A, const T* B, T* C,
+                      const T* C0) -> int {
+        if constexpr (std::is_same<T, double>::value) {
+            std::vector<int64_t> eo;
+            const int64_t tiles = gemm_oz_plan(q, eo);
+            int rc2;
+            if ((rc2 = upload(dq, q, st))) return rc2;
+            if ((rc2 = upload(de, eo, st))) return rc2;
+            RS_CUDA(op->t_ozx.alloc(sizeof(int) * (size_t)(eo.back() + 1)));
+            RS_CUDA(launch_gemm_oz(st, dq.as<GemmProb>(), (int)q.size(), tiles, de.as<int64_t>(), eo.back(),
+                                   op->t_ozx.as<int>(), A, B, C, C0));
+            return RS_OK;
+        } else {
+            (void)q; (void)dq; (void)de; (void)A; (void)B; (void)C; (void)C0;
+            return fail(RS_E_INVALID, "digit-product GEMM for FP64 only");
+        }
+    };
     std::vector<GemmProb> p1, p2, p2l;
     int64_t t1 = 0, t2 = 0, t2l = 0;
     for (int b = 0; b < nb; ++b) {
@@ -857,6 +876,11 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
                 RS_CUDA(launch_gemm<T>(st, op->t_q2.as<GemmProb>() + i, 1, n2, L.d_T.as<T>(), W.as<T>(),
                                        L.d_E.as<T>(), W.as<T>()));
             }
+        } else if (use_oz) {
+            if ((rc = run_oz(p1, op->t_oz1, op->t_ozo1, L.d_Phi.as<T>(), L.d_T.as<T>(), W.as<T>(), L.d_Phi.as<T>())))
+                return rc;
+            if ((rc = run_oz(sym ? p2l : p2, op->t_oz2, op->t_ozo2, L.d_T.as<T>(), W.as<T>(), L.d_E.as<T>(), W.as<T>())))
+                return rc;
         } else {
             RS_CUDA(launch_gemm<T>(st, d_p1.as<GemmProb>(), (int)p1.size(), t1, L.d_Phi.as<T>(), L.d_T.as<T>(),
                                    W.as<T>(), L.d_Phi.as<T>()));
@@ -872,9 +896,14 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
                                L.l, &redo)))
             return rc;
         if (redo && !p1.empty()) {   // E^{-1} again from W, all tiles (the sweep overwrote it)
-            if ((rc = upload(d_p2, p2, st))) return rc;
-            RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
-                                   L.d_E.as<T>(), W.as<T>()));
+            if (use_oz) {
+                if ((rc = run_oz(p2, op->t_oz2, op->t_ozo2, L.d_T.as<T>(), W.as<T>(), L.d_E.as<T>(), W.as<T>())))
+                    return rc;
+            } else {
+                if ((rc = upload(d_p2, p2, st))) return rc;
+                RS_CUDA(launch_gemm<T>(st, d_p2.as<GemmProb>(), (int)p2.size(), t2, L.d_T.as<T>(), W.as<T>(),
+                                       L.d_E.as<T>(), W.as<T>()));
+            }
         }
     }
     if (!redo) return RS_OK;
@@ -1238,6 +1267,7 @@ int factor_impl(const rs_tree* tree, const rs_kernel* kernel, const double* a, d
     if (op->opts.k_cut > 0 && op->opts.hss_leaf < 1) return fail(RS_E_INVALID, "hss_leaf must be >= 1");
     if (!(op->opts.hss_eps >= 0.0) || !(op->opts.hss_eps < 1.0)) return fail(RS_E_INVALID, "hss_eps must be in [0, 1)");
     if (op->opts.cpqr_variant < -1 || op->opts.cpqr_variant > 8) return fail(RS_E_INVALID, "cpqr_variant must be -1 .. 8");
+    if (op->opts.gemm_form != 0 && op->opts.gemm_form != 1) return fail(RS_E_INVALID, "gemm_form must be 0 or 1");
     if (op->opts.sweep_panel != 0 && op->opts.sweep_panel != 8 && op->opts.sweep_panel != 16)
         return fail(RS_E_INVALID, "sweep_panel must be 0, 8 or 16");
     if (op->opts.forward_only && (op->opts.translation_invariant || op->opts.k_cut > 0 || op->opts.per_box))

@@ -48,6 +48,15 @@ struct GemmProb {
     int lower;             // 1: only the tiles on and below the diagonal (M = N; tiles_m (tiles_m + 1) / 2)
 };
 
+// FP64 grouped GEMM from exact products of 7-bit digit slices on the bf16 tensor cores
+// (k_gemm_oz.cu): same descriptors and semantics as launch_gemm, T = double.  gemm_oz_plan
+// re-tiles the descriptors (64 x 32 tiles; `lower` problems keep every tile that touches the lower
+// triangle) and returns the tile count, with eoff[p] the first of problem p's M + N exponent
+// lines (eoff[np] in all); ex: eoff[np] ints of device scratch.
+int64_t gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff);
+cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const int64_t* eoff,
+                           int64_t nlines, int* ex, const double* A, const double* B, double* C, const double* C0);
+
 // Batched matrix-vector(s) descriptor: y = alpha * op(A) x + beta * y, A column-major
 // (rows x cols, ld), x and y point-major (entry p of RHS c at p * nrhs + c); x_off and y_off
 // count points (rows), so one descriptor serves every nrhs.

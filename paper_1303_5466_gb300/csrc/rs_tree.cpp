@@ -146,6 +146,7 @@ void rs_opts_default(rs_opts* o)
     o->translation_invariant = 0;
     o->sweep_panel = 0;
     o->forward_only = 0;
+    o->gemm_form = 1;
     o->solve_graph = 1;
     o->per_box = 0;
     o->hss_eps = 0.0;
