@@ -73,9 +73,8 @@ __global__ void __launch_bounds__(256) oz_exp_kernel(const GemmProb* __restrict_
     }
 }
 
-// The eight signed digits of x against 2^E: |x| 2^(56-E) truncated to an integer Z < 2^56, digit s
-// the bits 49-7s .. 55-7s of Z, with the sign of x.
-__device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16* out, int stride)
+// |x| 2^(56-E) truncated to an integer Z < 2^56 (|x| < 2^E), and the sign of x.
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int E, bool& neg)
 {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const int ef = (int)((u >> 52) & 0x7ff);
@@ -86,12 +85,26 @@ __device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16* out, in
         if (sh >= 0) Z = mt << sh;
         else if (sh > -64) Z = mt >> (-sh);
     }
-    const bool neg = (u >> 63) != 0;
+    neg = (u >> 63) != 0;
+    return Z;
+}
+
+// bf16 bits of the signed digit s of Z (bits 49-7s .. 55-7s): the 7-bit integer through an FP32
+// add of a power of two (exact), the top half of its bits, and the sign bit.
+__device__ __forceinline__ uint32_t oz_digit(unsigned long long Z, bool neg, int s)
+{
+    const uint32_t d = (uint32_t)(Z >> (49 - 7 * s)) & 127u;
+    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+    return (__float_as_uint(f) >> 16) | (neg ? 0x8000u : 0u);
+}
+
+// Digits of two entries (consecutive in k) of one row, one 32-bit word per slice.
+__device__ __forceinline__ void oz_split2(double x0, double x1, int E, uint32_t* out, int stride_words)
+{
+    bool n0, n1;
+    const unsigned long long Z0 = oz_fixed(x0, E, n0), Z1 = oz_fixed(x1, E, n1);
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-        const int d = (int)((Z >> (49 - 7 * s)) & 127ull);
-        out[s * stride] = __float2bfloat16_rn((float)(neg ? -d : d));
-    }
+    for (int s = 0; s < OZ_S; ++s) out[s * stride_words] = oz_digit(Z0, n0, s) | (oz_digit(Z1, n1, s) << 16);
 }
 
 __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
@@ -162,18 +175,20 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
     zeroS();
     __syncthreads();
     for (int k0 = 0; k0 < P.K; k0 += OZ_BK) {
-        // stage the digits of the A (64 x 32) and B (32 x 32) tiles
-        for (int e = threadIdx.x; e < OZ_BM * OZ_BK; e += OZ_NT) {
-            const int i = P.ta ? e / OZ_BK : e % OZ_BM, kk = P.ta ? e % OZ_BK : e / OZ_BM;
-            const int gi = row0 + i, gk = k0 + kk;
-            const double x = (gi < P.M && gk < P.K) ? oz_a(P, A, gi, gk) : 0.0;
-            oz_split(x, eA[i], &As[0][i][kk], OZ_BM * OZ_LD);
+        // stage the digits of the A (64 x 32) and B (32 x 32) tiles, two entries of a row per thread
+        for (int e = threadIdx.x; e < OZ_BM * OZ_BK / 2; e += OZ_NT) {
+            const int i = P.ta ? e / (OZ_BK / 2) : e % OZ_BM, kp = P.ta ? e % (OZ_BK / 2) : e / OZ_BM;
+            const int gi = row0 + i, gk = k0 + 2 * kp;
+            const double x0 = (gi < P.M && gk < P.K) ? oz_a(P, A, gi, gk) : 0.0;
+            const double x1 = (gi < P.M && gk + 1 < P.K) ? oz_a(P, A, gi, gk + 1) : 0.0;
+            oz_split2(x0, x1, eA[i], (uint32_t*)&As[0][i][2 * kp], OZ_BM * OZ_LD / 2);
         }
-        for (int e = threadIdx.x; e < OZ_BN * OZ_BK; e += OZ_NT) {
-            const int j = P.tb ? e % OZ_BN : e / OZ_BK, kk = P.tb ? e / OZ_BN : e % OZ_BK;
-            const int gj = col0 + j, gk = k0 + kk;
-            const double x = (gj < P.N && gk < P.K) ? oz_b(P, B, gk, gj) : 0.0;
-            oz_split(x, eB[j], &Bs[0][j][kk], OZ_BN * OZ_LD);
+        for (int e = threadIdx.x; e < OZ_BN * OZ_BK / 2; e += OZ_NT) {
+            const int j = P.tb ? e % OZ_BN : e / (OZ_BK / 2), kp = P.tb ? e / OZ_BN : e % (OZ_BK / 2);
+            const int gj = col0 + j, gk = k0 + 2 * kp;
+            const double x0 = (gj < P.N && gk < P.K) ? oz_b(P, B, gk, gj) : 0.0;
+            const double x1 = (gj < P.N && gk + 1 < P.K) ? oz_b(P, B, gk + 1, gj) : 0.0;
+            oz_split2(x0, x1, eB[j], (uint32_t*)&Bs[0][j][2 * kp], OZ_BN * OZ_LD / 2);
         }
         __syncthreads();
 #pragma unroll
