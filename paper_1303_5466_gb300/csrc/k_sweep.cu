@@ -361,7 +361,19 @@ cudaError_t launch_sweep_inverse(cudaStream_t st, int nb, int G, const int32_t* 
     return cudaGetLastError();
 }
 
+// The negation and mirroring of the sweep's result alone (for the blocked sweep of k_sweep_bl.cu).
+template <class T>
+cudaError_t launch_sweep_finish(cudaStream_t st, int nb, const int32_t* m, const int64_t* off, T* A, int max_m)
+{
+    if (nb <= 0 || max_m <= 0) return cudaSuccess;
+    const int64_t nt = (max_m + 31) / 32;
+    count_launches(1);
+    sweep_finish_kernel<T><<<dim3((unsigned)(nt * (nt + 1) / 2), (unsigned)nb), 256, 0, st>>>(m, off, A);
+    return cudaGetLastError();
+}
+
 #define RS_INST_SWEEP(T)                                                                                              \
+    template cudaError_t launch_sweep_finish<T>(cudaStream_t, int, const int32_t*, const int64_t*, T*, int);      \
     template int sweep_max_ctas<T>(int);                                                                            \
     template cudaError_t launch_sweep_inverse<T>(cudaStream_t, int, int, const int32_t*, int, const int32_t*,       \
                                                  const int64_t*, T*, T*, const int64_t*, unsigned int*, int*,       \

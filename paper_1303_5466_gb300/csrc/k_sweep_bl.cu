@@ -1,0 +1,199 @@
+// k_sweep_bl.cu -- the symmetric sweep of k_sweep.cu (S <- -S^{-1} for SPD S, lower triangle) in
+// panels of 64, with the rank-64 updates on the digit-slice GEMM of k_gemm_oz.cu.
+//
+// The sweep of a symmetric S on an index block K (D = S_KK) is
+//     S_KK <- -D^{-1},  S_OK <- S_OK D^{-1},  S_KO <- D^{-1} S_KO,  S_OO <- S_OO - S_OK D^{-1} S_KO,
+// so with Q = S[:, K] (the old panel, both triangles) and X = Q D^{-1}, one step is
+//   1. (copy kernel) Q, row-major, in 64 x 64 tiles; (one CTA per matrix) D^{-1} by the element
+//      sweep of the 64 x 64 block D in shared memory, FP64, with the pivot test of k_sweep.cu (a
+//      pivot not above 1e3 unit roundoff times the largest earlier one sets DEV_NOT_SPD);
+//   2. X = Q D^{-1} and S <- S - X Q^T on the tiles touching the lower triangle (both on the
+//      digit-slice GEMM: the m^3 flops of the inverse as 64-deep products);
+//   3. (write kernel) the rows and columns of K, which step 2 left meaningless: S[i, K] = X[i, :]
+//      below K, S[K, j] = X[j, :]^T left of K, S_KK = -D^{-1}.
+// After the last panel S holds -S^{-1} in its lower triangle; launch_sweep_finish negates and
+// mirrors it.  FP64 only.
+#include <float.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "k_common.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr int BS = 64;
+
+// Q (row-major m x 64: Q[i 64 + t] = S(i, k0 + t), both triangles from the lower one) in tiles of
+// 64 rows, each read where S is contiguous (down a column of storage below the panel, along a
+// column of storage -- the panel's rows -- left of it) and transposed through shared memory.
+__global__ void __launch_bounds__(256) sweep_bl_copy_kernel(int k0, const int32_t* __restrict__ msz,
+        const int64_t* __restrict__ off, const double* __restrict__ Aall, const int64_t* __restrict__ qoff,
+        double* __restrict__ Qall)
+{
+    __shared__ double tile[BS][BS + 1];
+    const int b = blockIdx.y;
+    const int m = msz[b];
+    const int i0 = blockIdx.x * BS;
+    if (k0 >= m || i0 >= m) return;
+    const int w = min(BS, m - k0);
+    const double* A = Aall + off[b];
+    double* Q = Qall + qoff[b];
+    const int rows = min(BS, m - i0);
+    if (i0 + BS <= k0) {
+        // rows left of the panel: S(i, k0 + t) = A[i m + k0 + t], contiguous in t
+        for (int e = threadIdx.x; e < BS * BS; e += 256) {
+            const int ii = e / BS, t = e - ii * BS;
+            tile[ii][t] = (ii < rows && t < w) ? A[(int64_t)(i0 + ii) * m + k0 + t] : 0.0;
+        }
+    } else {
+        // rows at or below the panel: S(i, c) = A[c m + i] for i >= c, contiguous in i
+        for (int e = threadIdx.x; e < BS * BS; e += 256) {
+            const int t = e / BS, ii = e - t * BS;
+            const int i = i0 + ii, c = k0 + t;
+            double v = 0.0;
+            if (ii < rows && t < w) v = i >= c ? A[(int64_t)c * m + i] : A[(int64_t)i * m + c];
+            tile[ii][t] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * BS; e += 256) {
+        const int ii = e / BS, t = e - ii * BS;
+        Q[(int64_t)(i0 + ii) * BS + t] = tile[ii][t];
+    }
+}
+
+// D^{-1} of the panel's diagonal block D = Q[k0 .. k0 + w) by the element sweep in shared memory,
+// FP64, with the pivot test of k_sweep.cu; one CTA per matrix.
+__global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_t* __restrict__ msz,
+        const int64_t* __restrict__ qoff, const double* __restrict__ Qall, double* __restrict__ Dall,
+        double* __restrict__ maxp, int* __restrict__ status)
+{
+    __shared__ double sM[BS][BS + 1];
+    __shared__ int s_fail;
+    const int b = blockIdx.x;
+    const int m = msz[b];
+    if (k0 >= m) return;
+    const int w = min(BS, m - k0);
+    const double* Q = Qall + qoff[b] + (int64_t)k0 * BS;
+    for (int e = threadIdx.x; e < BS * BS; e += 256) {
+        const int r = e / BS, c = e - r * BS;
+        sM[r][c] = (r < w && c < w) ? Q[e] : (r == c ? 1.0 : 0.0);
+    }
+    if (threadIdx.x == 0) s_fail = 0;
+    double mp = maxp[b];
+    __syncthreads();
+    // element sweep of D: sM <- -D^{-1} (the padding stays the identity)
+    for (int t = 0; t < w; ++t) {
+        const double p = sM[t][t];
+        if (threadIdx.x == 0 && (!(p > 1e3 * 0.5 * DBL_EPSILON * mp) || !isfinite(p))) s_fail = 1;
+        mp = fmax(mp, p);
+        const double pinv = 1.0 / p;
+        double nv[BS * BS / 256];
+#pragma unroll
+        for (int u = 0; u < BS * BS / 256; ++u) {
+            const int e = threadIdx.x + 256 * u, r = e / BS, c = e - r * BS;
+            if (r == t && c == t) nv[u] = -pinv;
+            else if (r == t) nv[u] = sM[t][c] * pinv;
+            else if (c == t) nv[u] = sM[r][t] * pinv;
+            else nv[u] = fma(-sM[r][t] * pinv, sM[t][c], sM[r][c]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < BS * BS / 256; ++u) {
+            const int e = threadIdx.x + 256 * u, r = e / BS, c = e - r * BS;
+            sM[r][c] = nv[u];
+        }
+        __syncthreads();
+    }
+    double* Dinv = Dall + (int64_t)b * BS * BS;          // D^{-1}, column-major 64 x 64
+    for (int e = threadIdx.x; e < BS * BS; e += 256) {
+        const int c = e / BS, r = e - c * BS;
+        Dinv[e] = (r < w && c < w) ? -sM[r][c] : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        maxp[b] = mp;
+        if (s_fail) atomicOr(status, DEV_NOT_SPD);
+    }
+}
+
+__global__ void __launch_bounds__(256) sweep_bl_write_kernel(int k0, const int32_t* __restrict__ msz,
+        const int64_t* __restrict__ off, double* __restrict__ Aall, const int64_t* __restrict__ qoff,
+        const double* __restrict__ Xall, const double* __restrict__ Dall)
+{
+    const int b = blockIdx.y;
+    const int m = msz[b];
+    if (k0 >= m) return;
+    const int w = min(BS, m - k0);
+    double* A = Aall + off[b];
+    const double* X = Xall + qoff[b];
+    const double* Dinv = Dall + (int64_t)b * BS * BS;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < (int64_t)m * w; e += (int64_t)gridDim.x * 256) {
+        const int t = (int)(e / m), i = (int)(e - (int64_t)t * m);
+        const int c = k0 + t;
+        if (i >= k0 + w) A[(int64_t)c * m + i] = X[(int64_t)t * m + i];          // S[i, K] below K
+        else if (i < k0) A[(int64_t)i * m + c] = X[(int64_t)t * m + i];          // S[K, i] left of K
+        else if (i - k0 >= t) A[(int64_t)c * m + i] = -Dinv[t * BS + (i - k0)];  // S_KK = -D^{-1}
+    }
+}
+
+}  // namespace
+
+size_t sweep_bl_plan(int nb, const std::vector<int64_t>& sizes, int max_m, std::vector<int64_t>& qoff,
+                     std::vector<std::vector<GemmProb>>& gx, std::vector<std::vector<GemmProb>>& gu,
+                     const std::vector<int64_t>& off)
+{
+    qoff.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) qoff[b + 1] = qoff[b] + (int64_t)BS * sizes[b];
+    const int steps = (max_m + BS - 1) / BS;
+    gx.assign(steps, {});
+    gu.assign(steps, {});
+    for (int q = 0; q < steps; ++q) {
+        const int k0 = q * BS;
+        for (int b = 0; b < nb; ++b) {
+            const int m = (int)sizes[b];
+            if (k0 >= m) continue;
+            const int w = std::min(BS, m - k0);
+            GemmProb g{};                                  // X = Q D^{-1}
+            g.M = m; g.N = w; g.K = w; g.ta = 1; g.tb = 0;
+            g.lda = BS; g.ldb = BS; g.ldc = m; g.ldc0 = m;
+            g.a_off = qoff[b]; g.b_off = (int64_t)b * BS * BS; g.c_off = qoff[b]; g.c0_off = 0;
+            g.alpha = 1.0; g.beta = 0.0;
+            gx[q].push_back(g);
+            GemmProb h{};                                  // S <- S - X Q^T, lower tiles
+            h.M = m; h.N = m; h.K = w; h.ta = 0; h.tb = 0;
+            h.lda = m; h.ldb = BS; h.ldc = m; h.ldc0 = m;
+            h.a_off = qoff[b]; h.b_off = qoff[b]; h.c_off = off[b]; h.c0_off = off[b];
+            h.alpha = -1.0; h.beta = 1.0; h.lower = 1;
+            gu[q].push_back(h);
+        }
+    }
+    return (size_t)qoff[nb];
+}
+
+cudaError_t launch_sweep_bl_panel(cudaStream_t st, int nb, int k0, int max_m, const int32_t* m, const int64_t* off,
+                                  const double* A, const int64_t* qoff, double* Q, double* D, double* maxp, int* status)
+{
+    if (nb <= 0 || max_m <= k0) return cudaSuccess;
+    count_launches(2);
+    sweep_bl_copy_kernel<<<dim3((unsigned)((max_m + BS - 1) / BS), (unsigned)nb), 256, 0, st>>>(k0, m, off, A, qoff, Q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sweep_bl_dinv_kernel<<<nb, 256, 0, st>>>(k0, m, qoff, Q, D, maxp, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_bl_write(cudaStream_t st, int nb, int k0, int max_m, const int32_t* m, const int64_t* off,
+                                  double* A, const int64_t* qoff, const double* X, const double* D)
+{
+    if (nb <= 0 || max_m <= k0) return cudaSuccess;
+    const int64_t work = (int64_t)(max_m - k0 < BS ? max_m - k0 : BS) * max_m;
+    const unsigned gx = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
+    count_launches(1);
+    sweep_bl_write_kernel<<<dim3(gx, (unsigned)nb), 256, 0, st>>>(k0, m, off, A, qoff, X, D);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

@@ -219,13 +219,92 @@ int run_gj(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& d
 // blocks are then partly swept and the caller rebuilds them for run_gj.  While op->defer_spd
 // is set the launch returns without waiting: the status word is read once after the whole
 // inverse phase, which is redone with Gauss-Jordan if any sweep found a block not SPD.
+// The sweep in panels of 64 with its rank-64 updates on the digit-slice GEMM (FP64).
+int run_sweep_bl(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, double* A,
+                 const std::vector<int64_t>& sizes, const std::vector<int64_t>& moff, int max_m, int cls, int level)
+{
+    std::vector<int64_t> qoff;
+    std::vector<std::vector<GemmProb>> gx, gu;
+    const size_t qn = sweep_bl_plan(nb, sizes, max_m, qoff, gx, gu, moff);
+    const int steps = (int)gx.size();
+    // every step's descriptors and exponent offsets in one array each
+    std::vector<GemmProb> ax, au;
+    std::vector<int64_t> ex, eu;
+    struct StepL { size_t px, pu, ex, eu; int64_t tx, tu, lx, lu; int nx, nu; };
+    std::vector<StepL> sl(steps);
+    int64_t max_lines = 1;
+    for (int q = 0; q < steps; ++q) {
+        std::vector<int64_t> eo;
+        StepL& z = sl[q];
+        z.px = ax.size(); z.ex = ex.size(); z.nx = (int)gx[q].size();
+        z.tx = gemm_oz_plan(gx[q], eo);
+        z.lx = eo.back();
+        ax.insert(ax.end(), gx[q].begin(), gx[q].end());
+        ex.insert(ex.end(), eo.begin(), eo.end());
+        z.pu = au.size(); z.eu = eu.size(); z.nu = (int)gu[q].size();
+        z.tu = gemm_oz_plan(gu[q], eo);
+        z.lu = eo.back();
+        au.insert(au.end(), gu[q].begin(), gu[q].end());
+        eu.insert(eu.end(), eo.begin(), eo.end());
+        max_lines = std::max(max_lines, std::max(z.lx, z.lu));
+    }
+    int rc;
+    if ((rc = upload(op->t_blq, qoff, st))) return rc;
+    if ((rc = upload(op->t_blgx, ax, st))) return rc;
+    if ((rc = upload(op->t_blgu, au, st))) return rc;
+    if ((rc = upload(op->t_blex, ex, st))) return rc;
+    if ((rc = upload(op->t_bleu, eu, st))) return rc;
+    RS_CUDA(op->t_blQ.alloc(sizeof(double) * (qn + 1)));
+    RS_CUDA(op->t_blX.alloc(sizeof(double) * (qn + 1)));
+    RS_CUDA(op->t_blD.alloc(sizeof(double) * 64 * 64 * (size_t)nb));
+    RS_CUDA(op->t_blmp.alloc(sizeof(double) * (size_t)nb));
+    RS_CUDA(op->t_ozx.alloc(sizeof(int) * (size_t)max_lines));
+    RS_CUDA(cudaMemsetAsync(op->t_blmp.p, 0, sizeof(double) * (size_t)nb, st));
+    double work = 0.0;
+    for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
+    ProfScope ps(op, cls, st, work, 2.0 * sizeof(double) * (double)moff[nb], level);
+    for (int q = 0; q < steps; ++q) {
+        const StepL& z = sl[q];
+        RS_CUDA(launch_sweep_bl_panel(st, nb, 64 * q, max_m, dm.as<int32_t>(), doff.as<int64_t>(), A,
+                                      op->t_blq.as<int64_t>(), op->t_blQ.as<double>(), op->t_blD.as<double>(),
+                                      op->t_blmp.as<double>(), op->d_status.as<int>()));
+        RS_CUDA(launch_gemm_oz(st, op->t_blgx.as<GemmProb>() + z.px, z.nx, z.tx, op->t_blex.as<int64_t>() + z.ex, z.lx,
+                               op->t_ozx.as<int>(), op->t_blQ.as<double>(), op->t_blD.as<double>(),
+                               op->t_blX.as<double>(), op->t_blX.as<double>()));
+        RS_CUDA(launch_gemm_oz(st, op->t_blgu.as<GemmProb>() + z.pu, z.nu, z.tu, op->t_bleu.as<int64_t>() + z.eu, z.lu,
+                               op->t_ozx.as<int>(), op->t_blX.as<double>(), op->t_blQ.as<double>(), A, A));
+        RS_CUDA(launch_sweep_bl_write(st, nb, 64 * q, max_m, dm.as<int32_t>(), doff.as<int64_t>(), A,
+                                      op->t_blq.as<int64_t>(), op->t_blX.as<double>(), op->t_blD.as<double>()));
+    }
+    RS_CUDA(launch_sweep_finish<double>(st, nb, dm.as<int32_t>(), doff.as<int64_t>(), A, max_m));
+    return RS_OK;
+}
+
 template <class T>
 int run_sweep(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const DevMem& doff, T* A,
               const std::vector<int64_t>& sizes, const std::vector<int64_t>& size_off, int max_m, int cls,
-              int level, bool* not_spd)
+              int level, bool* not_spd, const std::vector<int64_t>* moff = nullptr)
 {
     *not_spd = false;
     if (max_m <= 0) return RS_OK;
+    if constexpr (std::is_same<T, double>::value) {
+        if (moff && op->opts.gemm_form == 1 && !op->opts.per_box) {
+            int rc;
+            if ((rc = run_sweep_bl(op, st, nb, dm, doff, A, sizes, *moff, max_m, cls, level))) return rc;
+            if (op->defer_spd) return RS_OK;
+            RS_CUDA(cudaStreamSynchronize(st));
+            prof_flush(op);
+            int s = 0;
+            RS_CUDA(cudaMemcpy(&s, op->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+            if (s & DEV_NOT_SPD) {
+                RS_CUDA(cudaMemsetAsync(op->d_status.p, 0, sizeof(int), st));
+                op->stats.spd_fallbacks += 1;
+                *not_spd = true;
+                return RS_OK;
+            }
+            return check_status(op, st);
+        }
+    }
     if constexpr (is_cplx<T>::value) {
         return fail(RS_E_INVALID, "the symmetric sweep is for real kernels");
     } else {
@@ -788,7 +867,7 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
     bool redo = true;
     if (use_sweep(op)) {
         if ((rc = run_sweep<T>(op, st, nb, L.d_m, L.d_phi_off, L.d_Phi.as<T>(), L.m, L.act_off, L.max_m, cls_f, L.l,
-                               &redo)))
+                               &redo, &L.phi_off)))
             return rc;
         if (redo && (rc = assemble())) return rc;
     }
@@ -893,7 +972,7 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
     redo = true;
     if (use_sweep(op)) {
         if ((rc = run_sweep<T>(op, st, nb, d_k32, L.d_e_off, L.d_E.as<T>(), L.k, L.k_off, L.max_k, RS_PROF_INV_E,
-                               L.l, &redo)))
+                               L.l, &redo, &L.e_off)))
             return rc;
         if (redo && !p1.empty()) {   // E^{-1} again from W, all tiles (the sweep overwrote it)
             if (use_oz) {

@@ -57,6 +57,20 @@ int64_t gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff);
 cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const int64_t* eoff,
                            int64_t nlines, int* ex, const double* A, const double* B, double* C, const double* C0);
 
+// Blocked symmetric sweep (k_sweep_bl.cu), FP64: sweep_bl_plan lays out the panel buffers (qoff:
+// 64 m_b doubles per matrix, row-major; returns the total) and the two digit-GEMM lists of every step (gx:
+// X = Q D^{-1}; gu: S <- S - X Q^T), off = the matrices' offsets; per step one panel launch,
+// the two GEMMs, one write launch; launch_sweep_finish then negates and mirrors.
+size_t sweep_bl_plan(int nb, const std::vector<int64_t>& sizes, int max_m, std::vector<int64_t>& qoff,
+                     std::vector<std::vector<GemmProb>>& gx, std::vector<std::vector<GemmProb>>& gu,
+                     const std::vector<int64_t>& off);
+cudaError_t launch_sweep_bl_panel(cudaStream_t st, int nb, int k0, int max_m, const int32_t* m, const int64_t* off,
+                                  const double* A, const int64_t* qoff, double* Q, double* D, double* maxp, int* status);
+cudaError_t launch_sweep_bl_write(cudaStream_t st, int nb, int k0, int max_m, const int32_t* m, const int64_t* off,
+                                  double* A, const int64_t* qoff, const double* X, const double* D);
+template <class T>
+cudaError_t launch_sweep_finish(cudaStream_t st, int nb, const int32_t* m, const int64_t* off, T* A, int max_m);
+
 // Batched matrix-vector(s) descriptor: y = alpha * op(A) x + beta * y, A column-major
 // (rows x cols, ld), x and y point-major (entry p of RHS c at p * nrhs + c); x_off and y_off
 // count points (rows), so one descriptor serves every nrhs.
