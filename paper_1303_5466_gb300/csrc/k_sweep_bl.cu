@@ -5,8 +5,9 @@
 //     S_KK <- -D^{-1},  S_OK <- S_OK D^{-1},  S_KO <- D^{-1} S_KO,  S_OO <- S_OO - S_OK D^{-1} S_KO,
 // so with Q = S[:, K] (the old panel, both triangles) and X = Q D^{-1}, one step is
 //   1. (copy kernel) Q, row-major, in 64 x 64 tiles; (one CTA per matrix) D^{-1} by the element
-//      sweep of the 64 x 64 block D in shared memory, FP64, with the pivot test of k_sweep.cu (a
-//      pivot not above 1e3 unit roundoff times the largest earlier one sets DEV_NOT_SPD);
+//      sweep of the lower triangle of the 64 x 64 block D in shared memory, FP64, with the pivot
+//      test of k_sweep.cu (a pivot not above 1e3 unit roundoff times the largest earlier one sets
+//      DEV_NOT_SPD);
 //   2. X = Q D^{-1} and S <- S - X Q^T on the tiles touching the lower triangle (both on the
 //      digit-slice GEMM: the m^3 flops of the inverse as 64-deep products);
 //   3. (write kernel) the rows and columns of K, which step 2 left meaningless: S[i, K] = X[i, :]
@@ -65,13 +66,16 @@ __global__ void __launch_bounds__(256) sweep_bl_copy_kernel(int k0, const int32_
     }
 }
 
-// D^{-1} of the panel's diagonal block D = Q[k0 .. k0 + w) by the element sweep in shared memory,
-// FP64, with the pivot test of k_sweep.cu; one CTA per matrix.
+// D^{-1} of the panel's diagonal block D = Q[k0 .. k0 + w) by the element sweep of its lower
+// triangle in shared memory, FP64, with the pivot test of k_sweep.cu; one CTA per matrix.  Step t:
+// 64 threads take the pivot column c_r = D(r, t) and u_r = c_r / D(t, t); then every lower entry
+// (r, s) off row and column t becomes D(r, s) - u_r c_s in place, and row / column t become u.
 __global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_t* __restrict__ msz,
         const int64_t* __restrict__ qoff, const double* __restrict__ Qall, double* __restrict__ Dall,
         double* __restrict__ maxp, int* __restrict__ status)
 {
     __shared__ double sM[BS][BS + 1];
+    __shared__ double s_c[BS], s_u[BS];
     __shared__ int s_fail;
     const int b = blockIdx.x;
     const int m = msz[b];
@@ -85,33 +89,46 @@ __global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_
     if (threadIdx.x == 0) s_fail = 0;
     double mp = maxp[b];
     __syncthreads();
-    // element sweep of D: sM <- -D^{-1} (the padding stays the identity)
+    // the lower entries of this thread: e = tid + 256 u over the 2080 of the 64 x 64 triangle
+    constexpr int NL = BS * (BS + 1) / 2, PER = (NL + 255) / 256;
+    int er[PER], ec[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        int r = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+        while (r * (r + 1) / 2 > e) --r;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        er[u] = e < NL ? r : -1;
+        ec[u] = e - r * (r + 1) / 2;
+    }
     for (int t = 0; t < w; ++t) {
         const double p = sM[t][t];
         if (threadIdx.x == 0 && (!(p > 1e3 * 0.5 * DBL_EPSILON * mp) || !isfinite(p))) s_fail = 1;
         mp = fmax(mp, p);
-        const double pinv = 1.0 / p;
-        double nv[BS * BS / 256];
-#pragma unroll
-        for (int u = 0; u < BS * BS / 256; ++u) {
-            const int e = threadIdx.x + 256 * u, r = e / BS, c = e - r * BS;
-            if (r == t && c == t) nv[u] = -pinv;
-            else if (r == t) nv[u] = sM[t][c] * pinv;
-            else if (c == t) nv[u] = sM[r][t] * pinv;
-            else nv[u] = fma(-sM[r][t] * pinv, sM[t][c], sM[r][c]);
+        if (threadIdx.x < BS) {
+            const int r = threadIdx.x;
+            const double c = r >= t ? sM[r][t] : sM[t][r];
+            s_c[r] = c;
+            s_u[r] = c * (1.0 / p);
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < BS * BS / 256; ++u) {
-            const int e = threadIdx.x + 256 * u, r = e / BS, c = e - r * BS;
-            sM[r][c] = nv[u];
+        for (int u = 0; u < PER; ++u) {
+            const int r = er[u], c = ec[u];
+            if (r < 0) continue;
+            double v;
+            if (r == t && c == t) v = -1.0 / p;
+            else if (r == t) v = s_u[c];
+            else if (c == t) v = s_u[r];
+            else v = fma(-s_u[r], s_c[c], sM[r][c]);
+            sM[r][c] = v;
         }
         __syncthreads();
     }
-    double* Dinv = Dall + (int64_t)b * BS * BS;          // D^{-1}, column-major 64 x 64
+    double* Dinv = Dall + (int64_t)b * BS * BS;          // D^{-1}, column-major 64 x 64, both triangles
     for (int e = threadIdx.x; e < BS * BS; e += 256) {
         const int c = e / BS, r = e - c * BS;
-        Dinv[e] = (r < w && c < w) ? -sM[r][c] : 0.0;
+        Dinv[e] = (r < w && c < w) ? -(r >= c ? sM[r][c] : sM[c][r]) : 0.0;
     }
     if (threadIdx.x == 0) {
         maxp[b] = mp;
