@@ -56,20 +56,24 @@ __global__ void __launch_bounds__(256) oz_exp_kernel(const GemmProb* __restrict_
     }
     const GemmProb P = probs[lo];
     const int idx = (int)(w - eoff[lo]);
-    double mx = 0.0;
+    // the largest |x| as the largest bit pattern without the sign (the same order for x >= 0),
+    // in integer operations: this GPU's FP64 pipe is its scarcest
+    constexpr unsigned long long MAG = 0x7fffffffffffffffull;
+    unsigned long long mx = 0;
     if (idx < P.M) {
         const double* A = Ab + P.a_off;
-        for (int k = lane; k < P.K; k += 32) mx = fmax(mx, fabs(oz_a(P, A, idx, k)));
+        for (int k = lane; k < P.K; k += 32) mx = max(mx, (unsigned long long)__double_as_longlong(oz_a(P, A, idx, k)) & MAG);
     } else {
         const double* B = Bb + P.b_off;
-        for (int k = lane; k < P.K; k += 32) mx = fmax(mx, fabs(oz_b(P, B, k, idx - P.M)));
+        for (int k = lane; k < P.K; k += 32)
+            mx = max(mx, (unsigned long long)__double_as_longlong(oz_b(P, B, k, idx - P.M)) & MAG);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) {
-        int e = 0;
-        if (mx > 0.0) frexp(mx, &e);
-        ex[w] = e;
+        // max |x| = 1.f 2^(ef - 1023) < 2^(ef - 1022); subnormal lines count as zero digits
+        const int ef = (int)(mx >> 52);
+        ex[w] = mx == 0 ? 0 : (ef == 0 ? -1021 : ef - 1022);
     }
 }
 
@@ -105,6 +109,35 @@ __device__ __forceinline__ void oz_split2(double x0, double x1, int E, uint32_t*
     const unsigned long long Z0 = oz_fixed(x0, E, n0), Z1 = oz_fixed(x1, E, n1);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) out[s * stride_words] = oz_digit(Z0, n0, s) | (oz_digit(Z1, n1, s) << 16);
+}
+
+// (wa 2^28 + wb) 2^e2, rounded to nearest (ties to even) once, in integer operations.
+__device__ __forceinline__ double oz_round(long long wa, long long wb, int e2)
+{
+    const __int128 T = (__int128)wa * ((__int128)1 << 28) + (__int128)wb;
+    const bool neg = T < 0;
+    const unsigned __int128 M = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+    if (M == 0) return 0.0;
+    const unsigned long long hi = (unsigned long long)(M >> 64), lo = (unsigned long long)M;
+    int sh = (hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo)) - 53;
+    unsigned long long q;
+    if (sh > 0) {
+        q = (unsigned long long)(M >> sh);
+        const unsigned __int128 rem = M - ((unsigned __int128)q << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) {
+            if (++q == (1ull << 53)) {
+                q >>= 1;
+                ++sh;
+            }
+        }
+    } else {
+        q = (unsigned long long)M << (-sh);
+    }
+    const int ef = sh + e2 + 1075;                   // value = q 2^(sh + e2), 2^52 <= q < 2^53
+    if (ef <= 0 || ef >= 2047) return ldexp(fma((double)wb, 0x1p-28, (double)wa), e2 + 28);
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)ef << 52) |
+                                            (q & ((1ull << 52) - 1))));
 }
 
 __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
@@ -226,10 +259,17 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
             const int li = wm + g + (e >= 2 ? 8 : 0), lj = wn + 8 * n + 2 * q + (e & 1);
             const int gi = row0 + li, gj = col0 + lj;
             if (gi >= P.M || gj >= P.N) continue;
-            const double v = fma((double)WB[n][e], 0x1p-28, (double)WA[n][e]);
-            const double val = ldexp(v, eA[li] + eB[lj] - 35);
-            const double c0 = (P.beta == 0.0) ? 0.0 : C0b[P.c0_off + (int64_t)gj * P.ldc0 + gi];
-            C[(int64_t)gj * P.ldc + gi] = P.alpha * val + P.beta * c0;
+            // the one FP64 operation per entry is the update's addition (alpha = +-1, beta = 0 or 1
+            // in this library's products)
+            double val = oz_round(WA[n][e], WB[n][e], eA[li] + eB[lj] - 63);
+            if (P.alpha == -1.0) val = -val;
+            else if (P.alpha != 1.0) val *= P.alpha;
+            double out = val;
+            if (P.beta != 0.0) {
+                const double c0 = C0b[P.c0_off + (int64_t)gj * P.ldc0 + gi];
+                out = P.beta == 1.0 ? c0 + val : fma(P.beta, c0, val);
+            }
+            C[(int64_t)gj * P.ldc + gi] = out;
         }
 }
 
