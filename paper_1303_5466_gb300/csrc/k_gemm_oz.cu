@@ -15,7 +15,8 @@
 //
 // Launch: one warp per row of A and per column of B finds its exponent first; then one CTA of
 // 8 warps per 64 x 32 tile of C, the warps 16 x 16 each (two m16n8k16 tiles), K in stages of
-// 32 digits staged in shared memory (split on the fly from the FP64 operands).
+// 32 digits staged in shared memory, split from FP64 tiles that cp.async brings in during the
+// previous stage's products.
 #include <algorithm>
 #include <vector>
 
@@ -205,25 +206,48 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
                 WB[n][e] += b;
             }
     };
+    // the FP64 tiles of the next stage are copied to shared memory asynchronously (cp.async, zero
+    // fill outside the matrices) while the current stage's products run
+    double* rawA = reinterpret_cast<double*>(oz_smem + sizeof(__nv_bfloat16) * OZ_S * (OZ_BM + OZ_BN) * OZ_LD);
+    double* rawB = rawA + OZ_BM * OZ_BK;
+    auto issue = [&](int k0) {
+        for (int e = threadIdx.x; e < OZ_BM * OZ_BK; e += OZ_NT) {
+            const int i = P.ta ? e / OZ_BK : e % OZ_BM, kk = P.ta ? e % OZ_BK : e / OZ_BM;
+            const int gi = row0 + i, gk = k0 + kk;
+            const bool ok = gi < P.M && gk < P.K;
+            const double* src = ok ? (P.ta ? A + (int64_t)gi * P.lda + gk : A + (int64_t)gk * P.lda + gi) : A;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(rawA + e);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0));
+        }
+        for (int e = threadIdx.x; e < OZ_BN * OZ_BK; e += OZ_NT) {
+            const int j = P.tb ? e % OZ_BN : e / OZ_BK, kk = P.tb ? e / OZ_BN : e % OZ_BK;
+            const int gj = col0 + j, gk = k0 + kk;
+            const bool ok = gj < P.N && gk < P.K;
+            const double* src = ok ? (P.tb ? B + (int64_t)gk * P.ldb + gj : B + (int64_t)gj * P.ldb + gk) : B;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(rawB + e);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0));
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    // element (i, kk) of the raw tiles, in the order they were copied
+    auto rawa = [&](int i, int kk) { return P.ta ? rawA[i * OZ_BK + kk] : rawA[kk * OZ_BM + i]; };
+    auto rawb = [&](int j, int kk) { return P.tb ? rawB[kk * OZ_BN + j] : rawB[j * OZ_BK + kk]; };
     zeroS();
-    __syncthreads();
+    issue(0);
     for (int k0 = 0; k0 < P.K; k0 += OZ_BK) {
-        // stage the digits of the A (64 x 32) and B (32 x 32) tiles, two entries of a row per thread
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();                 // this stage's tiles landed; the last stage's products are done
+        // the digits of the A (64 x 32) and B (32 x 32) tiles, two entries of a row per thread
         for (int e = threadIdx.x; e < OZ_BM * OZ_BK / 2; e += OZ_NT) {
             const int i = P.ta ? e / (OZ_BK / 2) : e % OZ_BM, kp = P.ta ? e % (OZ_BK / 2) : e / OZ_BM;
-            const int gi = row0 + i, gk = k0 + 2 * kp;
-            const double x0 = (gi < P.M && gk < P.K) ? oz_a(P, A, gi, gk) : 0.0;
-            const double x1 = (gi < P.M && gk + 1 < P.K) ? oz_a(P, A, gi, gk + 1) : 0.0;
-            oz_split2(x0, x1, eA[i], (uint32_t*)&As[0][i][2 * kp], OZ_BM * OZ_LD / 2);
+            oz_split2(rawa(i, 2 * kp), rawa(i, 2 * kp + 1), eA[i], (uint32_t*)&As[0][i][2 * kp], OZ_BM * OZ_LD / 2);
         }
         for (int e = threadIdx.x; e < OZ_BN * OZ_BK / 2; e += OZ_NT) {
             const int j = P.tb ? e % OZ_BN : e / (OZ_BK / 2), kp = P.tb ? e / OZ_BN : e % (OZ_BK / 2);
-            const int gj = col0 + j, gk = k0 + 2 * kp;
-            const double x0 = (gj < P.N && gk < P.K) ? oz_b(P, B, gk, gj) : 0.0;
-            const double x1 = (gj < P.N && gk + 1 < P.K) ? oz_b(P, B, gk + 1, gj) : 0.0;
-            oz_split2(x0, x1, eB[j], (uint32_t*)&Bs[0][j][2 * kp], OZ_BN * OZ_LD / 2);
+            oz_split2(rawb(j, 2 * kp), rawb(j, 2 * kp + 1), eB[j], (uint32_t*)&Bs[0][j][2 * kp], OZ_BN * OZ_LD / 2);
         }
         __syncthreads();
+        if (k0 + OZ_BK < P.K) issue(k0 + OZ_BK);
 #pragma unroll
         for (int ks = 0; ks < OZ_BK; ks += 16) {
 #pragma unroll
@@ -244,7 +268,6 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
                 }
             }
         }
-        __syncthreads();
         if ((k0 + OZ_BK) % OZ_CHUNK == 0 || k0 + OZ_BK >= P.K) {
             flush();
             zeroS();
@@ -298,7 +321,8 @@ cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, int64
     oz_exp_kernel<<<(unsigned)((nlines * 32 + 255) / 256), 256, 0, st>>>(probs, np, eoff, nlines, A, B, ex);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    constexpr int shm = (int)(sizeof(__nv_bfloat16) * OZ_S * (OZ_BM + OZ_BN) * OZ_LD);
+    constexpr int shm = (int)(sizeof(__nv_bfloat16) * OZ_S * (OZ_BM + OZ_BN) * OZ_LD +
+                              sizeof(double) * (OZ_BM + OZ_BN) * OZ_BK);
     e = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
     if (e != cudaSuccess) return e;
     gemm_oz_kernel<<<(unsigned)tiles, OZ_NT, shm, st>>>(probs, np, eoff, ex, A, B, C, C0);
