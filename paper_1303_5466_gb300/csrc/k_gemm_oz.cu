@@ -28,10 +28,14 @@ namespace rs {
 
 namespace {
 
-constexpr int OZ_BM = 64, OZ_BN = 32, OZ_BK = 32, OZ_NT = 256;
+constexpr int OZ_BM = 64, OZ_BN = 32, OZ_BK = 16, OZ_NT = 256;
 constexpr int OZ_S = 8;               // digit slices per entry
 constexpr int OZ_CHUNK = 128;         // K per exact FP32 level sum
-constexpr int OZ_LD = OZ_BK + 8;      // padded row of a slice tile (bf16), conflict-free fragments
+constexpr int OZ_KP = 32;             // a digit line's K, padded to a multiple of this
+constexpr int OZ_LD = OZ_BK + 8;      // padded row of a slice tile (bf16): 48 B, conflict-free fragments
+constexpr int OZ_BUF = OZ_S * (OZ_BM + OZ_BN) * OZ_LD;   // bf16 of one stage buffer
+
+__host__ __device__ inline int oz_kp(int K) { return (K + OZ_KP - 1) / OZ_KP * OZ_KP; }
 
 __device__ __forceinline__ double oz_a(const GemmProb& P, const double* A, int i, int k)
 {
@@ -40,42 +44,6 @@ __device__ __forceinline__ double oz_a(const GemmProb& P, const double* A, int i
 __device__ __forceinline__ double oz_b(const GemmProb& P, const double* B, int k, int j)
 {
     return P.tb ? B[(int64_t)k * P.ldb + j] : B[(int64_t)j * P.ldb + k];
-}
-
-// Exponent E of every row of A and column of B: max |x| < 2^E (0 for an all-zero line).
-__global__ void __launch_bounds__(256) oz_exp_kernel(const GemmProb* __restrict__ probs, int np,
-        const int64_t* __restrict__ eoff, int64_t nlines, const double* __restrict__ Ab,
-        const double* __restrict__ Bb, int* __restrict__ ex)
-{
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= nlines) return;
-    int lo = 0, hi = np - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (eoff[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    const GemmProb P = probs[lo];
-    const int idx = (int)(w - eoff[lo]);
-    // the largest |x| as the largest bit pattern without the sign (the same order for x >= 0),
-    // in integer operations: this GPU's FP64 pipe is its scarcest
-    constexpr unsigned long long MAG = 0x7fffffffffffffffull;
-    unsigned long long mx = 0;
-    if (idx < P.M) {
-        const double* A = Ab + P.a_off;
-        for (int k = lane; k < P.K; k += 32) mx = max(mx, (unsigned long long)__double_as_longlong(oz_a(P, A, idx, k)) & MAG);
-    } else {
-        const double* B = Bb + P.b_off;
-        for (int k = lane; k < P.K; k += 32)
-            mx = max(mx, (unsigned long long)__double_as_longlong(oz_b(P, B, k, idx - P.M)) & MAG);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) {
-        // max |x| = 1.f 2^(ef - 1023) < 2^(ef - 1022); subnormal lines count as zero digits
-        const int ef = (int)(mx >> 52);
-        ex[w] = mx == 0 ? 0 : (ef == 0 ? -1021 : ef - 1022);
-    }
 }
 
 // |x| 2^(56-E) truncated to an integer Z < 2^56 (|x| < 2^E), and the sign of x.
@@ -149,13 +117,50 @@ __device__ __forceinline__ void oz_mma(float (&c)[4], const uint32_t (&a)[4], ui
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// One warp per line (a row of A or a column of B): its exponent E (max |x| < 2^E, 0 for an
+// all-zero line; in integer operations, this GPU's FP64 pipe being its scarcest), then the
+// digits of its K entries (zero up to the padded length), slice-major: line base + s Kp + k.
+// eoff[p] is problem p's first line, eoff[np + 1 + p] its first digit.
+__global__ void __launch_bounds__(256) oz_split_kernel(const GemmProb* __restrict__ probs, int np,
+        const int64_t* __restrict__ eoff, int64_t nlines, const double* __restrict__ Ab,
+        const double* __restrict__ Bb, int* __restrict__ ex, __nv_bfloat16* __restrict__ dig)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nlines) return;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (eoff[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const GemmProb P = probs[lo];
+    const int idx = (int)(w - eoff[lo]);
+    const bool isA = idx < P.M;
+    const double* A = Ab + P.a_off;
+    const double* B = Bb + P.b_off;
+    auto val = [&](int k) { return isA ? oz_a(P, A, idx, k) : oz_b(P, B, k, idx - P.M); };
+    constexpr unsigned long long MAG = 0x7fffffffffffffffull;
+    unsigned long long mx = 0;
+    for (int k = lane; k < P.K; k += 32) mx = max(mx, (unsigned long long)__double_as_longlong(val(k)) & MAG);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // max |x| = 1.f 2^(ef - 1023) < 2^(ef - 1022); subnormal lines count as zero digits
+    const int ef = (int)(mx >> 52);
+    const int E = mx == 0 ? 0 : (ef == 0 ? -1021 : ef - 1022);
+    if (lane == 0) ex[w] = E;
+    const int Kp = oz_kp(P.K);
+    uint32_t* out = (uint32_t*)(dig + eoff[np + 1 + lo] + (int64_t)idx * OZ_S * Kp);
+    for (int k = 2 * lane; k < Kp; k += 64) {
+        const double x0 = k < P.K ? val(k) : 0.0, x1 = k + 1 < P.K ? val(k + 1) : 0.0;
+        oz_split2(x0, x1, E, out + k / 2, Kp / 2);
+    }
+}
+
 __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __restrict__ probs, int np,
-        const int64_t* __restrict__ eoff, const int* __restrict__ ex, const double* __restrict__ Ab,
-        const double* __restrict__ Bb, double* Cb, const double* C0b)
+        const int64_t* __restrict__ eoff, const int* __restrict__ ex, const __nv_bfloat16* __restrict__ dig,
+        double* Cb, const double* C0b)
 {
     extern __shared__ __align__(16) unsigned char oz_smem[];
-    auto As = reinterpret_cast<__nv_bfloat16 (*)[OZ_BM][OZ_LD]>(oz_smem);
-    auto Bs = reinterpret_cast<__nv_bfloat16 (*)[OZ_BN][OZ_LD]>(oz_smem + sizeof(__nv_bfloat16) * OZ_S * OZ_BM * OZ_LD);
     __shared__ int eA[OZ_BM], eB[OZ_BN];
     const int64_t t = blockIdx.x;
     int lo = 0, hi = np - 1;
@@ -168,8 +173,9 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
     const int tm = (int)(lt % P.tiles_m), tn = (int)(lt / P.tiles_m);
     const int row0 = tm * OZ_BM, col0 = tn * OZ_BN;
     if (P.lower && col0 > row0 + OZ_BM - 1) return;          // wholly above the diagonal
-    const double* A = Ab + P.a_off;
-    const double* B = Bb + P.b_off;
+    const int Kp = oz_kp(P.K);
+    const __nv_bfloat16* digA = dig + eoff[np + 1 + lo];                  // line r: digA + r 8 Kp
+    const __nv_bfloat16* digB = digA + (int64_t)P.M * OZ_S * Kp;
     const int* exA = ex + eoff[lo];
     const int* exB = exA + P.M;
     for (int e = threadIdx.x; e < OZ_BM; e += OZ_NT) eA[e] = row0 + e < P.M ? exA[row0 + e] : 0;
@@ -206,48 +212,40 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
                 WB[n][e] += b;
             }
     };
-    // the FP64 tiles of the next stage are copied to shared memory asynchronously (cp.async, zero
-    // fill outside the matrices) while the current stage's products run
-    double* rawA = reinterpret_cast<double*>(oz_smem + sizeof(__nv_bfloat16) * OZ_S * (OZ_BM + OZ_BN) * OZ_LD);
-    double* rawB = rawA + OZ_BM * OZ_BK;
-    auto issue = [&](int k0) {
-        for (int e = threadIdx.x; e < OZ_BM * OZ_BK; e += OZ_NT) {
-            const int i = P.ta ? e / OZ_BK : e % OZ_BM, kk = P.ta ? e % OZ_BK : e / OZ_BM;
-            const int gi = row0 + i, gk = k0 + kk;
-            const bool ok = gi < P.M && gk < P.K;
-            const double* src = ok ? (P.ta ? A + (int64_t)gi * P.lda + gk : A + (int64_t)gk * P.lda + gi) : A;
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(rawA + e);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0));
-        }
-        for (int e = threadIdx.x; e < OZ_BN * OZ_BK; e += OZ_NT) {
-            const int j = P.tb ? e % OZ_BN : e / OZ_BK, kk = P.tb ? e / OZ_BN : e % OZ_BK;
-            const int gj = col0 + j, gk = k0 + kk;
-            const bool ok = gj < P.N && gk < P.K;
-            const double* src = ok ? (P.tb ? B + (int64_t)gk * P.ldb + gj : B + (int64_t)gj * P.ldb + gk) : B;
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(rawB + e);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0));
+    // the digit tiles of stage st (16 k of 8 slices: 64 rows of A, 32 columns of B) go to buffer
+    // st & 1 by cp.async, two 16-byte pieces per slice and line, zero fill outside the matrices;
+    // stage st + 1 is in flight while stage st's products run
+    auto issue = [&](int st, int buf) {
+        const int k0 = st * OZ_BK;
+        __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(oz_smem) + buf * OZ_BUF;
+        for (int e = threadIdx.x; e < OZ_S * (OZ_BM + OZ_BN) * 2; e += OZ_NT) {
+            const int sl = e / ((OZ_BM + OZ_BN) * 2), rem = e - sl * (OZ_BM + OZ_BN) * 2;
+            const int line = rem >> 1, c = rem & 1;
+            const bool isA = line < OZ_BM;
+            const int gl = isA ? row0 + line : col0 + line - OZ_BM;
+            const bool ok = gl < (isA ? P.M : P.N);
+            const __nv_bfloat16* src = (isA ? digA : digB) + (ok ? (int64_t)gl * OZ_S * Kp + sl * Kp + k0 + 8 * c : 0);
+            __nv_bfloat16* dst = sb + (isA ? (sl * OZ_BM + line) : (OZ_S * OZ_BM + sl * OZ_BN + line - OZ_BM)) * OZ_LD + 8 * c;
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0));
         }
         asm volatile("cp.async.commit_group;");
     };
-    // element (i, kk) of the raw tiles, in the order they were copied
-    auto rawa = [&](int i, int kk) { return P.ta ? rawA[i * OZ_BK + kk] : rawA[kk * OZ_BM + i]; };
-    auto rawb = [&](int j, int kk) { return P.tb ? rawB[kk * OZ_BN + j] : rawB[j * OZ_BK + kk]; };
     zeroS();
-    issue(0);
-    for (int k0 = 0; k0 < P.K; k0 += OZ_BK) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncthreads();                 // this stage's tiles landed; the last stage's products are done
-        // the digits of the A (64 x 32) and B (32 x 32) tiles, two entries of a row per thread
-        for (int e = threadIdx.x; e < OZ_BM * OZ_BK / 2; e += OZ_NT) {
-            const int i = P.ta ? e / (OZ_BK / 2) : e % OZ_BM, kp = P.ta ? e % (OZ_BK / 2) : e / OZ_BM;
-            oz_split2(rawa(i, 2 * kp), rawa(i, 2 * kp + 1), eA[i], (uint32_t*)&As[0][i][2 * kp], OZ_BM * OZ_LD / 2);
+    const int nst = (P.K + OZ_BK - 1) / OZ_BK;
+    issue(0, 0);
+    for (int st = 0; st < nst; ++st) {
+        const int k0 = st * OZ_BK;
+        if (st + 1 < nst) {
+            issue(st + 1, (st + 1) & 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        for (int e = threadIdx.x; e < OZ_BN * OZ_BK / 2; e += OZ_NT) {
-            const int j = P.tb ? e % OZ_BN : e / (OZ_BK / 2), kp = P.tb ? e / OZ_BN : e % (OZ_BK / 2);
-            oz_split2(rawb(j, 2 * kp), rawb(j, 2 * kp + 1), eB[j], (uint32_t*)&Bs[0][j][2 * kp], OZ_BN * OZ_LD / 2);
-        }
-        __syncthreads();
-        if (k0 + OZ_BK < P.K) issue(k0 + OZ_BK);
+        __syncthreads();                 // stage st landed in every thread's view
+        auto As = reinterpret_cast<__nv_bfloat16 (*)[OZ_BM][OZ_LD]>(oz_smem + sizeof(__nv_bfloat16) * (st & 1) * OZ_BUF);
+        auto Bs = reinterpret_cast<__nv_bfloat16 (*)[OZ_BN][OZ_LD]>(oz_smem + sizeof(__nv_bfloat16) *
+                                                                    ((st & 1) * OZ_BUF + OZ_S * OZ_BM * OZ_LD));
 #pragma unroll
         for (int ks = 0; ks < OZ_BK; ks += 16) {
 #pragma unroll
@@ -268,6 +266,7 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
                 }
             }
         }
+        __syncthreads();                 // buffer st & 1 is free for stage st + 2
         if ((k0 + OZ_BK) % OZ_CHUNK == 0 || k0 + OZ_BK >= P.K) {
             flush();
             zeroS();
@@ -298,34 +297,38 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
 
 }  // namespace
 
-int64_t gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff)
+OzPlan gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff)
 {
-    int64_t tiles = 0;
-    eoff.assign(probs.size() + 1, 0);
-    for (size_t p = 0; p < probs.size(); ++p) {
+    const size_t np = probs.size();
+    OzPlan pl{0, 0, 0};
+    eoff.assign(2 * (np + 1), 0);
+    for (size_t p = 0; p < np; ++p) {
         GemmProb& g = probs[p];
         g.tiles_m = (g.M + OZ_BM - 1) / OZ_BM;
         g.tiles_n = (g.N + OZ_BN - 1) / OZ_BN;
-        g.tile0 = tiles;
-        tiles += (int64_t)g.tiles_m * g.tiles_n;
+        g.tile0 = pl.tiles;
+        pl.tiles += (int64_t)g.tiles_m * g.tiles_n;
         eoff[p + 1] = eoff[p] + g.M + g.N;
+        eoff[np + 2 + p] = eoff[np + 1 + p] + (int64_t)(g.M + g.N) * OZ_S * oz_kp(g.K);
     }
-    return tiles;
+    pl.lines = eoff[np];
+    pl.digits = eoff[2 * np + 1];
+    return pl;
 }
 
-cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const int64_t* eoff,
-                           int64_t nlines, int* ex, const double* A, const double* B, double* C, const double* C0)
+cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, const OzPlan& pl, const int64_t* eoff,
+                           int* ex, void* digits, const double* A, const double* B, double* C, const double* C0)
 {
-    if (np <= 0 || tiles <= 0) return cudaSuccess;
+    if (np <= 0 || pl.tiles <= 0) return cudaSuccess;
     count_launches(2);
-    oz_exp_kernel<<<(unsigned)((nlines * 32 + 255) / 256), 256, 0, st>>>(probs, np, eoff, nlines, A, B, ex);
+    __nv_bfloat16* dig = (__nv_bfloat16*)digits;
+    oz_split_kernel<<<(unsigned)((pl.lines * 32 + 255) / 256), 256, 0, st>>>(probs, np, eoff, pl.lines, A, B, ex, dig);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    constexpr int shm = (int)(sizeof(__nv_bfloat16) * OZ_S * (OZ_BM + OZ_BN) * OZ_LD +
-                              sizeof(double) * (OZ_BM + OZ_BN) * OZ_BK);
+    constexpr int shm = (int)(sizeof(__nv_bfloat16) * 2 * OZ_BUF);
     e = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
     if (e != cudaSuccess) return e;
-    gemm_oz_kernel<<<(unsigned)tiles, OZ_NT, shm, st>>>(probs, np, eoff, ex, A, B, C, C0);
+    gemm_oz_kernel<<<(unsigned)pl.tiles, OZ_NT, shm, st>>>(probs, np, eoff, ex, dig, C, C0);
     return cudaGetLastError();
 }
 

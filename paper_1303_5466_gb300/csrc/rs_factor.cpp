@@ -230,23 +230,22 @@ int run_sweep_bl(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const Dev
     // every step's descriptors and exponent offsets in one array each
     std::vector<GemmProb> ax, au;
     std::vector<int64_t> ex, eu;
-    struct StepL { size_t px, pu, ex, eu; int64_t tx, tu, lx, lu; int nx, nu; };
+    struct StepL { size_t px, pu, ex, eu; OzPlan x, u; int nx, nu; };
     std::vector<StepL> sl(steps);
-    int64_t max_lines = 1;
+    int64_t max_lines = 1, max_digits = 1;
     for (int q = 0; q < steps; ++q) {
         std::vector<int64_t> eo;
         StepL& z = sl[q];
         z.px = ax.size(); z.ex = ex.size(); z.nx = (int)gx[q].size();
-        z.tx = gemm_oz_plan(gx[q], eo);
-        z.lx = eo.back();
+        z.x = gemm_oz_plan(gx[q], eo);
         ax.insert(ax.end(), gx[q].begin(), gx[q].end());
         ex.insert(ex.end(), eo.begin(), eo.end());
         z.pu = au.size(); z.eu = eu.size(); z.nu = (int)gu[q].size();
-        z.tu = gemm_oz_plan(gu[q], eo);
-        z.lu = eo.back();
+        z.u = gemm_oz_plan(gu[q], eo);
         au.insert(au.end(), gu[q].begin(), gu[q].end());
         eu.insert(eu.end(), eo.begin(), eo.end());
-        max_lines = std::max(max_lines, std::max(z.lx, z.lu));
+        max_lines = std::max(max_lines, std::max(z.x.lines, z.u.lines));
+        max_digits = std::max(max_digits, std::max(z.x.digits, z.u.digits));
     }
     int rc;
     if ((rc = upload(op->t_blq, qoff, st))) return rc;
@@ -259,6 +258,7 @@ int run_sweep_bl(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const Dev
     RS_CUDA(op->t_blD.alloc(sizeof(double) * 64 * 64 * (size_t)nb));
     RS_CUDA(op->t_blmp.alloc(sizeof(double) * (size_t)nb));
     RS_CUDA(op->t_ozx.alloc(sizeof(int) * (size_t)max_lines));
+    RS_CUDA(op->t_ozd.alloc(2 * (size_t)(max_digits + 8)));
     RS_CUDA(cudaMemsetAsync(op->t_blmp.p, 0, sizeof(double) * (size_t)nb, st));
     double work = 0.0;
     for (int b = 0; b < nb; ++b) work += (double)sizes[b] * (double)sizes[b] * (double)sizes[b];
@@ -268,11 +268,12 @@ int run_sweep_bl(rs_op* op, cudaStream_t st, int nb, const DevMem& dm, const Dev
         RS_CUDA(launch_sweep_bl_panel(st, nb, 64 * q, max_m, dm.as<int32_t>(), doff.as<int64_t>(), A,
                                       op->t_blq.as<int64_t>(), op->t_blQ.as<double>(), op->t_blD.as<double>(),
                                       op->t_blmp.as<double>(), op->d_status.as<int>()));
-        RS_CUDA(launch_gemm_oz(st, op->t_blgx.as<GemmProb>() + z.px, z.nx, z.tx, op->t_blex.as<int64_t>() + z.ex, z.lx,
-                               op->t_ozx.as<int>(), op->t_blQ.as<double>(), op->t_blD.as<double>(),
+        RS_CUDA(launch_gemm_oz(st, op->t_blgx.as<GemmProb>() + z.px, z.nx, z.x, op->t_blex.as<int64_t>() + z.ex,
+                               op->t_ozx.as<int>(), op->t_ozd.p, op->t_blQ.as<double>(), op->t_blD.as<double>(),
                                op->t_blX.as<double>(), op->t_blX.as<double>()));
-        RS_CUDA(launch_gemm_oz(st, op->t_blgu.as<GemmProb>() + z.pu, z.nu, z.tu, op->t_bleu.as<int64_t>() + z.eu, z.lu,
-                               op->t_ozx.as<int>(), op->t_blX.as<double>(), op->t_blQ.as<double>(), A, A));
+        RS_CUDA(launch_gemm_oz(st, op->t_blgu.as<GemmProb>() + z.pu, z.nu, z.u, op->t_bleu.as<int64_t>() + z.eu,
+                               op->t_ozx.as<int>(), op->t_ozd.p, op->t_blX.as<double>(), op->t_blQ.as<double>(), A,
+                               A));
         RS_CUDA(launch_sweep_bl_write(st, nb, 64 * q, max_m, dm.as<int32_t>(), doff.as<int64_t>(), A,
                                       op->t_blq.as<int64_t>(), op->t_blX.as<double>(), op->t_blD.as<double>()));
     }
@@ -891,13 +892,14 @@ int inverse_level(rs_op* op, Level& L, const ChildRef& cref, cudaStream_t st)
                       const T* C0) -> int {
         if constexpr (std::is_same<T, double>::value) {
             std::vector<int64_t> eo;
-            const int64_t tiles = gemm_oz_plan(q, eo);
+            const OzPlan pl = gemm_oz_plan(q, eo);
             int rc2;
             if ((rc2 = upload(dq, q, st))) return rc2;
             if ((rc2 = upload(de, eo, st))) return rc2;
-            RS_CUDA(op->t_ozx.alloc(sizeof(int) * (size_t)(eo.back() + 1)));
-            RS_CUDA(launch_gemm_oz(st, dq.as<GemmProb>(), (int)q.size(), tiles, de.as<int64_t>(), eo.back(),
-                                   op->t_ozx.as<int>(), A, B, C, C0));
+            RS_CUDA(op->t_ozx.alloc(sizeof(int) * (size_t)(pl.lines + 1)));
+            RS_CUDA(op->t_ozd.alloc(2 * (size_t)(pl.digits + 8)));
+            RS_CUDA(launch_gemm_oz(st, dq.as<GemmProb>(), (int)q.size(), pl, de.as<int64_t>(), op->t_ozx.as<int>(),
+                                   op->t_ozd.p, A, B, C, C0));
             return RS_OK;
         } else {
             (void)q; (void)dq; (void)de; (void)A; (void)B; (void)C; (void)C0;

@@ -275,7 +275,7 @@ struct rs_op {
     rs::DevMem d_a, d_ucirc, d_status, d_bar, d_ipiv, d_pivrow, d_pb;
     // factor-time scratch reused across levels, released with the op
     rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2, t_ck, t_ce;
-    rs::DevMem t_oz1, t_oz2, t_ozo1, t_ozo2, t_ozx;     // digit-product GEMM: descriptors, exponent offsets and lines
+    rs::DevMem t_oz1, t_oz2, t_ozo1, t_ozo2, t_ozx, t_ozd;   // digit-product GEMM: descriptors, offsets, exponents, digits
     rs::DevMem t_blq, t_blQ, t_blX, t_blD, t_blmp, t_blgx, t_blgu, t_blex, t_bleu;   // blocked sweep
     rs::DevMem d_zero;                // one int64 zero: the first block of a one-problem launch
     // solve workspace (grown on demand)

@@ -51,11 +51,15 @@ struct GemmProb {
 // FP64 grouped GEMM from exact products of 7-bit digit slices on the bf16 tensor cores
 // (k_gemm_oz.cu): same descriptors and semantics as launch_gemm, T = double.  gemm_oz_plan
 // re-tiles the descriptors (64 x 32 tiles; `lower` problems keep every tile that touches the lower
-// triangle) and returns the tile count, with eoff[p] the first of problem p's M + N exponent
-// lines (eoff[np] in all); ex: eoff[np] ints of device scratch.
-int64_t gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff);
-cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, int64_t tiles, const int64_t* eoff,
-                           int64_t nlines, int* ex, const double* A, const double* B, double* C, const double* C0);
+// triangle) and fills eoff (2 (np + 1) entries: each problem's first exponent line, then its first
+// digit); the launch needs pl.lines ints (ex) and pl.digits bf16 values (digits) of device
+// scratch, and eoff on the device.
+struct OzPlan {
+    int64_t tiles, lines, digits;
+};
+OzPlan gemm_oz_plan(std::vector<GemmProb>& probs, std::vector<int64_t>& eoff);
+cudaError_t launch_gemm_oz(cudaStream_t st, const GemmProb* probs, int np, const OzPlan& pl, const int64_t* eoff,
+                           int* ex, void* digits, const double* A, const double* B, double* C, const double* C0);
 
 // Blocked symmetric sweep (k_sweep_bl.cu), FP64: sweep_bl_plan lays out the panel buffers (qoff:
 // 64 m_b doubles per matrix, row-major; returns the total) and the two digit-GEMM lists of every step (gx:
