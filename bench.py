@@ -43,8 +43,10 @@ PEAK_FP32_TFLOPS = 80.5
 ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
 # factor kernels and the profile classes (rs_op_profile) whose launches they are (the inverse
 # classes run the symmetric sweep on the Laplace workload)
-KERNEL_CLASSES = {"sweep_kernel": ("inv_F", "inv_E", "inv_root"), "cpqr_kernel+cpqr_bl_kernel": ("cpqr",),
-                  "gemm_kernel": ("gemm_E",), "id_T_kernel": ("id_T",)}
+KERNEL_CLASSES = {"sweep (sweep_bl_dinv_kernel + gemm_oz_kernel)": ("inv_F", "inv_E", "inv_root"),
+                  "cpqr_kernel+cpqr_bl_kernel": ("cpqr",), "gemm_oz_kernel": ("gemm_E",), "id_T_kernel": ("id_T",)}
+# the digit-slice GEMM forms each FP64 product from 36 bf16 digit products
+OZ_BF16_PER_FP64 = 36
 
 
 def _args():
@@ -666,8 +668,9 @@ def run_ours(args):
     opts.profile = 1
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     # the FP64 pipe's measured rate: the roofline peak of every FP64 kernel below
-    probe = {"dfma_tflops": P.rs_fp64_probe(P.RS_PROBE_DFMA, st), "dmma_tflops": P.rs_fp64_probe(P.RS_PROBE_DMMA, st)}
-    peak64 = max(probe.values())
+    probe = {"dfma_tflops": P.rs_fp64_probe(P.RS_PROBE_DFMA, st), "dmma_tflops": P.rs_fp64_probe(P.RS_PROBE_DMMA, st),
+             "bf16_mma_tflops": P.rs_fp64_probe(P.RS_PROBE_BF16_MMA, st)}
+    peak64 = max(probe["dfma_tflops"], probe["dmma_tflops"])
 
     def step():
         tree = P.rs_build_tree(pts, leaf)
@@ -782,7 +785,13 @@ def run_ours(args):
         "profile_tflops": {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in prof.items() if v[0] > 0 and v[1] > 0},
         "roofline_by_kernel": {k: {"achieved_tflops": kern[k][1] / (kern[k][0] * 1e-3) / 1e12,
                                    "frac_fp64": kern[k][1] / (kern[k][0] * 1e-3) / 1e12 / peak64,
-                                   "ms_per_step": kern[k][0] / K}
+                                   "ms_per_step": kern[k][0] / K,
+                                   **({"bf16_tflops": OZ_BF16_PER_FP64 * kern[k][1] / (kern[k][0] * 1e-3) / 1e12,
+                                       "frac_bf16_mma": OZ_BF16_PER_FP64 * kern[k][1] / (kern[k][0] * 1e-3) / 1e12
+                                       / probe["bf16_mma_tflops"],
+                                       "note": "FP64 products from exact bf16 digit products on mma.sync; "
+                                               "frac_fp64 above 1 is the gain over the FP64 pipe"}
+                                      if k == "gemm_oz_kernel" else {})}
                                for k in kern if kern[k][0] > 0},
         "e2e": {"value": world * N / e2e_s, "unit": "unknowns/s",
                 "step": "rs_build_tree + rs_factor + 4-RHS rs_solve from pinned host buffers, copies timed",

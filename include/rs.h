@@ -225,8 +225,10 @@ int rs_wait_check(int64_t limit, void* stream);
  * 32 and 64 warps per SM (DFMA: three chain layouts, eight chains sharing their operands or
  * four or two with their own); the best rate of three timed launches per shape (after one
  * warm-up, CUDA events on `stream`) gives *tflops_out (host).  Synchronous; allocates a few
- * KB of device memory. */
-enum { RS_PROBE_DFMA = 0, RS_PROBE_DMMA = 1 };
+ * KB of device memory.  RS_PROBE_BF16_MMA: mma.sync m16n8k16 bf16 products with FP32
+ * accumulation, the pipe that the FP64 products of opts.gemm_form = 1 run on (flops of the bf16
+ * products). */
+enum { RS_PROBE_DFMA = 0, RS_PROBE_DMMA = 1, RS_PROBE_BF16_MMA = 2 };
 int rs_fp64_probe(int kind, double* tflops_out, void* stream);
 /* Release an operator.  Returns RS_E_INVALID, and frees nothing, while a server (or one of
  * its requests) still references it; NULL is accepted. */

@@ -239,12 +239,13 @@ def rs_wait_check(limit, stream=None):
     _check(lib().rs_wait_check(int(limit), _stream(stream)))
 
 
-RS_PROBE_DFMA, RS_PROBE_DMMA = 0, 1
+RS_PROBE_DFMA, RS_PROBE_DMMA, RS_PROBE_BF16_MMA = 0, 1, 2
 
 
 def rs_fp64_probe(kind, stream=None):
-    """Measured FP64 throughput (TFLOP/s) of DFMA chains (RS_PROBE_DFMA) or mma.sync f64
-    matrix instructions (RS_PROBE_DMMA) on the current device."""
+    """Measured throughput (TFLOP/s) of DFMA chains (RS_PROBE_DFMA), mma.sync f64 matrix
+    instructions (RS_PROBE_DMMA) or bf16 mma.sync products (RS_PROBE_BF16_MMA) on the current
+    device."""
     out = C.c_double()
     _check(lib().rs_fp64_probe(int(kind), C.byref(out), _stream(stream)))
     return out.value

@@ -1,4 +1,4 @@
-// k_probe.cu -- throughput probes of the FP64 pipes this library's factorization runs on.
+// k_probe.cu -- throughput probes of the pipes this library's factorization runs on.
 //
 // The factor and the solve are FP64 dense linear algebra, so the roofline that bounds them is
 // the chip's FP64 rate, which GB300 gives through two routes: the FP64 FMA of the CUDA cores
@@ -7,7 +7,8 @@
 // that launch cost is negligible, at 16, 32 and 64 warps per SM, and returns the best rate
 // from CUDA-event timing.  The
 // larger of the two is the FP64 peak the benchmark divides by; their ratio decides which pipe
-// the FP64 contractions should use.
+// the FP64 contractions should use.  A third probe measures the bf16 mma.sync rate that the
+// digit-slice GEMM (k_gemm_oz.cu) runs its FP64 products on.
 #include <algorithm>
 
 #include "k_common.cuh"
@@ -82,6 +83,32 @@ __global__ void __launch_bounds__(PROBE_NT) dmma_probe_kernel(int iters, double 
     if (s == 12345.678) out[blockIdx.x] = s;
 }
 
+// bf16 mma.sync m16n8k16 with FP32 accumulation (the pipe of the digit-slice GEMM): 4
+// independent accumulations per warp, operands fixed fragments of small values.
+__global__ void __launch_bounds__(PROBE_NT) bf16_mma_probe_kernel(int iters, double* out)
+{
+    float d[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[q][e] = 0.0f;
+    const uint32_t a = 0x3f803f80u ^ (threadIdx.x & 1u), b = 0x3c003c00u;   // bf16 1.0 and 2^-7
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                         "{%8,%9}, {%0,%1,%2,%3};"
+                         : "+f"(d[q][0]), "+f"(d[q][1]), "+f"(d[q][2]), "+f"(d[q][3])
+                         : "r"(a), "r"(a), "r"(a), "r"(a), "r"(b), "r"(b));
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s += d[q][e];
+    if (s == 12345.678f) out[blockIdx.x] = s;
+}
+
 }  // namespace
 
 }  // namespace rs
@@ -90,7 +117,8 @@ using namespace rs;
 
 extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
 {
-    if (!tflops_out || (kind != RS_PROBE_DFMA && kind != RS_PROBE_DMMA)) return fail(RS_E_INVALID, "bad argument");
+    if (!tflops_out || (kind != RS_PROBE_DFMA && kind != RS_PROBE_DMMA && kind != RS_PROBE_BF16_MMA))
+        return fail(RS_E_INVALID, "bad argument");
     const cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     RS_CUDA(cudaGetDevice(&dev));
@@ -110,7 +138,8 @@ extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
     for (int per_sm = 2; per_sm <= 8; per_sm *= 2) {
         const int blocks = per_sm * sms;
         const int chains = kind != RS_PROBE_DFMA ? 1 : form == 0 ? PROBE_CHAINS : form == 1 ? 4 : 2;
-        const int iters = kind == RS_PROBE_DFMA ? 32768 * PROBE_CHAINS / chains / per_sm : 8192 / per_sm;
+        const int iters = kind == RS_PROBE_DFMA ? 32768 * PROBE_CHAINS / chains / per_sm
+                          : kind == RS_PROBE_DMMA ? 8192 / per_sm : 65536 / per_sm;
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, st);
             count_launches(1);
@@ -120,8 +149,10 @@ extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
                 dfma_probe2_kernel<4><<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
             else if (kind == RS_PROBE_DFMA)
                 dfma_probe2_kernel<2><<<blocks, PROBE_NT, 0, st>>>(iters, 0.9999999, 1e-7, out.as<double>());
-            else
+            else if (kind == RS_PROBE_DMMA)
                 dmma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, 1e-3, 1e-3, out.as<double>());
+            else
+                bf16_mma_probe_kernel<<<blocks, PROBE_NT, 0, st>>>(iters, out.as<double>());
             cudaEventRecord(e1, st);
             cudaError_t e = cudaEventSynchronize(e1);
             if (e != cudaSuccess) {
@@ -133,9 +164,11 @@ extern "C" int rs_fp64_probe(int kind, double* tflops_out, void* stream)
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep == 0 || ms <= 0.0f) continue;
             const double threads = (double)blocks * PROBE_NT;
-            // DFMA: 2 flops per FMA; DMMA: 8 x 8 x 4 FMAs = 512 flops per warp-instruction
+            // DFMA: 2 flops per FMA; DMMA: 8 x 8 x 4 FMAs = 512 flops per warp-instruction;
+            // bf16: 16 x 8 x 16 FMAs = 4096 flops per warp-instruction
             const double flops = kind == RS_PROBE_DFMA ? threads * iters * chains * 2.0
-                                                        : threads / 32.0 * iters * 4 * 512.0;
+                                 : kind == RS_PROBE_DMMA ? threads / 32.0 * iters * 4 * 512.0
+                                                         : threads / 32.0 * iters * 4 * 4096.0;
             best_rate = std::max(best_rate, flops / (ms * 1e-3) / 1e12);
         }
     }
