@@ -4,10 +4,10 @@
 // The sweep of a symmetric S on an index block K (D = S_KK) is
 //     S_KK <- -D^{-1},  S_OK <- S_OK D^{-1},  S_KO <- D^{-1} S_KO,  S_OO <- S_OO - S_OK D^{-1} S_KO,
 // so with Q = S[:, K] (the old panel, both triangles) and X = Q D^{-1}, one step is
-//   1. (copy kernel) Q, row-major, in 64 x 64 tiles; (one CTA per matrix) D^{-1} by the element
-//      sweep of the lower triangle of the 64 x 64 block D in shared memory, FP64, with the pivot
-//      test of k_sweep.cu (a pivot not above 1e3 unit roundoff times the largest earlier one sets
-//      DEV_NOT_SPD);
+//   1. (copy kernel) Q, row-major, in 64 x 64 tiles; (one CTA per matrix) D^{-1} by the sweep of
+//      the lower triangle of the 64 x 64 block D in pivot blocks of 8, in shared memory, FP64,
+//      with the pivot test of k_sweep.cu (a pivot not above 1e3 unit roundoff times the largest
+//      earlier one sets DEV_NOT_SPD);
 //   2. X = Q D^{-1} and S <- S - X Q^T on the tiles touching the lower triangle (both on the
 //      digit-slice GEMM: the m^3 flops of the inverse as 64-deep products);
 //   3. (write kernel) the rows and columns of K, which step 2 left meaningless: S[i, K] = X[i, :]
@@ -66,17 +66,21 @@ __global__ void __launch_bounds__(256) sweep_bl_copy_kernel(int k0, const int32_
     }
 }
 
-// D^{-1} of the panel's diagonal block D = Q[k0 .. k0 + w) by the element sweep of its lower
-// triangle in shared memory, FP64, with the pivot test of k_sweep.cu; one CTA per matrix.  Step t:
-// 64 threads take the pivot column c_r = D(r, t) and u_r = c_r / D(t, t); then every lower entry
-// (r, s) off row and column t becomes D(r, s) - u_r c_s in place, and row / column t become u.
+// D^{-1} of the panel's diagonal block D = Q[k0 .. k0 + w) by the sweep of its lower triangle in
+// pivot blocks of 8, in shared memory, FP64, with the pivot test of k_sweep.cu (the element sweep
+// of each 8 x 8 pivot block by one warp); one CTA per matrix.  Block J: C = D(:, J) (old), the
+// warp sweeps P = D(J, J) into P^{-1}, U = C P^{-1}, then every lower entry (r, s) off J becomes
+// D(r, s) - U(r, :) C(s, :)^T, the entries of J's rows and columns U, and D(J, J) = -P^{-1}:
+// three block barriers per 8 pivots instead of two per pivot.
 __global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_t* __restrict__ msz,
         const int64_t* __restrict__ qoff, const double* __restrict__ Qall, double* __restrict__ Dall,
         double* __restrict__ maxp, int* __restrict__ status)
 {
+    constexpr int PB = 8;
     __shared__ double sM[BS][BS + 1];
-    __shared__ double s_c[BS], s_u[BS];
+    __shared__ double s_col[BS][PB + 1], s_U[BS][PB + 1], s_P[PB][PB + 1];
     __shared__ int s_fail;
+    __shared__ double s_mp;
     const int b = blockIdx.x;
     const int m = msz[b];
     if (k0 >= m) return;
@@ -86,9 +90,10 @@ __global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_
         const int r = e / BS, c = e - r * BS;
         sM[r][c] = (r < w && c < w) ? Q[e] : (r == c ? 1.0 : 0.0);
     }
-    if (threadIdx.x == 0) s_fail = 0;
-    double mp = maxp[b];
-    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        s_mp = maxp[b];
+    }
     // the lower entries of this thread: e = tid + 256 u over the 2080 of the 64 x 64 triangle
     constexpr int NL = BS * (BS + 1) / 2, PER = (NL + 255) / 256;
     int er[PER], ec[PER];
@@ -101,27 +106,81 @@ __global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_
         er[u] = e < NL ? r : -1;
         ec[u] = e - r * (r + 1) / 2;
     }
-    for (int t = 0; t < w; ++t) {
-        const double p = sM[t][t];
-        if (threadIdx.x == 0 && (!(p > 1e3 * 0.5 * DBL_EPSILON * mp) || !isfinite(p))) s_fail = 1;
-        mp = fmax(mp, p);
-        if (threadIdx.x < BS) {
-            const int r = threadIdx.x;
-            const double c = r >= t ? sM[r][t] : sM[t][r];
-            s_c[r] = c;
-            s_u[r] = c * (1.0 / p);
+    __syncthreads();
+    const int nblk = (w + PB - 1) / PB;
+    for (int J = 0; J < nblk; ++J) {
+        const int j0 = J * PB;
+        // 1. C = D(:, J), from the lower triangle
+        for (int e = threadIdx.x; e < BS * PB; e += 256) {
+            const int r = e / PB, t = e - r * PB, c = j0 + t;
+            s_col[r][t] = r >= c ? sM[r][c] : sM[c][r];
         }
         __syncthreads();
+        // 2. warp 0: the element sweep of P = C(J, :) in s_P into -P^{-1}, the pivot test
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double mp = s_mp;
+            int fail = 0;
+            int rr[2], cc[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                rr[u] = (lane + 32 * u) / PB;
+                cc[u] = (lane + 32 * u) % PB;
+                s_P[rr[u]][cc[u]] = s_col[j0 + rr[u]][cc[u]];
+            }
+            __syncwarp();
+            for (int t = 0; t < PB; ++t) {
+                const double p = s_P[t][t];
+                if (!(p > 1e3 * 0.5 * DBL_EPSILON * mp) || !isfinite(p)) fail = 1;
+                mp = fmax(mp, p);
+                const double pinv = 1.0 / p;
+                double nv[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int r = rr[u], c = cc[u];
+                    if (r == t && c == t) nv[u] = -pinv;
+                    else if (r == t) nv[u] = s_P[t][c] * pinv;
+                    else if (c == t) nv[u] = s_P[r][t] * pinv;
+                    else nv[u] = fma(-s_P[r][t] * pinv, s_P[t][c], s_P[r][c]);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < 2; ++u) s_P[rr[u]][cc[u]] = nv[u];
+                __syncwarp();
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) s_P[rr[u]][cc[u]] = -s_P[rr[u]][cc[u]];     // P^{-1}
+            if (lane == 0) {
+                s_mp = mp;
+                if (fail) s_fail = 1;
+            }
+        }
+        __syncthreads();
+        // 3. U = C P^{-1}
+        for (int e = threadIdx.x; e < BS * PB; e += 256) {
+            const int r = e / PB, t = e - r * PB;
+            double a = 0.0;
+#pragma unroll
+            for (int q = 0; q < PB; ++q) a = fma(s_col[r][q], s_P[q][t], a);
+            s_U[r][t] = a;
+        }
+        __syncthreads();
+        // 4. the lower entries
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int r = er[u], c = ec[u];
             if (r < 0) continue;
-            double v;
-            if (r == t && c == t) v = -1.0 / p;
-            else if (r == t) v = s_u[c];
-            else if (c == t) v = s_u[r];
-            else v = fma(-s_u[r], s_c[c], sM[r][c]);
-            sM[r][c] = v;
+            const bool rin = r >= j0 && r < j0 + PB, cin = c >= j0 && c < j0 + PB;
+            double x;
+            if (rin && cin) x = -s_P[r - j0][c - j0];
+            else if (cin) x = s_U[r][c - j0];
+            else if (rin) x = s_U[c][r - j0];
+            else {
+                x = sM[r][c];
+#pragma unroll
+                for (int t = 0; t < PB; ++t) x = fma(-s_U[r][t], s_col[c][t], x);
+            }
+            sM[r][c] = x;
         }
         __syncthreads();
     }
@@ -131,7 +190,7 @@ __global__ void __launch_bounds__(256) sweep_bl_dinv_kernel(int k0, const int32_
         Dinv[e] = (r < w && c < w) ? -(r >= c ? sM[r][c] : sM[c][r]) : 0.0;
     }
     if (threadIdx.x == 0) {
-        maxp[b] = mp;
+        maxp[b] = s_mp;
         if (s_fail) atomicOr(status, DEV_NOT_SPD);
     }
 }
