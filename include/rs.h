@@ -140,11 +140,13 @@ typedef struct {
                                     operator), rs_residual and rs_bicgstab's matvec, not
                                     rs_solve.  Not with translation_invariant, k_cut or
                                     per_box                                           [0]    */
-    int gemm_form;               /* products forming E (Algorithm 1) of RS_FP64 operators:
-                                    1 = exact products of 7-bit digit slices on the bf16
-                                    tensor cores, summed in integers (one rounding per
-                                    entry; parts below 2^-56 of the row and column maxima
-                                    left out); 0 = FP64 FMA tiles                     [1]    */
+    int gemm_form;               /* dense products of RS_FP64 operators (E of Algorithm 1,
+                                    the inverses of F, E and the root in panels of 64, the
+                                    block updates of T = R11^{-1} R12): 1 = exact products
+                                    of 7-bit digit slices on the bf16 tensor cores, summed
+                                    in integers (one rounding per entry; parts below 2^-56
+                                    of the row and column maxima left out); 0 = FP64 FMA
+                                    tiles and the element sweep                       [1]    */
 } rs_opts;
 
 void rs_opts_default(rs_opts* opts);

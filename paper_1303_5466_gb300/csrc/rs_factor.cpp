@@ -638,7 +638,56 @@ int id_core(rs_op* op, Level& L, IdWork& w, cudaStream_t st, const KernelK& K, c
     {
     ProfScope ps(op, RS_PROF_ID_T, st, t_work, sizeof(T) * (double)L.t_off[nb]);
     const bool pb = op->opts.per_box != 0;
-    for (int b0 = 0; b0 < nb; b0 += pb ? 1 : nb) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (!pb && op->opts.gemm_form == 1) {
+            // blocks of 64 rows of R11, the updates on the digit-slice GEMM
+            std::vector<int64_t> rgoff;
+            std::vector<std::vector<GemmProb>> gs;
+            const size_t rgn = idt_bl_plan(nb, L.m, L.k, L.max_k, rgoff, gs);
+            std::vector<GemmProb> ag;
+            std::vector<int64_t> eg;
+            struct StepI { size_t pg, eg; OzPlan pl; int n; };
+            std::vector<StepI> si(gs.size());
+            int64_t max_lines = 1, max_digits = 1, max_km = 0, max_kres = 0;
+            for (size_t q = 0; q < gs.size(); ++q) {
+                std::vector<int64_t> eo;
+                si[q].pg = ag.size(); si[q].eg = eg.size(); si[q].n = (int)gs[q].size();
+                si[q].pl = gemm_oz_plan(gs[q], eo);
+                ag.insert(ag.end(), gs[q].begin(), gs[q].end());
+                eg.insert(eg.end(), eo.begin(), eo.end());
+                max_lines = std::max(max_lines, si[q].pl.lines);
+                max_digits = std::max(max_digits, si[q].pl.digits);
+            }
+            for (int b = 0; b < nb; ++b) {
+                max_km = std::max<int64_t>(max_km, L.k[b] * L.m[b]);
+                max_kres = std::max<int64_t>(max_kres, L.k[b] * (L.m[b] - L.k[b]));
+            }
+            if ((rc = upload(op->t_idrg, rgoff, st))) return rc;
+            if ((rc = upload(op->t_idg, ag, st))) return rc;
+            if ((rc = upload(op->t_ide, eg, st))) return rc;
+            RS_CUDA(op->t_idR.alloc(sizeof(double) * (rgn + 1)));
+            RS_CUDA(op->t_ozx.alloc(sizeof(int) * (size_t)max_lines));
+            RS_CUDA(op->t_ozd.alloc(2 * (size_t)(max_digits + 8)));
+            RS_CUDA(launch_idt_gather(st, nb, max_km, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(), w.nn.as<int32_t>(),
+                                      P, w.y_off.as<int64_t>(), w.Y.as<double>(), w.piv.as<int32_t>(),
+                                      w.diag.as<double>(), w.rscol.as<int32_t>(), op->t_idrg.as<int64_t>(),
+                                      op->t_idR.as<double>()));
+            for (size_t q = 0; q < gs.size(); ++q) {
+                RS_CUDA(launch_idt_solve(st, nb, (int)q, max_res, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(),
+                                         op->t_idrg.as<int64_t>(), op->t_idR.as<double>()));
+                if (si[q].n > 0)
+                    RS_CUDA(launch_gemm_oz(st, op->t_idg.as<GemmProb>() + si[q].pg, si[q].n, si[q].pl,
+                                           op->t_ide.as<int64_t>() + si[q].eg, op->t_ozx.as<int>(), op->t_ozd.p,
+                                           op->t_idR.as<double>(), op->t_idR.as<double>(), op->t_idR.as<double>(),
+                                           op->t_idR.as<double>()));
+            }
+            RS_CUDA(launch_idt_scatter(st, nb, max_kres, L.d_act_off.as<int64_t>(), L.d_k.as<int32_t>(),
+                                       w.skpos.as<int32_t>(), op->t_idrg.as<int64_t>(), op->t_idR.as<double>(),
+                                       L.d_t_off.as<int64_t>(), L.d_T.as<double>()));
+        }
+    }
+    const bool idt_bl = std::is_same<T, double>::value && !pb && op->opts.gemm_form == 1;
+    for (int b0 = 0; !idt_bl && b0 < nb; b0 += pb ? 1 : nb) {
         const int cnt = pb ? 1 : nb;
         RS_CUDA(launch_id_T<T>(st, cnt, L.d_act_off.as<int64_t>() + b0, L.d_k.as<int32_t>() + b0,
                                w.nn.as<int32_t>() + b0, P, w.y_off.as<int64_t>() + b0, w.Y.as<T>(),

@@ -277,6 +277,7 @@ struct rs_op {
     rs::DevMem t_ipoff, t_pboff, t_cta, t_W, t_p1, t_p2, t_k32, t_q1, t_q2, t_ck, t_ce;
     rs::DevMem t_oz1, t_oz2, t_ozo1, t_ozo2, t_ozx, t_ozd;   // digit-product GEMM: descriptors, offsets, exponents, digits
     rs::DevMem t_blq, t_blQ, t_blX, t_blD, t_blmp, t_blgx, t_blgu, t_blex, t_bleu;   // blocked sweep
+    rs::DevMem t_idrg, t_idR, t_idg, t_ide;            // blocked id_T: offsets, [R11 | R12], GEMM lists
     rs::DevMem d_zero;                // one int64 zero: the first block of a one-problem launch
     // solve workspace (grown on demand)
     rs::DevMem s_u, s_w, s_g, s_phi, s_t, s_z, s_in, s_out, s_out2;

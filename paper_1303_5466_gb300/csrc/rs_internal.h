@@ -75,6 +75,20 @@ cudaError_t launch_sweep_bl_write(cudaStream_t st, int nb, int k0, int max_m, co
 template <class T>
 cudaError_t launch_sweep_finish(cudaStream_t st, int nb, const int32_t* m, const int64_t* off, T* A, int max_m);
 
+// T = R11^{-1} R12 by blocks of 64 rows with the updates on the digit-slice GEMM (k_idt_bl.cu,
+// FP64): idt_bl_plan lays out the gathered [R11 | R12] blocks (rg_off, k m doubles per box,
+// returns the total) and the GEMM list of every step; per step one solve launch and the GEMM.
+size_t idt_bl_plan(int nb, const std::vector<int64_t>& m, const std::vector<int64_t>& k, int max_k,
+                   std::vector<int64_t>& rg_off, std::vector<std::vector<GemmProb>>& gs);
+cudaError_t launch_idt_gather(cudaStream_t st, int nb, int64_t max_km, const int64_t* act_off, const int32_t* kk,
+                              const int32_t* nnear, int P, const int64_t* y_off, const double* Y, const int32_t* piv,
+                              const double* diag, const int32_t* rscol, const int64_t* rg_off, double* Rg);
+cudaError_t launch_idt_solve(cudaStream_t st, int nb, int q, int max_res, const int64_t* act_off, const int32_t* kk,
+                             const int64_t* rg_off, double* Rg);
+cudaError_t launch_idt_scatter(cudaStream_t st, int nb, int64_t max_kres, const int64_t* act_off, const int32_t* kk,
+                               const int32_t* skpos, const int64_t* rg_off, const double* Rg, const int64_t* t_off,
+                               double* Tout);
+
 // Batched matrix-vector(s) descriptor: y = alpha * op(A) x + beta * y, A column-major
 // (rows x cols, ld), x and y point-major (entry p of RHS c at p * nrhs + c); x_off and y_off
 // count points (rows), so one descriptor serves every nrhs.
