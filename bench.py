@@ -44,7 +44,8 @@ ORACLE_LEVELS = 3          # oracle sample: the three finest tree levels
 # factor kernels and the profile classes (rs_op_profile) whose launches they are (the inverse
 # classes run the symmetric sweep on the Laplace workload)
 KERNEL_CLASSES = {"sweep (sweep_bl_dinv_kernel + gemm_oz_kernel)": ("inv_F", "inv_E", "inv_root"),
-                  "cpqr_kernel+cpqr_bl_kernel": ("cpqr",), "gemm_oz_kernel": ("gemm_E",), "id_T_kernel": ("id_T",)}
+                  "cpqr_kernel+cpqr_bl_kernel": ("cpqr",), "gemm_oz_kernel": ("gemm_E",),
+                  "id_T (idt_solve_kernel + gemm_oz_kernel)": ("id_T",)}
 # the digit-slice GEMM forms each FP64 product from 36 bf16 digit products
 OZ_BF16_PER_FP64 = 36
 
