@@ -18,6 +18,7 @@
 // 32 digits staged in shared memory, split from FP64 tiles that cp.async brings in during the
 // previous stage's products.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -248,8 +249,11 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
                                                                     ((st & 1) * OZ_BUF + OZ_S * OZ_BM * OZ_LD));
 #pragma unroll
         for (int ks = 0; ks < OZ_BK; ks += 16) {
-#pragma unroll
-            for (int i = 0; i < OZ_S; ++i) {
+            // A slices in the order 7, 0, 4, 1, 5, 2, 6, 3 (compile-time, so the level sums stay in
+            // registers): with the B slices ascending inside, two products into the same level
+            // sum are at least two pairs apart
+            auto slice = [&](auto Ic) {
+                constexpr int i = decltype(Ic)::value;
                 uint32_t a[4];
                 a[0] = *(const uint32_t*)&As[i][wm + g][ks + 2 * q];
                 a[1] = *(const uint32_t*)&As[i][wm + g + 8][ks + 2 * q];
@@ -264,7 +268,15 @@ __global__ void __launch_bounds__(OZ_NT, 2) gemm_oz_kernel(const GemmProb* __res
                         oz_mma(S[i + j][n], a, b0, b1);
                     }
                 }
-            }
+            };
+            slice(std::integral_constant<int, 7>{});
+            slice(std::integral_constant<int, 0>{});
+            slice(std::integral_constant<int, 4>{});
+            slice(std::integral_constant<int, 1>{});
+            slice(std::integral_constant<int, 5>{});
+            slice(std::integral_constant<int, 2>{});
+            slice(std::integral_constant<int, 6>{});
+            slice(std::integral_constant<int, 3>{});
         }
         __syncthreads();                 // buffer st & 1 is free for stage st + 2
         if ((k0 + OZ_BK) % OZ_CHUNK == 0 || k0 + OZ_BK >= P.K) {
