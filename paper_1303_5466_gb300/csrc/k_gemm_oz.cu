@@ -1,5 +1,7 @@
 // k_gemm_oz.cu -- FP64 grouped GEMM from exact products of 7-bit digit slices on the bf16 tensor
-// cores (the E products of Algorithm 1: W = Phi_{:,r} T^T + Phi_{:,s}, E^{-1} = T W_r + W_s).
+// cores: the E products of Algorithm 1 (W = Phi_{:,r} T^T + Phi_{:,s}, E^{-1} = T W_r + W_s), the
+// rank-64 updates of the blocked sweep (k_sweep_bl.cu) and of the blocked T = R11^{-1} R12
+// (k_idt_bl.cu).
 //
 // This GPU runs FP64 FMAs at 1.2 TFLOP/s and bf16 tensor-core products (mma.sync, FP32
 // accumulation) at 0.6 PFLOP/s.  Each FP64 entry is written as a sum of eight signed 7-bit
@@ -13,10 +15,10 @@
 // FP64 FMAs.  Levels above 7 (products below 2^-56 of the row and column maxima) are left out:
 // the result differs from the exact product by at most about K 2^-56 max|A_i,:| max|B_:,j|.
 //
-// Launch: one warp per row of A and per column of B finds its exponent first; then one CTA of
-// 8 warps per 64 x 32 tile of C, the warps 16 x 16 each (two m16n8k16 tiles), K in stages of
-// 32 digits staged in shared memory, split from FP64 tiles that cp.async brings in during the
-// previous stage's products.
+// Launch: one warp per row of A and per column of B finds its exponent and writes the line's
+// digits (slice-major bf16, K padded to 32); then one CTA of 8 warps per 64 x 32 tile of C, the
+// warps 16 x 16 each (two m16n8k16 tiles), K in stages of 16 digits that cp.async copies into
+// one of two shared-memory buffers while the previous stage's products run.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
