@@ -118,3 +118,30 @@ def test_compression_orders_match_oracle(rs, oracle_mod, n, leaf):
             rs.rs_tree_box_order(t, 1, 0, 0, np.array([n * n], dtype=np.int64))
     finally:
         rs.rs_free_tree(t)
+
+
+def test_struct_layouts_match_the_header(rs, tmp_path):
+    """The ctypes mirrors of rs_kernel, rs_opts, rs_stats and rs_tune_report have the size and the
+    field offsets that a C compiler gives the structs of include/rs.h (a field missing on either
+    side, or out of order, fails), and rs_opts_default fills the documented defaults of the
+    fields added last."""
+    import subprocess
+    structs = [rs.rs_kernel, rs.rs_opts, rs.rs_stats, rs.rs_tune_report]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rs.h"', "int main(void) {"]
+    for S in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (S.__name__, S.__name__))
+        for name, _ in S._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (S.__name__, name, S.__name__, name))
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    for S in structs:
+        assert int(out[S.__name__]) == C.sizeof(S), S.__name__
+        for name, _ in S._fields_:
+            assert int(out["%s.%s" % (S.__name__, name)]) == getattr(S, name).offset, (S.__name__, name)
+    o = rs.rs_opts_default()
+    assert o.gemm_form == 1 and o.forward_only == 0 and o.cpqr_variant == -1
