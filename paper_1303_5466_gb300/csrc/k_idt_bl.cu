@@ -4,9 +4,9 @@
 //   1. (gather) R = [R11 | R12] of every box into a k x m column-major block (R11 from the pivot
 //      columns of Y, its diagonal from diag; R12 from the residual columns);
 //   2. for the blocks J of 64 rows from the bottom of R11: (solve) X_J = R_JJ^{-1} B_J in place,
-//      one warp per right-hand side, the rows of J held by the lanes, the reciprocals of R_JJ's
-//      diagonal taken once per block; (digit-slice GEMM) B_I <- B_I - R_IJ X_J for the rows I
-//      above J;
+//      one thread per right-hand side with the block's rows in registers, the reciprocals of
+//      R_JJ's diagonal taken once per block; (digit-slice GEMM) B_I <- B_I - R_IJ X_J for the rows
+//      I above J;
 //   3. (scatter) T in the layout of id_T_kernel: rows by sorted skeleton position, columns by
 //      residual rank.
 #include <algorithm>
@@ -41,9 +41,11 @@ __global__ void __launch_bounds__(256) idt_gather_kernel(const int64_t* __restri
     }
 }
 
-// Step q: the block J = [j0, j1), j1 = k - 64 q, of every box with j1 > 0; 64 right-hand sides per
-// CTA, 8 per warp, each solved by the whole warp (lane l holds rows j0 + l and j0 + l + 32).
-__global__ void __launch_bounds__(256) idt_solve_kernel(int q, const int64_t* __restrict__ act_off,
+// Step q: the block J = [j0, j1), j1 = k - 64 q, of every box with j1 > 0; one right-hand side per
+// thread, 64 per CTA, its 64 rows in registers (the block padded with the identity beyond w, so
+// every loop has compile-time bounds), R_JJ and the reciprocals of its diagonal in shared memory
+// (read by all threads at once): every FMA of the substitution does useful work.
+__global__ void __launch_bounds__(IB) idt_solve_kernel(int q, const int64_t* __restrict__ act_off,
         const int32_t* __restrict__ kk, const int64_t* __restrict__ rg_off, double* __restrict__ Rg)
 {
     __shared__ double sR[IB][IB + 1];
@@ -56,31 +58,31 @@ __global__ void __launch_bounds__(256) idt_solve_kernel(int q, const int64_t* __
     const int cb = blockIdx.x * IB;
     if (cb >= nres) return;
     const double* R = Rg + rg_off[b];
-    for (int e = threadIdx.x; e < IB * IB; e += 256) {
+    for (int e = threadIdx.x; e < IB * IB; e += IB) {
         const int l = e / IB, i = e - l * IB;              // column l, row i of R_JJ
-        sR[i][l] = (i < w && l < w && i <= l) ? R[(int64_t)(j0 + l) * k + j0 + i] : 0.0;
+        double v = 0.0;
+        if (i < w && l < w) v = i <= l ? R[(int64_t)(j0 + l) * k + j0 + i] : 0.0;
+        else if (i == l) v = 1.0;
+        sR[i][l] = v;
     }
     __syncthreads();
-    if (threadIdx.x < IB) sInv[threadIdx.x] = threadIdx.x < w ? 1.0 / sR[threadIdx.x][threadIdx.x] : 0.0;
+    sInv[threadIdx.x] = 1.0 / sR[threadIdx.x][threadIdx.x];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* B = Rg + rg_off[b] + (int64_t)k * k;          // R12, k x nres column-major
-    for (int cc = warp; cc < IB; cc += 8) {
-        const int c = cb + cc;
-        if (c >= nres) break;
-        double* col = B + (int64_t)c * k + j0;
-        double x0 = lane < w ? col[lane] : 0.0, x1 = lane + 32 < w ? col[lane + 32] : 0.0;
-        for (int i = w - 1; i >= 0; --i) {
-            const double xi = __shfl_sync(0xffffffffu, i >= 32 ? x1 : x0, i & 31);
-            const double t = xi * sInv[i];
-            if (lane == i) x0 = t;
-            if (lane + 32 == i) x1 = t;
-            if (lane < i) x0 = fma(-sR[lane][i], t, x0);
-            if (lane + 32 < i) x1 = fma(-sR[lane + 32][i], t, x1);
-        }
-        if (lane < w) col[lane] = x0;
-        if (lane + 32 < w) col[lane + 32] = x1;
+    const int c = cb + threadIdx.x;
+    if (c >= nres) return;
+    double* col = Rg + rg_off[b] + (int64_t)k * k + (int64_t)c * k + j0;   // column c of R12, rows J
+    double x[IB];
+#pragma unroll
+    for (int i = 0; i < IB; ++i) x[i] = i < w ? col[i] : 0.0;
+#pragma unroll
+    for (int i = IB - 1; i >= 0; --i) {
+        x[i] *= sInv[i];
+#pragma unroll
+        for (int l = 0; l < i; ++l) x[l] = fma(-sR[l][i], x[i], x[l]);
     }
+#pragma unroll
+    for (int i = 0; i < IB; ++i)
+        if (i < w) col[i] = x[i];
 }
 
 __global__ void __launch_bounds__(256) idt_scatter_kernel(const int64_t* __restrict__ act_off,
@@ -143,8 +145,8 @@ cudaError_t launch_idt_solve(cudaStream_t st, int nb, int q, int max_res, const 
 {
     if (nb <= 0 || max_res <= 0) return cudaSuccess;
     count_launches(1);
-    idt_solve_kernel<<<dim3((unsigned)((max_res + IB - 1) / IB), (unsigned)nb), 256, 0, st>>>(q, act_off, kk, rg_off,
-                                                                                               Rg);
+    idt_solve_kernel<<<dim3((unsigned)((max_res + IB - 1) / IB), (unsigned)nb), IB, 0, st>>>(q, act_off, kk, rg_off,
+                                                                                              Rg);
     return cudaGetLastError();
 }
 
